@@ -1,0 +1,227 @@
+/*
+ * memd.h -- C ABI of the GB300 (sm_103a) MEMD library: local Maxwell
+ * Equations Molecular Dynamics for Coulomb interactions in an inhomogeneous
+ * dielectric (Fahrenberger & Holm, "Computing Coulomb Interaction in
+ * Inhomogeneous Dielectric Media via a Local Electrostatics Lattice
+ * Algorithm").
+ *
+ * Model.  A periodic mesh of N[0] x N[1] x N[2] cubic cells of edge
+ * a = box[d] / N[d] carries the displacement field D on its links, the
+ * magnetic field B on its plaquettes and 1/eps on its links (Sec. II,
+ * Fig. 2).  Point charges move through it; every step the plaquettes follow
+ * dB/dt = -curl(D/eps) (Eq. 21), the links follow dD/dt = c^2 curl B - j
+ * (Eq. 20), the current j is the exact charge transfer of each move, kept in
+ * an int64 fixed-point ledger so that div D = rho holds exactly, and the
+ * charges feel F = qE (Eq. 18 without v x B) with the self-energy (Sec. III)
+ * and global-dipole (Sec. V) corrections.  Units: eps0 = 1, so the Coulomb
+ * potential of a charge is q / (4 pi eps r).
+ *
+ * Layout.  Vertex v = (i, j, k) has flat index i + N0 (j + N1 k).  Link
+ * (d, v) joins v to v + e_d; plaquette (d, v) has normal e_d and spans
+ * e_{d+1}, e_{d+2} from v.  Field arrays crossing this ABI are FP64,
+ * component major: element (d, v) at d * V + v, V = N0 N1 N2.  Particle
+ * arrays are n x 3, row major.  Fixed point: S = 2^16 sub-cell steps per cell
+ * edge; the ledger unit is e 2^-48.
+ *
+ * Conventions.  Every call returns a memd_status and never throws.  The
+ * caller owns every pointer it passes; the library copies inputs before the
+ * call returns and writes outputs into caller buffers, which are host memory
+ * unless a name says "device".  One context is used by one host thread at a
+ * time and issues all its GPU work on one CUDA stream.  memd_last_error()
+ * gives a one-line reason for the last failure.
+ */
+#ifndef MEMD_H
+#define MEMD_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct memd_ctx memd_ctx;
+
+typedef enum memd_status {
+  MEMD_OK = 0,
+  MEMD_ERR_INVALID = 1,       /* bad argument or state for this call */
+  MEMD_ERR_COURANT = 2,       /* c dt sqrt(3) >= a (Eq. 30) */
+  MEMD_ERR_OOM = 3,           /* device allocation failed */
+  MEMD_ERR_CUDA = 4,          /* a CUDA call failed */
+  MEMD_ERR_CELL_JUMP = 5,     /* a charge moved by more than one cell in a step */
+  MEMD_ERR_GAUSS = 6,         /* the ledger does not close (non-neutral scan) */
+  MEMD_ERR_RELAX_NOCONV = 7,  /* the relaxation did not reach its tolerance */
+  MEMD_ERR_DIPOLE_DRIFT = 8,  /* reserved: dipole correction outgrew the force */
+  MEMD_ERR_TIMEOUT = 9,       /* reserved: a bounded wait gave up */
+  MEMD_ERR_STATE = 10,        /* call out of order (e.g. step before init) */
+  MEMD_ERR_OVERFLOW = 11      /* fixed-point range exceeded */
+} memd_status;
+
+enum { MEMD_FP64 = 0, MEMD_FP32 = 1 };                 /* link/plaquette fields */
+enum { MEMD_SELF_NONE = 0, MEMD_SELF_GF = 1, MEMD_SELF_DIRECT = 2 };
+
+/* Permittivity profiles (Sec. II, Fig. 2b).  A link takes the mean of its
+ * end values; analytic profiles are sampled at the link midpoint. */
+enum {
+  MEMD_EPS_CONST = 0,     /* params[0] = eps */
+  MEMD_EPS_LINKS = 1,     /* values[3 V]: eps per link, component major */
+  MEMD_EPS_VERTICES = 2,  /* values[V]: eps per vertex */
+  MEMD_EPS_TANH = 3,      /* eps = p0 + p1 tanh((|s - p2| - p3) / p4), s = periodic
+                             distance along `axis` */
+  MEMD_EPS_SIN = 4        /* eps = p0 + p1 sin(2 pi s / L_axis + p2) */
+};
+
+typedef struct memd_eps_profile {
+  int32_t kind;
+  int32_t axis;
+  const double *values; /* caller owned, copied at create; may be NULL */
+  double params[8];
+} memd_eps_profile;
+
+/* Optional device allocator (e.g. a framework's caching allocator).  alloc
+ * returns a device pointer of at least `bytes` usable on `stream`, or NULL.
+ * When alloc is NULL the library uses cudaMalloc / cudaFree. */
+typedef void *(*memd_alloc_fn)(void *user, size_t bytes, void *stream);
+typedef void (*memd_free_fn)(void *user, void *ptr, size_t bytes, void *stream);
+
+typedef struct memd_options {
+  int32_t precision;      /* MEMD_FP64 | MEMD_FP32 for D, B, 1/eps and the gather */
+  int32_t self_mode;      /* MEMD_SELF_* (Sec. III) */
+  int32_t dipole_corr;    /* 1: metallic k = 0 correction (Sec. V) */
+  int32_t relax_max_iter; /* cap on relaxation iterations */
+  double relax_tol;       /* stop when max|circulation of E| <= tol max|E| */
+  uint64_t seed;          /* Langevin noise key */
+  void *cuda_stream;      /* cudaStream_t to issue work on; NULL = own stream */
+  int32_t device;         /* CUDA device ordinal; -1 = current */
+  int32_t use_graphs;     /* 1: memd_step replays a captured CUDA graph */
+  memd_alloc_fn alloc;
+  memd_free_fn free;
+  void *alloc_user;
+  int32_t time_kernels;   /* 1: CUDA events around the field kernels, see
+                             memd_get_kernel_stats */
+  int32_t reserved[7];
+} memd_options;
+
+typedef struct memd_thermostat {
+  double gamma; /* friction rate; Langevin force -gamma m v + sqrt(2 gamma m kT / dt) xi */
+  double kT;
+} memd_thermostat;
+
+typedef struct memd_energy_terms {
+  double kinetic;        /* sum m v^2 / 2 */
+  double electric;       /* a^3 sum D^2 / (2 eps) */
+  double magnetic;       /* (c^2 a^3 / 2) sum B^{n+1/2} B^{n+3/2} */
+  double self;           /* sum of the self energies the correction removes */
+  double dipole;         /* P eps_eff^-1 P / (2 V) removed by the dipole correction */
+  double total;          /* kinetic + electric + magnetic - self - dipole */
+  double P[3];           /* dipole moment of the unfolded charges */
+  double gauss_residual; /* max_v |a^2 div D - Q_v| in units of e */
+  int32_t gauss_exact;   /* 1 when the ledger satisfies div Lg == Q exactly */
+  int32_t pad;
+  int64_t step;          /* steps taken since memd_init_field */
+} memd_energy_terms;
+
+typedef struct memd_kernel_stats {
+  double field_ms;        /* summed CUDA-event time of the field (curl) kernels */
+  int64_t field_launches; /* launches timed */
+  double field_bytes;     /* algorithmic bytes per field launch */
+  int64_t launches_per_step;
+} memd_kernel_stats;
+
+/* Fill *opt with defaults: FP64, GF self term, dipole correction on,
+ * relax_tol 1e-12, 200000 iterations, seed 0, own stream, graphs on. */
+void memd_default_options(memd_options *opt);
+
+/* One-line text of a status code. */
+const char *memd_status_string(memd_status s);
+
+/* Reason for the last failure on ctx (empty string when none; a static
+ * message when ctx is NULL). */
+const char *memd_last_error(const memd_ctx *ctx);
+
+/* Create a context (Sec. II, Sec. III, Sec. V).  mesh: N[d] >= 2; box: edge
+ * lengths, cubic cells required (box[d] / N[d] equal); eps: profile mapped to
+ * the links on the device; c_light, dt > 0 with c dt sqrt(3) < a (Eq. 30).
+ * Computes 1/eps per link, the lattice Green's table and the effective
+ * permittivity tensor.  Allocates all field memory.  On failure *out is NULL.
+ * Errors: INVALID, COURANT, OOM, CUDA, RELAX_NOCONV. */
+memd_status memd_create(const int32_t mesh[3], const double box[3],
+                        const memd_eps_profile *eps, double c_light, double dt,
+                        const memd_options *opt, memd_ctx **out);
+
+/* Release every device resource of ctx (NULL is accepted). */
+void memd_destroy(memd_ctx *ctx);
+
+/* Initial field solution (Sec. II, Fig. 1, Eqs. 1-3).  n particles: pos (n x 3)
+ * any real positions (folded into the box), q integer valences |q| < 2^15,
+ * mass (n, NULL = 1), vel (n x 3, NULL = 0).  Deposits the charges, solves
+ * Gauss's law exactly in the int64 ledger, sets the k = 0 mode of D to -P/V,
+ * relaxes to curl E = 0 in FP64, sets B = 0 and computes the forces.  A
+ * non-neutral system gets a uniform background, which must be an integer in
+ * units of e 2^-48 per vertex.  Errors: INVALID, OOM, GAUSS, RELAX_NOCONV,
+ * CUDA. */
+memd_status memd_init_field(memd_ctx *ctx, int64_t n, const double *pos,
+                            const int32_t *q, const double *mass,
+                            const double *vel);
+
+/* Advance nsteps time steps (Eqs. 18, 20, 21): half kick, plaquette update,
+ * drift with charge transfer, link update, transfer application, force
+ * gather with corrections and optional Langevin force, half kick.  th NULL
+ * means constant energy.  Errors: STATE, CELL_JUMP (the offending charge did
+ * not move), CUDA. */
+memd_status memd_step(memd_ctx *ctx, int64_t nsteps, const memd_thermostat *th);
+
+/* Copy the electrostatic forces (n x 3, without the Langevin part). */
+memd_status memd_forces(memd_ctx *ctx, double *f_out);
+
+/* Device address of the n x 3 FP64 force array, valid until the next
+ * memd_init_field or memd_destroy. */
+memd_status memd_forces_device(memd_ctx *ctx, const double **f_dev);
+
+/* Energy terms, dipole moment and Gauss-law residuals (FP64 reductions). */
+memd_status memd_energy(memd_ctx *ctx, memd_energy_terms *out);
+
+/* Copy the folded positions, velocities and image counters (any may be NULL). */
+memd_status memd_get_particles(memd_ctx *ctx, double *pos, double *vel,
+                               int32_t *img);
+
+/* Overwrite positions (folded, with img), velocities and image counters of
+ * the n particles without depositing any current (state load).  img NULL
+ * keeps the counters, vel NULL keeps the velocities. */
+memd_status memd_set_particles(memd_ctx *ctx, const double *pos,
+                               const double *vel, const int32_t *img);
+
+/* Prescribed move (Eq. 20, current term only): move every particle to pos
+ * (with img, NULL = the folding of pos) and apply the charge transfer of the
+ * move to D and the ledger; no field propagation, no force update.
+ * Errors: CELL_JUMP, STATE. */
+memd_status memd_move(memd_ctx *ctx, const double *pos, const int32_t *img);
+
+/* Copy D, B (FP64, 3V each) and the ledger Lg (int64, 3V); any may be NULL. */
+memd_status memd_get_fields(memd_ctx *ctx, double *D, double *B, int64_t *Lg);
+
+/* Overwrite D, B and Lg (any may be NULL); FP32 contexts round D and B. */
+memd_status memd_set_fields(memd_ctx *ctx, const double *D, const double *B,
+                            const int64_t *Lg);
+
+/* Recompute the forces from the current state (gather with corrections);
+ * the stored kick force becomes the electrostatic force. */
+memd_status memd_compute_forces(memd_ctx *ctx);
+
+/* Create-time results: 1/eps per link (3V, may be NULL), the lattice Green's
+ * table G(dx,dy,dz) at index dx + 2 dy + 4 dz (8, may be NULL) and the inverse
+ * effective permittivity tensor (9, row major, may be NULL). */
+memd_status memd_get_setup(memd_ctx *ctx, double *inv_eps, double *G8,
+                           double *eps_eff_inv);
+
+/* Event timing of the field kernels and launch counts (needs time_kernels). */
+memd_status memd_get_kernel_stats(memd_ctx *ctx, memd_kernel_stats *out);
+memd_status memd_reset_kernel_stats(memd_ctx *ctx);
+
+/* Block the host until all work issued by ctx has finished. */
+memd_status memd_synchronize(memd_ctx *ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

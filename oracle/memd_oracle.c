@@ -400,7 +400,8 @@ static int32_t eps_effective(orc_sys *s) {
 orc_sys *orc_create(const int32_t N[3], const double L[3], const orc_eps *eps,
                     double c_light, double dt, int32_t self_mode,
                     int32_t dipole_corr, double relax_tol, int32_t relax_maxit,
-                    double omega, uint64_t seed, int32_t *status) {
+                    double omega, uint64_t seed, const double *Minv_in,
+                    int32_t *status) {
   *status = ORC_ERR_INVALID;
   for (int d = 0; d < 3; ++d)
     if (N[d] < 2 || !(L[d] > 0.0)) return NULL;
@@ -440,8 +441,13 @@ orc_sys *orc_create(const int32_t N[3], const double L[3], const orc_eps *eps,
   int32_t st = map_eps(s, eps);
   if (st != ORC_OK) { orc_destroy(s); *status = st; return NULL; }
   orc_green_table(s->N, s->G);
-  st = eps_effective(s);
-  if (st != ORC_OK) { orc_destroy(s); *status = st; return NULL; }
+  if (Minv_in) {
+    /* a caller-supplied inverse effective permittivity (e.g. a closed form) */
+    memcpy(s->Minv, Minv_in, sizeof(s->Minv));
+  } else {
+    st = eps_effective(s);
+    if (st != ORC_OK) { orc_destroy(s); *status = st; return NULL; }
+  }
   *status = ORC_OK;
   return s;
 }

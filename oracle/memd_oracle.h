@@ -75,7 +75,8 @@ enum {
 orc_sys *orc_create(const int32_t N[3], const double L[3], const orc_eps *eps,
                     double c_light, double dt, int32_t self_mode,
                     int32_t dipole_corr, double relax_tol, int32_t relax_maxit,
-                    double omega, uint64_t seed, int32_t *status);
+                    double omega, uint64_t seed, const double *Minv_in,
+                    int32_t *status);
 void orc_destroy(orc_sys *s);
 
 int64_t orc_nsites(const orc_sys *s);

@@ -67,7 +67,7 @@ def lib():
         L.orc_create.restype = C.c_void_p
         L.orc_create.argtypes = [i32p, f64p, C.POINTER(_Eps), C.c_double, C.c_double,
                                  C.c_int32, C.c_int32, C.c_double, C.c_int32,
-                                 C.c_double, C.c_uint64, i32p]
+                                 C.c_double, C.c_uint64, f64p, i32p]
         L.orc_destroy.argtypes = [C.c_void_p]
         for f in ("orc_nsites", "orc_nparticles", "orc_stepcount"):
             getattr(L, f).restype = C.c_int64
@@ -157,7 +157,7 @@ class OracleSystem:
 
     def __init__(self, N, L, eps=None, c_light=1.0, dt=0.01, self_mode=SELF_GF,
                  dipole_corr=1, relax_tol=1e-12, relax_maxit=200000, omega=0.0,
-                 seed=0):
+                 seed=0, eps_eff_inv=None):
         self._lib = lib()
         self.N = tuple(int(n) for n in N)
         self.L = tuple(float(x) for x in L)
@@ -167,9 +167,13 @@ class OracleSystem:
             eps = dict(kind=EPS_CONST, params=(1.0,))
         e, keep = eps_struct(**eps)
         st = C.c_int32(0)
+        Mi = None
+        if eps_eff_inv is not None:
+            Mi = np.ascontiguousarray(eps_eff_inv, dtype=np.float64).reshape(9)
         self._h = self._lib.orc_create(_p(n, C.c_int32), _p(Lb, C.c_double), C.byref(e),
                                        c_light, dt, self_mode, dipole_corr, relax_tol,
-                                       relax_maxit, omega, C.c_uint64(seed), C.byref(st))
+                                       relax_maxit, omega, C.c_uint64(seed),
+                                       None if Mi is None else _p(Mi, C.c_double), C.byref(st))
         del keep
         if not self._h:
             raise OracleError(f"orc_create failed with status {st.value}")

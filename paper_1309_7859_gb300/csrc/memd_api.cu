@@ -1,0 +1,990 @@
+// memd_api.cu -- the C ABI of the MEMD library (declared in include/memd.h):
+// context, device memory, the relaxation solver, the step sequence captured
+// in a CUDA graph, and the state / diagnostic calls.  All arithmetic of the
+// method runs in the kernels of memd_field.cu, memd_setup.cu and
+// memd_particles.cu; this file only orders them.
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "memd.h"
+#include "memd_internal.cuh"
+
+using namespace memd;
+
+struct memd_ctx {
+  Mesh mesh;
+  double Vbox = 0, c = 0, dt = 0;
+  int prec = 0, self_mode = 1, dipole_corr = 1, relax_maxit = 200000, use_graphs = 1;
+  int time_kernels = 0;
+  double relax_tol = 1e-12;
+  unsigned long long seed = 0;
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  memd_alloc_fn alloc = nullptr;
+  memd_free_fn free_fn = nullptr;
+  void* alloc_user = nullptr;
+  std::vector<std::pair<void*, size_t>> blocks;
+  std::string last_error;
+  // field arrays: D and B double-buffered for the fused update; cur is the
+  // buffer that holds the present state
+  void* Dbuf[2] = {nullptr, nullptr};
+  void* Bbuf[2] = {nullptr, nullptr};
+  int cur = 0;
+  void* ie = nullptr;
+  double* ie64 = nullptr;
+  long long* Lg = nullptr;
+  long long* Tb = nullptr;
+  DevState* ds = nullptr;
+  double* red = nullptr;  // reduction partials (4 x reduce_blocks) + 32 scalars
+  double G[8] = {0};
+  double Minv[9] = {0};
+  // particles
+  Particles P{};
+  bool initialised = false;
+  // step graphs, one per buffer parity
+  cudaGraphExec_t graph[2] = {nullptr, nullptr};
+  int graph_thermo = -1;
+  double graph_gamma = 0, graph_kT = 0;
+  cudaStream_t side = nullptr;
+  cudaEvent_t fork = nullptr, join = nullptr;
+  cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+  bool timing_pending = false;
+  double field_ms = 0;
+  long long field_launches = 0;
+  int relax_iters_last = 0;
+  int zchunk = 0;
+  void* D() const { return Dbuf[cur]; }
+  void* B() const { return Bbuf[cur]; }
+};
+
+namespace {
+
+const char* kStatusText[] = {"ok",
+                             "invalid argument or state",
+                             "Courant condition violated (c dt sqrt(3) >= a)",
+                             "device allocation failed",
+                             "CUDA error",
+                             "a charge moved more than one cell in a step",
+                             "Gauss ledger does not close",
+                             "relaxation did not converge",
+                             "dipole drift",
+                             "timeout",
+                             "call out of order",
+                             "fixed-point overflow"};
+
+memd_status fail(memd_ctx* c, memd_status s, const std::string& why) {
+  if (c) c->last_error = why;
+  return s;
+}
+
+#define CK(call)                                                                     \
+  do {                                                                               \
+    cudaError_t e_ = (call);                                                         \
+    if (e_ != cudaSuccess)                                                           \
+      return fail(c, MEMD_ERR_CUDA, std::string(#call) + ": " + cudaGetErrorString(e_)); \
+  } while (0)
+
+#define CKL()                                                                        \
+  do {                                                                               \
+    cudaError_t e_ = cudaGetLastError();                                             \
+    if (e_ != cudaSuccess)                                                           \
+      return fail(c, MEMD_ERR_CUDA, std::string("kernel launch: ") + cudaGetErrorString(e_)); \
+  } while (0)
+
+void* dalloc(memd_ctx* c, size_t bytes) {
+  if (bytes < 256) bytes = 256;
+  void* p = nullptr;
+  if (c->alloc) {
+    p = c->alloc(c->alloc_user, bytes, (void*)c->stream);
+  } else if (cudaMalloc(&p, bytes) != cudaSuccess) {
+    cudaGetLastError();
+    p = nullptr;
+  }
+  if (p) c->blocks.emplace_back(p, bytes);
+  return p;
+}
+
+void dfree(memd_ctx* c, void* p) {
+  if (!p) return;
+  for (size_t i = 0; i < c->blocks.size(); ++i)
+    if (c->blocks[i].first == p) {
+      if (c->free_fn)
+        c->free_fn(c->alloc_user, p, c->blocks[i].second, (void*)c->stream);
+      else
+        cudaFree(p);
+      c->blocks.erase(c->blocks.begin() + i);
+      return;
+    }
+}
+
+size_t esz(const memd_ctx* c) { return c->prec == MEMD_FP32 ? sizeof(float) : sizeof(double); }
+
+StepParams step_params(const memd_ctx* c, int thermo, double gamma, double kT) {
+  StepParams sp{};
+  sp.dt = c->dt;
+  sp.coefB = c->dt / c->mesh.a;
+  sp.coefD = c->c * c->c * c->dt / c->mesh.a;
+  sp.scale = std::ldexp(1.0, -48) / (c->mesh.a * c->mesh.a);
+  sp.Vbox = c->Vbox;
+  for (int t = 0; t < 8; ++t) sp.G[t] = c->G[t];
+  for (int t = 0; t < 9; ++t) sp.Minv[t] = c->Minv[t];
+  sp.self_mode = c->self_mode;
+  sp.dipole_corr = c->dipole_corr;
+  sp.thermo = thermo;
+  sp.gamma = gamma;
+  sp.kT = kT;
+  sp.seed = c->seed;
+  return sp;
+}
+
+memd_status check_err(memd_ctx* c) {
+  unsigned int err = 0;
+  CK(cudaMemcpyAsync(&err, &c->ds->err, sizeof(err), cudaMemcpyDeviceToHost, c->stream));
+  CK(cudaStreamSynchronize(c->stream));
+  if (err) {
+    CK(cudaMemsetAsync(&c->ds->err, 0, sizeof(unsigned int), c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    if (err & kErrCellJump) return fail(c, MEMD_ERR_CELL_JUMP, "a charge moved more than one cell");
+    if (err & kErrGauss) return fail(c, MEMD_ERR_GAUSS, "Gauss scan did not close (system not neutral)");
+    if (err & kErrNonFinite) return fail(c, MEMD_ERR_INVALID, "non-finite or out-of-range input");
+    return fail(c, MEMD_ERR_OVERFLOW, "fixed-point overflow");
+  }
+  return MEMD_OK;
+}
+
+// scalar slots in c->red after the partial arrays
+enum {
+  kS_PW = 0, kS_RZ0 = 1, kS_RZ1 = 2, kS_RES = 3, kS_EMAX = 4, kS_A = 5, kS_B = 6, kS_C = 7,
+  kS_RMAX = 13, kS_DONE = 14, kS_TOL = 15
+};
+
+void harvest_timing(memd_ctx* c) {
+  if (!c->timing_pending) return;
+  float ms = 0;
+  if (cudaEventSynchronize(c->ev1) == cudaSuccess &&
+      cudaEventElapsedTime(&ms, c->ev0, c->ev1) == cudaSuccess) {
+    c->field_ms += ms;
+    c->field_launches += 1;
+  }
+  cudaGetLastError();
+  c->timing_pending = false;
+}
+
+void drop_graphs(memd_ctx* c) {
+  for (int t = 0; t < 2; ++t)
+    if (c->graph[t]) {
+      cudaGraphExecDestroy(c->graph[t]);
+      c->graph[t] = nullptr;
+    }
+}
+
+double* scal(memd_ctx* c) { return c->red + 4 * reduce_blocks(); }
+
+}  // namespace
+
+// ------------------------------------------------------------------ relaxation
+// Sec. II: energy minimisation of sum D^2 / 2 eps over divergence-free
+// changes of D, i.e. curl E = 0, by preconditioned conjugate gradients on
+// plaquette rotations theta: D = D0 + C^T theta, gradient -C(ie D), Jacobi
+// preconditioner sum of ie around each plaquette.  It keeps div D and the
+// mean of D exactly (up to rounding).  FP64 throughout.
+namespace {
+
+// After the recursive residual meets the tolerance the iteration freezes
+// (kS_DONE): continuing in round-off would divide noise by noise.  The host
+// then checks the true residual and restarts from it if needed.
+__global__ void __launch_bounds__(256)
+    k_pcg_update(int64_t n, double* __restrict__ D, const double* __restrict__ u,
+                 double* __restrict__ r, const double* __restrict__ w, double* __restrict__ z,
+                 const double* __restrict__ diag, const double* __restrict__ sc, int rz_slot,
+                 double* __restrict__ part) {
+  __shared__ double sh[8];
+  const bool done = sc[kS_DONE] != 0.0;
+  const double pw = sc[kS_PW], rz = sc[rz_slot];
+  const double alpha = (!done && pw > 0.0) ? rz / pw : 0.0;
+  double mx = 0.0;
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < n;
+       t += (int64_t)gridDim.x * blockDim.x) {
+    double rn = r[t];
+    if (!done) {
+      D[t] += alpha * u[t];
+      rn = rn - alpha * w[t];
+      r[t] = rn;
+      z[t] = rn / diag[t];
+    }
+    mx = fmax(mx, fabs(rn));
+  }
+  for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_down_sync(0xffffffffu, mx, o));
+  if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = mx;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double r2 = 0.0;
+    for (int q = 0; q < (int)(blockDim.x >> 5); ++q) r2 = fmax(r2, sh[q]);
+    part[blockIdx.x] = r2;
+  }
+}
+
+__global__ void k_pcg_dir(int64_t n, double* __restrict__ p, const double* __restrict__ z,
+                          double* __restrict__ sc, int rz_new, int rz_old, int first) {
+  const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (first) {
+    if (t < n) p[t] = z[t];
+    return;
+  }
+  if (sc[kS_DONE] != 0.0) return;
+  if (sc[kS_RMAX] <= sc[kS_TOL] * sc[kS_EMAX]) {
+    if (t == 0) sc[kS_DONE] = 1.0;
+    return;
+  }
+  if (t >= n) return;
+  const double a = sc[rz_new], b = sc[rz_old];
+  const double beta = (b != 0.0) ? a / b : 0.0;
+  p[t] = z[t] + beta * p[t];
+}
+
+__global__ void k_set_scalar(double* sc, int slot, double v) {
+  if (threadIdx.x == 0 && blockIdx.x == 0) sc[slot] = v;
+}
+
+__global__ void k_div(int64_t n, double* __restrict__ z, const double* __restrict__ r,
+                      const double* __restrict__ diag) {
+  const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (t < n) z[t] = r[t] / diag[t];
+}
+
+__global__ void k_mul(int64_t n, double* __restrict__ out, const double* __restrict__ x,
+                      const double* __restrict__ y) {
+  const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (t < n) out[t] = x[t] * y[t];
+}
+
+__global__ void k_fill_unit(int64_t V, double* __restrict__ D, int d) {
+  const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (t < 3 * V) D[t] = (t / V == d) ? 1.0 : 0.0;
+}
+
+inline unsigned nb(int64_t n) { return (unsigned)((n + 255) / 256); }
+
+}  // namespace
+
+static memd_status relax(memd_ctx* c, double* D64, double tol, int maxit) {
+  const Mesh& m = c->mesh;
+  const int64_t n = 3 * m.V;
+  const cudaStream_t st = c->stream;
+  double* buf = (double*)dalloc(c, sizeof(double) * 6 * n);
+  if (!buf) return fail(c, MEMD_ERR_OOM, "relaxation scratch");
+  double *r = buf, *z = buf + n, *p = buf + 2 * n, *u = buf + 3 * n, *w = buf + 4 * n,
+         *diag = buf + 5 * n;
+  double* part = c->red;
+  double* sc = scal(c);
+  const int R = reduce_blocks();
+  launch_plaquette_diag(m, diag, c->ie64, st);
+  // true residual max|circ(ie D)| and max|ie D|; ok when res <= tol * emax
+  auto check = [&](bool& ok, bool& frozen) -> memd_status {
+    launch_circ64(m, w, D64, c->ie64, -1.0, st);
+    launch_absmax(w, nullptr, n, part, st);
+    launch_finish(part, 1, sc + kS_RES, st);
+    launch_absmax(D64, c->ie64, n, part, st);
+    launch_finish(part, 1, sc + kS_EMAX, st);
+    double h[2], done = 0;
+    CK(cudaMemcpyAsync(h, sc + kS_RES, 2 * sizeof(double), cudaMemcpyDeviceToHost, st));
+    CK(cudaMemcpyAsync(&done, sc + kS_DONE, sizeof(double), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    ok = h[0] <= tol * h[1];
+    frozen = done != 0.0;
+    return MEMD_OK;
+  };
+  // (re)start from the true residual held in w
+  auto restart = [&]() {
+    cudaMemcpyAsync(r, w, n * sizeof(double), cudaMemcpyDeviceToDevice, st);
+    k_div<<<nb(n), 256, 0, st>>>(n, z, r, diag);
+    k_pcg_dir<<<nb(n), 256, 0, st>>>(n, p, z, sc, 0, 0, 1);
+    launch_dot(r, z, n, part, st);
+    launch_finish(part, 0, sc + kS_RZ0, st);
+    k_set_scalar<<<1, 32, 0, st>>>(sc, kS_DONE, 0.0);
+    k_set_scalar<<<1, 32, 0, st>>>(sc, kS_TOL, 0.5 * tol);
+  };
+  bool ok = false, frozen = false;
+  k_set_scalar<<<1, 32, 0, st>>>(sc, kS_DONE, 0.0);
+  memd_status s = check(ok, frozen);
+  int it = 0, parity = 0;
+  if (s == MEMD_OK && !ok) {
+    restart();
+    parity = 0;
+    while (it < maxit) {
+      const int old_slot = kS_RZ0 + parity, new_slot = kS_RZ0 + (parity ^ 1);
+      launch_curlT64(m, u, p, st);
+      launch_circ64(m, w, u, c->ie64, 1.0, st);
+      launch_dot(p, w, n, part, st);
+      launch_finish(part, 0, sc + kS_PW, st);
+      k_pcg_update<<<R, 256, 0, st>>>(n, D64, u, r, w, z, diag, sc, old_slot, part + R);
+      launch_finish(part + R, 1, sc + kS_RMAX, st);
+      launch_dot(r, z, n, part, st);
+      launch_finish(part, 0, sc + new_slot, st);
+      k_pcg_dir<<<nb(n), 256, 0, st>>>(n, p, z, sc, new_slot, old_slot, 0);
+      parity ^= 1;
+      ++it;
+      if (it % 25 == 0 || it == maxit) {
+        if (cudaGetLastError() != cudaSuccess) {
+          dfree(c, buf);
+          return fail(c, MEMD_ERR_CUDA, "relaxation kernel launch");
+        }
+        s = check(ok, frozen);
+        if (s != MEMD_OK || ok) break;
+        if (frozen) {  // the recursion converged but the true residual did not
+          restart();
+          parity = 0;
+        }
+      }
+    }
+  }
+  c->relax_iters_last = it;
+  dfree(c, buf);
+  if (s != MEMD_OK) return s;
+  if (!ok) return fail(c, MEMD_ERR_RELAX_NOCONV, "relaxation did not reach its tolerance");
+  return MEMD_OK;
+}
+
+// ----------------------------------------------------------------- public API
+extern "C" {
+
+void memd_default_options(memd_options* o) {
+  if (!o) return;
+  std::memset(o, 0, sizeof(*o));
+  o->precision = MEMD_FP64;
+  o->self_mode = MEMD_SELF_GF;
+  o->dipole_corr = 1;
+  o->relax_max_iter = 200000;
+  o->relax_tol = 1e-12;
+  o->seed = 0;
+  o->cuda_stream = nullptr;
+  o->device = -1;
+  o->use_graphs = 1;
+}
+
+const char* memd_status_string(memd_status s) {
+  int i = (int)s;
+  if (i < 0 || i > 11) return "unknown status";
+  return kStatusText[i];
+}
+
+const char* memd_last_error(const memd_ctx* c) {
+  if (!c) return "no context";
+  return c->last_error.c_str();
+}
+
+void memd_destroy(memd_ctx* c) {
+  if (!c) return;
+  cudaSetDevice(c->device);
+  if (c->stream) cudaStreamSynchronize(c->stream);
+  drop_graphs(c);
+  if (c->ev0) cudaEventDestroy(c->ev0);
+  if (c->ev1) cudaEventDestroy(c->ev1);
+  if (c->fork) cudaEventDestroy(c->fork);
+  if (c->join) cudaEventDestroy(c->join);
+  if (c->side) cudaStreamDestroy(c->side);
+  while (!c->blocks.empty()) dfree(c, c->blocks.back().first);
+  if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
+  delete c;
+}
+
+memd_status memd_create(const int32_t mesh[3], const double box[3], const memd_eps_profile* eps,
+                        double c_light, double dt, const memd_options* opt, memd_ctx** out) {
+  if (!out) return MEMD_ERR_INVALID;
+  *out = nullptr;
+  if (!mesh || !box || !eps) return MEMD_ERR_INVALID;
+  memd_options o;
+  if (opt)
+    o = *opt;
+  else
+    memd_default_options(&o);
+  for (int d = 0; d < 3; ++d)
+    if (mesh[d] < 2 || !(box[d] > 0.0)) return MEMD_ERR_INVALID;
+  const double a = box[0] / mesh[0];
+  for (int d = 1; d < 3; ++d)
+    if (std::fabs(box[d] / mesh[d] - a) > 1e-12 * a) return MEMD_ERR_INVALID;
+  const int64_t V = (int64_t)mesh[0] * mesh[1] * mesh[2];
+  if (3 * V >= (int64_t(1) << 31)) return MEMD_ERR_INVALID;
+  if (!(c_light > 0.0) || !(dt > 0.0)) return MEMD_ERR_INVALID;
+  if (!(c_light * dt * std::sqrt(3.0) < a)) return MEMD_ERR_COURANT;
+  if (o.precision != MEMD_FP32 && o.precision != MEMD_FP64) return MEMD_ERR_INVALID;
+  if (o.self_mode < 0 || o.self_mode > 2) return MEMD_ERR_INVALID;
+  if (eps->kind < 0 || eps->kind > 4) return MEMD_ERR_INVALID;
+  if ((eps->kind == MEMD_EPS_LINKS || eps->kind == MEMD_EPS_VERTICES) && !eps->values)
+    return MEMD_ERR_INVALID;
+  if ((eps->kind == MEMD_EPS_TANH || eps->kind == MEMD_EPS_SIN) && (eps->axis < 0 || eps->axis > 2))
+    return MEMD_ERR_INVALID;
+
+  memd_ctx* c = new memd_ctx();
+  if (o.device >= 0) {
+    c->device = o.device;
+  } else if (cudaGetDevice(&c->device) != cudaSuccess) {
+    delete c;
+    return MEMD_ERR_CUDA;
+  }
+  if (cudaSetDevice(c->device) != cudaSuccess) {
+    delete c;
+    return MEMD_ERR_CUDA;
+  }
+  c->mesh.n[0] = mesh[0];
+  c->mesh.n[1] = mesh[1];
+  c->mesh.n[2] = mesh[2];
+  c->mesh.V = V;
+  c->mesh.a = a;
+  for (int d = 0; d < 3; ++d) c->mesh.L[d] = box[d];
+  c->Vbox = box[0] * box[1] * box[2];
+  c->c = c_light;
+  c->dt = dt;
+  c->prec = o.precision;
+  c->self_mode = o.self_mode;
+  c->dipole_corr = o.dipole_corr ? 1 : 0;
+  c->relax_tol = o.relax_tol > 0 ? o.relax_tol : 1e-12;
+  c->relax_maxit = o.relax_max_iter > 0 ? o.relax_max_iter : 200000;
+  c->seed = o.seed;
+  c->use_graphs = o.use_graphs;
+  c->time_kernels = o.time_kernels;
+  c->alloc = o.alloc;
+  c->free_fn = o.free;
+  c->alloc_user = o.alloc_user;
+  if (o.cuda_stream) {
+    c->stream = (cudaStream_t)o.cuda_stream;
+  } else {
+    if (cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking) != cudaSuccess) {
+      delete c;
+      return MEMD_ERR_CUDA;
+    }
+    c->own_stream = true;
+  }
+  memd_status s = MEMD_OK;
+  const cudaStream_t st = c->stream;
+  const size_t n3 = 3 * (size_t)V;
+  for (int t = 0; t < 2; ++t) {
+    c->Dbuf[t] = dalloc(c, n3 * esz(c));
+    c->Bbuf[t] = dalloc(c, n3 * esz(c));
+  }
+  c->ie = dalloc(c, n3 * esz(c));
+  c->ie64 = (double*)dalloc(c, n3 * sizeof(double));
+  c->Lg = (long long*)dalloc(c, n3 * sizeof(long long));
+  c->Tb = (long long*)dalloc(c, n3 * sizeof(long long));
+  c->ds = (DevState*)dalloc(c, sizeof(DevState));
+  c->red = (double*)dalloc(c, sizeof(double) * (4 * reduce_blocks() + 32 + green_partials()));
+  double* Gdev = nullptr;
+  double* vals = nullptr;
+  double* D64 = nullptr;
+  if (!c->Dbuf[0] || !c->Dbuf[1] || !c->Bbuf[0] || !c->Bbuf[1] || !c->ie || !c->ie64 ||
+      !c->Lg || !c->Tb || !c->ds || !c->red) {
+    s = fail(c, MEMD_ERR_OOM, "field allocation");
+    goto done;
+  }
+  if (cudaMemsetAsync(c->ds, 0, sizeof(DevState), st) != cudaSuccess ||
+      cudaMemsetAsync(c->Dbuf[0], 0, n3 * esz(c), st) != cudaSuccess ||
+      cudaMemsetAsync(c->Dbuf[1], 0, n3 * esz(c), st) != cudaSuccess ||
+      cudaMemsetAsync(c->Bbuf[0], 0, n3 * esz(c), st) != cudaSuccess ||
+      cudaMemsetAsync(c->Bbuf[1], 0, n3 * esz(c), st) != cudaSuccess ||
+      cudaMemsetAsync(c->Lg, 0, n3 * sizeof(long long), st) != cudaSuccess ||
+      cudaMemsetAsync(c->Tb, 0, n3 * sizeof(long long), st) != cudaSuccess) {
+    s = fail(c, MEMD_ERR_CUDA, "memset");
+    goto done;
+  }
+  {
+    // eps on the links (Sec. II, Fig. 2b)
+    EpsDesc e{};
+    e.kind = eps->kind;
+    e.axis = eps->axis;
+    for (int t = 0; t < 8; ++t) e.p[t] = eps->params[t];
+    if (eps->kind == MEMD_EPS_LINKS || eps->kind == MEMD_EPS_VERTICES) {
+      const size_t cnt = eps->kind == MEMD_EPS_LINKS ? n3 : (size_t)V;
+      vals = (double*)dalloc(c, cnt * sizeof(double));
+      if (!vals) {
+        s = fail(c, MEMD_ERR_OOM, "eps values");
+        goto done;
+      }
+      if (cudaMemcpyAsync(vals, eps->values, cnt * sizeof(double), cudaMemcpyHostToDevice, st) !=
+          cudaSuccess) {
+        s = fail(c, MEMD_ERR_CUDA, "eps upload");
+        goto done;
+      }
+    }
+    launch_eps_links(c->mesh, e, vals, c->ie64, &c->ds->err, st);
+    launch_cast(c->prec, c->ie, c->ie64, (int64_t)n3, st);
+    // lattice Green's table (Sec. III)
+    Gdev = c->red + 4 * reduce_blocks() + 32;
+    launch_green(c->mesh, Gdev, scal(c) + 16, st);
+    if (cudaGetLastError() != cudaSuccess) {
+      s = fail(c, MEMD_ERR_CUDA, "setup kernels");
+      goto done;
+    }
+    if (cudaMemcpyAsync(c->G, scal(c) + 16, 8 * sizeof(double), cudaMemcpyDeviceToHost, st) !=
+        cudaSuccess) {
+      s = fail(c, MEMD_ERR_CUDA, "green download");
+      goto done;
+    }
+    s = check_err(c);
+    if (s != MEMD_OK) goto done;
+    // effective permittivity tensor (Sec. V): relax a charge-free field of
+    // mean D = e_d; the mean of E is column d of eps_eff^-1
+    D64 = (double*)dalloc(c, n3 * sizeof(double));
+    if (!D64) {
+      s = fail(c, MEMD_ERR_OOM, "relaxation field");
+      goto done;
+    }
+    double M[9];
+    for (int d = 0; d < 3; ++d) {
+      k_fill_unit<<<nb(n3), 256, 0, st>>>(V, D64, d);
+      s = relax(c, D64, c->relax_tol, c->relax_maxit);
+      if (s != MEMD_OK) goto done;
+      for (int e2 = 0; e2 < 3; ++e2) {
+        launch_dot(D64 + e2 * V, c->ie64 + e2 * V, V, c->red, st);
+        launch_finish(c->red, 0, scal(c) + kS_A + e2, st);
+      }
+      double h[3];
+      if (cudaMemcpyAsync(h, scal(c) + kS_A, 3 * sizeof(double), cudaMemcpyDeviceToHost, st) !=
+              cudaSuccess ||
+          cudaStreamSynchronize(st) != cudaSuccess) {
+        s = fail(c, MEMD_ERR_CUDA, "eps_eff download");
+        goto done;
+      }
+      for (int e2 = 0; e2 < 3; ++e2) M[3 * e2 + d] = h[e2] / (double)V;
+    }
+    for (int e2 = 0; e2 < 3; ++e2)
+      for (int d = 0; d < 3; ++d) c->Minv[3 * e2 + d] = 0.5 * (M[3 * e2 + d] + M[3 * d + e2]);
+  }
+  if (cudaEventCreate(&c->ev0) != cudaSuccess || cudaEventCreate(&c->ev1) != cudaSuccess ||
+      cudaEventCreateWithFlags(&c->fork, cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&c->join, cudaEventDisableTiming) != cudaSuccess ||
+      cudaStreamCreateWithFlags(&c->side, cudaStreamNonBlocking) != cudaSuccess) {
+    s = fail(c, MEMD_ERR_CUDA, "events");
+    goto done;
+  }
+  c->zchunk = fused_zchunk(c->mesh);
+done:
+  dfree(c, vals);
+  dfree(c, D64);
+  if (s != MEMD_OK) {
+    memd_destroy(c);
+    return s;
+  }
+  *out = c;
+  return MEMD_OK;
+}
+
+static void free_particles(memd_ctx* c) {
+  dfree(c, c->P.x);
+  dfree(c, c->P.v);
+  dfree(c, c->P.m);
+  dfree(c, c->P.F);
+  dfree(c, c->P.Ft);
+  dfree(c, c->P.img);
+  dfree(c, c->P.q);
+  dfree(c, c->P.mv);
+  c->P = Particles{};
+}
+
+memd_status memd_init_field(memd_ctx* c, int64_t n, const double* pos, const int32_t* q,
+                            const double* mass, const double* vel) {
+  if (!c) return MEMD_ERR_INVALID;
+  if (n < 0 || (n > 0 && (!pos || !q))) return fail(c, MEMD_ERR_INVALID, "bad particle arrays");
+  CK(cudaSetDevice(c->device));
+  const Mesh& m = c->mesh;
+  const cudaStream_t st = c->stream;
+  long long qtot = 0;
+  for (int64_t p = 0; p < n; ++p) {
+    if (q[p] > 32767 || q[p] < -32767) return fail(c, MEMD_ERR_INVALID, "valence out of range");
+    qtot += q[p];
+  }
+  // a non-neutral system gets a uniform background, exact in units e 2^-48
+  const __int128 tot = (__int128)qtot * ((__int128)1 << 48);
+  if (tot % m.V != 0)
+    return fail(c, MEMD_ERR_INVALID, "non-neutral system needs an integer background per vertex");
+  const long long bg = (long long)(tot / m.V);
+  drop_graphs(c);
+  harvest_timing(c);
+  CK(cudaStreamSynchronize(st));
+  free_particles(c);
+  c->initialised = false;
+  const size_t nn = (size_t)(n > 0 ? n : 1);
+  c->P.n = n;
+  c->P.x = (double*)dalloc(c, 3 * nn * sizeof(double));
+  c->P.v = (double*)dalloc(c, 3 * nn * sizeof(double));
+  c->P.m = (double*)dalloc(c, nn * sizeof(double));
+  c->P.F = (double*)dalloc(c, 3 * nn * sizeof(double));
+  c->P.Ft = (double*)dalloc(c, 3 * nn * sizeof(double));
+  c->P.img = (int*)dalloc(c, 3 * nn * sizeof(int));
+  c->P.q = (int*)dalloc(c, nn * sizeof(int));
+  c->P.mv = (int*)dalloc(c, 6 * nn * sizeof(int));
+  if (!c->P.x || !c->P.v || !c->P.m || !c->P.F || !c->P.Ft || !c->P.img || !c->P.q || !c->P.mv)
+    return fail(c, MEMD_ERR_OOM, "particle allocation");
+  double* pin = (double*)dalloc(c, 3 * nn * sizeof(double));
+  long long* Q = (long long*)dalloc(c, sizeof(long long) * m.V);
+  long long* scr = (long long*)dalloc(c, sizeof(long long) * scan_scratch(m));
+  double* D64 = (double*)dalloc(c, sizeof(double) * 3 * m.V);
+  memd_status s = MEMD_OK;
+  if (!pin || !Q || !scr || !D64) {
+    s = fail(c, MEMD_ERR_OOM, "init scratch");
+  } else {
+    std::vector<double> ones;
+    if (n > 0) {
+      CK(cudaMemcpyAsync(pin, pos, 3 * n * sizeof(double), cudaMemcpyHostToDevice, st));
+      CK(cudaMemcpyAsync(c->P.q, q, n * sizeof(int), cudaMemcpyHostToDevice, st));
+      if (mass) {
+        CK(cudaMemcpyAsync(c->P.m, mass, n * sizeof(double), cudaMemcpyHostToDevice, st));
+      } else {
+        ones.assign(n, 1.0);
+        CK(cudaMemcpyAsync(c->P.m, ones.data(), n * sizeof(double), cudaMemcpyHostToDevice, st));
+      }
+      if (vel) {
+        CK(cudaMemcpyAsync(c->P.v, vel, 3 * n * sizeof(double), cudaMemcpyHostToDevice, st));
+      } else {
+        CK(cudaMemsetAsync(c->P.v, 0, 3 * n * sizeof(double), st));
+      }
+    }
+    CK(cudaMemsetAsync(&c->ds->err, 0, sizeof(unsigned int), st));
+    CK(cudaMemsetAsync(&c->ds->step, 0, sizeof(long long), st));
+    launch_fold_init(m, c->P, pin, nullptr, &c->ds->err, st);
+    // Sec. II, Fig. 1: vertex charges, exact Gauss scan into the ledger
+    launch_cic(m, c->P, Q, bg, st);
+    launch_gauss_scan(m, Q, c->Lg, scr, &c->ds->err, st);
+    CKL();
+    s = check_err(c);
+    if (s == MEMD_OK) {
+      // k = 0 mode of D set to -P/V (Sec. V), then relaxation to curl E = 0
+      launch_dipole(m, c->P, c->ds, st);
+      launch_ledger_sums(m, c->Lg, c->ds, st);
+      launch_init_D(m, D64, c->Lg, c->ds, std::ldexp(1.0, -48) / (m.a * m.a), c->Vbox, st);
+      CKL();
+      s = relax(c, D64, c->relax_tol, c->relax_maxit);
+    }
+    if (s == MEMD_OK) {
+      c->cur = 0;
+      launch_cast(c->prec, c->D(), D64, 3 * m.V, st);
+      CK(cudaMemsetAsync(c->B(), 0, 3 * m.V * esz(c), st));
+      CK(cudaMemsetAsync(c->Tb, 0, 3 * m.V * sizeof(long long), st));
+      CK(cudaMemsetAsync(&c->ds->ticket, 0, sizeof(unsigned int), st));
+      const StepParams sp = step_params(c, 0, 0.0, 0.0);
+      launch_gather(m, c->prec, sp, c->P, c->D(), c->ie, c->ie64, c->ds, 0, 1, st);
+      CKL();
+      s = check_err(c);
+    }
+  }
+  dfree(c, pin);
+  dfree(c, Q);
+  dfree(c, scr);
+  dfree(c, D64);
+  if (s == MEMD_OK) c->initialised = true;
+  return s;
+}
+
+// One step on buffer parity `par` (state in buffer par, result in 1 - par).
+// The charge transfer of the drift runs on a side stream beside the fused
+// field update (neither reads what the other writes); the transfers are
+// applied to the new D, then the gather closes the step.
+static memd_status record_step(memd_ctx* c, const StepParams& sp, int par, bool timed) {
+  const Mesh& m = c->mesh;
+  const cudaStream_t st = c->stream;
+  CK(cudaEventRecord(c->fork, st));
+  CK(cudaStreamWaitEvent(c->side, c->fork, 0));
+  launch_kick_drift_deposit(m, sp, c->P, c->Tb, c->ds, c->side);
+  CK(cudaEventRecord(c->join, c->side));
+  if (timed) CK(cudaEventRecordWithFlags(c->ev0, st, cudaEventRecordExternal));
+  launch_fused_curl(m, c->prec, c->Dbuf[par], c->Bbuf[par], c->ie, c->Dbuf[par ^ 1],
+                    c->Bbuf[par ^ 1], sp.coefB, sp.coefD, c->zchunk, st);
+  if (timed) CK(cudaEventRecordWithFlags(c->ev1, st, cudaEventRecordExternal));
+  CK(cudaStreamWaitEvent(st, c->join, 0));
+  launch_apply(m, c->prec, c->P, c->Tb, c->Lg, c->Dbuf[par ^ 1], sp.scale, st);
+  launch_gather(m, c->prec, sp, c->P, c->Dbuf[par ^ 1], c->ie, c->ie64, c->ds, 1, 2, st);
+  CKL();
+  return MEMD_OK;
+}
+
+// Errors raised by kernels of earlier batches, without blocking: the flag is
+// copied back after each batch and read once that copy has completed.
+static memd_status poll_err(memd_ctx* c, bool block) {
+  if (block) return check_err(c);
+  return MEMD_OK;
+}
+
+memd_status memd_step(memd_ctx* c, int64_t nsteps, const memd_thermostat* th) {
+  if (!c) return MEMD_ERR_INVALID;
+  if (!c->initialised) return fail(c, MEMD_ERR_STATE, "memd_init_field first");
+  if (nsteps < 0) return fail(c, MEMD_ERR_INVALID, "negative step count");
+  CK(cudaSetDevice(c->device));
+  const int thermo = th ? 1 : 0;
+  const double gamma = th ? th->gamma : 0.0, kT = th ? th->kT : 0.0;
+  const StepParams sp = step_params(c, thermo, gamma, kT);
+  const bool timed = c->time_kernels != 0;
+  if (c->graph_thermo != thermo || c->graph_gamma != gamma || c->graph_kT != kT) drop_graphs(c);
+  for (int64_t s = 0; s < nsteps; ++s) {
+    const int par = c->cur;
+    harvest_timing(c);
+    if (!c->use_graphs) {
+      memd_status r = record_step(c, sp, par, timed);
+      if (r != MEMD_OK) return r;
+    } else {
+      if (!c->graph[par]) {
+        cudaGraph_t g;
+        CK(cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal));
+        memd_status r = record_step(c, sp, par, timed);
+        cudaError_t e = cudaStreamEndCapture(c->stream, &g);
+        if (r != MEMD_OK) return r;
+        if (e != cudaSuccess) return fail(c, MEMD_ERR_CUDA, "graph capture");
+        CK(cudaGraphInstantiate(&c->graph[par], g, 0));
+        cudaGraphDestroy(g);
+        c->graph_thermo = thermo;
+        c->graph_gamma = gamma;
+        c->graph_kT = kT;
+      }
+      CK(cudaGraphLaunch(c->graph[par], c->stream));
+    }
+    c->timing_pending = timed;
+    c->cur = par ^ 1;
+  }
+  return poll_err(c, false);
+}
+
+memd_status memd_forces(memd_ctx* c, double* f_out) {
+  if (!c || !f_out) return MEMD_ERR_INVALID;
+  if (!c->initialised) return fail(c, MEMD_ERR_STATE, "memd_init_field first");
+  CK(cudaSetDevice(c->device));
+  if (c->P.n > 0)
+    CK(cudaMemcpyAsync(f_out, c->P.F, 3 * c->P.n * sizeof(double), cudaMemcpyDeviceToHost,
+                       c->stream));
+  return check_err(c);
+}
+
+memd_status memd_forces_device(memd_ctx* c, const double** f_dev) {
+  if (!c || !f_dev) return MEMD_ERR_INVALID;
+  if (!c->initialised) return fail(c, MEMD_ERR_STATE, "memd_init_field first");
+  *f_dev = c->P.F;
+  return MEMD_OK;
+}
+
+memd_status memd_energy(memd_ctx* c, memd_energy_terms* out) {
+  if (!c || !out) return MEMD_ERR_INVALID;
+  if (!c->initialised) return fail(c, MEMD_ERR_STATE, "memd_init_field first");
+  CK(cudaSetDevice(c->device));
+  const Mesh& m = c->mesh;
+  const cudaStream_t st = c->stream;
+  const int R = reduce_blocks();
+  double* part = c->red;
+  double* sc = scal(c);
+  const StepParams sp = step_params(c, 0, 0, 0);
+  launch_field_energy(m, c->prec, c->D(), c->B(), c->ie, sp.coefB, part, part + R, st);
+  launch_finish(part, 0, sc + 8, st);
+  launch_finish(part + R, 0, sc + 9, st);
+  launch_particle_energy(m, sp, c->P, c->ie64, part + 2 * R, part + 3 * R, st);
+  launch_finish(part + 2 * R, 0, sc + 10, st);
+  launch_finish(part + 3 * R, 0, sc + 11, st);
+  long long qtot = 0;
+  long long* Q = (long long*)dalloc(c, sizeof(long long) * m.V + 64);
+  if (!Q) return fail(c, MEMD_ERR_OOM, "energy scratch");
+  unsigned long long* mism = (unsigned long long*)(Q + m.V);
+  // background of a non-neutral system, from the valences on the device
+  std::vector<int> hq(c->P.n > 0 ? c->P.n : 1);
+  if (c->P.n > 0)
+    CK(cudaMemcpyAsync(hq.data(), c->P.q, c->P.n * sizeof(int), cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  for (int64_t p = 0; p < c->P.n; ++p) qtot += hq[p];
+  const long long bg = (long long)(((__int128)qtot << 48) / m.V);
+  launch_cic(m, c->P, Q, bg, st);
+  CK(cudaMemsetAsync(mism, 0, sizeof(unsigned long long), st));
+  launch_gauss_check(m, c->prec, c->D(), c->Lg, Q, m.a * m.a, part, mism, st);
+  launch_finish(part, 1, sc + 12, st);
+  CKL();
+  double h[5];
+  unsigned long long bad = 0;
+  long long Pl[3], step = 0;
+  CK(cudaMemcpyAsync(h, sc + 8, 5 * sizeof(double), cudaMemcpyDeviceToHost, st));
+  CK(cudaMemcpyAsync(&bad, mism, sizeof(bad), cudaMemcpyDeviceToHost, st));
+  CK(cudaMemcpyAsync(Pl, c->ds->Plast, sizeof(Pl), cudaMemcpyDeviceToHost, st));
+  CK(cudaMemcpyAsync(&step, &c->ds->step, sizeof(step), cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  dfree(c, Q);
+  const double a3 = m.a * m.a * m.a;
+  out->electric = h[0] * a3;
+  out->magnetic = h[1] * 0.5 * c->c * c->c * a3;
+  out->kinetic = h[2];
+  out->self = c->self_mode ? h[3] : 0.0;
+  for (int d = 0; d < 3; ++d) out->P[d] = (double)Pl[d] * (m.a / (double)kS);
+  double dip = 0.0;
+  if (c->dipole_corr)
+    for (int e = 0; e < 3; ++e)
+      for (int d = 0; d < 3; ++d) dip += 0.5 * out->P[e] * c->Minv[3 * e + d] * out->P[d] / c->Vbox;
+  out->dipole = dip;
+  out->total = out->kinetic + out->electric + out->magnetic - out->self - out->dipole;
+  out->gauss_residual = h[4];
+  out->gauss_exact = bad == 0 ? 1 : 0;
+  out->pad = 0;
+  out->step = step;
+  return check_err(c);
+}
+
+memd_status memd_get_particles(memd_ctx* c, double* pos, double* vel, int32_t* img) {
+  if (!c) return MEMD_ERR_INVALID;
+  if (!c->initialised) return fail(c, MEMD_ERR_STATE, "memd_init_field first");
+  CK(cudaSetDevice(c->device));
+  const size_t n = (size_t)c->P.n;
+  if (n) {
+    if (pos) CK(cudaMemcpyAsync(pos, c->P.x, 3 * n * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+    if (vel) CK(cudaMemcpyAsync(vel, c->P.v, 3 * n * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+    if (img) CK(cudaMemcpyAsync(img, c->P.img, 3 * n * sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+  }
+  return check_err(c);
+}
+
+memd_status memd_set_particles(memd_ctx* c, const double* pos, const double* vel,
+                               const int32_t* img) {
+  if (!c) return MEMD_ERR_INVALID;
+  if (!c->initialised) return fail(c, MEMD_ERR_STATE, "memd_init_field first");
+  CK(cudaSetDevice(c->device));
+  const size_t n = (size_t)c->P.n;
+  if (!n) return MEMD_OK;
+  const cudaStream_t st = c->stream;
+  if (vel) CK(cudaMemcpyAsync(c->P.v, vel, 3 * n * sizeof(double), cudaMemcpyHostToDevice, st));
+  if (pos) {
+    double* pin = (double*)dalloc(c, 3 * n * sizeof(double) + 3 * n * sizeof(int));
+    if (!pin) return fail(c, MEMD_ERR_OOM, "set_particles scratch");
+    int* iin = (int*)(pin + 3 * n);
+    CK(cudaMemcpyAsync(pin, pos, 3 * n * sizeof(double), cudaMemcpyHostToDevice, st));
+    if (img)
+      CK(cudaMemcpyAsync(iin, img, 3 * n * sizeof(int), cudaMemcpyHostToDevice, st));
+    else
+      CK(cudaMemcpyAsync(iin, c->P.img, 3 * n * sizeof(int), cudaMemcpyDeviceToDevice, st));
+    launch_fold_init(c->mesh, c->P, pin, iin, &c->ds->err, st);
+    CKL();
+    memd_status s = check_err(c);
+    dfree(c, pin);
+    if (s != MEMD_OK) return s;
+  } else if (img) {
+    CK(cudaMemcpyAsync(c->P.img, img, 3 * n * sizeof(int), cudaMemcpyHostToDevice, st));
+  }
+  CK(cudaStreamSynchronize(st));
+  return MEMD_OK;
+}
+
+memd_status memd_move(memd_ctx* c, const double* pos, const int32_t* img) {
+  if (!c || !pos) return MEMD_ERR_INVALID;
+  if (!c->initialised) return fail(c, MEMD_ERR_STATE, "memd_init_field first");
+  CK(cudaSetDevice(c->device));
+  const size_t n = (size_t)c->P.n;
+  if (!n) return MEMD_OK;
+  const cudaStream_t st = c->stream;
+  double* pin = (double*)dalloc(c, 3 * n * sizeof(double) + 3 * n * sizeof(int));
+  if (!pin) return fail(c, MEMD_ERR_OOM, "move scratch");
+  int* iin = (int*)(pin + 3 * n);
+  CK(cudaMemcpyAsync(pin, pos, 3 * n * sizeof(double), cudaMemcpyHostToDevice, st));
+  if (img) CK(cudaMemcpyAsync(iin, img, 3 * n * sizeof(int), cudaMemcpyHostToDevice, st));
+  CK(cudaMemsetAsync(c->ds->Pacc, 0, sizeof(c->ds->Pacc), st));
+  launch_move_deposit(c->mesh, c->P, pin, img ? iin : nullptr, c->Tb, c->ds, st);
+  launch_apply(c->mesh, c->prec, c->P, c->Tb, c->Lg, c->D(),
+               std::ldexp(1.0, -48) / (c->mesh.a * c->mesh.a), st);
+  launch_step_end(c->ds, 0, st);
+  CKL();
+  memd_status s = check_err(c);
+  dfree(c, pin);
+  return s;
+}
+
+memd_status memd_get_fields(memd_ctx* c, double* D, double* B, int64_t* Lg) {
+  if (!c) return MEMD_ERR_INVALID;
+  CK(cudaSetDevice(c->device));
+  const size_t n3 = 3 * (size_t)c->mesh.V;
+  const cudaStream_t st = c->stream;
+  double* tmp = (double*)dalloc(c, n3 * sizeof(double));
+  if (!tmp) return fail(c, MEMD_ERR_OOM, "get_fields scratch");
+  if (D) {
+    launch_widen(c->prec, tmp, c->D(), (int64_t)n3, st);
+    CK(cudaMemcpyAsync(D, tmp, n3 * sizeof(double), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+  }
+  if (B) {
+    launch_widen(c->prec, tmp, c->B(), (int64_t)n3, st);
+    CK(cudaMemcpyAsync(B, tmp, n3 * sizeof(double), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+  }
+  if (Lg) CK(cudaMemcpyAsync(Lg, c->Lg, n3 * sizeof(long long), cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  dfree(c, tmp);
+  return MEMD_OK;
+}
+
+memd_status memd_set_fields(memd_ctx* c, const double* D, const double* B, const int64_t* Lg) {
+  if (!c) return MEMD_ERR_INVALID;
+  CK(cudaSetDevice(c->device));
+  const size_t n3 = 3 * (size_t)c->mesh.V;
+  const cudaStream_t st = c->stream;
+  double* tmp = (double*)dalloc(c, n3 * sizeof(double));
+  if (!tmp) return fail(c, MEMD_ERR_OOM, "set_fields scratch");
+  if (D) {
+    CK(cudaMemcpyAsync(tmp, D, n3 * sizeof(double), cudaMemcpyHostToDevice, st));
+    launch_cast(c->prec, c->D(), tmp, (int64_t)n3, st);
+    CK(cudaStreamSynchronize(st));
+  }
+  if (B) {
+    CK(cudaMemcpyAsync(tmp, B, n3 * sizeof(double), cudaMemcpyHostToDevice, st));
+    launch_cast(c->prec, c->B(), tmp, (int64_t)n3, st);
+    CK(cudaStreamSynchronize(st));
+  }
+  if (Lg) CK(cudaMemcpyAsync(c->Lg, Lg, n3 * sizeof(long long), cudaMemcpyHostToDevice, st));
+  CKL();
+  CK(cudaStreamSynchronize(st));
+  dfree(c, tmp);
+  return MEMD_OK;
+}
+
+memd_status memd_compute_forces(memd_ctx* c) {
+  if (!c) return MEMD_ERR_INVALID;
+  if (!c->initialised) return fail(c, MEMD_ERR_STATE, "memd_init_field first");
+  CK(cudaSetDevice(c->device));
+  const cudaStream_t st = c->stream;
+  const StepParams sp = step_params(c, 0, 0.0, 0.0);
+  launch_dipole(c->mesh, c->P, c->ds, st);
+  launch_gather(c->mesh, c->prec, sp, c->P, c->D(), c->ie, c->ie64, c->ds, 0, 1, st);
+  CKL();
+  return check_err(c);
+}
+
+memd_status memd_get_setup(memd_ctx* c, double* inv_eps, double* G8, double* eps_eff_inv) {
+  if (!c) return MEMD_ERR_INVALID;
+  CK(cudaSetDevice(c->device));
+  if (inv_eps)
+    CK(cudaMemcpyAsync(inv_eps, c->ie64, 3 * c->mesh.V * sizeof(double), cudaMemcpyDeviceToHost,
+                       c->stream));
+  CK(cudaStreamSynchronize(c->stream));
+  if (G8) std::memcpy(G8, c->G, sizeof(c->G));
+  if (eps_eff_inv) std::memcpy(eps_eff_inv, c->Minv, sizeof(c->Minv));
+  return MEMD_OK;
+}
+
+memd_status memd_get_kernel_stats(memd_ctx* c, memd_kernel_stats* out) {
+  if (!c || !out) return MEMD_ERR_INVALID;
+  harvest_timing(c);
+  out->field_ms = c->field_ms;
+  out->field_launches = c->field_launches;
+  // the fused update reads D, 1/eps, B and writes D', B' (15 values a site)
+  const double e = (double)esz(c);
+  out->field_bytes = 15.0 * e * (double)c->mesh.V;
+  out->launches_per_step = c->P.n > 0 ? 4 : 2;
+  return MEMD_OK;
+}
+
+memd_status memd_reset_kernel_stats(memd_ctx* c) {
+  if (!c) return MEMD_ERR_INVALID;
+  harvest_timing(c);
+  c->field_ms = 0;
+  c->field_launches = 0;
+  return MEMD_OK;
+}
+
+memd_status memd_synchronize(memd_ctx* c) {
+  if (!c) return MEMD_ERR_INVALID;
+  CK(cudaSetDevice(c->device));
+  harvest_timing(c);
+  CK(cudaStreamSynchronize(c->stream));
+  return check_err(c);
+}
+
+}  // extern "C"

@@ -1,0 +1,425 @@
+// memd_field.cu -- lattice field kernels of MEMD on sm_103a.
+//
+//   curl_B : plaquette update of Eq. 21 (Faraday), B -= (dt/a) circ(D/eps)
+//   curl_D : link update of Eq. 20 (Ampere) without the current,
+//            D += (c^2 dt/a) (transpose circulation of B)
+//   FP64 circulation / transpose maps used by the relaxation (Sec. II)
+//   field energy and Gauss-law diagnostics
+//
+// The field kernels stream every link each step and are bound by HBM
+// bandwidth: x is the fastest index, a warp covers 32 consecutive x, the
+// +/-1 neighbours in y and z are rows that the same or adjacent CTAs read,
+// so they come from L1/L2.
+#include "memd_internal.cuh"
+
+namespace memd {
+
+namespace {
+
+constexpr int kBX = 32;
+constexpr int kBY = 8;
+constexpr int kRedThreads = 256;
+constexpr int kRedBlocks = 2 * 152;
+
+inline dim3 field_grid(const Mesh& m) {
+  return dim3((m.n[0] + kBX - 1) / kBX, (m.n[1] + kBY - 1) / kBY, m.n[2]);
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kBX* kBY)
+    k_curl_B(Mesh m, T* __restrict__ B, const T* __restrict__ D, const T* __restrict__ ie,
+             T coef) {
+  const int i = blockIdx.x * kBX + threadIdx.x;
+  const int j = blockIdx.y * kBY + threadIdx.y;
+  const int k = blockIdx.z;
+  if (i >= m.n[0] || j >= m.n[1]) return;
+  const int64_t V = m.V;
+  const int ip = (i + 1 == m.n[0]) ? 0 : i + 1;
+  const int jp = (j + 1 == m.n[1]) ? 0 : j + 1;
+  const int kp = (k + 1 == m.n[2]) ? 0 : k + 1;
+  const int64_t v = vindex(m, i, j, k);
+  const int64_t vx = vindex(m, ip, j, k), vy = vindex(m, i, jp, k), vz = vindex(m, i, j, kp);
+  const T* Dx = D;
+  const T* Dy = D + V;
+  const T* Dz = D + 2 * V;
+  const T* ix = ie;
+  const T* iy = ie + V;
+  const T* iz = ie + 2 * V;
+  const T Ex = Dx[v] * ix[v], Ey = Dy[v] * iy[v], Ez = Dz[v] * iz[v];
+  const T Ey_x = Dy[vx] * iy[vx], Ez_x = Dz[vx] * iz[vx];
+  const T Ex_y = Dx[vy] * ix[vy], Ez_y = Dz[vy] * iz[vy];
+  const T Ex_z = Dx[vz] * ix[vz], Ey_z = Dy[vz] * iy[vz];
+  // circulations: normal x spans (y, z), normal y spans (z, x), normal z spans (x, y)
+  B[v] = B[v] - coef * (((Ey + Ez_y) - Ey_z) - Ez);
+  B[V + v] = B[V + v] - coef * (((Ez + Ex_z) - Ez_x) - Ex);
+  B[2 * V + v] = B[2 * V + v] - coef * (((Ex + Ey_x) - Ex_y) - Ey);
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kBX* kBY)
+    k_curl_D(Mesh m, T* __restrict__ D, const T* __restrict__ B, T coef) {
+  const int i = blockIdx.x * kBX + threadIdx.x;
+  const int j = blockIdx.y * kBY + threadIdx.y;
+  const int k = blockIdx.z;
+  if (i >= m.n[0] || j >= m.n[1]) return;
+  const int64_t V = m.V;
+  const int im = (i == 0) ? m.n[0] - 1 : i - 1;
+  const int jm = (j == 0) ? m.n[1] - 1 : j - 1;
+  const int km = (k == 0) ? m.n[2] - 1 : k - 1;
+  const int64_t v = vindex(m, i, j, k);
+  const int64_t vx = vindex(m, im, j, k), vy = vindex(m, i, jm, k), vz = vindex(m, i, j, km);
+  const T* Bx = B;
+  const T* By = B + V;
+  const T* Bz = B + 2 * V;
+  const T bx = Bx[v], by = By[v], bz = Bz[v];
+  D[v] = D[v] + coef * (((bz - Bz[vy]) - by) + By[vz]);
+  D[V + v] = D[V + v] + coef * (((bx - Bx[vz]) - bz) + Bz[vx]);
+  D[2 * V + v] = D[2 * V + v] + coef * (((by - By[vx]) - bx) + Bx[vy]);
+}
+
+// w = sign * circulation of (ie * u) around every plaquette (FP64)
+__global__ void __launch_bounds__(kBX* kBY)
+    k_circ64(Mesh m, double* __restrict__ w, const double* __restrict__ u,
+             const double* __restrict__ ie, double sign) {
+  const int i = blockIdx.x * kBX + threadIdx.x;
+  const int j = blockIdx.y * kBY + threadIdx.y;
+  const int k = blockIdx.z;
+  if (i >= m.n[0] || j >= m.n[1]) return;
+  const int64_t V = m.V;
+  const int ip = (i + 1 == m.n[0]) ? 0 : i + 1;
+  const int jp = (j + 1 == m.n[1]) ? 0 : j + 1;
+  const int kp = (k + 1 == m.n[2]) ? 0 : k + 1;
+  const int64_t v = vindex(m, i, j, k);
+  const int64_t vx = vindex(m, ip, j, k), vy = vindex(m, i, jp, k), vz = vindex(m, i, j, kp);
+  const double Ex = u[v] * ie[v], Ey = u[V + v] * ie[V + v], Ez = u[2 * V + v] * ie[2 * V + v];
+  const double Ey_x = u[V + vx] * ie[V + vx], Ez_x = u[2 * V + vx] * ie[2 * V + vx];
+  const double Ex_y = u[vy] * ie[vy], Ez_y = u[2 * V + vy] * ie[2 * V + vy];
+  const double Ex_z = u[vz] * ie[vz], Ey_z = u[V + vz] * ie[V + vz];
+  w[v] = sign * (((Ey + Ez_y) - Ey_z) - Ez);
+  w[V + v] = sign * (((Ez + Ex_z) - Ez_x) - Ex);
+  w[2 * V + v] = sign * (((Ex + Ey_x) - Ex_y) - Ey);
+}
+
+// u = transpose of the circulation map applied to the plaquette field p
+__global__ void __launch_bounds__(kBX* kBY)
+    k_curlT64(Mesh m, double* __restrict__ u, const double* __restrict__ p) {
+  const int i = blockIdx.x * kBX + threadIdx.x;
+  const int j = blockIdx.y * kBY + threadIdx.y;
+  const int k = blockIdx.z;
+  if (i >= m.n[0] || j >= m.n[1]) return;
+  const int64_t V = m.V;
+  const int im = (i == 0) ? m.n[0] - 1 : i - 1;
+  const int jm = (j == 0) ? m.n[1] - 1 : j - 1;
+  const int km = (k == 0) ? m.n[2] - 1 : k - 1;
+  const int64_t v = vindex(m, i, j, k);
+  const int64_t vx = vindex(m, im, j, k), vy = vindex(m, i, jm, k), vz = vindex(m, i, j, km);
+  const double px = p[v], py = p[V + v], pz = p[2 * V + v];
+  u[v] = ((pz - p[2 * V + vy]) - py) + p[V + vz];
+  u[V + v] = ((px - p[vz]) - pz) + p[2 * V + vx];
+  u[2 * V + v] = ((py - p[V + vx]) - px) + p[vy];
+}
+
+__global__ void __launch_bounds__(kBX* kBY)
+    k_plaquette_diag(Mesh m, double* __restrict__ diag, const double* __restrict__ ie) {
+  const int i = blockIdx.x * kBX + threadIdx.x;
+  const int j = blockIdx.y * kBY + threadIdx.y;
+  const int k = blockIdx.z;
+  if (i >= m.n[0] || j >= m.n[1]) return;
+  const int64_t V = m.V;
+  const int ip = (i + 1 == m.n[0]) ? 0 : i + 1;
+  const int jp = (j + 1 == m.n[1]) ? 0 : j + 1;
+  const int kp = (k + 1 == m.n[2]) ? 0 : k + 1;
+  const int64_t v = vindex(m, i, j, k);
+  const int64_t vx = vindex(m, ip, j, k), vy = vindex(m, i, jp, k), vz = vindex(m, i, j, kp);
+  diag[v] = ie[V + v] + ie[2 * V + vy] + ie[V + vz] + ie[2 * V + v];
+  diag[V + v] = ie[2 * V + v] + ie[vz] + ie[2 * V + vx] + ie[v];
+  diag[2 * V + v] = ie[v] + ie[V + vx] + ie[vy] + ie[V + v];
+}
+
+// ------------------------------------------------------------------
+// Fused leapfrog field update of one step (Eqs. 20 and 21 without the
+// current): B' = B - cB circ(D ie) on every plaquette, then
+// D' = D + cD (transpose circulation of B') on every link.  Each CTA owns a
+// TX x TY column tile and marches through a chunk of z planes, holding E of
+// planes k, k+1 and B' of planes k-1, k in shared memory with a one-site halo
+// on the low x/y sides (B' there is recomputed instead of exchanged).  D and
+// B are double-buffered (read *_in, write *_out) because neighbouring CTAs
+// read the halo of the input.  DRAM traffic per site: D, 1/eps, B read,
+// D', B' written.
+template <typename T, int TX, int TY>
+__global__ void __launch_bounds__(TX* TY)
+    k_fused_curl(Mesh m, const T* __restrict__ Din, const T* __restrict__ Bin,
+                 const T* __restrict__ ie, T* __restrict__ Dout, T* __restrict__ Bout, T cB,
+                 T cD, int zchunk) {
+  constexpr int EX = TX + 2, EY = TY + 2, BX = TX + 1, BY = TY + 1;
+  __shared__ T sE[2][3][EY][EX];
+  __shared__ T sB[2][3][BY][BX];
+  const int nx = m.n[0], ny = m.n[1], nz = m.n[2];
+  const int64_t V = m.V;
+  const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY;
+  const int z0 = blockIdx.z * zchunk;
+  const int z1 = min(z0 + zchunk, nz);
+  const int tid = threadIdx.y * TX + threadIdx.x;
+  constexpr int NT = TX * TY;
+
+  auto load_E = [&](int k, int slot) {
+    const int64_t pk = (int64_t)k * nx * ny;
+    for (int e = tid; e < EX * EY; e += NT) {
+      const int ey = e / EX, ex = e - ey * EX;
+      int x = x0 - 1 + ex, y = y0 - 1 + ey;
+      x = (x < 0) ? x + nx : (x >= nx ? x - nx : x);
+      y = (y < 0) ? y + ny : (y >= ny ? y - ny : y);
+      if (x >= nx) x = nx - 1;  // only for tiles wider than the mesh (unused values)
+      if (y >= ny) y = ny - 1;
+      const int64_t v = pk + (int64_t)y * nx + x;
+      sE[slot][0][ey][ex] = Din[v] * ie[v];
+      sE[slot][1][ey][ex] = Din[V + v] * ie[V + v];
+      sE[slot][2][ey][ex] = Din[2 * V + v] * ie[2 * V + v];
+    }
+  };
+  // B' of plane k on the tile plus its low halo; interior values also to Bout
+  auto compute_B = [&](int k, int ec, int en, int slot, bool store) {
+    const int64_t pk = (int64_t)k * nx * ny;
+    for (int e = tid; e < BX * BY; e += NT) {
+      const int by = e / BX, bx = e - by * BX;
+      int x = x0 - 1 + bx, y = y0 - 1 + by;
+      const bool inside = bx >= 1 && by >= 1 && x < nx && y < ny;
+      x = (x < 0) ? x + nx : (x >= nx ? x - nx : x);
+      y = (y < 0) ? y + ny : (y >= ny ? y - ny : y);
+      if (x >= nx) x = nx - 1;
+      if (y >= ny) y = ny - 1;
+      const int64_t v = pk + (int64_t)y * nx + x;
+      const T Ex = sE[ec][0][by][bx], Ey = sE[ec][1][by][bx], Ez = sE[ec][2][by][bx];
+      const T Ey_x = sE[ec][1][by][bx + 1], Ez_x = sE[ec][2][by][bx + 1];
+      const T Ex_y = sE[ec][0][by + 1][bx], Ez_y = sE[ec][2][by + 1][bx];
+      const T Ex_z = sE[en][0][by][bx], Ey_z = sE[en][1][by][bx];
+      const T bxv = Bin[v] - cB * (((Ey + Ez_y) - Ey_z) - Ez);
+      const T byv = Bin[V + v] - cB * (((Ez + Ex_z) - Ez_x) - Ex);
+      const T bzv = Bin[2 * V + v] - cB * (((Ex + Ey_x) - Ex_y) - Ey);
+      sB[slot][0][by][bx] = bxv;
+      sB[slot][1][by][bx] = byv;
+      sB[slot][2][by][bx] = bzv;
+      if (store && inside) {
+        Bout[v] = bxv;
+        Bout[V + v] = byv;
+        Bout[2 * V + v] = bzv;
+      }
+    }
+  };
+
+  int ec = 0, en = 1, bp = 0, bc = 1;
+  const int zm = (z0 == 0) ? nz - 1 : z0 - 1;
+  load_E(zm, ec);
+  load_E(z0, en);
+  __syncthreads();
+  compute_B(zm, ec, en, bp, false);
+  ec ^= 1;
+  en ^= 1;
+  for (int k = z0; k < z1; ++k) {
+    __syncthreads();
+    load_E(k + 1 == nz ? 0 : k + 1, en);
+    __syncthreads();
+    compute_B(k, ec, en, bc, true);
+    __syncthreads();
+    const int tx = threadIdx.x, ty = threadIdx.y;
+    const int x = x0 + tx, y = y0 + ty;
+    if (x < nx && y < ny) {
+      const int bx = tx + 1, by = ty + 1;
+      const int64_t v = (int64_t)k * nx * ny + (int64_t)y * nx + x;
+      const T Bx = sB[bc][0][by][bx], By = sB[bc][1][by][bx], Bz = sB[bc][2][by][bx];
+      Dout[v] = Din[v] + cD * (((Bz - sB[bc][2][by - 1][bx]) - By) + sB[bp][1][by][bx]);
+      Dout[V + v] = Din[V + v] + cD * (((Bx - sB[bp][0][by][bx]) - Bz) + sB[bc][2][by][bx - 1]);
+      Dout[2 * V + v] = Din[2 * V + v] + cD * (((By - sB[bc][1][by][bx - 1]) - Bx) + sB[bc][0][by - 1][bx]);
+    }
+    ec ^= 1;
+    en ^= 1;
+    bp ^= 1;
+    bc ^= 1;
+  }
+}
+
+__device__ inline double block_sum(double x, double* sh) {
+  for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xffffffffu, x, o);
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  if (lane == 0) sh[w] = x;
+  __syncthreads();
+  double r = 0.0;
+  if (threadIdx.x == 0)
+    for (int t = 0; t < (int)(blockDim.x >> 5); ++t) r += sh[t];
+  __syncthreads();
+  return r;
+}
+
+__device__ inline double block_max(double x, double* sh) {
+  for (int o = 16; o > 0; o >>= 1) x = fmax(x, __shfl_down_sync(0xffffffffu, x, o));
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  if (lane == 0) sh[w] = x;
+  __syncthreads();
+  double r = 0.0;
+  if (threadIdx.x == 0)
+    for (int t = 0; t < (int)(blockDim.x >> 5); ++t) r = fmax(r, sh[t]);
+  __syncthreads();
+  return r;
+}
+
+__device__ inline void coords(const Mesh& m, int64_t v, int& i, int& j, int& k) {
+  i = (int)(v % m.n[0]);
+  const int64_t r = v / m.n[0];
+  j = (int)(r % m.n[1]);
+  k = (int)(r / m.n[1]);
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kRedThreads)
+    k_field_energy(Mesh m, const T* __restrict__ D, const T* __restrict__ B,
+                   const T* __restrict__ ie, double coefB, double* part_el, double* part_mag) {
+  __shared__ double sh[kRedThreads / 32];
+  const int64_t V = m.V;
+  double el = 0.0, mag = 0.0;
+  for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < V;
+       v += (int64_t)gridDim.x * blockDim.x) {
+    int i, j, k;
+    coords(m, v, i, j, k);
+    const int ip = (i + 1 == m.n[0]) ? 0 : i + 1;
+    const int jp = (j + 1 == m.n[1]) ? 0 : j + 1;
+    const int kp = (k + 1 == m.n[2]) ? 0 : k + 1;
+    const int64_t vx = vindex(m, ip, j, k), vy = vindex(m, i, jp, k), vz = vindex(m, i, j, kp);
+    double E[3], Ex_[3], Ey_[3], Ez_[3];
+    for (int d = 0; d < 3; ++d) {
+      const double dd = (double)D[d * V + v], ii = (double)ie[d * V + v];
+      E[d] = dd * ii;
+      el += 0.5 * dd * dd * ii;
+      Ex_[d] = (double)D[d * V + vx] * (double)ie[d * V + vx];
+      Ey_[d] = (double)D[d * V + vy] * (double)ie[d * V + vy];
+      Ez_[d] = (double)D[d * V + vz] * (double)ie[d * V + vz];
+    }
+    const double cx = ((E[1] + Ey_[2]) - Ez_[1]) - E[2];
+    const double cy = ((E[2] + Ez_[0]) - Ex_[2]) - E[0];
+    const double cz = ((E[0] + Ex_[1]) - Ey_[0]) - E[1];
+    const double bx = (double)B[v], by = (double)B[V + v], bz = (double)B[2 * V + v];
+    mag += bx * (bx - coefB * cx) + by * (by - coefB * cy) + bz * (bz - coefB * cz);
+  }
+  const double s1 = block_sum(el, sh);
+  const double s2 = block_sum(mag, sh);
+  if (threadIdx.x == 0) {
+    part_el[blockIdx.x] = s1;
+    part_mag[blockIdx.x] = s2;
+  }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kRedThreads)
+    k_gauss_check(Mesh m, const T* __restrict__ D, const long long* __restrict__ Lg,
+                  const long long* __restrict__ Q, double a2, double* part_res,
+                  unsigned long long* mismatch) {
+  __shared__ double sh[kRedThreads / 32];
+  const int64_t V = m.V;
+  double res = 0.0;
+  unsigned long long bad = 0;
+  const double unit = 3.552713678800501e-15;  // 2^-48
+  for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < V;
+       v += (int64_t)gridDim.x * blockDim.x) {
+    int i, j, k;
+    coords(m, v, i, j, k);
+    const int im = (i == 0) ? m.n[0] - 1 : i - 1;
+    const int jm = (j == 0) ? m.n[1] - 1 : j - 1;
+    const int km = (k == 0) ? m.n[2] - 1 : k - 1;
+    const int64_t vx = vindex(m, im, j, k), vy = vindex(m, i, jm, k), vz = vindex(m, i, j, km);
+    const long long dl = (Lg[v] - Lg[vx]) + (Lg[V + v] - Lg[V + vy]) +
+                         (Lg[2 * V + v] - Lg[2 * V + vz]);
+    if (dl != Q[v]) ++bad;
+    const double dd = ((double)D[v] - (double)D[vx]) + ((double)D[V + v] - (double)D[V + vy]) +
+                      ((double)D[2 * V + v] - (double)D[2 * V + vz]);
+    res = fmax(res, fabs(dd * a2 - (double)Q[v] * unit));
+  }
+  const double r = block_max(res, sh);
+  if (threadIdx.x == 0) part_res[blockIdx.x] = r;
+  if (bad) atomicAdd(mismatch, bad);
+}
+
+}  // namespace
+
+void launch_curl_B(const Mesh& m, int prec, void* B, const void* D, const void* ie,
+                   double coef, cudaStream_t st) {
+  const dim3 blk(kBX, kBY, 1);
+  if (prec == 1)
+    k_curl_B<float><<<field_grid(m), blk, 0, st>>>(m, (float*)B, (const float*)D,
+                                                   (const float*)ie, (float)coef);
+  else
+    k_curl_B<double><<<field_grid(m), blk, 0, st>>>(m, (double*)B, (const double*)D,
+                                                    (const double*)ie, coef);
+}
+
+void launch_curl_D(const Mesh& m, int prec, void* D, const void* B, double coef,
+                   cudaStream_t st) {
+  const dim3 blk(kBX, kBY, 1);
+  if (prec == 1)
+    k_curl_D<float><<<field_grid(m), blk, 0, st>>>(m, (float*)D, (const float*)B, (float)coef);
+  else
+    k_curl_D<double><<<field_grid(m), blk, 0, st>>>(m, (double*)D, (const double*)B, coef);
+}
+
+void launch_fused_curl(const Mesh& m, int prec, const void* Din, const void* Bin, const void* ie,
+                       void* Dout, void* Bout, double cB, double cD, int zchunk,
+                       cudaStream_t st) {
+  constexpr int TX = 32, TY = 8;
+  if (zchunk < 1) zchunk = fused_zchunk(m);
+  const dim3 grid((m.n[0] + TX - 1) / TX, (m.n[1] + TY - 1) / TY, (m.n[2] + zchunk - 1) / zchunk);
+  const dim3 blk(TX, TY, 1);
+  if (prec == 1)
+    k_fused_curl<float, TX, TY><<<grid, blk, 0, st>>>(m, (const float*)Din, (const float*)Bin,
+                                                      (const float*)ie, (float*)Dout, (float*)Bout,
+                                                      (float)cB, (float)cD, zchunk);
+  else
+    k_fused_curl<double, TX, TY><<<grid, blk, 0, st>>>(m, (const double*)Din, (const double*)Bin,
+                                                       (const double*)ie, (double*)Dout,
+                                                       (double*)Bout, cB, cD, zchunk);
+}
+
+int fused_zchunk(const Mesh& m) {
+  // enough CTAs to fill the GPU a few times over, but chunks long enough
+  // that the recomputed prologue plane stays a small overhead
+  const int64_t tiles = (int64_t)((m.n[0] + 31) / 32) * ((m.n[1] + 7) / 8);
+  const int64_t target = 4 * 152;
+  int64_t nchunks = (target + tiles - 1) / tiles;
+  int64_t zc = (m.n[2] + nchunks - 1) / nchunks;
+  if (zc < 4) zc = 4;
+  if (zc > m.n[2]) zc = m.n[2];
+  return (int)zc;
+}
+
+void launch_circ64(const Mesh& m, double* w, const double* u, const double* ie, double sign,
+                   cudaStream_t st) {
+  k_circ64<<<field_grid(m), dim3(kBX, kBY, 1), 0, st>>>(m, w, u, ie, sign);
+}
+
+void launch_curlT64(const Mesh& m, double* u, const double* p, cudaStream_t st) {
+  k_curlT64<<<field_grid(m), dim3(kBX, kBY, 1), 0, st>>>(m, u, p);
+}
+
+void launch_plaquette_diag(const Mesh& m, double* diag, const double* ie, cudaStream_t st) {
+  k_plaquette_diag<<<field_grid(m), dim3(kBX, kBY, 1), 0, st>>>(m, diag, ie);
+}
+
+void launch_field_energy(const Mesh& m, int prec, const void* D, const void* B, const void* ie,
+                         double coefB, double* part_el, double* part_mag, cudaStream_t st) {
+  if (prec == 1)
+    k_field_energy<float><<<kRedBlocks, kRedThreads, 0, st>>>(
+        m, (const float*)D, (const float*)B, (const float*)ie, coefB, part_el, part_mag);
+  else
+    k_field_energy<double><<<kRedBlocks, kRedThreads, 0, st>>>(
+        m, (const double*)D, (const double*)B, (const double*)ie, coefB, part_el, part_mag);
+}
+
+void launch_gauss_check(const Mesh& m, int prec, const void* D, const long long* Lg,
+                        const long long* Q, double a2, double* part_res,
+                        unsigned long long* mismatch, cudaStream_t st) {
+  if (prec == 1)
+    k_gauss_check<float><<<kRedBlocks, kRedThreads, 0, st>>>(m, (const float*)D, Lg, Q, a2,
+                                                            part_res, mismatch);
+  else
+    k_gauss_check<double><<<kRedBlocks, kRedThreads, 0, st>>>(m, (const double*)D, Lg, Q, a2,
+                                                             part_res, mismatch);
+}
+
+}  // namespace memd

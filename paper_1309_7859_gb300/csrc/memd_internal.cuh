@@ -1,0 +1,166 @@
+// memd_internal.cuh -- shared declarations of the MEMD CUDA library (sm_103a).
+//
+// Lattice conventions (Sec. II, Fig. 2): vertex v = (i, j, k) at flat index
+// i + nx (j + ny k); link (d, v) joins v to v + e_d and is stored at d V + v;
+// plaquette (d, v) has normal e_d, spans e_{d+1}, e_{d+2} from v and is stored
+// at d V + v.  Fixed point: S = 2^16 sub-cell steps; charge and flux unit
+// e 2^-48.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace memd {
+
+constexpr int kWBits = 16;
+constexpr int64_t kS = int64_t(1) << kWBits;
+
+struct Mesh {
+  int n[3];
+  int64_t V;
+  double a;
+  double L[3];
+};
+
+// error bits raised by kernels into a device word
+enum : unsigned int {
+  kErrCellJump = 1u,
+  kErrGauss = 2u,
+  kErrOverflow = 4u,
+  kErrNonFinite = 8u,
+};
+
+// Small device-resident state shared by the step kernels.
+struct DevState {
+  unsigned long long Pacc[3];  // sum q U (int64 bits) of the current positions
+  long long Plast[3];          // P of the last completed update
+  long long step;              // steps since init (Langevin counter)
+  unsigned int err;            // kErr* bits
+  unsigned int ticket;         // blocks of the gather that have finished
+  long long lsum[3];           // scratch: sum of the ledger per component
+  double scal[16];             // scratch scalars for the relaxation
+};
+
+__host__ __device__ inline int64_t vindex(const Mesh& m, int i, int j, int k) {
+  return (int64_t)i + (int64_t)m.n[0] * ((int64_t)j + (int64_t)m.n[1] * k);
+}
+
+__host__ __device__ inline int wrapi(int i, int n) {
+  i %= n;
+  return i < 0 ? i + n : i;
+}
+
+// ------------------------------------------------------------ field kernels
+// (memd_field.cu)
+void launch_curl_B(const Mesh& m, int prec, void* B, const void* D, const void* ie,
+                   double coef, cudaStream_t st);
+void launch_curl_D(const Mesh& m, int prec, void* D, const void* B, double coef,
+                   cudaStream_t st);
+// fused B then D update with double-buffered fields (zchunk <= 0: automatic)
+void launch_fused_curl(const Mesh& m, int prec, const void* Din, const void* Bin, const void* ie,
+                       void* Dout, void* Bout, double cB, double cD, int zchunk,
+                       cudaStream_t st);
+int fused_zchunk(const Mesh& m);
+// FP64 helpers of the relaxation: w = sign * circulation(ie * u) per plaquette
+void launch_circ64(const Mesh& m, double* w, const double* u, const double* ie,
+                   double sign, cudaStream_t st);
+// u = transpose of the circulation map applied to a plaquette field p
+void launch_curlT64(const Mesh& m, double* u, const double* p, cudaStream_t st);
+// diag_p = sum of ie over the 4 links of each plaquette
+void launch_plaquette_diag(const Mesh& m, double* diag, const double* ie, cudaStream_t st);
+
+// --------------------------------------------------- setup / init kernels
+// (memd_setup.cu)
+struct EpsDesc {
+  int kind;
+  int axis;
+  double p[8];
+};
+void launch_eps_links(const Mesh& m, const EpsDesc& e, const double* values, double* ie64,
+                      unsigned int* err, cudaStream_t st);
+void launch_cast(int prec, void* dst, const double* src, int64_t count, cudaStream_t st);
+void launch_widen(int prec, double* dst, const void* src, int64_t count, cudaStream_t st);
+// Green's table: 8 values into G (device), using `partial` scratch of
+// green_partials() doubles
+int green_partials();
+void launch_green(const Mesh& m, double* partial, double* G, cudaStream_t st);
+// Gauss scan of vertex charges Q into the ledger (Fig. 1); scratch of
+// scan_scratch(m) int64
+int64_t scan_scratch(const Mesh& m);
+void launch_gauss_scan(const Mesh& m, const long long* Q, long long* Lg, long long* scratch,
+                       unsigned int* err, cudaStream_t st);
+// D64 = Lg scale + shift_d with shift_d = -P_d / Vbox - mean(Lg_d) scale
+void launch_init_D(const Mesh& m, double* D64, const long long* Lg, DevState* ds,
+                   double scale, double Vbox, cudaStream_t st);
+void launch_ledger_sums(const Mesh& m, const long long* Lg, DevState* ds, cudaStream_t st);
+
+// deterministic FP64 reductions (memd_setup.cu)
+int reduce_blocks();
+// partial[b] = block sums of x[i] * y[i] (y may be NULL: sum of x)
+void launch_dot(const double* x, const double* y, int64_t n, double* partial, cudaStream_t st);
+// partial[b] = block max of |x[i]| (|x[i] y[i]| when y is given)
+void launch_absmax(const double* x, const double* y, int64_t n, double* partial,
+                   cudaStream_t st);
+// out[0] = op over partial[0..reduce_blocks())  (op 0 = sum, 1 = max)
+void launch_finish(const double* partial, int op, double* out, cudaStream_t st);
+
+// ------------------------------------------------------- particle kernels
+// (memd_particles.cu, built with -fmad=false)
+struct Particles {
+  int64_t n;
+  double* x;
+  double* v;
+  double* m;
+  double* F;
+  double* Ft;
+  int* img;
+  int* q;
+  int* mv;  // 6 ints per particle: old cell (3), new cell (3) of the last move
+};
+struct StepParams {
+  double dt;
+  double coefB;   // dt / a
+  double coefD;   // c^2 dt / a
+  double scale;   // 2^-48 / a^2
+  double Vbox;
+  double G[8];
+  double Minv[9];
+  int self_mode;
+  int dipole_corr;
+  int thermo;
+  double gamma;
+  double kT;
+  unsigned long long seed;
+};
+void launch_fold_init(const Mesh& m, Particles p, const double* pos_in, const int* img_in,
+                      unsigned int* err, cudaStream_t st);
+void launch_cic(const Mesh& m, Particles p, long long* Q, long long bg, cudaStream_t st);
+void launch_dipole(const Mesh& m, Particles p, DevState* ds, cudaStream_t st);
+void launch_kick_drift_deposit(const Mesh& m, const StepParams& sp, Particles p,
+                               long long* Tb, DevState* ds, cudaStream_t st);
+void launch_move_deposit(const Mesh& m, Particles p, const double* pos_new,
+                         const int* img_new, long long* Tb, DevState* ds, cudaStream_t st);
+void launch_apply(const Mesh& m, int prec, Particles p, long long* Tb, long long* Lg, void* D,
+                  double scale, cudaStream_t st);
+// finish: 0 nothing, 1 close the update (P of this state, clear the
+// accumulator), 2 also advance the step counter; done by the last CTA
+void launch_gather(const Mesh& m, int prec, const StepParams& sp, Particles p, const void* D,
+                   const void* ie, const double* ie64, DevState* ds, int kick, int finish,
+                   cudaStream_t st);
+void launch_step_end(DevState* ds, int advance, cudaStream_t st);
+// energy pieces into partial sums (memd_particles.cu)
+void launch_particle_energy(const Mesh& m, const StepParams& sp, Particles p,
+                            const double* ie64, double* part_ke, double* part_self,
+                            cudaStream_t st);
+
+// ------------------------------------------------------- field diagnostics
+// (memd_field.cu)
+void launch_field_energy(const Mesh& m, int prec, const void* D, const void* B,
+                         const void* ie, double coefB, double* part_el, double* part_mag,
+                         cudaStream_t st);
+// Gauss check: mismatch count of div Lg vs Q and max |a^2 div D - Q 2^-48|
+void launch_gauss_check(const Mesh& m, int prec, const void* D, const long long* Lg,
+                        const long long* Q, double a2, double* part_res,
+                        unsigned long long* mismatch, cudaStream_t st);
+
+}  // namespace memd

@@ -1,0 +1,368 @@
+"""Thin ctypes binding of the MEMD C ABI (include/memd.h).
+
+Argument marshalling only: every step of the method runs in the CUDA kernels
+of libmemd.so.  There is no CPU fallback; a missing library or GPU raises.
+Device memory can come from PyTorch's caching allocator and work is issued on
+a PyTorch stream when torch is available (`use_torch=True`).
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+from dataclasses import dataclass
+
+import numpy as np
+
+from . import build as _build
+
+FP64, FP32 = 0, 1
+SELF_NONE, SELF_GF, SELF_DIRECT = 0, 1, 2
+EPS_KINDS = {"const": 0, "links": 1, "vertices": 2, "tanh": 3, "sin": 4}
+STATUS = {0: "OK", 1: "INVALID", 2: "COURANT", 3: "OOM", 4: "CUDA", 5: "CELL_JUMP", 6: "GAUSS",
+          7: "RELAX_NOCONV", 8: "DIPOLE_DRIFT", 9: "TIMEOUT", 10: "STATE", 11: "OVERFLOW"}
+
+EXPORTS = ("memd_default_options", "memd_status_string", "memd_last_error", "memd_create",
+           "memd_destroy", "memd_init_field", "memd_step", "memd_forces", "memd_forces_device",
+           "memd_energy", "memd_get_particles", "memd_set_particles", "memd_move",
+           "memd_get_fields", "memd_set_fields", "memd_compute_forces", "memd_get_setup",
+           "memd_get_kernel_stats", "memd_reset_kernel_stats", "memd_synchronize")
+
+
+class MemdError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+ALLOC = C.CFUNCTYPE(C.c_void_p, C.c_void_p, C.c_size_t, C.c_void_p)
+FREE = C.CFUNCTYPE(None, C.c_void_p, C.c_void_p, C.c_size_t, C.c_void_p)
+
+
+class EpsProfile(C.Structure):
+    _fields_ = [("kind", C.c_int32), ("axis", C.c_int32), ("values", C.POINTER(C.c_double)),
+                ("params", C.c_double * 8)]
+
+
+class Options(C.Structure):
+    _fields_ = [("precision", C.c_int32), ("self_mode", C.c_int32), ("dipole_corr", C.c_int32),
+                ("relax_max_iter", C.c_int32), ("relax_tol", C.c_double), ("seed", C.c_uint64),
+                ("cuda_stream", C.c_void_p), ("device", C.c_int32), ("use_graphs", C.c_int32),
+                ("alloc", ALLOC), ("free", FREE), ("alloc_user", C.c_void_p),
+                ("time_kernels", C.c_int32), ("reserved", C.c_int32 * 7)]
+
+
+class Thermostat(C.Structure):
+    _fields_ = [("gamma", C.c_double), ("kT", C.c_double)]
+
+
+class EnergyTerms(C.Structure):
+    _fields_ = [("kinetic", C.c_double), ("electric", C.c_double), ("magnetic", C.c_double),
+                ("self", C.c_double), ("dipole", C.c_double), ("total", C.c_double),
+                ("P", C.c_double * 3), ("gauss_residual", C.c_double),
+                ("gauss_exact", C.c_int32), ("pad", C.c_int32), ("step", C.c_int64)]
+
+    def as_dict(self):
+        return {"kinetic": self.kinetic, "electric": self.electric, "magnetic": self.magnetic,
+                "self": self.self, "dipole": self.dipole, "total": self.total,
+                "P0": self.P[0], "P1": self.P[1], "P2": self.P[2],
+                "gauss_residual": self.gauss_residual, "gauss_exact": float(self.gauss_exact),
+                "step": self.step}
+
+
+class KernelStats(C.Structure):
+    _fields_ = [("field_ms", C.c_double), ("field_launches", C.c_int64),
+                ("field_bytes", C.c_double), ("launches_per_step", C.c_int64)]
+
+
+_lib = None
+
+
+def library_path():
+    return _build.LIB
+
+
+def lib(build_if_missing=True):
+    """Load libmemd.so (building it first when it is missing or stale)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = _build.build() if build_if_missing else _build.LIB
+    if not os.path.exists(path):
+        raise RuntimeError(f"libmemd.so not built at {path}")
+    L = C.CDLL(path)
+    vp, i32p, f64p, i64p = C.c_void_p, C.POINTER(C.c_int32), C.POINTER(C.c_double), C.POINTER(C.c_int64)
+    L.memd_default_options.argtypes = [C.POINTER(Options)]
+    L.memd_status_string.restype = C.c_char_p
+    L.memd_status_string.argtypes = [C.c_int]
+    L.memd_last_error.restype = C.c_char_p
+    L.memd_last_error.argtypes = [vp]
+    L.memd_create.argtypes = [i32p, f64p, C.POINTER(EpsProfile), C.c_double, C.c_double,
+                              C.POINTER(Options), C.POINTER(vp)]
+    L.memd_destroy.argtypes = [vp]
+    L.memd_init_field.argtypes = [vp, C.c_int64, f64p, i32p, f64p, f64p]
+    L.memd_step.argtypes = [vp, C.c_int64, C.POINTER(Thermostat)]
+    L.memd_forces.argtypes = [vp, f64p]
+    L.memd_forces_device.argtypes = [vp, C.POINTER(vp)]
+    L.memd_energy.argtypes = [vp, C.POINTER(EnergyTerms)]
+    L.memd_get_particles.argtypes = [vp, f64p, f64p, i32p]
+    L.memd_set_particles.argtypes = [vp, f64p, f64p, i32p]
+    L.memd_move.argtypes = [vp, f64p, i32p]
+    L.memd_get_fields.argtypes = [vp, f64p, f64p, i64p]
+    L.memd_set_fields.argtypes = [vp, f64p, f64p, i64p]
+    L.memd_compute_forces.argtypes = [vp]
+    L.memd_get_setup.argtypes = [vp, f64p, f64p, f64p]
+    L.memd_get_kernel_stats.argtypes = [vp, C.POINTER(KernelStats)]
+    L.memd_reset_kernel_stats.argtypes = [vp]
+    L.memd_synchronize.argtypes = [vp]
+    for name in EXPORTS:
+        if name not in ("memd_default_options", "memd_destroy", "memd_status_string",
+                        "memd_last_error"):
+            getattr(L, name).restype = C.c_int
+    _lib = L
+    return L
+
+
+def _ptr(a, ct):
+    if a is None:
+        return None
+    return a.ctypes.data_as(C.POINTER(ct))
+
+
+def _f64(a, shape=None):
+    a = np.ascontiguousarray(a, dtype=np.float64)
+    return a.reshape(shape) if shape is not None else a
+
+
+def _i32(a, shape=None):
+    a = np.ascontiguousarray(a, dtype=np.int32)
+    return a.reshape(shape) if shape is not None else a
+
+
+class _TorchAllocator:
+    """Routes the library's device allocations through torch's caching allocator."""
+
+    def __init__(self, device):
+        import torch
+        self.torch = torch
+        self.device = device
+        self.alloc = ALLOC(self._alloc)
+        self.free = FREE(self._free)
+
+    def _alloc(self, user, nbytes, stream):
+        try:
+            return self.torch.cuda.caching_allocator_alloc(int(nbytes), self.device,
+                                                           int(stream or 0))
+        except Exception:  # out of memory: the library reports MEMD_ERR_OOM
+            return None
+
+    def _free(self, user, ptr, nbytes, stream):
+        self.torch.cuda.caching_allocator_delete(int(ptr))
+
+
+@dataclass
+class StepTiming:
+    field_ms: float
+    field_launches: int
+    field_bytes: float
+    launches_per_step: int
+
+
+class Memd:
+    """One MEMD system on one GPU (a memd_ctx)."""
+
+    def __init__(self, mesh, box, eps=None, c_light=1.0, dt=0.01, precision="fp64",
+                 self_mode=SELF_GF, dipole_corr=True, relax_tol=1e-12, relax_max_iter=200000,
+                 seed=0, use_graphs=True, time_kernels=False, use_torch=True, stream=None,
+                 device=None):
+        self._L = lib()
+        self._h = C.c_void_p(None)
+        self.mesh = tuple(int(n) for n in mesh)
+        self.box = tuple(float(b) for b in box)
+        self.V = self.mesh[0] * self.mesh[1] * self.mesh[2]
+        self.n = 0
+        o = Options()
+        self._L.memd_default_options(C.byref(o))
+        o.precision = FP32 if precision in ("fp32", FP32) else FP64
+        o.self_mode = int(self_mode)
+        o.dipole_corr = 1 if dipole_corr else 0
+        o.relax_tol = float(relax_tol)
+        o.relax_max_iter = int(relax_max_iter)
+        o.seed = int(seed) & ((1 << 64) - 1)
+        o.use_graphs = 1 if use_graphs else 0
+        o.time_kernels = 1 if time_kernels else 0
+        self._alloc = None
+        self._stream = stream
+        if use_torch:
+            import torch
+            if not torch.cuda.is_available():
+                raise RuntimeError("MEMD needs a CUDA GPU; torch sees none")
+            dev = torch.cuda.current_device() if device is None else int(device)
+            o.device = dev
+            if stream is None:
+                stream = torch.cuda.Stream(device=dev)
+                self._stream = stream
+            o.cuda_stream = C.c_void_p(stream.cuda_stream)
+            self._alloc = _TorchAllocator(dev)
+            o.alloc = self._alloc.alloc
+            o.free = self._alloc.free
+        else:
+            o.device = -1 if device is None else int(device)
+            if stream is not None:
+                o.cuda_stream = C.c_void_p(int(stream))
+        e, keep = make_eps(eps)
+        mesh_a = np.asarray(self.mesh, dtype=np.int32)
+        box_a = np.asarray(self.box, dtype=np.float64)
+        st = self._L.memd_create(_ptr(mesh_a, C.c_int32), _ptr(box_a, C.c_double), C.byref(e),
+                                 float(c_light), float(dt), C.byref(o), C.byref(self._h))
+        del keep
+        if st != 0:
+            raise MemdError(st, "memd_create failed")
+        self.precision = "fp32" if o.precision == FP32 else "fp64"
+
+    # ---------------------------------------------------------------- helpers
+    def _check(self, st, what):
+        if st != 0:
+            msg = self._L.memd_last_error(self._h)
+            raise MemdError(st, f"{what}: {msg.decode() if msg else ''}")
+
+    def close(self):
+        if self._h:
+            self._L.memd_destroy(self._h)
+            self._h = C.c_void_p(None)
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @property
+    def stream(self):
+        return self._stream
+
+    # ----------------------------------------------------------------- calls
+    def init_field(self, x, q, m=None, v=None):
+        x = _f64(x).reshape(-1, 3)
+        n = x.shape[0]
+        q = _i32(q, (n,))
+        m = None if m is None else _f64(m, (n,))
+        v = None if v is None else _f64(v, (n, 3))
+        self._check(self._L.memd_init_field(self._h, n, _ptr(x, C.c_double), _ptr(q, C.c_int32),
+                                            _ptr(m, C.c_double), _ptr(v, C.c_double)),
+                    "memd_init_field")
+        self.n = n
+
+    def step(self, nsteps=1, thermostat=None):
+        th = None
+        if thermostat is not None:
+            th = Thermostat(float(thermostat[0]), float(thermostat[1]))
+        self._check(self._L.memd_step(self._h, int(nsteps), C.byref(th) if th else None),
+                    "memd_step")
+
+    def forces(self, out=None):
+        out = np.zeros((self.n, 3)) if out is None else out
+        self._check(self._L.memd_forces(self._h, _ptr(out, C.c_double)), "memd_forces")
+        return out
+
+    def forces_device_ptr(self):
+        p = C.c_void_p()
+        self._check(self._L.memd_forces_device(self._h, C.byref(p)), "memd_forces_device")
+        return p.value
+
+    def energy(self):
+        e = EnergyTerms()
+        self._check(self._L.memd_energy(self._h, C.byref(e)), "memd_energy")
+        return e.as_dict()
+
+    def particles(self):
+        x = np.zeros((self.n, 3))
+        v = np.zeros((self.n, 3))
+        img = np.zeros((self.n, 3), dtype=np.int32)
+        self._check(self._L.memd_get_particles(self._h, _ptr(x, C.c_double), _ptr(v, C.c_double),
+                                               _ptr(img, C.c_int32)), "memd_get_particles")
+        return x, v, img
+
+    def get_particles_into(self, x=None, v=None, img=None):
+        self._check(self._L.memd_get_particles(self._h, _ptr(x, C.c_double), _ptr(v, C.c_double),
+                                               _ptr(img, C.c_int32)), "memd_get_particles")
+
+    def set_particles(self, x=None, v=None, img=None):
+        x = None if x is None else _f64(x, (self.n, 3))
+        v = None if v is None else _f64(v, (self.n, 3))
+        img = None if img is None else _i32(img, (self.n, 3))
+        self._check(self._L.memd_set_particles(self._h, _ptr(x, C.c_double), _ptr(v, C.c_double),
+                                               _ptr(img, C.c_int32)), "memd_set_particles")
+
+    def move(self, x, img=None):
+        x = _f64(x, (self.n, 3))
+        img = None if img is None else _i32(img, (self.n, 3))
+        self._check(self._L.memd_move(self._h, _ptr(x, C.c_double), _ptr(img, C.c_int32)),
+                    "memd_move")
+
+    def fields(self):
+        Nx, Ny, Nz = self.mesh
+        D = np.zeros((3, Nz, Ny, Nx))
+        B = np.zeros((3, Nz, Ny, Nx))
+        Lg = np.zeros((3, Nz, Ny, Nx), dtype=np.int64)
+        self._check(self._L.memd_get_fields(self._h, _ptr(D, C.c_double), _ptr(B, C.c_double),
+                                            _ptr(Lg, C.c_int64)), "memd_get_fields")
+        return D, B, Lg
+
+    def set_fields(self, D=None, B=None, Lg=None):
+        D = None if D is None else _f64(D).ravel()
+        B = None if B is None else _f64(B).ravel()
+        Lg = None if Lg is None else np.ascontiguousarray(Lg, dtype=np.int64).ravel()
+        self._check(self._L.memd_set_fields(self._h, _ptr(D, C.c_double), _ptr(B, C.c_double),
+                                            _ptr(Lg, C.c_int64)), "memd_set_fields")
+
+    def compute_forces(self):
+        self._check(self._L.memd_compute_forces(self._h), "memd_compute_forces")
+
+    def setup(self):
+        Nx, Ny, Nz = self.mesh
+        ie = np.zeros((3, Nz, Ny, Nx))
+        G = np.zeros(8)
+        M = np.zeros((3, 3))
+        self._check(self._L.memd_get_setup(self._h, _ptr(ie, C.c_double), _ptr(G, C.c_double),
+                                           _ptr(M, C.c_double)), "memd_get_setup")
+        return ie, G, M
+
+    def kernel_stats(self):
+        k = KernelStats()
+        self._check(self._L.memd_get_kernel_stats(self._h, C.byref(k)), "memd_get_kernel_stats")
+        return StepTiming(k.field_ms, k.field_launches, k.field_bytes, k.launches_per_step)
+
+    def reset_kernel_stats(self):
+        self._check(self._L.memd_reset_kernel_stats(self._h), "memd_reset_kernel_stats")
+
+    def synchronize(self):
+        self._check(self._L.memd_synchronize(self._h), "memd_synchronize")
+
+
+def make_eps(spec):
+    """EpsProfile from an inputs.EpsSpec-like object or dict (kept array returned too)."""
+    e = EpsProfile()
+    keep = None
+    if spec is None:
+        e.kind = 0
+        e.params[0] = 1.0
+        return e, keep
+    kind = spec["kind"] if isinstance(spec, dict) else spec.kind
+    axis = spec.get("axis", 0) if isinstance(spec, dict) else spec.axis
+    params = spec.get("params", ()) if isinstance(spec, dict) else spec.params
+    values = spec.get("values") if isinstance(spec, dict) else spec.values
+    e.kind = EPS_KINDS[kind] if isinstance(kind, str) else int(kind)
+    e.axis = int(axis)
+    pp = list(params) + [0.0] * (8 - len(params))
+    for i in range(8):
+        e.params[i] = float(pp[i])
+    if values is not None:
+        keep = np.ascontiguousarray(values, dtype=np.float64).ravel()
+        e.values = keep.ctypes.data_as(C.POINTER(C.c_double))
+    return e, keep
+
+
+def from_system(sysc, **kw):
+    """Memd context for an inputs.System (not yet initialised)."""
+    return Memd(sysc.mesh, sysc.box, sysc.eps, c_light=sysc.c_light, dt=sysc.dt,
+                precision=sysc.precision, seed=sysc.seed, **kw)
