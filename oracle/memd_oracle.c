@@ -177,14 +177,17 @@ void orc_green_table(const int32_t N[3], double *G8) {
 }
 
 /* ------------------------------------------------ particle fixed point
- * Positions are folded into [0, L) with a per-axis image counter; the
+ * Sec. V: the periodic box is stitched locally, so a position leaving [0, L)
+ * re-enters shifted by whole box lengths, counted in a per-axis image
+ * counter (the unfolded coordinate is x + img L).  A sum that rounds up to L
+ * is the start of the next image.  Callers bound |x| by a few L.  The
  * lattice coordinate u = x / a splits into a cell c and a sub-cell step
  * f = floor((u - c) S) in [0, S). */
 static void fold(double L, double *x, int32_t *img) {
-  double fl = floor(*x / L);
-  double y = *x - fl * L;
-  int32_t k = (int32_t)fl;
-  if (y < 0.0) { y += L; k -= 1; }
+  double y = *x;
+  int32_t k = 0;
+  while (y >= L) { y -= L; k += 1; }
+  while (y < 0.0) { y += L; k -= 1; }
   if (y >= L) { y = 0.0; k += 1; }
   *x = y;
   *img += k;

@@ -460,3 +460,18 @@ def test_langevin_uses_counter_noise_and_drives_to_kT():
         s.step(1, thermostat=(1.0, 1.0))
         ke.append(s.energy()["kinetic"])
     assert 0.5 * 1.5 * 16 < np.mean(ke[150:]) < 1.6 * 1.5 * 16
+
+
+def test_fold_keeps_unfolded_position():
+    # folding shifts by whole box lengths: x + img L is unchanged (exactly,
+    # when the shift is exact), the result lies in [0, L), and a value that
+    # rounds up to L becomes 0 in the next image
+    s = make((4, 4, 4), 1.0)
+    L = 4.0
+    xs = np.array([[4.0, -1e-17, 7.9999], [-4.0, 3.0, 12.0 - 1e-15], [15.9, -15.9, 0.0]])
+    s.set_particles(xs, [1, -1, 0])
+    x, img = s.particles("x"), s.particles("img")
+    assert np.all((x >= 0) & (x < L))
+    assert np.allclose(x + img * L, xs, rtol=0, atol=1e-14)
+    assert x[0, 1] == 0.0 and img[0, 1] == 0      # -1e-17 + 4 rounds to 4 -> 0, same image
+    assert x[0, 0] == 0.0 and img[0, 0] == 1
