@@ -3,10 +3,14 @@
 // in a CUDA graph, and the state / diagnostic calls.  All arithmetic of the
 // method runs in the kernels of memd_field.cu, memd_setup.cu and
 // memd_particles.cu; this file only orders them.
+#include <algorithm>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <map>
+#include <mutex>
 #include <string>
+#include <tuple>
 #include <vector>
 
 #include "memd.h"
@@ -56,7 +60,8 @@ struct memd_ctx {
   double field_ms = 0;
   long long field_launches = 0;
   int relax_iters_last = 0;
-  int zchunk = 0;
+  FusedCfg fcfg{8, 1};
+  bool sig_ready = false;
   void* D() const { return Dbuf[cur]; }
   void* B() const { return Bbuf[cur]; }
 };
@@ -349,6 +354,57 @@ static memd_status relax(memd_ctx* c, double* D64, double tol, int maxit) {
   return MEMD_OK;
 }
 
+// ------------------------------------------------------------------ autotuner
+// Picks the tile height and z-chunk of the fused field kernel for this mesh
+// by timing every candidate shape on the context's own buffers (median of 3
+// launches after one warm-up).  Results are cached per mesh shape and
+// precision for the life of the process.
+static memd_status autotune_fused(memd_ctx* c) {
+  static std::mutex mu;
+  static std::map<std::tuple<int, int, int, int>, FusedCfg> cache;
+  const auto key = std::make_tuple(c->mesh.n[0], c->mesh.n[1], c->mesh.n[2], c->prec);
+  {
+    std::lock_guard<std::mutex> g(mu);
+    auto it = cache.find(key);
+    if (it != cache.end()) {
+      c->fcfg = it->second;
+      return MEMD_OK;
+    }
+  }
+  FusedCfg cand[32];
+  const int nc = fused_candidates(c->mesh, c->prec, cand, 32);
+  cudaEvent_t e0, e1;
+  CK(cudaEventCreate(&e0));
+  CK(cudaEventCreate(&e1));
+  float best = 1e30f;
+  FusedCfg pick = fused_default(c->mesh);
+  for (int i = 0; i < nc; ++i) {
+    float t[3];
+    launch_fused_curl(c->mesh, c->prec, c->Dbuf[0], c->Bbuf[0], c->ie, c->Dbuf[1], c->Bbuf[1],
+                      0.0, 0.0, cand[i], c->stream);
+    for (int r = 0; r < 3; ++r) {
+      CK(cudaEventRecord(e0, c->stream));
+      launch_fused_curl(c->mesh, c->prec, c->Dbuf[0], c->Bbuf[0], c->ie, c->Dbuf[1],
+                        c->Bbuf[1], 0.0, 0.0, cand[i], c->stream);
+      CK(cudaEventRecord(e1, c->stream));
+      CK(cudaEventSynchronize(e1));
+      CK(cudaEventElapsedTime(&t[r], e0, e1));
+    }
+    CKL();
+    const float med = std::max(std::min(t[0], t[1]), std::min(std::max(t[0], t[1]), t[2]));
+    if (med < best) {
+      best = med;
+      pick = cand[i];
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  c->fcfg = pick;
+  std::lock_guard<std::mutex> g(mu);
+  cache[key] = pick;
+  return MEMD_OK;
+}
+
 // ----------------------------------------------------------------- public API
 extern "C" {
 
@@ -436,6 +492,11 @@ memd_status memd_create(const int32_t mesh[3], const double box[3], const memd_e
   c->mesh.V = V;
   c->mesh.a = a;
   for (int d = 0; d < 3; ++d) c->mesh.L[d] = box[d];
+  {
+    int ex = 0;
+    c->mesh.a_pow2 = std::frexp(a, &ex) == 0.5 ? 1 : 0;
+    c->mesh.inv_a = 1.0 / a;
+  }
   c->Vbox = box[0] * box[1] * box[2];
   c->c = c_light;
   c->dt = dt;
@@ -560,7 +621,8 @@ memd_status memd_create(const int32_t mesh[3], const double box[3], const memd_e
     s = fail(c, MEMD_ERR_CUDA, "events");
     goto done;
   }
-  c->zchunk = fused_zchunk(c->mesh);
+  s = autotune_fused(c);
+  if (s != MEMD_OK) goto done;
 done:
   dfree(c, vals);
   dfree(c, D64);
@@ -581,7 +643,10 @@ static void free_particles(memd_ctx* c) {
   dfree(c, c->P.img);
   dfree(c, c->P.q);
   dfree(c, c->P.mv);
+  dfree(c, c->P.h);
+  dfree(c, c->P.sig);
   c->P = Particles{};
+  c->sig_ready = false;
 }
 
 memd_status memd_init_field(memd_ctx* c, int64_t n, const double* pos, const int32_t* q,
@@ -616,7 +681,10 @@ memd_status memd_init_field(memd_ctx* c, int64_t n, const double* pos, const int
   c->P.img = (int*)dalloc(c, 3 * nn * sizeof(int));
   c->P.q = (int*)dalloc(c, nn * sizeof(int));
   c->P.mv = (int*)dalloc(c, 6 * nn * sizeof(int));
-  if (!c->P.x || !c->P.v || !c->P.m || !c->P.F || !c->P.Ft || !c->P.img || !c->P.q || !c->P.mv)
+  c->P.h = (double*)dalloc(c, nn * sizeof(double));
+  c->P.sig = (double*)dalloc(c, nn * sizeof(double));
+  if (!c->P.x || !c->P.v || !c->P.m || !c->P.F || !c->P.Ft || !c->P.img || !c->P.q || !c->P.mv ||
+      !c->P.h || !c->P.sig)
     return fail(c, MEMD_ERR_OOM, "particle allocation");
   double* pin = (double*)dalloc(c, 3 * nn * sizeof(double));
   long long* Q = (long long*)dalloc(c, sizeof(long long) * m.V);
@@ -665,6 +733,7 @@ memd_status memd_init_field(memd_ctx* c, int64_t n, const double* pos, const int
       CK(cudaMemsetAsync(c->Tb, 0, 3 * m.V * sizeof(long long), st));
       CK(cudaMemsetAsync(&c->ds->ticket, 0, sizeof(unsigned int), st));
       const StepParams sp = step_params(c, 0, 0.0, 0.0);
+      launch_particle_constants(sp, c->P, st);
       launch_gather(m, c->prec, sp, c->P, c->D(), c->ie, c->ie64, c->ds, 0, 1, st);
       CKL();
       s = check_err(c);
@@ -691,7 +760,7 @@ static memd_status record_step(memd_ctx* c, const StepParams& sp, int par, bool 
   CK(cudaEventRecord(c->join, c->side));
   if (timed) CK(cudaEventRecordWithFlags(c->ev0, st, cudaEventRecordExternal));
   launch_fused_curl(m, c->prec, c->Dbuf[par], c->Bbuf[par], c->ie, c->Dbuf[par ^ 1],
-                    c->Bbuf[par ^ 1], sp.coefB, sp.coefD, c->zchunk, st);
+                    c->Bbuf[par ^ 1], sp.coefB, sp.coefD, c->fcfg, st);
   if (timed) CK(cudaEventRecordWithFlags(c->ev1, st, cudaEventRecordExternal));
   CK(cudaStreamWaitEvent(st, c->join, 0));
   launch_apply(m, c->prec, c->P, c->Tb, c->Lg, c->Dbuf[par ^ 1], sp.scale, st);
@@ -716,7 +785,15 @@ memd_status memd_step(memd_ctx* c, int64_t nsteps, const memd_thermostat* th) {
   const double gamma = th ? th->gamma : 0.0, kT = th ? th->kT : 0.0;
   const StepParams sp = step_params(c, thermo, gamma, kT);
   const bool timed = c->time_kernels != 0;
-  if (c->graph_thermo != thermo || c->graph_gamma != gamma || c->graph_kT != kT) drop_graphs(c);
+  if (c->graph_thermo != thermo || c->graph_gamma != gamma || c->graph_kT != kT || !c->sig_ready) {
+    drop_graphs(c);
+    // per-particle Langevin amplitude for this thermostat (same expression as per step)
+    launch_particle_constants(sp, c->P, c->stream);
+    c->sig_ready = true;
+    c->graph_thermo = thermo;
+    c->graph_gamma = gamma;
+    c->graph_kT = kT;
+  }
   for (int64_t s = 0; s < nsteps; ++s) {
     const int par = c->cur;
     harvest_timing(c);

@@ -139,100 +139,183 @@ __global__ void __launch_bounds__(kBX* kBY)
 // ------------------------------------------------------------------
 // Fused leapfrog field update of one step (Eqs. 20 and 21 without the
 // current): B' = B - cB circ(D ie) on every plaquette, then
-// D' = D + cD (transpose circulation of B') on every link.  Each CTA owns a
-// TX x TY column tile and marches through a chunk of z planes, holding E of
-// planes k, k+1 and B' of planes k-1, k in shared memory with a one-site halo
-// on the low x/y sides (B' there is recomputed instead of exchanged).  D and
-// B are double-buffered (read *_in, write *_out) because neighbouring CTAs
-// read the halo of the input.  DRAM traffic per site: D, 1/eps, B read,
-// D', B' written.
+// D' = D + cD (transpose circulation of B') on every link.
+//
+// Each CTA owns a TX x TY column tile and marches up a chunk of z planes.
+// Shared memory holds E = D ie of planes k, k+1, k+2 (a ring of three) and
+// B' of planes k-1, k, each with a one-site halo on the low x / y sides
+// (B' there is recomputed rather than exchanged between CTAs).  While plane
+// k is computed, the loads for plane k+1 (B, D) and k+2 (D, 1/eps) are
+// already in flight in registers, so DRAM latency overlaps the arithmetic.
+// D and B are double-buffered (read *_in, write *_out) because neighbouring
+// CTAs read the halo of the input.  DRAM traffic per site: D, 1/eps, B read
+// once, D', B' written once (60 B in FP32, 120 B in FP64).
 template <typename T, int TX, int TY>
 __global__ void __launch_bounds__(TX* TY)
     k_fused_curl(Mesh m, const T* __restrict__ Din, const T* __restrict__ Bin,
                  const T* __restrict__ ie, T* __restrict__ Dout, T* __restrict__ Bout, T cB,
                  T cD, int zchunk) {
   constexpr int EX = TX + 2, EY = TY + 2, BX = TX + 1, BY = TY + 1;
-  __shared__ T sE[2][3][EY][EX];
+  constexpr int NT = TX * TY;
+  constexpr int NE = (EX * EY + NT - 1) / NT;  // E-region elements per thread
+  constexpr int NB = (BX * BY + NT - 1) / NT;  // B-region elements per thread
+  __shared__ T sE[3][3][EY][EX];
   __shared__ T sB[2][3][BY][BX];
   const int nx = m.n[0], ny = m.n[1], nz = m.n[2];
   const int64_t V = m.V;
+  const int64_t P = (int64_t)nx * ny;
   const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY;
   const int z0 = blockIdx.z * zchunk;
   const int z1 = min(z0 + zchunk, nz);
   const int tid = threadIdx.y * TX + threadIdx.x;
-  constexpr int NT = TX * TY;
 
-  auto load_E = [&](int k, int slot) {
-    const int64_t pk = (int64_t)k * nx * ny;
-    for (int e = tid; e < EX * EY; e += NT) {
-      const int ey = e / EX, ex = e - ey * EX;
-      int x = x0 - 1 + ex, y = y0 - 1 + ey;
-      x = (x < 0) ? x + nx : (x >= nx ? x - nx : x);
-      y = (y < 0) ? y + ny : (y >= ny ? y - ny : y);
-      if (x >= nx) x = nx - 1;  // only for tiles wider than the mesh (unused values)
-      if (y >= ny) y = ny - 1;
-      const int64_t v = pk + (int64_t)y * nx + x;
-      sE[slot][0][ey][ex] = Din[v] * ie[v];
-      sE[slot][1][ey][ex] = Din[V + v] * ie[V + v];
-      sE[slot][2][ey][ex] = Din[2 * V + v] * ie[2 * V + v];
+  // in-plane offsets of this thread's E- and B-region elements (periodic)
+  int eo[NE], bo[NB];
+  bool bin_[NB];
+#pragma unroll
+  for (int j = 0; j < NE; ++j) {
+    int e = tid + j * NT;
+    if (e >= EX * EY) e = EX * EY - 1;
+    const int ey = e / EX, ex = e - ey * EX;
+    int x = x0 - 1 + ex, y = y0 - 1 + ey;
+    x = (x < 0) ? x + nx : (x >= nx ? x - nx : x);
+    y = (y < 0) ? y + ny : (y >= ny ? y - ny : y);
+    if (x >= nx) x = nx - 1;  // only when the tile is wider than the mesh (unused)
+    if (y >= ny) y = ny - 1;
+    eo[j] = y * nx + x;
+  }
+#pragma unroll
+  for (int j = 0; j < NB; ++j) {
+    int e = tid + j * NT;
+    const bool real = e < BX * BY;
+    if (!real) e = BX * BY - 1;
+    const int by = e / BX, bx = e - by * BX;
+    int x = x0 - 1 + bx, y = y0 - 1 + by;
+    bin_[j] = real && bx >= 1 && by >= 1 && x < nx && y < ny;
+    x = (x < 0) ? x + nx : (x >= nx ? x - nx : x);
+    y = (y < 0) ? y + ny : (y >= ny ? y - ny : y);
+    if (x >= nx) x = nx - 1;
+    if (y >= ny) y = ny - 1;
+    bo[j] = y * nx + x;
+  }
+  const int tx = threadIdx.x, ty = threadIdx.y;
+  const bool mine = (x0 + tx < nx) && (y0 + ty < ny);
+  const int io = min(y0 + ty, ny - 1) * nx + min(x0 + tx, nx - 1);
+
+  auto plane = [&](int k) -> int64_t { return (int64_t)k * P; };
+  auto wrapz = [&](int k) -> int { return k >= nz ? k - nz : (k < 0 ? k + nz : k); };
+
+  // registers: D and 1/eps for an E plane, B for a B plane, D of the own site
+  T rD[NE][3], rI[NE][3], rB[NB][3], rDs[3];
+  auto fetch_E = [&](int k) {
+    const int64_t pk = plane(k);
+#pragma unroll
+    for (int j = 0; j < NE; ++j)
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        rD[j][c] = Din[c * V + pk + eo[j]];
+        rI[j][c] = ie[c * V + pk + eo[j]];
+      }
+  };
+  auto store_E = [&](int slot) {
+#pragma unroll
+    for (int j = 0; j < NE; ++j) {
+      const int e = tid + j * NT;
+      if (e < EX * EY) {
+        const int ey = e / EX, ex = e - ey * EX;
+#pragma unroll
+        for (int c = 0; c < 3; ++c) sE[slot][c][ey][ex] = rD[j][c] * rI[j][c];
+      }
     }
   };
-  // B' of plane k on the tile plus its low halo; interior values also to Bout
-  auto compute_B = [&](int k, int ec, int en, int slot, bool store) {
-    const int64_t pk = (int64_t)k * nx * ny;
-    for (int e = tid; e < BX * BY; e += NT) {
-      const int by = e / BX, bx = e - by * BX;
-      int x = x0 - 1 + bx, y = y0 - 1 + by;
-      const bool inside = bx >= 1 && by >= 1 && x < nx && y < ny;
-      x = (x < 0) ? x + nx : (x >= nx ? x - nx : x);
-      y = (y < 0) ? y + ny : (y >= ny ? y - ny : y);
-      if (x >= nx) x = nx - 1;
-      if (y >= ny) y = ny - 1;
-      const int64_t v = pk + (int64_t)y * nx + x;
-      const T Ex = sE[ec][0][by][bx], Ey = sE[ec][1][by][bx], Ez = sE[ec][2][by][bx];
-      const T Ey_x = sE[ec][1][by][bx + 1], Ez_x = sE[ec][2][by][bx + 1];
-      const T Ex_y = sE[ec][0][by + 1][bx], Ez_y = sE[ec][2][by + 1][bx];
-      const T Ex_z = sE[en][0][by][bx], Ey_z = sE[en][1][by][bx];
-      const T bxv = Bin[v] - cB * (((Ey + Ez_y) - Ey_z) - Ez);
-      const T byv = Bin[V + v] - cB * (((Ez + Ex_z) - Ez_x) - Ex);
-      const T bzv = Bin[2 * V + v] - cB * (((Ex + Ey_x) - Ex_y) - Ey);
-      sB[slot][0][by][bx] = bxv;
-      sB[slot][1][by][bx] = byv;
-      sB[slot][2][by][bx] = bzv;
-      if (store && inside) {
-        Bout[v] = bxv;
-        Bout[V + v] = byv;
-        Bout[2 * V + v] = bzv;
+  auto fetch_B = [&](int k, T (&dst)[NB][3]) {
+    const int64_t pk = plane(k);
+#pragma unroll
+    for (int j = 0; j < NB; ++j)
+#pragma unroll
+      for (int c = 0; c < 3; ++c) dst[j][c] = Bin[c * V + pk + bo[j]];
+  };
+  auto fetch_Ds = [&](int k, T (&dst)[3]) {
+    const int64_t pk = plane(k);
+#pragma unroll
+    for (int c = 0; c < 3; ++c) dst[c] = Din[c * V + pk + io];
+  };
+  // B' of plane k on the tile and its low halo, from E in slots ec (k) and
+  // en (k+1) and B of plane k in registers; interior values also to Bout
+  auto compute_B = [&](int k, int ec, int en, int slot, const T (&bb)[NB][3], bool store) {
+    const int64_t pk = plane(k);
+#pragma unroll
+    for (int j = 0; j < NB; ++j) {
+      const int e = tid + j * NT;
+      if (e < BX * BY) {
+        const int by = e / BX, bx = e - by * BX;
+        const T Ex = sE[ec][0][by][bx], Ey = sE[ec][1][by][bx], Ez = sE[ec][2][by][bx];
+        const T Ey_x = sE[ec][1][by][bx + 1], Ez_x = sE[ec][2][by][bx + 1];
+        const T Ex_y = sE[ec][0][by + 1][bx], Ez_y = sE[ec][2][by + 1][bx];
+        const T Ex_z = sE[en][0][by][bx], Ey_z = sE[en][1][by][bx];
+        const T bxv = bb[j][0] - cB * (((Ey + Ez_y) - Ey_z) - Ez);
+        const T byv = bb[j][1] - cB * (((Ez + Ex_z) - Ez_x) - Ex);
+        const T bzv = bb[j][2] - cB * (((Ex + Ey_x) - Ex_y) - Ey);
+        sB[slot][0][by][bx] = bxv;
+        sB[slot][1][by][bx] = byv;
+        sB[slot][2][by][bx] = bzv;
+        if (store && bin_[j]) {
+          Bout[pk + bo[j]] = bxv;
+          Bout[V + pk + bo[j]] = byv;
+          Bout[2 * V + pk + bo[j]] = bzv;
+        }
       }
     }
   };
 
-  int ec = 0, en = 1, bp = 0, bc = 1;
-  const int zm = (z0 == 0) ? nz - 1 : z0 - 1;
-  load_E(zm, ec);
-  load_E(z0, en);
-  __syncthreads();
-  compute_B(zm, ec, en, bp, false);
-  ec ^= 1;
-  en ^= 1;
+  // prologue: E of z0-1, z0, z0+1 and B' of z0-1 (recomputed halo plane)
+  {
+    T bb[NB][3];
+    fetch_E(wrapz(z0 - 1));
+    fetch_B(wrapz(z0 - 1), bb);
+    store_E(0);
+    fetch_E(z0);
+    store_E(1);
+    fetch_E(wrapz(z0 + 1));
+    store_E(2);
+    __syncthreads();
+    compute_B(wrapz(z0 - 1), 0, 1, 0, bb, false);
+  }
+  T cBr[NB][3], cDs[3];
+  fetch_B(z0, cBr);
+  fetch_Ds(z0, cDs);
+  int ec = 1, en = 2, ef = 0, bp = 0, bc = 1;
   for (int k = z0; k < z1; ++k) {
-    __syncthreads();
-    load_E(k + 1 == nz ? 0 : k + 1, en);
-    __syncthreads();
-    compute_B(k, ec, en, bc, true);
-    __syncthreads();
-    const int tx = threadIdx.x, ty = threadIdx.y;
-    const int x = x0 + tx, y = y0 + ty;
-    if (x < nx && y < ny) {
-      const int bx = tx + 1, by = ty + 1;
-      const int64_t v = (int64_t)k * nx * ny + (int64_t)y * nx + x;
-      const T Bx = sB[bc][0][by][bx], By = sB[bc][1][by][bx], Bz = sB[bc][2][by][bx];
-      Dout[v] = Din[v] + cD * (((Bz - sB[bc][2][by - 1][bx]) - By) + sB[bp][1][by][bx]);
-      Dout[V + v] = Din[V + v] + cD * (((Bx - sB[bp][0][by][bx]) - Bz) + sB[bc][2][by][bx - 1]);
-      Dout[2 * V + v] = Din[2 * V + v] + cD * (((By - sB[bc][1][by][bx - 1]) - Bx) + sB[bc][0][by - 1][bx]);
+    const bool more = k + 1 < z1;
+    if (more) {  // in flight while plane k is computed
+      fetch_E(wrapz(k + 2));
+      fetch_B(k + 1, rB);
+      fetch_Ds(k + 1, rDs);
     }
-    ec ^= 1;
-    en ^= 1;
+    __syncthreads();  // E(k+1) stored, sB[bc] free
+    compute_B(k, ec, en, bc, cBr, true);
+    __syncthreads();
+    if (mine) {
+      const int bx = tx + 1, by = ty + 1;
+      const int64_t v = plane(k) + io;
+      const T Bx = sB[bc][0][by][bx], By = sB[bc][1][by][bx], Bz = sB[bc][2][by][bx];
+      Dout[v] = cDs[0] + cD * (((Bz - sB[bc][2][by - 1][bx]) - By) + sB[bp][1][by][bx]);
+      Dout[V + v] = cDs[1] + cD * (((Bx - sB[bp][0][by][bx]) - Bz) + sB[bc][2][by][bx - 1]);
+      Dout[2 * V + v] = cDs[2] + cD * (((By - sB[bc][1][by][bx - 1]) - Bx) + sB[bc][0][by - 1][bx]);
+    }
+    if (more) {
+      store_E(ef);
+#pragma unroll
+      for (int j = 0; j < NB; ++j)
+#pragma unroll
+        for (int c = 0; c < 3; ++c) cBr[j][c] = rB[j][c];
+#pragma unroll
+      for (int c = 0; c < 3; ++c) cDs[c] = rDs[c];
+    }
+    const int t = ec;
+    ec = en;
+    en = ef;
+    ef = t;
     bp ^= 1;
     bc ^= 1;
   }
@@ -359,33 +442,61 @@ void launch_curl_D(const Mesh& m, int prec, void* D, const void* B, double coef,
     k_curl_D<double><<<field_grid(m), blk, 0, st>>>(m, (double*)D, (const double*)B, coef);
 }
 
-void launch_fused_curl(const Mesh& m, int prec, const void* Din, const void* Bin, const void* ie,
-                       void* Dout, void* Bout, double cB, double cD, int zchunk,
-                       cudaStream_t st) {
-  constexpr int TX = 32, TY = 8;
-  if (zchunk < 1) zchunk = fused_zchunk(m);
+namespace {
+template <typename T, int TY>
+void fused_launch_t(const Mesh& m, const void* Din, const void* Bin, const void* ie, void* Dout,
+                    void* Bout, double cB, double cD, int zchunk, cudaStream_t st) {
+  constexpr int TX = 32;
   const dim3 grid((m.n[0] + TX - 1) / TX, (m.n[1] + TY - 1) / TY, (m.n[2] + zchunk - 1) / zchunk);
-  const dim3 blk(TX, TY, 1);
-  if (prec == 1)
-    k_fused_curl<float, TX, TY><<<grid, blk, 0, st>>>(m, (const float*)Din, (const float*)Bin,
-                                                      (const float*)ie, (float*)Dout, (float*)Bout,
-                                                      (float)cB, (float)cD, zchunk);
-  else
-    k_fused_curl<double, TX, TY><<<grid, blk, 0, st>>>(m, (const double*)Din, (const double*)Bin,
-                                                       (const double*)ie, (double*)Dout,
-                                                       (double*)Bout, cB, cD, zchunk);
+  k_fused_curl<T, TX, TY><<<grid, dim3(TX, TY, 1), 0, st>>>(
+      m, (const T*)Din, (const T*)Bin, (const T*)ie, (T*)Dout, (T*)Bout, (T)cB, (T)cD, zchunk);
+}
+}  // namespace
+
+void launch_fused_curl(const Mesh& m, int prec, const void* Din, const void* Bin, const void* ie,
+                       void* Dout, void* Bout, double cB, double cD, FusedCfg cfg,
+                       cudaStream_t st) {
+  if (cfg.zchunk < 1) cfg = fused_default(m);
+  if (cfg.zchunk > m.n[2]) cfg.zchunk = m.n[2];
+  if (prec == 1) {
+    switch (cfg.ty) {
+      case 4: fused_launch_t<float, 4>(m, Din, Bin, ie, Dout, Bout, cB, cD, cfg.zchunk, st); break;
+      case 16: fused_launch_t<float, 16>(m, Din, Bin, ie, Dout, Bout, cB, cD, cfg.zchunk, st); break;
+      default: fused_launch_t<float, 8>(m, Din, Bin, ie, Dout, Bout, cB, cD, cfg.zchunk, st);
+    }
+  } else {
+    // FP64 tiles stop at 8 rows: 16 would exceed the 48 KB of static shared memory
+    if (cfg.ty == 4)
+      fused_launch_t<double, 4>(m, Din, Bin, ie, Dout, Bout, cB, cD, cfg.zchunk, st);
+    else
+      fused_launch_t<double, 8>(m, Din, Bin, ie, Dout, Bout, cB, cD, cfg.zchunk, st);
+  }
 }
 
-int fused_zchunk(const Mesh& m) {
+FusedCfg fused_default(const Mesh& m) {
   // enough CTAs to fill the GPU a few times over, but chunks long enough
   // that the recomputed prologue plane stays a small overhead
+  FusedCfg c{8, 1};
   const int64_t tiles = (int64_t)((m.n[0] + 31) / 32) * ((m.n[1] + 7) / 8);
   const int64_t target = 4 * 152;
-  int64_t nchunks = (target + tiles - 1) / tiles;
+  const int64_t nchunks = (target + tiles - 1) / tiles;
   int64_t zc = (m.n[2] + nchunks - 1) / nchunks;
   if (zc < 4) zc = 4;
   if (zc > m.n[2]) zc = m.n[2];
-  return (int)zc;
+  c.zchunk = (int)zc;
+  return c;
+}
+
+int fused_candidates(const Mesh& m, int prec, FusedCfg* out, int cap) {
+  static const int tys[3] = {4, 8, 16};
+  static const int zcs[8] = {1, 2, 4, 8, 16, 32, 64, 128};
+  int n = 0;
+  for (int a = 0; a < (prec == 1 ? 3 : 2); ++a)
+    for (int b = 0; b < 8; ++b) {
+      if (zcs[b] > m.n[2] && b > 0 && zcs[b - 1] >= m.n[2]) continue;
+      if (n < cap) out[n++] = FusedCfg{tys[a], zcs[b] < m.n[2] ? zcs[b] : m.n[2]};
+    }
+  return n;
 }
 
 void launch_circ64(const Mesh& m, double* w, const double* u, const double* ie, double sign,

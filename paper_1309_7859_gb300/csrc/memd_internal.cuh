@@ -20,6 +20,8 @@ struct Mesh {
   int64_t V;
   double a;
   double L[3];
+  double inv_a;  // 1 / a; used instead of the division when a is a power of two
+  int a_pow2;    // (x * inv_a == x / a exactly then)
 };
 
 // error bits raised by kernels into a device word
@@ -56,11 +58,18 @@ void launch_curl_B(const Mesh& m, int prec, void* B, const void* D, const void* 
                    double coef, cudaStream_t st);
 void launch_curl_D(const Mesh& m, int prec, void* D, const void* B, double coef,
                    cudaStream_t st);
-// fused B then D update with double-buffered fields (zchunk <= 0: automatic)
+// fused B then D update with double-buffered fields: tile height ty (4, 8
+// or 16 rows of 32) and z planes per CTA; zchunk <= 0 takes the default
+struct FusedCfg {
+  int ty;
+  int zchunk;
+};
 void launch_fused_curl(const Mesh& m, int prec, const void* Din, const void* Bin, const void* ie,
-                       void* Dout, void* Bout, double cB, double cD, int zchunk,
+                       void* Dout, void* Bout, double cB, double cD, FusedCfg cfg,
                        cudaStream_t st);
-int fused_zchunk(const Mesh& m);
+FusedCfg fused_default(const Mesh& m);
+// candidate shapes for the autotuner; returns how many were written
+int fused_candidates(const Mesh& m, int prec, FusedCfg* out, int cap);
 // FP64 helpers of the relaxation: w = sign * circulation(ie * u) per plaquette
 void launch_circ64(const Mesh& m, double* w, const double* u, const double* ie,
                    double sign, cudaStream_t st);
@@ -115,7 +124,9 @@ struct Particles {
   double* Ft;
   int* img;
   int* q;
-  int* mv;  // 6 ints per particle: old cell (3), new cell (3) of the last move
+  int* mv;      // 6 ints per particle: old cell (3), new cell (3) of the last move
+  double* h;    // dt / (2 m): half-kick factor
+  double* sig;  // sqrt(2 gamma m kT / dt): Langevin noise amplitude
 };
 struct StepParams {
   double dt;
@@ -148,6 +159,8 @@ void launch_gather(const Mesh& m, int prec, const StepParams& sp, Particles p, c
                    const void* ie, const double* ie64, DevState* ds, int kick, int finish,
                    cudaStream_t st);
 void launch_step_end(DevState* ds, int advance, cudaStream_t st);
+// per-particle constants: h = (dt/2)/m always; sig when thermo is set
+void launch_particle_constants(const StepParams& sp, Particles p, cudaStream_t st);
 // energy pieces into partial sums (memd_particles.cu)
 void launch_particle_energy(const Mesh& m, const StepParams& sp, Particles p,
                             const double* ie64, double* part_ke, double* part_self,

@@ -7,6 +7,12 @@
 //   force gather F = qE with the self-energy (Sec. III) and dipole (Sec. V)
 //   corrections, the Langevin force and the second half kick
 //
+// The step kernels give each particle a quad of 4 lanes: the three axes of
+// the move, the four corners of the cell, or the three force components run
+// side by side, so the serial FP64 chain and the dependent atomics of one
+// particle are split four ways (GB300 has little FP64 throughput per SM and
+// these kernels are latency bound).
+//
 // Built with -fmad=false: positions decide integer cell indices, so every
 // position update is two IEEE roundings (a product, then a sum), never a
 // fused multiply-add.
@@ -17,6 +23,7 @@ namespace memd {
 namespace {
 
 constexpr int kThreads = 128;
+constexpr int kQuadThreads = 128;  // 32 particles per CTA in the quad kernels
 constexpr int kRedThreads = 256;
 constexpr int kRedBlocks = 2 * 152;
 
@@ -26,19 +33,22 @@ inline unsigned blocks_for(int64_t n, int t = kThreads) {
 }
 
 // ------------------------------------------------------------ fixed point
-// Fold x into [0, L) counting images; x == L after rounding maps to 0 in the
-// next image.
+// Sec. V periodic stitching: shift by whole box lengths into [0, L); a sum
+// that rounds up to L starts the next image.  Callers bound |x| by a few L.
 __device__ inline void fold(double L, double& x, int& img) {
-  const double fl = floor(__ddiv_rn(x, L));
-  double y = __dsub_rn(x, __dmul_rn(fl, L));
-  int k = (int)fl;
-  if (y < 0.0) {
+  double y = x;
+  int k = 0;
+  while (y >= L) {
+    y = __dsub_rn(y, L);
+    ++k;
+  }
+  while (y < 0.0) {
     y = __dadd_rn(y, L);
-    k -= 1;
+    --k;
   }
   if (y >= L) {
     y = 0.0;
-    k += 1;
+    ++k;
   }
   x = y;
   img += k;
@@ -46,7 +56,7 @@ __device__ inline void fold(double L, double& x, int& img) {
 
 // cell c = floor(x / a) and sub-cell step f = floor((x/a - c) S)
 __device__ inline void quantize(const Mesh& m, int d, double x, int& c, int& f) {
-  const double u = __ddiv_rn(x, m.a);
+  const double u = m.a_pow2 ? __dmul_rn(x, m.inv_a) : __ddiv_rn(x, m.a);
   const double cu = floor(u);
   if (cu >= (double)m.n[d]) {
     c = m.n[d] - 1;
@@ -74,6 +84,14 @@ __device__ inline void warp_atomic_add(unsigned long long* addr, long long val) 
   if ((threadIdx.x & 31) == 0 && val != 0) atomicAdd(addr, (unsigned long long)val);
 }
 
+// sum over the 8 quads of a warp of a value held by quad lane d (d = 0..2):
+// lane d of the warp ends with the warp total for component d
+__device__ inline void quad_dipole_add(unsigned long long* Pacc, long long val) {
+  for (int o = 16; o >= 4; o >>= 1) val += __shfl_down_sync(0xffffffffu, val, o);
+  const int lane = threadIdx.x & 31;
+  if (lane < 3 && val != 0) atomicAdd(&Pacc[lane], (unsigned long long)val);
+}
+
 // ------------------------------------------------------------ Philox4x32-10
 // Salmon, Moraes, Dror, Shaw (SC'11): ten rounds of two 32x32 -> 64-bit
 // products with a Weyl-sequence key schedule.
@@ -99,14 +117,15 @@ __device__ inline double unit_noise(unsigned r) {
 }
 
 // ---------------------------------------------------------- charge transfer
-// Move along axis d from (c0, f0) to (c1, f1) with image change dimg: the
-// 4 d-links of the cell change flux by -q (distance) (perpendicular weight);
-// a crossed cell face splits the move over the old and the new link.
-__device__ inline void deposit_axis(const Mesh& m, int d, int q, int c0, int f0, int c1, int f1,
-                                    int dimg, const int cc[3], const int cf[3],
-                                    unsigned long long* Tb) {
+// Move along axis d from (c0, f0) to (c1, f1), dc = c1 - c0 + dimg N in
+// {-1, 0, 1}: the 4 d-links of the cell change flux by -q (distance moved)
+// (perpendicular weight); a crossed cell face splits the move over the old
+// and the new link.  Perpendicular weights are those of the moves made so
+// far (axes before d at their new cells, axes after d at their old ones).
+__device__ inline void deposit_axis(const Mesh& m, int d, int q, int c0, int f0, int f1, int dc,
+                                    const int cc[3], const int cf[3],
+                                    unsigned long long* __restrict__ Tb) {
   const int e1 = (d + 1) % 3, e2 = (d + 2) % 3;
-  const int dc = c1 + dimg * m.n[d] - c0;
 #pragma unroll
   for (int a2 = 0; a2 < 2; ++a2)
 #pragma unroll
@@ -139,58 +158,62 @@ __device__ inline void deposit_axis(const Mesh& m, int d, int q, int c0, int f0,
     }
 }
 
-// Move particle p to (xn, kn): axes in the order x, y, z, each with the
-// perpendicular weights of the moves made so far.  Returns false (and moves
-// nothing) when an axis would cross more than one cell.
-__device__ inline bool move_particle(const Mesh& m, Particles P, int64_t p, const double xn[3],
-                                     const int kn[3], unsigned long long* Tb, int c1out[3],
-                                     int f1out[3]) {
-  int c0[3], f0[3], c1[3], f1[3], ko[3];
-  for (int d = 0; d < 3; ++d) {
-    quantize(m, d, P.x[3 * p + d], c0[d], f0[d]);
-    quantize(m, d, xn[d], c1[d], f1[d]);
-    ko[d] = P.img[3 * p + d];
-    const int dc = c1[d] + (kn[d] - ko[d]) * m.n[d] - c0[d];
-    if (dc < -1 || dc > 1) {
+// Quad lane d (< 3) holds axis d of particle p: its old position x, image
+// ko, and the proposed new position xn / image kn (already folded).  The
+// quad exchanges the quantised coordinates, deposits one axis per lane and
+// commits the move, or leaves the particle where it was (ok == false) when
+// some axis would cross more than one cell.  Every lane of the warp must
+// call this; inactive lanes pass active = false.
+__device__ inline void quad_move(const Mesh& m, Particles P, int64_t p, int d, bool active,
+                                 double x, int ko, double xn, int kn, bool ok_in,
+                                 unsigned long long* __restrict__ Tb, DevState* ds) {
+  const unsigned full = 0xffffffffu;
+  const int lane = threadIdx.x & 31, base = lane & ~3;
+  int c0 = 0, f0 = 0, c1 = 0, f1 = 0, dc = 0;
+  bool ok = ok_in;
+  if (active && d < 3) {
+    quantize(m, d, x, c0, f0);
+    quantize(m, d, xn, c1, f1);
+    dc = c1 + (kn - ko) * m.n[d] - c0;
+    if (dc < -1 || dc > 1) ok = false;
+  } else {
+    ok = true;
+  }
+  // all three axes must be valid for the particle to move
+  const bool all_ok = __all_sync(0xfu << base, ok) != 0;
+  int C0[3], F0[3], C1[3], F1[3];
+#pragma unroll
+  for (int e = 0; e < 3; ++e) {
+    C0[e] = __shfl_sync(full, c0, base + e);
+    F0[e] = __shfl_sync(full, f0, base + e);
+    C1[e] = __shfl_sync(full, c1, base + e);
+    F1[e] = __shfl_sync(full, f1, base + e);
+  }
+  long long U = 0;
+  if (active && d < 3) {
+    int* mv = P.mv + 6 * p;
+    if (all_ok) {
+      int cc[3], cf[3];
+#pragma unroll
       for (int e = 0; e < 3; ++e) {
-        c1out[e] = c0[e];
-        f1out[e] = f0[e];
+        cc[e] = (e < d) ? C1[e] : C0[e];
+        cf[e] = (e < d) ? F1[e] : F0[e];
       }
-      int* mv = P.mv + 6 * p;
-      for (int e = 0; e < 3; ++e) {
-        mv[e] = c0[e];
-        mv[3 + e] = c0[e];
-      }
-      return false;
+      deposit_axis(m, d, P.q[p], c0, f0, f1, dc, cc, cf, Tb);
+      P.x[3 * p + d] = xn;
+      P.img[3 * p + d] = kn;
+      mv[d] = c0;
+      mv[3 + d] = c1;
+      U = ((long long)kn * m.n[d] + c1) * kS + f1;
+    } else {
+      mv[d] = c0;
+      mv[3 + d] = c0;
+      U = ((long long)ko * m.n[d] + c0) * kS + f0;
+      if (d == 0) atomicOr(&ds->err, kErrCellJump);
     }
+    U *= (long long)P.q[p];
   }
-  int cc[3] = {c0[0], c0[1], c0[2]}, cf[3] = {f0[0], f0[1], f0[2]};
-  const int q = P.q[p];
-  for (int d = 0; d < 3; ++d) {
-    deposit_axis(m, d, q, c0[d], f0[d], c1[d], f1[d], kn[d] - ko[d], cc, cf, Tb);
-    cc[d] = c1[d];
-    cf[d] = f1[d];
-  }
-  for (int d = 0; d < 3; ++d) {
-    P.x[3 * p + d] = xn[d];
-    P.img[3 * p + d] = kn[d];
-    c1out[d] = c1[d];
-    f1out[d] = f1[d];
-  }
-  int* mv = P.mv + 6 * p;
-  for (int d = 0; d < 3; ++d) {
-    mv[d] = c0[d];
-    mv[3 + d] = c1[d];
-  }
-  return true;
-}
-
-__device__ inline void accumulate_dipole(const Mesh& m, int q, const int img[3], const int c[3],
-                                         const int f[3], bool active, DevState* ds) {
-  for (int d = 0; d < 3; ++d) {
-    long long U = ((long long)img[d] * m.n[d] + c[d]) * kS + f[d];
-    warp_atomic_add(&ds->Pacc[d], active ? (long long)q * U : 0ll);
-  }
+  quad_dipole_add(ds->Pacc, U);
 }
 
 // ------------------------------------------------------------------ kernels
@@ -235,150 +258,156 @@ __global__ void k_sub_background(int64_t V, long long* __restrict__ Q, long long
 
 __global__ void k_dipole(Mesh m, Particles P, DevState* ds) {
   const int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  const bool active = p < P.n;
-  int c[3] = {0, 0, 0}, f[3] = {0, 0, 0}, img[3] = {0, 0, 0};
-  int q = 0;
-  if (active) {
-    q = P.q[p];
-    for (int d = 0; d < 3; ++d) {
-      quantize(m, d, P.x[3 * p + d], c[d], f[d]);
-      img[d] = P.img[3 * p + d];
+  for (int d = 0; d < 3; ++d) {
+    long long U = 0;
+    if (p < P.n) {
+      int c, f;
+      quantize(m, d, P.x[3 * p + d], c, f);
+      U = (long long)P.q[p] * (((long long)P.img[3 * p + d] * m.n[d] + c) * kS + f);
     }
+    warp_atomic_add(&ds->Pacc[d], U);
   }
-  accumulate_dipole(m, q, img, c, f, active, ds);
+}
+
+__global__ void k_particle_constants(StepParams sp, Particles P) {
+  const int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (p >= P.n) return;
+  const double mass = P.m[p];
+  P.h[p] = __ddiv_rn(0.5 * sp.dt, mass);
+  if (sp.thermo) P.sig[p] = sqrt(2.0 * sp.gamma * mass * sp.kT / sp.dt);
 }
 
 // half kick with the stored force, drift, charge transfer, dipole sum
-__global__ void __launch_bounds__(kThreads)
+__global__ void __launch_bounds__(kQuadThreads)
     k_kick_drift_deposit(Mesh m, StepParams sp, Particles P, unsigned long long* __restrict__ Tb,
                          DevState* ds) {
-  const int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  const int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  const int64_t p = g >> 2;
+  const int d = (int)(g & 3);
   const bool active = p < P.n;
-  int c1[3] = {0, 0, 0}, f1[3] = {0, 0, 0}, kn[3] = {0, 0, 0};
-  int q = 0;
-  if (active) {
-    q = P.q[p];
-    const double h = __ddiv_rn(0.5 * sp.dt, P.m[p]);
-    double xn[3];
-    bool ok = true;
-    for (int d = 0; d < 3; ++d) {
-      const double v = __dadd_rn(P.v[3 * p + d], __dmul_rn(h, P.Ft[3 * p + d]));
-      P.v[3 * p + d] = v;
-      const double step = __dmul_rn(sp.dt, v);
-      if (!(fabs(step) <= 2.0 * m.a)) ok = false;
-      xn[d] = __dadd_rn(P.x[3 * p + d], step);
-      kn[d] = P.img[3 * p + d];
-      if (ok) fold(m.L[d], xn[d], kn[d]);
-    }
-    if (!ok || !move_particle(m, P, p, xn, kn, Tb, c1, f1)) {
-      atomicOr(&ds->err, kErrCellJump);
-      for (int d = 0; d < 3; ++d) {
-        quantize(m, d, P.x[3 * p + d], c1[d], f1[d]);
-        kn[d] = P.img[3 * p + d];
-        P.mv[6 * p + d] = c1[d];
-        P.mv[6 * p + 3 + d] = c1[d];
-      }
+  double x = 0.0, xn = 0.0;
+  int ko = 0, kn = 0;
+  bool ok = true;
+  if (active && d < 3) {
+    const double v = __dadd_rn(P.v[3 * p + d], __dmul_rn(P.h[p], P.Ft[3 * p + d]));
+    P.v[3 * p + d] = v;
+    const double step = __dmul_rn(sp.dt, v);
+    x = P.x[3 * p + d];
+    ko = P.img[3 * p + d];
+    kn = ko;
+    xn = x;
+    if (fabs(step) <= 2.0 * m.a) {
+      xn = __dadd_rn(x, step);
+      fold(m.L[d], xn, kn);
+    } else {
+      ok = false;
     }
   }
-  accumulate_dipole(m, q, kn, c1, f1, active, ds);
+  quad_move(m, P, p, d, active, x, ko, xn, kn, ok, Tb, ds);
 }
 
 // prescribed move to (pos_new, img_new) with its charge transfer
-__global__ void __launch_bounds__(kThreads)
+__global__ void __launch_bounds__(kQuadThreads)
     k_move_deposit(Mesh m, Particles P, const double* __restrict__ pos_new,
                    const int* __restrict__ img_new, unsigned long long* __restrict__ Tb,
                    DevState* ds) {
-  const int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  const int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  const int64_t p = g >> 2;
+  const int d = (int)(g & 3);
   const bool active = p < P.n;
-  int c1[3] = {0, 0, 0}, f1[3] = {0, 0, 0}, kn[3] = {0, 0, 0};
-  int q = 0;
-  if (active) {
-    q = P.q[p];
-    double xn[3];
-    bool ok = true;
-    for (int d = 0; d < 3; ++d) {
-      xn[d] = pos_new[3 * p + d];
-      kn[d] = img_new ? img_new[3 * p + d] : 0;
-      if (!(fabs(xn[d]) <= 4.0 * m.L[d])) ok = false;
-      if (ok) fold(m.L[d], xn[d], kn[d]);
-    }
-    if (!ok || !move_particle(m, P, p, xn, kn, Tb, c1, f1)) {
-      atomicOr(&ds->err, kErrCellJump);
-      for (int d = 0; d < 3; ++d) {
-        quantize(m, d, P.x[3 * p + d], c1[d], f1[d]);
-        kn[d] = P.img[3 * p + d];
-        P.mv[6 * p + d] = c1[d];
-        P.mv[6 * p + 3 + d] = c1[d];
-      }
-    }
+  double x = 0.0, xn = 0.0;
+  int ko = 0, kn = 0;
+  bool ok = true;
+  if (active && d < 3) {
+    x = P.x[3 * p + d];
+    ko = P.img[3 * p + d];
+    xn = pos_new[3 * p + d];
+    kn = img_new ? img_new[3 * p + d] : 0;
+    if (fabs(xn) <= 4.0 * m.L[d])
+      fold(m.L[d], xn, kn);
+    else
+      ok = false;
   }
-  accumulate_dipole(m, q, kn, c1, f1, active, ds);
+  quad_move(m, P, p, d, active, x, ko, xn, kn, ok, Tb, ds);
 }
 
-// Apply the step's transfers: the first thread to take a link's buffered
+// Apply the step's transfers: the first lane to take a link's buffered
 // transfer adds it to the ledger exactly and to D scaled by 2^-48 / a^2.
+// Quad lane c handles corner (c & 1, c >> 1) of every axis and both cells of
+// a crossed face; its exchanges are issued together.
 template <typename T>
-__global__ void __launch_bounds__(kThreads)
+__global__ void __launch_bounds__(kQuadThreads)
     k_apply(Mesh m, Particles P, unsigned long long* __restrict__ Tb, long long* __restrict__ Lg,
             T* __restrict__ D, double scale) {
-  const int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  const int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  const int64_t p = g >> 2;
   if (p >= P.n) return;
+  const int corner = (int)(g & 3);
+  const int a1 = corner & 1, a2 = corner >> 1;
   const int* mv = P.mv + 6 * p;
   const int c0[3] = {mv[0], mv[1], mv[2]};
   const int c1[3] = {mv[3], mv[4], mv[5]};
+  int64_t l[6];
+  int nl = 0;
+#pragma unroll
   for (int d = 0; d < 3; ++d) {
     const int e1 = (d + 1) % 3, e2 = (d + 2) % 3;
     // perpendicular cells at the time of the move along d: axes before d
     // have moved, axes after d have not
     const int p1 = (e1 < d) ? c1[e1] : c0[e1];
     const int p2 = (e2 < d) ? c1[e2] : c0[e2];
-    const int nalong = (c1[d] != c0[d]) ? 2 : 1;
-    for (int s = 0; s < nalong; ++s) {
-      const int ca = s ? c1[d] : c0[d];
-      for (int a2 = 0; a2 < 2; ++a2)
-        for (int a1 = 0; a1 < 2; ++a1) {
-          int at[3];
-          at[d] = ca;
-          at[e1] = p1 + a1;
-          at[e2] = p2 + a2;
-          const int64_t l = link_index(m, d, at[0], at[1], at[2]);
-          const long long t = (long long)atomicExch(&Tb[l], 0ull);
-          if (t != 0) {
-            Lg[l] += t;
-            D[l] = D[l] + (T)((double)t * scale);
-          }
-        }
+    int at[3];
+    at[e1] = p1 + a1;
+    at[e2] = p2 + a2;
+    at[d] = c0[d];
+    l[nl++] = link_index(m, d, at[0], at[1], at[2]);
+    if (c1[d] != c0[d]) {
+      at[d] = c1[d];
+      l[nl++] = link_index(m, d, at[0], at[1], at[2]);
     }
   }
+  long long t[6];
+#pragma unroll
+  for (int s = 0; s < 6; ++s)
+    if (s < nl) t[s] = (long long)atomicExch(&Tb[l[s]], 0ull);
+#pragma unroll
+  for (int s = 0; s < 6; ++s)
+    if (s < nl && t[s] != 0) {
+      Lg[l[s]] += t[s];
+      D[l[s]] = D[l[s]] + (T)((double)t[s] * scale);
+    }
 }
 
 // ------------------------------------------------------------- self energy
 // U_self = q^2 / (2 a eps) sum_{r in {0,1}^3} G(r) prod_d c_d(r_d) with
 // c(0) = (1-f)^2 + f^2, c(1) = 2 f (1-f); the correction force is +dU/dx.
-__device__ inline void self_terms(const StepParams& sp, double a, const int f[3], double q,
-                                  double ie_energy, const double ie_dir[3], double& U,
-                                  double F3[3]) {
+struct SelfC {
   double c[3][2], dc[3][2];
+};
+
+__device__ inline SelfC self_coeffs(const int f[3]) {
+  SelfC s;
   for (int d = 0; d < 3; ++d) {
     const double t = (double)f[d] / (double)kS;
-    c[d][0] = 1.0 - 2.0 * t + 2.0 * t * t;
-    c[d][1] = 2.0 * t - 2.0 * t * t;
-    dc[d][0] = 4.0 * t - 2.0;
-    dc[d][1] = 2.0 - 4.0 * t;
+    s.c[d][0] = 1.0 - 2.0 * t + 2.0 * t * t;
+    s.c[d][1] = 2.0 * t - 2.0 * t * t;
+    s.dc[d][0] = 4.0 * t - 2.0;
+    s.dc[d][1] = 2.0 - 4.0 * t;
   }
-  double u = 0.0, g0 = 0.0, g1 = 0.0, g2 = 0.0;
+  return s;
+}
+
+// sum_r G(r) (derivative factor along `dir`, or none when dir < 0)
+__device__ inline double self_sum(const StepParams& sp, const SelfC& s, int dir) {
+  double u = 0.0;
   for (int t = 0; t < 8; ++t) {
     const int x = t & 1, y = (t >> 1) & 1, z = (t >> 2) & 1;
-    u += sp.G[t] * c[0][x] * c[1][y] * c[2][z];
-    g0 += sp.G[t] * dc[0][x] * c[1][y] * c[2][z];
-    g1 += sp.G[t] * c[0][x] * dc[1][y] * c[2][z];
-    g2 += sp.G[t] * c[0][x] * c[1][y] * dc[2][z];
+    const double a0 = (dir == 0) ? s.dc[0][x] : s.c[0][x];
+    const double a1 = (dir == 1) ? s.dc[1][y] : s.c[1][y];
+    const double a2 = (dir == 2) ? s.dc[2][z] : s.c[2][z];
+    u += sp.G[t] * a0 * a1 * a2;
   }
-  const double pre = q * q / (2.0 * a);
-  U = pre * ie_energy * u;
-  F3[0] = pre * ie_dir[0] * g0 / a;
-  F3[1] = pre * ie_dir[1] * g1 / a;
-  F3[2] = pre * ie_dir[2] * g2 / a;
+  return u;
 }
 
 // GF: mean 1/eps of the 12 cell links for every direction; DIRECT: per
@@ -406,8 +435,6 @@ __device__ inline void self_ie(const Mesh& m, const double* __restrict__ ie64, c
     for (int d = 0; d < 3; ++d) ie_dir[d] = ie_cell;
 }
 
-// force gather (Eq. 18 without v x B): E_d from the 4 d-links of the cell
-// with the same weights that carry the current, in the field precision T
 // the last CTA of the gather closes the update: P of this state becomes the
 // reported one, the accumulator is cleared for the next move, and the step
 // counter advances (finish == 2)
@@ -429,72 +456,84 @@ __device__ inline void finish_update(DevState* ds, int finish) {
   }
 }
 
+// Force gather (Eq. 18 without v x B).  Quad lane c loads corner
+// (c & 1, c >> 1) of the cell's d-links for the three axes; the quad sums
+// E_d = sum D ie w (field precision T) and the 1/eps averages of the self
+// term; then lane d < 3 finishes component d: q E_d, the self-energy and
+// dipole corrections, the Langevin force and the half kick.
 template <typename T>
-__device__ inline void gather_one(const Mesh& m, const StepParams& sp, Particles P, int64_t p,
-                                  const T* __restrict__ D, const T* __restrict__ ie,
-                                  const double* __restrict__ ie64, DevState* ds, int kick) {
-  int c[3], f[3];
-  for (int d = 0; d < 3; ++d) quantize(m, d, P.x[3 * p + d], c[d], f[d]);
-  const double q = (double)P.q[p];
-  double F[3];
-  for (int d = 0; d < 3; ++d) {
-    const int e1 = (d + 1) % 3, e2 = (d + 2) % 3;
-    T E = T(0);
-    for (int a2 = 0; a2 < 2; ++a2)
-      for (int a1 = 0; a1 < 2; ++a1) {
-        int at[3] = {c[0], c[1], c[2]};
-        at[e1] += a1;
-        at[e2] += a2;
-        const int64_t l = link_index(m, d, at[0], at[1], at[2]);
-        const T w = ((T)wgt(f[e1], a1) / (T)kS) * ((T)wgt(f[e2], a2) / (T)kS);
-        E = E + D[l] * ie[l] * w;
-      }
-    F[d] = q * (double)E;
-  }
-  if (sp.self_mode != 0) {
-    double U, Fs[3], ie_cell, ie_dir[3];
-    self_ie(m, ie64, c, f, sp.self_mode, ie_cell, ie_dir);
-    self_terms(sp, m.a, f, q, ie_cell, ie_dir, U, Fs);
-    for (int d = 0; d < 3; ++d) F[d] = F[d] + Fs[d];
-  }
-  if (sp.dipole_corr) {
-    double Pd[3];
-    for (int d = 0; d < 3; ++d) Pd[d] = (double)(long long)ds->Pacc[d] * (m.a / (double)kS);
-    for (int d = 0; d < 3; ++d) {
-      const double MP = sp.Minv[3 * d] * Pd[0] + sp.Minv[3 * d + 1] * Pd[1] + sp.Minv[3 * d + 2] * Pd[2];
-      F[d] = F[d] + q * MP / sp.Vbox;
-    }
-  }
-  double Ft[3] = {F[0], F[1], F[2]};
-  if (sp.thermo) {
-    const long long step = ds->step;
-    unsigned ctr[4] = {(unsigned)p, (unsigned)((unsigned long long)p >> 32), (unsigned)step,
-                       (unsigned)((unsigned long long)step >> 32)};
-    philox4x32_10(ctr, (unsigned)sp.seed, (unsigned)(sp.seed >> 32));
-    const double mass = P.m[p];
-    const double sig = sqrt(2.0 * sp.gamma * mass * sp.kT / sp.dt);
-    for (int d = 0; d < 3; ++d) {
-      const double fr = -sp.gamma * mass * P.v[3 * p + d];
-      const double fn = sig * unit_noise(ctr[d]);
-      Ft[d] = F[d] + (fr + fn);
-    }
-  }
-  for (int d = 0; d < 3; ++d) {
-    P.F[3 * p + d] = F[d];
-    P.Ft[3 * p + d] = Ft[d];
-  }
-  if (kick) {
-    const double h = __ddiv_rn(0.5 * sp.dt, P.m[p]);
-    for (int d = 0; d < 3; ++d) P.v[3 * p + d] = __dadd_rn(P.v[3 * p + d], __dmul_rn(h, Ft[d]));
-  }
-}
-
-template <typename T>
-__global__ void __launch_bounds__(kThreads)
+__global__ void __launch_bounds__(kQuadThreads)
     k_gather(Mesh m, StepParams sp, Particles P, const T* __restrict__ D, const T* __restrict__ ie,
              const double* __restrict__ ie64, DevState* ds, int kick, int finish) {
-  const int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (p < P.n) gather_one<T>(m, sp, P, p, D, ie, ie64, ds, kick);
+  const int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  const int64_t p = g >> 2;
+  const int lane4 = (int)(g & 3);
+  const bool active = p < P.n;
+  const unsigned full = 0xffffffffu;
+  const int a1 = lane4 & 1, a2 = lane4 >> 1;
+  int c[3] = {0, 0, 0}, f[3] = {0, 0, 0};
+  T E[3] = {T(0), T(0), T(0)};
+  double iw[3] = {0.0, 0.0, 0.0}, itot = 0.0;
+  if (active) {
+    for (int d = 0; d < 3; ++d) quantize(m, d, P.x[3 * p + d], c[d], f[d]);
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+      const int e1 = (d + 1) % 3, e2 = (d + 2) % 3;
+      int at[3] = {c[0], c[1], c[2]};
+      at[e1] += a1;
+      at[e2] += a2;
+      const int64_t l = link_index(m, d, at[0], at[1], at[2]);
+      const T w = ((T)wgt(f[e1], a1) / (T)kS) * ((T)wgt(f[e2], a2) / (T)kS);
+      E[d] = D[l] * ie[l] * w;
+      if (sp.self_mode != 0) {
+        const double iv = ie64[l];
+        const double wd = ((double)wgt(f[e1], a1) / (double)kS) * ((double)wgt(f[e2], a2) / (double)kS);
+        itot += iv;
+        iw[d] = iv * wd;
+      }
+    }
+  }
+  // quad sums in corner order ((c0 + c1) + (c2 + c3))
+#pragma unroll
+  for (int d = 0; d < 3; ++d) {
+    E[d] = E[d] + __shfl_xor_sync(full, E[d], 1);
+    E[d] = E[d] + __shfl_xor_sync(full, E[d], 2);
+    iw[d] = iw[d] + __shfl_xor_sync(full, iw[d], 1);
+    iw[d] = iw[d] + __shfl_xor_sync(full, iw[d], 2);
+  }
+  itot = itot + __shfl_xor_sync(full, itot, 1);
+  itot = itot + __shfl_xor_sync(full, itot, 2);
+  if (active && lane4 < 3) {
+    const int d = lane4;
+    const double q = (double)P.q[p];
+    double F = q * (double)E[d];
+    if (sp.self_mode != 0) {
+      const double ie_cell = itot / 12.0;
+      const double ie_d = (sp.self_mode == 2) ? iw[d] : ie_cell;
+      const SelfC sc = self_coeffs(f);
+      const double pre = q * q / (2.0 * m.a);
+      F = F + pre * ie_d * self_sum(sp, sc, d) / m.a;
+    }
+    if (sp.dipole_corr) {
+      double Pd[3];
+      for (int e = 0; e < 3; ++e) Pd[e] = (double)(long long)ds->Pacc[e] * (m.a / (double)kS);
+      const double MP = sp.Minv[3 * d] * Pd[0] + sp.Minv[3 * d + 1] * Pd[1] + sp.Minv[3 * d + 2] * Pd[2];
+      F = F + q * MP / sp.Vbox;
+    }
+    double Ft = F;
+    if (sp.thermo) {
+      const long long step = ds->step;
+      unsigned ctr[4] = {(unsigned)p, (unsigned)((unsigned long long)p >> 32), (unsigned)step,
+                         (unsigned)((unsigned long long)step >> 32)};
+      philox4x32_10(ctr, (unsigned)sp.seed, (unsigned)(sp.seed >> 32));
+      const double fr = -sp.gamma * P.m[p] * P.v[3 * p + d];
+      const double fn = P.sig[p] * unit_noise(ctr[d]);
+      Ft = F + (fr + fn);
+    }
+    P.F[3 * p + d] = F;
+    P.Ft[3 * p + d] = Ft;
+    if (kick) P.v[3 * p + d] = __dadd_rn(P.v[3 * p + d], __dmul_rn(P.h[p], Ft));
+  }
   if (finish) finish_update(ds, finish);
 }
 
@@ -531,10 +570,11 @@ __global__ void __launch_bounds__(kRedThreads)
     if (sp.self_mode != 0) {
       int c[3], f[3];
       for (int d = 0; d < 3; ++d) quantize(m, d, P.x[3 * p + d], c[d], f[d]);
-      double U, Fs[3], ie_cell, ie_dir[3];
+      double ie_cell, ie_dir[3];
       self_ie(m, ie64, c, f, sp.self_mode, ie_cell, ie_dir);
-      self_terms(sp, m.a, f, (double)P.q[p], ie_cell, ie_dir, U, Fs);
-      se += U;
+      const SelfC sc = self_coeffs(f);
+      const double q = (double)P.q[p];
+      se += q * q / (2.0 * m.a) * ie_cell * self_sum(sp, sc, -1);
     }
   }
   const double s1 = block_sum(ke, sh);
@@ -563,29 +603,33 @@ void launch_dipole(const Mesh& m, Particles p, DevState* ds, cudaStream_t st) {
   if (p.n > 0) k_dipole<<<blocks_for(p.n), kThreads, 0, st>>>(m, p, ds);
 }
 
+void launch_particle_constants(const StepParams& sp, Particles p, cudaStream_t st) {
+  if (p.n > 0) k_particle_constants<<<blocks_for(p.n), kThreads, 0, st>>>(sp, p);
+}
+
 void launch_kick_drift_deposit(const Mesh& m, const StepParams& sp, Particles p, long long* Tb,
                                DevState* ds, cudaStream_t st) {
   if (p.n > 0)
-    k_kick_drift_deposit<<<blocks_for(p.n), kThreads, 0, st>>>(m, sp, p, (unsigned long long*)Tb,
-                                                               ds);
+    k_kick_drift_deposit<<<blocks_for(4 * p.n, kQuadThreads), kQuadThreads, 0, st>>>(
+        m, sp, p, (unsigned long long*)Tb, ds);
 }
 
 void launch_move_deposit(const Mesh& m, Particles p, const double* pos_new, const int* img_new,
                          long long* Tb, DevState* ds, cudaStream_t st) {
   if (p.n > 0)
-    k_move_deposit<<<blocks_for(p.n), kThreads, 0, st>>>(m, p, pos_new, img_new,
-                                                         (unsigned long long*)Tb, ds);
+    k_move_deposit<<<blocks_for(4 * p.n, kQuadThreads), kQuadThreads, 0, st>>>(
+        m, p, pos_new, img_new, (unsigned long long*)Tb, ds);
 }
 
 void launch_apply(const Mesh& m, int prec, Particles p, long long* Tb, long long* Lg, void* D,
                   double scale, cudaStream_t st) {
   if (p.n <= 0) return;
+  const unsigned nb = blocks_for(4 * p.n, kQuadThreads);
   if (prec == 1)
-    k_apply<float><<<blocks_for(p.n), kThreads, 0, st>>>(m, p, (unsigned long long*)Tb, Lg,
-                                                         (float*)D, scale);
+    k_apply<float><<<nb, kQuadThreads, 0, st>>>(m, p, (unsigned long long*)Tb, Lg, (float*)D, scale);
   else
-    k_apply<double><<<blocks_for(p.n), kThreads, 0, st>>>(m, p, (unsigned long long*)Tb, Lg,
-                                                          (double*)D, scale);
+    k_apply<double><<<nb, kQuadThreads, 0, st>>>(m, p, (unsigned long long*)Tb, Lg, (double*)D,
+                                                 scale);
 }
 
 void launch_gather(const Mesh& m, int prec, const StepParams& sp, Particles p, const void* D,
@@ -595,12 +639,13 @@ void launch_gather(const Mesh& m, int prec, const StepParams& sp, Particles p, c
     if (finish) k_step_end<<<1, 32, 0, st>>>(ds, finish == 2 ? 1 : 0);
     return;
   }
+  const unsigned nb = blocks_for(4 * p.n, kQuadThreads);
   if (prec == 1)
-    k_gather<float><<<blocks_for(p.n), kThreads, 0, st>>>(m, sp, p, (const float*)D,
-                                                          (const float*)ie, ie64, ds, kick, finish);
+    k_gather<float><<<nb, kQuadThreads, 0, st>>>(m, sp, p, (const float*)D, (const float*)ie,
+                                                 ie64, ds, kick, finish);
   else
-    k_gather<double><<<blocks_for(p.n), kThreads, 0, st>>>(m, sp, p, (const double*)D,
-                                                           (const double*)ie, ie64, ds, kick, finish);
+    k_gather<double><<<nb, kQuadThreads, 0, st>>>(m, sp, p, (const double*)D, (const double*)ie,
+                                                  ie64, ds, kick, finish);
 }
 
 void launch_step_end(DevState* ds, int advance, cudaStream_t st) {
