@@ -221,6 +221,40 @@ memd_status memd_reset_kernel_stats(memd_ctx *ctx);
 /* Block the host until all work issued by ctx has finished. */
 memd_status memd_synchronize(memd_ctx *ctx);
 
+/* ---------------------------------------------------------------------------
+ * Field energy without any device allocation.  The paper has no counterpart:
+ * this is a service for callers that cannot allocate device memory -- code
+ * that runs inside another framework's memory pool, a host that reserved all
+ * device memory up front for its own arena, or a real-time loop where an
+ * allocation could fail or stall the device.  It computes the same electric
+ * and magnetic terms as memd_energy from device arrays the caller owns, and
+ * calls no cudaMalloc, cudaFree or allocating library routine.
+ *
+ * mesh, a, c_light, dt: as at memd_create; precision: MEMD_FP32 or MEMD_FP64,
+ * the element type of D, B and inv_eps, which are device arrays of 3 V values
+ * in the library's layout (component major, x fastest).  out2: device pointer
+ * to 2 doubles, set to a^3 sum D^2 / (2 eps) and (c^2 a^3 / 2) sum B^{n+1/2}
+ * B^{n+3/2}.  cuda_stream: cudaStream_t the work is queued on (NULL = legacy
+ * default stream); the call returns without synchronising.
+ *
+ * The per-block partial sums live in one fixed device array of
+ * MEMD_STATIC_MAX_BLOCKS x 2 doubles (1 MiB) inside the library, held by
+ * every GPU that loads the library until the process exits.  Meshes with
+ * more than MEMD_STATIC_MAX_SITES vertices are rejected with
+ * MEMD_ERR_INVALID.  The first call on each device (made with that device
+ * current) looks up the array's device address; make that first call before
+ * any CUDA stream capture.  All calls share the array and each overwrites it
+ * completely, so nothing has to be cleared, but calls whose kernels overlap
+ * on the GPU race: queue them on one stream or order them with events.
+ * Errors: INVALID (bad argument, mesh too large), CUDA. */
+#define MEMD_STATIC_SITES_PER_BLOCK 2048
+#define MEMD_STATIC_MAX_BLOCKS 65536
+#define MEMD_STATIC_MAX_SITES ((int64_t)MEMD_STATIC_SITES_PER_BLOCK * MEMD_STATIC_MAX_BLOCKS)
+memd_status memd_field_energy_static(const int32_t mesh[3], double a, double c_light,
+                                     double dt, int32_t precision, const void *D,
+                                     const void *B, const void *inv_eps, double *out2,
+                                     void *cuda_stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -27,6 +27,7 @@ SOURCES = {
     "memd_field.cu": [],
     "memd_setup.cu": [],
     "memd_particles.cu": ["--fmad=false"],
+    "memd_static.cu": [],
 }
 
 

@@ -25,7 +25,8 @@ EXPORTS = ("memd_default_options", "memd_status_string", "memd_last_error", "mem
            "memd_destroy", "memd_init_field", "memd_step", "memd_forces", "memd_forces_device",
            "memd_energy", "memd_get_particles", "memd_set_particles", "memd_move",
            "memd_get_fields", "memd_set_fields", "memd_compute_forces", "memd_get_setup",
-           "memd_get_kernel_stats", "memd_reset_kernel_stats", "memd_synchronize")
+           "memd_get_kernel_stats", "memd_reset_kernel_stats", "memd_synchronize",
+           "memd_field_energy_static")
 
 
 class MemdError(RuntimeError):
@@ -114,6 +115,8 @@ def lib(build_if_missing=True):
     L.memd_get_kernel_stats.argtypes = [vp, C.POINTER(KernelStats)]
     L.memd_reset_kernel_stats.argtypes = [vp]
     L.memd_synchronize.argtypes = [vp]
+    L.memd_field_energy_static.argtypes = [i32p, C.c_double, C.c_double, C.c_double, C.c_int32,
+                                           vp, vp, vp, vp, vp]
     for name in EXPORTS:
         if name not in ("memd_default_options", "memd_destroy", "memd_status_string",
                         "memd_last_error"):
