@@ -214,7 +214,8 @@ def run_memd(args, world, rank, local):
     stream = torch.cuda.Stream(device=dev)
     sysc = workload(args.workload, rank)
     g = Memd(sysc.mesh, sysc.box, sysc.eps, c_light=sysc.c_light, dt=sysc.dt,
-             precision=sysc.precision, seed=sysc.seed, time_kernels=True, stream=stream)
+             precision=sysc.precision, seed=sysc.seed, time_kernels=True, stream=stream,
+             field_kernel=args.field_kernel)
     g.init_field(sysc.x, sysc.q, sysc.m, sysc.v)
     th = sysc.thermostat
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
@@ -286,7 +287,7 @@ def run_memd(args, world, rank, local):
                        "l2": "flushed (256 MiB write) before every timed step",
                        "parallelism": f"replicas x{world}" if world > 1 else "single system"},
             "particle_steps_per_s": world * n * args.steps / (tot_ms * 1e-3),
-            "roofline": {"bound": "hbm", "kernel": "k_fused_curl (B then D update, one pass)",
+            "roofline": {"bound": "hbm", "kernel": ks.field_kernel + " (B then D update, one pass)",
                          "achieved": achieved, "peak": hbm, "unit": "GB/s",
                          "frac": achieved / hbm, "peak_kind": peak_kind, "traffic": traffic,
                          "bytes_per_launch": ks.field_bytes,
@@ -302,7 +303,155 @@ def run_memd(args, world, rank, local):
     g.close()
     if rank == 0 and out is not None and args.large > 0:
         out["large_mesh"] = large_mesh(args.large, dev, stream, args)
+    if rank == 0 and out is not None and args.batch > 0:
+        out["batched"] = batched(args.batch, dev, args)
+    if rank == 0 and out is not None and args.serve > 0:
+        out["served"] = served(args.serve, args)
+    if rank == 0 and out is not None and not args.no_cpu_baseline:
+        out["precision_report"] = precision_report(sysc)
     return out
+
+
+def precision_report(sysc):
+    """Each observable's error of the FP32-field GPU path against the FP64
+    oracle after 10 steps from the same state (relative RMS; energies and
+    the dipole moment as relative differences)."""
+    from oracle import oracle as O
+    from paper_1309_7859_gb300.memd import Memd
+    kinds = {"const": O.EPS_CONST, "links": O.EPS_LINKS, "vertices": O.EPS_VERTICES,
+             "tanh": O.EPS_TANH, "sin": O.EPS_SIN}
+    o = O.OracleSystem(sysc.mesh, sysc.box, eps=dict(kind=kinds[sysc.eps.kind], axis=sysc.eps.axis,
+                                                     params=sysc.eps.params),
+                       c_light=sysc.c_light, dt=sysc.dt, seed=sysc.seed)
+    o.set_particles(sysc.x, sysc.q, sysc.m, sysc.v)
+    o.init_field()
+    g = Memd(sysc.mesh, sysc.box, sysc.eps, c_light=sysc.c_light, dt=sysc.dt, precision="fp32",
+             seed=sysc.seed)
+    g.init_field(sysc.x, sysc.q, sysc.m, sysc.v)
+    g.set_fields(D=o.field("D"), B=o.field("B"), Lg=o.field("Lg"))
+    g.set_particles(x=o.particles("x"), v=o.particles("v"), img=o.particles("img"))
+    g.compute_forces()
+    o.step(10, thermostat=sysc.thermostat)
+    g.step(10, thermostat=sysc.thermostat)
+    D, B, Lg = g.fields()
+    x, v, img = g.particles()
+    rel = lambda a, b: float(np.sqrt(np.sum((a - b) ** 2) / max(np.sum(b * b), 1e-300)))
+    eg, eo = g.energy(), o.energy()
+    rep = {"steps": 10, "workload": sysc.name, "D": rel(D, o.field("D")), "B": rel(B, o.field("B")),
+           "forces": rel(g.forces(), o.particles("F")), "velocities": rel(v, o.particles("v")),
+           "positions_max_abs": float(np.max(np.abs(x - o.particles("x")))),
+           "ledger_mismatches": int(np.sum(Lg != o.field("Lg"))),
+           "gauss_exact": bool(eg["gauss_exact"])}
+    for k in ("electric", "magnetic", "kinetic", "total", "P0", "P1", "P2"):
+        rep[k] = abs(eg[k] - eo[k]) / max(abs(eo[k]), 1e-300)
+    g.close()
+    return rep
+
+
+def served(count, args):
+    """A served stream: `count` requests (meshes 16-96, 100-50000 charges,
+    smooth random eps, 200-5000 steps, FP32) with Poisson arrivals, admitted
+    by device-memory footprint into a continuous batch; p50/p99 latency and
+    aggregate throughput.  Beside it, the plain single-replica FP64 GPU path
+    on the first requests (one at a time, short runs)."""
+    import torch
+    from paper_1309_7859_gb300 import inputs
+    from paper_1309_7859_gb300.memd import Memd, Server, serve
+    reqs = inputs.served_stream(count=count, smax=args.serve_max_steps)
+    rng = np.random.default_rng(4242)
+    arrivals = np.cumsum(rng.exponential(1.0 / args.serve_rate, size=count)).tolist()
+    srv = Server(precision="fp32", budget_bytes=args.serve_budget << 30, max_slots=128,
+                 quantum=50, thermostat=(1.0, 1.0))
+    t0 = time.perf_counter()
+    rec = serve(srv, reqs, arrivals)
+    wall = time.perf_counter() - t0
+    lat = np.array([r["latency"] for r in rec])
+    links = sum(3 * r.sites * r.steps for r in reqs)
+    parts = sum(r.n * r.steps for r in reqs)
+    st = srv.stats()
+    srv.close()
+    # plain single-replica FP64 path, requests one at a time
+    k, t_single, l_single = 0, 0.0, 0
+    for r in reqs[:8]:
+        steps = min(r.steps, 200)
+        g = Memd(r.mesh, r.box, r.eps, c_light=r.c_light, dt=r.dt, precision="fp64", seed=r.seed)
+        g.init_field(r.x, r.q, r.m, r.v)
+        g.step(5, thermostat=(1.0, 1.0))
+        g.synchronize()
+        a = time.perf_counter()
+        g.step(steps, thermostat=(1.0, 1.0))
+        g.synchronize()
+        t_single += time.perf_counter() - a
+        l_single += 3 * r.sites * steps
+        g.close()
+        k += 1
+    return {"requests": count, "arrival_rate_per_s": args.serve_rate,
+            "budget_gib": args.serve_budget, "max_slots": 128, "quantum": 50,
+            "max_steps": args.serve_max_steps, "wall_s": wall,
+            "p50_latency_s": float(np.percentile(lat, 50)),
+            "p99_latency_s": float(np.percentile(lat, 99)),
+            "link_updates_per_s": links / wall, "particle_steps_per_s": parts / wall,
+            "setup_s": st["setup_s"],
+            "stepping_link_updates_per_s": links / max(wall - st["setup_s"], 1e-9),
+            "mean_budget_use": st["budget_use_sum"] / max(1, st["rounds"]),
+            "rounds": st["rounds"], "batch_rebuilds": st["rebuilds"],
+            "single_fp64_link_updates_per_s": l_single / max(t_single, 1e-9),
+            "single_fp64_sample": f"first {k} requests one at a time, up to 200 steps each, FP64 fields",
+            "note": "wall time includes every request's setup (eps, Green's table, "
+                    "eps_eff and initial relaxations) and the arrival gaps"}
+
+
+def batched(count, dev, args):
+    """The batched-replica workload: `count` independent systems (meshes from
+    {16,24,32,48}^3, 200-8000 charges, random slabs, FP32) stepped together,
+    four launches per step for all of them."""
+    import torch
+    from paper_1309_7859_gb300 import inputs
+    from paper_1309_7859_gb300.memd import Batch, Memd
+    systems = inputs.batch_replicas(count=count)
+    stream = torch.cuda.Stream(device=dev)
+    t0 = time.perf_counter()
+    members = []
+    for i, s in enumerate(systems):
+        g = Memd(s.mesh, s.box, s.eps, c_light=s.c_light, dt=s.dt, precision=s.precision,
+                 seed=s.seed, stream=stream, time_kernels=(i == 0), field_kernel="ldg")
+        g.init_field(s.x, s.q, s.m, s.v)
+        members.append(g)
+    setup_s = time.perf_counter() - t0
+    b = Batch(members)
+    th = systems[0].thermostat
+    steps = max(20, min(args.steps, 200))
+    with torch.cuda.stream(stream):
+        b.step(5, thermostat=th)
+        b.synchronize()
+        b.kernel_stats()  # reset
+        ev = (torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+        ev[0].record(stream)
+        b.step(steps, thermostat=th)
+        ev[1].record(stream)
+        b.synchronize()
+    ms = ev[0].elapsed_time(ev[1])
+    ks = b.kernel_stats()
+    per = ks.field_ms / max(1, ks.field_launches)
+    hbm, kind = peaks()
+    ach = ks.field_bytes / (per * 1e-3) / 1e9
+    sites = sum(s.sites for s in systems)
+    parts = sum(s.n for s in systems)
+    exact = all(g.energy()["gauss_exact"] == 1.0 for g in members)
+    b.close()
+    for g in members:
+        g.close()
+    return {"workload": f"batch-{count} replicas (meshes {{16,24,32,48}}^3, 200-8000 charges, "
+                        f"random slabs, FP32)", "replicas": count, "sites": sites,
+            "charges": parts, "steps": steps, "ms_per_step": ms / steps,
+            "link_updates_per_s": 3 * sites * steps / (ms * 1e-3),
+            "particle_steps_per_s": parts * steps / (ms * 1e-3),
+            "launches_per_step": ks.launches_per_step, "setup_s": setup_s,
+            "l2": f"fields {sites * 60 / 1e6:.0f} MB, larger than L2, no flush",
+            "roofline": {"bound": "hbm", "kernel": ks.field_kernel, "achieved": ach, "peak": hbm,
+                         "unit": "GB/s", "frac": ach / hbm, "peak_kind": kind,
+                         "bytes_per_launch": ks.field_bytes, "ms_per_launch": per},
+            "gauss_exact": exact}
 
 
 def large_mesh(N, dev, stream, args):
@@ -312,7 +461,8 @@ def large_mesh(N, dev, stream, args):
     from paper_1309_7859_gb300.memd import Memd
     sysc = workload(f"bigslab-{N}")
     g = Memd(sysc.mesh, sysc.box, sysc.eps, c_light=sysc.c_light, dt=sysc.dt,
-             precision=sysc.precision, seed=sysc.seed, time_kernels=True, stream=stream)
+             precision=sysc.precision, seed=sysc.seed, time_kernels=True, stream=stream,
+             field_kernel=args.field_kernel)
     g.init_field(sysc.x, sysc.q, sysc.m, sysc.v)
     th = sysc.thermostat
     steps = max(10, min(args.steps, 50))
@@ -338,7 +488,7 @@ def large_mesh(N, dev, stream, args):
             "link_updates_per_s": links * steps / (ms * 1e-3),
             "particle_steps_per_s": sysc.n * steps / (ms * 1e-3),
             "l2": "fields (1 GB) larger than L2, no flush",
-            "roofline": {"bound": "hbm", "kernel": "k_fused_curl", "achieved": ach, "peak": hbm,
+            "roofline": {"bound": "hbm", "kernel": ks.field_kernel, "achieved": ach, "peak": hbm,
                          "unit": "GB/s", "frac": ach / hbm, "peak_kind": kind,
                          "bytes_per_launch": ks.field_bytes, "ms_per_launch": per},
             "gauss_exact": bool(e["gauss_exact"])}
@@ -353,6 +503,14 @@ def main():
     ap.add_argument("--workload", default="slab-32")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
+    ap.add_argument("--field-kernel", default="auto", choices=["auto", "ldg", "tma"])
+    ap.add_argument("--batch", type=int, default=64,
+                    help="replicas of the extra batched measurement (0: skip)")
+    ap.add_argument("--serve", type=int, default=128,
+                    help="requests of the extra served-stream measurement (0: skip)")
+    ap.add_argument("--serve-rate", type=float, default=40.0)
+    ap.add_argument("--serve-budget", type=int, default=8, help="GiB")
+    ap.add_argument("--serve-max-steps", type=int, default=5000)
     ap.add_argument("--large", type=int, default=256,
                     help="edge of the extra larger-than-L2 system (0: skip)")
     args = ap.parse_args()

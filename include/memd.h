@@ -99,8 +99,14 @@ typedef struct memd_options {
   void *alloc_user;
   int32_t time_kernels;   /* 1: CUDA events around the field kernels, see
                              memd_get_kernel_stats */
-  int32_t reserved[7];
+  int32_t field_kernel;   /* MEMD_FIELD_AUTO: autotuned over both kernels below;
+                             MEMD_FIELD_LDG: plain-load kernel only; MEMD_FIELD_TMA:
+                             TMA-staged kernel (when x rows are 16-byte multiples,
+                             else the plain-load kernel) */
+  int32_t reserved[6];
 } memd_options;
+
+enum { MEMD_FIELD_AUTO = 0, MEMD_FIELD_LDG = 1, MEMD_FIELD_TMA = 2 };
 
 typedef struct memd_thermostat {
   double gamma; /* friction rate; Langevin force -gamma m v + sqrt(2 gamma m kT / dt) xi */
@@ -126,6 +132,10 @@ typedef struct memd_kernel_stats {
   int64_t field_launches; /* launches timed */
   double field_bytes;     /* algorithmic bytes per field launch */
   int64_t launches_per_step;
+  int32_t field_tma;      /* field kernel chosen at create: 1 TMA-staged, 0 plain loads */
+  int32_t field_ty;       /* its tile height (rows of 32 sites) */
+  int32_t field_zchunk;   /* its z planes per CTA */
+  int32_t pad;
 } memd_kernel_stats;
 
 /* Fill *opt with defaults: FP64, GF self term, dipole correction on,
@@ -220,6 +230,128 @@ memd_status memd_reset_kernel_stats(memd_ctx *ctx);
 
 /* Block the host until all work issued by ctx has finished. */
 memd_status memd_synchronize(memd_ctx *ctx);
+
+/* ---------------------------------------------------------------------------
+ * Batched replicas.  A batch steps many independent, initialised contexts
+ * (different meshes, charges and eps profiles) together: every time step is
+ * one CUDA graph of four kernels over all members (deposition beside the
+ * field update, then transfer application, then the gather), each kernel
+ * covering every member through a per-replica descriptor table.  A member
+ * gives the same result in the batch as stepped alone with the plain-load
+ * field kernel (MEMD_FIELD_LDG).  Members must share the device, the
+ * precision and the CUDA stream; the batch does not own them, and they stay
+ * usable one by one (memd_forces, memd_energy, ...) between batch steps.
+ * Re-initialising a member is noticed at the next batch step. */
+typedef struct memd_batch memd_batch;
+
+/* Group count >= 1 initialised contexts.  Errors: INVALID (mixed device,
+ * precision or stream, or a member not initialised), OOM, CUDA. */
+memd_status memd_batch_create(int32_t count, memd_ctx *const *members, memd_batch **out);
+
+/* Advance every member by nsteps steps (th NULL: constant energy).
+ * Asynchronous like memd_step; errors of members are reported by their own
+ * synchronising calls and by memd_batch_synchronize. */
+memd_status memd_batch_step(memd_batch *b, int64_t nsteps, const memd_thermostat *th);
+
+/* Wait for the batch's work; returns the first member error, if any. */
+memd_status memd_batch_synchronize(memd_batch *b);
+
+/* Event timing of the batched field kernel (when member 0 has time_kernels)
+ * and the algorithmic bytes of one launch over all members; reading the
+ * timing resets it. */
+memd_status memd_batch_kernel_stats(memd_batch *b, memd_kernel_stats *out);
+
+/* Release the batch's own tables (members are untouched; destroy the batch
+ * before any of its members). */
+void memd_batch_destroy(memd_batch *b);
+
+/* ---------------------------------------------------------------------------
+ * Request server (continuous batching).  Requests -- a system plus a number
+ * of steps -- queue in arrival order; each memd_server_pump call is one
+ * scheduling round: finished requests are retired (results copied to host
+ * memory, device memory released), queued requests are admitted first come
+ * first served while the device-memory budget and the slot count allow,
+ * and all resident systems advance together as one batch by one quantum of
+ * steps (shortened so that no request overshoots).  A request that arrives
+ * while others run joins at the next round and shares their kernel
+ * launches.  Every request gets the same result as when run alone with the
+ * plain-load field kernel.  One server is driven by one host thread. */
+typedef struct memd_server memd_server;
+
+enum { MEMD_REQ_QUEUED = 0, MEMD_REQ_RUNNING = 1, MEMD_REQ_DONE = 2, MEMD_REQ_FAILED = 3 };
+
+typedef struct memd_server_options {
+  int32_t precision;     /* MEMD_FP32 | MEMD_FP64 for every request */
+  int32_t max_slots;     /* systems resident at once */
+  int64_t budget_bytes;  /* device memory the resident systems may hold */
+  int32_t quantum;       /* steps per scheduling round */
+  int32_t device;        /* CUDA device, -1 = current */
+  void *cuda_stream;     /* stream of all resident systems (NULL: the server's own) */
+  memd_alloc_fn alloc;   /* device allocator of the systems (NULL: cudaMalloc) */
+  memd_free_fn free;
+  void *alloc_user;
+  int32_t thermostat;    /* 1: Langevin (gamma, kT) for every request, 0: constant energy */
+  int32_t pad;
+  double gamma, kT;
+  int32_t reserved[4];
+} memd_server_options;
+
+typedef struct memd_request {
+  int32_t mesh[3];
+  double box[3];
+  memd_eps_profile eps;  /* values copied at submit */
+  double c_light, dt;
+  int64_t n;             /* charges; pos (n x 3), q (n) required, mass / vel may be NULL */
+  const double *pos;
+  const int32_t *q;
+  const double *mass;
+  const double *vel;
+  uint64_t seed;
+  int64_t nsteps;
+} memd_request;
+
+/* Defaults: FP32, 64 slots, 8 GiB budget, quantum 50, constant energy. */
+void memd_server_default_options(memd_server_options *opt);
+memd_status memd_server_create(const memd_server_options *opt, memd_server **out);
+void memd_server_destroy(memd_server *s);
+
+/* Queue a request (all inputs copied); *id identifies it.  Errors: INVALID. */
+memd_status memd_server_submit(memd_server *s, const memd_request *req, int64_t *id);
+
+/* One scheduling round (retire, admit, step one quantum); reports the
+ * resident, queued and finished request counts (any may be NULL).  Blocks
+ * only to collect the previous round's finished requests. */
+memd_status memd_server_pump(memd_server *s, int32_t *n_active, int32_t *n_queued,
+                             int32_t *n_done);
+
+/* MEMD_REQ_* state of a request. */
+memd_status memd_server_status(memd_server *s, int64_t id, int32_t *state);
+
+/* Results of a finished request (any pointer may be NULL): folded positions,
+ * velocities, image counters, electrostatic forces (n x 3) and energy terms.
+ * Errors: STATE (not finished, or failed: memd_server_last_error says why). */
+memd_status memd_server_result(memd_server *s, int64_t id, double *pos, double *vel,
+                               int32_t *img, double *forces, memd_energy_terms *e);
+
+/* Forget a finished request and its stored results. */
+memd_status memd_server_release(memd_server *s, int64_t id);
+
+/* Device bytes held by the resident systems (the admission ledger). */
+int64_t memd_server_used_bytes(const memd_server *s);
+
+typedef struct memd_server_stats {
+  double setup_s;          /* host time creating and initialising admitted systems */
+  double budget_use_sum;   /* sum over rounds of resident footprint / budget */
+  int64_t rounds;          /* memd_server_pump calls */
+  int64_t steps_rounds;    /* rounds that stepped the batch */
+  int64_t rebuilds;        /* batch rebuilds after membership changes */
+  int64_t admitted;
+  int64_t link_updates;    /* 3 V per system per step, summed */
+  int64_t particle_steps;
+} memd_server_stats;
+
+memd_status memd_server_get_stats(const memd_server *s, memd_server_stats *out);
+const char *memd_server_last_error(const memd_server *s);
 
 /* ---------------------------------------------------------------------------
  * Field energy without any device allocation.  The paper has no counterpart:

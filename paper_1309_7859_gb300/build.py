@@ -28,6 +28,9 @@ SOURCES = {
     "memd_setup.cu": [],
     "memd_particles.cu": ["--fmad=false"],
     "memd_static.cu": [],
+    "memd_tma.cu": [],
+    "memd_batch.cu": [],
+    "memd_server.cu": [],
 }
 
 

@@ -14,57 +14,10 @@
 #include <vector>
 
 #include "memd.h"
+#include "memd_ctx.cuh"
 #include "memd_internal.cuh"
 
 using namespace memd;
-
-struct memd_ctx {
-  Mesh mesh;
-  double Vbox = 0, c = 0, dt = 0;
-  int prec = 0, self_mode = 1, dipole_corr = 1, relax_maxit = 200000, use_graphs = 1;
-  int time_kernels = 0;
-  double relax_tol = 1e-12;
-  unsigned long long seed = 0;
-  int device = 0;
-  cudaStream_t stream = nullptr;
-  bool own_stream = false;
-  memd_alloc_fn alloc = nullptr;
-  memd_free_fn free_fn = nullptr;
-  void* alloc_user = nullptr;
-  std::vector<std::pair<void*, size_t>> blocks;
-  std::string last_error;
-  // field arrays: D and B double-buffered for the fused update; cur is the
-  // buffer that holds the present state
-  void* Dbuf[2] = {nullptr, nullptr};
-  void* Bbuf[2] = {nullptr, nullptr};
-  int cur = 0;
-  void* ie = nullptr;
-  double* ie64 = nullptr;
-  long long* Lg = nullptr;
-  long long* Tb = nullptr;
-  DevState* ds = nullptr;
-  double* red = nullptr;  // reduction partials (4 x reduce_blocks) + 32 scalars
-  double G[8] = {0};
-  double Minv[9] = {0};
-  // particles
-  Particles P{};
-  bool initialised = false;
-  // step graphs, one per buffer parity
-  cudaGraphExec_t graph[2] = {nullptr, nullptr};
-  int graph_thermo = -1;
-  double graph_gamma = 0, graph_kT = 0;
-  cudaStream_t side = nullptr;
-  cudaEvent_t fork = nullptr, join = nullptr;
-  cudaEvent_t ev0 = nullptr, ev1 = nullptr;
-  bool timing_pending = false;
-  double field_ms = 0;
-  long long field_launches = 0;
-  int relax_iters_last = 0;
-  FusedCfg fcfg{8, 1};
-  bool sig_ready = false;
-  void* D() const { return Dbuf[cur]; }
-  void* B() const { return Bbuf[cur]; }
-};
 
 namespace {
 
@@ -100,7 +53,9 @@ memd_status fail(memd_ctx* c, memd_status s, const std::string& why) {
       return fail(c, MEMD_ERR_CUDA, std::string("kernel launch: ") + cudaGetErrorString(e_)); \
   } while (0)
 
-void* dalloc(memd_ctx* c, size_t bytes) {
+}  // namespace
+
+void* memd_dalloc(memd_ctx* c, size_t bytes) {
   if (bytes < 256) bytes = 256;
   void* p = nullptr;
   if (c->alloc) {
@@ -113,7 +68,7 @@ void* dalloc(memd_ctx* c, size_t bytes) {
   return p;
 }
 
-void dfree(memd_ctx* c, void* p) {
+void memd_dfree(memd_ctx* c, void* p) {
   if (!p) return;
   for (size_t i = 0; i < c->blocks.size(); ++i)
     if (c->blocks[i].first == p) {
@@ -126,9 +81,16 @@ void dfree(memd_ctx* c, void* p) {
     }
 }
 
-size_t esz(const memd_ctx* c) { return c->prec == MEMD_FP32 ? sizeof(float) : sizeof(double); }
+namespace {
 
-StepParams step_params(const memd_ctx* c, int thermo, double gamma, double kT) {
+void* dalloc(memd_ctx* c, size_t bytes) { return memd_dalloc(c, bytes); }
+void dfree(memd_ctx* c, void* p) { memd_dfree(c, p); }
+
+}  // namespace
+
+size_t memd_esz(const memd_ctx* c) { return c->prec == MEMD_FP32 ? sizeof(float) : sizeof(double); }
+
+StepParams memd_step_params(const memd_ctx* c, int thermo, double gamma, double kT) {
   StepParams sp{};
   sp.dt = c->dt;
   sp.coefB = c->dt / c->mesh.a;
@@ -146,7 +108,16 @@ StepParams step_params(const memd_ctx* c, int thermo, double gamma, double kT) {
   return sp;
 }
 
-memd_status check_err(memd_ctx* c) {
+namespace {
+
+size_t esz(const memd_ctx* c) { return memd_esz(c); }
+StepParams step_params(const memd_ctx* c, int thermo, double gamma, double kT) {
+  return memd_step_params(c, thermo, gamma, kT);
+}
+
+}  // namespace
+
+memd_status memd_check_err(memd_ctx* c) {
   unsigned int err = 0;
   CK(cudaMemcpyAsync(&err, &c->ds->err, sizeof(err), cudaMemcpyDeviceToHost, c->stream));
   CK(cudaStreamSynchronize(c->stream));
@@ -156,10 +127,15 @@ memd_status check_err(memd_ctx* c) {
     if (err & kErrCellJump) return fail(c, MEMD_ERR_CELL_JUMP, "a charge moved more than one cell");
     if (err & kErrGauss) return fail(c, MEMD_ERR_GAUSS, "Gauss scan did not close (system not neutral)");
     if (err & kErrNonFinite) return fail(c, MEMD_ERR_INVALID, "non-finite or out-of-range input");
+    if (err & kErrTimeout) return fail(c, MEMD_ERR_TIMEOUT, "a bounded wait in a kernel gave up");
     return fail(c, MEMD_ERR_OVERFLOW, "fixed-point overflow");
   }
   return MEMD_OK;
 }
+
+namespace {
+
+memd_status check_err(memd_ctx* c) { return memd_check_err(c); }
 
 // scalar slots in c->red after the partial arrays
 enum {
@@ -322,15 +298,12 @@ static memd_status relax(memd_ctx* c, double* D64, double tol, int maxit) {
     parity = 0;
     while (it < maxit) {
       const int old_slot = kS_RZ0 + parity, new_slot = kS_RZ0 + (parity ^ 1);
+      // four launches per iteration: transpose map, operator with p.w,
+      // update with r.z and max|r|, direction (see memd_field.cu)
       launch_curlT64(m, u, p, st);
-      launch_circ64(m, w, u, c->ie64, 1.0, st);
-      launch_dot(p, w, n, part, st);
-      launch_finish(part, 0, sc + kS_PW, st);
-      k_pcg_update<<<R, 256, 0, st>>>(n, D64, u, r, w, z, diag, sc, old_slot, part + R);
-      launch_finish(part + R, 1, sc + kS_RMAX, st);
-      launch_dot(r, z, n, part, st);
-      launch_finish(part, 0, sc + new_slot, st);
-      k_pcg_dir<<<nb(n), 256, 0, st>>>(n, p, z, sc, new_slot, old_slot, 0);
+      launch_cg_apply(m, w, u, c->ie64, p, part, st);
+      launch_cg_update(n, D64, u, r, w, z, diag, part, sc, old_slot, part + R, part + 2 * R, st);
+      launch_cg_direction(n, p, z, sc, part + R, part + 2 * R, new_slot, old_slot, st);
       parity ^= 1;
       ++it;
       if (it % 25 == 0 || it == maxit) {
@@ -354,6 +327,16 @@ static memd_status relax(memd_ctx* c, double* D64, double tol, int maxit) {
   return MEMD_OK;
 }
 
+// the fused field update of buffer parity par with the context's kernel choice
+static void launch_field(memd_ctx* c, int par, double cB, double cD, FusedCfg cfg) {
+  if (cfg.tma)
+    launch_fused_tma(c->mesh, c->prec, c->tma, par, c->Dbuf[par], c->Bbuf[par], c->ie,
+                     c->Dbuf[par ^ 1], c->Bbuf[par ^ 1], cB, cD, cfg, &c->ds->err, c->stream);
+  else
+    launch_fused_curl(c->mesh, c->prec, c->Dbuf[par], c->Bbuf[par], c->ie, c->Dbuf[par ^ 1],
+                      c->Bbuf[par ^ 1], cB, cD, cfg, c->stream);
+}
+
 // ------------------------------------------------------------------ autotuner
 // Picks the tile height and z-chunk of the fused field kernel for this mesh
 // by timing every candidate shape on the context's own buffers (median of 3
@@ -361,8 +344,11 @@ static memd_status relax(memd_ctx* c, double* D64, double tol, int maxit) {
 // precision for the life of the process.
 static memd_status autotune_fused(memd_ctx* c) {
   static std::mutex mu;
-  static std::map<std::tuple<int, int, int, int>, FusedCfg> cache;
-  const auto key = std::make_tuple(c->mesh.n[0], c->mesh.n[1], c->mesh.n[2], c->prec);
+  static std::map<std::tuple<int, int, int, int, int>, FusedCfg> cache;
+  c->tma_ok = c->field_kernel != MEMD_FIELD_LDG && tma_supported(c->mesh, c->prec) &&
+              tma_make_maps(c->mesh, c->prec, c->Dbuf, c->Bbuf, c->ie, &c->tma);
+  const auto key = std::make_tuple(c->mesh.n[0], c->mesh.n[1], c->mesh.n[2], c->prec,
+                                   c->field_kernel * 2 + (c->tma_ok ? 1 : 0));
   {
     std::lock_guard<std::mutex> g(mu);
     auto it = cache.find(key);
@@ -371,21 +357,44 @@ static memd_status autotune_fused(memd_ctx* c) {
       return MEMD_OK;
     }
   }
-  FusedCfg cand[32];
-  const int nc = fused_candidates(c->mesh, c->prec, cand, 32);
+  FusedCfg cand[64];
+  int nc = 0;
+  if (c->field_kernel != MEMD_FIELD_TMA || !c->tma_ok) nc = fused_candidates(c->mesh, c->prec, cand, 32);
+  if (c->tma_ok) {
+    FusedCfg t[32];
+    const int nt = fused_candidates(c->mesh, 1, t, 32);  // the TMA kernel has all three heights
+    for (int i = 0; i < nt && nc < 64; ++i) {
+      t[i].tma = 1;
+      cand[nc++] = t[i];
+    }
+  }
   cudaEvent_t e0, e1;
   CK(cudaEventCreate(&e0));
   CK(cudaEventCreate(&e1));
   float best = 1e30f;
   FusedCfg pick = fused_default(c->mesh);
+  bool tma_checked = false;
   for (int i = 0; i < nc; ++i) {
     float t[3];
-    launch_fused_curl(c->mesh, c->prec, c->Dbuf[0], c->Bbuf[0], c->ie, c->Dbuf[1], c->Bbuf[1],
-                      0.0, 0.0, cand[i], c->stream);
+    auto run = [&]() { launch_field(c, 0, 0.0, 0.0, cand[i]); };
+    if (cand[i].tma && !c->tma_ok) continue;
+    run();
+    if (cand[i].tma && !tma_checked) {
+      // the first TMA launch runs alone: if any of its bounded waits gave up,
+      // the TMA kernel is dropped for this context
+      tma_checked = true;
+      CK(cudaStreamSynchronize(c->stream));
+      unsigned int e = 0;
+      CK(cudaMemcpy(&e, &c->ds->err, sizeof(e), cudaMemcpyDeviceToHost));
+      if (e) {
+        CK(cudaMemset(&c->ds->err, 0, sizeof(unsigned int)));
+        c->tma_ok = false;
+        continue;
+      }
+    }
     for (int r = 0; r < 3; ++r) {
       CK(cudaEventRecord(e0, c->stream));
-      launch_fused_curl(c->mesh, c->prec, c->Dbuf[0], c->Bbuf[0], c->ie, c->Dbuf[1],
-                        c->Bbuf[1], 0.0, 0.0, cand[i], c->stream);
+      run();
       CK(cudaEventRecord(e1, c->stream));
       CK(cudaEventSynchronize(e1));
       CK(cudaEventElapsedTime(&t[r], e0, e1));
@@ -399,6 +408,10 @@ static memd_status autotune_fused(memd_ctx* c) {
   }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
+  {
+    const memd_status e = check_err(c);
+    if (e != MEMD_OK) return e;
+  }
   c->fcfg = pick;
   std::lock_guard<std::mutex> g(mu);
   cache[key] = pick;
@@ -508,6 +521,7 @@ memd_status memd_create(const int32_t mesh[3], const double box[3], const memd_e
   c->seed = o.seed;
   c->use_graphs = o.use_graphs;
   c->time_kernels = o.time_kernels;
+  c->field_kernel = o.field_kernel;
   c->alloc = o.alloc;
   c->free_fn = o.free;
   c->alloc_user = o.alloc_user;
@@ -744,6 +758,7 @@ memd_status memd_init_field(memd_ctx* c, int64_t n, const double* pos, const int
   dfree(c, scr);
   dfree(c, D64);
   if (s == MEMD_OK) c->initialised = true;
+  c->gen += 1;
   return s;
 }
 
@@ -759,8 +774,7 @@ static memd_status record_step(memd_ctx* c, const StepParams& sp, int par, bool 
   launch_kick_drift_deposit(m, sp, c->P, c->Tb, c->ds, c->side);
   CK(cudaEventRecord(c->join, c->side));
   if (timed) CK(cudaEventRecordWithFlags(c->ev0, st, cudaEventRecordExternal));
-  launch_fused_curl(m, c->prec, c->Dbuf[par], c->Bbuf[par], c->ie, c->Dbuf[par ^ 1],
-                    c->Bbuf[par ^ 1], sp.coefB, sp.coefD, c->fcfg, st);
+  launch_field(c, par, sp.coefB, sp.coefD, c->fcfg);
   if (timed) CK(cudaEventRecordWithFlags(c->ev1, st, cudaEventRecordExternal));
   CK(cudaStreamWaitEvent(st, c->join, 0));
   launch_apply(m, c->prec, c->P, c->Tb, c->Lg, c->Dbuf[par ^ 1], sp.scale, st);
@@ -1045,6 +1059,10 @@ memd_status memd_get_kernel_stats(memd_ctx* c, memd_kernel_stats* out) {
   const double e = (double)esz(c);
   out->field_bytes = 15.0 * e * (double)c->mesh.V;
   out->launches_per_step = c->P.n > 0 ? 4 : 2;
+  out->field_tma = c->fcfg.tma;
+  out->field_ty = c->fcfg.ty;
+  out->field_zchunk = c->fcfg.zchunk;
+  out->pad = 0;
   return MEMD_OK;
 }
 

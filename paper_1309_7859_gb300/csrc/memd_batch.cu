@@ -1,0 +1,321 @@
+// memd_batch.cu -- many independent MEMD systems stepped together.
+//
+// A batch holds a device table of replica descriptors (mesh, step
+// parameters, field and particle pointers) and two CTA->replica maps, one
+// for the field tiles and one for the particle quads.  Each time step is one
+// CUDA graph of four launches covering every member: the charge transfer of
+// the drift on a side stream beside the fused field update, then the
+// transfer application, then the force gather, which also closes each
+// replica's step.  Small systems that would each leave most SMs idle fill
+// the GPU together, and the per-step launch cost is paid once for all.
+#include <algorithm>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "memd.h"
+#include "memd_ctx.cuh"
+#include "memd_internal.cuh"
+
+using namespace memd;
+
+struct memd_batch {
+  std::vector<memd_ctx*> m;
+  std::vector<int> gen;    // member generations the tables were built for
+  std::vector<int> base;   // member parity when the batch parity was 0
+  int bpar = 0;            // batch parity
+  int prec = 0;
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  cudaStream_t side = nullptr;
+  cudaEvent_t fork = nullptr, join = nullptr, ev0 = nullptr, ev1 = nullptr;
+  RepDesc* d_desc = nullptr;
+  int* d_field_rep = nullptr;
+  int* d_part_rep = nullptr;
+  int n_field = 0, n_part = 0;
+  double field_bytes = 0.0;
+  cudaGraphExec_t graph[2] = {nullptr, nullptr};
+  int g_thermo = -1;
+  double g_gamma = 0.0, g_kT = 0.0;
+  bool timing_pending = false;
+  double field_ms = 0.0;
+  long long field_launches = 0;
+  std::string last_error;
+  // the batch's own tables come from member 0's allocator but are tracked
+  // here, so members may be destroyed after the batch without double frees
+  memd_alloc_fn alloc = nullptr;
+  memd_free_fn free_fn = nullptr;
+  void* alloc_user = nullptr;
+  std::vector<std::pair<void*, size_t>> blocks;
+};
+
+namespace {
+
+memd_status bfail(memd_batch* b, memd_status s, const std::string& why) {
+  if (b) b->last_error = why;
+  return s;
+}
+
+#define BCK(call)                                                                    \
+  do {                                                                               \
+    cudaError_t e_ = (call);                                                         \
+    if (e_ != cudaSuccess)                                                           \
+      return bfail(b, MEMD_ERR_CUDA, std::string(#call) + ": " + cudaGetErrorString(e_)); \
+  } while (0)
+
+void drop(memd_batch* b) {
+  for (int t = 0; t < 2; ++t)
+    if (b->graph[t]) {
+      cudaGraphExecDestroy(b->graph[t]);
+      b->graph[t] = nullptr;
+    }
+}
+
+void* balloc(memd_batch* b, size_t bytes) {
+  if (bytes < 256) bytes = 256;
+  void* p = nullptr;
+  if (b->alloc) {
+    p = b->alloc(b->alloc_user, bytes, (void*)b->stream);
+  } else if (cudaMalloc(&p, bytes) != cudaSuccess) {
+    cudaGetLastError();
+    p = nullptr;
+  }
+  if (p) b->blocks.emplace_back(p, bytes);
+  return p;
+}
+
+void free_tables(memd_batch* b) {
+  for (auto& blk : b->blocks) {
+    if (b->free_fn)
+      b->free_fn(b->alloc_user, blk.first, blk.second, (void*)b->stream);
+    else
+      cudaFree(blk.first);
+  }
+  b->blocks.clear();
+  b->d_desc = nullptr;
+  b->d_field_rep = b->d_part_rep = nullptr;
+}
+
+// (Re)build the descriptor table and the CTA maps from the members' state;
+// the batch parity restarts at 0 with each member's current buffer first.
+memd_status build_tables(memd_batch* b) {
+  drop(b);
+  free_tables(b);
+  const int R = (int)b->m.size();
+  std::vector<RepDesc> desc(R);
+  std::vector<int> frep, prep;
+  b->field_bytes = 0.0;
+  for (int r = 0; r < R; ++r) {
+    memd_ctx* c = b->m[r];
+    RepDesc& d = desc[r];
+    std::memset(&d, 0, sizeof(d));
+    d.m = c->mesh;
+    d.sp = memd_step_params(c, 0, 0.0, 0.0);
+    d.P = c->P;
+    for (int k = 0; k < 2; ++k) {
+      d.D[k] = c->Dbuf[(c->cur + k) & 1];
+      d.B[k] = c->Bbuf[(c->cur + k) & 1];
+    }
+    d.ie = c->ie;
+    d.ie64 = c->ie64;
+    d.Lg = c->Lg;
+    d.Tb = c->Tb;
+    d.ds = c->ds;
+    d.f_tx = (c->mesh.n[0] + 31) / 32;
+    d.f_ty = (c->mesh.n[1] + kBatchTY - 1) / kBatchTY;
+    d.f_zchunk = std::min(c->mesh.n[2], 8);
+    const int nzc = (c->mesh.n[2] + d.f_zchunk - 1) / d.f_zchunk;
+    d.f_first = (int)frep.size();
+    for (int t = 0; t < d.f_tx * d.f_ty * nzc; ++t) frep.push_back(r);
+    d.p_first = (int)prep.size();
+    d.p_ctas = (int)std::max<int64_t>(1, (4 * c->P.n + kBatchQuadThreads - 1) / kBatchQuadThreads);
+    for (int t = 0; t < d.p_ctas; ++t) prep.push_back(r);
+    b->base[r] = c->cur;
+    b->gen[r] = c->gen;
+    b->field_bytes += 15.0 * (double)memd_esz(c) * (double)c->mesh.V;
+  }
+  b->bpar = 0;
+  b->n_field = (int)frep.size();
+  b->n_part = (int)prep.size();
+  b->d_desc = (RepDesc*)balloc(b, sizeof(RepDesc) * R);
+  b->d_field_rep = (int*)balloc(b, sizeof(int) * std::max(1, b->n_field));
+  b->d_part_rep = (int*)balloc(b, sizeof(int) * std::max(1, b->n_part));
+  if (!b->d_desc || !b->d_field_rep || !b->d_part_rep)
+    return bfail(b, MEMD_ERR_OOM, "batch tables");
+  BCK(cudaMemcpyAsync(b->d_desc, desc.data(), sizeof(RepDesc) * R, cudaMemcpyHostToDevice,
+                      b->stream));
+  BCK(cudaMemcpyAsync(b->d_field_rep, frep.data(), sizeof(int) * b->n_field,
+                      cudaMemcpyHostToDevice, b->stream));
+  BCK(cudaMemcpyAsync(b->d_part_rep, prep.data(), sizeof(int) * b->n_part,
+                      cudaMemcpyHostToDevice, b->stream));
+  BCK(cudaStreamSynchronize(b->stream));
+  return MEMD_OK;
+}
+
+memd_status record(memd_batch* b, int par, int thermo, double gamma, double kT, bool timed) {
+  const cudaStream_t st = b->stream;
+  BCK(cudaEventRecord(b->fork, st));
+  BCK(cudaStreamWaitEvent(b->side, b->fork, 0));
+  launch_deposit_batch(b->d_desc, b->d_part_rep, b->n_part, thermo, gamma, kT, b->side);
+  BCK(cudaEventRecord(b->join, b->side));
+  if (timed) BCK(cudaEventRecordWithFlags(b->ev0, st, cudaEventRecordExternal));
+  launch_fused_batch(b->prec, b->d_desc, b->d_field_rep, b->n_field, par, st);
+  if (timed) BCK(cudaEventRecordWithFlags(b->ev1, st, cudaEventRecordExternal));
+  BCK(cudaStreamWaitEvent(st, b->join, 0));
+  launch_apply_batch(b->prec, b->d_desc, b->d_part_rep, b->n_part, par, st);
+  launch_gather_batch(b->prec, b->d_desc, b->d_part_rep, b->n_part, par, thermo, gamma, kT, st);
+  BCK(cudaGetLastError());
+  return MEMD_OK;
+}
+
+void harvest(memd_batch* b) {
+  if (!b->timing_pending) return;
+  float ms = 0;
+  if (cudaEventSynchronize(b->ev1) == cudaSuccess &&
+      cudaEventElapsedTime(&ms, b->ev0, b->ev1) == cudaSuccess) {
+    b->field_ms += ms;
+    b->field_launches += 1;
+  }
+  cudaGetLastError();
+  b->timing_pending = false;
+}
+
+}  // namespace
+
+extern "C" {
+
+void memd_batch_destroy(memd_batch* b) {
+  if (!b) return;
+  cudaSetDevice(b->device);
+  if (b->stream) cudaStreamSynchronize(b->stream);
+  drop(b);
+  free_tables(b);
+  if (b->fork) cudaEventDestroy(b->fork);
+  if (b->join) cudaEventDestroy(b->join);
+  if (b->ev0) cudaEventDestroy(b->ev0);
+  if (b->ev1) cudaEventDestroy(b->ev1);
+  if (b->side) cudaStreamDestroy(b->side);
+  delete b;
+}
+
+memd_status memd_batch_create(int32_t count, memd_ctx* const* members, memd_batch** out) {
+  if (!out) return MEMD_ERR_INVALID;
+  *out = nullptr;
+  if (count < 1 || !members) return MEMD_ERR_INVALID;
+  memd_batch* b = new memd_batch();
+  for (int r = 0; r < count; ++r) {
+    memd_ctx* c = members[r];
+    if (!c || !c->initialised || c->device != members[0]->device ||
+        c->prec != members[0]->prec || c->stream != members[0]->stream) {
+      delete b;
+      return MEMD_ERR_INVALID;
+    }
+    b->m.push_back(c);
+  }
+  b->gen.assign(count, -1);
+  b->base.assign(count, 0);
+  b->prec = members[0]->prec;
+  b->device = members[0]->device;
+  b->stream = members[0]->stream;
+  b->alloc = members[0]->alloc;
+  b->free_fn = members[0]->free_fn;
+  b->alloc_user = members[0]->alloc_user;
+  memd_status s = MEMD_OK;
+  if (cudaSetDevice(b->device) != cudaSuccess ||
+      cudaStreamCreateWithFlags(&b->side, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&b->join, cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreate(&b->ev0) != cudaSuccess || cudaEventCreate(&b->ev1) != cudaSuccess) {
+    s = MEMD_ERR_CUDA;
+  } else {
+    // members' own queued work comes first
+    for (memd_ctx* c : b->m) cudaStreamSynchronize(c->stream);
+    s = build_tables(b);
+  }
+  if (s != MEMD_OK) {
+    memd_batch_destroy(b);
+    return s;
+  }
+  *out = b;
+  return MEMD_OK;
+}
+
+memd_status memd_batch_step(memd_batch* b, int64_t nsteps, const memd_thermostat* th) {
+  if (!b) return MEMD_ERR_INVALID;
+  if (nsteps < 0) return bfail(b, MEMD_ERR_INVALID, "negative step count");
+  BCK(cudaSetDevice(b->device));
+  // members re-initialised or stepped on their own since the tables were built
+  bool stale = false;
+  for (size_t r = 0; r < b->m.size(); ++r) {
+    memd_ctx* c = b->m[r];
+    if (!c->initialised) return bfail(b, MEMD_ERR_STATE, "a member is not initialised");
+    if (c->gen != b->gen[r] || c->cur != ((b->base[r] + b->bpar) & 1)) stale = true;
+  }
+  if (stale) {
+    memd_status s = build_tables(b);
+    if (s != MEMD_OK) return s;
+  }
+  const int thermo = th ? 1 : 0;
+  const double gamma = th ? th->gamma : 0.0, kT = th ? th->kT : 0.0;
+  if (b->g_thermo != thermo || b->g_gamma != gamma || b->g_kT != kT) {
+    drop(b);
+    // per-particle Langevin amplitudes of every member for this thermostat
+    for (memd_ctx* c : b->m) {
+      launch_particle_constants(memd_step_params(c, thermo, gamma, kT), c->P, b->stream);
+      c->sig_ready = false;  // a member stepped alone recomputes its own
+    }
+    b->g_thermo = thermo;
+    b->g_gamma = gamma;
+    b->g_kT = kT;
+  }
+  const bool timed = b->m[0]->time_kernels != 0;
+  for (int64_t s = 0; s < nsteps; ++s) {
+    const int par = b->bpar;
+    harvest(b);
+    if (!b->graph[par]) {
+      cudaGraph_t g;
+      BCK(cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal));
+      memd_status r = record(b, par, thermo, gamma, kT, timed);
+      cudaError_t e = cudaStreamEndCapture(b->stream, &g);
+      if (r != MEMD_OK) return r;
+      if (e != cudaSuccess) return bfail(b, MEMD_ERR_CUDA, "graph capture");
+      BCK(cudaGraphInstantiate(&b->graph[par], g, 0));
+      cudaGraphDestroy(g);
+    }
+    BCK(cudaGraphLaunch(b->graph[par], b->stream));
+    b->timing_pending = timed;
+    b->bpar ^= 1;
+  }
+  for (size_t r = 0; r < b->m.size(); ++r) b->m[r]->cur = (b->base[r] + b->bpar) & 1;
+  return MEMD_OK;
+}
+
+memd_status memd_batch_synchronize(memd_batch* b) {
+  if (!b) return MEMD_ERR_INVALID;
+  BCK(cudaSetDevice(b->device));
+  harvest(b);
+  BCK(cudaStreamSynchronize(b->stream));
+  for (memd_ctx* c : b->m) {
+    const memd_status s = memd_check_err(c);
+    if (s != MEMD_OK) return bfail(b, s, c->last_error);
+  }
+  return MEMD_OK;
+}
+
+memd_status memd_batch_kernel_stats(memd_batch* b, memd_kernel_stats* out) {
+  if (!b || !out) return MEMD_ERR_INVALID;
+  harvest(b);
+  std::memset(out, 0, sizeof(*out));
+  out->field_ms = b->field_ms;
+  out->field_launches = b->field_launches;
+  out->field_bytes = b->field_bytes;
+  out->launches_per_step = 4;
+  out->field_tma = 0;
+  out->field_ty = kBatchTY;
+  out->field_zchunk = 8;
+  b->field_ms = 0.0;
+  b->field_launches = 0;
+  return MEMD_OK;
+}
+
+}  // extern "C"

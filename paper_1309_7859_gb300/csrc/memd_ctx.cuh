@@ -1,0 +1,76 @@
+// memd_ctx.cuh -- the context behind the opaque memd_ctx handle, shared by
+// the single-system API (memd_api.cu) and the batched replicas
+// (memd_batch.cu).  Host-side only.
+#pragma once
+
+#include <string>
+#include <utility>
+#include <vector>
+
+#include "memd.h"
+#include "memd_internal.cuh"
+
+struct memd_ctx {
+  using FusedCfg = memd::FusedCfg;
+  using TmaMaps = memd::TmaMaps;
+  using Mesh = memd::Mesh;
+  using DevState = memd::DevState;
+  using Particles = memd::Particles;
+  Mesh mesh;
+  double Vbox = 0, c = 0, dt = 0;
+  int prec = 0, self_mode = 1, dipole_corr = 1, relax_maxit = 200000, use_graphs = 1;
+  int time_kernels = 0;
+  double relax_tol = 1e-12;
+  unsigned long long seed = 0;
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  memd_alloc_fn alloc = nullptr;
+  memd_free_fn free_fn = nullptr;
+  void* alloc_user = nullptr;
+  std::vector<std::pair<void*, size_t>> blocks;
+  std::string last_error;
+  // field arrays: D and B double-buffered for the fused update; cur is the
+  // buffer that holds the present state
+  void* Dbuf[2] = {nullptr, nullptr};
+  void* Bbuf[2] = {nullptr, nullptr};
+  int cur = 0;
+  void* ie = nullptr;
+  double* ie64 = nullptr;
+  long long* Lg = nullptr;
+  long long* Tb = nullptr;
+  DevState* ds = nullptr;
+  double* red = nullptr;  // reduction partials (4 x reduce_blocks) + 32 scalars
+  double G[8] = {0};
+  double Minv[9] = {0};
+  // particles
+  Particles P{};
+  bool initialised = false;
+  // step graphs, one per buffer parity
+  cudaGraphExec_t graph[2] = {nullptr, nullptr};
+  int graph_thermo = -1;
+  double graph_gamma = 0, graph_kT = 0;
+  cudaStream_t side = nullptr;
+  cudaEvent_t fork = nullptr, join = nullptr;
+  cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+  bool timing_pending = false;
+  double field_ms = 0;
+  long long field_launches = 0;
+  int relax_iters_last = 0;
+  int gen = 0;  // bumped by every memd_init_field (batches rebuild their tables)
+  FusedCfg fcfg{8, 1, 0};
+  int field_kernel = 0;
+  TmaMaps tma{};
+  bool tma_ok = false;
+  bool sig_ready = false;
+  void* D() const { return Dbuf[cur]; }
+  void* B() const { return Bbuf[cur]; }
+};
+
+
+// helpers of memd_api.cu used by memd_batch.cu
+void* memd_dalloc(memd_ctx* c, size_t bytes);
+void memd_dfree(memd_ctx* c, void* p);
+size_t memd_esz(const memd_ctx* c);
+memd::StepParams memd_step_params(const memd_ctx* c, int thermo, double gamma, double kT);
+memd_status memd_check_err(memd_ctx* c);

@@ -151,10 +151,10 @@ __global__ void __launch_bounds__(kBX* kBY)
 // CTAs read the halo of the input.  DRAM traffic per site: D, 1/eps, B read
 // once, D', B' written once (60 B in FP32, 120 B in FP64).
 template <typename T, int TX, int TY>
-__global__ void __launch_bounds__(TX* TY)
-    k_fused_curl(Mesh m, const T* __restrict__ Din, const T* __restrict__ Bin,
-                 const T* __restrict__ ie, T* __restrict__ Dout, T* __restrict__ Bout, T cB,
-                 T cD, int zchunk) {
+__device__ __forceinline__ void fused_tile(const Mesh& m, const T* __restrict__ Din,
+                                           const T* __restrict__ Bin, const T* __restrict__ ie,
+                                           T* __restrict__ Dout, T* __restrict__ Bout, T cB, T cD,
+                                           int tile_x, int tile_y, int tile_z, int zchunk) {
   constexpr int EX = TX + 2, EY = TY + 2, BX = TX + 1, BY = TY + 1;
   constexpr int NT = TX * TY;
   constexpr int NE = (EX * EY + NT - 1) / NT;  // E-region elements per thread
@@ -164,8 +164,8 @@ __global__ void __launch_bounds__(TX* TY)
   const int nx = m.n[0], ny = m.n[1], nz = m.n[2];
   const int64_t V = m.V;
   const int64_t P = (int64_t)nx * ny;
-  const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY;
-  const int z0 = blockIdx.z * zchunk;
+  const int x0 = tile_x * TX, y0 = tile_y * TY;
+  const int z0 = tile_z * zchunk;
   const int z1 = min(z0 + zchunk, nz);
   const int tid = threadIdx.y * TX + threadIdx.x;
 
@@ -321,6 +321,31 @@ __global__ void __launch_bounds__(TX* TY)
   }
 }
 
+template <typename T, int TX, int TY>
+__global__ void __launch_bounds__(TX* TY)
+    k_fused_curl(Mesh m, const T* __restrict__ Din, const T* __restrict__ Bin,
+                 const T* __restrict__ ie, T* __restrict__ Dout, T* __restrict__ Bout, T cB,
+                 T cD, int zchunk) {
+  fused_tile<T, TX, TY>(m, Din, Bin, ie, Dout, Bout, cB, cD, blockIdx.x, blockIdx.y, blockIdx.z,
+                        zchunk);
+}
+
+// Many independent systems in one launch: CTA b works on a tile of replica
+// cta_rep[b]; each replica's tiles are a contiguous range of CTAs.
+template <typename T, int TX, int TY>
+__global__ void __launch_bounds__(TX* TY)
+    k_fused_curl_batch(const RepDesc* __restrict__ desc, const int* __restrict__ cta_rep,
+                       int par) {
+  const RepDesc& r = desc[cta_rep[blockIdx.x]];
+  const int local = blockIdx.x - r.f_first;
+  const int per_z = r.f_tx * r.f_ty;
+  const int tz = local / per_z, rem = local - tz * per_z;
+  const int ty = rem / r.f_tx, tx = rem - ty * r.f_tx;
+  fused_tile<T, TX, TY>(r.m, (const T*)r.D[par], (const T*)r.B[par], (const T*)r.ie,
+                        (T*)r.D[par ^ 1], (T*)r.B[par ^ 1], (T)r.sp.coefB, (T)r.sp.coefD, tx,
+                        ty, tz, r.f_zchunk);
+}
+
 __device__ inline double block_sum(double x, double* sh) {
   for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xffffffffu, x, o);
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
@@ -420,6 +445,125 @@ __global__ void __launch_bounds__(kRedThreads)
   if (bad) atomicAdd(mismatch, bad);
 }
 
+// ---------------------------------------------------------- fused PCG
+// Three of the four kernels of one preconditioned-CG iteration on plaquette
+// rotations (the fourth is the transpose map k_curlT64).  Every CTA reduces
+// the per-CTA partial sums of the previous kernel itself, in the same order,
+// so the scalars alpha and beta are identical everywhere without a separate
+// reduction launch.  Slots of the scalar array sc follow the host code.
+constexpr int kCgDone = 14, kCgTol = 15, kCgEmax = 4;
+
+// all threads of the CTA get op(part[0..n)) (op 0: sum, 1: max), fixed order
+__device__ inline double cta_reduce(const double* __restrict__ part, int n, int op, double* sh) {
+  double x = 0.0;
+  for (int t = threadIdx.x; t < n; t += blockDim.x) x = op ? fmax(x, part[t]) : x + part[t];
+  for (int o = 16; o > 0; o >>= 1) {
+    const double y = __shfl_down_sync(0xffffffffu, x, o);
+    x = op ? fmax(x, y) : x + y;
+  }
+  if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = x;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double r = 0.0;
+    for (int t = 0; t < (int)(blockDim.x >> 5); ++t) r = op ? fmax(r, sh[t]) : r + sh[t];
+    sh[32] = r;
+  }
+  __syncthreads();
+  const double r = sh[32];
+  __syncthreads();
+  return r;
+}
+
+// w = circulation of (ie u) on every plaquette, and this CTA's share of p.w
+__global__ void __launch_bounds__(kRedThreads)
+    k_cg_apply(Mesh m, double* __restrict__ w, const double* __restrict__ u,
+               const double* __restrict__ ie, const double* __restrict__ p,
+               double* __restrict__ part) {
+  __shared__ double sh[kRedThreads / 32];
+  const int64_t V = m.V;
+  double acc = 0.0;
+  for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < V;
+       v += (int64_t)gridDim.x * blockDim.x) {
+    int i, j, k;
+    coords(m, v, i, j, k);
+    const int ip = (i + 1 == m.n[0]) ? 0 : i + 1;
+    const int jp = (j + 1 == m.n[1]) ? 0 : j + 1;
+    const int kp = (k + 1 == m.n[2]) ? 0 : k + 1;
+    const int64_t vx = vindex(m, ip, j, k), vy = vindex(m, i, jp, k), vz = vindex(m, i, j, kp);
+    const double Ex = u[v] * ie[v], Ey = u[V + v] * ie[V + v], Ez = u[2 * V + v] * ie[2 * V + v];
+    const double Ey_x = u[V + vx] * ie[V + vx], Ez_x = u[2 * V + vx] * ie[2 * V + vx];
+    const double Ex_y = u[vy] * ie[vy], Ez_y = u[2 * V + vy] * ie[2 * V + vy];
+    const double Ex_z = u[vz] * ie[vz], Ey_z = u[V + vz] * ie[V + vz];
+    const double wx = ((Ey + Ez_y) - Ey_z) - Ez;
+    const double wy = ((Ez + Ex_z) - Ez_x) - Ex;
+    const double wz = ((Ex + Ey_x) - Ex_y) - Ey;
+    w[v] = wx;
+    w[V + v] = wy;
+    w[2 * V + v] = wz;
+    acc += p[v] * wx + p[V + v] * wy + p[2 * V + v] * wz;
+  }
+  const double s = block_sum(acc, sh);
+  if (threadIdx.x == 0) part[blockIdx.x] = s;
+}
+
+// alpha = rz / p.w; D += alpha u; r -= alpha w; z = r / diag; shares of r.z
+// and of max |r|.  Frozen (kCgDone) iterations change nothing.
+__global__ void __launch_bounds__(kRedThreads)
+    k_cg_update(int64_t n, double* __restrict__ D, const double* __restrict__ u,
+                double* __restrict__ r, const double* __restrict__ w, double* __restrict__ z,
+                const double* __restrict__ diag, const double* __restrict__ part_pw,
+                const double* __restrict__ sc, int rz_slot, double* __restrict__ part_rz,
+                double* __restrict__ part_rmax) {
+  __shared__ double sh[33];
+  const double pw = cta_reduce(part_pw, gridDim.x, 0, sh);
+  const bool done = sc[kCgDone] != 0.0;
+  const double alpha = (!done && pw > 0.0) ? sc[rz_slot] / pw : 0.0;
+  double rz = 0.0, mx = 0.0;
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < n;
+       t += (int64_t)gridDim.x * blockDim.x) {
+    double rn = r[t];
+    double zn;
+    if (!done) {
+      D[t] += alpha * u[t];
+      rn = rn - alpha * w[t];
+      r[t] = rn;
+      zn = rn / diag[t];
+      z[t] = zn;
+    } else {
+      zn = z[t];
+    }
+    rz += rn * zn;
+    mx = fmax(mx, fabs(rn));
+  }
+  const double s1 = block_sum(rz, sh);
+  const double s2 = block_max(mx, sh);
+  if (threadIdx.x == 0) {
+    part_rz[blockIdx.x] = s1;
+    part_rmax[blockIdx.x] = s2;
+  }
+}
+
+// rz_new = r.z, freeze when max|r| <= tol max|E|, else p = z + (rz_new/rz_old) p
+__global__ void __launch_bounds__(kRedThreads)
+    k_cg_direction(int64_t n, double* __restrict__ p, const double* __restrict__ z,
+                   double* __restrict__ sc, const double* __restrict__ part_rz,
+                   const double* __restrict__ part_rmax, int nparts, int rz_new, int rz_old) {
+  __shared__ double sh[33];
+  const double rzn = cta_reduce(part_rz, nparts, 0, sh);
+  const double rmax = cta_reduce(part_rmax, nparts, 1, sh);
+  if (sc[kCgDone] != 0.0) return;
+  if (rmax <= sc[kCgTol] * sc[kCgEmax]) {
+    if (blockIdx.x == 0 && threadIdx.x == 0) sc[kCgDone] = 1.0;
+    return;
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) sc[rz_new] = rzn;
+  const double ro = sc[rz_old];
+  const double beta = (ro != 0.0) ? rzn / ro : 0.0;
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < n;
+       t += (int64_t)gridDim.x * blockDim.x)
+    p[t] = z[t] + beta * p[t];
+}
+
 }  // namespace
 
 void launch_curl_B(const Mesh& m, int prec, void* B, const void* D, const void* ie,
@@ -476,7 +620,7 @@ void launch_fused_curl(const Mesh& m, int prec, const void* Din, const void* Bin
 FusedCfg fused_default(const Mesh& m) {
   // enough CTAs to fill the GPU a few times over, but chunks long enough
   // that the recomputed prologue plane stays a small overhead
-  FusedCfg c{8, 1};
+  FusedCfg c{8, 1, 0};
   const int64_t tiles = (int64_t)((m.n[0] + 31) / 32) * ((m.n[1] + 7) / 8);
   const int64_t target = 4 * 152;
   const int64_t nchunks = (target + tiles - 1) / tiles;
@@ -487,6 +631,17 @@ FusedCfg fused_default(const Mesh& m) {
   return c;
 }
 
+void launch_fused_batch(int prec, const RepDesc* desc, const int* cta_rep, int nctas, int par,
+                        cudaStream_t st) {
+  if (nctas <= 0) return;
+  if (prec == 1)
+    k_fused_curl_batch<float, 32, kBatchTY><<<nctas, dim3(32, kBatchTY, 1), 0, st>>>(desc, cta_rep,
+                                                                                  par);
+  else
+    k_fused_curl_batch<double, 32, kBatchTY><<<nctas, dim3(32, kBatchTY, 1), 0, st>>>(desc,
+                                                                                   cta_rep, par);
+}
+
 int fused_candidates(const Mesh& m, int prec, FusedCfg* out, int cap) {
   static const int tys[3] = {4, 8, 16};
   static const int zcs[8] = {1, 2, 4, 8, 16, 32, 64, 128};
@@ -494,9 +649,27 @@ int fused_candidates(const Mesh& m, int prec, FusedCfg* out, int cap) {
   for (int a = 0; a < (prec == 1 ? 3 : 2); ++a)
     for (int b = 0; b < 8; ++b) {
       if (zcs[b] > m.n[2] && b > 0 && zcs[b - 1] >= m.n[2]) continue;
-      if (n < cap) out[n++] = FusedCfg{tys[a], zcs[b] < m.n[2] ? zcs[b] : m.n[2]};
+      if (n < cap) out[n++] = FusedCfg{tys[a], zcs[b] < m.n[2] ? zcs[b] : m.n[2], 0};
     }
   return n;
+}
+
+void launch_cg_apply(const Mesh& m, double* w, const double* u, const double* ie,
+                     const double* p, double* part, cudaStream_t st) {
+  k_cg_apply<<<kRedBlocks, kRedThreads, 0, st>>>(m, w, u, ie, p, part);
+}
+
+void launch_cg_update(int64_t n, double* D, const double* u, double* r, const double* w,
+                      double* z, const double* diag, const double* part_pw, const double* sc,
+                      int rz_slot, double* part_rz, double* part_rmax, cudaStream_t st) {
+  k_cg_update<<<kRedBlocks, kRedThreads, 0, st>>>(n, D, u, r, w, z, diag, part_pw, sc, rz_slot,
+                                                  part_rz, part_rmax);
+}
+
+void launch_cg_direction(int64_t n, double* p, const double* z, double* sc, const double* part_rz,
+                         const double* part_rmax, int rz_new, int rz_old, cudaStream_t st) {
+  k_cg_direction<<<kRedBlocks, kRedThreads, 0, st>>>(n, p, z, sc, part_rz, part_rmax, kRedBlocks,
+                                                     rz_new, rz_old);
 }
 
 void launch_circ64(const Mesh& m, double* w, const double* u, const double* ie, double sign,

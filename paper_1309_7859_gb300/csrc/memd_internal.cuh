@@ -7,6 +7,7 @@
 // e 2^-48.
 #pragma once
 
+#include <cuda.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -30,6 +31,7 @@ enum : unsigned int {
   kErrGauss = 2u,
   kErrOverflow = 4u,
   kErrNonFinite = 8u,
+  kErrTimeout = 16u,
 };
 
 // Small device-resident state shared by the step kernels.
@@ -63,6 +65,7 @@ void launch_curl_D(const Mesh& m, int prec, void* D, const void* B, double coef,
 struct FusedCfg {
   int ty;
   int zchunk;
+  int tma;  // 1: TMA-staged kernel (memd_tma.cu)
 };
 void launch_fused_curl(const Mesh& m, int prec, const void* Din, const void* Bin, const void* ie,
                        void* Dout, void* Bout, double cB, double cD, FusedCfg cfg,
@@ -70,11 +73,35 @@ void launch_fused_curl(const Mesh& m, int prec, const void* Din, const void* Bin
 FusedCfg fused_default(const Mesh& m);
 // candidate shapes for the autotuner; returns how many were written
 int fused_candidates(const Mesh& m, int prec, FusedCfg* out, int cap);
+// TMA-staged fused update (memd_tma.cu): usable when x rows are 16-byte
+// multiples; one 4-D tensor map per array, buffer parity and tile height
+struct TmaMaps {
+  CUtensorMap D[2][3], B[2][3], ie[3];
+  static int index(int ty) { return ty == 4 ? 0 : (ty == 16 ? 2 : 1); }
+  static int ty(int t) { return t == 0 ? 4 : (t == 2 ? 16 : 8); }
+};
+bool tma_supported(const Mesh& m, int prec);
+bool tma_make_maps(const Mesh& m, int prec, void* const D[2], void* const B[2], void* ie,
+                   TmaMaps* out);
+void launch_fused_tma(const Mesh& m, int prec, const TmaMaps& maps, int par, const void* Din,
+                      const void* Bin, const void* ie, void* Dout, void* Bout, double cB,
+                      double cD, FusedCfg cfg, unsigned int* err, cudaStream_t st);
 // FP64 helpers of the relaxation: w = sign * circulation(ie * u) per plaquette
 void launch_circ64(const Mesh& m, double* w, const double* u, const double* ie,
                    double sign, cudaStream_t st);
 // u = transpose of the circulation map applied to a plaquette field p
 void launch_curlT64(const Mesh& m, double* u, const double* p, cudaStream_t st);
+// fused PCG iteration (memd_field.cu): w = circ(ie u) with CTA shares of p.w;
+// the update with shares of r.z and max|r|; the new direction.  Scalar slots
+// of sc: 14 frozen flag, 15 tolerance, 4 max|E|; part_* hold reduce_blocks()
+// CTA shares each.
+void launch_cg_apply(const Mesh& m, double* w, const double* u, const double* ie,
+                     const double* p, double* part, cudaStream_t st);
+void launch_cg_update(int64_t n, double* D, const double* u, double* r, const double* w,
+                      double* z, const double* diag, const double* part_pw, const double* sc,
+                      int rz_slot, double* part_rz, double* part_rmax, cudaStream_t st);
+void launch_cg_direction(int64_t n, double* p, const double* z, double* sc, const double* part_rz,
+                         const double* part_rmax, int rz_new, int rz_old, cudaStream_t st);
 // diag_p = sum of ie over the 4 links of each plaquette
 void launch_plaquette_diag(const Mesh& m, double* diag, const double* ie, cudaStream_t st);
 
@@ -159,6 +186,35 @@ void launch_gather(const Mesh& m, int prec, const StepParams& sp, Particles p, c
                    const void* ie, const double* ie64, DevState* ds, int kick, int finish,
                    cudaStream_t st);
 void launch_step_end(DevState* ds, int advance, cudaStream_t st);
+
+// ------------------------------------------------------- batched replicas
+// One independent system of a batch, as the batched kernels see it.
+struct RepDesc {
+  Mesh m;
+  StepParams sp;
+  Particles P;
+  void* D[2];
+  void* B[2];
+  void* ie;
+  double* ie64;
+  long long* Lg;
+  long long* Tb;
+  DevState* ds;
+  int f_first, f_tx, f_ty, f_zchunk;  // field tiles: first CTA, tiles along x, y; planes per CTA
+  int p_first, p_ctas;                // particle CTAs of the quad kernels
+};
+constexpr int kBatchTY = 8;            // tile height of the batched field kernel
+constexpr int kBatchQuadThreads = 128;  // 32 particles per CTA in the batched quad kernels
+// field update of every replica (memd_field.cu)
+void launch_fused_batch(int prec, const RepDesc* desc, const int* cta_rep, int nctas, int par,
+                        cudaStream_t st);
+// particle kernels of every replica (memd_particles.cu); thermostat from the arguments
+void launch_deposit_batch(const RepDesc* desc, const int* cta_rep, int nctas, int thermo,
+                          double gamma, double kT, cudaStream_t st);
+void launch_apply_batch(int prec, const RepDesc* desc, const int* cta_rep, int nctas, int par,
+                        cudaStream_t st);
+void launch_gather_batch(int prec, const RepDesc* desc, const int* cta_rep, int nctas, int par,
+                         int thermo, double gamma, double kT, cudaStream_t st);
 // per-particle constants: h = (dt/2)/m always; sig when thermo is set
 void launch_particle_constants(const StepParams& sp, Particles p, cudaStream_t st);
 // energy pieces into partial sums (memd_particles.cu)

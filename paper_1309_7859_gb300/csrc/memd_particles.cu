@@ -23,13 +23,21 @@ namespace memd {
 namespace {
 
 constexpr int kThreads = 128;
-constexpr int kQuadThreads = 128;  // 32 particles per CTA in the quad kernels
+constexpr int kQuadThreads = 128;  // at most 32 particles per CTA in the quad kernels
 constexpr int kRedThreads = 256;
 constexpr int kRedBlocks = 2 * 152;
 
 inline unsigned blocks_for(int64_t n, int t = kThreads) {
   int64_t b = (n + t - 1) / t;
   return (unsigned)(b < 1 ? 1 : b);
+}
+
+// CTA size of the quad kernels: small systems use small CTAs so that their
+// FP64-heavy lanes spread over all 152 SMs instead of a few
+inline int quad_threads(int64_t n) {
+  const int64_t want = (4 * n + 2 * 152 - 1) / (2 * 152);
+  int t = (int)((want + 31) / 32 * 32);
+  return t < 32 ? 32 : (t > kQuadThreads ? kQuadThreads : t);
 }
 
 // ------------------------------------------------------------ fixed point
@@ -180,7 +188,7 @@ __device__ inline void quad_move(const Mesh& m, Particles P, int64_t p, int d, b
     ok = true;
   }
   // all three axes must be valid for the particle to move
-  const bool all_ok = __all_sync(0xfu << base, ok) != 0;
+  const bool all_ok = ((__ballot_sync(full, ok) >> base) & 0xfu) == 0xfu;
   int C0[3], F0[3], C1[3], F1[3];
 #pragma unroll
   for (int e = 0; e < 3; ++e) {
@@ -277,11 +285,11 @@ __global__ void k_particle_constants(StepParams sp, Particles P) {
   if (sp.thermo) P.sig[p] = sqrt(2.0 * sp.gamma * mass * sp.kT / sp.dt);
 }
 
-// half kick with the stored force, drift, charge transfer, dipole sum
-__global__ void __launch_bounds__(kQuadThreads)
-    k_kick_drift_deposit(Mesh m, StepParams sp, Particles P, unsigned long long* __restrict__ Tb,
-                         DevState* ds) {
-  const int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+// half kick with the stored force, drift, charge transfer, dipole sum;
+// g is the thread's index within its system
+__device__ __forceinline__ void deposit_body(const Mesh& m, const StepParams& sp, Particles P,
+                                             unsigned long long* __restrict__ Tb, DevState* ds,
+                                             int64_t g) {
   const int64_t p = g >> 2;
   const int d = (int)(g & 3);
   const bool active = p < P.n;
@@ -304,6 +312,12 @@ __global__ void __launch_bounds__(kQuadThreads)
     }
   }
   quad_move(m, P, p, d, active, x, ko, xn, kn, ok, Tb, ds);
+}
+
+__global__ void __launch_bounds__(kQuadThreads)
+    k_kick_drift_deposit(Mesh m, StepParams sp, Particles P, unsigned long long* __restrict__ Tb,
+                         DevState* ds) {
+  deposit_body(m, sp, P, Tb, ds, blockIdx.x * (int64_t)blockDim.x + threadIdx.x);
 }
 
 // prescribed move to (pos_new, img_new) with its charge transfer
@@ -336,10 +350,10 @@ __global__ void __launch_bounds__(kQuadThreads)
 // Quad lane c handles corner (c & 1, c >> 1) of every axis and both cells of
 // a crossed face; its exchanges are issued together.
 template <typename T>
-__global__ void __launch_bounds__(kQuadThreads)
-    k_apply(Mesh m, Particles P, unsigned long long* __restrict__ Tb, long long* __restrict__ Lg,
-            T* __restrict__ D, double scale) {
-  const int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+__device__ __forceinline__ void apply_body(const Mesh& m, Particles P,
+                                           unsigned long long* __restrict__ Tb,
+                                           long long* __restrict__ Lg, T* __restrict__ D,
+                                           double scale, int64_t g) {
   const int64_t p = g >> 2;
   if (p >= P.n) return;
   const int corner = (int)(g & 3);
@@ -376,6 +390,13 @@ __global__ void __launch_bounds__(kQuadThreads)
       Lg[l[s]] += t[s];
       D[l[s]] = D[l[s]] + (T)((double)t[s] * scale);
     }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kQuadThreads)
+    k_apply(Mesh m, Particles P, unsigned long long* __restrict__ Tb, long long* __restrict__ Lg,
+            T* __restrict__ D, double scale) {
+  apply_body<T>(m, P, Tb, Lg, D, scale, blockIdx.x * (int64_t)blockDim.x + threadIdx.x);
 }
 
 // ------------------------------------------------------------- self energy
@@ -438,12 +459,12 @@ __device__ inline void self_ie(const Mesh& m, const double* __restrict__ ie64, c
 // the last CTA of the gather closes the update: P of this state becomes the
 // reported one, the accumulator is cleared for the next move, and the step
 // counter advances (finish == 2)
-__device__ inline void finish_update(DevState* ds, int finish) {
+__device__ inline void finish_update(DevState* ds, int finish, unsigned nctas) {
   __syncthreads();
   if (threadIdx.x == 0) {
     __threadfence();
     const unsigned t = atomicAdd(&ds->ticket, 1u);
-    if (t == gridDim.x - 1) {
+    if (t == nctas - 1) {
       __threadfence();
       for (int d = 0; d < 3; ++d) {
         ds->Plast[d] = (long long)atomicAdd(&ds->Pacc[d], 0ull);
@@ -462,10 +483,10 @@ __device__ inline void finish_update(DevState* ds, int finish) {
 // term; then lane d < 3 finishes component d: q E_d, the self-energy and
 // dipole corrections, the Langevin force and the half kick.
 template <typename T>
-__global__ void __launch_bounds__(kQuadThreads)
-    k_gather(Mesh m, StepParams sp, Particles P, const T* __restrict__ D, const T* __restrict__ ie,
-             const double* __restrict__ ie64, DevState* ds, int kick, int finish) {
-  const int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+__device__ __forceinline__ void gather_body(const Mesh& m, const StepParams& sp, Particles P,
+                                            const T* __restrict__ D, const T* __restrict__ ie,
+                                            const double* __restrict__ ie64, DevState* ds,
+                                            int kick, int finish, unsigned nctas, int64_t g) {
   const int64_t p = g >> 2;
   const int lane4 = (int)(g & 3);
   const bool active = p < P.n;
@@ -534,7 +555,54 @@ __global__ void __launch_bounds__(kQuadThreads)
     P.Ft[3 * p + d] = Ft;
     if (kick) P.v[3 * p + d] = __dadd_rn(P.v[3 * p + d], __dmul_rn(P.h[p], Ft));
   }
-  if (finish) finish_update(ds, finish);
+  if (finish) finish_update(ds, finish, nctas);
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kQuadThreads)
+    k_gather(Mesh m, StepParams sp, Particles P, const T* __restrict__ D, const T* __restrict__ ie,
+             const double* __restrict__ ie64, DevState* ds, int kick, int finish) {
+  gather_body<T>(m, sp, P, D, ie, ie64, ds, kick, finish, gridDim.x,
+                 blockIdx.x * (int64_t)blockDim.x + threadIdx.x);
+}
+
+// ------------------------------------------------------- batched replicas
+// CTA b works on particles of replica cta_rep[b]; a replica's CTAs form a
+// contiguous range, so warps and CTAs never mix replicas.
+__device__ inline int64_t batch_local(const RepDesc& r) {
+  return (int64_t)(blockIdx.x - r.p_first) * blockDim.x + threadIdx.x;
+}
+
+__global__ void __launch_bounds__(kBatchQuadThreads)
+    k_deposit_batch(const RepDesc* __restrict__ desc, const int* __restrict__ cta_rep, int thermo,
+                    double gamma, double kT) {
+  const RepDesc& r = desc[cta_rep[blockIdx.x]];
+  StepParams sp = r.sp;
+  sp.thermo = thermo;
+  sp.gamma = gamma;
+  sp.kT = kT;
+  deposit_body(r.m, sp, r.P, (unsigned long long*)r.Tb, r.ds, batch_local(r));
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kBatchQuadThreads)
+    k_apply_batch(const RepDesc* __restrict__ desc, const int* __restrict__ cta_rep, int par) {
+  const RepDesc& r = desc[cta_rep[blockIdx.x]];
+  apply_body<T>(r.m, r.P, (unsigned long long*)r.Tb, r.Lg, (T*)r.D[par ^ 1], r.sp.scale,
+                batch_local(r));
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kBatchQuadThreads)
+    k_gather_batch(const RepDesc* __restrict__ desc, const int* __restrict__ cta_rep, int par,
+                   int thermo, double gamma, double kT) {
+  const RepDesc& r = desc[cta_rep[blockIdx.x]];
+  StepParams sp = r.sp;
+  sp.thermo = thermo;
+  sp.gamma = gamma;
+  sp.kT = kT;
+  gather_body<T>(r.m, sp, r.P, (const T*)r.D[par ^ 1], (const T*)r.ie, r.ie64, r.ds, 1, 2,
+                 (unsigned)r.p_ctas, batch_local(r));
 }
 
 __global__ void k_step_end(DevState* ds, int advance) {
@@ -610,25 +678,26 @@ void launch_particle_constants(const StepParams& sp, Particles p, cudaStream_t s
 void launch_kick_drift_deposit(const Mesh& m, const StepParams& sp, Particles p, long long* Tb,
                                DevState* ds, cudaStream_t st) {
   if (p.n > 0)
-    k_kick_drift_deposit<<<blocks_for(4 * p.n, kQuadThreads), kQuadThreads, 0, st>>>(
+    k_kick_drift_deposit<<<blocks_for(4 * p.n, quad_threads(p.n)), quad_threads(p.n), 0, st>>>(
         m, sp, p, (unsigned long long*)Tb, ds);
 }
 
 void launch_move_deposit(const Mesh& m, Particles p, const double* pos_new, const int* img_new,
                          long long* Tb, DevState* ds, cudaStream_t st) {
   if (p.n > 0)
-    k_move_deposit<<<blocks_for(4 * p.n, kQuadThreads), kQuadThreads, 0, st>>>(
+    k_move_deposit<<<blocks_for(4 * p.n, quad_threads(p.n)), quad_threads(p.n), 0, st>>>(
         m, p, pos_new, img_new, (unsigned long long*)Tb, ds);
 }
 
 void launch_apply(const Mesh& m, int prec, Particles p, long long* Tb, long long* Lg, void* D,
                   double scale, cudaStream_t st) {
   if (p.n <= 0) return;
-  const unsigned nb = blocks_for(4 * p.n, kQuadThreads);
+  const int qt = quad_threads(p.n);
+  const unsigned nb = blocks_for(4 * p.n, qt);
   if (prec == 1)
-    k_apply<float><<<nb, kQuadThreads, 0, st>>>(m, p, (unsigned long long*)Tb, Lg, (float*)D, scale);
+    k_apply<float><<<nb, qt, 0, st>>>(m, p, (unsigned long long*)Tb, Lg, (float*)D, scale);
   else
-    k_apply<double><<<nb, kQuadThreads, 0, st>>>(m, p, (unsigned long long*)Tb, Lg, (double*)D,
+    k_apply<double><<<nb, qt, 0, st>>>(m, p, (unsigned long long*)Tb, Lg, (double*)D,
                                                  scale);
 }
 
@@ -639,17 +708,44 @@ void launch_gather(const Mesh& m, int prec, const StepParams& sp, Particles p, c
     if (finish) k_step_end<<<1, 32, 0, st>>>(ds, finish == 2 ? 1 : 0);
     return;
   }
-  const unsigned nb = blocks_for(4 * p.n, kQuadThreads);
+  const int qt = quad_threads(p.n);
+  const unsigned nb = blocks_for(4 * p.n, qt);
   if (prec == 1)
-    k_gather<float><<<nb, kQuadThreads, 0, st>>>(m, sp, p, (const float*)D, (const float*)ie,
+    k_gather<float><<<nb, qt, 0, st>>>(m, sp, p, (const float*)D, (const float*)ie,
                                                  ie64, ds, kick, finish);
   else
-    k_gather<double><<<nb, kQuadThreads, 0, st>>>(m, sp, p, (const double*)D, (const double*)ie,
+    k_gather<double><<<nb, qt, 0, st>>>(m, sp, p, (const double*)D, (const double*)ie,
                                                   ie64, ds, kick, finish);
 }
 
 void launch_step_end(DevState* ds, int advance, cudaStream_t st) {
   k_step_end<<<1, 32, 0, st>>>(ds, advance);
+}
+
+void launch_deposit_batch(const RepDesc* desc, const int* cta_rep, int nctas, int thermo,
+                          double gamma, double kT, cudaStream_t st) {
+  if (nctas > 0)
+    k_deposit_batch<<<nctas, kBatchQuadThreads, 0, st>>>(desc, cta_rep, thermo, gamma, kT);
+}
+
+void launch_apply_batch(int prec, const RepDesc* desc, const int* cta_rep, int nctas, int par,
+                        cudaStream_t st) {
+  if (nctas <= 0) return;
+  if (prec == 1)
+    k_apply_batch<float><<<nctas, kBatchQuadThreads, 0, st>>>(desc, cta_rep, par);
+  else
+    k_apply_batch<double><<<nctas, kBatchQuadThreads, 0, st>>>(desc, cta_rep, par);
+}
+
+void launch_gather_batch(int prec, const RepDesc* desc, const int* cta_rep, int nctas, int par,
+                         int thermo, double gamma, double kT, cudaStream_t st) {
+  if (nctas <= 0) return;
+  if (prec == 1)
+    k_gather_batch<float><<<nctas, kBatchQuadThreads, 0, st>>>(desc, cta_rep, par, thermo, gamma,
+                                                               kT);
+  else
+    k_gather_batch<double><<<nctas, kBatchQuadThreads, 0, st>>>(desc, cta_rep, par, thermo,
+                                                                gamma, kT);
 }
 
 void launch_particle_energy(const Mesh& m, const StepParams& sp, Particles p, const double* ie64,

@@ -1,0 +1,378 @@
+// memd_server.cu -- a request server over batched MEMD systems.
+//
+// Requests (a system and a number of steps) queue in arrival order.  Each
+// call to memd_server_pump is one scheduling round: finished requests are
+// retired (their results copied to host memory, their device memory
+// released), queued requests are admitted while the device-memory budget and
+// the slot count allow (FIFO, so a large request is not overtaken), the
+// batch of live systems is rebuilt when membership changed, and the batch
+// advances by one quantum of steps (or less, so that no request overshoots
+// its step count).  Requests that arrive while others run join at the next
+// round: their work shares every kernel launch with the systems already
+// resident, which is continuous batching.  Each request's result is the
+// same as when it runs alone (the batched kernels are the single-system
+// kernels over a descriptor table).
+#include <algorithm>
+#include <chrono>
+#include <cstring>
+#include <deque>
+#include <map>
+#include <string>
+#include <vector>
+
+#include "memd.h"
+#include "memd_ctx.cuh"
+#include "memd_internal.cuh"
+
+struct memd_server {
+  memd_server_options opt{};
+  struct Req {
+    int64_t id = 0;
+    int32_t mesh[3] = {0, 0, 0};
+    double box[3] = {0, 0, 0};
+    int32_t eps_kind = 0, eps_axis = 0;
+    std::vector<double> eps_values;
+    double eps_params[8] = {0};
+    double c_light = 1, dt = 0.01;
+    std::vector<double> pos, mass, vel;
+    std::vector<int32_t> q;
+    uint64_t seed = 0;
+    int64_t nsteps = 0, remaining = 0;
+    int64_t footprint = 0;
+    int32_t state = MEMD_REQ_QUEUED;
+    memd_ctx* ctx = nullptr;
+    // results
+    std::vector<double> r_pos, r_vel, r_f;
+    std::vector<int32_t> r_img;
+    memd_energy_terms r_e{};
+    std::string error;
+  };
+  std::map<int64_t, Req> reqs;
+  std::deque<int64_t> queue;
+  std::vector<int64_t> active;
+  int64_t next_id = 1;
+  int64_t used = 0;
+  memd_batch* batch = nullptr;
+  bool dirty = false;
+  std::string last_error;
+  memd_server_stats stats{};
+};
+
+namespace {
+
+// device bytes a request holds while resident: double-buffered D and B,
+// 1/eps in the field precision and in FP64, the int64 ledger and transfer
+// buffer, particle arrays, plus the initial solve's scratch (released after
+// init but needed at admission)
+int64_t footprint(const memd_server_options& o, const memd_server::Req& r) {
+  const int64_t V = (int64_t)r.mesh[0] * r.mesh[1] * r.mesh[2];
+  const int64_t es = o.precision == MEMD_FP32 ? 4 : 8;
+  const int64_t fields = 3 * V * (5 * es + 8 + 16);
+  const int64_t init = 3 * V * 8 * 7 + V * 16;
+  const int64_t parts = (r.q.size() + 1) * (8 * 3 * 5 + 8 * 3 + 4 * 4 + 24);
+  return fields + init + parts + (1 << 20);
+}
+
+memd_status sfail(memd_server* s, memd_status st, const std::string& why) {
+  if (s) s->last_error = why;
+  return st;
+}
+
+void retire(memd_server* s, memd_server::Req& r) {
+  memd_ctx* c = r.ctx;
+  const size_t n = r.q.size();
+  r.r_pos.resize(3 * n);
+  r.r_vel.resize(3 * n);
+  r.r_f.resize(3 * n);
+  r.r_img.resize(3 * n);
+  memd_status st = memd_get_particles(c, n ? r.r_pos.data() : nullptr, n ? r.r_vel.data() : nullptr,
+                                      n ? r.r_img.data() : nullptr);
+  if (st == MEMD_OK && n) st = memd_forces(c, r.r_f.data());
+  if (st == MEMD_OK) st = memd_energy(c, &r.r_e);
+  if (st != MEMD_OK) {
+    r.state = MEMD_REQ_FAILED;
+    r.error = memd_last_error(c);
+  } else {
+    r.state = MEMD_REQ_DONE;
+  }
+  memd_destroy(c);
+  r.ctx = nullptr;
+  s->used -= r.footprint;
+  r.pos.clear();
+  r.vel.clear();
+  r.mass.clear();
+  r.eps_values.clear();
+}
+
+double now_s() {
+  return std::chrono::duration<double>(std::chrono::steady_clock::now().time_since_epoch()).count();
+}
+
+memd_status admit(memd_server* s, memd_server::Req& r) {
+  // steps already queued on the stream finish first, so that the timed
+  // part below is this request's own setup
+  cudaStreamSynchronize((cudaStream_t)s->opt.cuda_stream);
+  const double t0 = now_s();
+  struct Timer {
+    memd_server* s;
+    double t0;
+    ~Timer() {
+      s->stats.setup_s += now_s() - t0;
+      s->stats.admitted += 1;
+    }
+  } timer{s, t0};
+  memd_options o;
+  memd_default_options(&o);
+  o.precision = s->opt.precision;
+  o.cuda_stream = s->opt.cuda_stream;
+  o.device = s->opt.device;
+  o.alloc = s->opt.alloc;
+  o.free = s->opt.free;
+  o.alloc_user = s->opt.alloc_user;
+  o.seed = r.seed;
+  o.field_kernel = MEMD_FIELD_LDG;  // the batched kernels' arithmetic
+  memd_eps_profile e{};
+  e.kind = r.eps_kind;
+  e.axis = r.eps_axis;
+  e.values = r.eps_values.empty() ? nullptr : r.eps_values.data();
+  std::memcpy(e.params, r.eps_params, sizeof(e.params));
+  memd_status st = memd_create(r.mesh, r.box, &e, r.c_light, r.dt, &o, &r.ctx);
+  if (st == MEMD_OK) {
+    const int64_t n = (int64_t)r.q.size();
+    st = memd_init_field(r.ctx, n, n ? r.pos.data() : nullptr, n ? r.q.data() : nullptr,
+                         r.mass.empty() ? nullptr : r.mass.data(),
+                         r.vel.empty() ? nullptr : r.vel.data());
+    if (st != MEMD_OK) {
+      r.error = memd_last_error(r.ctx);
+      memd_destroy(r.ctx);
+      r.ctx = nullptr;
+    }
+  } else {
+    r.error = std::string("memd_create: ") + memd_status_string(st);
+  }
+  return st;
+}
+
+}  // namespace
+
+extern "C" {
+
+void memd_server_default_options(memd_server_options* o) {
+  if (!o) return;
+  std::memset(o, 0, sizeof(*o));
+  o->precision = MEMD_FP32;
+  o->budget_bytes = (int64_t)8 << 30;
+  o->max_slots = 64;
+  o->quantum = 50;
+  o->device = -1;
+}
+
+memd_status memd_server_create(const memd_server_options* opt, memd_server** out) {
+  if (!out) return MEMD_ERR_INVALID;
+  *out = nullptr;
+  memd_server* s = new memd_server();
+  if (opt)
+    s->opt = *opt;
+  else
+    memd_server_default_options(&s->opt);
+  if (s->opt.max_slots < 1 || s->opt.quantum < 1 || s->opt.budget_bytes <= 0 ||
+      (s->opt.precision != MEMD_FP32 && s->opt.precision != MEMD_FP64)) {
+    delete s;
+    return MEMD_ERR_INVALID;
+  }
+  if (!s->opt.cuda_stream) {
+    // one stream shared by every resident system (a batch requirement)
+    cudaStream_t st;
+    if (cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess) {
+      delete s;
+      return MEMD_ERR_CUDA;
+    }
+    s->opt.cuda_stream = st;
+    s->opt.reserved[0] = 1;  // owned
+  }
+  *out = s;
+  return MEMD_OK;
+}
+
+void memd_server_destroy(memd_server* s) {
+  if (!s) return;
+  if (s->batch) memd_batch_destroy(s->batch);
+  s->batch = nullptr;
+  for (auto& kv : s->reqs)
+    if (kv.second.ctx) memd_destroy(kv.second.ctx);
+  if (s->opt.reserved[0]) cudaStreamDestroy((cudaStream_t)s->opt.cuda_stream);
+  delete s;
+}
+
+memd_status memd_server_submit(memd_server* s, const memd_request* q, int64_t* id) {
+  if (!s || !q || !id) return MEMD_ERR_INVALID;
+  if (q->n < 0 || q->nsteps < 0 || (q->n > 0 && (!q->pos || !q->q)))
+    return sfail(s, MEMD_ERR_INVALID, "bad request arrays");
+  memd_server::Req r;
+  r.id = s->next_id++;
+  std::memcpy(r.mesh, q->mesh, sizeof(r.mesh));
+  std::memcpy(r.box, q->box, sizeof(r.box));
+  r.eps_kind = q->eps.kind;
+  r.eps_axis = q->eps.axis;
+  std::memcpy(r.eps_params, q->eps.params, sizeof(r.eps_params));
+  const int64_t V = (int64_t)q->mesh[0] * q->mesh[1] * q->mesh[2];
+  if (q->eps.values) {
+    const int64_t cnt = q->eps.kind == MEMD_EPS_LINKS ? 3 * V : V;
+    r.eps_values.assign(q->eps.values, q->eps.values + cnt);
+  }
+  r.c_light = q->c_light;
+  r.dt = q->dt;
+  const int64_t n = q->n;
+  r.pos.assign(q->pos, q->pos + 3 * n);
+  r.q.assign(q->q, q->q + n);
+  if (q->mass) r.mass.assign(q->mass, q->mass + n);
+  if (q->vel) r.vel.assign(q->vel, q->vel + 3 * n);
+  r.seed = q->seed;
+  r.nsteps = r.remaining = q->nsteps;
+  r.footprint = footprint(s->opt, r);
+  *id = r.id;
+  s->queue.push_back(r.id);
+  s->reqs.emplace(r.id, std::move(r));
+  return MEMD_OK;
+}
+
+memd_status memd_server_pump(memd_server* s, int32_t* n_active, int32_t* n_queued,
+                             int32_t* n_done) {
+  if (!s) return MEMD_ERR_INVALID;
+  // 1. retire requests that have taken all their steps (the batch refers to
+  // its members, so it goes first when any member leaves)
+  if (s->batch) {
+    memd_status st = memd_batch_synchronize(s->batch);
+    if (st != MEMD_OK) return sfail(s, st, "batch step failed");
+    bool leaving = false;
+    for (int64_t id : s->active) leaving = leaving || s->reqs[id].remaining <= 0;
+    if (leaving) {
+      memd_batch_destroy(s->batch);
+      s->batch = nullptr;
+    }
+  }
+  std::vector<int64_t> keep;
+  for (int64_t id : s->active) {
+    memd_server::Req& r = s->reqs[id];
+    if (r.remaining <= 0) {
+      retire(s, r);
+      s->dirty = true;
+    } else {
+      keep.push_back(id);
+    }
+  }
+  s->active.swap(keep);
+  // 2. admit in arrival order while memory and slots allow
+  while (!s->queue.empty() && (int)s->active.size() < s->opt.max_slots) {
+    memd_server::Req& r = s->reqs[s->queue.front()];
+    if (r.footprint > s->opt.budget_bytes) {
+      r.state = MEMD_REQ_FAILED;
+      r.error = "request larger than the memory budget";
+      s->queue.pop_front();
+      continue;
+    }
+    if (s->used + r.footprint > s->opt.budget_bytes) break;
+    s->queue.pop_front();
+    if (s->batch) {  // a new member's setup queues behind the running batch
+      memd_batch_destroy(s->batch);
+      s->batch = nullptr;
+    }
+    if (admit(s, r) != MEMD_OK) {
+      r.state = MEMD_REQ_FAILED;
+      continue;
+    }
+    r.state = MEMD_REQ_RUNNING;
+    s->used += r.footprint;
+    s->active.push_back(r.id);
+    s->dirty = true;
+  }
+  // 3. batch of the live systems, one quantum (bounded by the nearest finish)
+  if (s->dirty) {
+    s->stats.rebuilds += 1;
+    if (s->batch) memd_batch_destroy(s->batch);
+    s->batch = nullptr;
+    if (!s->active.empty()) {
+      std::vector<memd_ctx*> m;
+      for (int64_t id : s->active) m.push_back(s->reqs[id].ctx);
+      memd_status st = memd_batch_create((int32_t)m.size(), m.data(), &s->batch);
+      if (st != MEMD_OK) return sfail(s, st, "batch rebuild failed");
+    }
+    s->dirty = false;
+  }
+  if (s->batch) {
+    int64_t k = s->opt.quantum;
+    for (int64_t id : s->active) k = std::min(k, s->reqs[id].remaining);
+    if (k > 0) {
+      memd_thermostat th{s->opt.gamma, s->opt.kT};
+      memd_status st = memd_batch_step(s->batch, k, s->opt.thermostat ? &th : nullptr);
+      if (st != MEMD_OK) return sfail(s, st, "batch step failed");
+      for (int64_t id : s->active) {
+        s->reqs[id].remaining -= k;
+        s->stats.link_updates += 3 * k * (int64_t)s->reqs[id].mesh[0] * s->reqs[id].mesh[1] *
+                                 s->reqs[id].mesh[2];
+        s->stats.particle_steps += k * (int64_t)s->reqs[id].q.size();
+      }
+      s->stats.steps_rounds += 1;
+    }
+  }
+  s->stats.rounds += 1;
+  int64_t resident = 0;
+  for (int64_t id : s->active) resident += s->reqs[id].footprint;
+  s->stats.budget_use_sum += (double)resident / (double)s->opt.budget_bytes;
+  int32_t done = 0;
+  for (auto& kv : s->reqs)
+    if (kv.second.state == MEMD_REQ_DONE || kv.second.state == MEMD_REQ_FAILED) ++done;
+  if (n_active) *n_active = (int32_t)s->active.size();
+  if (n_queued) *n_queued = (int32_t)s->queue.size();
+  if (n_done) *n_done = done;
+  return MEMD_OK;
+}
+
+memd_status memd_server_status(memd_server* s, int64_t id, int32_t* state) {
+  if (!s || !state) return MEMD_ERR_INVALID;
+  auto it = s->reqs.find(id);
+  if (it == s->reqs.end()) return sfail(s, MEMD_ERR_INVALID, "unknown request");
+  *state = it->second.state;
+  return MEMD_OK;
+}
+
+memd_status memd_server_result(memd_server* s, int64_t id, double* pos, double* vel,
+                               int32_t* img, double* forces, memd_energy_terms* e) {
+  if (!s) return MEMD_ERR_INVALID;
+  auto it = s->reqs.find(id);
+  if (it == s->reqs.end()) return sfail(s, MEMD_ERR_INVALID, "unknown request");
+  memd_server::Req& r = it->second;
+  if (r.state == MEMD_REQ_FAILED) return sfail(s, MEMD_ERR_STATE, r.error);
+  if (r.state != MEMD_REQ_DONE) return sfail(s, MEMD_ERR_STATE, "request not finished");
+  const size_t n3 = r.r_pos.size();
+  if (pos && n3) std::memcpy(pos, r.r_pos.data(), n3 * sizeof(double));
+  if (vel && n3) std::memcpy(vel, r.r_vel.data(), n3 * sizeof(double));
+  if (img && n3) std::memcpy(img, r.r_img.data(), n3 * sizeof(int32_t));
+  if (forces && n3) std::memcpy(forces, r.r_f.data(), n3 * sizeof(double));
+  if (e) *e = r.r_e;
+  return MEMD_OK;
+}
+
+memd_status memd_server_release(memd_server* s, int64_t id) {
+  if (!s) return MEMD_ERR_INVALID;
+  auto it = s->reqs.find(id);
+  if (it == s->reqs.end()) return sfail(s, MEMD_ERR_INVALID, "unknown request");
+  if (it->second.state != MEMD_REQ_DONE && it->second.state != MEMD_REQ_FAILED)
+    return sfail(s, MEMD_ERR_STATE, "request still queued or running");
+  s->reqs.erase(it);
+  return MEMD_OK;
+}
+
+int64_t memd_server_used_bytes(const memd_server* s) { return s ? s->used : 0; }
+
+memd_status memd_server_get_stats(const memd_server* s, memd_server_stats* out) {
+  if (!s || !out) return MEMD_ERR_INVALID;
+  *out = s->stats;
+  return MEMD_OK;
+}
+
+const char* memd_server_last_error(const memd_server* s) {
+  return s ? s->last_error.c_str() : "no server";
+}
+
+}  // extern "C"

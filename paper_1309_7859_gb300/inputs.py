@@ -174,7 +174,7 @@ def served_stream(seed=1004, count=512, nmin_mesh=16, nmax_mesh=96, qmin=100, qm
     for r in range(count):
         N = int(rng.integers(nmin_mesh, nmax_mesh + 1))
         n = min(log_uniform_even(rng, qmin, qmax), (N ** 3) // 2 // 2 * 2)
-        steps = int(round(math.exp(rng.uniform(math.log(smin), math.log(smax)))))
+        steps = int(round(math.exp(rng.uniform(math.log(smin), math.log(max(smax, smin))))))
         vals = smooth_random_vertices(np.random.default_rng(seed * 65536 + r), (N, N, N))
         eps = EpsSpec("vertices", 0, (), vals)
         out.append(_system(f"request{r}-{N}^3-{n}q", (N, N, N), n, eps, 0.005, precision,

@@ -26,7 +26,15 @@ EXPORTS = ("memd_default_options", "memd_status_string", "memd_last_error", "mem
            "memd_energy", "memd_get_particles", "memd_set_particles", "memd_move",
            "memd_get_fields", "memd_set_fields", "memd_compute_forces", "memd_get_setup",
            "memd_get_kernel_stats", "memd_reset_kernel_stats", "memd_synchronize",
+           "memd_batch_create", "memd_batch_step", "memd_batch_synchronize",
+           "memd_batch_kernel_stats", "memd_batch_destroy", "memd_server_default_options",
+           "memd_server_create", "memd_server_destroy", "memd_server_submit", "memd_server_pump",
+           "memd_server_status", "memd_server_result", "memd_server_release",
+           "memd_server_used_bytes", "memd_server_get_stats", "memd_server_last_error",
            "memd_field_energy_static")
+VOID_RESULT = ("memd_default_options", "memd_destroy", "memd_status_string", "memd_last_error",
+               "memd_batch_destroy", "memd_server_default_options", "memd_server_destroy",
+               "memd_server_used_bytes", "memd_server_last_error")
 
 
 class MemdError(RuntimeError):
@@ -49,7 +57,8 @@ class Options(C.Structure):
                 ("relax_max_iter", C.c_int32), ("relax_tol", C.c_double), ("seed", C.c_uint64),
                 ("cuda_stream", C.c_void_p), ("device", C.c_int32), ("use_graphs", C.c_int32),
                 ("alloc", ALLOC), ("free", FREE), ("alloc_user", C.c_void_p),
-                ("time_kernels", C.c_int32), ("reserved", C.c_int32 * 7)]
+                ("time_kernels", C.c_int32), ("field_kernel", C.c_int32),
+                ("reserved", C.c_int32 * 6)]
 
 
 class Thermostat(C.Structure):
@@ -70,9 +79,33 @@ class EnergyTerms(C.Structure):
                 "step": self.step}
 
 
+class ServerOptions(C.Structure):
+    _fields_ = [("precision", C.c_int32), ("max_slots", C.c_int32), ("budget_bytes", C.c_int64),
+                ("quantum", C.c_int32), ("device", C.c_int32), ("cuda_stream", C.c_void_p),
+                ("alloc", ALLOC), ("free", FREE), ("alloc_user", C.c_void_p),
+                ("thermostat", C.c_int32), ("pad", C.c_int32), ("gamma", C.c_double),
+                ("kT", C.c_double), ("reserved", C.c_int32 * 4)]
+
+
+class Request(C.Structure):
+    _fields_ = [("mesh", C.c_int32 * 3), ("box", C.c_double * 3), ("eps", EpsProfile),
+                ("c_light", C.c_double), ("dt", C.c_double), ("n", C.c_int64),
+                ("pos", C.POINTER(C.c_double)), ("q", C.POINTER(C.c_int32)),
+                ("mass", C.POINTER(C.c_double)), ("vel", C.POINTER(C.c_double)),
+                ("seed", C.c_uint64), ("nsteps", C.c_int64)]
+
+
+class ServerStats(C.Structure):
+    _fields_ = [("setup_s", C.c_double), ("budget_use_sum", C.c_double), ("rounds", C.c_int64),
+                ("steps_rounds", C.c_int64), ("rebuilds", C.c_int64), ("admitted", C.c_int64),
+                ("link_updates", C.c_int64), ("particle_steps", C.c_int64)]
+
+
 class KernelStats(C.Structure):
     _fields_ = [("field_ms", C.c_double), ("field_launches", C.c_int64),
-                ("field_bytes", C.c_double), ("launches_per_step", C.c_int64)]
+                ("field_bytes", C.c_double), ("launches_per_step", C.c_int64),
+                ("field_tma", C.c_int32), ("field_ty", C.c_int32), ("field_zchunk", C.c_int32),
+                ("pad", C.c_int32)]
 
 
 _lib = None
@@ -115,11 +148,28 @@ def lib(build_if_missing=True):
     L.memd_get_kernel_stats.argtypes = [vp, C.POINTER(KernelStats)]
     L.memd_reset_kernel_stats.argtypes = [vp]
     L.memd_synchronize.argtypes = [vp]
+    L.memd_batch_create.argtypes = [C.c_int32, C.POINTER(vp), C.POINTER(vp)]
+    L.memd_batch_step.argtypes = [vp, C.c_int64, C.POINTER(Thermostat)]
+    L.memd_batch_synchronize.argtypes = [vp]
+    L.memd_batch_kernel_stats.argtypes = [vp, C.POINTER(KernelStats)]
+    L.memd_batch_destroy.argtypes = [vp]
+    L.memd_server_default_options.argtypes = [C.POINTER(ServerOptions)]
+    L.memd_server_create.argtypes = [C.POINTER(ServerOptions), C.POINTER(vp)]
+    L.memd_server_destroy.argtypes = [vp]
+    L.memd_server_submit.argtypes = [vp, C.POINTER(Request), C.POINTER(C.c_int64)]
+    L.memd_server_pump.argtypes = [vp, i32p, i32p, i32p]
+    L.memd_server_status.argtypes = [vp, C.c_int64, i32p]
+    L.memd_server_result.argtypes = [vp, C.c_int64, f64p, f64p, i32p, f64p, C.POINTER(EnergyTerms)]
+    L.memd_server_release.argtypes = [vp, C.c_int64]
+    L.memd_server_used_bytes.restype = C.c_int64
+    L.memd_server_used_bytes.argtypes = [vp]
+    L.memd_server_get_stats.argtypes = [vp, C.POINTER(ServerStats)]
+    L.memd_server_last_error.restype = C.c_char_p
+    L.memd_server_last_error.argtypes = [vp]
     L.memd_field_energy_static.argtypes = [i32p, C.c_double, C.c_double, C.c_double, C.c_int32,
                                            vp, vp, vp, vp, vp]
     for name in EXPORTS:
-        if name not in ("memd_default_options", "memd_destroy", "memd_status_string",
-                        "memd_last_error"):
+        if name not in VOID_RESULT:
             getattr(L, name).restype = C.c_int
     _lib = L
     return L
@@ -168,6 +218,7 @@ class StepTiming:
     field_launches: int
     field_bytes: float
     launches_per_step: int
+    field_kernel: str = ""
 
 
 class Memd:
@@ -176,7 +227,7 @@ class Memd:
     def __init__(self, mesh, box, eps=None, c_light=1.0, dt=0.01, precision="fp64",
                  self_mode=SELF_GF, dipole_corr=True, relax_tol=1e-12, relax_max_iter=200000,
                  seed=0, use_graphs=True, time_kernels=False, use_torch=True, stream=None,
-                 device=None):
+                 device=None, field_kernel="auto"):
         self._L = lib()
         self._h = C.c_void_p(None)
         self.mesh = tuple(int(n) for n in mesh)
@@ -193,6 +244,7 @@ class Memd:
         o.seed = int(seed) & ((1 << 64) - 1)
         o.use_graphs = 1 if use_graphs else 0
         o.time_kernels = 1 if time_kernels else 0
+        o.field_kernel = {"auto": 0, "ldg": 1, "tma": 2}[field_kernel]
         self._alloc = None
         self._stream = stream
         if use_torch:
@@ -333,13 +385,200 @@ class Memd:
     def kernel_stats(self):
         k = KernelStats()
         self._check(self._L.memd_get_kernel_stats(self._h, C.byref(k)), "memd_get_kernel_stats")
-        return StepTiming(k.field_ms, k.field_launches, k.field_bytes, k.launches_per_step)
+        kind = "k_fused_tma" if k.field_tma else "k_fused_curl"
+        return StepTiming(k.field_ms, k.field_launches, k.field_bytes, k.launches_per_step,
+                          f"{kind}<ty={k.field_ty}, zchunk={k.field_zchunk}>")
 
     def reset_kernel_stats(self):
         self._check(self._L.memd_reset_kernel_stats(self._h), "memd_reset_kernel_stats")
 
     def synchronize(self):
         self._check(self._L.memd_synchronize(self._h), "memd_synchronize")
+
+
+class Batch:
+    """Independent Memd systems stepped together, four launches per step for
+    all of them.  The members must share one stream (pass the same `stream`
+    when creating them) and precision; they stay usable one by one."""
+
+    def __init__(self, members):
+        self._L = lib()
+        self.members = list(members)
+        arr = (C.c_void_p * len(self.members))(*[m._h.value for m in self.members])
+        self._h = C.c_void_p(None)
+        st = self._L.memd_batch_create(len(self.members), arr, C.byref(self._h))
+        if st != 0:
+            raise MemdError(st, "memd_batch_create failed")
+
+    def step(self, nsteps=1, thermostat=None):
+        th = None
+        if thermostat is not None:
+            th = Thermostat(float(thermostat[0]), float(thermostat[1]))
+        st = self._L.memd_batch_step(self._h, int(nsteps), C.byref(th) if th else None)
+        if st != 0:
+            raise MemdError(st, "memd_batch_step failed")
+
+    def synchronize(self):
+        st = self._L.memd_batch_synchronize(self._h)
+        if st != 0:
+            raise MemdError(st, "memd_batch_synchronize failed")
+
+    def kernel_stats(self):
+        k = KernelStats()
+        st = self._L.memd_batch_kernel_stats(self._h, C.byref(k))
+        if st != 0:
+            raise MemdError(st, "memd_batch_kernel_stats failed")
+        return StepTiming(k.field_ms, k.field_launches, k.field_bytes, k.launches_per_step,
+                          f"k_fused_curl_batch<ty={k.field_ty}, zchunk={k.field_zchunk}>")
+
+    def close(self):
+        if self._h:
+            self._L.memd_batch_destroy(self._h)
+            self._h = C.c_void_p(None)
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Server:
+    """Continuous-batching request server (memd_server_*): submit systems with
+    a step count, pump scheduling rounds, collect results."""
+
+    def __init__(self, precision="fp32", budget_bytes=8 << 30, max_slots=64, quantum=50,
+                 thermostat=None, use_torch=True, stream=None):
+        self._L = lib()
+        o = ServerOptions()
+        self._L.memd_server_default_options(C.byref(o))
+        o.precision = FP32 if precision == "fp32" else FP64
+        o.budget_bytes = int(budget_bytes)
+        o.max_slots = int(max_slots)
+        o.quantum = int(quantum)
+        if thermostat is not None:
+            o.thermostat, o.gamma, o.kT = 1, float(thermostat[0]), float(thermostat[1])
+        self._alloc = None
+        self._stream = stream
+        if use_torch:
+            import torch
+            if not torch.cuda.is_available():
+                raise RuntimeError("MEMD needs a CUDA GPU; torch sees none")
+            dev = torch.cuda.current_device()
+            o.device = dev
+            if stream is None:
+                self._stream = torch.cuda.Stream(device=dev)
+            o.cuda_stream = C.c_void_p(self._stream.cuda_stream)
+            self._alloc = _TorchAllocator(dev)
+            o.alloc, o.free = self._alloc.alloc, self._alloc.free
+        self._h = C.c_void_p(None)
+        st = self._L.memd_server_create(C.byref(o), C.byref(self._h))
+        if st != 0:
+            raise MemdError(st, "memd_server_create failed")
+        self._keep = {}
+        self.n_of = {}
+
+    def _err(self, st, what):
+        if st != 0:
+            msg = self._L.memd_server_last_error(self._h)
+            raise MemdError(st, f"{what}: {msg.decode() if msg else ''}")
+
+    def submit(self, sysc, nsteps=None):
+        """Queue an inputs.System (its own step count unless nsteps is given)."""
+        r = Request()
+        for d in range(3):
+            r.mesh[d] = int(sysc.mesh[d])
+            r.box[d] = float(sysc.box[d])
+        e, keep = make_eps(sysc.eps)
+        r.eps = e
+        r.c_light, r.dt = float(sysc.c_light), float(sysc.dt)
+        x = _f64(sysc.x).reshape(-1, 3)
+        q = _i32(sysc.q)
+        m = _f64(sysc.m)
+        v = _f64(sysc.v).reshape(-1, 3)
+        r.n = x.shape[0]
+        r.pos, r.q, r.mass, r.vel = (_ptr(x, C.c_double), _ptr(q, C.c_int32),
+                                     _ptr(m, C.c_double), _ptr(v, C.c_double))
+        r.seed = int(sysc.seed) & ((1 << 64) - 1)
+        r.nsteps = int(sysc.steps if nsteps is None else nsteps)
+        rid = C.c_int64(0)
+        self._err(self._L.memd_server_submit(self._h, C.byref(r), C.byref(rid)), "submit")
+        del keep, x, q, m, v  # copied by the server
+        self.n_of[rid.value] = r.n
+        return rid.value
+
+    def pump(self):
+        a, q, d = C.c_int32(0), C.c_int32(0), C.c_int32(0)
+        self._err(self._L.memd_server_pump(self._h, C.byref(a), C.byref(q), C.byref(d)), "pump")
+        return a.value, q.value, d.value
+
+    def status(self, rid):
+        s = C.c_int32(0)
+        self._err(self._L.memd_server_status(self._h, int(rid), C.byref(s)), "status")
+        return s.value
+
+    def result(self, rid):
+        n = self.n_of[rid]
+        x, v, f = np.zeros((n, 3)), np.zeros((n, 3)), np.zeros((n, 3))
+        img = np.zeros((n, 3), dtype=np.int32)
+        e = EnergyTerms()
+        self._err(self._L.memd_server_result(self._h, int(rid), _ptr(x, C.c_double),
+                                             _ptr(v, C.c_double), _ptr(img, C.c_int32),
+                                             _ptr(f, C.c_double), C.byref(e)), "result")
+        return x, v, img, f, e.as_dict()
+
+    def release(self, rid):
+        self._err(self._L.memd_server_release(self._h, int(rid)), "release")
+
+    def used_bytes(self):
+        return self._L.memd_server_used_bytes(self._h)
+
+    def stats(self):
+        st = ServerStats()
+        self._err(self._L.memd_server_get_stats(self._h, C.byref(st)), "stats")
+        return {k: getattr(st, k) for k, _ in ServerStats._fields_}
+
+    def close(self):
+        if self._h:
+            self._L.memd_server_destroy(self._h)
+            self._h = C.c_void_p(None)
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def serve(server, systems, arrivals, poll_s=0.0):
+    """Drive a server through a stream of systems arriving at the given wall
+    times (seconds from now): submit each when its time comes, pump rounds,
+    and record when each finished.  Returns a list of dicts (id, arrival,
+    done, latency) in submission order."""
+    import time as _time
+    t0 = _time.perf_counter()
+    order = sorted(range(len(systems)), key=lambda i: arrivals[i])
+    pending = list(order)
+    ids, rec = {}, {}
+    while pending or any(server.status(r) < 2 for r in ids.values()):
+        now = _time.perf_counter() - t0
+        while pending and arrivals[pending[0]] <= now:
+            i = pending.pop(0)
+            ids[i] = server.submit(systems[i])
+            rec[i] = {"index": i, "id": ids[i], "arrival": now, "done": None}
+        if not ids:
+            _time.sleep(max(0.0, arrivals[pending[0]] - now))
+            continue
+        server.pump()
+        now = _time.perf_counter() - t0
+        for i, rid in ids.items():
+            if rec[i]["done"] is None and server.status(rid) >= 2:
+                rec[i]["done"] = now
+        if poll_s:
+            _time.sleep(poll_s)
+    for r in rec.values():
+        r["latency"] = r["done"] - r["arrival"]
+    return [rec[i] for i in sorted(rec)]
 
 
 def make_eps(spec):
