@@ -503,7 +503,7 @@ def main():
     ap.add_argument("--workload", default="slab-32")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
-    ap.add_argument("--field-kernel", default="auto", choices=["auto", "ldg", "tma"])
+    ap.add_argument("--field-kernel", default="auto", choices=["auto", "ldg", "tma", "site"])
     ap.add_argument("--batch", type=int, default=64,
                     help="replicas of the extra batched measurement (0: skip)")
     ap.add_argument("--serve", type=int, default=128,

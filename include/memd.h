@@ -99,14 +99,16 @@ typedef struct memd_options {
   void *alloc_user;
   int32_t time_kernels;   /* 1: CUDA events around the field kernels, see
                              memd_get_kernel_stats */
-  int32_t field_kernel;   /* MEMD_FIELD_AUTO: autotuned over both kernels below;
-                             MEMD_FIELD_LDG: plain-load kernel only; MEMD_FIELD_TMA:
-                             TMA-staged kernel (when x rows are 16-byte multiples,
-                             else the plain-load kernel) */
+  int32_t field_kernel;   /* MEMD_FIELD_AUTO: autotuned over the three kernels below;
+                             MEMD_FIELD_LDG: plain-load kernel, halo loops per thread;
+                             MEMD_FIELD_TMA: TMA-staged kernel (when x rows are
+                             16-byte multiples, else the plain-load kernel);
+                             MEMD_FIELD_SITE: plain loads, one thread per site of the
+                             tile and its halo.  All three give identical results. */
   int32_t reserved[6];
 } memd_options;
 
-enum { MEMD_FIELD_AUTO = 0, MEMD_FIELD_LDG = 1, MEMD_FIELD_TMA = 2 };
+enum { MEMD_FIELD_AUTO = 0, MEMD_FIELD_LDG = 1, MEMD_FIELD_TMA = 2, MEMD_FIELD_SITE = 3 };
 
 typedef struct memd_thermostat {
   double gamma; /* friction rate; Langevin force -gamma m v + sqrt(2 gamma m kT / dt) xi */
@@ -135,7 +137,7 @@ typedef struct memd_kernel_stats {
   int32_t field_tma;      /* field kernel chosen at create: 1 TMA-staged, 0 plain loads */
   int32_t field_ty;       /* its tile height (rows of 32 sites) */
   int32_t field_zchunk;   /* its z planes per CTA */
-  int32_t pad;
+  int32_t field_site;     /* 1: the one-thread-per-site plain-load kernel */
 } memd_kernel_stats;
 
 /* Fill *opt with defaults: FP64, GF self term, dipole correction on,
@@ -237,8 +239,9 @@ memd_status memd_synchronize(memd_ctx *ctx);
  * one CUDA graph of four kernels over all members (deposition beside the
  * field update, then transfer application, then the gather), each kernel
  * covering every member through a per-replica descriptor table.  A member
- * gives the same result in the batch as stepped alone with the plain-load
- * field kernel (MEMD_FIELD_LDG).  Members must share the device, the
+ * gives the same result in the batch as stepped alone (the batched field
+ * kernel is the one-thread-per-site kernel, whose arithmetic all field kernels
+ * share).  Members must share the device, the
  * precision and the CUDA stream; the batch does not own them, and they stay
  * usable one by one (memd_forces, memd_energy, ...) between batch steps.
  * Re-initialising a member is noticed at the next batch step. */

@@ -97,6 +97,9 @@ StepParams memd_step_params(const memd_ctx* c, int thermo, double gamma, double 
   sp.coefD = c->c * c->c * c->dt / c->mesh.a;
   sp.scale = std::ldexp(1.0, -48) / (c->mesh.a * c->mesh.a);
   sp.Vbox = c->Vbox;
+  sp.inv_V = 1.0 / c->Vbox;
+  sp.self_pre = 0.5 / (c->mesh.a * c->mesh.a);
+  sp.dip_unit = c->mesh.a / (double)kS;
   for (int t = 0; t < 8; ++t) sp.G[t] = c->G[t];
   for (int t = 0; t < 9; ++t) sp.Minv[t] = c->Minv[t];
   sp.self_mode = c->self_mode;
@@ -338,14 +341,16 @@ static void launch_field(memd_ctx* c, int par, double cB, double cD, FusedCfg cf
 }
 
 // ------------------------------------------------------------------ autotuner
-// Picks the tile height and z-chunk of the fused field kernel for this mesh
-// by timing every candidate shape on the context's own buffers (median of 3
-// launches after one warm-up).  Results are cached per mesh shape and
-// precision for the life of the process.
+// Picks the field kernel (halo-loop, one-thread-per-site with its prefetch
+// depth, or TMA-staged), its tile height and z-chunk for this mesh by timing
+// every candidate on the context's own buffers (median of 3 samples of 1 to
+// 20 back-to-back launches, after one warm-up).  Results are cached per mesh
+// shape, precision and kernel choice for the life of the process.
 static memd_status autotune_fused(memd_ctx* c) {
   static std::mutex mu;
   static std::map<std::tuple<int, int, int, int, int>, FusedCfg> cache;
-  c->tma_ok = c->field_kernel != MEMD_FIELD_LDG && tma_supported(c->mesh, c->prec) &&
+  c->tma_ok = (c->field_kernel == MEMD_FIELD_AUTO || c->field_kernel == MEMD_FIELD_TMA) &&
+              tma_supported(c->mesh, c->prec) &&
               tma_make_maps(c->mesh, c->prec, c->Dbuf, c->Bbuf, c->ie, &c->tma);
   const auto key = std::make_tuple(c->mesh.n[0], c->mesh.n[1], c->mesh.n[2], c->prec,
                                    c->field_kernel * 2 + (c->tma_ok ? 1 : 0));
@@ -357,13 +362,30 @@ static memd_status autotune_fused(memd_ctx* c) {
       return MEMD_OK;
     }
   }
-  FusedCfg cand[64];
+  FusedCfg cand[160];
   int nc = 0;
-  if (c->field_kernel != MEMD_FIELD_TMA || !c->tma_ok) nc = fused_candidates(c->mesh, c->prec, cand, 32);
+  const int fk = c->field_kernel;
+  const bool want_ldg = fk == MEMD_FIELD_AUTO || fk == MEMD_FIELD_LDG ||
+                        (fk == MEMD_FIELD_TMA && !c->tma_ok);
+  const bool want_site = fk == MEMD_FIELD_AUTO || fk == MEMD_FIELD_SITE;
+  if (want_ldg) nc = fused_candidates(c->mesh, c->prec, cand, 32);
+  if (want_site) {
+    // the one-thread-per-site plain-load kernel, same tile shapes, loads 1 to
+    // 3 planes ahead
+    for (int pf = 1; pf <= 3; ++pf) {
+      FusedCfg t[32];
+      const int nt = fused_candidates(c->mesh, c->prec, t, 32);
+      for (int i = 0; i < nt; ++i) {
+        if (pf > 1 && t[i].zchunk < 4) continue;  // too few planes to run ahead
+        t[i].site = pf;
+        cand[nc++] = t[i];
+      }
+    }
+  }
   if (c->tma_ok) {
     FusedCfg t[32];
     const int nt = fused_candidates(c->mesh, 1, t, 32);  // the TMA kernel has all three heights
-    for (int i = 0; i < nt && nc < 64; ++i) {
+    for (int i = 0; i < nt && nc < 160; ++i) {
       t[i].tma = 1;
       cand[nc++] = t[i];
     }
@@ -373,6 +395,9 @@ static memd_status autotune_fused(memd_ctx* c) {
   CK(cudaEventCreate(&e1));
   float best = 1e30f;
   FusedCfg pick = fused_default(c->mesh);
+  // launches per timing sample: small meshes take a few microseconds a
+  // launch, so one launch between two events would time mostly the events
+  const int reps = c->mesh.V <= (1 << 16) ? 20 : (c->mesh.V <= (1 << 20) ? 5 : 1);
   bool tma_checked = false;
   for (int i = 0; i < nc; ++i) {
     float t[3];
@@ -394,7 +419,7 @@ static memd_status autotune_fused(memd_ctx* c) {
     }
     for (int r = 0; r < 3; ++r) {
       CK(cudaEventRecord(e0, c->stream));
-      run();
+      for (int k = 0; k < reps; ++k) run();
       CK(cudaEventRecord(e1, c->stream));
       CK(cudaEventSynchronize(e1));
       CK(cudaEventElapsedTime(&t[r], e0, e1));
@@ -482,6 +507,7 @@ memd_status memd_create(const int32_t mesh[3], const double box[3], const memd_e
   if (!(c_light * dt * std::sqrt(3.0) < a)) return MEMD_ERR_COURANT;
   if (o.precision != MEMD_FP32 && o.precision != MEMD_FP64) return MEMD_ERR_INVALID;
   if (o.self_mode < 0 || o.self_mode > 2) return MEMD_ERR_INVALID;
+  if (o.field_kernel < MEMD_FIELD_AUTO || o.field_kernel > MEMD_FIELD_SITE) return MEMD_ERR_INVALID;
   if (eps->kind < 0 || eps->kind > 4) return MEMD_ERR_INVALID;
   if ((eps->kind == MEMD_EPS_LINKS || eps->kind == MEMD_EPS_VERTICES) && !eps->values)
     return MEMD_ERR_INVALID;
@@ -1062,7 +1088,7 @@ memd_status memd_get_kernel_stats(memd_ctx* c, memd_kernel_stats* out) {
   out->field_tma = c->fcfg.tma;
   out->field_ty = c->fcfg.ty;
   out->field_zchunk = c->fcfg.zchunk;
-  out->pad = 0;
+  out->field_site = c->fcfg.site;
   return MEMD_OK;
 }
 

@@ -313,6 +313,7 @@ memd_status memd_batch_kernel_stats(memd_batch* b, memd_kernel_stats* out) {
   out->field_tma = 0;
   out->field_ty = kBatchTY;
   out->field_zchunk = 8;
+  out->field_site = b->prec == MEMD_FP32 ? kBatchPF32 : kBatchPF64;
   b->field_ms = 0.0;
   b->field_launches = 0;
   return MEMD_OK;

@@ -58,7 +58,7 @@ struct memd_ctx {
   long long field_launches = 0;
   int relax_iters_last = 0;
   int gen = 0;  // bumped by every memd_init_field (batches rebuild their tables)
-  FusedCfg fcfg{8, 1, 0};
+  FusedCfg fcfg{8, 1, 0, 0};
   int field_kernel = 0;
   TmaMaps tma{};
   bool tma_ok = false;

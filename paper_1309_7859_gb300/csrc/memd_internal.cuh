@@ -65,7 +65,9 @@ void launch_curl_D(const Mesh& m, int prec, void* D, const void* B, double coef,
 struct FusedCfg {
   int ty;
   int zchunk;
-  int tma;  // 1: TMA-staged kernel (memd_tma.cu)
+  int tma;   // 1: TMA-staged kernel (memd_tma.cu)
+  int site;  // k >= 1: one-thread-per-site kernel (k_fused_site), loads k planes ahead;
+             // 0: k_fused_curl
 };
 void launch_fused_curl(const Mesh& m, int prec, const void* Din, const void* Bin, const void* ie,
                        void* Dout, void* Bout, double cB, double cD, FusedCfg cfg,
@@ -161,6 +163,9 @@ struct StepParams {
   double coefD;   // c^2 dt / a
   double scale;   // 2^-48 / a^2
   double Vbox;
+  double inv_V;     // 1 / Vbox
+  double self_pre;  // 1 / (2 a^2): self-energy force q^2 ie sum / (2 a a)
+  double dip_unit;  // a / S: length of one sub-cell step
   double G[8];
   double Minv[9];
   int self_mode;
@@ -204,6 +209,8 @@ struct RepDesc {
   int p_first, p_ctas;                // particle CTAs of the quad kernels
 };
 constexpr int kBatchTY = 8;            // tile height of the batched field kernel
+constexpr int kBatchPF32 = 2;          // its prefetch depth in planes, FP32 fields
+constexpr int kBatchPF64 = 1;          // and FP64 fields (register bound)
 constexpr int kBatchQuadThreads = 128;  // 32 particles per CTA in the batched quad kernels
 // field update of every replica (memd_field.cu)
 void launch_fused_batch(int prec, const RepDesc* desc, const int* cta_rep, int nctas, int par,

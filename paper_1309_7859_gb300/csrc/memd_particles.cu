@@ -82,8 +82,12 @@ __device__ inline void quantize(const Mesh& m, int d, double x, int& c, int& f) 
 
 __device__ inline long long wgt(int f, int a) { return a ? (long long)f : (long long)(kS - f); }
 
+// periodic wrap of a cell index in [-n, 2n): the step kernels only ever
+// look one cell beyond a quantised cell, so no integer division is needed
+__device__ inline int wrap1(int i, int n) { return i < 0 ? i + n : (i >= n ? i - n : i); }
+
 __device__ inline int64_t link_index(const Mesh& m, int d, int ci, int cj, int ck) {
-  return (int64_t)d * m.V + vindex(m, wrapi(ci, m.n[0]), wrapi(cj, m.n[1]), wrapi(ck, m.n[2]));
+  return (int64_t)d * m.V + vindex(m, wrap1(ci, m.n[0]), wrap1(cj, m.n[1]), wrap1(ck, m.n[2]));
 }
 
 // warp-aggregated int64 atomic add into a device word
@@ -130,34 +134,43 @@ __device__ inline double unit_noise(unsigned r) {
 // (perpendicular weight); a crossed cell face splits the move over the old
 // and the new link.  Perpendicular weights are those of the moves made so
 // far (axes before d at their new cells, axes after d at their old ones).
+__device__ inline int sel3(int d, int a, int b, int c) { return d == 0 ? a : (d == 1 ? b : c); }
+
 __device__ inline void deposit_axis(const Mesh& m, int d, int q, int c0, int f0, int f1, int dc,
                                     const int cc[3], const int cf[3],
                                     unsigned long long* __restrict__ Tb) {
-  const int e1 = (d + 1) % 3, e2 = (d + 2) % 3;
+  // axis d is the lane's own (a run-time value): select sizes, strides and
+  // perpendicular coordinates instead of indexing arrays with it
+  const int e1 = d == 2 ? 0 : d + 1, e2 = d == 0 ? 2 : d - 1;
+  const int64_t st[3] = {1, (int64_t)m.n[0], (int64_t)m.n[0] * m.n[1]};
+  const int nd = sel3(d, m.n[0], m.n[1], m.n[2]);
+  const int n1 = sel3(e1, m.n[0], m.n[1], m.n[2]), n2 = sel3(e2, m.n[0], m.n[1], m.n[2]);
+  const int64_t sd = d == 0 ? st[0] : (d == 1 ? st[1] : st[2]);
+  const int64_t s1 = e1 == 0 ? st[0] : (e1 == 1 ? st[1] : st[2]);
+  const int64_t s2 = e2 == 0 ? st[0] : (e2 == 1 ? st[1] : st[2]);
+  const int v0 = sel3(e1, cc[0], cc[1], cc[2]), w0 = sel3(e2, cc[0], cc[1], cc[2]);
+  const int fv = sel3(e1, cf[0], cf[1], cf[2]), fw = sel3(e2, cf[0], cf[1], cf[2]);
+  const int64_t u0 = (int64_t)d * m.V + (int64_t)wrap1(c0, nd) * sd;
+  const int64_t u1 = (int64_t)d * m.V + (int64_t)wrap1(c0 + dc, nd) * sd;
 #pragma unroll
   for (int a2 = 0; a2 < 2; ++a2)
 #pragma unroll
     for (int a1 = 0; a1 < 2; ++a1) {
-      const long long wp = wgt(cf[e1], a1) * wgt(cf[e2], a2);
+      const long long wp = wgt(fv, a1) * wgt(fw, a2);
       if (wp == 0) continue;
-      int at[3] = {cc[0], cc[1], cc[2]};
-      at[e1] += a1;
-      at[e2] += a2;
-      at[d] = c0;
-      const int64_t l0 = link_index(m, d, at[0], at[1], at[2]);
+      const int64_t perp = (int64_t)wrap1(v0 + a1, n1) * s1 + (int64_t)wrap1(w0 + a2, n2) * s2;
+      const int64_t l0 = u0 + perp;
       if (dc == 0) {
         const long long t = -(long long)q * (long long)(f1 - f0) * wp;
         if (t) atomicAdd(&Tb[l0], (unsigned long long)t);
       } else if (dc == 1) {
-        at[d] = c0 + 1;
-        const int64_t l1 = link_index(m, d, at[0], at[1], at[2]);
+        const int64_t l1 = u1 + perp;
         const long long t0 = -(long long)q * (long long)(kS - f0) * wp;
         const long long t1 = -(long long)q * (long long)f1 * wp;
         if (t0) atomicAdd(&Tb[l0], (unsigned long long)t0);
         if (t1) atomicAdd(&Tb[l1], (unsigned long long)t1);
       } else {
-        at[d] = c0 - 1;
-        const int64_t l1 = link_index(m, d, at[0], at[1], at[2]);
+        const int64_t l1 = u1 + perp;
         const long long t0 = (long long)q * (long long)f0 * wp;
         const long long t1 = (long long)q * (long long)(kS - f1) * wp;
         if (t0) atomicAdd(&Tb[l0], (unsigned long long)t0);
@@ -253,8 +266,8 @@ __global__ void k_cic(Mesh m, Particles P, unsigned long long* __restrict__ Q) {
       for (int ax = 0; ax < 2; ++ax) {
         const long long w = wgt(f[0], ax) * wgt(f[1], ay) * wgt(f[2], az);
         if (w == 0) continue;
-        const int64_t v = vindex(m, wrapi(c[0] + ax, m.n[0]), wrapi(c[1] + ay, m.n[1]),
-                                 wrapi(c[2] + az, m.n[2]));
+        const int64_t v = vindex(m, wrap1(c[0] + ax, m.n[0]), wrap1(c[1] + ay, m.n[1]),
+                                 wrap1(c[2] + az, m.n[2]));
         atomicAdd(&Q[v], (unsigned long long)(q * w));
       }
 }
@@ -315,14 +328,15 @@ __device__ __forceinline__ void deposit_body(const Mesh& m, const StepParams& sp
 }
 
 __global__ void __launch_bounds__(kQuadThreads)
-    k_kick_drift_deposit(Mesh m, StepParams sp, Particles P, unsigned long long* __restrict__ Tb,
+    k_kick_drift_deposit(const __grid_constant__ Mesh m, const __grid_constant__ StepParams sp,
+                         Particles P, unsigned long long* __restrict__ Tb,
                          DevState* ds) {
   deposit_body(m, sp, P, Tb, ds, blockIdx.x * (int64_t)blockDim.x + threadIdx.x);
 }
 
 // prescribed move to (pos_new, img_new) with its charge transfer
 __global__ void __launch_bounds__(kQuadThreads)
-    k_move_deposit(Mesh m, Particles P, const double* __restrict__ pos_new,
+    k_move_deposit(const __grid_constant__ Mesh m, Particles P, const double* __restrict__ pos_new,
                    const int* __restrict__ img_new, unsigned long long* __restrict__ Tb,
                    DevState* ds) {
   const int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
@@ -361,8 +375,10 @@ __device__ __forceinline__ void apply_body(const Mesh& m, Particles P,
   const int* mv = P.mv + 6 * p;
   const int c0[3] = {mv[0], mv[1], mv[2]};
   const int c1[3] = {mv[3], mv[4], mv[5]};
+  // slot 2d: the d-link at the old cell along d; slot 2d+1: at the new
+  // cell, when the move crossed a face
   int64_t l[6];
-  int nl = 0;
+  bool has[6];
 #pragma unroll
   for (int d = 0; d < 3; ++d) {
     const int e1 = (d + 1) % 3, e2 = (d + 2) % 3;
@@ -374,21 +390,23 @@ __device__ __forceinline__ void apply_body(const Mesh& m, Particles P,
     at[e1] = p1 + a1;
     at[e2] = p2 + a2;
     at[d] = c0[d];
-    l[nl++] = link_index(m, d, at[0], at[1], at[2]);
-    if (c1[d] != c0[d]) {
-      at[d] = c1[d];
-      l[nl++] = link_index(m, d, at[0], at[1], at[2]);
-    }
+    l[2 * d] = link_index(m, d, at[0], at[1], at[2]);
+    has[2 * d] = true;
+    at[d] = c1[d];
+    l[2 * d + 1] = link_index(m, d, at[0], at[1], at[2]);
+    has[2 * d + 1] = c1[d] != c0[d];
   }
   long long t[6];
 #pragma unroll
-  for (int s = 0; s < 6; ++s)
-    if (s < nl) t[s] = (long long)atomicExch(&Tb[l[s]], 0ull);
+  for (int s = 0; s < 6; ++s) t[s] = has[s] ? (long long)atomicExch(&Tb[l[s]], 0ull) : 0ll;
+  // only the lane that took a link's transfer adds it, so each reduction
+  // below is the one addition to its word in this kernel: exact for the
+  // ledger, D + x rounded once for the field
 #pragma unroll
   for (int s = 0; s < 6; ++s)
-    if (s < nl && t[s] != 0) {
-      Lg[l[s]] += t[s];
-      D[l[s]] = D[l[s]] + (T)((double)t[s] * scale);
+    if (t[s] != 0) {
+      atomicAdd((unsigned long long*)&Lg[l[s]], (unsigned long long)t[s]);
+      atomicAdd(&D[l[s]], (T)((double)t[s] * scale));
     }
 }
 
@@ -406,29 +424,35 @@ struct SelfC {
   double c[3][2], dc[3][2];
 };
 
+// c(1) = 2 t (1 - t), c(0) = 1 - c(1), dc/dt = +-(4 t - 2), t = f / S
 __device__ inline SelfC self_coeffs(const int f[3]) {
   SelfC s;
+#pragma unroll
   for (int d = 0; d < 3; ++d) {
-    const double t = (double)f[d] / (double)kS;
-    s.c[d][0] = 1.0 - 2.0 * t + 2.0 * t * t;
-    s.c[d][1] = 2.0 * t - 2.0 * t * t;
+    const double t = (double)f[d] * (1.0 / (double)kS);
+    const double u = 2.0 * (t * (1.0 - t));
+    s.c[d][0] = 1.0 - u;
+    s.c[d][1] = u;
     s.dc[d][0] = 4.0 * t - 2.0;
-    s.dc[d][1] = 2.0 - 4.0 * t;
+    s.dc[d][1] = -s.dc[d][0];
   }
   return s;
 }
 
-// sum_r G(r) (derivative factor along `dir`, or none when dir < 0)
+// sum_r G(r) a_x(r_x) a_y(r_y) a_z(r_z) with the derivative factor along
+// `dir`, summed axis by axis (x first, then y, then z)
 __device__ inline double self_sum(const StepParams& sp, const SelfC& s, int dir) {
-  double u = 0.0;
-  for (int t = 0; t < 8; ++t) {
-    const int x = t & 1, y = (t >> 1) & 1, z = (t >> 2) & 1;
-    const double a0 = (dir == 0) ? s.dc[0][x] : s.c[0][x];
-    const double a1 = (dir == 1) ? s.dc[1][y] : s.c[1][y];
-    const double a2 = (dir == 2) ? s.dc[2][z] : s.c[2][z];
-    u += sp.G[t] * a0 * a1 * a2;
+  const double x0 = dir == 0 ? s.dc[0][0] : s.c[0][0], x1 = dir == 0 ? s.dc[0][1] : s.c[0][1];
+  const double y0 = dir == 1 ? s.dc[1][0] : s.c[1][0], y1 = dir == 1 ? s.dc[1][1] : s.c[1][1];
+  const double z0 = dir == 2 ? s.dc[2][0] : s.c[2][0], z1 = dir == 2 ? s.dc[2][1] : s.c[2][1];
+  double sz[2];
+#pragma unroll
+  for (int z = 0; z < 2; ++z) {
+    const double s0 = sp.G[4 * z] * x0 + sp.G[4 * z + 1] * x1;
+    const double s1 = sp.G[4 * z + 2] * x0 + sp.G[4 * z + 3] * x1;
+    sz[z] = s0 * y0 + s1 * y1;
   }
-  return u;
+  return sz[0] * z0 + sz[1] * z1;
 }
 
 // GF: mean 1/eps of the 12 cell links for every direction; DIRECT: per
@@ -459,20 +483,27 @@ __device__ inline void self_ie(const Mesh& m, const double* __restrict__ ie64, c
 // the last CTA of the gather closes the update: P of this state becomes the
 // reported one, the accumulator is cleared for the next move, and the step
 // counter advances (finish == 2)
+// The accumulator was completed by an earlier kernel; what must not be
+// overtaken are this kernel's reads of it (and of the step counter), which
+// every CTA finishes before its barrier and its acq_rel ticket.
 __device__ inline void finish_update(DevState* ds, int finish, unsigned nctas) {
   __syncthreads();
-  if (threadIdx.x == 0) {
-    __threadfence();
-    const unsigned t = atomicAdd(&ds->ticket, 1u);
+  if (threadIdx.x == 0 && threadIdx.y == 0) {
+    unsigned t;
+    asm volatile("atom.acq_rel.gpu.global.add.u32 %0, [%1], 1;"
+                 : "=r"(t)
+                 : "l"(&ds->ticket)
+                 : "memory");
     if (t == nctas - 1) {
-      __threadfence();
-      for (int d = 0; d < 3; ++d) {
-        ds->Plast[d] = (long long)atomicAdd(&ds->Pacc[d], 0ull);
-        ds->Pacc[d] = 0ull;
-      }
+      const unsigned long long p0 = ds->Pacc[0], p1 = ds->Pacc[1], p2 = ds->Pacc[2];
+      ds->Plast[0] = (long long)p0;
+      ds->Plast[1] = (long long)p1;
+      ds->Plast[2] = (long long)p2;
+      ds->Pacc[0] = 0ull;
+      ds->Pacc[1] = 0ull;
+      ds->Pacc[2] = 0ull;
       if (finish == 2) ds->step += 1;
       ds->ticket = 0u;
-      __threadfence();
     }
   }
 }
@@ -483,20 +514,55 @@ __device__ inline void finish_update(DevState* ds, int finish, unsigned nctas) {
 // term; then lane d < 3 finishes component d: q E_d, the self-energy and
 // dipole corrections, the Langevin force and the half kick.
 template <typename T>
-__device__ __forceinline__ void gather_body(const Mesh& m, const StepParams& sp, Particles P,
+__device__ __forceinline__ void gather_body(const Mesh& m, const StepParams& sp, int thermo,
+                                            double gamma, double kT, Particles P,
                                             const T* __restrict__ D, const T* __restrict__ ie,
                                             const double* __restrict__ ie64, DevState* ds,
                                             int kick, int finish, unsigned nctas, int64_t g) {
   const int64_t p = g >> 2;
   const int lane4 = (int)(g & 3);
   const bool active = p < P.n;
+  const bool comp = active && lane4 < 3;  // this lane finishes force component lane4
   const unsigned full = 0xffffffffu;
   const int a1 = lane4 & 1, a2 = lane4 >> 1;
+  // every independent load first: positions, the lane's particle data, the
+  // dipole accumulator and the step counter
+  double x3[3] = {0.0, 0.0, 0.0}, vd = 0.0, mass = 0.0, sig = 0.0, hh = 0.0;
+  int qi = 0;
+  if (active) {
+    x3[0] = P.x[3 * p];
+    x3[1] = P.x[3 * p + 1];
+    x3[2] = P.x[3 * p + 2];
+    qi = P.q[p];
+  }
+  if (comp) {
+    vd = P.v[3 * p + lane4];
+    mass = P.m[p];
+    hh = P.h[p];
+    if (thermo) sig = P.sig[p];
+  }
+  long long Pl[3] = {0, 0, 0};
+  if (comp && sp.dipole_corr) {
+    Pl[0] = (long long)ds->Pacc[0];
+    Pl[1] = (long long)ds->Pacc[1];
+    Pl[2] = (long long)ds->Pacc[2];
+  }
+  unsigned rnd = 0;
+  if (comp && thermo) {
+    const long long step = ds->step;
+    unsigned ctr[4] = {(unsigned)p, (unsigned)((unsigned long long)p >> 32), (unsigned)step,
+                       (unsigned)((unsigned long long)step >> 32)};
+    philox4x32_10(ctr, (unsigned)sp.seed, (unsigned)(sp.seed >> 32));
+    rnd = lane4 == 0 ? ctr[0] : (lane4 == 1 ? ctr[1] : ctr[2]);
+  }
   int c[3] = {0, 0, 0}, f[3] = {0, 0, 0};
   T E[3] = {T(0), T(0), T(0)};
   double iw[3] = {0.0, 0.0, 0.0}, itot = 0.0;
   if (active) {
-    for (int d = 0; d < 3; ++d) quantize(m, d, P.x[3 * p + d], c[d], f[d]);
+#pragma unroll
+    for (int d = 0; d < 3; ++d) quantize(m, d, x3[d], c[d], f[d]);
+    T Dv[3], Iv[3];
+    double I64[3] = {0.0, 0.0, 0.0};
 #pragma unroll
     for (int d = 0; d < 3; ++d) {
       const int e1 = (d + 1) % 3, e2 = (d + 2) % 3;
@@ -504,13 +570,19 @@ __device__ __forceinline__ void gather_body(const Mesh& m, const StepParams& sp,
       at[e1] += a1;
       at[e2] += a2;
       const int64_t l = link_index(m, d, at[0], at[1], at[2]);
+      Dv[d] = D[l];
+      Iv[d] = ie[l];
+      if (sp.self_mode != 0) I64[d] = ie64[l];
+    }
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+      const int e1 = (d + 1) % 3, e2 = (d + 2) % 3;
       const T w = ((T)wgt(f[e1], a1) / (T)kS) * ((T)wgt(f[e2], a2) / (T)kS);
-      E[d] = D[l] * ie[l] * w;
+      E[d] = Dv[d] * Iv[d] * w;
       if (sp.self_mode != 0) {
-        const double iv = ie64[l];
         const double wd = ((double)wgt(f[e1], a1) / (double)kS) * ((double)wgt(f[e2], a2) / (double)kS);
-        itot += iv;
-        iw[d] = iv * wd;
+        itot += I64[d];
+        iw[d] = I64[d] * wd;
       }
     }
   }
@@ -524,36 +596,33 @@ __device__ __forceinline__ void gather_body(const Mesh& m, const StepParams& sp,
   }
   itot = itot + __shfl_xor_sync(full, itot, 1);
   itot = itot + __shfl_xor_sync(full, itot, 2);
-  if (active && lane4 < 3) {
+  if (comp) {
     const int d = lane4;
-    const double q = (double)P.q[p];
-    double F = q * (double)E[d];
+    const double q = (double)qi;
+    const T Ed = d == 0 ? E[0] : (d == 1 ? E[1] : E[2]);
+    double F = q * (double)Ed;
     if (sp.self_mode != 0) {
-      const double ie_cell = itot / 12.0;
-      const double ie_d = (sp.self_mode == 2) ? iw[d] : ie_cell;
+      const double ie_cell = itot * (1.0 / 12.0);
+      const double iwd = d == 0 ? iw[0] : (d == 1 ? iw[1] : iw[2]);
+      const double ie_d = (sp.self_mode == 2) ? iwd : ie_cell;
       const SelfC sc = self_coeffs(f);
-      const double pre = q * q / (2.0 * m.a);
-      F = F + pre * ie_d * self_sum(sp, sc, d) / m.a;
+      F = F + (q * q * sp.self_pre) * ie_d * self_sum(sp, sc, d);
     }
     if (sp.dipole_corr) {
-      double Pd[3];
-      for (int e = 0; e < 3; ++e) Pd[e] = (double)(long long)ds->Pacc[e] * (m.a / (double)kS);
-      const double MP = sp.Minv[3 * d] * Pd[0] + sp.Minv[3 * d + 1] * Pd[1] + sp.Minv[3 * d + 2] * Pd[2];
-      F = F + q * MP / sp.Vbox;
+      const double MP = sp.Minv[3 * d] * ((double)Pl[0] * sp.dip_unit) +
+                        sp.Minv[3 * d + 1] * ((double)Pl[1] * sp.dip_unit) +
+                        sp.Minv[3 * d + 2] * ((double)Pl[2] * sp.dip_unit);
+      F = F + q * MP * sp.inv_V;
     }
     double Ft = F;
-    if (sp.thermo) {
-      const long long step = ds->step;
-      unsigned ctr[4] = {(unsigned)p, (unsigned)((unsigned long long)p >> 32), (unsigned)step,
-                         (unsigned)((unsigned long long)step >> 32)};
-      philox4x32_10(ctr, (unsigned)sp.seed, (unsigned)(sp.seed >> 32));
-      const double fr = -sp.gamma * P.m[p] * P.v[3 * p + d];
-      const double fn = P.sig[p] * unit_noise(ctr[d]);
+    if (thermo) {
+      const double fr = -gamma * mass * vd;
+      const double fn = sig * unit_noise(rnd);
       Ft = F + (fr + fn);
     }
     P.F[3 * p + d] = F;
     P.Ft[3 * p + d] = Ft;
-    if (kick) P.v[3 * p + d] = __dadd_rn(P.v[3 * p + d], __dmul_rn(P.h[p], Ft));
+    if (kick) P.v[3 * p + d] = __dadd_rn(vd, __dmul_rn(hh, Ft));
   }
   if (finish) finish_update(ds, finish, nctas);
 }
@@ -562,7 +631,7 @@ template <typename T>
 __global__ void __launch_bounds__(kQuadThreads)
     k_gather(Mesh m, StepParams sp, Particles P, const T* __restrict__ D, const T* __restrict__ ie,
              const double* __restrict__ ie64, DevState* ds, int kick, int finish) {
-  gather_body<T>(m, sp, P, D, ie, ie64, ds, kick, finish, gridDim.x,
+  gather_body<T>(m, sp, sp.thermo, sp.gamma, sp.kT, P, D, ie, ie64, ds, kick, finish, gridDim.x,
                  blockIdx.x * (int64_t)blockDim.x + threadIdx.x);
 }
 
@@ -577,11 +646,7 @@ __global__ void __launch_bounds__(kBatchQuadThreads)
     k_deposit_batch(const RepDesc* __restrict__ desc, const int* __restrict__ cta_rep, int thermo,
                     double gamma, double kT) {
   const RepDesc& r = desc[cta_rep[blockIdx.x]];
-  StepParams sp = r.sp;
-  sp.thermo = thermo;
-  sp.gamma = gamma;
-  sp.kT = kT;
-  deposit_body(r.m, sp, r.P, (unsigned long long*)r.Tb, r.ds, batch_local(r));
+  deposit_body(r.m, r.sp, r.P, (unsigned long long*)r.Tb, r.ds, batch_local(r));
 }
 
 template <typename T>
@@ -597,11 +662,7 @@ __global__ void __launch_bounds__(kBatchQuadThreads)
     k_gather_batch(const RepDesc* __restrict__ desc, const int* __restrict__ cta_rep, int par,
                    int thermo, double gamma, double kT) {
   const RepDesc& r = desc[cta_rep[blockIdx.x]];
-  StepParams sp = r.sp;
-  sp.thermo = thermo;
-  sp.gamma = gamma;
-  sp.kT = kT;
-  gather_body<T>(r.m, sp, r.P, (const T*)r.D[par ^ 1], (const T*)r.ie, r.ie64, r.ds, 1, 2,
+  gather_body<T>(r.m, r.sp, thermo, gamma, kT, r.P, (const T*)r.D[par ^ 1], (const T*)r.ie, r.ie64, r.ds, 1, 2,
                  (unsigned)r.p_ctas, batch_local(r));
 }
 

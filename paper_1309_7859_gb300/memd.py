@@ -105,7 +105,7 @@ class KernelStats(C.Structure):
     _fields_ = [("field_ms", C.c_double), ("field_launches", C.c_int64),
                 ("field_bytes", C.c_double), ("launches_per_step", C.c_int64),
                 ("field_tma", C.c_int32), ("field_ty", C.c_int32), ("field_zchunk", C.c_int32),
-                ("pad", C.c_int32)]
+                ("field_site", C.c_int32)]
 
 
 _lib = None
@@ -244,7 +244,7 @@ class Memd:
         o.seed = int(seed) & ((1 << 64) - 1)
         o.use_graphs = 1 if use_graphs else 0
         o.time_kernels = 1 if time_kernels else 0
-        o.field_kernel = {"auto": 0, "ldg": 1, "tma": 2}[field_kernel]
+        o.field_kernel = {"auto": 0, "ldg": 1, "tma": 2, "site": 3}[field_kernel]
         self._alloc = None
         self._stream = stream
         if use_torch:
@@ -385,9 +385,13 @@ class Memd:
     def kernel_stats(self):
         k = KernelStats()
         self._check(self._L.memd_get_kernel_stats(self._h, C.byref(k)), "memd_get_kernel_stats")
-        kind = "k_fused_tma" if k.field_tma else "k_fused_curl"
-        return StepTiming(k.field_ms, k.field_launches, k.field_bytes, k.launches_per_step,
-                          f"{kind}<ty={k.field_ty}, zchunk={k.field_zchunk}>")
+        if k.field_tma:
+            kind = f"k_fused_tma<ty={k.field_ty}, zchunk={k.field_zchunk}>"
+        elif k.field_site:
+            kind = f"k_fused_site<ty={k.field_ty}, zchunk={k.field_zchunk}, planes_ahead={k.field_site}>"
+        else:
+            kind = f"k_fused_curl<ty={k.field_ty}, zchunk={k.field_zchunk}>"
+        return StepTiming(k.field_ms, k.field_launches, k.field_bytes, k.launches_per_step, kind)
 
     def reset_kernel_stats(self):
         self._check(self._L.memd_reset_kernel_stats(self._h), "memd_reset_kernel_stats")
@@ -429,7 +433,8 @@ class Batch:
         if st != 0:
             raise MemdError(st, "memd_batch_kernel_stats failed")
         return StepTiming(k.field_ms, k.field_launches, k.field_bytes, k.launches_per_step,
-                          f"k_fused_curl_batch<ty={k.field_ty}, zchunk={k.field_zchunk}>")
+                          f"k_fused_site_batch<ty={k.field_ty}, zchunk={k.field_zchunk}, "
+                          f"planes_ahead={k.field_site}>")
 
     def close(self):
         if self._h:

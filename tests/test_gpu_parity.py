@@ -146,7 +146,7 @@ def compare_state(g, o, tol, ledger_exact=True):
                                         ((40, 20, 12), 300, SLAB),
                                         ((33, 9, 7), 60, SINX)])
 @pytest.mark.parametrize("self_mode", [O.SELF_GF, O.SELF_DIRECT, O.SELF_NONE])
-@pytest.mark.parametrize("field_kernel", ["ldg", "tma"])
+@pytest.mark.parametrize("field_kernel", ["ldg", "site", "tma"])
 def test_ten_steps_fp64(mesh, n, eps, self_mode, field_kernel):
     sysc = small_system(mesh, n, eps, dt=0.01)
     g, o = make_pair(sysc, self_mode=self_mode, field_kernel=field_kernel)
@@ -165,7 +165,7 @@ def test_ten_steps_fp64(mesh, n, eps, self_mode, field_kernel):
                                         ((40, 20, 12), 300, SLAB),
                                         ((72, 20, 6), 200, SINX),
                                         ((4, 6, 2), 8, EpsSpec("const", 0, (2.0,)))])
-@pytest.mark.parametrize("field_kernel", ["ldg", "tma"])
+@pytest.mark.parametrize("field_kernel", ["ldg", "site", "tma"])
 def test_ten_steps_fp32(mesh, n, eps, field_kernel):
     sysc = small_system(mesh, n, eps, precision="fp32", dt=0.005)
     g, o = make_pair(sysc, field_kernel=field_kernel)
@@ -240,7 +240,7 @@ def test_plain_8_full_run_matches_oracle():
     compare_state(g, o, 1e-10)
 
 
-@pytest.mark.parametrize("field_kernel", ["ldg", "tma"])
+@pytest.mark.parametrize("field_kernel", ["ldg", "site", "tma"])
 def test_slab_32_full_size_matches_oracle(field_kernel):
     # 32^3 slab, 1000 charges, FP32 fields: init on both sides, then 10 steps
     sysc = inputs.slab_32()
@@ -290,12 +290,12 @@ def test_salt_64_full_size_sampled_forces():
 
 @pytest.mark.parametrize("precision", ["fp64", "fp32"])
 def test_field_kernels_agree_on_a_large_mesh(precision):
-    # both field kernels against each other on a mesh of many tiles (ragged in
+    # the field kernels against each other on a mesh of many tiles (ragged in
     # y and z): same state, 3 steps, fields equal to rounding
     from paper_1309_7859_gb300.memd import Memd
     sysc = small_system((96, 44, 37), 2000, SLAB, precision=precision, dt=0.005)
     out = []
-    for fk in ("ldg", "tma"):
+    for fk in ("ldg", "tma", "site"):
         g = Memd(sysc.mesh, sysc.box, sysc.eps, c_light=1.0, dt=sysc.dt, precision=precision,
                  seed=3, field_kernel=fk)
         g.init_field(sysc.x, sysc.q, sysc.m, sysc.v)
@@ -306,6 +306,10 @@ def test_field_kernels_agree_on_a_large_mesh(precision):
     # different rounding of E = D / eps shows up amplified by that cancellation;
     # the bound is the FP32 field tolerance used against the oracle
     tol = 1e-13 if precision == "fp64" else 1e-5
-    for a, b in zip(out[0][:2], out[1][:2]):
-        assert rel(a, b) < tol
-    assert rel(out[0][3], out[1][3]) < tol
+    for other in out[1:]:
+        for a, b in zip(out[0][:2], other[:2]):
+            assert rel(a, b) < tol
+        assert rel(out[0][3], other[3]) < tol
+    # the two plain-load kernels share every operation: bit-identical
+    for a, b in zip(out[0], out[2]):
+        assert np.array_equal(a, b)
