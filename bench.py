@@ -215,7 +215,7 @@ def run_memd(args, world, rank, local):
     sysc = workload(args.workload, rank)
     g = Memd(sysc.mesh, sysc.box, sysc.eps, c_light=sysc.c_light, dt=sysc.dt,
              precision=sysc.precision, seed=sysc.seed, time_kernels=True, stream=stream,
-             field_kernel=args.field_kernel)
+             field_kernel=args.field_kernel, step_engine=args.step_engine)
     g.init_field(sysc.x, sysc.q, sysc.m, sysc.v)
     th = sysc.thermostat
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
@@ -287,7 +287,12 @@ def run_memd(args, world, rank, local):
                        "l2": "flushed (256 MiB write) before every timed step",
                        "parallelism": f"replicas x{world}" if world > 1 else "single system"},
             "particle_steps_per_s": world * n * args.steps / (tot_ms * 1e-3),
-            "roofline": {"bound": "hbm", "kernel": ks.field_kernel + " (B then D update, one pass)",
+            "roofline": {"bound": "hbm",
+                         "kernel": ks.field_kernel if ks.single
+                         else ks.field_kernel + " (B then D update, one pass)",
+                         "note": ("the whole step in one launch: latency bound at this size, "
+                                  "bytes are the step's field and particle state")
+                         if ks.single else "field update of the step",
                          "achieved": achieved, "peak": hbm, "unit": "GB/s",
                          "frac": achieved / hbm, "peak_kind": peak_kind, "traffic": traffic,
                          "bytes_per_launch": ks.field_bytes,
@@ -462,7 +467,7 @@ def large_mesh(N, dev, stream, args):
     sysc = workload(f"bigslab-{N}")
     g = Memd(sysc.mesh, sysc.box, sysc.eps, c_light=sysc.c_light, dt=sysc.dt,
              precision=sysc.precision, seed=sysc.seed, time_kernels=True, stream=stream,
-             field_kernel=args.field_kernel)
+             field_kernel=args.field_kernel, step_engine=args.step_engine)
     g.init_field(sysc.x, sysc.q, sysc.m, sysc.v)
     th = sysc.thermostat
     steps = max(10, min(args.steps, 50))
@@ -504,6 +509,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
     ap.add_argument("--field-kernel", default="auto", choices=["auto", "ldg", "tma", "site"])
+    ap.add_argument("--step-engine", default="auto", choices=["auto", "graph", "single"])
     ap.add_argument("--batch", type=int, default=64,
                     help="replicas of the extra batched measurement (0: skip)")
     ap.add_argument("--serve", type=int, default=128,

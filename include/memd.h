@@ -105,10 +105,18 @@ typedef struct memd_options {
                              16-byte multiples, else the plain-load kernel);
                              MEMD_FIELD_SITE: plain loads, one thread per site of the
                              tile and its halo.  All three give identical results. */
-  int32_t reserved[6];
+  int32_t step_engine;    /* MEMD_STEP_AUTO: the single launch for small systems (at
+                             most 2^17 sites and 16 particles per SM), else the graph;
+                             MEMD_STEP_GRAPH: four kernels a step (field update beside
+                             the deposition, transfers, gather); MEMD_STEP_SINGLE: the
+                             whole step in one cooperative launch with two grid
+                             barriers (when the device supports cooperative launches,
+                             else the graph).  Both give identical results. */
+  int32_t reserved[5];
 } memd_options;
 
 enum { MEMD_FIELD_AUTO = 0, MEMD_FIELD_LDG = 1, MEMD_FIELD_TMA = 2, MEMD_FIELD_SITE = 3 };
+enum { MEMD_STEP_AUTO = 0, MEMD_STEP_GRAPH = 1, MEMD_STEP_SINGLE = 2 };
 
 typedef struct memd_thermostat {
   double gamma; /* friction rate; Langevin force -gamma m v + sqrt(2 gamma m kT / dt) xi */
@@ -137,7 +145,11 @@ typedef struct memd_kernel_stats {
   int32_t field_tma;      /* field kernel chosen at create: 1 TMA-staged, 0 plain loads */
   int32_t field_ty;       /* its tile height (rows of 32 sites) */
   int32_t field_zchunk;   /* its z planes per CTA */
-  int32_t field_site;     /* 1: the one-thread-per-site plain-load kernel */
+  int32_t field_site;     /* k >= 1: the one-thread-per-site plain-load kernel, loads k
+                             planes ahead */
+  int32_t step_single;    /* 1: steps run as one cooperative launch; field_ms, field_bytes
+                             and field_launches then time that whole kernel */
+  int32_t pad;
 } memd_kernel_stats;
 
 /* Fill *opt with defaults: FP64, GF self term, dipole correction on,

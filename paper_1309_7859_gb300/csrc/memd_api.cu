@@ -102,6 +102,7 @@ StepParams memd_step_params(const memd_ctx* c, int thermo, double gamma, double 
   sp.dip_unit = c->mesh.a / (double)kS;
   for (int t = 0; t < 8; ++t) sp.G[t] = c->G[t];
   for (int t = 0; t < 9; ++t) sp.Minv[t] = c->Minv[t];
+  for (int t = 0; t < 9; ++t) sp.Mdip[t] = c->Minv[t] * sp.dip_unit * sp.inv_V;
   sp.self_mode = c->self_mode;
   sp.dipole_corr = c->dipole_corr;
   sp.thermo = thermo;
@@ -126,6 +127,8 @@ memd_status memd_check_err(memd_ctx* c) {
   CK(cudaStreamSynchronize(c->stream));
   if (err) {
     CK(cudaMemsetAsync(&c->ds->err, 0, sizeof(unsigned int), c->stream));
+    if (err & kErrTimeout)  // a grid barrier gave up: start its words afresh
+      CK(cudaMemsetAsync(&c->ds->bar_count, 0, 2 * sizeof(unsigned int), c->stream));
     CK(cudaStreamSynchronize(c->stream));
     if (err & kErrCellJump) return fail(c, MEMD_ERR_CELL_JUMP, "a charge moved more than one cell");
     if (err & kErrGauss) return fail(c, MEMD_ERR_GAUSS, "Gauss scan did not close (system not neutral)");
@@ -508,6 +511,7 @@ memd_status memd_create(const int32_t mesh[3], const double box[3], const memd_e
   if (o.precision != MEMD_FP32 && o.precision != MEMD_FP64) return MEMD_ERR_INVALID;
   if (o.self_mode < 0 || o.self_mode > 2) return MEMD_ERR_INVALID;
   if (o.field_kernel < MEMD_FIELD_AUTO || o.field_kernel > MEMD_FIELD_SITE) return MEMD_ERR_INVALID;
+  if (o.step_engine < MEMD_STEP_AUTO || o.step_engine > MEMD_STEP_SINGLE) return MEMD_ERR_INVALID;
   if (eps->kind < 0 || eps->kind > 4) return MEMD_ERR_INVALID;
   if ((eps->kind == MEMD_EPS_LINKS || eps->kind == MEMD_EPS_VERTICES) && !eps->values)
     return MEMD_ERR_INVALID;
@@ -535,6 +539,7 @@ memd_status memd_create(const int32_t mesh[3], const double box[3], const memd_e
     int ex = 0;
     c->mesh.a_pow2 = std::frexp(a, &ex) == 0.5 ? 1 : 0;
     c->mesh.inv_a = 1.0 / a;
+    c->mesh.inv_aS = c->mesh.inv_a * (double)kS;
   }
   c->Vbox = box[0] * box[1] * box[2];
   c->c = c_light;
@@ -548,6 +553,7 @@ memd_status memd_create(const int32_t mesh[3], const double box[3], const memd_e
   c->use_graphs = o.use_graphs;
   c->time_kernels = o.time_kernels;
   c->field_kernel = o.field_kernel;
+  c->step_engine = o.step_engine;
   c->alloc = o.alloc;
   c->free_fn = o.free;
   c->alloc_user = o.alloc_user;
@@ -662,6 +668,7 @@ memd_status memd_create(const int32_t mesh[3], const double box[3], const memd_e
     goto done;
   }
   s = autotune_fused(c);
+  c->coop_grid = coop_grid(c->prec, c->device);
   if (s != MEMD_OK) goto done;
 done:
   dfree(c, vals);
@@ -795,18 +802,45 @@ memd_status memd_init_field(memd_ctx* c, int64_t n, const double* pos, const int
 static memd_status record_step(memd_ctx* c, const StepParams& sp, int par, bool timed) {
   const Mesh& m = c->mesh;
   const cudaStream_t st = c->stream;
-  CK(cudaEventRecord(c->fork, st));
-  CK(cudaStreamWaitEvent(c->side, c->fork, 0));
-  launch_kick_drift_deposit(m, sp, c->P, c->Tb, c->ds, c->side);
-  CK(cudaEventRecord(c->join, c->side));
+  const bool serial = 15.0 * (double)esz(c) * (double)m.V >= kSerialFieldBytes;
+  if (!serial) {
+    CK(cudaEventRecord(c->fork, st));
+    CK(cudaStreamWaitEvent(c->side, c->fork, 0));
+    launch_kick_drift_deposit(m, sp, c->P, c->Tb, c->ds, c->side);
+    CK(cudaEventRecord(c->join, c->side));
+  }
   if (timed) CK(cudaEventRecordWithFlags(c->ev0, st, cudaEventRecordExternal));
   launch_field(c, par, sp.coefB, sp.coefD, c->fcfg);
   if (timed) CK(cudaEventRecordWithFlags(c->ev1, st, cudaEventRecordExternal));
-  CK(cudaStreamWaitEvent(st, c->join, 0));
+  if (serial)
+    launch_kick_drift_deposit(m, sp, c->P, c->Tb, c->ds, st);
+  else
+    CK(cudaStreamWaitEvent(st, c->join, 0));
   launch_apply(m, c->prec, c->P, c->Tb, c->Lg, c->Dbuf[par ^ 1], sp.scale, st);
   launch_gather(m, c->prec, sp, c->P, c->Dbuf[par ^ 1], c->ie, c->ie64, c->ds, 1, 2, st);
   CKL();
   return MEMD_OK;
+}
+
+// the whole step as one cooperative launch (same kernels' device functions)
+static memd_status record_step_coop(memd_ctx* c, const StepParams& sp, int par, bool timed) {
+  const cudaStream_t st = c->stream;
+  if (timed) CK(cudaEventRecordWithFlags(c->ev0, st, cudaEventRecordExternal));
+  const cudaError_t e = launch_step_coop(
+      c->mesh, c->prec, sp, c->P, c->Dbuf[par], c->Bbuf[par], c->ie, c->Dbuf[par ^ 1],
+      c->Bbuf[par ^ 1], c->ie64, c->Tb, c->Lg, c->ds, c->coop_grid,
+      coop_zchunk(c->mesh, c->coop_grid), st);
+  if (e != cudaSuccess) return fail(c, MEMD_ERR_CUDA, cudaGetErrorString(e));
+  if (timed) CK(cudaEventRecordWithFlags(c->ev1, st, cudaEventRecordExternal));
+  return MEMD_OK;
+}
+
+// single launch or graph of four kernels for this system (decided when the
+// step graphs are built, once the particle count is known)
+static bool want_coop(const memd_ctx* c) {
+  if (c->coop_grid <= 0 || c->step_engine == MEMD_STEP_GRAPH) return false;
+  if (c->step_engine == MEMD_STEP_SINGLE) return true;
+  return c->mesh.V <= (int64_t(1) << 17) && c->P.n <= (int64_t)16 * c->coop_grid;
 }
 
 // Errors raised by kernels of earlier batches, without blocking: the flag is
@@ -834,22 +868,40 @@ memd_status memd_step(memd_ctx* c, int64_t nsteps, const memd_thermostat* th) {
     c->graph_gamma = gamma;
     c->graph_kT = kT;
   }
+  if (!c->graph[0] && !c->graph[1]) c->coop = want_coop(c);
+  auto record = [&](int par) {
+    return c->coop ? record_step_coop(c, sp, par, timed) : record_step(c, sp, par, timed);
+  };
   for (int64_t s = 0; s < nsteps; ++s) {
     const int par = c->cur;
     harvest_timing(c);
-    if (!c->use_graphs) {
-      memd_status r = record_step(c, sp, par, timed);
+    if (!c->use_graphs || (c->coop && !c->coop_graph_ok)) {
+      memd_status r = record(par);
       if (r != MEMD_OK) return r;
     } else {
       if (!c->graph[par]) {
-        cudaGraph_t g;
+        cudaGraph_t g = nullptr;
         CK(cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal));
-        memd_status r = record_step(c, sp, par, timed);
+        memd_status r = record(par);
         cudaError_t e = cudaStreamEndCapture(c->stream, &g);
+        cudaError_t ie = cudaErrorUnknown;
+        if (r == MEMD_OK && e == cudaSuccess) ie = cudaGraphInstantiate(&c->graph[par], g, 0);
+        if (g) cudaGraphDestroy(g);
+        if (ie != cudaSuccess && c->coop) {
+          // a cooperative launch that cannot be captured or replayed: launch
+          // it directly from now on
+          cudaGetLastError();
+          c->graph[par] = nullptr;
+          c->coop_graph_ok = false;
+          memd_status r2 = record(par);
+          if (r2 != MEMD_OK) return r2;
+          c->timing_pending = timed;
+          c->cur = par ^ 1;
+          continue;
+        }
         if (r != MEMD_OK) return r;
         if (e != cudaSuccess) return fail(c, MEMD_ERR_CUDA, "graph capture");
-        CK(cudaGraphInstantiate(&c->graph[par], g, 0));
-        cudaGraphDestroy(g);
+        if (ie != cudaSuccess) return fail(c, MEMD_ERR_CUDA, "graph instantiate");
         c->graph_thermo = thermo;
         c->graph_gamma = gamma;
         c->graph_kT = kT;
@@ -1084,7 +1136,12 @@ memd_status memd_get_kernel_stats(memd_ctx* c, memd_kernel_stats* out) {
   // the fused update reads D, 1/eps, B and writes D', B' (15 values a site)
   const double e = (double)esz(c);
   out->field_bytes = 15.0 * e * (double)c->mesh.V;
-  out->launches_per_step = c->P.n > 0 ? 4 : 2;
+  // the single launch also moves each particle's state once: x, v, Ft, img
+  // read and written, F and the move written, q, m, h, sigma read, and the
+  // 12 links of its cell (D, 1/eps, 1/eps FP64) read: 460 bytes
+  if (c->coop) out->field_bytes += 460.0 * (double)c->P.n;
+  out->launches_per_step = c->coop ? 1 : (c->P.n > 0 ? 4 : 2);
+  out->step_single = c->coop ? 1 : 0;
   out->field_tma = c->fcfg.tma;
   out->field_ty = c->fcfg.ty;
   out->field_zchunk = c->fcfg.zchunk;

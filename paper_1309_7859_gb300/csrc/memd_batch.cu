@@ -154,14 +154,20 @@ memd_status build_tables(memd_batch* b) {
 
 memd_status record(memd_batch* b, int par, int thermo, double gamma, double kT, bool timed) {
   const cudaStream_t st = b->stream;
-  BCK(cudaEventRecord(b->fork, st));
-  BCK(cudaStreamWaitEvent(b->side, b->fork, 0));
-  launch_deposit_batch(b->d_desc, b->d_part_rep, b->n_part, thermo, gamma, kT, b->side);
-  BCK(cudaEventRecord(b->join, b->side));
+  const bool serial = b->field_bytes >= kSerialFieldBytes;
+  if (!serial) {
+    BCK(cudaEventRecord(b->fork, st));
+    BCK(cudaStreamWaitEvent(b->side, b->fork, 0));
+    launch_deposit_batch(b->d_desc, b->d_part_rep, b->n_part, thermo, gamma, kT, b->side);
+    BCK(cudaEventRecord(b->join, b->side));
+  }
   if (timed) BCK(cudaEventRecordWithFlags(b->ev0, st, cudaEventRecordExternal));
   launch_fused_batch(b->prec, b->d_desc, b->d_field_rep, b->n_field, par, st);
   if (timed) BCK(cudaEventRecordWithFlags(b->ev1, st, cudaEventRecordExternal));
-  BCK(cudaStreamWaitEvent(st, b->join, 0));
+  if (serial)
+    launch_deposit_batch(b->d_desc, b->d_part_rep, b->n_part, thermo, gamma, kT, st);
+  else
+    BCK(cudaStreamWaitEvent(st, b->join, 0));
   launch_apply_batch(b->prec, b->d_desc, b->d_part_rep, b->n_part, par, st);
   launch_gather_batch(b->prec, b->d_desc, b->d_part_rep, b->n_part, par, thermo, gamma, kT, st);
   BCK(cudaGetLastError());

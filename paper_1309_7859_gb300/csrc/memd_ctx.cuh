@@ -48,6 +48,10 @@ struct memd_ctx {
   bool initialised = false;
   // step graphs, one per buffer parity
   cudaGraphExec_t graph[2] = {nullptr, nullptr};
+  int step_engine = 0;   // MEMD_STEP_*
+  int coop_grid = 0;     // CTAs of the single-launch step (0: unsupported)
+  bool coop = false;     // the steps run as one cooperative launch
+  bool coop_graph_ok = true;  // its launch can be captured in a graph
   int graph_thermo = -1;
   double graph_gamma = 0, graph_kT = 0;
   cudaStream_t side = nullptr;

@@ -23,6 +23,7 @@ struct Mesh {
   double L[3];
   double inv_a;  // 1 / a; used instead of the division when a is a power of two
   int a_pow2;    // (x * inv_a == x / a exactly then)
+  double inv_aS; // S / a (exact when a is a power of two)
 };
 
 // error bits raised by kernels into a device word
@@ -41,6 +42,8 @@ struct DevState {
   long long step;              // steps since init (Langevin counter)
   unsigned int err;            // kErr* bits
   unsigned int ticket;         // blocks of the gather that have finished
+  unsigned int bar_count;      // grid barrier of the single-launch step: arrivals
+  unsigned int bar_gen;        // and its generation
   long long lsum[3];           // scratch: sum of the ledger per component
   double scal[16];             // scratch scalars for the relaxation
 };
@@ -168,6 +171,7 @@ struct StepParams {
   double dip_unit;  // a / S: length of one sub-cell step
   double G[8];
   double Minv[9];
+  double Mdip[9];   // Minv (a / S) / Vbox: dipole force per unit charge per fixed-point P
   int self_mode;
   int dipole_corr;
   int thermo;
@@ -175,6 +179,16 @@ struct StepParams {
   double kT;
   unsigned long long seed;
 };
+// single-launch step (memd_particles.cu): the whole time step in one
+// cooperative launch, for systems small enough that launch gaps dominate
+constexpr int kCoopFieldWarps = 11;                  // 34 x 10 site tile of 8 rows
+constexpr int kCoopThreads = 32 * (kCoopFieldWarps + 1);
+int coop_grid(int prec, int device);                 // CTAs of one cooperative launch, 0 if none
+int coop_zchunk(const Mesh& m, int grid);
+cudaError_t launch_step_coop(const Mesh& m, int prec, const StepParams& sp, Particles p,
+                             const void* Din, const void* Bin, const void* ie, void* Dout,
+                             void* Bout, const double* ie64, long long* Tb, long long* Lg,
+                             DevState* ds, int grid, int zchunk, cudaStream_t st);
 void launch_fold_init(const Mesh& m, Particles p, const double* pos_in, const int* img_in,
                       unsigned int* err, cudaStream_t st);
 void launch_cic(const Mesh& m, Particles p, long long* Q, long long bg, cudaStream_t st);
@@ -208,6 +222,13 @@ struct RepDesc {
   int f_first, f_tx, f_ty, f_zchunk;  // field tiles: first CTA, tiles along x, y; planes per CTA
   int p_first, p_ctas;                // particle CTAs of the quad kernels
 };
+// A field pass that moves at least this many bytes is HBM bound: the step
+// then runs the deposition after it on the same stream instead of beside it.
+// Beside it, the deposition's scattered atomics take HBM and SM slots from
+// the stencil and the pair ends later than the two in turn; after it, the
+// transfer words the deposition touches are still in L2 when the transfers
+// are applied and the forces gathered.
+constexpr double kSerialFieldBytes = 64.0 * 1024 * 1024;
 constexpr int kBatchTY = 8;            // tile height of the batched field kernel
 constexpr int kBatchPF32 = 2;          // its prefetch depth in planes, FP32 fields
 constexpr int kBatchPF64 = 1;          // and FP64 fields (register bound)

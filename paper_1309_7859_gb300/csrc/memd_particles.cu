@@ -17,6 +17,7 @@
 // position update is two IEEE roundings (a product, then a sum), never a
 // fused multiply-add.
 #include "memd_internal.cuh"
+#include "memd_site.cuh"
 
 namespace memd {
 
@@ -62,9 +63,26 @@ __device__ inline void fold(double L, double& x, int& img) {
   img += k;
 }
 
-// cell c = floor(x / a) and sub-cell step f = floor((x/a - c) S)
+// cell c = floor(x / a) and sub-cell step f = floor((x/a - c) S).  When a is
+// a power of two, x / a, x / a - c and the scaling by S are all exact, so
+// floor(x S / a) = c S + f holds both in one rounding-free product.
 __device__ inline void quantize(const Mesh& m, int d, double x, int& c, int& f) {
-  const double u = m.a_pow2 ? __dmul_rn(x, m.inv_a) : __ddiv_rn(x, m.a);
+  if (m.a_pow2) {
+    const long long W = __double2ll_rd(__dmul_rn(x, m.inv_aS));
+    const long long cw = W >> kWBits;  // floor(W / S)
+    if (cw >= (long long)m.n[d]) {
+      c = m.n[d] - 1;
+      f = (int)kS - 1;
+    } else if (cw < 0) {
+      c = 0;
+      f = 0;
+    } else {
+      c = (int)cw;
+      f = (int)(W & (long long)(kS - 1));
+    }
+    return;
+  }
+  const double u = __ddiv_rn(x, m.a);
   const double cu = floor(u);
   if (cu >= (double)m.n[d]) {
     c = m.n[d] - 1;
@@ -123,9 +141,11 @@ __device__ inline void philox4x32_10(unsigned c[4], unsigned k0, unsigned k1) {
   }
 }
 
+// xi = sqrt(3) (2 u - 1), u = (r + 1/2) 2^-32; 2 u is formed as (r + 1/2) 2^-31,
+// which is the same double (scaling by 2 is exact)
 __device__ inline double unit_noise(unsigned r) {
-  const double u = __dmul_rn(__dadd_rn((double)r, 0.5), 2.3283064365386963e-10);  // 2^-32
-  return __dmul_rn(sqrt(3.0), __dsub_rn(__dmul_rn(2.0, u), 1.0));
+  const double u2 = __dmul_rn(__dadd_rn((double)r, 0.5), 4.656612873077393e-10);  // 2^-31
+  return __dmul_rn(1.7320508075688772, __dsub_rn(u2, 1.0));
 }
 
 // ---------------------------------------------------------- charge transfer
@@ -412,7 +432,7 @@ __device__ __forceinline__ void apply_body(const Mesh& m, Particles P,
 
 template <typename T>
 __global__ void __launch_bounds__(kQuadThreads)
-    k_apply(Mesh m, Particles P, unsigned long long* __restrict__ Tb, long long* __restrict__ Lg,
+    k_apply(const __grid_constant__ Mesh m, Particles P, unsigned long long* __restrict__ Tb, long long* __restrict__ Lg,
             T* __restrict__ D, double scale) {
   apply_body<T>(m, P, Tb, Lg, D, scale, blockIdx.x * (int64_t)blockDim.x + threadIdx.x);
 }
@@ -420,20 +440,24 @@ __global__ void __launch_bounds__(kQuadThreads)
 // ------------------------------------------------------------- self energy
 // U_self = q^2 / (2 a eps) sum_{r in {0,1}^3} G(r) prod_d c_d(r_d) with
 // c(0) = (1-f)^2 + f^2, c(1) = 2 f (1-f); the correction force is +dU/dx.
+// R is the arithmetic type of the force terms: double with FP64 fields,
+// float with FP32 fields.
+template <typename R>
 struct SelfC {
-  double c[3][2], dc[3][2];
+  R c[3][2], dc[3][2];
 };
 
 // c(1) = 2 t (1 - t), c(0) = 1 - c(1), dc/dt = +-(4 t - 2), t = f / S
-__device__ inline SelfC self_coeffs(const int f[3]) {
-  SelfC s;
+template <typename R>
+__device__ inline SelfC<R> self_coeffs(const int f[3]) {
+  SelfC<R> s;
 #pragma unroll
   for (int d = 0; d < 3; ++d) {
-    const double t = (double)f[d] * (1.0 / (double)kS);
-    const double u = 2.0 * (t * (1.0 - t));
-    s.c[d][0] = 1.0 - u;
+    const R t = (R)f[d] * (R(1) / (R)kS);
+    const R u = R(2) * (t * (R(1) - t));
+    s.c[d][0] = R(1) - u;
     s.c[d][1] = u;
-    s.dc[d][0] = 4.0 * t - 2.0;
+    s.dc[d][0] = R(4) * t - R(2);
     s.dc[d][1] = -s.dc[d][0];
   }
   return s;
@@ -441,19 +465,21 @@ __device__ inline SelfC self_coeffs(const int f[3]) {
 
 // sum_r G(r) a_x(r_x) a_y(r_y) a_z(r_z) with the derivative factor along
 // `dir`, summed axis by axis (x first, then y, then z)
-__device__ inline double self_sum(const StepParams& sp, const SelfC& s, int dir) {
-  const double x0 = dir == 0 ? s.dc[0][0] : s.c[0][0], x1 = dir == 0 ? s.dc[0][1] : s.c[0][1];
-  const double y0 = dir == 1 ? s.dc[1][0] : s.c[1][0], y1 = dir == 1 ? s.dc[1][1] : s.c[1][1];
-  const double z0 = dir == 2 ? s.dc[2][0] : s.c[2][0], z1 = dir == 2 ? s.dc[2][1] : s.c[2][1];
-  double sz[2];
+template <typename R>
+__device__ inline R self_sum(const StepParams& sp, const SelfC<R>& s, int dir) {
+  const R x0 = dir == 0 ? s.dc[0][0] : s.c[0][0], x1 = dir == 0 ? s.dc[0][1] : s.c[0][1];
+  const R y0 = dir == 1 ? s.dc[1][0] : s.c[1][0], y1 = dir == 1 ? s.dc[1][1] : s.c[1][1];
+  const R z0 = dir == 2 ? s.dc[2][0] : s.c[2][0], z1 = dir == 2 ? s.dc[2][1] : s.c[2][1];
+  R sz[2];
 #pragma unroll
   for (int z = 0; z < 2; ++z) {
-    const double s0 = sp.G[4 * z] * x0 + sp.G[4 * z + 1] * x1;
-    const double s1 = sp.G[4 * z + 2] * x0 + sp.G[4 * z + 3] * x1;
+    const R s0 = (R)sp.G[4 * z] * x0 + (R)sp.G[4 * z + 1] * x1;
+    const R s1 = (R)sp.G[4 * z + 2] * x0 + (R)sp.G[4 * z + 3] * x1;
     sz[z] = s0 * y0 + s1 * y1;
   }
   return sz[0] * z0 + sz[1] * z1;
 }
+
 
 // GF: mean 1/eps of the 12 cell links for every direction; DIRECT: per
 // direction d the weighted mean of 1/eps over the 4 d-links.
@@ -555,12 +581,19 @@ __device__ __forceinline__ void gather_body(const Mesh& m, const StepParams& sp,
     philox4x32_10(ctr, (unsigned)sp.seed, (unsigned)(sp.seed >> 32));
     rnd = lane4 == 0 ? ctr[0] : (lane4 == 1 ? ctr[1] : ctr[2]);
   }
-  int c[3] = {0, 0, 0}, f[3] = {0, 0, 0};
+  // lane d < 3 quantises axis d; the quad shares the cells and sub-cell steps
+  int cq = 0, fq = 0;
+  if (comp) quantize(m, lane4, lane4 == 0 ? x3[0] : (lane4 == 1 ? x3[1] : x3[2]), cq, fq);
+  const int base = (threadIdx.x + blockDim.x * threadIdx.y) & 28;
+  int c[3], f[3];
+#pragma unroll
+  for (int e = 0; e < 3; ++e) {
+    c[e] = __shfl_sync(full, cq, base + e);
+    f[e] = __shfl_sync(full, fq, base + e);
+  }
   T E[3] = {T(0), T(0), T(0)};
   double iw[3] = {0.0, 0.0, 0.0}, itot = 0.0;
   if (active) {
-#pragma unroll
-    for (int d = 0; d < 3; ++d) quantize(m, d, x3[d], c[d], f[d]);
     T Dv[3], Iv[3];
     double I64[3] = {0.0, 0.0, 0.0};
 #pragma unroll
@@ -570,18 +603,21 @@ __device__ __forceinline__ void gather_body(const Mesh& m, const StepParams& sp,
       at[e1] += a1;
       at[e2] += a2;
       const int64_t l = link_index(m, d, at[0], at[1], at[2]);
-      Dv[d] = D[l];
+      Dv[d] = __ldcg(D + l);  // D was updated in this launch by other CTAs (single launch)
       Iv[d] = ie[l];
-      if (sp.self_mode != 0) I64[d] = ie64[l];
+      if (sp.self_mode != 0 && sizeof(T) == 8) I64[d] = ie64[l];
     }
 #pragma unroll
     for (int d = 0; d < 3; ++d) {
       const int e1 = (d + 1) % 3, e2 = (d + 2) % 3;
       const T w = ((T)wgt(f[e1], a1) / (T)kS) * ((T)wgt(f[e2], a2) / (T)kS);
       E[d] = Dv[d] * Iv[d] * w;
-      if (sp.self_mode != 0) {
+      // 1/eps of the self term: FP64 table with FP64 fields, the field's
+      // own 1/eps with FP32 fields
+      if (sizeof(T) == 4) I64[d] = (double)Iv[d];
+      if (sp.self_mode != 0) itot += I64[d];
+      if (sp.self_mode == 2) {
         const double wd = ((double)wgt(f[e1], a1) / (double)kS) * ((double)wgt(f[e2], a2) / (double)kS);
-        itot += I64[d];
         iw[d] = I64[d] * wd;
       }
     }
@@ -591,36 +627,48 @@ __device__ __forceinline__ void gather_body(const Mesh& m, const StepParams& sp,
   for (int d = 0; d < 3; ++d) {
     E[d] = E[d] + __shfl_xor_sync(full, E[d], 1);
     E[d] = E[d] + __shfl_xor_sync(full, E[d], 2);
-    iw[d] = iw[d] + __shfl_xor_sync(full, iw[d], 1);
-    iw[d] = iw[d] + __shfl_xor_sync(full, iw[d], 2);
   }
-  itot = itot + __shfl_xor_sync(full, itot, 1);
-  itot = itot + __shfl_xor_sync(full, itot, 2);
+  if (sp.self_mode == 2) {
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+      iw[d] = iw[d] + __shfl_xor_sync(full, iw[d], 1);
+      iw[d] = iw[d] + __shfl_xor_sync(full, iw[d], 2);
+    }
+  }
+  if (sp.self_mode != 0) {
+    itot = itot + __shfl_xor_sync(full, itot, 1);
+    itot = itot + __shfl_xor_sync(full, itot, 2);
+  }
   if (comp) {
+    // field force terms (q E, self energy, dipole) in R = T: FP64 with FP64
+    // fields, FP32 with FP32 fields; the Langevin force, the velocity and the
+    // kick stay FP64 (a single-precision noise of amplitude sqrt(2 gamma m
+    // kT / dt) would move the velocities by more than the field rounding)
+    using R = T;
     const int d = lane4;
-    const double q = (double)qi;
+    const R q = (R)qi;
     const T Ed = d == 0 ? E[0] : (d == 1 ? E[1] : E[2]);
-    double F = q * (double)Ed;
+    R F = q * (R)Ed;
     if (sp.self_mode != 0) {
-      const double ie_cell = itot * (1.0 / 12.0);
+      const R ie_cell = (R)itot * (R(1) / R(12));
       const double iwd = d == 0 ? iw[0] : (d == 1 ? iw[1] : iw[2]);
-      const double ie_d = (sp.self_mode == 2) ? iwd : ie_cell;
-      const SelfC sc = self_coeffs(f);
-      F = F + (q * q * sp.self_pre) * ie_d * self_sum(sp, sc, d);
+      const R ie_d = (sp.self_mode == 2) ? (R)iwd : ie_cell;
+      const SelfC<R> sc = self_coeffs<R>(f);
+      F = F + (q * q * (R)sp.self_pre) * ie_d * self_sum<R>(sp, sc, d);
     }
     if (sp.dipole_corr) {
-      const double MP = sp.Minv[3 * d] * ((double)Pl[0] * sp.dip_unit) +
-                        sp.Minv[3 * d + 1] * ((double)Pl[1] * sp.dip_unit) +
-                        sp.Minv[3 * d + 2] * ((double)Pl[2] * sp.dip_unit);
-      F = F + q * MP * sp.inv_V;
+      const R MP = (R)sp.Mdip[3 * d] * (R)Pl[0] + (R)sp.Mdip[3 * d + 1] * (R)Pl[1] +
+                   (R)sp.Mdip[3 * d + 2] * (R)Pl[2];
+      F = F + q * MP;
     }
-    double Ft = F;
+    const double Fd = (double)F;
+    double Ft = Fd;
     if (thermo) {
       const double fr = -gamma * mass * vd;
       const double fn = sig * unit_noise(rnd);
-      Ft = F + (fr + fn);
+      Ft = Fd + (fr + fn);
     }
-    P.F[3 * p + d] = F;
+    P.F[3 * p + d] = Fd;
     P.Ft[3 * p + d] = Ft;
     if (kick) P.v[3 * p + d] = __dadd_rn(vd, __dmul_rn(hh, Ft));
   }
@@ -629,7 +677,7 @@ __device__ __forceinline__ void gather_body(const Mesh& m, const StepParams& sp,
 
 template <typename T>
 __global__ void __launch_bounds__(kQuadThreads)
-    k_gather(Mesh m, StepParams sp, Particles P, const T* __restrict__ D, const T* __restrict__ ie,
+    k_gather(const __grid_constant__ Mesh m, const __grid_constant__ StepParams sp, Particles P, const T* __restrict__ D, const T* __restrict__ ie,
              const double* __restrict__ ie64, DevState* ds, int kick, int finish) {
   gather_body<T>(m, sp, sp.thermo, sp.gamma, sp.kT, P, D, ie, ie64, ds, kick, finish, gridDim.x,
                  blockIdx.x * (int64_t)blockDim.x + threadIdx.x);
@@ -664,6 +712,103 @@ __global__ void __launch_bounds__(kBatchQuadThreads)
   const RepDesc& r = desc[cta_rep[blockIdx.x]];
   gather_body<T>(r.m, r.sp, thermo, gamma, kT, r.P, (const T*)r.D[par ^ 1], (const T*)r.ie, r.ie64, r.ds, 1, 2,
                  (unsigned)r.p_ctas, batch_local(r));
+}
+
+// ---------------------------------------------------- single-launch step
+// The whole time step of one system in one cooperative launch of G CTAs:
+// warps 0-10 of every CTA run field tiles (B' then D', one-thread-per-site
+// tiles of 8 rows) while warp 11 runs the kick, drift and deposition of its
+// particles; a grid barrier; warp 11 applies the transfers; a grid barrier;
+// warp 11 gathers the forces (Langevin, half kick), and the last CTA closes
+// the step.  Same device functions, hence the same results, as the four
+// launches of the graph step.
+
+// Grid-wide barrier of a cooperative launch: each CTA releases its writes
+// with its arrival, the last CTA to arrive acquires them all and opens the
+// next generation with a release store; the others poll that word with
+// relaxed loads and acquire once it has changed.  The wait is bounded by the
+// global timer (0.2 s); a wait that runs out sets kErrTimeout and goes on,
+// the step is then void and the host resets the barrier words when it
+// reports the error.
+__device__ inline void grid_barrier(DevState* ds, unsigned nctas) {
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    unsigned gen, arrived;
+    asm volatile("ld.relaxed.gpu.global.u32 %0, [%1];" : "=r"(gen) : "l"(&ds->bar_gen) : "memory");
+    asm volatile("atom.acq_rel.gpu.global.add.u32 %0, [%1], 1;"
+                 : "=r"(arrived)
+                 : "l"(&ds->bar_count)
+                 : "memory");
+    if (arrived == nctas - 1) {
+      asm volatile("st.relaxed.gpu.global.u32 [%0], %1;" ::"l"(&ds->bar_count), "r"(0u) : "memory");
+      asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(&ds->bar_gen), "r"(gen + 1u)
+                   : "memory");
+    } else {
+      unsigned long long t0, t;
+      asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t0));
+      unsigned cur = gen;
+      for (unsigned it = 1;; ++it) {
+        asm volatile("ld.relaxed.gpu.global.u32 %0, [%1];" : "=r"(cur) : "l"(&ds->bar_gen) : "memory");
+        if (cur != gen) break;
+        if ((it & 255u) == 0u) {
+          asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+          if (t - t0 > 200000000ull) {
+            atomicOr(&ds->err, kErrTimeout);
+            break;
+          }
+        }
+      }
+      asm volatile("fence.acq_rel.gpu;" ::: "memory");
+    }
+  }
+  __syncthreads();
+}
+
+// barrier of the field warps of a CTA (named barrier 1)
+struct FieldWarpsSync {
+  __device__ void operator()() const {
+    asm volatile("barrier.sync.aligned 1, %0;" ::"n"(32 * kCoopFieldWarps) : "memory");
+  }
+};
+
+template <typename T>
+__global__ void __launch_bounds__(kCoopThreads)
+    k_step_coop(const __grid_constant__ Mesh m, const __grid_constant__ StepParams sp, Particles P,
+                const T* __restrict__ Din, const T* __restrict__ Bin, const T* __restrict__ ie,
+                T* __restrict__ Dout, T* __restrict__ Bout, const double* __restrict__ ie64,
+                unsigned long long* __restrict__ Tb, long long* __restrict__ Lg, DevState* ds,
+                int zchunk) {
+  const int tid = threadIdx.x;
+  const bool pwarp = (tid >> 5) == kCoopFieldWarps;
+  const unsigned G = gridDim.x;
+  const int lane = tid & 31;
+  const int64_t nq = 4 * P.n;  // quad lanes of all particles
+  const int64_t stride = (int64_t)G * 32;
+  if (!pwarp) {
+    const int tiles_x = (m.n[0] + 31) / 32, tiles_y = (m.n[1] + 7) / 8;
+    const int tiles_z = (m.n[2] + zchunk - 1) / zchunk;
+    const int ntiles = tiles_x * tiles_y * tiles_z;
+    const bool live = tid < 34 * 10;
+    const int tx = live ? tid % 34 : 0, ty = live ? tid / 34 : 0;
+    for (int t = blockIdx.x; t < ntiles; t += (int)G) {
+      const int tz = t / (tiles_x * tiles_y), r = t - tz * (tiles_x * tiles_y);
+      const int tyi = r / tiles_x, txi = r - tyi * tiles_x;
+      site_tile<T, 8, 1>(m, Din, Bin, ie, Dout, Bout, (T)sp.coefB, (T)sp.coefD, txi, tyi, tz,
+                         zchunk, tx, ty, live, FieldWarpsSync{});
+    }
+  } else {
+    for (int64_t b = (int64_t)blockIdx.x * 32; b < nq; b += stride)
+      deposit_body(m, sp, P, Tb, ds, b + lane);
+  }
+  grid_barrier(ds, G);
+  if (pwarp)
+    for (int64_t b = (int64_t)blockIdx.x * 32; b < nq; b += stride)
+      apply_body<T>(m, P, Tb, Lg, Dout, sp.scale, b + lane);
+  grid_barrier(ds, G);
+  if (pwarp)
+    for (int64_t b = (int64_t)blockIdx.x * 32; b < nq; b += stride)
+      gather_body<T>(m, sp, sp.thermo, sp.gamma, sp.kT, P, Dout, ie, ie64, ds, 1, 0, G, b + lane);
+  finish_update(ds, 2, G);
 }
 
 __global__ void k_step_end(DevState* ds, int advance) {
@@ -701,9 +846,9 @@ __global__ void __launch_bounds__(kRedThreads)
       for (int d = 0; d < 3; ++d) quantize(m, d, P.x[3 * p + d], c[d], f[d]);
       double ie_cell, ie_dir[3];
       self_ie(m, ie64, c, f, sp.self_mode, ie_cell, ie_dir);
-      const SelfC sc = self_coeffs(f);
+      const SelfC<double> sc = self_coeffs<double>(f);
       const double q = (double)P.q[p];
-      se += q * q / (2.0 * m.a) * ie_cell * self_sum(sp, sc, -1);
+      se += q * q / (2.0 * m.a) * ie_cell * self_sum<double>(sp, sc, -1);
     }
   }
   const double s1 = block_sum(ke, sh);
@@ -760,6 +905,54 @@ void launch_apply(const Mesh& m, int prec, Particles p, long long* Tb, long long
   else
     k_apply<double><<<nb, qt, 0, st>>>(m, p, (unsigned long long*)Tb, Lg, (double*)D,
                                                  scale);
+}
+
+int coop_grid(int prec, int device) {
+  int coop = 0, sms = 0, per = 0;
+  if (cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, device) != cudaSuccess || !coop ||
+      cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device) != cudaSuccess) {
+    cudaGetLastError();
+    return 0;
+  }
+  const cudaError_t e =
+      prec == 1 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_step_coop<float>, kCoopThreads, 0)
+                : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_step_coop<double>, kCoopThreads, 0);
+  if (e != cudaSuccess || per < 1) {
+    cudaGetLastError();
+    return 0;
+  }
+  return sms;  // one CTA per SM
+}
+
+int coop_zchunk(const Mesh& m, int grid) {
+  const int tiles_xy = ((m.n[0] + 31) / 32) * ((m.n[1] + 7) / 8);
+  int zc = 1;
+  while (zc < m.n[2] && (int64_t)tiles_xy * ((m.n[2] + zc - 1) / zc) > grid) zc *= 2;
+  return zc < m.n[2] ? zc : m.n[2];
+}
+
+cudaError_t launch_step_coop(const Mesh& m, int prec, const StepParams& sp, Particles p,
+                             const void* Din, const void* Bin, const void* ie, void* Dout,
+                             void* Bout, const double* ie64, long long* Tb, long long* Lg,
+                             DevState* ds, int grid, int zchunk, cudaStream_t st) {
+  cudaLaunchConfig_t cfg{};
+  cfg.gridDim = dim3((unsigned)grid, 1, 1);
+  cfg.blockDim = dim3(kCoopThreads, 1, 1);
+  cfg.dynamicSmemBytes = 0;
+  cfg.stream = st;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeCooperative;
+  at[0].val.cooperative = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  unsigned long long* tb = (unsigned long long*)Tb;
+  if (prec == 1)
+    return cudaLaunchKernelEx(&cfg, k_step_coop<float>, m, sp, p, (const float*)Din,
+                              (const float*)Bin, (const float*)ie, (float*)Dout, (float*)Bout, ie64,
+                              tb, Lg, ds, zchunk);
+  return cudaLaunchKernelEx(&cfg, k_step_coop<double>, m, sp, p, (const double*)Din,
+                            (const double*)Bin, (const double*)ie, (double*)Dout, (double*)Bout,
+                            ie64, tb, Lg, ds, zchunk);
 }
 
 void launch_gather(const Mesh& m, int prec, const StepParams& sp, Particles p, const void* D,

@@ -7,8 +7,10 @@ a PyTorch stream when torch is available (`use_torch=True`).
 """
 from __future__ import annotations
 
+import atexit
 import ctypes as C
 import os
+import weakref
 from dataclasses import dataclass
 
 import numpy as np
@@ -58,7 +60,7 @@ class Options(C.Structure):
                 ("cuda_stream", C.c_void_p), ("device", C.c_int32), ("use_graphs", C.c_int32),
                 ("alloc", ALLOC), ("free", FREE), ("alloc_user", C.c_void_p),
                 ("time_kernels", C.c_int32), ("field_kernel", C.c_int32),
-                ("reserved", C.c_int32 * 6)]
+                ("step_engine", C.c_int32), ("reserved", C.c_int32 * 5)]
 
 
 class Thermostat(C.Structure):
@@ -105,7 +107,7 @@ class KernelStats(C.Structure):
     _fields_ = [("field_ms", C.c_double), ("field_launches", C.c_int64),
                 ("field_bytes", C.c_double), ("launches_per_step", C.c_int64),
                 ("field_tma", C.c_int32), ("field_ty", C.c_int32), ("field_zchunk", C.c_int32),
-                ("field_site", C.c_int32)]
+                ("field_site", C.c_int32), ("step_single", C.c_int32), ("pad", C.c_int32)]
 
 
 _lib = None
@@ -209,7 +211,25 @@ class _TorchAllocator:
             return None
 
     def _free(self, user, ptr, nbytes, stream):
-        self.torch.cuda.caching_allocator_delete(int(ptr))
+        try:
+            self.torch.cuda.caching_allocator_delete(int(ptr))
+        except Exception:  # torch already torn down at interpreter exit
+            pass
+
+
+# handles still open at interpreter exit are closed while torch is alive:
+# servers and batches before the systems they use
+_live = {"server": weakref.WeakSet(), "batch": weakref.WeakSet(), "memd": weakref.WeakSet()}
+
+
+@atexit.register
+def _close_all():
+    for kind in ("server", "batch", "memd"):
+        for obj in list(_live[kind]):
+            try:
+                obj.close()
+            except Exception:
+                pass
 
 
 @dataclass
@@ -219,6 +239,7 @@ class StepTiming:
     field_bytes: float
     launches_per_step: int
     field_kernel: str = ""
+    single: bool = False
 
 
 class Memd:
@@ -227,8 +248,9 @@ class Memd:
     def __init__(self, mesh, box, eps=None, c_light=1.0, dt=0.01, precision="fp64",
                  self_mode=SELF_GF, dipole_corr=True, relax_tol=1e-12, relax_max_iter=200000,
                  seed=0, use_graphs=True, time_kernels=False, use_torch=True, stream=None,
-                 device=None, field_kernel="auto"):
+                 device=None, field_kernel="auto", step_engine="auto"):
         self._L = lib()
+        _live["memd"].add(self)
         self._h = C.c_void_p(None)
         self.mesh = tuple(int(n) for n in mesh)
         self.box = tuple(float(b) for b in box)
@@ -245,6 +267,7 @@ class Memd:
         o.use_graphs = 1 if use_graphs else 0
         o.time_kernels = 1 if time_kernels else 0
         o.field_kernel = {"auto": 0, "ldg": 1, "tma": 2, "site": 3}[field_kernel]
+        o.step_engine = {"auto": 0, "graph": 1, "single": 2}[step_engine]
         self._alloc = None
         self._stream = stream
         if use_torch:
@@ -385,13 +408,16 @@ class Memd:
     def kernel_stats(self):
         k = KernelStats()
         self._check(self._L.memd_get_kernel_stats(self._h, C.byref(k)), "memd_get_kernel_stats")
-        if k.field_tma:
+        if k.step_single:
+            kind = "k_step_coop (whole step, one cooperative launch)"
+        elif k.field_tma:
             kind = f"k_fused_tma<ty={k.field_ty}, zchunk={k.field_zchunk}>"
         elif k.field_site:
             kind = f"k_fused_site<ty={k.field_ty}, zchunk={k.field_zchunk}, planes_ahead={k.field_site}>"
         else:
             kind = f"k_fused_curl<ty={k.field_ty}, zchunk={k.field_zchunk}>"
-        return StepTiming(k.field_ms, k.field_launches, k.field_bytes, k.launches_per_step, kind)
+        return StepTiming(k.field_ms, k.field_launches, k.field_bytes, k.launches_per_step, kind,
+                          bool(k.step_single))
 
     def reset_kernel_stats(self):
         self._check(self._L.memd_reset_kernel_stats(self._h), "memd_reset_kernel_stats")
@@ -407,6 +433,7 @@ class Batch:
 
     def __init__(self, members):
         self._L = lib()
+        _live["batch"].add(self)
         self.members = list(members)
         arr = (C.c_void_p * len(self.members))(*[m._h.value for m in self.members])
         self._h = C.c_void_p(None)
@@ -455,6 +482,7 @@ class Server:
     def __init__(self, precision="fp32", budget_bytes=8 << 30, max_slots=64, quantum=50,
                  thermostat=None, use_torch=True, stream=None):
         self._L = lib()
+        _live["server"].add(self)
         o = ServerOptions()
         self._L.memd_server_default_options(C.byref(o))
         o.precision = FP32 if precision == "fp32" else FP64

@@ -40,12 +40,18 @@ def oracle_eps(e):
     return d
 
 
-def make_pair(sysc, self_mode=1, dipole_corr=1, precision=None, init=True, field_kernel="auto"):
+# (step engine, field kernel) pairs: the graph of four kernels with each
+# field kernel, and the single cooperative launch (its own field tiles)
+ENGINES = [("graph", "ldg"), ("graph", "site"), ("graph", "tma"), ("single", "auto")]
+
+
+def make_pair(sysc, self_mode=1, dipole_corr=1, precision=None, init=True, field_kernel="auto",
+              step_engine="auto"):
     from paper_1309_7859_gb300.memd import Memd
     prec = precision or sysc.precision
     g = Memd(sysc.mesh, sysc.box, sysc.eps, c_light=sysc.c_light, dt=sysc.dt, precision=prec,
              self_mode=self_mode, dipole_corr=dipole_corr, seed=sysc.seed,
-             field_kernel=field_kernel)
+             field_kernel=field_kernel, step_engine=step_engine)
     o = O.OracleSystem(sysc.mesh, sysc.box, eps=oracle_eps(sysc.eps), c_light=sysc.c_light,
                        dt=sysc.dt, self_mode=self_mode, dipole_corr=dipole_corr, seed=sysc.seed)
     if init:
@@ -146,10 +152,10 @@ def compare_state(g, o, tol, ledger_exact=True):
                                         ((40, 20, 12), 300, SLAB),
                                         ((33, 9, 7), 60, SINX)])
 @pytest.mark.parametrize("self_mode", [O.SELF_GF, O.SELF_DIRECT, O.SELF_NONE])
-@pytest.mark.parametrize("field_kernel", ["ldg", "site", "tma"])
-def test_ten_steps_fp64(mesh, n, eps, self_mode, field_kernel):
+@pytest.mark.parametrize("engine,field_kernel", ENGINES)
+def test_ten_steps_fp64(mesh, n, eps, self_mode, engine, field_kernel):
     sysc = small_system(mesh, n, eps, dt=0.01)
-    g, o = make_pair(sysc, self_mode=self_mode, field_kernel=field_kernel)
+    g, o = make_pair(sysc, self_mode=self_mode, field_kernel=field_kernel, step_engine=engine)
     load_oracle_state(g, o)
     assert rel(g.forces(), o.particles("F")) < 1e-12
     o.step(10, thermostat=(1.0, 1.0))
@@ -165,10 +171,10 @@ def test_ten_steps_fp64(mesh, n, eps, self_mode, field_kernel):
                                         ((40, 20, 12), 300, SLAB),
                                         ((72, 20, 6), 200, SINX),
                                         ((4, 6, 2), 8, EpsSpec("const", 0, (2.0,)))])
-@pytest.mark.parametrize("field_kernel", ["ldg", "site", "tma"])
-def test_ten_steps_fp32(mesh, n, eps, field_kernel):
+@pytest.mark.parametrize("engine,field_kernel", ENGINES)
+def test_ten_steps_fp32(mesh, n, eps, engine, field_kernel):
     sysc = small_system(mesh, n, eps, precision="fp32", dt=0.005)
-    g, o = make_pair(sysc, field_kernel=field_kernel)
+    g, o = make_pair(sysc, field_kernel=field_kernel, step_engine=engine)
     load_oracle_state(g, o)
     o.step(10, thermostat=(1.0, 1.0))
     g.step(10, thermostat=(1.0, 1.0))
@@ -240,16 +246,17 @@ def test_plain_8_full_run_matches_oracle():
     compare_state(g, o, 1e-10)
 
 
-@pytest.mark.parametrize("field_kernel", ["ldg", "site", "tma"])
-def test_slab_32_full_size_matches_oracle(field_kernel):
+@pytest.mark.parametrize("engine,field_kernel", ENGINES)
+def test_slab_32_full_size_matches_oracle(engine, field_kernel):
     # 32^3 slab, 1000 charges, FP32 fields: init on both sides, then 10 steps
     sysc = inputs.slab_32()
-    g, o = make_pair(sysc, field_kernel=field_kernel)
+    g, o = make_pair(sysc, field_kernel=field_kernel, step_engine=engine)
     _, _, Lg = g.fields()
     assert np.array_equal(Lg, o.field("Lg"))
     load_oracle_state(g, o)
     o.step(10, thermostat=sysc.thermostat)
     g.step(10, thermostat=sysc.thermostat)
+    assert g.kernel_stats().single == (engine == "single")   # the engine is chosen at the first step
     compare_state(g, o, 1e-5, ledger_exact=False)
 
 
@@ -313,3 +320,30 @@ def test_field_kernels_agree_on_a_large_mesh(precision):
     # the two plain-load kernels share every operation: bit-identical
     for a, b in zip(out[0], out[2]):
         assert np.array_equal(a, b)
+
+
+@pytest.mark.parametrize("mesh,n,eps,precision", [((8, 8, 8), 16, EpsSpec("const", 0, (1.0,)), "fp64"),
+                                                  ((40, 20, 12), 300, SLAB, "fp32"),
+                                                  ((24, 24, 24), 5000, SLAB, "fp32"),
+                                                  ((72, 20, 6), 200, SINX, "fp64"),
+                                                  ((4, 6, 2), 8, EpsSpec("const", 0, (2.0,)), "fp32")])
+def test_step_engines_bit_identical(mesh, n, eps, precision):
+    # the single cooperative launch and the graph of four kernels run the same
+    # device functions: 20 thermostatted steps give identical bits, also with
+    # several particle passes per CTA (5000 charges) and ragged tiles
+    from paper_1309_7859_gb300.memd import Memd
+    sysc = small_system(mesh, n, eps, precision=precision, dt=0.005)
+    out = []
+    for engine in ("graph", "single"):
+        g = Memd(sysc.mesh, sysc.box, sysc.eps, c_light=1.0, dt=sysc.dt, precision=precision,
+                 seed=5, step_engine=engine, field_kernel="site")
+        g.init_field(sysc.x, sysc.q, sysc.m, sysc.v)
+        g.step(20, thermostat=(1.0, 1.0))
+        assert g.kernel_stats().single == (engine == "single")
+        D, B, Lg = g.fields()
+        x, v, img = g.particles()
+        e = g.energy()
+        out.append((D, B, Lg, x, v, img, g.forces(), e["total"], e["P0"], e["step"]))
+        g.close()
+    for a, b in zip(out[0], out[1]):
+        assert np.array_equal(np.asarray(a), np.asarray(b))
