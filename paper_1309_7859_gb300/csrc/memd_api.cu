@@ -373,9 +373,9 @@ static memd_status autotune_fused(memd_ctx* c) {
   const bool want_site = fk == MEMD_FIELD_AUTO || fk == MEMD_FIELD_SITE;
   if (want_ldg) nc = fused_candidates(c->mesh, c->prec, cand, 32);
   if (want_site) {
-    // the one-thread-per-site plain-load kernel, same tile shapes, loads 1 to
-    // 3 planes ahead
-    for (int pf = 1; pf <= 3; ++pf) {
+    // the one-thread-per-site plain-load kernel, same tile shapes, loads 1 or
+    // 2 planes ahead
+    for (int pf = 1; pf <= 2; ++pf) {
       FusedCfg t[32];
       const int nt = fused_candidates(c->mesh, c->prec, t, 32);
       for (int i = 0; i < nt; ++i) {

@@ -631,9 +631,7 @@ void site_launch_t(const Mesh& m, const void* Din, const void* Bin, const void* 
 template <typename T, int TY>
 void site_launch_pf(int pf, const Mesh& m, const void* Din, const void* Bin, const void* ie,
                     void* Dout, void* Bout, double cB, double cD, int zchunk, cudaStream_t st) {
-  if (pf >= 3)
-    site_launch_t<T, TY, 3>(m, Din, Bin, ie, Dout, Bout, cB, cD, zchunk, st);
-  else if (pf == 2)
+  if (pf >= 2)
     site_launch_t<T, TY, 2>(m, Din, Bin, ie, Dout, Bout, cB, cD, zchunk, st);
   else
     site_launch_t<T, TY, 1>(m, Din, Bin, ie, Dout, Bout, cB, cD, zchunk, st);
