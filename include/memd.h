@@ -259,8 +259,11 @@ memd_status memd_synchronize(memd_ctx *ctx);
  * Re-initialising a member is noticed at the next batch step. */
 typedef struct memd_batch memd_batch;
 
-/* Group count >= 1 initialised contexts.  Errors: INVALID (mixed device,
- * precision or stream, or a member not initialised), OOM, CUDA. */
+/* Group count >= 1 initialised contexts.  The field tiles of the batched
+ * kernel (tile height 4 or 8 rows, 1 or 2 planes loaded ahead, 4 to 32
+ * planes per CTA) are chosen here by timing each shape on the members' own
+ * buffers, which leaves their state unchanged.  Errors: INVALID (mixed
+ * device, precision or stream, or a member not initialised), OOM, CUDA. */
 memd_status memd_batch_create(int32_t count, memd_ctx *const *members, memd_batch **out);
 
 /* Advance every member by nsteps steps (th NULL: constant energy).

@@ -34,6 +34,7 @@ struct memd_batch {
   int* d_part_rep = nullptr;
   int n_field = 0, n_part = 0;
   double field_bytes = 0.0;
+  int f_ty = kBatchTY, f_pf = kBatchPF32, f_z = kBatchZ;  // field tiles (autotuned)
   cudaGraphExec_t graph[2] = {nullptr, nullptr};
   int g_thermo = -1;
   double g_gamma = 0.0, g_kT = 0.0;
@@ -122,8 +123,8 @@ memd_status build_tables(memd_batch* b) {
     d.Tb = c->Tb;
     d.ds = c->ds;
     d.f_tx = (c->mesh.n[0] + 31) / 32;
-    d.f_ty = (c->mesh.n[1] + kBatchTY - 1) / kBatchTY;
-    d.f_zchunk = std::min(c->mesh.n[2], 8);
+    d.f_ty = (c->mesh.n[1] + b->f_ty - 1) / b->f_ty;
+    d.f_zchunk = std::min(c->mesh.n[2], b->f_z);
     const int nzc = (c->mesh.n[2] + d.f_zchunk - 1) / d.f_zchunk;
     d.f_first = (int)frep.size();
     for (int t = 0; t < d.f_tx * d.f_ty * nzc; ++t) frep.push_back(r);
@@ -152,6 +153,89 @@ memd_status build_tables(memd_batch* b) {
   return MEMD_OK;
 }
 
+// Reads a scratch buffer larger than L2, leaving L2 full of clean lines of
+// it: the field update timed next starts from DRAM, as in a step.
+__global__ void k_read_flush(const float4* __restrict__ p, size_t n4, float* sink) {
+  float acc = 0.f;
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n4;
+       i += (size_t)gridDim.x * blockDim.x) {
+    const float4 v = p[i];
+    acc += v.x + v.y + v.z + v.w;
+  }
+  if (acc == 1234.5f) *sink = acc;  // keeps the loads
+}
+
+// Field tiles of the batched kernel: tile height 4 or 8 rows, loads 1 or 2
+// planes ahead, 4 to 32 planes per CTA, timed on the members' buffers (the
+// update reads the current parity and writes the other one, which the next
+// step overwrites with the same values).  Each sample is one launch after
+// a 256 MiB read that evicts L2; median of 3 samples after a warm-up.
+memd_status autotune_batch(memd_batch* b) {
+  static const int tys[2] = {4, 8}, zs[4] = {4, 8, 16, 32};
+  const int pfs = b->prec == MEMD_FP32 ? 2 : 1;  // FP64: one plane ahead (registers)
+  const size_t flush_bytes = size_t(256) << 20;
+  void* flush = nullptr;
+  if (b->alloc) {
+    flush = b->alloc(b->alloc_user, flush_bytes, (void*)b->stream);
+  } else if (cudaMalloc(&flush, flush_bytes) != cudaSuccess) {
+    cudaGetLastError();
+    flush = nullptr;
+  }
+  if (!flush) return build_tables(b);  // no room to tune: keep the defaults
+  cudaMemsetAsync(flush, 0, flush_bytes, b->stream);
+  cudaEvent_t e0, e1;
+  BCK(cudaEventCreate(&e0));
+  BCK(cudaEventCreate(&e1));
+  float best = 1e30f;
+  int bt = b->f_ty, bpf = b->f_pf, bz = b->f_z;
+  memd_status s = MEMD_OK;
+  for (int a = 0; a < 2 && s == MEMD_OK; ++a)
+    for (int pf = 1; pf <= pfs && s == MEMD_OK; ++pf)
+      for (int zi = 0; zi < 4 && s == MEMD_OK; ++zi) {
+        b->f_ty = tys[a];
+        b->f_pf = pf;
+        b->f_z = zs[zi];
+        s = build_tables(b);
+        if (s != MEMD_OK) break;
+        launch_fused_batch(b->prec, b->d_desc, b->d_field_rep, b->n_field, 0, b->f_ty, b->f_pf,
+                           b->stream);
+        float t[3];
+        for (int r = 0; r < 3; ++r) {
+          k_read_flush<<<4 * 152, 512, 0, b->stream>>>((const float4*)flush, flush_bytes / 16,
+                                                        (float*)flush);
+          cudaEventRecord(e0, b->stream);
+          launch_fused_batch(b->prec, b->d_desc, b->d_field_rep, b->n_field, 0, b->f_ty, b->f_pf,
+                             b->stream);
+          cudaEventRecord(e1, b->stream);
+          cudaEventSynchronize(e1);
+          cudaEventElapsedTime(&t[r], e0, e1);
+        }
+        if (cudaGetLastError() != cudaSuccess) {
+          s = bfail(b, MEMD_ERR_CUDA, "batch field autotune");
+          break;
+        }
+        const float med = std::max(std::min(t[0], t[1]), std::min(std::max(t[0], t[1]), t[2]));
+        if (med < best) {
+          best = med;
+          bt = b->f_ty;
+          bpf = b->f_pf;
+          bz = b->f_z;
+        }
+      }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  cudaStreamSynchronize(b->stream);
+  if (b->free_fn)
+    b->free_fn(b->alloc_user, flush, flush_bytes, (void*)b->stream);
+  else
+    cudaFree(flush);
+  if (s != MEMD_OK) return s;
+  b->f_ty = bt;
+  b->f_pf = bpf;
+  b->f_z = bz;
+  return build_tables(b);
+}
+
 memd_status record(memd_batch* b, int par, int thermo, double gamma, double kT, bool timed) {
   const cudaStream_t st = b->stream;
   const bool serial = b->field_bytes >= kSerialFieldBytes;
@@ -162,7 +246,7 @@ memd_status record(memd_batch* b, int par, int thermo, double gamma, double kT, 
     BCK(cudaEventRecord(b->join, b->side));
   }
   if (timed) BCK(cudaEventRecordWithFlags(b->ev0, st, cudaEventRecordExternal));
-  launch_fused_batch(b->prec, b->d_desc, b->d_field_rep, b->n_field, par, st);
+  launch_fused_batch(b->prec, b->d_desc, b->d_field_rep, b->n_field, par, b->f_ty, b->f_pf, st);
   if (timed) BCK(cudaEventRecordWithFlags(b->ev1, st, cudaEventRecordExternal));
   if (serial)
     launch_deposit_batch(b->d_desc, b->d_part_rep, b->n_part, thermo, gamma, kT, st);
@@ -188,23 +272,9 @@ void harvest(memd_batch* b) {
 
 }  // namespace
 
-extern "C" {
-
-void memd_batch_destroy(memd_batch* b) {
-  if (!b) return;
-  cudaSetDevice(b->device);
-  if (b->stream) cudaStreamSynchronize(b->stream);
-  drop(b);
-  free_tables(b);
-  if (b->fork) cudaEventDestroy(b->fork);
-  if (b->join) cudaEventDestroy(b->join);
-  if (b->ev0) cudaEventDestroy(b->ev0);
-  if (b->ev1) cudaEventDestroy(b->ev1);
-  if (b->side) cudaStreamDestroy(b->side);
-  delete b;
-}
-
-memd_status memd_batch_create(int32_t count, memd_ctx* const* members, memd_batch** out) {
+// the batch, with its field tiles autotuned (tune) or the defaults
+memd_status memd_batch_create_opt(int32_t count, memd_ctx* const* members, memd_batch** out,
+                                  bool tune) {
   if (!out) return MEMD_ERR_INVALID;
   *out = nullptr;
   if (count < 1 || !members) return MEMD_ERR_INVALID;
@@ -236,7 +306,8 @@ memd_status memd_batch_create(int32_t count, memd_ctx* const* members, memd_batc
   } else {
     // members' own queued work comes first
     for (memd_ctx* c : b->m) cudaStreamSynchronize(c->stream);
-    s = build_tables(b);
+    b->f_pf = b->prec == MEMD_FP32 ? kBatchPF32 : kBatchPF64;
+    s = tune ? autotune_batch(b) : build_tables(b);
   }
   if (s != MEMD_OK) {
     memd_batch_destroy(b);
@@ -244,6 +315,26 @@ memd_status memd_batch_create(int32_t count, memd_ctx* const* members, memd_batc
   }
   *out = b;
   return MEMD_OK;
+}
+
+extern "C" {
+
+void memd_batch_destroy(memd_batch* b) {
+  if (!b) return;
+  cudaSetDevice(b->device);
+  if (b->stream) cudaStreamSynchronize(b->stream);
+  drop(b);
+  free_tables(b);
+  if (b->fork) cudaEventDestroy(b->fork);
+  if (b->join) cudaEventDestroy(b->join);
+  if (b->ev0) cudaEventDestroy(b->ev0);
+  if (b->ev1) cudaEventDestroy(b->ev1);
+  if (b->side) cudaStreamDestroy(b->side);
+  delete b;
+}
+
+memd_status memd_batch_create(int32_t count, memd_ctx* const* members, memd_batch** out) {
+  return memd_batch_create_opt(count, members, out, true);
 }
 
 memd_status memd_batch_step(memd_batch* b, int64_t nsteps, const memd_thermostat* th) {
@@ -317,9 +408,9 @@ memd_status memd_batch_kernel_stats(memd_batch* b, memd_kernel_stats* out) {
   out->field_bytes = b->field_bytes;
   out->launches_per_step = 4;
   out->field_tma = 0;
-  out->field_ty = kBatchTY;
-  out->field_zchunk = 8;
-  out->field_site = b->prec == MEMD_FP32 ? kBatchPF32 : kBatchPF64;
+  out->field_ty = b->f_ty;
+  out->field_zchunk = b->f_z;
+  out->field_site = b->f_pf;
   b->field_ms = 0.0;
   b->field_launches = 0;
   return MEMD_OK;

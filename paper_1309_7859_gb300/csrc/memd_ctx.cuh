@@ -78,3 +78,7 @@ void memd_dfree(memd_ctx* c, void* p);
 size_t memd_esz(const memd_ctx* c);
 memd::StepParams memd_step_params(const memd_ctx* c, int thermo, double gamma, double kT);
 memd_status memd_check_err(memd_ctx* c);
+// memd_batch.cu, for the server: a batch whose field tiles are autotuned
+// (tune) or left at their defaults
+memd_status memd_batch_create_opt(int32_t count, memd_ctx* const* members, memd_batch** out,
+                                  bool tune);

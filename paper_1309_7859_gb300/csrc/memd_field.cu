@@ -689,15 +689,35 @@ FusedCfg fused_default(const Mesh& m) {
   return c;
 }
 
+namespace {
+template <typename T, int TY, int PF>
+void batch_launch_t(const RepDesc* desc, const int* cta_rep, int nctas, int par, cudaStream_t st) {
+  k_fused_site_batch<T, TY, PF><<<nctas, dim3(34, TY + 2, 1), 0, st>>>(desc, cta_rep, par);
+}
+template <typename T>
+void batch_launch_ty(const RepDesc* desc, const int* cta_rep, int nctas, int par, int ty, int pf,
+                     cudaStream_t st) {
+  if (ty == 4) {
+    if (pf >= 2)
+      batch_launch_t<T, 4, 2>(desc, cta_rep, nctas, par, st);
+    else
+      batch_launch_t<T, 4, 1>(desc, cta_rep, nctas, par, st);
+  } else {
+    if (pf >= 2)
+      batch_launch_t<T, 8, 2>(desc, cta_rep, nctas, par, st);
+    else
+      batch_launch_t<T, 8, 1>(desc, cta_rep, nctas, par, st);
+  }
+}
+}  // namespace
+
 void launch_fused_batch(int prec, const RepDesc* desc, const int* cta_rep, int nctas, int par,
-                        cudaStream_t st) {
+                        int ty, int pf, cudaStream_t st) {
   if (nctas <= 0) return;
   if (prec == 1)
-    k_fused_site_batch<float, kBatchTY, kBatchPF32><<<nctas, dim3(34, kBatchTY + 2, 1), 0, st>>>(
-        desc, cta_rep, par);
+    batch_launch_ty<float>(desc, cta_rep, nctas, par, ty, pf, st);
   else
-    k_fused_site_batch<double, kBatchTY, kBatchPF64><<<nctas, dim3(34, kBatchTY + 2, 1), 0, st>>>(
-        desc, cta_rep, par);
+    batch_launch_ty<double>(desc, cta_rep, nctas, par, ty, pf, st);
 }
 
 int fused_candidates(const Mesh& m, int prec, FusedCfg* out, int cap) {

@@ -229,13 +229,14 @@ struct RepDesc {
 // transfer words the deposition touches are still in L2 when the transfers
 // are applied and the forces gathered.
 constexpr double kSerialFieldBytes = 64.0 * 1024 * 1024;
-constexpr int kBatchTY = 8;            // tile height of the batched field kernel
+constexpr int kBatchTY = 8;            // default tile height of the batched field kernel
 constexpr int kBatchPF32 = 2;          // its prefetch depth in planes, FP32 fields
 constexpr int kBatchPF64 = 1;          // and FP64 fields (register bound)
+constexpr int kBatchZ = 8;             // and its planes per CTA
 constexpr int kBatchQuadThreads = 128;  // 32 particles per CTA in the batched quad kernels
 // field update of every replica (memd_field.cu)
 void launch_fused_batch(int prec, const RepDesc* desc, const int* cta_rep, int nctas, int par,
-                        cudaStream_t st);
+                        int ty, int pf, cudaStream_t st);
 // particle kernels of every replica (memd_particles.cu); thermostat from the arguments
 void launch_deposit_batch(const RepDesc* desc, const int* cta_rep, int nctas, int thermo,
                           double gamma, double kT, cudaStream_t st);
