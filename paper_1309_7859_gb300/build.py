@@ -31,6 +31,7 @@ SOURCES = {
     "memd_tma.cu": [],
     "memd_batch.cu": [],
     "memd_server.cu": [],
+    "memd_mg.cu": [],
 }
 
 

@@ -258,6 +258,25 @@ inline unsigned nb(int64_t n) { return (unsigned)((n + 255) / 256); }
 
 }  // namespace
 
+// inverse of a 3 x 3 matrix (row major); false if singular
+static bool invert3(const double a[9], double out[9]) {
+  const double c00 = a[4] * a[8] - a[5] * a[7], c01 = a[5] * a[6] - a[3] * a[8],
+               c02 = a[3] * a[7] - a[4] * a[6];
+  const double det = a[0] * c00 + a[1] * c01 + a[2] * c02;
+  if (!(std::fabs(det) > 0.0)) return false;
+  const double id = 1.0 / det;
+  out[0] = c00 * id;
+  out[1] = (a[2] * a[7] - a[1] * a[8]) * id;
+  out[2] = (a[1] * a[5] - a[2] * a[4]) * id;
+  out[3] = c01 * id;
+  out[4] = (a[0] * a[8] - a[2] * a[6]) * id;
+  out[5] = (a[2] * a[3] - a[0] * a[5]) * id;
+  out[6] = c02 * id;
+  out[7] = (a[1] * a[6] - a[0] * a[7]) * id;
+  out[8] = (a[0] * a[4] - a[1] * a[3]) * id;
+  return true;
+}
+
 static memd_status relax(memd_ctx* c, double* D64, double tol, int maxit) {
   const Mesh& m = c->mesh;
   const int64_t n = 3 * m.V;
@@ -295,14 +314,13 @@ static memd_status relax(memd_ctx* c, double* D64, double tol, int maxit) {
     k_set_scalar<<<1, 32, 0, st>>>(sc, kS_DONE, 0.0);
     k_set_scalar<<<1, 32, 0, st>>>(sc, kS_TOL, 0.5 * tol);
   };
-  bool ok = false, frozen = false;
-  k_set_scalar<<<1, 32, 0, st>>>(sc, kS_DONE, 0.0);
-  memd_status s = check(ok, frozen);
-  int it = 0, parity = 0;
-  if (s == MEMD_OK && !ok) {
-    restart();
-    parity = 0;
-    while (it < maxit) {
+  // kChunk iterations (an even count, so that the r.z slots are back in
+  // place) between checks of the true residual; the chunk is captured once
+  // as a CUDA graph and replayed, or launched directly if capture fails
+  constexpr int kChunk = 24;
+  auto chunk = [&]() {
+    for (int j = 0; j < kChunk; ++j) {
+      const int parity = j & 1;
       const int old_slot = kS_RZ0 + parity, new_slot = kS_RZ0 + (parity ^ 1);
       // four launches per iteration: transpose map, operator with p.w,
       // update with r.z and max|r|, direction (see memd_field.cu)
@@ -310,22 +328,42 @@ static memd_status relax(memd_ctx* c, double* D64, double tol, int maxit) {
       launch_cg_apply(m, w, u, c->ie64, p, part, st);
       launch_cg_update(n, D64, u, r, w, z, diag, part, sc, old_slot, part + R, part + 2 * R, st);
       launch_cg_direction(n, p, z, sc, part + R, part + 2 * R, new_slot, old_slot, st);
-      parity ^= 1;
-      ++it;
-      if (it % 25 == 0 || it == maxit) {
-        if (cudaGetLastError() != cudaSuccess) {
-          dfree(c, buf);
-          return fail(c, MEMD_ERR_CUDA, "relaxation kernel launch");
-        }
-        s = check(ok, frozen);
-        if (s != MEMD_OK || ok) break;
-        if (frozen) {  // the recursion converged but the true residual did not
-          restart();
-          parity = 0;
-        }
+    }
+  };
+  cudaGraphExec_t gexec = nullptr;
+  bool ok = false, frozen = false;
+  k_set_scalar<<<1, 32, 0, st>>>(sc, kS_DONE, 0.0);
+  memd_status s = check(ok, frozen);
+  int it = 0;
+  if (s == MEMD_OK && !ok) {
+    restart();
+    if (c->use_graphs) {
+      cudaGraph_t g = nullptr;
+      if (cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal) == cudaSuccess) {
+        chunk();
+        if (cudaStreamEndCapture(st, &g) != cudaSuccess ||
+            cudaGraphInstantiate(&gexec, g, 0) != cudaSuccess)
+          gexec = nullptr;
+        if (g) cudaGraphDestroy(g);
       }
+      cudaGetLastError();
+    }
+    while (it < maxit) {
+      if (gexec)
+        CK(cudaGraphLaunch(gexec, st));
+      else
+        chunk();
+      it += kChunk;
+      if (cudaGetLastError() != cudaSuccess) {
+        s = fail(c, MEMD_ERR_CUDA, "relaxation kernel launch");
+        break;
+      }
+      s = check(ok, frozen);
+      if (s != MEMD_OK || ok) break;
+      if (frozen) restart();  // the recursion converged but the true residual did not
     }
   }
+  if (gexec) cudaGraphExecDestroy(gexec);
   c->relax_iters_last = it;
   dfree(c, buf);
   if (s != MEMD_OK) return s;
@@ -404,7 +442,8 @@ static memd_status autotune_fused(memd_ctx* c) {
   bool tma_checked = false;
   for (int i = 0; i < nc; ++i) {
     float t[3];
-    auto run = [&]() { launch_field(c, 0, 0.0, 0.0, cand[i]); };
+    // reads the current parity, writes a copy of it into the other one
+    auto run = [&]() { launch_field(c, c->cur, 0.0, 0.0, cand[i]); };
     if (cand[i].tma && !c->tma_ok) continue;
     run();
     if (cand[i].tma && !tma_checked) {
@@ -632,14 +671,32 @@ memd_status memd_create(const int32_t mesh[3], const double box[3], const memd_e
     }
     s = check_err(c);
     if (s != MEMD_OK) goto done;
-    // effective permittivity tensor (Sec. V): relax a charge-free field of
-    // mean D = e_d; the mean of E is column d of eps_eff^-1
+    // effective permittivity tensor (Sec. V).  First through the three cell
+    // problems of the scalar potential; if that solver does not converge,
+    // by relaxing a charge-free field of mean D = e_d, whose mean E is then
+    // column d of eps_eff^-1.
+    double M[9];
+    c->psi = (double*)dalloc(c, n3 * sizeof(double));
+    if (c->psi) {
+      double ef[9];
+      const memd_status ms = mg_eps_eff(c, c->psi, ef, 1e-2 * std::min(c->relax_tol, 1e-12),
+                                        c->relax_maxit);
+      if (ms == MEMD_OK && invert3(ef, M)) {
+        for (int t = 0; t < 9; ++t) c->eps_eff_inv[t] = M[t];
+        for (int e2 = 0; e2 < 3; ++e2)
+          for (int d = 0; d < 3; ++d)
+            c->Minv[3 * e2 + d] = 0.5 * (M[3 * e2 + d] + M[3 * d + e2]);
+        goto eps_done;
+      }
+      dfree(c, c->psi);
+      c->psi = nullptr;
+      cudaGetLastError();
+    }
     D64 = (double*)dalloc(c, n3 * sizeof(double));
     if (!D64) {
       s = fail(c, MEMD_ERR_OOM, "relaxation field");
       goto done;
     }
-    double M[9];
     for (int d = 0; d < 3; ++d) {
       k_fill_unit<<<nb(n3), 256, 0, st>>>(V, D64, d);
       s = relax(c, D64, c->relax_tol, c->relax_maxit);
@@ -659,7 +716,9 @@ memd_status memd_create(const int32_t mesh[3], const double box[3], const memd_e
     }
     for (int e2 = 0; e2 < 3; ++e2)
       for (int d = 0; d < 3; ++d) c->Minv[3 * e2 + d] = 0.5 * (M[3 * e2 + d] + M[3 * d + e2]);
+    for (int t = 0; t < 9; ++t) c->eps_eff_inv[t] = M[t];
   }
+eps_done:
   if (cudaEventCreate(&c->ev0) != cudaSuccess || cudaEventCreate(&c->ev1) != cudaSuccess ||
       cudaEventCreateWithFlags(&c->fork, cudaEventDisableTiming) != cudaSuccess ||
       cudaEventCreateWithFlags(&c->join, cudaEventDisableTiming) != cudaSuccess ||
@@ -667,9 +726,9 @@ memd_status memd_create(const int32_t mesh[3], const double box[3], const memd_e
     s = fail(c, MEMD_ERR_CUDA, "events");
     goto done;
   }
-  s = autotune_fused(c);
+  // the field kernel is autotuned when a step first needs it (a system
+  // stepped as one cooperative launch or only in batches never does)
   c->coop_grid = coop_grid(c->prec, c->device);
-  if (s != MEMD_OK) goto done;
 done:
   dfree(c, vals);
   dfree(c, D64);
@@ -771,6 +830,18 @@ memd_status memd_init_field(memd_ctx* c, int64_t n, const double* pos, const int
       launch_ledger_sums(m, c->Lg, c->ds, st);
       launch_init_D(m, D64, c->Lg, c->ds, std::ldexp(1.0, -48) / (m.a * m.a), c->Vbox, st);
       CKL();
+      // the minimiser through the scalar potential; the relaxation below then
+      // only confirms the circulation residual (or, if the potential solve
+      // did not converge, relaxes from the scanned field)
+      if (c->psi) {
+        int its = 0;
+        const memd_status ms = mg_relax(c, D64, c->psi, c->eps_eff_inv,
+                                        1e-2 * std::min(c->relax_tol, 1e-12), c->relax_maxit, &its);
+        if (ms != MEMD_OK) {
+          cudaGetLastError();
+          launch_init_D(m, D64, c->Lg, c->ds, std::ldexp(1.0, -48) / (m.a * m.a), c->Vbox, st);
+        }
+      }
       s = relax(c, D64, c->relax_tol, c->relax_maxit);
     }
     if (s == MEMD_OK) {
@@ -869,6 +940,11 @@ memd_status memd_step(memd_ctx* c, int64_t nsteps, const memd_thermostat* th) {
     c->graph_kT = kT;
   }
   if (!c->graph[0] && !c->graph[1]) c->coop = want_coop(c);
+  if (!c->coop && !c->fcfg_ready) {
+    const memd_status e = autotune_fused(c);
+    if (e != MEMD_OK) return e;
+    c->fcfg_ready = true;
+  }
   auto record = [&](int par) {
     return c->coop ? record_step_coop(c, sp, par, timed) : record_step(c, sp, par, timed);
   };

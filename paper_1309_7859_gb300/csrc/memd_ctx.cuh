@@ -43,6 +43,8 @@ struct memd_ctx {
   double* red = nullptr;  // reduction partials (4 x reduce_blocks) + 32 scalars
   double G[8] = {0};
   double Minv[9] = {0};
+  double eps_eff_inv[9] = {0};  // exact inverse of the effective permittivity (Minv symmetrised)
+  double* psi = nullptr;        // cell-problem potentials of the scalar solver (3V), or null
   // particles
   Particles P{};
   bool initialised = false;
@@ -63,6 +65,7 @@ struct memd_ctx {
   int relax_iters_last = 0;
   int gen = 0;  // bumped by every memd_init_field (batches rebuild their tables)
   FusedCfg fcfg{8, 1, 0, 0};
+  bool fcfg_ready = false;  // fcfg autotuned (at the first step that needs it)
   int field_kernel = 0;
   TmaMaps tma{};
   bool tma_ok = false;
@@ -78,6 +81,13 @@ void memd_dfree(memd_ctx* c, void* p);
 size_t memd_esz(const memd_ctx* c);
 memd::StepParams memd_step_params(const memd_ctx* c, int thermo, double gamma, double kT);
 memd_status memd_check_err(memd_ctx* c);
+// memd_mg.cu: effective permittivity and initial field through the scalar
+// potential (multigrid-preconditioned CG on the vertices)
+namespace memd {
+memd_status mg_eps_eff(memd_ctx* c, double* psi, double eps_eff[9], double tol, int maxit);
+memd_status mg_relax(memd_ctx* c, double* D64, const double* psi, const double eps_eff_inv[9],
+                     double tol, int maxit, int* iters);
+}  // namespace memd
 // memd_batch.cu, for the server: a batch whose field tiles are autotuned
 // (tune) or left at their defaults
 memd_status memd_batch_create_opt(int32_t count, memd_ctx* const* members, memd_batch** out,

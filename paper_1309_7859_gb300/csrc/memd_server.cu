@@ -67,7 +67,9 @@ namespace {
 int64_t footprint(const memd_server_options& o, const memd_server::Req& r) {
   const int64_t V = (int64_t)r.mesh[0] * r.mesh[1] * r.mesh[2];
   const int64_t es = o.precision == MEMD_FP32 ? 4 : 8;
-  const int64_t fields = 3 * V * (5 * es + 8 + 16);
+  // D, B (two parities each) and 1/eps in field precision; 1/eps FP64, the
+  // ledger, the transfer buffer and the cell-problem potentials (8 B each)
+  const int64_t fields = 3 * V * (5 * es + 8 + 16 + 8);
   const int64_t init = 3 * V * 8 * 7 + V * 16;
   const int64_t parts = (r.q.size() + 1) * (8 * 3 * 5 + 8 * 3 + 4 * 4 + 24);
   return fields + init + parts + (1 << 20);
