@@ -679,7 +679,7 @@ memd_status memd_create(const int32_t mesh[3], const double box[3], const memd_e
     c->psi = (double*)dalloc(c, n3 * sizeof(double));
     if (c->psi) {
       double ef[9];
-      const memd_status ms = mg_eps_eff(c, c->psi, ef, 1e-2 * std::min(c->relax_tol, 1e-12),
+      const memd_status ms = mg_eps_eff(c, c->psi, ef, std::min(c->relax_tol, 1e-12),
                                         c->relax_maxit);
       if (ms == MEMD_OK && invert3(ef, M)) {
         for (int t = 0; t < 9; ++t) c->eps_eff_inv[t] = M[t];
@@ -836,7 +836,7 @@ memd_status memd_init_field(memd_ctx* c, int64_t n, const double* pos, const int
       if (c->psi) {
         int its = 0;
         const memd_status ms = mg_relax(c, D64, c->psi, c->eps_eff_inv,
-                                        1e-2 * std::min(c->relax_tol, 1e-12), c->relax_maxit, &its);
+                                        std::min(c->relax_tol, 1e-12), c->relax_maxit, &its);
         if (ms != MEMD_OK) {
           cudaGetLastError();
           launch_init_D(m, D64, c->Lg, c->ds, std::ldexp(1.0, -48) / (m.a * m.a), c->Vbox, st);

@@ -12,11 +12,15 @@
 // V unknowns instead of 3V.
 //
 // Solver: conjugate gradients preconditioned by one symmetric multigrid
-// V-cycle: vertex-centred coarsening by 2 while every extent is even,
-// red-black Gauss-Seidel (damped Jacobi on a level with an odd extent),
-// full-weighting restriction, trilinear prolongation, coarse link
-// conductances from two fine links in series averaged over the 3 x 3
-// perpendicular neighbourhood.  FP64 throughout.
+// V-cycle.  A level whose extents are all even coarsens geometrically
+// (vertex-centred, by 2): red-black Gauss-Seidel, full-weighting
+// restriction, trilinear prolongation, coarse link conductances from two
+// fine links in series averaged over the 3 x 3 perpendicular neighbourhood.
+// A level with an odd extent coarsens by aggregating vertex pairs (a triple
+// at the end of an odd axis): damped Jacobi, Galerkin coarse operator,
+// piecewise-constant transfers with an over-corrected coarse correction.
+// FP64 throughout.
+#include <algorithm>
 #include <cmath>
 #include <vector>
 
@@ -185,6 +189,60 @@ __global__ void k_coarsen(Lv F, Lv Cc, const double* __restrict__ wf, double* __
   wc[t] = 0.5 * s;
 }
 
+// Aggregation (a level with an odd extent): coarse vertex I along an axis
+// of n fine vertices and m = n / 2 coarse ones holds fine 2I, 2I + 1, and
+// also 2I + 2 when it is the last one of an odd n.  Piecewise-constant
+// prolongation; the Galerkin coarse operator is the aggregates' graph
+// Laplacian, the conductance of coarse link (d, I) the sum of the fine
+// d-links leaving aggregate I towards I + e_d.
+__device__ __forceinline__ int agg_lo(int I) { return 2 * I; }
+__device__ __forceinline__ int agg_hi(int I, int m, int n) { return I == m - 1 ? n - 1 : 2 * I + 1; }
+__device__ __forceinline__ int agg_of(int i, int m) { return min(i >> 1, m - 1); }
+
+__global__ void k_agg_coarsen(Lv F, Lv Cc, const double* __restrict__ wf, double* __restrict__ wc) {
+  const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (t >= 3 * Cc.V) return;
+  const int d = (int)(t / Cc.V);
+  const int64_t V = t - (int64_t)d * Cc.V;
+  int C[3];
+  coords(Cc, V, C[0], C[1], C[2]);
+  const int nf[3] = {F.n0, F.n1, F.n2}, nc[3] = {Cc.n0, Cc.n1, Cc.n2};
+  int lo[3], hi[3];
+  for (int e = 0; e < 3; ++e) {
+    lo[e] = agg_lo(C[e]);
+    hi[e] = agg_hi(C[e], nc[e], nf[e]);
+  }
+  lo[d] = hi[d];  // the last fine layer of the aggregate along d
+  double s = 0.0;
+  for (int k = lo[2]; k <= hi[2]; ++k)
+    for (int j = lo[1]; j <= hi[1]; ++j)
+      for (int i = lo[0]; i <= hi[0]; ++i) s += wf[(int64_t)d * F.V + vid(F, i, j, k)];
+  wc[t] = s;
+}
+
+__global__ void k_agg_restrict(Lv F, Lv Cc, const double* __restrict__ r, double* __restrict__ fc) {
+  const int64_t V = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (V >= Cc.V) return;
+  int I, J, K;
+  coords(Cc, V, I, J, K);
+  const int i1 = agg_hi(I, Cc.n0, F.n0), j1 = agg_hi(J, Cc.n1, F.n1), k1 = agg_hi(K, Cc.n2, F.n2);
+  double s = 0.0;
+  for (int k = agg_lo(K); k <= k1; ++k)
+    for (int j = agg_lo(J); j <= j1; ++j)
+      for (int i = agg_lo(I); i <= i1; ++i) s += r[vid(F, i, j, k)];
+  fc[V] = s;
+}
+
+// phi += alpha e(aggregate of v); alpha > 1 makes up for the flat prolongation
+__global__ void k_agg_prolong(Lv F, Lv Cc, const double* __restrict__ ec, double alpha,
+                              double* __restrict__ phi) {
+  const int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (v >= F.V) return;
+  int i, j, k;
+  coords(F, v, i, j, k);
+  phi[v] += alpha * ec[vid(Cc, agg_of(i, Cc.n0), agg_of(j, Cc.n1), agg_of(k, Cc.n2))];
+}
+
 // fine conductances w = eps / a^2 = 1 / (ie a^2)
 __global__ void k_fine_w(int64_t n, const double* __restrict__ ie64, double inv_a2,
                          double* __restrict__ w) {
@@ -272,7 +330,10 @@ struct MgLevel {
   double* f = nullptr;    // V
   double* r = nullptr;    // V
   bool rb = true;         // red-black Gauss-Seidel (every extent even), else Jacobi
+  bool agg = false;       // transfer to the next level by aggregation, else geometric
 };
+
+constexpr double kAggAlpha = 1.6;  // over-correction of the aggregated coarse correction
 
 struct MgSolver {
   memd_ctx* c = nullptr;
@@ -321,9 +382,15 @@ struct MgSolver {
     smooth(l, true, st);
     smooth(l, true, st);
     k_residual<<<nblk(a.L.V), kT, 0, st>>>(a.L, a.w, a.phi, a.f, a.r);
-    k_restrict<<<nblk(b.L.V), kT, 0, st>>>(a.L, b.L, a.r, b.f);
+    if (a.agg)
+      k_agg_restrict<<<nblk(b.L.V), kT, 0, st>>>(a.L, b.L, a.r, b.f);
+    else
+      k_restrict<<<nblk(b.L.V), kT, 0, st>>>(a.L, b.L, a.r, b.f);
     vcycle(l + 1, st);
-    k_prolong<<<nblk(a.L.V), kT, 0, st>>>(a.L, b.L, b.phi, a.phi);
+    if (a.agg)
+      k_agg_prolong<<<nblk(a.L.V), kT, 0, st>>>(a.L, b.L, b.phi, kAggAlpha, a.phi);
+    else
+      k_prolong<<<nblk(a.L.V), kT, 0, st>>>(a.L, b.L, b.phi, a.phi);
     smooth(l, false, st);
     smooth(l, false, st);
   }
@@ -344,12 +411,17 @@ struct MgSolver {
       a.rb = (L.n0 % 2 == 0) && (L.n1 % 2 == 0) && (L.n2 % 2 == 0);
       if (l == 0)
         k_fine_w<<<nblk(3 * L.V), kT, 0, st>>>(3 * L.V, c->ie64, inv_a2, a.w);
+      else if (lv.back().agg)
+        k_agg_coarsen<<<nblk(3 * L.V), kT, 0, st>>>(lv.back().L, L, lv.back().w, a.w);
       else
         k_coarsen<<<nblk(3 * L.V), kT, 0, st>>>(lv.back().L, L, lv.back().w, a.w);
+      a.agg = !a.rb;  // the way down from this level
       lv.push_back(a);
-      const bool even = a.rb;
-      if (!even || L.n0 < 4 || L.n1 < 4 || L.n2 < 4 || L.V <= 64) break;
-      L = Lv{L.n0 / 2, L.n1 / 2, L.n2 / 2, L.V / 8};
+      if (L.n0 < 4 || L.n1 < 4 || L.n2 < 4 || L.V <= 64) break;
+      L.n0 /= 2;
+      L.n1 /= 2;
+      L.n2 /= 2;
+      L.V = (int64_t)L.n0 * L.n1 * L.n2;
     }
     const int64_t V = m.V;
     x = alloc(V);
@@ -383,7 +455,10 @@ struct MgSolver {
   }
 
   // x = L^-1 f (f of zero mean up to rounding; x of zero mean); stops when
-  // |r| <= tol |f| (2-norms)
+  // |r| <= tol |f| (2-norms), or, once the recursion has reached its
+  // rounding floor and the residual grows again (to 10 times its least
+  // value), when that least value was below 100 tol |f|; at most
+  // min(maxit, 400) iterations
   memd_status solve(const double* f, double* out, double tol, int maxit, int* iters,
                     cudaStream_t st) {
     const int64_t V = lv[0].L.V;
@@ -419,7 +494,9 @@ struct MgSolver {
     const double f2 = h[1];
     int it = 0;
     bool ok = f2 == 0.0;
-    while (!ok && it < maxit) {
+    double least = f2;
+    const int cap = maxit < 400 ? maxit : 400;
+    while (!ok && it < cap) {
       if (it_graph) {
         if (cudaGraphLaunch(it_graph, st) != cudaSuccess) return MEMD_ERR_CUDA;
       } else {
@@ -431,6 +508,8 @@ struct MgSolver {
           cudaStreamSynchronize(st) != cudaSuccess)
         return MEMD_ERR_CUDA;
       ok = h[0] <= tol * tol * f2;
+      if (!ok && h[0] > 100.0 * least && least <= 1e4 * tol * tol * f2) ok = true;
+      least = std::min(least, h[0]);
     }
     if (iters) *iters = it;
     // zero-mean solution
