@@ -249,7 +249,7 @@ def run_memd(args, world, rank, local):
     hi = torch.empty((n, 3), dtype=torch.int32, pin_memory=True).numpy()
     hf = torch.empty((n, 3), dtype=torch.float64, pin_memory=True).numpy()
     g.get_particles_into(hx, hv, hi)
-    e2e_steps = max(1, args.steps)
+    e2e_steps = max(1, min(args.steps, 1000))
     barrier(world)
     t0 = time.perf_counter()
     for _ in range(e2e_steps):
@@ -396,14 +396,17 @@ def served(count, args):
             "p50_latency_s": float(np.percentile(lat, 50)),
             "p99_latency_s": float(np.percentile(lat, 99)),
             "link_updates_per_s": links / wall, "particle_steps_per_s": parts / wall,
-            "setup_s": st["setup_s"],
-            "stepping_link_updates_per_s": links / max(wall - st["setup_s"], 1e-9),
+            "setup_s_summed": st["setup_s"], "admission_workers": 3,
+            "step_gpu_s": st["step_gpu_s"],
+            "stepping_link_updates_per_s": links / max(st["step_gpu_s"], 1e-9),
             "mean_budget_use": st["budget_use_sum"] / max(1, st["rounds"]),
             "rounds": st["rounds"], "batch_rebuilds": st["rebuilds"],
             "single_fp64_link_updates_per_s": l_single / max(t_single, 1e-9),
             "single_fp64_sample": f"first {k} requests one at a time, up to 200 steps each, FP64 fields",
             "note": "wall time includes every request's setup (eps, Green's table, "
-                    "eps_eff and initial relaxations) and the arrival gaps"}
+                    "eps_eff and initial solve; run by admission workers beside the "
+                    "stepping) and the arrival gaps; stepping rate = link updates over "
+                    "the device time of the batch steps"}
 
 
 def batched(count, dev, args):
@@ -502,7 +505,7 @@ def large_mesh(N, dev, stream, args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--steps", type=int, default=20000)
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", default="memd", choices=["memd", "reference"])
     ap.add_argument("--workload", default="slab-32")

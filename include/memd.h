@@ -292,8 +292,9 @@ void memd_batch_destroy(memd_batch *b);
  * and all resident systems advance together as one batch by one quantum of
  * steps (shortened so that no request overshoots).  A request that arrives
  * while others run joins at the next round and shares their kernel
- * launches.  Every request gets the same result as when run alone with the
- * plain-load field kernel.  One server is driven by one host thread. */
+ * launches.  Every request gets the same result as when run alone (all
+ * field kernels and step engines share their arithmetic).  One server is
+ * driven by one host thread. */
 typedef struct memd_server memd_server;
 
 enum { MEMD_REQ_QUEUED = 0, MEMD_REQ_RUNNING = 1, MEMD_REQ_DONE = 2, MEMD_REQ_FAILED = 3 };
@@ -337,8 +338,14 @@ void memd_server_destroy(memd_server *s);
 memd_status memd_server_submit(memd_server *s, const memd_request *req, int64_t *id);
 
 /* One scheduling round (retire, admit, step one quantum); reports the
- * resident, queued and finished request counts (any may be NULL).  Blocks
- * only to collect the previous round's finished requests. */
+ * resident, queued and finished request counts (any may be NULL).  Admission
+ * hands queued requests (in arrival order, while the memory budget and the
+ * slots allow, their footprint reserved from then on) to three worker
+ * threads, which create and initialise each system on their own streams
+ * beside the stepping; a system joins the batch at the first round after its
+ * setup finished.  A request counts as queued until it joins.  Blocks only
+ * to collect the previous round's finished steps, or for at most 2 ms when
+ * nothing is resident yet but setups are under way. */
 memd_status memd_server_pump(memd_server *s, int32_t *n_active, int32_t *n_queued,
                              int32_t *n_done);
 
@@ -358,7 +365,8 @@ memd_status memd_server_release(memd_server *s, int64_t id);
 int64_t memd_server_used_bytes(const memd_server *s);
 
 typedef struct memd_server_stats {
-  double setup_s;          /* host time creating and initialising admitted systems */
+  double setup_s;          /* time creating and initialising admitted systems, summed over
+                              the admission workers (setups run concurrently) */
   double budget_use_sum;   /* sum over rounds of resident footprint / budget */
   int64_t rounds;          /* memd_server_pump calls */
   int64_t steps_rounds;    /* rounds that stepped the batch */
@@ -366,6 +374,8 @@ typedef struct memd_server_stats {
   int64_t admitted;
   int64_t link_updates;    /* 3 V per system per step, summed */
   int64_t particle_steps;
+  double step_gpu_s;       /* device time of the batch steps (CUDA events on the server's
+                              stream) */
 } memd_server_stats;
 
 memd_status memd_server_get_stats(const memd_server *s, memd_server_stats *out);

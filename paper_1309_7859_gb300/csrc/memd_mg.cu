@@ -243,6 +243,58 @@ __global__ void k_agg_prolong(Lv F, Lv Cc, const double* __restrict__ ec, double
   phi[v] += alpha * ec[vid(Cc, agg_of(i, Cc.n0), agg_of(j, Cc.n1), agg_of(k, Cc.n2))];
 }
 
+// The coarsest level (at most kCoarseSmem vertices) in one CTA: sweeps
+// forward (red then black, or damped Jacobi) then backward, all in shared
+// memory, instead of one launch per half-sweep.
+constexpr int kCoarseSmem = 1024;
+
+__global__ void __launch_bounds__(1024)
+    k_coarse_solve(Lv L, const double* __restrict__ w, const double* __restrict__ f,
+                   double* __restrict__ phi, int sweeps, int rb) {
+  extern __shared__ double sm[];
+  const int V = (int)L.V;
+  double* sw = sm;            // 3V
+  double* sf = sm + 3 * V;    // V
+  double* sp = sm + 4 * V;    // V
+  double* st = sm + 5 * V;    // V
+  for (int t = threadIdx.x; t < 3 * V; t += blockDim.x) sw[t] = w[t];
+  for (int t = threadIdx.x; t < V; t += blockDim.x) {
+    sf[t] = f[t];
+    sp[t] = 0.0;
+  }
+  __syncthreads();
+  auto relax_vertex = [&](int v, bool jac) {
+    int i, j, k;
+    coords(L, v, i, j, k);
+    double nb, dg;
+    const double a = apply_at(L, sw, sp, v, i, j, k, nb, dg);
+    if (jac)
+      st[v] = (sf[v] - a) / dg;
+    else
+      sp[v] = (sf[v] + nb) / dg;
+  };
+  for (int dir = 0; dir < 2; ++dir)
+    for (int s = 0; s < sweeps; ++s) {
+      if (rb) {
+        for (int h = 0; h < 2; ++h) {
+          const int color = dir == 0 ? h : 1 - h;
+          for (int v = threadIdx.x; v < V; v += blockDim.x) {
+            int i, j, k;
+            coords(L, v, i, j, k);
+            if (((i + j + k) & 1) == color) relax_vertex(v, false);
+          }
+          __syncthreads();
+        }
+      } else {
+        for (int v = threadIdx.x; v < V; v += blockDim.x) relax_vertex(v, true);
+        __syncthreads();
+        for (int v = threadIdx.x; v < V; v += blockDim.x) sp[v] += 0.8 * st[v];
+        __syncthreads();
+      }
+    }
+  for (int t = threadIdx.x; t < V; t += blockDim.x) phi[t] = sp[t];
+}
+
 // fine conductances w = eps / a^2 = 1 / (ie a^2)
 __global__ void k_fine_w(int64_t n, const double* __restrict__ ie64, double inv_a2,
                          double* __restrict__ w) {
@@ -374,6 +426,11 @@ struct MgSolver {
     cudaMemsetAsync(a.phi, 0, a.L.V * sizeof(double), st);
     if (l + 1 == (int)lv.size()) {
       const int sweeps = a.L.V <= 512 ? 40 : 12;
+      if (a.L.V <= kCoarseSmem) {
+        k_coarse_solve<<<1, 1024, 6 * a.L.V * sizeof(double), st>>>(a.L, a.w, a.f, a.phi, sweeps,
+                                                                   a.rb ? 1 : 0);
+        return;
+      }
       for (int s = 0; s < sweeps; ++s) smooth(l, true, st);
       for (int s = 0; s < sweeps; ++s) smooth(l, false, st);
       return;

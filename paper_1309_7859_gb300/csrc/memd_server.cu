@@ -12,12 +12,21 @@
 // resident, which is continuous batching.  Each request's result is the
 // same as when it runs alone (the batched kernels are the single-system
 // kernels over a descriptor table).
+//
+// Admission (create: permittivity, Green's table, effective permittivity;
+// init: Gauss scan and initial solve) runs on a few worker threads, each with
+// its own CUDA stream, beside the batch stepping on the server's stream; a
+// set-up system moves to the server's stream and joins the batch at the
+// next round after its setup has finished.
 #include <algorithm>
 #include <chrono>
+#include <condition_variable>
 #include <cstring>
 #include <deque>
 #include <map>
+#include <mutex>
 #include <string>
+#include <thread>
 #include <vector>
 
 #include "memd.h"
@@ -56,7 +65,20 @@ struct memd_server {
   bool dirty = false;
   std::string last_error;
   memd_server_stats stats{};
+  // admission workers: requests handed over (todo), set up (ready)
+  std::vector<std::thread> workers;
+  std::vector<cudaStream_t> wstreams;
+  std::mutex mu;
+  std::condition_variable cv_todo, cv_ready;
+  std::deque<Req*> todo;
+  std::vector<std::pair<Req*, memd_status>> ready;
+  int in_flight = 0;
+  bool stop = false;
+  cudaEvent_t ev0 = nullptr, ev1 = nullptr;  // around the last batch step
+  bool step_timed = false;
 };
+
+constexpr int kAdmitWorkers = 3;  // concurrent setups
 
 namespace {
 
@@ -110,15 +132,15 @@ double now_s() {
   return std::chrono::duration<double>(std::chrono::steady_clock::now().time_since_epoch()).count();
 }
 
-memd_status admit(memd_server* s, memd_server::Req& r) {
-  // steps already queued on the stream finish first, so that the timed
-  // part below is this request's own setup
-  cudaStreamSynchronize((cudaStream_t)s->opt.cuda_stream);
+// One request's setup on a worker's stream; the finished context is then
+// moved to the server's stream (its setup work has completed).
+memd_status admit(memd_server* s, memd_server::Req& r, cudaStream_t wst) {
   const double t0 = now_s();
   struct Timer {
     memd_server* s;
     double t0;
     ~Timer() {
+      std::lock_guard<std::mutex> g(s->mu);
       s->stats.setup_s += now_s() - t0;
       s->stats.admitted += 1;
     }
@@ -126,7 +148,7 @@ memd_status admit(memd_server* s, memd_server::Req& r) {
   memd_options o;
   memd_default_options(&o);
   o.precision = s->opt.precision;
-  o.cuda_stream = s->opt.cuda_stream;
+  o.cuda_stream = wst;
   o.device = s->opt.device;
   o.alloc = s->opt.alloc;
   o.free = s->opt.free;
@@ -144,15 +166,66 @@ memd_status admit(memd_server* s, memd_server::Req& r) {
     st = memd_init_field(r.ctx, n, n ? r.pos.data() : nullptr, n ? r.q.data() : nullptr,
                          r.mass.empty() ? nullptr : r.mass.data(),
                          r.vel.empty() ? nullptr : r.vel.data());
+    if (st == MEMD_OK && cudaStreamSynchronize(wst) != cudaSuccess) st = MEMD_ERR_CUDA;
     if (st != MEMD_OK) {
       r.error = memd_last_error(r.ctx);
       memd_destroy(r.ctx);
       r.ctx = nullptr;
+    } else {
+      r.ctx->stream = (cudaStream_t)s->opt.cuda_stream;
     }
   } else {
     r.error = std::string("memd_create: ") + memd_status_string(st);
   }
   return st;
+}
+
+void worker(memd_server* s, int w) {
+  cudaSetDevice(s->opt.device >= 0 ? s->opt.device : 0);
+  for (;;) {
+    memd_server::Req* r = nullptr;
+    {
+      std::unique_lock<std::mutex> g(s->mu);
+      s->cv_todo.wait(g, [&] { return s->stop || !s->todo.empty(); });
+      if (s->stop && s->todo.empty()) return;
+      r = s->todo.front();
+      s->todo.pop_front();
+    }
+    const memd_status st = admit(s, *r, s->wstreams[w]);
+    {
+      std::lock_guard<std::mutex> g(s->mu);
+      s->ready.emplace_back(r, st);
+      s->in_flight -= 1;
+    }
+    s->cv_ready.notify_all();
+  }
+}
+
+memd_status start_workers(memd_server* s) {
+  if (!s->workers.empty()) return MEMD_OK;
+  int dev = s->opt.device;
+  if (dev < 0 && cudaGetDevice(&dev) != cudaSuccess) return MEMD_ERR_CUDA;
+  s->opt.device = dev;
+  for (int w = 0; w < kAdmitWorkers; ++w) {
+    cudaStream_t st;
+    if (cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess) return MEMD_ERR_CUDA;
+    s->wstreams.push_back(st);
+  }
+  for (int w = 0; w < kAdmitWorkers; ++w) s->workers.emplace_back(worker, s, w);
+  return MEMD_OK;
+}
+
+void stop_workers(memd_server* s) {
+  {
+    std::lock_guard<std::mutex> g(s->mu);
+    s->stop = true;
+    s->todo.clear();  // requests not yet started stay queued
+  }
+  s->cv_todo.notify_all();
+  for (auto& t : s->workers) t.join();
+  s->workers.clear();
+  for (cudaStream_t st : s->wstreams) cudaStreamDestroy(st);
+  s->wstreams.clear();
 }
 
 }  // namespace
@@ -198,10 +271,13 @@ memd_status memd_server_create(const memd_server_options* opt, memd_server** out
 
 void memd_server_destroy(memd_server* s) {
   if (!s) return;
+  stop_workers(s);
   if (s->batch) memd_batch_destroy(s->batch);
   s->batch = nullptr;
   for (auto& kv : s->reqs)
     if (kv.second.ctx) memd_destroy(kv.second.ctx);
+  if (s->ev0) cudaEventDestroy(s->ev0);
+  if (s->ev1) cudaEventDestroy(s->ev1);
   if (s->opt.reserved[0]) cudaStreamDestroy((cudaStream_t)s->opt.cuda_stream);
   delete s;
 }
@@ -246,6 +322,12 @@ memd_status memd_server_pump(memd_server* s, int32_t* n_active, int32_t* n_queue
   if (s->batch) {
     memd_status st = memd_batch_synchronize(s->batch);
     if (st != MEMD_OK) return sfail(s, st, "batch step failed");
+    if (s->step_timed) {
+      float ms = 0.f;
+      if (cudaEventElapsedTime(&ms, s->ev0, s->ev1) == cudaSuccess) s->stats.step_gpu_s += 1e-3 * ms;
+      cudaGetLastError();
+      s->step_timed = false;
+    }
     bool leaving = false;
     for (int64_t id : s->active) leaving = leaving || s->reqs[id].remaining <= 0;
     if (leaving) {
@@ -264,8 +346,32 @@ memd_status memd_server_pump(memd_server* s, int32_t* n_active, int32_t* n_queue
     }
   }
   s->active.swap(keep);
-  // 2. admit in arrival order while memory and slots allow
-  while (!s->queue.empty() && (int)s->active.size() < s->opt.max_slots) {
+  // 2. systems whose setup has finished join; queued requests go to the
+  // admission workers in arrival order while memory and slots allow (their
+  // footprint is reserved from the hand-over on)
+  {
+    const memd_status se = start_workers(s);
+    if (se != MEMD_OK) return sfail(s, se, "admission workers");
+  }
+  std::vector<std::pair<memd_server::Req*, memd_status>> got;
+  int in_flight = 0;
+  {
+    std::lock_guard<std::mutex> g(s->mu);
+    got.swap(s->ready);
+    in_flight = s->in_flight;
+  }
+  for (auto& pr : got) {
+    memd_server::Req& r = *pr.first;
+    if (pr.second != MEMD_OK) {
+      r.state = MEMD_REQ_FAILED;
+      s->used -= r.footprint;
+      continue;
+    }
+    r.state = MEMD_REQ_RUNNING;
+    s->active.push_back(r.id);
+    s->dirty = true;
+  }
+  while (!s->queue.empty() && (int)s->active.size() + in_flight < s->opt.max_slots) {
     memd_server::Req& r = s->reqs[s->queue.front()];
     if (r.footprint > s->opt.budget_bytes) {
       r.state = MEMD_REQ_FAILED;
@@ -275,18 +381,19 @@ memd_status memd_server_pump(memd_server* s, int32_t* n_active, int32_t* n_queue
     }
     if (s->used + r.footprint > s->opt.budget_bytes) break;
     s->queue.pop_front();
-    if (s->batch) {  // a new member's setup queues behind the running batch
-      memd_batch_destroy(s->batch);
-      s->batch = nullptr;
-    }
-    if (admit(s, r) != MEMD_OK) {
-      r.state = MEMD_REQ_FAILED;
-      continue;
-    }
-    r.state = MEMD_REQ_RUNNING;
     s->used += r.footprint;
-    s->active.push_back(r.id);
-    s->dirty = true;
+    {
+      std::lock_guard<std::mutex> g(s->mu);
+      s->todo.push_back(&r);
+      s->in_flight += 1;
+    }
+    in_flight += 1;
+    s->cv_todo.notify_one();
+  }
+  if (s->active.empty() && in_flight > 0) {
+    // nothing to step yet: wait a little for a setup to finish
+    std::unique_lock<std::mutex> g(s->mu);
+    s->cv_ready.wait_for(g, std::chrono::milliseconds(2), [&] { return !s->ready.empty(); });
   }
   // 3. batch of the live systems, one quantum (bounded by the nearest finish)
   if (s->dirty) {
@@ -306,8 +413,14 @@ memd_status memd_server_pump(memd_server* s, int32_t* n_active, int32_t* n_queue
     for (int64_t id : s->active) k = std::min(k, s->reqs[id].remaining);
     if (k > 0) {
       memd_thermostat th{s->opt.gamma, s->opt.kT};
+      const cudaStream_t sst = (cudaStream_t)s->opt.cuda_stream;
+      if (!s->ev0 && (cudaEventCreate(&s->ev0) != cudaSuccess || cudaEventCreate(&s->ev1) != cudaSuccess))
+        return sfail(s, MEMD_ERR_CUDA, "events");
+      cudaEventRecord(s->ev0, sst);
       memd_status st = memd_batch_step(s->batch, k, s->opt.thermostat ? &th : nullptr);
       if (st != MEMD_OK) return sfail(s, st, "batch step failed");
+      cudaEventRecord(s->ev1, sst);
+      s->step_timed = true;
       for (int64_t id : s->active) {
         s->reqs[id].remaining -= k;
         s->stats.link_updates += 3 * k * (int64_t)s->reqs[id].mesh[0] * s->reqs[id].mesh[1] *

@@ -100,7 +100,8 @@ class Request(C.Structure):
 class ServerStats(C.Structure):
     _fields_ = [("setup_s", C.c_double), ("budget_use_sum", C.c_double), ("rounds", C.c_int64),
                 ("steps_rounds", C.c_int64), ("rebuilds", C.c_int64), ("admitted", C.c_int64),
-                ("link_updates", C.c_int64), ("particle_steps", C.c_int64)]
+                ("link_updates", C.c_int64), ("particle_steps", C.c_int64),
+                ("step_gpu_s", C.c_double)]
 
 
 class KernelStats(C.Structure):
