@@ -425,7 +425,7 @@ struct MgSolver {
     MgLevel& a = lv[l];
     cudaMemsetAsync(a.phi, 0, a.L.V * sizeof(double), st);
     if (l + 1 == (int)lv.size()) {
-      const int sweeps = a.L.V <= 512 ? 40 : 12;
+      const int sweeps = a.L.V <= 512 ? 8 : 12;
       if (a.L.V <= kCoarseSmem) {
         k_coarse_solve<<<1, 1024, 6 * a.L.V * sizeof(double), st>>>(a.L, a.w, a.f, a.phi, sweeps,
                                                                    a.rb ? 1 : 0);
