@@ -751,6 +751,8 @@ static void free_particles(memd_ctx* c) {
   dfree(c, c->P.mv);
   dfree(c, c->P.h);
   dfree(c, c->P.sig);
+  dfree(c, c->pin);
+  c->pin = nullptr;
   c->P = Particles{};
   c->sig_ready = false;
 }
@@ -789,8 +791,10 @@ memd_status memd_init_field(memd_ctx* c, int64_t n, const double* pos, const int
   c->P.mv = (int*)dalloc(c, 6 * nn * sizeof(int));
   c->P.h = (double*)dalloc(c, nn * sizeof(double));
   c->P.sig = (double*)dalloc(c, nn * sizeof(double));
+  // staging of memd_set_particles (positions and images), kept with the particles
+  c->pin = (double*)dalloc(c, 3 * nn * sizeof(double) + 3 * nn * sizeof(int));
   if (!c->P.x || !c->P.v || !c->P.m || !c->P.F || !c->P.Ft || !c->P.img || !c->P.q || !c->P.mv ||
-      !c->P.h || !c->P.sig)
+      !c->P.h || !c->P.sig || !c->pin)
     return fail(c, MEMD_ERR_OOM, "particle allocation");
   double* pin = (double*)dalloc(c, 3 * nn * sizeof(double));
   long long* Q = (long long*)dalloc(c, sizeof(long long) * m.V);
@@ -849,6 +853,8 @@ memd_status memd_init_field(memd_ctx* c, int64_t n, const double* pos, const int
       launch_cast(c->prec, c->D(), D64, 3 * m.V, st);
       CK(cudaMemsetAsync(c->B(), 0, 3 * m.V * esz(c), st));
       CK(cudaMemsetAsync(c->Tb, 0, 3 * m.V * sizeof(long long), st));
+      if (c->Tb2) CK(cudaMemsetAsync(c->Tb2, 0, 3 * m.V * sizeof(long long), st));
+      c->pending = false;
       CK(cudaMemsetAsync(&c->ds->ticket, 0, sizeof(unsigned int), st));
       const StepParams sp = step_params(c, 0, 0.0, 0.0);
       launch_particle_constants(sp, c->P, st);
@@ -893,18 +899,39 @@ static memd_status record_step(memd_ctx* c, const StepParams& sp, int par, bool 
   return MEMD_OK;
 }
 
+// transfer buffer of buffer parity q: the single-launch step leaves the
+// transfers of its move, not yet applied, in the buffer of the parity it
+// wrote (the graph step uses buffer 0 only, and applies them at once)
+static long long* tbuf(memd_ctx* c, int q) { return q == 0 ? c->Tb : c->Tb2; }
+
 // the whole step as one cooperative launch (same kernels' device functions)
 static memd_status record_step_coop(memd_ctx* c, const StepParams& sp, int par, bool timed) {
   const cudaStream_t st = c->stream;
   if (timed) CK(cudaEventRecordWithFlags(c->ev0, st, cudaEventRecordExternal));
   const cudaError_t e = launch_step_coop(
       c->mesh, c->prec, sp, c->P, c->Dbuf[par], c->Bbuf[par], c->ie, c->Dbuf[par ^ 1],
-      c->Bbuf[par ^ 1], c->ie64, c->Tb, c->Lg, c->ds, c->coop_grid,
+      c->Bbuf[par ^ 1], c->ie64, tbuf(c, par), tbuf(c, par ^ 1), c->Lg, c->ds, c->coop_grid,
       coop_zchunk(c->mesh, c->coop_grid), st);
   if (e != cudaSuccess) return fail(c, MEMD_ERR_CUDA, cudaGetErrorString(e));
   if (timed) CK(cudaEventRecordWithFlags(c->ev1, st, cudaEventRecordExternal));
   return MEMD_OK;
 }
+
+}  // extern "C"
+
+// Apply the transfers a single-launch step left pending (to D and the
+// ledger, through the last move's links) before anything reads or replaces
+// the state.  (C++ linkage: used by the batch, not part of the C ABI.)
+memd_status memd_flush(memd_ctx* c) {
+  if (!c->pending) return MEMD_OK;
+  launch_apply(c->mesh, c->prec, c->P, tbuf(c, c->cur), c->Lg, c->D(),
+               std::ldexp(1.0, -48) / (c->mesh.a * c->mesh.a), c->stream);
+  c->pending = false;
+  if (cudaGetLastError() != cudaSuccess) return fail(c, MEMD_ERR_CUDA, "applying pending transfers");
+  return MEMD_OK;
+}
+
+extern "C" {
 
 // single launch or graph of four kernels for this system (decided when the
 // step graphs are built, once the particle count is known)
@@ -940,6 +967,15 @@ memd_status memd_step(memd_ctx* c, int64_t nsteps, const memd_thermostat* th) {
     c->graph_kT = kT;
   }
   if (!c->graph[0] && !c->graph[1]) c->coop = want_coop(c);
+  if (c->coop && !c->Tb2) {
+    c->Tb2 = (long long*)dalloc(c, 3 * c->mesh.V * sizeof(long long));
+    if (!c->Tb2) return fail(c, MEMD_ERR_OOM, "second transfer buffer");
+    CK(cudaMemsetAsync(c->Tb2, 0, 3 * c->mesh.V * sizeof(long long), c->stream));
+  }
+  if (!c->coop) {
+    const memd_status e = memd_flush(c);
+    if (e != MEMD_OK) return e;
+  }
   if (!c->coop && !c->fcfg_ready) {
     const memd_status e = autotune_fused(c);
     if (e != MEMD_OK) return e;
@@ -973,6 +1009,7 @@ memd_status memd_step(memd_ctx* c, int64_t nsteps, const memd_thermostat* th) {
           if (r2 != MEMD_OK) return r2;
           c->timing_pending = timed;
           c->cur = par ^ 1;
+          c->pending = true;
           continue;
         }
         if (r != MEMD_OK) return r;
@@ -986,6 +1023,7 @@ memd_status memd_step(memd_ctx* c, int64_t nsteps, const memd_thermostat* th) {
     }
     c->timing_pending = timed;
     c->cur = par ^ 1;
+    if (c->coop) c->pending = true;
   }
   return poll_err(c, false);
 }
@@ -1011,6 +1049,10 @@ memd_status memd_energy(memd_ctx* c, memd_energy_terms* out) {
   if (!c || !out) return MEMD_ERR_INVALID;
   if (!c->initialised) return fail(c, MEMD_ERR_STATE, "memd_init_field first");
   CK(cudaSetDevice(c->device));
+  {
+    const memd_status fe = memd_flush(c);
+    if (fe != MEMD_OK) return fe;
+  }
   const Mesh& m = c->mesh;
   const cudaStream_t st = c->stream;
   const int R = reduce_blocks();
@@ -1085,13 +1127,16 @@ memd_status memd_set_particles(memd_ctx* c, const double* pos, const double* vel
   if (!c) return MEMD_ERR_INVALID;
   if (!c->initialised) return fail(c, MEMD_ERR_STATE, "memd_init_field first");
   CK(cudaSetDevice(c->device));
+  {
+    const memd_status fe = memd_flush(c);
+    if (fe != MEMD_OK) return fe;
+  }
   const size_t n = (size_t)c->P.n;
   if (!n) return MEMD_OK;
   const cudaStream_t st = c->stream;
   if (vel) CK(cudaMemcpyAsync(c->P.v, vel, 3 * n * sizeof(double), cudaMemcpyHostToDevice, st));
   if (pos) {
-    double* pin = (double*)dalloc(c, 3 * n * sizeof(double) + 3 * n * sizeof(int));
-    if (!pin) return fail(c, MEMD_ERR_OOM, "set_particles scratch");
+    double* pin = c->pin;
     int* iin = (int*)(pin + 3 * n);
     CK(cudaMemcpyAsync(pin, pos, 3 * n * sizeof(double), cudaMemcpyHostToDevice, st));
     if (img)
@@ -1100,9 +1145,7 @@ memd_status memd_set_particles(memd_ctx* c, const double* pos, const double* vel
       CK(cudaMemcpyAsync(iin, c->P.img, 3 * n * sizeof(int), cudaMemcpyDeviceToDevice, st));
     launch_fold_init(c->mesh, c->P, pin, iin, &c->ds->err, st);
     CKL();
-    memd_status s = check_err(c);
-    dfree(c, pin);
-    if (s != MEMD_OK) return s;
+    return check_err(c);  // synchronises the stream
   } else if (img) {
     CK(cudaMemcpyAsync(c->P.img, img, 3 * n * sizeof(int), cudaMemcpyHostToDevice, st));
   }
@@ -1114,11 +1157,14 @@ memd_status memd_move(memd_ctx* c, const double* pos, const int32_t* img) {
   if (!c || !pos) return MEMD_ERR_INVALID;
   if (!c->initialised) return fail(c, MEMD_ERR_STATE, "memd_init_field first");
   CK(cudaSetDevice(c->device));
+  {
+    const memd_status fe = memd_flush(c);
+    if (fe != MEMD_OK) return fe;
+  }
   const size_t n = (size_t)c->P.n;
   if (!n) return MEMD_OK;
   const cudaStream_t st = c->stream;
-  double* pin = (double*)dalloc(c, 3 * n * sizeof(double) + 3 * n * sizeof(int));
-  if (!pin) return fail(c, MEMD_ERR_OOM, "move scratch");
+  double* pin = c->pin;
   int* iin = (int*)(pin + 3 * n);
   CK(cudaMemcpyAsync(pin, pos, 3 * n * sizeof(double), cudaMemcpyHostToDevice, st));
   if (img) CK(cudaMemcpyAsync(iin, img, 3 * n * sizeof(int), cudaMemcpyHostToDevice, st));
@@ -1128,14 +1174,16 @@ memd_status memd_move(memd_ctx* c, const double* pos, const int32_t* img) {
                std::ldexp(1.0, -48) / (c->mesh.a * c->mesh.a), st);
   launch_step_end(c->ds, 0, st);
   CKL();
-  memd_status s = check_err(c);
-  dfree(c, pin);
-  return s;
+  return check_err(c);
 }
 
 memd_status memd_get_fields(memd_ctx* c, double* D, double* B, int64_t* Lg) {
   if (!c) return MEMD_ERR_INVALID;
   CK(cudaSetDevice(c->device));
+  {
+    const memd_status fe = memd_flush(c);
+    if (fe != MEMD_OK) return fe;
+  }
   const size_t n3 = 3 * (size_t)c->mesh.V;
   const cudaStream_t st = c->stream;
   double* tmp = (double*)dalloc(c, n3 * sizeof(double));
@@ -1159,6 +1207,10 @@ memd_status memd_get_fields(memd_ctx* c, double* D, double* B, int64_t* Lg) {
 memd_status memd_set_fields(memd_ctx* c, const double* D, const double* B, const int64_t* Lg) {
   if (!c) return MEMD_ERR_INVALID;
   CK(cudaSetDevice(c->device));
+  {
+    const memd_status fe = memd_flush(c);
+    if (fe != MEMD_OK) return fe;
+  }
   const size_t n3 = 3 * (size_t)c->mesh.V;
   const cudaStream_t st = c->stream;
   double* tmp = (double*)dalloc(c, n3 * sizeof(double));
@@ -1184,6 +1236,10 @@ memd_status memd_compute_forces(memd_ctx* c) {
   if (!c) return MEMD_ERR_INVALID;
   if (!c->initialised) return fail(c, MEMD_ERR_STATE, "memd_init_field first");
   CK(cudaSetDevice(c->device));
+  {
+    const memd_status fe = memd_flush(c);
+    if (fe != MEMD_OK) return fe;
+  }
   const cudaStream_t st = c->stream;
   const StepParams sp = step_params(c, 0, 0.0, 0.0);
   launch_dipole(c->mesh, c->P, c->ds, st);

@@ -108,6 +108,11 @@ memd_status build_tables(memd_batch* b) {
   b->field_bytes = 0.0;
   for (int r = 0; r < R; ++r) {
     memd_ctx* c = b->m[r];
+    {
+      // transfers a member's single-launch steps left pending go in first
+      const memd_status fe = memd_flush(c);
+      if (fe != MEMD_OK) return bfail(b, fe, "member flush");
+    }
     RepDesc& d = desc[r];
     std::memset(&d, 0, sizeof(d));
     d.m = c->mesh;

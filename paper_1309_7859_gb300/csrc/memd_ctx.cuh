@@ -45,6 +45,9 @@ struct memd_ctx {
   double Minv[9] = {0};
   double eps_eff_inv[9] = {0};  // exact inverse of the effective permittivity (Minv symmetrised)
   double* psi = nullptr;        // cell-problem potentials of the scalar solver (3V), or null
+  double* pin = nullptr;        // memd_set_particles staging (3n doubles + 3n ints)
+  long long* Tb2 = nullptr;     // second transfer buffer of the single-launch step
+  bool pending = false;         // transfers of the last single-launch step not yet applied
   // particles
   Particles P{};
   bool initialised = false;
@@ -81,6 +84,7 @@ void memd_dfree(memd_ctx* c, void* p);
 size_t memd_esz(const memd_ctx* c);
 memd::StepParams memd_step_params(const memd_ctx* c, int thermo, double gamma, double kT);
 memd_status memd_check_err(memd_ctx* c);
+memd_status memd_flush(memd_ctx* c);  // apply pending transfers of the single-launch step
 // memd_mg.cu: effective permittivity and initial field through the scalar
 // potential (multigrid-preconditioned CG on the vertices)
 namespace memd {

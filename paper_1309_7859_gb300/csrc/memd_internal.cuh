@@ -187,8 +187,8 @@ int coop_grid(int prec, int device);                 // CTAs of one cooperative 
 int coop_zchunk(const Mesh& m, int grid);
 cudaError_t launch_step_coop(const Mesh& m, int prec, const StepParams& sp, Particles p,
                              const void* Din, const void* Bin, const void* ie, void* Dout,
-                             void* Bout, const double* ie64, long long* Tb, long long* Lg,
-                             DevState* ds, int grid, int zchunk, cudaStream_t st);
+                             void* Bout, const double* ie64, long long* Tprev, long long* Tcur,
+                             long long* Lg, DevState* ds, int grid, int zchunk, cudaStream_t st);
 void launch_fold_init(const Mesh& m, Particles p, const double* pos_in, const int* img_in,
                       unsigned int* err, cudaStream_t st);
 void launch_cic(const Mesh& m, Particles p, long long* Q, long long bg, cudaStream_t st);

@@ -544,7 +544,8 @@ __device__ __forceinline__ void gather_body(const Mesh& m, const StepParams& sp,
                                             double gamma, double kT, Particles P,
                                             const T* __restrict__ D, const T* __restrict__ ie,
                                             const double* __restrict__ ie64, DevState* ds,
-                                            int kick, int finish, unsigned nctas, int64_t g) {
+                                            int kick, int finish, unsigned nctas, int64_t g,
+                                            const long long* __restrict__ Tpend = nullptr) {
   const int64_t p = g >> 2;
   const int lane4 = (int)(g & 3);
   const bool active = p < P.n;
@@ -606,6 +607,10 @@ __device__ __forceinline__ void gather_body(const Mesh& m, const StepParams& sp,
       Dv[d] = __ldcg(D + l);  // D was updated in this launch by other CTAs (single launch)
       Iv[d] = ie[l];
       if (sp.self_mode != 0 && sizeof(T) == 8) I64[d] = ie64[l];
+      if (Tpend) {  // transfers of this step not yet applied: as their application rounds
+        const long long t = __ldcg(Tpend + l);
+        if (t != 0) Dv[d] = Dv[d] + (T)((double)t * sp.scale);
+      }
     }
 #pragma unroll
     for (int d = 0; d < 3; ++d) {
@@ -715,13 +720,18 @@ __global__ void __launch_bounds__(kBatchQuadThreads)
 }
 
 // ---------------------------------------------------- single-launch step
-// The whole time step of one system in one cooperative launch of G CTAs:
-// warps 0-10 of every CTA run field tiles (B' then D', one-thread-per-site
-// tiles of 8 rows) while warp 11 runs the kick, drift and deposition of its
-// particles; a grid barrier; warp 11 applies the transfers; a grid barrier;
-// warp 11 gathers the forces (Langevin, half kick), and the last CTA closes
-// the step.  Same device functions, hence the same results, as the four
-// launches of the graph step.
+// The whole time step of one system in one cooperative launch of G CTAs,
+// with one grid barrier.  The transfers of a step are applied lazily: they
+// stay in the transfer buffer Tcur, the gather reads D + Tcur scale (rounded
+// as their application rounds), and the next step's field tiles read their
+// D the same way from that buffer (then Tprev) before updating it; after
+// that step's barrier the field warps move Tprev into the ledger and clear
+// it.  Phase 1: warps 0-10 of every CTA run field tiles (B' then D',
+// one-thread-per-site tiles of 8 rows) while warp 11 runs the kick, drift
+// and deposition into Tcur; grid barrier; phase 2: warp 11 gathers the
+// forces (Langevin, half kick) while the field warps commit Tprev; the last
+// CTA closes the step.  The values are those of the four launches of the
+// graph step, bit for bit.
 
 // Grid-wide barrier of a cooperative launch: each CTA releases its writes
 // with its arrival, the last CTA to arrive acquires them all and opens the
@@ -771,43 +781,68 @@ struct FieldWarpsSync {
   }
 };
 
+// ledger += Tprev, Tprev = 0 on the sites a field thread updates
+__device__ __forceinline__ void commit_tile(const Mesh& m, int txi, int tyi, int tz, int zchunk,
+                                            int tx, int ty, bool live, long long* __restrict__ Tp,
+                                            long long* __restrict__ Lg) {
+  const int nx = m.n[0], ny = m.n[1];
+  const int x = txi * 32 - 1 + tx, y = tyi * 8 - 1 + ty;
+  if (!live || tx < 1 || tx > 32 || ty < 1 || ty > 8 || x >= nx || y >= ny) return;
+  const int z0 = tz * zchunk, z1 = min(z0 + zchunk, m.n[2]);
+  const int64_t P = (int64_t)nx * ny;
+  for (int k = z0; k < z1; ++k)
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      const int64_t l = (int64_t)c * m.V + (int64_t)k * P + (int64_t)y * nx + x;
+      const long long t = Tp[l];
+      if (t != 0) {
+        Lg[l] += t;
+        Tp[l] = 0;
+      }
+    }
+}
+
 template <typename T>
 __global__ void __launch_bounds__(kCoopThreads)
     k_step_coop(const __grid_constant__ Mesh m, const __grid_constant__ StepParams sp, Particles P,
                 const T* __restrict__ Din, const T* __restrict__ Bin, const T* __restrict__ ie,
                 T* __restrict__ Dout, T* __restrict__ Bout, const double* __restrict__ ie64,
-                unsigned long long* __restrict__ Tb, long long* __restrict__ Lg, DevState* ds,
-                int zchunk) {
+                long long* __restrict__ Tprev, unsigned long long* __restrict__ Tcur,
+                long long* __restrict__ Lg, DevState* ds, int zchunk) {
   const int tid = threadIdx.x;
   const bool pwarp = (tid >> 5) == kCoopFieldWarps;
   const unsigned G = gridDim.x;
   const int lane = tid & 31;
   const int64_t nq = 4 * P.n;  // quad lanes of all particles
   const int64_t stride = (int64_t)G * 32;
+  const int tiles_x = (m.n[0] + 31) / 32, tiles_y = (m.n[1] + 7) / 8;
+  const int tiles_z = (m.n[2] + zchunk - 1) / zchunk;
+  const int ntiles = tiles_x * tiles_y * tiles_z;
+  const bool live = tid < 34 * 10;
+  const int tx = live ? tid % 34 : 0, ty = live ? tid / 34 : 0;
   if (!pwarp) {
-    const int tiles_x = (m.n[0] + 31) / 32, tiles_y = (m.n[1] + 7) / 8;
-    const int tiles_z = (m.n[2] + zchunk - 1) / zchunk;
-    const int ntiles = tiles_x * tiles_y * tiles_z;
-    const bool live = tid < 34 * 10;
-    const int tx = live ? tid % 34 : 0, ty = live ? tid / 34 : 0;
     for (int t = blockIdx.x; t < ntiles; t += (int)G) {
       const int tz = t / (tiles_x * tiles_y), r = t - tz * (tiles_x * tiles_y);
       const int tyi = r / tiles_x, txi = r - tyi * tiles_x;
       site_tile<T, 8, 1>(m, Din, Bin, ie, Dout, Bout, (T)sp.coefB, (T)sp.coefD, txi, tyi, tz,
-                         zchunk, tx, ty, live, FieldWarpsSync{});
+                         zchunk, tx, ty, live, FieldWarpsSync{}, Tprev, sp.scale);
     }
   } else {
     for (int64_t b = (int64_t)blockIdx.x * 32; b < nq; b += stride)
-      deposit_body(m, sp, P, Tb, ds, b + lane);
+      deposit_body(m, sp, P, Tcur, ds, b + lane);
   }
   grid_barrier(ds, G);
-  if (pwarp)
+  if (pwarp) {
     for (int64_t b = (int64_t)blockIdx.x * 32; b < nq; b += stride)
-      apply_body<T>(m, P, Tb, Lg, Dout, sp.scale, b + lane);
-  grid_barrier(ds, G);
-  if (pwarp)
-    for (int64_t b = (int64_t)blockIdx.x * 32; b < nq; b += stride)
-      gather_body<T>(m, sp, sp.thermo, sp.gamma, sp.kT, P, Dout, ie, ie64, ds, 1, 0, G, b + lane);
+      gather_body<T>(m, sp, sp.thermo, sp.gamma, sp.kT, P, Dout, ie, ie64, ds, 1, 0, G, b + lane,
+                     (const long long*)Tcur);
+  } else {
+    for (int t = blockIdx.x; t < ntiles; t += (int)G) {
+      const int tz = t / (tiles_x * tiles_y), r = t - tz * (tiles_x * tiles_y);
+      const int tyi = r / tiles_x, txi = r - tyi * tiles_x;
+      commit_tile(m, txi, tyi, tz, zchunk, tx, ty, live, Tprev, Lg);
+    }
+  }
   finish_update(ds, 2, G);
 }
 
@@ -933,8 +968,8 @@ int coop_zchunk(const Mesh& m, int grid) {
 
 cudaError_t launch_step_coop(const Mesh& m, int prec, const StepParams& sp, Particles p,
                              const void* Din, const void* Bin, const void* ie, void* Dout,
-                             void* Bout, const double* ie64, long long* Tb, long long* Lg,
-                             DevState* ds, int grid, int zchunk, cudaStream_t st) {
+                             void* Bout, const double* ie64, long long* Tprev, long long* Tcur,
+                             long long* Lg, DevState* ds, int grid, int zchunk, cudaStream_t st) {
   cudaLaunchConfig_t cfg{};
   cfg.gridDim = dim3((unsigned)grid, 1, 1);
   cfg.blockDim = dim3(kCoopThreads, 1, 1);
@@ -945,14 +980,14 @@ cudaError_t launch_step_coop(const Mesh& m, int prec, const StepParams& sp, Part
   at[0].val.cooperative = 1;
   cfg.attrs = at;
   cfg.numAttrs = 1;
-  unsigned long long* tb = (unsigned long long*)Tb;
+  unsigned long long* tc = (unsigned long long*)Tcur;
   if (prec == 1)
     return cudaLaunchKernelEx(&cfg, k_step_coop<float>, m, sp, p, (const float*)Din,
                               (const float*)Bin, (const float*)ie, (float*)Dout, (float*)Bout, ie64,
-                              tb, Lg, ds, zchunk);
+                              Tprev, tc, Lg, ds, zchunk);
   return cudaLaunchKernelEx(&cfg, k_step_coop<double>, m, sp, p, (const double*)Din,
                             (const double*)Bin, (const double*)ie, (double*)Dout, (double*)Bout,
-                            ie64, tb, Lg, ds, zchunk);
+                            ie64, Tprev, tc, Lg, ds, zchunk);
 }
 
 void launch_gather(const Mesh& m, int prec, const StepParams& sp, Particles p, const void* D,

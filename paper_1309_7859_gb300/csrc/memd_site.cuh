@@ -16,6 +16,9 @@ namespace memd {
 // 9 PF values per thread are in flight while a plane is computed.  Same
 // arithmetic per site as k_fused_curl.
 //
+// Tp (optional): transfers not yet applied to D (int64, 3V): D(site) is
+// then read as D + Tp scale, rounded exactly as their application would.
+//
 // tx, ty: the thread's place in the 34 x (TY + 2) block; live == false for
 // threads of a larger block that hold no site: they run the same code with
 // every memory access switched off, so that all threads of a warp meet the
@@ -39,7 +42,9 @@ __device__ __forceinline__ void site_tile(const Mesh& m, const T* __restrict__ D
                                           const T* __restrict__ Bin, const T* __restrict__ ie,
                                           T* __restrict__ Dout, T* __restrict__ Bout, T cB, T cD,
                                           int tile_x, int tile_y, int tile_z, int zchunk, int tx,
-                                          int ty, bool live, Sync sync) {
+                                          int ty, bool live, Sync sync,
+                                          const long long* __restrict__ Tp = nullptr,
+                                          double tscale = 0.0) {
   static_assert(PF >= 1 && PF <= 2, "prefetch depth");
   constexpr int TX = 32, EX = TX + 2, EY = TY + 2;
   __shared__ T sE[3][3][EY][EX];
@@ -66,6 +71,16 @@ __device__ __forceinline__ void site_tile(const Mesh& m, const T* __restrict__ D
     r[0] = p[0];
     r[1] = p[V];
     r[2] = p[2 * V];
+  };
+  auto ldD = [&](int k, T (&r)[3]) {
+    ld3(Din, k, r);
+    if (!live || !Tp) return;
+    const long long* q = Tp + (int64_t)k * P + off;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      const long long t = q[c * V];
+      if (t != 0) r[c] = r[c] + (T)((double)t * tscale);
+    }
   };
   auto putE = [&](int slot, const T (&d)[3], const T (&i)[3]) {
     if (!live) return;
@@ -105,18 +120,18 @@ __device__ __forceinline__ void site_tile(const Mesh& m, const T* __restrict__ D
   {
     T dm[3] = {}, im[3] = {}, bm[3] = {}, i0[3] = {}, i1[3] = {};
     const int zm = wrapz(z0 - 1), zp = wrapz(z0 + 1);
-    ld3(Din, zm, dm);
+    ldD(zm, dm);
     ld3(ie, zm, im);
     ld3(Bin, zm, bm);
-    ld3(Din, z0, dq[0]);
+    ldD(z0, dq[0]);
     ld3(ie, z0, i0);
     ld3(Bin, z0, bq[0]);
-    ld3(Din, zp, dq[1]);
+    ldD(zp, dq[1]);
     ld3(ie, zp, i1);
 #pragma unroll
     for (int j = 0; j + 1 < PF; ++j)  // planes z0+2 .. z0+PF
       if (z0 + 2 + j <= z1) {
-        ld3(Din, wrapz(z0 + 2 + j), dq[2 + j]);
+        ldD(wrapz(z0 + 2 + j), dq[2 + j]);
         ld3(ie, wrapz(z0 + 2 + j), iq[j]);
       }
 #pragma unroll
@@ -132,7 +147,7 @@ __device__ __forceinline__ void site_tile(const Mesh& m, const T* __restrict__ D
   for (int k = z0; k < z1; ++k) {
     // issue plane k+PF+1 of D and 1/eps, plane k+PF of B
     if (k + PF + 1 <= z1) {
-      ld3(Din, wrapz(k + PF + 1), dq[PF + 1]);
+      ldD(wrapz(k + PF + 1), dq[PF + 1]);
       ld3(ie, wrapz(k + PF + 1), iq[PF - 1]);
     }
     if (k + PF < z1) ld3(Bin, wrapz(k + PF), bq[PF]);
