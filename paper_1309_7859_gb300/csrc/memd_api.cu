@@ -876,6 +876,15 @@ memd_status memd_init_field(memd_ctx* c, int64_t n, const double* pos, const int
 // The charge transfer of the drift runs on a side stream beside the fused
 // field update (neither reads what the other writes); the transfers are
 // applied to the new D, then the gather closes the step.
+// a timing event inside a captured graph is an external event node; outside
+// capture it is recorded as usual
+static cudaError_t record_timing_event(cudaEvent_t ev, cudaStream_t st) {
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  if (cudaStreamIsCapturing(st, &cs) != cudaSuccess) return cudaGetLastError();
+  return cs == cudaStreamCaptureStatusActive ? cudaEventRecordWithFlags(ev, st, cudaEventRecordExternal)
+                                             : cudaEventRecord(ev, st);
+}
+
 static memd_status record_step(memd_ctx* c, const StepParams& sp, int par, bool timed) {
   const Mesh& m = c->mesh;
   const cudaStream_t st = c->stream;
@@ -886,9 +895,9 @@ static memd_status record_step(memd_ctx* c, const StepParams& sp, int par, bool 
     launch_kick_drift_deposit(m, sp, c->P, c->Tb, c->ds, c->side);
     CK(cudaEventRecord(c->join, c->side));
   }
-  if (timed) CK(cudaEventRecordWithFlags(c->ev0, st, cudaEventRecordExternal));
+  if (timed) CK(record_timing_event(c->ev0, st));
   launch_field(c, par, sp.coefB, sp.coefD, c->fcfg);
-  if (timed) CK(cudaEventRecordWithFlags(c->ev1, st, cudaEventRecordExternal));
+  if (timed) CK(record_timing_event(c->ev1, st));
   if (serial)
     launch_kick_drift_deposit(m, sp, c->P, c->Tb, c->ds, st);
   else
@@ -907,13 +916,13 @@ static long long* tbuf(memd_ctx* c, int q) { return q == 0 ? c->Tb : c->Tb2; }
 // the whole step as one cooperative launch (same kernels' device functions)
 static memd_status record_step_coop(memd_ctx* c, const StepParams& sp, int par, bool timed) {
   const cudaStream_t st = c->stream;
-  if (timed) CK(cudaEventRecordWithFlags(c->ev0, st, cudaEventRecordExternal));
+  if (timed) CK(record_timing_event(c->ev0, st));
   const cudaError_t e = launch_step_coop(
       c->mesh, c->prec, sp, c->P, c->Dbuf[par], c->Bbuf[par], c->ie, c->Dbuf[par ^ 1],
       c->Bbuf[par ^ 1], c->ie64, tbuf(c, par), tbuf(c, par ^ 1), c->Lg, c->ds, c->coop_grid,
       coop_zchunk(c->mesh, c->coop_grid), st);
   if (e != cudaSuccess) return fail(c, MEMD_ERR_CUDA, cudaGetErrorString(e));
-  if (timed) CK(cudaEventRecordWithFlags(c->ev1, st, cudaEventRecordExternal));
+  if (timed) CK(record_timing_event(c->ev1, st));
   return MEMD_OK;
 }
 

@@ -545,7 +545,8 @@ __device__ __forceinline__ void gather_body(const Mesh& m, const StepParams& sp,
                                             const T* __restrict__ D, const T* __restrict__ ie,
                                             const double* __restrict__ ie64, DevState* ds,
                                             int kick, int finish, unsigned nctas, int64_t g,
-                                            const long long* __restrict__ Tpend = nullptr) {
+                                            const long long* __restrict__ Tpend = nullptr,
+                                            bool exact32 = false, const long long* pre = nullptr) {
   const int64_t p = g >> 2;
   const int lane4 = (int)(g & 3);
   const bool active = p < P.n;
@@ -568,15 +569,16 @@ __device__ __forceinline__ void gather_body(const Mesh& m, const StepParams& sp,
     hh = P.h[p];
     if (thermo) sig = P.sig[p];
   }
+  // pre (optional): the dipole sum and the step counter, read by the caller
   long long Pl[3] = {0, 0, 0};
   if (comp && sp.dipole_corr) {
-    Pl[0] = (long long)ds->Pacc[0];
-    Pl[1] = (long long)ds->Pacc[1];
-    Pl[2] = (long long)ds->Pacc[2];
+    Pl[0] = pre ? pre[0] : (long long)ds->Pacc[0];
+    Pl[1] = pre ? pre[1] : (long long)ds->Pacc[1];
+    Pl[2] = pre ? pre[2] : (long long)ds->Pacc[2];
   }
   unsigned rnd = 0;
   if (comp && thermo) {
-    const long long step = ds->step;
+    const long long step = pre ? pre[3] : ds->step;
     unsigned ctr[4] = {(unsigned)p, (unsigned)((unsigned long long)p >> 32), (unsigned)step,
                        (unsigned)((unsigned long long)step >> 32)};
     philox4x32_10(ctr, (unsigned)sp.seed, (unsigned)(sp.seed >> 32));
@@ -609,7 +611,7 @@ __device__ __forceinline__ void gather_body(const Mesh& m, const StepParams& sp,
       if (sp.self_mode != 0 && sizeof(T) == 8) I64[d] = ie64[l];
       if (Tpend) {  // transfers of this step not yet applied: as their application rounds
         const long long t = __ldcg(Tpend + l);
-        if (t != 0) Dv[d] = Dv[d] + (T)((double)t * sp.scale);
+        if (t != 0) Dv[d] = Dv[d] + pending_inc<T>(t, sp.scale, exact32);
       }
     }
 #pragma unroll
@@ -809,6 +811,7 @@ __global__ void __launch_bounds__(kCoopThreads)
                 T* __restrict__ Dout, T* __restrict__ Bout, const double* __restrict__ ie64,
                 long long* __restrict__ Tprev, unsigned long long* __restrict__ Tcur,
                 long long* __restrict__ Lg, DevState* ds, int zchunk) {
+  const bool exact32 = m.a_pow2 != 0;  // power-of-two scale (FP32 fields use it)
   const int tid = threadIdx.x;
   const bool pwarp = (tid >> 5) == kCoopFieldWarps;
   const unsigned G = gridDim.x;
@@ -825,7 +828,7 @@ __global__ void __launch_bounds__(kCoopThreads)
       const int tz = t / (tiles_x * tiles_y), r = t - tz * (tiles_x * tiles_y);
       const int tyi = r / tiles_x, txi = r - tyi * tiles_x;
       site_tile<T, 8, 1>(m, Din, Bin, ie, Dout, Bout, (T)sp.coefB, (T)sp.coefD, txi, tyi, tz,
-                         zchunk, tx, ty, live, FieldWarpsSync{}, Tprev, sp.scale);
+                         zchunk, tx, ty, live, FieldWarpsSync{}, Tprev, sp.scale, exact32);
     }
   } else {
     for (int64_t b = (int64_t)blockIdx.x * 32; b < nq; b += stride)
@@ -833,9 +836,37 @@ __global__ void __launch_bounds__(kCoopThreads)
   }
   grid_barrier(ds, G);
   if (pwarp) {
+    // the dipole sum of this move and the step counter, read once; this
+    // CTA's ticket follows at once, so the last CTA closes the step (P of
+    // this state reported, the sum cleared, the counter advanced) while the
+    // gathers still run: every CTA has read both before its ticket
+    long long pre[4] = {0, 0, 0, 0};
+    if (lane == 0) {
+      pre[0] = (long long)__ldcg(&ds->Pacc[0]);
+      pre[1] = (long long)__ldcg(&ds->Pacc[1]);
+      pre[2] = (long long)__ldcg(&ds->Pacc[2]);
+      pre[3] = __ldcg(&ds->step);
+      unsigned t;
+      asm volatile("atom.acq_rel.gpu.global.add.u32 %0, [%1], 1;"
+                   : "=r"(t)
+                   : "l"(&ds->ticket)
+                   : "memory");
+      if (t == G - 1) {
+        ds->Plast[0] = pre[0];
+        ds->Plast[1] = pre[1];
+        ds->Plast[2] = pre[2];
+        ds->Pacc[0] = 0ull;
+        ds->Pacc[1] = 0ull;
+        ds->Pacc[2] = 0ull;
+        ds->step = pre[3] + 1;
+        ds->ticket = 0u;
+      }
+    }
+#pragma unroll
+    for (int e = 0; e < 4; ++e) pre[e] = __shfl_sync(0xffffffffu, pre[e], 0);
     for (int64_t b = (int64_t)blockIdx.x * 32; b < nq; b += stride)
       gather_body<T>(m, sp, sp.thermo, sp.gamma, sp.kT, P, Dout, ie, ie64, ds, 1, 0, G, b + lane,
-                     (const long long*)Tcur);
+                     (const long long*)Tcur, exact32, pre);
   } else {
     for (int t = blockIdx.x; t < ntiles; t += (int)G) {
       const int tz = t / (tiles_x * tiles_y), r = t - tz * (tiles_x * tiles_y);
@@ -843,7 +874,6 @@ __global__ void __launch_bounds__(kCoopThreads)
       commit_tile(m, txi, tyi, tz, zchunk, tx, ty, live, Tprev, Lg);
     }
   }
-  finish_update(ds, 2, G);
 }
 
 __global__ void k_step_end(DevState* ds, int advance) {

@@ -17,7 +17,19 @@ namespace memd {
 // arithmetic per site as k_fused_curl.
 //
 // Tp (optional): transfers not yet applied to D (int64, 3V): D(site) is
-// then read as D + Tp scale, rounded exactly as their application would.
+// then read as D + Tp scale, rounded exactly as their application would
+// (pending_inc).
+
+// (T)((double)t * scale), the increment a transfer t adds to D.  With FP32
+// fields and a power-of-two scale (exact32) it is computed as the rounded
+// conversion of t to float times the scale, which is the same value (t is
+// exact in double, scaling by a power of two is exact, and rounding commutes
+// with it) without FP64 arithmetic.
+template <typename T>
+__device__ __forceinline__ T pending_inc(long long t, double scale, bool exact32) {
+  if (sizeof(T) == 4 && exact32) return (T)(__ll2float_rn(t) * (float)scale);
+  return (T)((double)t * scale);
+}
 //
 // tx, ty: the thread's place in the 34 x (TY + 2) block; live == false for
 // threads of a larger block that hold no site: they run the same code with
@@ -44,7 +56,7 @@ __device__ __forceinline__ void site_tile(const Mesh& m, const T* __restrict__ D
                                           int tile_x, int tile_y, int tile_z, int zchunk, int tx,
                                           int ty, bool live, Sync sync,
                                           const long long* __restrict__ Tp = nullptr,
-                                          double tscale = 0.0) {
+                                          double tscale = 0.0, bool exact32 = false) {
   static_assert(PF >= 1 && PF <= 2, "prefetch depth");
   constexpr int TX = 32, EX = TX + 2, EY = TY + 2;
   __shared__ T sE[3][3][EY][EX];
@@ -79,7 +91,7 @@ __device__ __forceinline__ void site_tile(const Mesh& m, const T* __restrict__ D
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
       const long long t = q[c * V];
-      if (t != 0) r[c] = r[c] + (T)((double)t * tscale);
+      if (t != 0) r[c] = r[c] + pending_inc<T>(t, tscale, exact32);
     }
   };
   auto putE = [&](int slot, const T (&d)[3], const T (&i)[3]) {

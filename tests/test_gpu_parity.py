@@ -347,3 +347,25 @@ def test_step_engines_bit_identical(mesh, n, eps, precision):
         g.close()
     for a, b in zip(out[0], out[1]):
         assert np.array_equal(np.asarray(a), np.asarray(b))
+
+
+@pytest.mark.parametrize("engine", ["graph", "single"])
+def test_direct_launches_match_graphs_with_timing(engine):
+    # the same steps launched directly (no CUDA graph) with kernel timing on
+    # give the graph-replayed result bit for bit
+    from paper_1309_7859_gb300.memd import Memd
+    sysc = small_system((24, 16, 12), 120, SLAB, precision="fp32", dt=0.005)
+    out = []
+    for graphs in (True, False):
+        g = Memd(sysc.mesh, sysc.box, sysc.eps, c_light=1.0, dt=sysc.dt, precision="fp32", seed=9,
+                 step_engine=engine, use_graphs=graphs, time_kernels=True)
+        g.init_field(sysc.x, sysc.q, sysc.m, sysc.v)
+        g.step(12, thermostat=(1.0, 1.0))
+        ks = g.kernel_stats()
+        assert ks.field_launches >= 1 and ks.field_ms > 0
+        D, B, Lg = g.fields()
+        x, v, img = g.particles()
+        out.append((D, B, Lg, x, v, img, g.forces()))
+        g.close()
+    for a, b in zip(out[0], out[1]):
+        assert np.array_equal(a, b)
