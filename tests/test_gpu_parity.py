@@ -103,9 +103,15 @@ def test_setup_matches_oracle(mesh, eps):
                                         ((40, 20, 12), 200, SLAB),
                                         ((33, 9, 7), 50, SINX),
                                         ((4, 4, 4), 6, EpsSpec("const", 0, (3.0,))),
-                                        ((2, 3, 2), 2, EpsSpec("const", 0, (1.0,)))])
+                                        ((2, 3, 2), 2, EpsSpec("const", 0, (1.0,))),
+                                        # multigrid levels with odd extents (aggregation)
+                                        ((36, 20, 10), 150, "vertices"),
+                                        ((45, 12, 14), 100, SLAB)])
 @pytest.mark.parametrize("precision", ["fp64", "fp32"])
 def test_initial_solution_matches_oracle(mesh, n, eps, precision):
+    if eps == "vertices":
+        vals = inputs.smooth_random_vertices(np.random.default_rng(8), mesh)
+        eps = EpsSpec("vertices", 0, (), vals)
     sysc = small_system(mesh, n, eps, precision=precision)
     g, o = make_pair(sysc)
     D, B, Lg = g.fields()
