@@ -109,9 +109,11 @@ typedef struct memd_options {
                              most 2^17 sites and 16 particles per SM), else the graph;
                              MEMD_STEP_GRAPH: four kernels a step (field update beside
                              the deposition, transfers, gather); MEMD_STEP_SINGLE: the
-                             whole step in one cooperative launch with two grid
-                             barriers (when the device supports cooperative launches,
-                             else the graph).  Both give identical results. */
+                             whole step in one cooperative launch with one grid
+                             barrier, its charge transfers applied lazily (every call
+                             that reads or replaces the state applies them first);
+                             when the device has no cooperative launches, the graph.
+                             Both give identical results. */
   int32_t reserved[5];
 } memd_options;
 
