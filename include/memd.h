@@ -145,13 +145,13 @@ typedef struct memd_kernel_stats {
   double field_bytes;     /* algorithmic bytes per field launch */
   int64_t launches_per_step;
   int32_t field_tma;      /* field kernel chosen at create: 1 TMA-staged, 0 plain loads */
-  int32_t field_ty;       /* its tile height (rows of 32 sites) */
+  int32_t field_ty;       /* its tile height (rows of field_tx sites) */
   int32_t field_zchunk;   /* its z planes per CTA */
   int32_t field_site;     /* k >= 1: the one-thread-per-site plain-load kernel, loads k
                              planes ahead */
   int32_t step_single;    /* 1: steps run as one cooperative launch; field_ms, field_bytes
                              and field_launches then time that whole kernel */
-  int32_t pad;
+  int32_t field_tx;       /* tile width in sites (32, or 16 in batches of narrow meshes) */
 } memd_kernel_stats;
 
 /* Fill *opt with defaults: FP64, GF self term, dipole correction on,

@@ -1283,6 +1283,7 @@ memd_status memd_get_kernel_stats(memd_ctx* c, memd_kernel_stats* out) {
   if (c->coop) out->field_bytes += 460.0 * (double)c->P.n;
   out->launches_per_step = c->coop ? 1 : (c->P.n > 0 ? 4 : 2);
   out->step_single = c->coop ? 1 : 0;
+  out->field_tx = 32;
   out->field_tma = c->fcfg.tma;
   out->field_ty = c->fcfg.ty;
   out->field_zchunk = c->fcfg.zchunk;

@@ -35,6 +35,7 @@ struct memd_batch {
   int n_field = 0, n_part = 0;
   double field_bytes = 0.0;
   int f_ty = kBatchTY, f_pf = kBatchPF32, f_z = kBatchZ;  // field tiles (autotuned)
+  int f_w = 32;                                          // tile width: 32 or 16 sites
   cudaGraphExec_t graph[2] = {nullptr, nullptr};
   int g_thermo = -1;
   double g_gamma = 0.0, g_kT = 0.0;
@@ -127,7 +128,7 @@ memd_status build_tables(memd_batch* b) {
     d.Lg = c->Lg;
     d.Tb = c->Tb;
     d.ds = c->ds;
-    d.f_tx = (c->mesh.n[0] + 31) / 32;
+    d.f_tx = (c->mesh.n[0] + b->f_w - 1) / b->f_w;
     d.f_ty = (c->mesh.n[1] + b->f_ty - 1) / b->f_ty;
     d.f_zchunk = std::min(c->mesh.n[2], b->f_z);
     const int nzc = (c->mesh.n[2] + d.f_zchunk - 1) / d.f_zchunk;
@@ -170,8 +171,8 @@ __global__ void k_read_flush(const float4* __restrict__ p, size_t n4, float* sin
   if (acc == 1234.5f) *sink = acc;  // keeps the loads
 }
 
-// Field tiles of the batched kernel: tile height 4 or 8 rows, loads 1 or 2
-// planes ahead, 4 to 32 planes per CTA, timed on the members' buffers (the
+// Field tiles of the batched kernel: tile width 32 or 16 sites, height 4 or
+// 8 rows, loads 1 or 2 planes ahead, 4 to 32 planes per CTA, timed on the members' buffers (the
 // update reads the current parity and writes the other one, which the next
 // step overwrites with the same values).  Each sample is one launch after
 // a 256 MiB read that evicts L2; median of 3 samples after a warm-up.
@@ -192,25 +193,27 @@ memd_status autotune_batch(memd_batch* b) {
   BCK(cudaEventCreate(&e0));
   BCK(cudaEventCreate(&e1));
   float best = 1e30f;
-  int bt = b->f_ty, bpf = b->f_pf, bz = b->f_z;
+  int bt = b->f_ty, bpf = b->f_pf, bz = b->f_z, bw = b->f_w;
   memd_status s = MEMD_OK;
+  for (int w = 32; w >= 16 && s == MEMD_OK; w /= 2)
   for (int a = 0; a < 2 && s == MEMD_OK; ++a)
     for (int pf = 1; pf <= pfs && s == MEMD_OK; ++pf)
       for (int zi = 0; zi < 4 && s == MEMD_OK; ++zi) {
+        b->f_w = w;
         b->f_ty = tys[a];
         b->f_pf = pf;
         b->f_z = zs[zi];
         s = build_tables(b);
         if (s != MEMD_OK) break;
         launch_fused_batch(b->prec, b->d_desc, b->d_field_rep, b->n_field, 0, b->f_ty, b->f_pf,
-                           b->stream);
+                           b->f_w, b->stream);
         float t[3];
         for (int r = 0; r < 3; ++r) {
           k_read_flush<<<4 * 152, 512, 0, b->stream>>>((const float4*)flush, flush_bytes / 16,
                                                         (float*)flush);
           cudaEventRecord(e0, b->stream);
           launch_fused_batch(b->prec, b->d_desc, b->d_field_rep, b->n_field, 0, b->f_ty, b->f_pf,
-                             b->stream);
+                             b->f_w, b->stream);
           cudaEventRecord(e1, b->stream);
           cudaEventSynchronize(e1);
           cudaEventElapsedTime(&t[r], e0, e1);
@@ -225,6 +228,7 @@ memd_status autotune_batch(memd_batch* b) {
           bt = b->f_ty;
           bpf = b->f_pf;
           bz = b->f_z;
+          bw = b->f_w;
         }
       }
   cudaEventDestroy(e0);
@@ -238,6 +242,7 @@ memd_status autotune_batch(memd_batch* b) {
   b->f_ty = bt;
   b->f_pf = bpf;
   b->f_z = bz;
+  b->f_w = bw;
   return build_tables(b);
 }
 
@@ -251,7 +256,7 @@ memd_status record(memd_batch* b, int par, int thermo, double gamma, double kT, 
     BCK(cudaEventRecord(b->join, b->side));
   }
   if (timed) BCK(cudaEventRecordWithFlags(b->ev0, st, cudaEventRecordExternal));
-  launch_fused_batch(b->prec, b->d_desc, b->d_field_rep, b->n_field, par, b->f_ty, b->f_pf, st);
+  launch_fused_batch(b->prec, b->d_desc, b->d_field_rep, b->n_field, par, b->f_ty, b->f_pf, b->f_w, st);
   if (timed) BCK(cudaEventRecordWithFlags(b->ev1, st, cudaEventRecordExternal));
   if (serial)
     launch_deposit_batch(b->d_desc, b->d_part_rep, b->n_part, thermo, gamma, kT, st);
@@ -414,6 +419,8 @@ memd_status memd_batch_kernel_stats(memd_batch* b, memd_kernel_stats* out) {
   out->launches_per_step = 4;
   out->field_tma = 0;
   out->field_ty = b->f_ty;
+  out->field_tma = 0;
+  out->field_tx = b->f_w;
   out->field_zchunk = b->f_z;
   out->field_site = b->f_pf;
   b->field_ms = 0.0;

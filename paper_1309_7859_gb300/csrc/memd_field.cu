@@ -331,17 +331,18 @@ __global__ void __launch_bounds__(34 * (TY + 2))
                        zchunk, threadIdx.x, threadIdx.y, true, CtaSync{});
 }
 
-template <typename T, int TY, int PF>
-__global__ void __launch_bounds__(34 * (TY + 2))
+template <typename T, int TY, int PF, int TX>
+__global__ void __launch_bounds__((TX + 2) * (TY + 2))
     k_fused_site_batch(const RepDesc* __restrict__ desc, const int* __restrict__ cta_rep, int par) {
   const RepDesc& r = desc[cta_rep[blockIdx.x]];
   const int local = blockIdx.x - r.f_first;
   const int per_z = r.f_tx * r.f_ty;
   const int tz = local / per_z, rem = local - tz * per_z;
   const int ty = rem / r.f_tx, tx = rem - ty * r.f_tx;
-  site_tile<T, TY, PF>(r.m, (const T*)r.D[par], (const T*)r.B[par], (const T*)r.ie,
-                       (T*)r.D[par ^ 1], (T*)r.B[par ^ 1], (T)r.sp.coefB, (T)r.sp.coefD, tx, ty,
-                       tz, r.f_zchunk, threadIdx.x, threadIdx.y, true, CtaSync{});
+  site_tile<T, TY, PF, CtaSync, TX>(r.m, (const T*)r.D[par], (const T*)r.B[par], (const T*)r.ie,
+                                    (T*)r.D[par ^ 1], (T*)r.B[par ^ 1], (T)r.sp.coefB,
+                                    (T)r.sp.coefD, tx, ty, tz, r.f_zchunk, threadIdx.x,
+                                    threadIdx.y, true, CtaSync{});
 }
 
 template <typename T, int TX, int TY>
@@ -691,33 +692,37 @@ FusedCfg fused_default(const Mesh& m) {
 
 namespace {
 template <typename T, int TY, int PF>
-void batch_launch_t(const RepDesc* desc, const int* cta_rep, int nctas, int par, cudaStream_t st) {
-  k_fused_site_batch<T, TY, PF><<<nctas, dim3(34, TY + 2, 1), 0, st>>>(desc, cta_rep, par);
+void batch_launch_t(const RepDesc* desc, const int* cta_rep, int nctas, int par, int tw,
+                    cudaStream_t st) {
+  if (tw == 16)
+    k_fused_site_batch<T, TY, PF, 16><<<nctas, dim3(18, TY + 2, 1), 0, st>>>(desc, cta_rep, par);
+  else
+    k_fused_site_batch<T, TY, PF, 32><<<nctas, dim3(34, TY + 2, 1), 0, st>>>(desc, cta_rep, par);
 }
 template <typename T>
 void batch_launch_ty(const RepDesc* desc, const int* cta_rep, int nctas, int par, int ty, int pf,
-                     cudaStream_t st) {
+                     int tw, cudaStream_t st) {
   if (ty == 4) {
     if (pf >= 2)
-      batch_launch_t<T, 4, 2>(desc, cta_rep, nctas, par, st);
+      batch_launch_t<T, 4, 2>(desc, cta_rep, nctas, par, tw, st);
     else
-      batch_launch_t<T, 4, 1>(desc, cta_rep, nctas, par, st);
+      batch_launch_t<T, 4, 1>(desc, cta_rep, nctas, par, tw, st);
   } else {
     if (pf >= 2)
-      batch_launch_t<T, 8, 2>(desc, cta_rep, nctas, par, st);
+      batch_launch_t<T, 8, 2>(desc, cta_rep, nctas, par, tw, st);
     else
-      batch_launch_t<T, 8, 1>(desc, cta_rep, nctas, par, st);
+      batch_launch_t<T, 8, 1>(desc, cta_rep, nctas, par, tw, st);
   }
 }
 }  // namespace
 
 void launch_fused_batch(int prec, const RepDesc* desc, const int* cta_rep, int nctas, int par,
-                        int ty, int pf, cudaStream_t st) {
+                        int ty, int pf, int tw, cudaStream_t st) {
   if (nctas <= 0) return;
   if (prec == 1)
-    batch_launch_ty<float>(desc, cta_rep, nctas, par, ty, pf, st);
+    batch_launch_ty<float>(desc, cta_rep, nctas, par, ty, pf, tw, st);
   else
-    batch_launch_ty<double>(desc, cta_rep, nctas, par, ty, pf, st);
+    batch_launch_ty<double>(desc, cta_rep, nctas, par, ty, pf, tw, st);
 }
 
 int fused_candidates(const Mesh& m, int prec, FusedCfg* out, int cap) {

@@ -236,7 +236,7 @@ constexpr int kBatchZ = 8;             // and its planes per CTA
 constexpr int kBatchQuadThreads = 128;  // 32 particles per CTA in the batched quad kernels
 // field update of every replica (memd_field.cu)
 void launch_fused_batch(int prec, const RepDesc* desc, const int* cta_rep, int nctas, int par,
-                        int ty, int pf, cudaStream_t st);
+                        int ty, int pf, int tw, cudaStream_t st);
 // particle kernels of every replica (memd_particles.cu); thermostat from the arguments
 void launch_deposit_batch(const RepDesc* desc, const int* cta_rep, int nctas, int thermo,
                           double gamma, double kT, cudaStream_t st);

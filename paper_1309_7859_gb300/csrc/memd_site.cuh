@@ -7,8 +7,8 @@
 namespace memd {
 
 // Fused field update, one thread per site of the tile and of its halo ring.
-// A CTA of 34 x (TY + 2) threads covers the 32 x TY tile plus one site on
-// every side.  Each thread loads D, 1/eps and B of its own site only (nine
+// A CTA of (TX + 2) x (TY + 2) threads covers the TX x TY tile (TX = 32, or 16
+// for narrow meshes) plus one site on every side.  Each thread loads D, 1/eps and B of its own site only (nine
 // values a plane, one base pointer), writes its E = D / eps into the shared
 // ring of planes k, k+1, k+2, computes B' at its site (tile and low halo),
 // and, inside the tile, D' from its own D kept in registers.  Loads run PF
@@ -49,7 +49,7 @@ __device__ __forceinline__ float fma_t<float>(float a, float b, float c) { retur
 template <>
 __device__ __forceinline__ double fma_t<double>(double a, double b, double c) { return __fma_rn(a, b, c); }
 
-template <typename T, int TY, int PF, class Sync>
+template <typename T, int TY, int PF, class Sync, int TX = 32>
 __device__ __forceinline__ void site_tile(const Mesh& m, const T* __restrict__ Din,
                                           const T* __restrict__ Bin, const T* __restrict__ ie,
                                           T* __restrict__ Dout, T* __restrict__ Bout, T cB, T cD,
@@ -58,7 +58,8 @@ __device__ __forceinline__ void site_tile(const Mesh& m, const T* __restrict__ D
                                           const long long* __restrict__ Tp = nullptr,
                                           double tscale = 0.0, bool exact32 = false) {
   static_assert(PF >= 1 && PF <= 2, "prefetch depth");
-  constexpr int TX = 32, EX = TX + 2, EY = TY + 2;
+  static_assert(TX == 16 || TX == 32, "tile width");
+  constexpr int EX = TX + 2, EY = TY + 2;
   __shared__ T sE[3][3][EY][EX];
   __shared__ T sB[2][3][EY][EX];
   const int nx = m.n[0], ny = m.n[1], nz = m.n[2];

@@ -108,7 +108,7 @@ class KernelStats(C.Structure):
     _fields_ = [("field_ms", C.c_double), ("field_launches", C.c_int64),
                 ("field_bytes", C.c_double), ("launches_per_step", C.c_int64),
                 ("field_tma", C.c_int32), ("field_ty", C.c_int32), ("field_zchunk", C.c_int32),
-                ("field_site", C.c_int32), ("step_single", C.c_int32), ("pad", C.c_int32)]
+                ("field_site", C.c_int32), ("step_single", C.c_int32), ("field_tx", C.c_int32)]
 
 
 _lib = None
@@ -461,7 +461,7 @@ class Batch:
         if st != 0:
             raise MemdError(st, "memd_batch_kernel_stats failed")
         return StepTiming(k.field_ms, k.field_launches, k.field_bytes, k.launches_per_step,
-                          f"k_fused_site_batch<ty={k.field_ty}, zchunk={k.field_zchunk}, "
+                          f"k_fused_site_batch<tx={k.field_tx}, ty={k.field_ty}, zchunk={k.field_zchunk}, "
                           f"planes_ahead={k.field_site}>")
 
     def close(self):
