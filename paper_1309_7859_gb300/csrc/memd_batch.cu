@@ -171,13 +171,14 @@ __global__ void k_read_flush(const float4* __restrict__ p, size_t n4, float* sin
   if (acc == 1234.5f) *sink = acc;  // keeps the loads
 }
 
-// Field tiles of the batched kernel: tile width 32 or 16 sites, height 4 or
-// 8 rows, loads 1 or 2 planes ahead, 4 to 32 planes per CTA, timed on the members' buffers (the
+// Field tiles of the batched kernel: tile width 32 or 16 sites, height 4, 8
+// or (FP32) 16 rows, loads 1 or 2 planes ahead, 4 to 32 planes per CTA, timed on the members' buffers (the
 // update reads the current parity and writes the other one, which the next
 // step overwrites with the same values).  Each sample is one launch after
 // a 256 MiB read that evicts L2; median of 3 samples after a warm-up.
 memd_status autotune_batch(memd_batch* b) {
-  static const int tys[2] = {4, 8}, zs[4] = {4, 8, 16, 32};
+  static const int tys[3] = {4, 8, 16}, zs[4] = {4, 8, 16, 32};
+  const int nty = b->prec == MEMD_FP32 ? 3 : 2;  // FP64 16-row tiles exceed static shared memory
   const int pfs = b->prec == MEMD_FP32 ? 2 : 1;  // FP64: one plane ahead (registers)
   const size_t flush_bytes = size_t(256) << 20;
   void* flush = nullptr;
@@ -196,7 +197,7 @@ memd_status autotune_batch(memd_batch* b) {
   int bt = b->f_ty, bpf = b->f_pf, bz = b->f_z, bw = b->f_w;
   memd_status s = MEMD_OK;
   for (int w = 32; w >= 16 && s == MEMD_OK; w /= 2)
-  for (int a = 0; a < 2 && s == MEMD_OK; ++a)
+  for (int a = 0; a < nty && s == MEMD_OK; ++a)
     for (int pf = 1; pf <= pfs && s == MEMD_OK; ++pf)
       for (int zi = 0; zi < 4 && s == MEMD_OK; ++zi) {
         b->f_w = w;

@@ -707,6 +707,11 @@ void batch_launch_ty(const RepDesc* desc, const int* cta_rep, int nctas, int par
       batch_launch_t<T, 4, 2>(desc, cta_rep, nctas, par, tw, st);
     else
       batch_launch_t<T, 4, 1>(desc, cta_rep, nctas, par, tw, st);
+  } else if (ty == 16 && sizeof(T) == 4) {
+    if (pf >= 2)
+      batch_launch_t<float, 16, 2>(desc, cta_rep, nctas, par, tw, st);
+    else
+      batch_launch_t<float, 16, 1>(desc, cta_rep, nctas, par, tw, st);
   } else {
     if (pf >= 2)
       batch_launch_t<T, 8, 2>(desc, cta_rep, nctas, par, tw, st);
