@@ -349,10 +349,14 @@ static memd_status relax(memd_ctx* c, double* D64, double tol, int maxit) {
       cudaGetLastError();
     }
     while (it < maxit) {
-      if (gexec)
-        CK(cudaGraphLaunch(gexec, st));
-      else
+      if (gexec) {
+        if (cudaGraphLaunch(gexec, st) != cudaSuccess) {
+          s = fail(c, MEMD_ERR_CUDA, "relaxation graph launch");
+          break;
+        }
+      } else {
         chunk();
+      }
       it += kChunk;
       if (cudaGetLastError() != cudaSuccess) {
         s = fail(c, MEMD_ERR_CUDA, "relaxation kernel launch");

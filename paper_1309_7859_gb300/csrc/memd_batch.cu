@@ -180,6 +180,12 @@ memd_status autotune_batch(memd_batch* b) {
   static const int tys[3] = {4, 8, 16}, zs[4] = {4, 8, 16, 32};
   const int nty = b->prec == MEMD_FP32 ? 3 : 2;  // FP64 16-row tiles exceed static shared memory
   const int pfs = b->prec == MEMD_FP32 ? 2 : 1;  // FP64: one plane ahead (registers)
+  cudaEvent_t e0, e1;
+  BCK(cudaEventCreate(&e0));
+  if (cudaEventCreate(&e1) != cudaSuccess) {
+    cudaEventDestroy(e0);
+    return bfail(b, MEMD_ERR_CUDA, "events");
+  }
   const size_t flush_bytes = size_t(256) << 20;
   void* flush = nullptr;
   if (b->alloc) {
@@ -188,11 +194,12 @@ memd_status autotune_batch(memd_batch* b) {
     cudaGetLastError();
     flush = nullptr;
   }
-  if (!flush) return build_tables(b);  // no room to tune: keep the defaults
+  if (!flush) {  // no room to tune: keep the defaults
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    return build_tables(b);
+  }
   cudaMemsetAsync(flush, 0, flush_bytes, b->stream);
-  cudaEvent_t e0, e1;
-  BCK(cudaEventCreate(&e0));
-  BCK(cudaEventCreate(&e1));
   float best = 1e30f;
   int bt = b->f_ty, bpf = b->f_pf, bz = b->f_z, bw = b->f_w;
   memd_status s = MEMD_OK;

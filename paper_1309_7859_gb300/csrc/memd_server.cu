@@ -74,6 +74,7 @@ struct memd_server {
   std::vector<std::pair<Req*, memd_status>> ready;
   int in_flight = 0;
   bool stop = false;
+  bool own_stream = false;  // the server created opt.cuda_stream
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;  // around the last batch step
   bool step_timed = false;
 };
@@ -263,7 +264,7 @@ memd_status memd_server_create(const memd_server_options* opt, memd_server** out
       return MEMD_ERR_CUDA;
     }
     s->opt.cuda_stream = st;
-    s->opt.reserved[0] = 1;  // owned
+    s->own_stream = true;
   }
   *out = s;
   return MEMD_OK;
@@ -278,7 +279,7 @@ void memd_server_destroy(memd_server* s) {
     if (kv.second.ctx) memd_destroy(kv.second.ctx);
   if (s->ev0) cudaEventDestroy(s->ev0);
   if (s->ev1) cudaEventDestroy(s->ev1);
-  if (s->opt.reserved[0]) cudaStreamDestroy((cudaStream_t)s->opt.cuda_stream);
+  if (s->own_stream) cudaStreamDestroy((cudaStream_t)s->opt.cuda_stream);
   delete s;
 }
 
