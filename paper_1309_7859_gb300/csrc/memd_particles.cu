@@ -205,9 +205,13 @@ __device__ inline void deposit_axis(const Mesh& m, int d, int q, int c0, int f0,
 // commits the move, or leaves the particle where it was (ok == false) when
 // some axis would cross more than one cell.  Every lane of the warp must
 // call this; inactive lanes pass active = false.
+// pf_ie (optional, element size pf_es): 1/eps in the field precision; the
+// links of the cell the charge ends in, which the gather reads next, and the
+// charge's mass, valence and noise amplitude are then prefetched into L2.
 __device__ inline void quad_move(const Mesh& m, Particles P, int64_t p, int d, bool active,
                                  double x, int ko, double xn, int kn, bool ok_in,
-                                 unsigned long long* __restrict__ Tb, DevState* ds) {
+                                 unsigned long long* __restrict__ Tb, DevState* ds,
+                                 const char* pf_ie = nullptr, int pf_es = 0) {
   const unsigned full = 0xffffffffu;
   const int lane = threadIdx.x & 31, base = lane & ~3;
   int c0 = 0, f0 = 0, c1 = 0, f1 = 0, dc = 0;
@@ -229,6 +233,24 @@ __device__ inline void quad_move(const Mesh& m, Particles P, int64_t p, int d, b
     F0[e] = __shfl_sync(full, f0, base + e);
     C1[e] = __shfl_sync(full, c1, base + e);
     F1[e] = __shfl_sync(full, f1, base + e);
+  }
+  if (pf_ie && active) {
+    // quad lane d holds corner (d & 1, d >> 1): its three links of the final cell
+    const int a1 = d & 1, a2 = d >> 1;
+#pragma unroll
+    for (int e = 0; e < 3; ++e) {
+      const int e1 = (e + 1) % 3, e2 = (e + 2) % 3;
+      int at[3] = {all_ok ? C1[0] : C0[0], all_ok ? C1[1] : C0[1], all_ok ? C1[2] : C0[2]};
+      at[e1] += a1;
+      at[e2] += a2;
+      const char* a = pf_ie + link_index(m, e, at[0], at[1], at[2]) * pf_es;
+      asm volatile("prefetch.global.L2 [%0];" ::"l"(a));
+    }
+    if (d == 0) {
+      asm volatile("prefetch.global.L2 [%0];" ::"l"(P.m + p));
+      asm volatile("prefetch.global.L2 [%0];" ::"l"(P.sig + p));
+      asm volatile("prefetch.global.L2 [%0];" ::"l"(P.q + p));
+    }
   }
   long long U = 0;
   if (active && d < 3) {
@@ -322,7 +344,8 @@ __global__ void k_particle_constants(StepParams sp, Particles P) {
 // g is the thread's index within its system
 __device__ __forceinline__ void deposit_body(const Mesh& m, const StepParams& sp, Particles P,
                                              unsigned long long* __restrict__ Tb, DevState* ds,
-                                             int64_t g) {
+                                             int64_t g, const char* pf_ie = nullptr,
+                                             int pf_es = 0) {
   const int64_t p = g >> 2;
   const int d = (int)(g & 3);
   const bool active = p < P.n;
@@ -344,7 +367,7 @@ __device__ __forceinline__ void deposit_body(const Mesh& m, const StepParams& sp
       ok = false;
     }
   }
-  quad_move(m, P, p, d, active, x, ko, xn, kn, ok, Tb, ds);
+  quad_move(m, P, p, d, active, x, ko, xn, kn, ok, Tb, ds, pf_ie, pf_es);
 }
 
 __global__ void __launch_bounds__(kQuadThreads)
@@ -832,38 +855,23 @@ __global__ void __launch_bounds__(kCoopThreads)
     }
   } else {
     for (int64_t b = (int64_t)blockIdx.x * 32; b < nq; b += stride)
-      deposit_body(m, sp, P, Tcur, ds, b + lane);
+      deposit_body(m, sp, P, Tcur, ds, b + lane, (const char*)ie, (int)sizeof(T));
   }
   grid_barrier(ds, G);
   if (pwarp) {
-    // the dipole sum of this move and the step counter, read once; this
-    // CTA's ticket follows at once, so the last CTA closes the step (P of
-    // this state reported, the sum cleared, the counter advanced) while the
-    // gathers still run: every CTA has read both before its ticket
-    long long pre[4] = {0, 0, 0, 0};
-    if (lane == 0) {
-      pre[0] = (long long)__ldcg(&ds->Pacc[0]);
-      pre[1] = (long long)__ldcg(&ds->Pacc[1]);
-      pre[2] = (long long)__ldcg(&ds->Pacc[2]);
-      pre[3] = __ldcg(&ds->step);
-      unsigned t;
-      asm volatile("atom.acq_rel.gpu.global.add.u32 %0, [%1], 1;"
-                   : "=r"(t)
-                   : "l"(&ds->ticket)
-                   : "memory");
-      if (t == G - 1) {
-        ds->Plast[0] = pre[0];
-        ds->Plast[1] = pre[1];
-        ds->Plast[2] = pre[2];
-        ds->Pacc[0] = 0ull;
-        ds->Pacc[1] = 0ull;
-        ds->Pacc[2] = 0ull;
-        ds->step = pre[3] + 1;
-        ds->ticket = 0u;
-      }
-    }
-#pragma unroll
-    for (int e = 0; e < 4; ++e) pre[e] = __shfl_sync(0xffffffffu, pre[e], 0);
+    // the dipole sum of this move and the step counter, read once; the
+    // particle warp then signals field warp 0 (named barrier 2), which takes
+    // the CTA's ticket while the gather runs, so the last CTA closes the step
+    // (P of this state reported, the sum cleared, the counter advanced) off
+    // the gather's path.  Every CTA's reads are complete before its signal:
+    // the signal consumes them.
+    long long pre[4];
+    pre[0] = (long long)__ldcg(&ds->Pacc[0]);
+    pre[1] = (long long)__ldcg(&ds->Pacc[1]);
+    pre[2] = (long long)__ldcg(&ds->Pacc[2]);
+    pre[3] = __ldcg(&ds->step);
+    const long long used = ((pre[0] ^ pre[1]) ^ pre[2]) ^ pre[3];
+    asm volatile("bar.arrive 2, 64;" ::"l"(used) : "memory");
     for (int64_t b = (int64_t)blockIdx.x * 32; b < nq; b += stride)
       gather_body<T>(m, sp, sp.thermo, sp.gamma, sp.kT, P, Dout, ie, ie64, ds, 1, 0, G, b + lane,
                      (const long long*)Tcur, exact32, pre);
@@ -872,6 +880,29 @@ __global__ void __launch_bounds__(kCoopThreads)
       const int tz = t / (tiles_x * tiles_y), r = t - tz * (tiles_x * tiles_y);
       const int tyi = r / tiles_x, txi = r - tyi * tiles_x;
       commit_tile(m, txi, tyi, tz, zchunk, tx, ty, live, Tprev, Lg);
+    }
+    if (tid < 32) {
+      asm volatile("bar.sync 2, 64;" ::: "memory");
+      if (tid == 0) {
+        unsigned t;
+        asm volatile("atom.acq_rel.gpu.global.add.u32 %0, [%1], 1;"
+                     : "=r"(t)
+                     : "l"(&ds->ticket)
+                     : "memory");
+        if (t == G - 1) {
+          const unsigned long long p0 = __ldcg(&ds->Pacc[0]), p1 = __ldcg(&ds->Pacc[1]),
+                                   p2 = __ldcg(&ds->Pacc[2]);
+          const long long st = __ldcg(&ds->step);
+          ds->Plast[0] = (long long)p0;
+          ds->Plast[1] = (long long)p1;
+          ds->Plast[2] = (long long)p2;
+          ds->Pacc[0] = 0ull;
+          ds->Pacc[1] = 0ull;
+          ds->Pacc[2] = 0ull;
+          ds->step = st + 1;
+          ds->ticket = 0u;
+        }
+      }
     }
   }
 }
