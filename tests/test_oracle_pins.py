@@ -276,6 +276,47 @@ def test_self_force_symmetry_and_direct_reduces_to_gf():
         assert abs(Ug - Ud) < 1e-15 and np.max(np.abs(Fg - Fd)) < 1e-15
 
 
+# ------------------------------------------------------ planar dielectric jump
+def image_force_z(ein, eout, d, W, L):
+    # charge +1 in a slab of eps_in, a distance d below its upper face, its
+    # partner -1 at the same height L/2 away along x; continuum image charges
+    # q' = (eps_in - eps_out) / (eps_in + eps_out) q for each face (first
+    # reflection only), Coulomb constant 1 / (4 pi eps_in): own images above
+    # (distance 2d) and below (2(W - d)), and the partner's two images
+    beta = (ein - eout) / (ein + eout)
+    k = 1.0 / (4.0 * math.pi * ein)
+    own = -beta * k / (2 * d) ** 2 + beta * k / (2 * (W - d)) ** 2
+    r1, r2 = math.hypot(L / 2, 2 * d), math.hypot(L / 2, 2 * (W - d))
+    partner = beta * k * 2 * d / r1 ** 3 - beta * k * 2 * (W - d) / r2 ** 3
+    return own + partner
+
+
+@pytest.mark.parametrize("ein,eout,d", [(10.0, 15.0, 4.0), (10.0, 15.0, 5.0), (15.0, 10.0, 4.0)])
+def test_static_force_near_a_planar_dielectric_jump_matches_image_charges(ein, eout, d):
+    # The force on a charge near a flat interface between two dielectrics is
+    # that of its image charge (method of images for a planar boundary; the
+    # paper compares MEMD with image-charge/ICC results for such geometries).
+    # Weak contrast (|beta| = 0.2) keeps the multiple reflections below 5%;
+    # the lattice (linear charge assignment, eps sampled at link midpoints
+    # across a 0.5-wide tanh step) adds the rest: 25% at d = 4-5 cells.  A
+    # wrong sign, a factor 2, or eps on the wrong side of the face fails.
+    N, W, c = 32, 16.0, 16.0
+    z = c + W / 2 - d
+    x = np.array([[N / 4 + 0.5, N / 2 + 0.5, z], [3 * N / 4 + 0.5, N / 2 + 0.5, z]])
+    q = np.array([1, -1], dtype=np.int32)
+    o = O.OracleSystem((N,) * 3, (float(N),) * 3,
+                       eps=dict(kind=O.EPS_TANH, axis=2,
+                                params=(0.5 * (ein + eout), 0.5 * (eout - ein), c, W / 2, 0.5)),
+                       c_light=1.0, dt=0.01, seed=1, relax_tol=1e-9)
+    o.set_particles(x, q, np.ones(2), np.zeros((2, 3)))
+    o.init_field()
+    F = o.particles("F")
+    want = image_force_z(ein, eout, d, W, N)
+    assert np.sign(F[0, 2]) == np.sign(want) and np.sign(F[1, 2]) == np.sign(want)
+    assert abs(F[0, 2] / want - 1.0) < 0.25 and abs(F[1, 2] / want - 1.0) < 0.25
+    assert abs(F[0, 0]) < 1e-6 * abs(want) + 1e-12   # the pair's x forces cancel by symmetry
+
+
 # ---------------------------------------------------------- Ewald comparison
 def test_static_forces_converge_to_tinfoil_ewald():
     # The lattice force with the charge-conserving linear scheme is the exact
