@@ -19,6 +19,9 @@
  *   DIRECT self term                    parity unpinned (Eq. 29 is garbled;
  *                                       pinned only by its reduction to GF)
  *   dipole correction, eps_eff          pinned (layered closed forms)
+ *   interface links (planes, ball, cut) pinned (series closed form across
+ *                                       off-lattice planes, chord lengths
+ *                                       of a ball, image-charge force)
  */
 #include "memd_oracle.h"
 
@@ -120,7 +123,134 @@ static double eps_profile_at(const orc_sys *s, const orc_eps *e, double pos) {
   return p[0] + p[1] * sin(2.0 * M_PI * pos / s->L[e->axis] + p[2]);
 }
 
+/* Eq. (dielectric-interpolation).  The text calls the interface-link value a
+ * harmonic average; the printed expression eps1 d2/a + eps2 d1/a is its
+ * denominator, the numerator eps1 eps2 being lost:
+ *   eps_link = eps1 eps2 / (eps1 d2 / a + eps2 d1 / a),
+ * where d1 (d2) is the distance from the first (second) end of the link to
+ * the interface, d1 + d2 = a.  Equivalently 1/eps_link is the mean of 1/eps
+ * along the link, i.e. the two media in series. */
+static double interface_link_eps(double eps1, double eps2, double d1, double a) {
+  double d2 = a - d1;
+  return eps1 * eps2 / (eps1 * d2 / a + eps2 * d1 / a);
+}
+
+/* periodic representative of x (in cells) on a ring of n cells, in
+ * [-n/2, n/2] */
+static double min_image(double x, int32_t n) {
+  return x - (double)n * round(x / (double)n);
+}
+
+static double clamp01(double t) { return t < 0.0 ? 0.0 : (t > 1.0 ? 1.0 : t); }
+
+/* Two-medium profiles place each vertex inside (+1), outside (-1) or exactly
+ * on the interface (0); a vertex on the interface takes the mean of the two
+ * media, so that a link lying in the interface gets their average.
+ *
+ * Planar slab: eps_in (p1) between the planes s = p2 and s = p3 normal to
+ * the axis, eps_out (p0) elsewhere, 0 <= p2 <= p3 < L; positions in cells. */
+static int planes_side(const orc_sys *s, const orc_eps *e, int64_t k) {
+  if (e->params[2] == e->params[3]) return -1;
+  double u_lo = e->params[2] / s->a, u_hi = e->params[3] / s->a, u = (double)k;
+  if (u == u_lo || u == u_hi) return 0;
+  return (u > u_lo && u < u_hi) ? 1 : -1;
+}
+
+/* ball: eps_in (p1) closer than p5 to the centre (p2, p3, p4) in the
+ * periodic metric, eps_out (p0) farther; offsets in cells */
+static void sphere_offset(const orc_sys *s, const orc_eps *e, const int64_t c[3], double del[3]) {
+  for (int d = 0; d < 3; ++d) del[d] = min_image((double)c[d] - e->params[2 + d] / s->a, s->N[d]);
+}
+
+static int sphere_side(const orc_sys *s, const orc_eps *e, const int64_t c[3]) {
+  double del[3], r = e->params[5] / s->a;
+  sphere_offset(s, e, c, del);
+  double r2 = del[0] * del[0] + del[1] * del[1] + del[2] * del[2];
+  double rr = r * r;
+  return r2 < rr ? 1 : (r2 == rr ? 0 : -1);
+}
+
+static int vertex_side(const orc_sys *s, const orc_eps *e, const int64_t c[3]) {
+  return e->kind == ORC_EPS_PLANES ? planes_side(s, e, c[e->axis]) : sphere_side(s, e, c);
+}
+
+static double side_eps(const orc_eps *e, int side) {
+  return side > 0 ? e->params[1] : (side < 0 ? e->params[0] : 0.5 * (e->params[0] + e->params[1]));
+}
+
+/* value of the profile at vertex c for the kinds defined per vertex */
+static double vertex_eps(const orc_sys *s, const orc_eps *e, const int64_t c[3]) {
+  switch (e->kind) {
+  case ORC_EPS_PLANES:
+  case ORC_EPS_SPHERE: return side_eps(e, vertex_side(s, e, c));
+  default: return e->values[vidx(s, c[0], c[1], c[2])]; /* VERTICES, CUT */
+  }
+}
+
+/* where the interface cuts the link from vertex c (end 1) along d to its
+ * neighbour c2 (end 2), as a fraction of a from end 1, for a link whose end
+ * values differ; negative if the link is not an interface link */
+static double interface_cut(const orc_sys *s, const orc_eps *e, const int64_t c[3],
+                            const int64_t c2[3], int d, int64_t l, double eps1, double eps2) {
+  switch (e->kind) {
+  case ORC_EPS_VERTICES: {
+    double lo = eps1 < eps2 ? eps1 : eps2;
+    /* no position is known: the interface sits at the link midpoint */
+    return (e->params[0] > 0.0 && fabs(eps2 - eps1) > e->params[0] * lo) ? 0.5 : -1.0;
+  }
+  case ORC_EPS_CUT: {
+    double t = e->values[s->V + l];
+    return (t >= 0.0 && t <= 1.0) ? t : -1.0;
+  }
+  case ORC_EPS_PLANES:
+  case ORC_EPS_SPHERE: {
+    int s1 = vertex_side(s, e, c), s2 = vertex_side(s, e, c2);
+    if (s1 == 0) return 0.0; /* the interface passes through an end */
+    if (s2 == 0) return 1.0;
+    if (e->kind == ORC_EPS_PLANES) {
+      /* entering the slab crosses the plane p2, leaving it the plane p3 */
+      double face = (s1 < 0 ? e->params[2] : e->params[3]) / s->a;
+      return clamp01(face - (double)c[d]);
+    }
+    /* the line c + t e_d meets the sphere where (del_d + t)^2 + rho^2 = r^2:
+     * leaving at the larger root, entering at the smaller */
+    double del[3], r = e->params[5] / s->a;
+    sphere_offset(s, e, c, del);
+    int d1 = d == 0 ? 1 : 0, d2 = d == 2 ? 1 : 2;
+    double rho2 = del[d1] * del[d1] + del[d2] * del[d2];
+    double h2 = r * r - rho2;
+    double h = h2 > 0.0 ? sqrt(h2) : 0.0;
+    return clamp01(s1 > 0 ? -del[d] + h : -del[d] - h);
+  }
+  default: return -1.0;
+  }
+}
+
+static int eps_profile_valid(const orc_sys *s, const orc_eps *e) {
+  const double *p = e->params;
+  switch (e->kind) {
+  case ORC_EPS_CONST: return 1;
+  case ORC_EPS_LINKS: return e->values != NULL;
+  case ORC_EPS_VERTICES: return e->values != NULL && p[0] >= 0.0 && isfinite(p[0]);
+  case ORC_EPS_CUT: return e->values != NULL;
+  case ORC_EPS_TANH:
+  case ORC_EPS_SIN: return e->axis >= 0 && e->axis <= 2;
+  case ORC_EPS_PLANES:
+    return e->axis >= 0 && e->axis <= 2 && p[0] > 0.0 && p[1] > 0.0 && isfinite(p[0]) &&
+           isfinite(p[1]) && p[2] >= 0.0 && p[2] <= p[3] && p[3] < s->L[e->axis];
+  case ORC_EPS_SPHERE: {
+    if (!(p[0] > 0.0 && p[1] > 0.0 && isfinite(p[0]) && isfinite(p[1]) && p[5] > 0.0))
+      return 0;
+    for (int d = 0; d < 3; ++d)
+      if (!isfinite(p[2 + d]) || !(p[5] + s->a < 0.5 * s->L[d])) return 0;
+    return 1;
+  }
+  default: return 0;
+  }
+}
+
 static int map_eps(orc_sys *s, const orc_eps *e) {
+  if (!eps_profile_valid(s, e)) return ORC_ERR_INVALID;
   int64_t V = s->V;
   for (int d = 0; d < 3; ++d) {
     for (int64_t v = 0; v < V; ++v) {
@@ -131,11 +261,23 @@ static int map_eps(orc_sys *s, const orc_eps *e) {
       case ORC_EPS_CONST: eps = e->params[0]; break;
       case ORC_EPS_LINKS: eps = e->values[d * V + v]; break;
       case ORC_EPS_VERTICES:
-        eps = 0.5 * (e->values[v] + e->values[vshift(s, c, d, 1)]);
+      case ORC_EPS_CUT:
+      case ORC_EPS_PLANES:
+      case ORC_EPS_SPHERE: {
+        /* end values; an interface link takes Eq. (dielectric-interpolation),
+         * any other link the mean of its ends (Fig. 2b) */
+        int64_t c2[3] = {c[0], c[1], c[2]};
+        c2[d] = (c[d] + 1) % s->N[d];
+        double eps1 = vertex_eps(s, e, c), eps2 = vertex_eps(s, e, c2);
+        double t = eps1 != eps2 ? interface_cut(s, e, c, c2, d, d * V + v, eps1, eps2) : -1.0;
+        if (t >= 0.0)
+          eps = interface_link_eps(eps1, eps2, t * s->a, s->a);
+        else
+          eps = 0.5 * (eps1 + eps2);
         break;
+      }
       case ORC_EPS_TANH:
       case ORC_EPS_SIN: {
-        if (e->axis < 0 || e->axis > 2) return ORC_ERR_INVALID;
         double pos = (double)c[e->axis] * s->a;
         if (d == e->axis) pos += 0.5 * s->a;
         eps = eps_profile_at(s, e, pos);
@@ -834,14 +976,9 @@ int32_t orc_move(orc_sys *s, const double *x_new, const int32_t *img_new) {
  * Sec. II: Gauss solution by the recursive scheme of Fig. 1 (exact, int64),
  * the k = 0 mode set to -P/V (Sec. V), relaxation to curl E = 0, B = 0 from
  * the initial condition dTheta/dt(0) = 0 (Eq. 13), then the forces. */
-int32_t orc_init_field(orc_sys *s) {
-  int64_t *Q = (int64_t *)malloc(sizeof(int64_t) * s->V);
-  if (!Q) return ORC_ERR_OOM;
-  orc_cic_charges(s, Q);
-  int32_t st = orc_gauss_scan(s->N, Q, s->Lg);
-  free(Q);
-  if (st != ORC_OK) return st;
-  memset(s->Tb, 0, sizeof(int64_t) * 3 * s->V);
+/* Sec. II and V: D from the exact flux ledger, its k = 0 mode set to -P/V,
+ * then relaxed to curl E = 0; B = 0 and the forces gathered */
+static int32_t field_from_ledger(orc_sys *s) {
   double scale = ldexp(1.0, -48) / (s->a * s->a);
   double P[3];
   dipole(s, P);
@@ -852,10 +989,43 @@ int32_t orc_init_field(orc_sys *s) {
     for (int64_t v = 0; v < s->V; ++v)
       s->D[d * s->V + v] = (double)s->Lg[d * s->V + v] * scale + shift;
   }
-  st = orc_relax(s, s->relax_tol, s->relax_maxit, NULL);
+  int32_t st = orc_relax(s, s->relax_tol, s->relax_maxit, NULL);
   if (st != ORC_OK) return st;
   memset(s->B, 0, sizeof(double) * 3 * s->V);
+  orc_gather(s);
+  return ORC_OK;
+}
+
+int32_t orc_init_field(orc_sys *s) {
+  int64_t *Q = (int64_t *)malloc(sizeof(int64_t) * s->V);
+  if (!Q) return ORC_ERR_OOM;
+  orc_cic_charges(s, Q);
+  int32_t st = orc_gauss_scan(s->N, Q, s->Lg);
+  free(Q);
+  if (st != ORC_OK) return st;
+  memset(s->Tb, 0, sizeof(int64_t) * 3 * s->V);
   s->step = 0;
+  return field_from_ledger(s);
+}
+
+int32_t orc_set_eps(orc_sys *s, const orc_eps *eps, int32_t relax) {
+  size_t bytes = sizeof(double) * 3 * s->V;
+  double *ie0 = (double *)malloc(bytes), *D0 = (double *)malloc(bytes), M0[9];
+  if (!ie0 || !D0) { free(ie0); free(D0); return ORC_ERR_OOM; }
+  memcpy(ie0, s->ie, bytes);
+  memcpy(D0, s->D, bytes);
+  memcpy(M0, s->Minv, sizeof(M0));
+  int32_t st = map_eps(s, eps);
+  if (st == ORC_OK) st = eps_effective(s); /* uses D as scratch */
+  memcpy(s->D, D0, bytes);
+  if (st != ORC_OK) {
+    memcpy(s->ie, ie0, bytes);
+    memcpy(s->Minv, M0, sizeof(M0));
+  }
+  free(ie0);
+  free(D0);
+  if (st != ORC_OK) return st;
+  if (relax) return field_from_ledger(s);
   orc_gather(s);
   return ORC_OK;
 }

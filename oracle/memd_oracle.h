@@ -45,6 +45,21 @@ extern "C" {
 #define ORC_EPS_VERTICES 2 /* values[V] = eps per vertex, link = endpoint mean */
 #define ORC_EPS_TANH 3     /* eps = p0 + p1 tanh((|s - p2| - p3) / p4), s along axis */
 #define ORC_EPS_SIN 4      /* eps = p0 + p1 sin(2 pi s / L_axis + p2) */
+/* Profiles with an explicit interface (Sec. II, Eq. dielectric-interpolation):
+ * a link whose two end values differ crosses the interface and takes the
+ * harmonic average weighted by the distances of its ends to the interface.
+ * A vertex exactly on the interface of PLANES or SPHERE takes the mean of the
+ * two media. */
+#define ORC_EPS_PLANES 5   /* p1 between the planes s = p2 and s = p3 along
+                              axis, p0 elsewhere; 0 <= p2 <= p3 < L_axis */
+#define ORC_EPS_SPHERE 6   /* p1 inside the periodic ball of centre (p2, p3, p4)
+                              and radius p5, p0 outside; p5 + a < L_d / 2 */
+#define ORC_EPS_CUT 7      /* values[V] = eps per vertex, values[V + l] = where a
+                              surface cuts link l, as a fraction of a from its
+                              lower end (in [0, 1]; anything else: no cut) */
+/* ORC_EPS_VERTICES reads params[0] = theta >= 0: a link with
+ * |eps2 - eps1| > theta min(eps1, eps2) is an interface link with the
+ * interface at its midpoint; theta = 0 marks none. */
 
 /* self-energy corrections */
 #define ORC_SELF_NONE 0
@@ -95,6 +110,11 @@ int32_t orc_move(orc_sys *s, const double *x_new, const int32_t *img_new);
 void orc_gather(orc_sys *s);
 void orc_energy(orc_sys *s, double *out);
 int32_t orc_relax(orc_sys *s, double tol, int32_t maxit, int32_t *iters);
+/* replace the permittivity of a live system: map the profile onto the links,
+ * recompute eps_eff; D keeps its value (Gauss' law does not involve eps)
+ * unless relax != 0, which rebuilds the electrostatic minimum from the ledger
+ * as orc_init_field does (B = 0).  Forces are gathered again. */
+int32_t orc_set_eps(orc_sys *s, const orc_eps *eps, int32_t relax);
 
 /* building blocks exposed for the tests */
 void orc_cic_charges(const orc_sys *s, int64_t *Q);

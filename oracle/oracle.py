@@ -24,6 +24,7 @@ _lib = None
 S = 1 << 16
 
 EPS_CONST, EPS_LINKS, EPS_VERTICES, EPS_TANH, EPS_SIN = 0, 1, 2, 3, 4
+EPS_PLANES, EPS_SPHERE, EPS_CUT = 5, 6, 7
 SELF_NONE, SELF_GF, SELF_DIRECT = 0, 1, 2
 OK, ERR_INVALID, ERR_COURANT, ERR_OOM, ERR_CELL_JUMP = 0, 1, 2, 3, 5
 ERR_RELAX_NOCONV, ERR_OVERFLOW = 7, 11
@@ -88,6 +89,8 @@ def lib():
         L.orc_energy.argtypes = [C.c_void_p, f64p]
         L.orc_relax.restype = C.c_int32
         L.orc_relax.argtypes = [C.c_void_p, C.c_double, C.c_int32, i32p]
+        L.orc_set_eps.restype = C.c_int32
+        L.orc_set_eps.argtypes = [C.c_void_p, C.POINTER(_Eps), C.c_int32]
         L.orc_cic_charges.argtypes = [C.c_void_p, i64p]
         L.orc_gauss_scan.restype = C.c_int32
         L.orc_gauss_scan.argtypes = [i32p, i64p, i64p]
@@ -276,6 +279,13 @@ class OracleSystem:
         it = C.c_int32(0)
         st = self._lib.orc_relax(self._h, tol, maxit, C.byref(it))
         return st, it.value
+
+    def set_eps(self, eps, relax=False):
+        e, keep = eps_struct(**eps)
+        st = self._lib.orc_set_eps(self._h, C.byref(e), 1 if relax else 0)
+        del keep
+        if st != OK:
+            raise OracleError(f"orc_set_eps failed with status {st}")
 
     def energy(self):
         out = np.zeros(len(ENERGY_KEYS))

@@ -95,6 +95,58 @@ def layer_eps(kind, params, Nz, a):
     return e_par, e_par.copy(), e_z
 
 
+def planes_layer_eps(e_out, e_in, lo, hi, Nz, a):
+    """Link eps per plane k for a slab of e_in between the planes z = lo and
+    z = hi (0 <= lo <= hi < Nz a) in e_out.  Tangential links lie in plane k:
+    the medium there, or the mean of both media on a face.  A z-link from
+    plane k to k + 1 takes the mean of 1/eps along its length (the two media
+    in series), from the overlap of the link with the slab."""
+    k = np.arange(Nz, dtype=np.float64)
+    z = k * a
+    if lo == hi:
+        e_par = np.full(Nz, e_out)
+    else:
+        e_par = np.where((z > lo) & (z < hi), e_in, e_out)
+        e_par = np.where((z == lo) | (z == hi), 0.5 * (e_in + e_out), e_par)
+    inside = np.clip(np.minimum(z + a, hi) - np.maximum(z, lo), 0.0, a)
+    inv = (inside / e_in + (a - inside) / e_out) / a
+    return e_par, e_par.copy(), 1.0 / inv
+
+
+def chord_fraction_sums(ie, e_out, e_in, centre, r, N):
+    """Per lattice line along each axis: the summed fraction of its links
+    inside a ball, read back from 1/eps (a link's 1/eps is the mix of the
+    two media by the fraction of its length in each), and the chord length
+    the ball cuts from that line (zero when no vertex lies strictly inside
+    the chord).  Lengths in cells; centre and r in cells."""
+    f = (ie - 1.0 / e_out) / (1.0 / e_in - 1.0 / e_out)
+    got, want = [], []
+    Nx, Ny, Nz = N
+    for d in range(3):
+        others = [e for e in range(3) if e != d]
+        n = N[d]
+        for i in range(N[others[0]]):
+            for j in range(N[others[1]]):
+                idx = [slice(None)] * 3
+                # arrays are [z, y, x]; axis e sits at position 2 - e
+                idx[2 - others[0]] = i
+                idx[2 - others[1]] = j
+                line = f[d][tuple(idx)]
+                o0 = i - centre[others[0]]
+                o0 -= N[others[0]] * round(o0 / N[others[0]])
+                o1 = j - centre[others[1]]
+                o1 -= N[others[1]] * round(o1 / N[others[1]])
+                rho2 = o0 * o0 + o1 * o1
+                chord = 0.0
+                if rho2 < r * r:
+                    h = math.sqrt(r * r - rho2)
+                    ks = [k for k in range(-n, 2 * n) if abs(k - centre[d]) < h]
+                    chord = 2 * h if ks else 0.0
+                got.append(float(line.sum()))
+                want.append(chord)
+    return np.array(got), np.array(want)
+
+
 def layered_solution(N, a, Qe, ex, ey, ez, Dbar):
     """Exact curl-free lattice field with div D = Qe / a^2 (flux form) and mean
     D = Dbar, for eps varying only with the plane index k.  Returns D shaped

@@ -516,3 +516,241 @@ def test_fold_keeps_unfolded_position():
     assert np.allclose(x + img * L, xs, rtol=0, atol=1e-14)
     assert x[0, 1] == 0.0 and img[0, 1] == 0      # -1e-17 + 4 rounds to 4 -> 0, same image
     assert x[0, 0] == 0.0 and img[0, 0] == 1
+
+
+# ------------------------------------------------------------ interface links
+# Eq. (dielectric-interpolation) read as the harmonic average its text names:
+# an interface link is the two media in series, 1/eps_link = (d1/eps1 +
+# d2/eps2)/a.  The pins below use geometry and continuum closed forms only.
+@pytest.mark.parametrize("lo,hi,a", [(2.3, 5.85, 1.0), (0.0, 2.6, 1.0), (2.0, 6.0, 1.0),
+                                     (1.15, 2.925, 0.5), (0.0, 0.0, 1.0)])
+def test_planar_slab_links_match_the_series_integral(lo, hi, a):
+    # z-links: the mean of 1/eps over their length (exact for any plane
+    # position); tangential links: the medium of their plane, both media
+    # averaged on a face.  A swapped d1/d2 or an arithmetic mean fails.
+    e_out, e_in, N = 2.0, 80.0, (8, 6, 8)
+    s = make(N, a, eps=dict(kind=O.EPS_PLANES, axis=2, params=(e_out, e_in, lo, hi)))
+    ex, ey, ez = refs.planes_layer_eps(e_out, e_in, lo, hi, N[2], a)
+    ie = s.field("ie")
+    assert np.allclose(1 / ie[0], ex[:, None, None], rtol=1e-14)
+    assert np.allclose(1 / ie[1], ey[:, None, None], rtol=1e-14)
+    assert np.allclose(1 / ie[2], ez[:, None, None], rtol=1e-14)
+    # homogenised tensor: the continuum series value across the layers
+    L = N[2] * a
+    w = hi - lo
+    assert abs(s.Minv[2, 2] - (w / e_in + (L - w) / e_out) / L) < 1e-12 * s.Minv[2, 2]
+    assert abs(s.Minv[0, 0] - 1 / np.mean(ex)) < 1e-12 * s.Minv[0, 0]
+
+
+def test_planar_slab_along_x_is_the_transpose_of_z():
+    sx = make((8, 6, 4), 1.0, eps=dict(kind=O.EPS_PLANES, axis=0, params=(3.0, 50.0, 1.7, 4.2)))
+    sz = make((4, 6, 8), 1.0, eps=dict(kind=O.EPS_PLANES, axis=2, params=(3.0, 50.0, 1.7, 4.2)))
+    ix, iz = sx.field("ie"), sz.field("ie")
+    assert np.array_equal(ix[0], np.transpose(iz[2], (2, 1, 0)))
+    assert np.array_equal(ix[2], np.transpose(iz[0], (2, 1, 0)))
+
+
+def test_planar_slab_initial_solution_matches_layered_exact():
+    rng = np.random.default_rng(14)
+    N, a, params = (8, 6, 8), 1.0, (2.0, 80.0, 2.3, 5.85)
+    s = make(N, a, eps=dict(kind=O.EPS_PLANES, axis=2, params=params))
+    x, q = neutral_system(rng, 10, N, a)
+    s.set_particles(x, q)
+    s.init_field()
+    ex, ey, ez = refs.planes_layer_eps(*params, N[2], a)
+    Qe = refs.cic(x, q, N, a).astype(np.float64) * 2.0 ** -48
+    P = refs.dipole_fixed(x, np.zeros((10, 3)), q, N, a)
+    want = refs.layered_solution(N, a, Qe, ex, ey, ez, -P / s.Vbox)
+    assert np.max(np.abs(s.field("D") - want)) < 1e-9 * np.max(np.abs(want))
+
+
+def test_slab_thinner_than_a_link_is_not_seen():
+    # the interface rule compares end values: a slab between two vertices
+    # changes no vertex, so no link is an interface link
+    s = make((8, 8, 8), 1.0, eps=dict(kind=O.EPS_PLANES, axis=2, params=(2.0, 80.0, 0.7, 0.9)))
+    assert np.all(s.field("ie") == 0.5)
+
+
+@pytest.mark.parametrize("centre,r", [((7.3, 8.1, 7.6), 4.2), ((8.0, 8.0, 8.0), 5.0),
+                                      ((1.5, 14.2, 0.4), 3.3)])
+def test_ball_link_fractions_sum_to_chord_lengths(centre, r):
+    # along every lattice line the fractions of its links inside the ball add
+    # up to the chord the ball cuts from the line (Pythagoras); the integer
+    # centre and radius 5 put vertices exactly on the surface (3-4-5 triples)
+    N, e_out, e_in = (16, 16, 16), 2.0, 80.0
+    s = make(N, 1.0, eps=dict(kind=O.EPS_SPHERE, params=(e_out, e_in) + tuple(centre) + (r,)),
+             eps_eff_inv=np.eye(3))
+    got, want = refs.chord_fraction_sums(s.field("ie"), e_out, e_in, centre, r, N)
+    assert np.max(np.abs(got - want)) < 1e-12
+    assert np.count_nonzero(want) > 100
+
+
+def test_ball_with_spacing_scales_with_the_cell():
+    # the same ball in a box of half the spacing gives the same link values
+    p1 = (2.0, 80.0, 7.3, 8.1, 7.6, 4.2)
+    p2 = (2.0, 80.0, 3.65, 4.05, 3.8, 2.1)
+    s1 = make((16, 16, 16), 1.0, eps=dict(kind=O.EPS_SPHERE, params=p1), eps_eff_inv=np.eye(3))
+    s2 = make((16, 16, 16), 0.5, eps=dict(kind=O.EPS_SPHERE, params=p2), eps_eff_inv=np.eye(3))
+    assert np.max(np.abs(s1.field("ie") - s2.field("ie"))) < 1e-14
+
+
+@pytest.mark.parametrize("r", [3.3, 4.2])
+def test_ball_lattice_eps_eff_matches_maxwell_garnett(r):
+    # a cubic array of dielectric balls at volume fraction f: Maxwell Garnett
+    # eps_eff = eps_o (1 + 2 f b) / (1 - f b), b = (eps_i - eps_o)/(eps_i +
+    # 2 eps_o) (exact to O(f^(10/3)) for the array).  With interface links the
+    # excess over eps_o is within 5% at r = 3-4 cells; the plain mean of the
+    # same vertex values is 30% or more off, so the pin tells them apart.
+    Nn, e_out, e_in, c = 16, 2.0, 80.0, (7.3, 8.1, 7.6)
+    s = make((Nn,) * 3, 1.0, eps=dict(kind=O.EPS_SPHERE, params=(e_out, e_in) + c + (r,)),
+             relax_tol=1e-10)
+    f = 4.0 / 3.0 * math.pi * r ** 3 / Nn ** 3
+    b = (e_in - e_out) / (e_in + 2 * e_out)
+    mg = e_out * (1 + 2 * f * b) / (1 - f * b) - e_out
+    got = 1.0 / np.mean(np.diag(s.Minv)) - e_out
+    assert abs(got / mg - 1.0) < 0.05
+    assert np.max(np.abs(s.Minv - np.diag(np.diag(s.Minv)))) < 1e-3 * s.Minv[0, 0]
+    k, j, i = np.meshgrid(*(np.arange(Nn),) * 3, indexing="ij")
+    off = [np.mod(v - cc + Nn / 2, Nn) - Nn / 2 for v, cc in ((i, c[0]), (j, c[1]), (k, c[2]))]
+    vals = np.where(off[0] ** 2 + off[1] ** 2 + off[2] ** 2 < r * r, e_in, e_out)
+    m = make((Nn,) * 3, 1.0, eps=dict(kind=O.EPS_VERTICES, values=vals, params=(0.0,)),
+             relax_tol=1e-10)
+    assert abs((1.0 / np.mean(np.diag(m.Minv)) - e_out) / mg - 1.0) > 0.3
+
+
+def cut_planes(e_out, e_in, lo, hi, N, a):
+    """CUT profile of a planar slab written by hand: vertex values by plane,
+    and on z-links crossing a face the distance of the face from the lower
+    end as a fraction of a."""
+    Nx, Ny, Nz = N
+    z = np.arange(Nz) * a
+    side = np.where((z > lo) & (z < hi), e_in, e_out)
+    side = np.where((z == lo) | (z == hi), 0.5 * (e_in + e_out), side)
+    vals = np.broadcast_to(side[:, None, None], (Nz, Ny, Nx)).astype(np.float64)
+    t = -np.ones((3, Nz, Ny, Nx))
+    for k in range(Nz):
+        for face in (lo, hi):
+            if z[k] < face < z[k] + a:
+                t[2, k] = (face - z[k]) / a
+    return np.concatenate([vals.ravel(), t.ravel()])
+
+
+def test_cut_links_reproduce_the_series_integral():
+    N, a, e_out, e_in, lo, hi = (6, 5, 8), 1.0, 2.0, 80.0, 2.3, 5.85
+    s = make(N, a, eps=dict(kind=O.EPS_CUT, values=cut_planes(e_out, e_in, lo, hi, N, a)))
+    ex, ey, ez = refs.planes_layer_eps(e_out, e_in, lo, hi, N[2], a)
+    ie = s.field("ie")
+    assert np.allclose(1 / ie[0], ex[:, None, None], rtol=1e-14)
+    assert np.allclose(1 / ie[2], ez[:, None, None], rtol=1e-14)
+    # no cut anywhere: the plain endpoint mean of the vertex values
+    rng = np.random.default_rng(5)
+    vals = rng.uniform(1.0, 40.0, size=N[::-1])
+    c = make(N, a, eps=dict(kind=O.EPS_CUT, values=np.concatenate([vals.ravel(),
+                                                                    -np.ones(3 * vals.size)])))
+    v = make(N, a, eps=dict(kind=O.EPS_VERTICES, values=vals, params=(0.0,)))
+    assert np.array_equal(c.field("ie"), v.field("ie"))
+
+
+def test_vertex_threshold_marks_interface_links_at_midpoints():
+    # layers whose jumps sit halfway between vertex planes: with theta = 1
+    # every jump link is an interface link cut at its midpoint, which is the
+    # continuum series value exactly; theta = 0 (the plain mean) is not
+    N, a = (4, 4, 8), 1.0
+    eps_k = np.array([2.0, 2.0, 80.0, 80.0, 80.0, 2.0, 2.0, 2.0])
+    vals = np.broadcast_to(eps_k[:, None, None], N[::-1]).astype(np.float64)
+    lo, hi = 1.5, 4.5
+    _, _, ez = refs.planes_layer_eps(2.0, 80.0, lo, hi, N[2], a)
+    on = make(N, a, eps=dict(kind=O.EPS_VERTICES, values=vals, params=(1.0,)))
+    assert np.allclose(1 / on.field("ie")[2], ez[:, None, None], rtol=1e-14)
+    off = make(N, a, eps=dict(kind=O.EPS_VERTICES, values=vals, params=(0.0,)))
+    big = make(N, a, eps=dict(kind=O.EPS_VERTICES, values=vals, params=(100.0,)))
+    assert np.array_equal(off.field("ie"), big.field("ie"))
+    assert abs(1 / off.field("ie")[2, 1, 0, 0] - 41.0) < 1e-12
+
+
+def test_invalid_interface_profiles_are_rejected():
+    for eps in (dict(kind=O.EPS_PLANES, axis=2, params=(2.0, 80.0, 5.0, 3.0)),
+                dict(kind=O.EPS_PLANES, axis=2, params=(2.0, 80.0, 1.0, 8.0)),
+                dict(kind=O.EPS_PLANES, axis=3, params=(2.0, 80.0, 1.0, 3.0)),
+                dict(kind=O.EPS_PLANES, axis=2, params=(0.0, 80.0, 1.0, 3.0)),
+                dict(kind=O.EPS_SPHERE, params=(2.0, 80.0, 4.0, 4.0, 4.0, 3.5)),
+                dict(kind=O.EPS_SPHERE, params=(2.0, 80.0, 4.0, 4.0, 4.0, 0.0)),
+                dict(kind=O.EPS_VERTICES, values=np.ones(512), params=(-1.0,)),
+                dict(kind=O.EPS_CUT, params=())):
+        with pytest.raises(O.OracleError):
+            make((8, 8, 8), 1.0, eps=eps)
+
+
+@pytest.mark.parametrize("ein,eout,c", [(10.0, 15.0, 16.3), (15.0, 10.0, 16.3),
+                                        (10.0, 15.0, 15.7)])
+def test_sharp_planar_faces_give_the_image_charge_force(ein, eout, c):
+    # faces off the lattice planes, the charge 4 cells below the upper face:
+    # first-reflection image force within 10% (the weak contrast keeps the
+    # higher reflections near 4%)
+    N, W, d = 32, 16.0, 4.0
+    z = c + W / 2 - d
+    x = np.array([[N / 4 + 0.5, N / 2 + 0.5, z], [3 * N / 4 + 0.5, N / 2 + 0.5, z]])
+    o = O.OracleSystem((N,) * 3, (float(N),) * 3,
+                       eps=dict(kind=O.EPS_PLANES, axis=2, params=(eout, ein, c - W / 2, c + W / 2)),
+                       c_light=1.0, dt=0.01, seed=1, relax_tol=1e-9)
+    o.set_particles(x, np.array([1, -1], dtype=np.int32), np.ones(2), np.zeros((2, 3)))
+    o.init_field()
+    F = o.particles("F")
+    want = image_force_z(ein, eout, d, W, N)
+    assert abs(F[0, 2] / want - 1.0) < 0.10 and abs(F[1, 2] / want - 1.0) < 0.10
+
+
+# ---------------------------------------------------- moving the permittivity
+def test_set_eps_keeps_D_and_maps_like_a_fresh_system():
+    rng = np.random.default_rng(31)
+    N, a = (8, 6, 8), 1.0
+    first = dict(kind=O.EPS_TANH, axis=2, params=(41.0, 39.0, 4.0, 2.0, 1.5))
+    then = dict(kind=O.EPS_SPHERE, params=(2.0, 80.0, 4.1, 2.9, 3.6, 1.8))
+    s = make(N, a, eps=first, relax_tol=1e-11)
+    x, q = neutral_system(rng, 10, N, a)
+    s.set_particles(x, q)
+    s.init_field()
+    s.step(5)
+    D0, B0 = s.field("D").copy(), s.field("B").copy()
+    s.set_eps(then)
+    fresh = make(N, a, eps=then, relax_tol=1e-11)
+    assert np.array_equal(s.field("ie"), fresh.field("ie"))
+    assert np.array_equal(s.Minv, fresh.Minv)
+    assert np.array_equal(s.field("D"), D0) and np.array_equal(s.field("B"), B0)
+    e = s.energy()
+    assert e["gauss_exact"] == 1.0
+    # the electric energy now weighs the same D with the new 1/eps
+    assert abs(e["electric"] - 0.5 * a ** 3 * np.sum(D0 ** 2 * fresh.field("ie"))) < \
+        1e-12 * e["electric"]
+
+
+def test_set_eps_with_relaxation_is_the_fresh_electrostatic_minimum():
+    # after a few steps, re-relaxing under a new profile reaches the unique
+    # minimum for the present charges and dipole: the same field as a fresh
+    # system initialised at the present positions
+    rng = np.random.default_rng(32)
+    N, a = (8, 6, 8), 1.0
+    then = dict(kind=O.EPS_PLANES, axis=1, params=(3.0, 30.0, 1.4, 3.9))
+    s = make(N, a, eps=dict(kind=O.EPS_CONST, params=(2.0,)), relax_tol=1e-11)
+    x, q = neutral_system(rng, 10, N, a)
+    s.set_particles(x, q, v=rng.normal(size=(10, 3)))
+    s.init_field()
+    s.step(20)
+    s.set_eps(then, relax=True)
+    fresh = make(N, a, eps=then, relax_tol=1e-11)
+    fresh.set_particles(s.particles("x"), q, img=s.particles("img"))
+    fresh.init_field()
+    D, Df = s.field("D"), fresh.field("D")
+    assert np.max(np.abs(D - Df)) < 1e-9 * np.max(np.abs(Df))
+    assert np.all(s.field("B") == 0.0)
+    assert np.max(np.abs(s.particles("F") - fresh.particles("F"))) < \
+        1e-8 * np.max(np.abs(fresh.particles("F")))
+    assert s.step_count == 20
+
+
+def test_set_eps_failure_leaves_the_system_unchanged():
+    s = make((8, 8, 8), 1.0, eps=dict(kind=O.EPS_CONST, params=(3.0,)))
+    ie0, M0 = s.field("ie").copy(), s.Minv
+    with pytest.raises(O.OracleError):
+        s.set_eps(dict(kind=O.EPS_LINKS, values=-np.ones(3 * 512)))
+    assert np.array_equal(s.field("ie"), ie0) and np.array_equal(s.Minv, M0)
