@@ -61,14 +61,33 @@ enum { MEMD_FP64 = 0, MEMD_FP32 = 1 };                 /* link/plaquette fields 
 enum { MEMD_SELF_NONE = 0, MEMD_SELF_GF = 1, MEMD_SELF_DIRECT = 2 };
 
 /* Permittivity profiles (Sec. II, Fig. 2b).  A link takes the mean of its
- * end values; analytic profiles are sampled at the link midpoint. */
+ * end values; analytic profiles are sampled at the link midpoint.
+ *
+ * Interface links (Sec. II, Eq. dielectric-interpolation, read as the
+ * harmonic average the text names): a link whose ends lie in different media
+ * holds them in series, 1/eps_link = (d1/eps1 + d2/eps2) / a, d1 and d2 the
+ * distances of its ends to the interface.  A link is an interface link when
+ *   PLANES, SPHERE: its ends are on different sides of the interface (a
+ *     vertex exactly on the interface takes the mean of the two media);
+ *   CUT: the caller gives its cut position;
+ *   VERTICES with params[0] = theta > 0: |eps2 - eps1| > theta min(eps1, eps2),
+ *     the interface then at its midpoint (theta = 0: no interface links).
+ * A slab or ball thinner than a link between two vertices is not seen. */
 enum {
   MEMD_EPS_CONST = 0,     /* params[0] = eps */
   MEMD_EPS_LINKS = 1,     /* values[3 V]: eps per link, component major */
-  MEMD_EPS_VERTICES = 2,  /* values[V]: eps per vertex */
+  MEMD_EPS_VERTICES = 2,  /* values[V]: eps per vertex; params[0] = theta >= 0 */
   MEMD_EPS_TANH = 3,      /* eps = p0 + p1 tanh((|s - p2| - p3) / p4), s = periodic
                              distance along `axis` */
-  MEMD_EPS_SIN = 4        /* eps = p0 + p1 sin(2 pi s / L_axis + p2) */
+  MEMD_EPS_SIN = 4,       /* eps = p0 + p1 sin(2 pi s / L_axis + p2) */
+  MEMD_EPS_PLANES = 5,    /* p1 between the planes s = p2 and s = p3 normal to `axis`,
+                             p0 elsewhere; 0 <= p2 <= p3 < L_axis */
+  MEMD_EPS_SPHERE = 6,    /* p1 inside the ball of centre (p2, p3, p4) and radius p5
+                             (nearest periodic image), p0 outside; p5 + a < L_d / 2 */
+  MEMD_EPS_CUT = 7        /* values[4 V]: eps per vertex (V), then per link
+                             (3 V, component major) where a surface cuts it, as a
+                             fraction of a from its lower vertex in [0, 1]; any
+                             other value (e.g. -1) marks an uncut link */
 };
 
 typedef struct memd_eps_profile {
@@ -233,6 +252,19 @@ memd_status memd_set_fields(memd_ctx *ctx, const double *D, const double *B,
 /* Recompute the forces from the current state (gather with corrections);
  * the stored kick force becomes the electrostatic force. */
 memd_status memd_compute_forces(memd_ctx *ctx);
+
+/* Replace the permittivity of a context (Sec. II; moving or re-shaped
+ * dielectric backgrounds).  Valid before or after memd_init_field.  The
+ * profile is mapped as at memd_create and the effective tensor recomputed.
+ * Gauss' law constrains D alone, so D and B are kept unless relax_field != 0,
+ * which rebuilds D from the exact charge ledger and relaxes it to the
+ * electrostatic minimum of the new medium (B = 0), as memd_init_field does.
+ * Forces are gathered again; the step counter (noise stream) continues.
+ * Errors: MEMD_ERR_INVALID for a bad profile (nothing changed); a failure in
+ * mapping or in the effective tensor restores the previous permittivity;
+ * MEMD_ERR_RELAX_NOCONV from the relaxation leaves the new permittivity with
+ * the previous D.  Batches holding the context rebuild their tables. */
+memd_status memd_set_eps(memd_ctx *ctx, const memd_eps_profile *eps, int32_t relax_field);
 
 /* Create-time results: 1/eps per link (3V, may be NULL), the lattice Green's
  * table G(dx,dy,dz) at index dx + 2 dy + 4 dz (8, may be NULL) and the inverse

@@ -532,6 +532,145 @@ void memd_destroy(memd_ctx* c) {
   delete c;
 }
 
+// the profile's parameters against the box (Sec. II; the interface kinds
+// need their interface inside the box)
+static bool eps_valid(const memd_eps_profile* e, const double box[3], double a) {
+  const double* p = e->params;
+  const bool axis_ok = e->axis >= 0 && e->axis <= 2;
+  auto pos = [](double x) { return x > 0.0 && std::isfinite(x); };
+  switch (e->kind) {
+    case MEMD_EPS_CONST:
+      return true;
+    case MEMD_EPS_LINKS:
+    case MEMD_EPS_CUT:
+      return e->values != nullptr;
+    case MEMD_EPS_VERTICES:
+      return e->values != nullptr && p[0] >= 0.0 && std::isfinite(p[0]);
+    case MEMD_EPS_TANH:
+    case MEMD_EPS_SIN:
+      return axis_ok;
+    case MEMD_EPS_PLANES:
+      return axis_ok && pos(p[0]) && pos(p[1]) && p[2] >= 0.0 && p[2] <= p[3] &&
+             p[3] < box[e->axis];
+    case MEMD_EPS_SPHERE:
+      if (!pos(p[0]) || !pos(p[1]) || !pos(p[5])) return false;
+      for (int d = 0; d < 3; ++d)
+        if (!std::isfinite(p[2 + d]) || !(p[5] + a < 0.5 * box[d])) return false;
+      return true;
+    default:
+      return false;
+  }
+}
+
+// Permittivity on the links (Sec. II, Fig. 2b, Eq. dielectric-interpolation)
+// and the effective tensor (Sec. V): first through the three cell problems
+// of the scalar potential; if that solver does not converge, by relaxing a
+// charge-free field of mean D = e_d, whose mean E is then column d of
+// eps_eff^-1.  A context that already had a permittivity gets it back, with
+// its potentials and tensor, when any step fails.
+static memd_status setup_eps(memd_ctx* c, const memd_eps_profile* eps) {
+  const cudaStream_t st = c->stream;
+  const int64_t V = c->mesh.V;
+  const size_t n3 = 3 * (size_t)V;
+  const bool had = c->eps_ready;
+  memd_status s = MEMD_OK;
+  double *vals = nullptr, *save = nullptr, *psi = nullptr, *D64 = nullptr;
+  double M[9];
+  bool mapped = false;
+  EpsDesc e{};
+  e.kind = eps->kind;
+  e.axis = eps->axis;
+  for (int t = 0; t < 8; ++t) e.p[t] = eps->params[t];
+  const size_t cnt = eps->kind == MEMD_EPS_LINKS      ? n3
+                     : eps->kind == MEMD_EPS_VERTICES ? (size_t)V
+                     : eps->kind == MEMD_EPS_CUT      ? 4 * (size_t)V
+                                                      : 0;
+  if (cnt) {
+    vals = (double*)dalloc(c, cnt * sizeof(double));
+    if (!vals) {
+      s = fail(c, MEMD_ERR_OOM, "eps values");
+      goto out;
+    }
+    if (cudaMemcpyAsync(vals, eps->values, cnt * sizeof(double), cudaMemcpyHostToDevice, st) !=
+        cudaSuccess) {
+      s = fail(c, MEMD_ERR_CUDA, "eps upload");
+      goto out;
+    }
+  }
+  if (had) {
+    save = (double*)dalloc(c, n3 * sizeof(double));
+    if (!save) {
+      s = fail(c, MEMD_ERR_OOM, "eps save");
+      goto out;
+    }
+    if (cudaMemcpyAsync(save, c->ie64, n3 * sizeof(double), cudaMemcpyDeviceToDevice, st) !=
+        cudaSuccess) {
+      s = fail(c, MEMD_ERR_CUDA, "eps save");
+      goto out;
+    }
+  }
+  launch_eps_links(c->mesh, e, vals, c->ie64, &c->ds->err, st);
+  launch_cast(c->prec, c->ie, c->ie64, (int64_t)n3, st);
+  mapped = true;
+  if (cudaGetLastError() != cudaSuccess) {
+    s = fail(c, MEMD_ERR_CUDA, "eps kernels");
+    goto out;
+  }
+  s = check_err(c);
+  if (s != MEMD_OK) goto out;
+  psi = (double*)dalloc(c, n3 * sizeof(double));
+  if (psi) {
+    double ef[9];
+    const memd_status ms =
+        mg_eps_eff(c, psi, ef, std::min(c->relax_tol, 1e-12), c->relax_maxit);
+    if (ms == MEMD_OK && invert3(ef, M)) goto tensor;
+    dfree(c, psi);
+    psi = nullptr;
+    cudaGetLastError();
+  }
+  D64 = (double*)dalloc(c, n3 * sizeof(double));
+  if (!D64) {
+    s = fail(c, MEMD_ERR_OOM, "relaxation field");
+    goto out;
+  }
+  for (int d = 0; d < 3; ++d) {
+    k_fill_unit<<<nb(n3), 256, 0, st>>>(V, D64, d);
+    s = relax(c, D64, c->relax_tol, c->relax_maxit);
+    if (s != MEMD_OK) goto out;
+    for (int e2 = 0; e2 < 3; ++e2) {
+      launch_dot(D64 + e2 * V, c->ie64 + e2 * V, V, c->red, st);
+      launch_finish(c->red, 0, scal(c) + kS_A + e2, st);
+    }
+    double h[3];
+    if (cudaMemcpyAsync(h, scal(c) + kS_A, 3 * sizeof(double), cudaMemcpyDeviceToHost, st) !=
+            cudaSuccess ||
+        cudaStreamSynchronize(st) != cudaSuccess) {
+      s = fail(c, MEMD_ERR_CUDA, "eps_eff download");
+      goto out;
+    }
+    for (int e2 = 0; e2 < 3; ++e2) M[3 * e2 + d] = h[e2] / (double)V;
+  }
+tensor:
+  for (int t = 0; t < 9; ++t) c->eps_eff_inv[t] = M[t];
+  for (int e2 = 0; e2 < 3; ++e2)
+    for (int d = 0; d < 3; ++d) c->Minv[3 * e2 + d] = 0.5 * (M[3 * e2 + d] + M[3 * d + e2]);
+  dfree(c, c->psi);
+  c->psi = psi;
+  psi = nullptr;
+  c->eps_ready = true;
+out:
+  if (s != MEMD_OK && had && mapped) {
+    cudaMemcpyAsync(c->ie64, save, n3 * sizeof(double), cudaMemcpyDeviceToDevice, st);
+    launch_cast(c->prec, c->ie, c->ie64, (int64_t)n3, st);
+    cudaStreamSynchronize(st);
+  }
+  dfree(c, vals);
+  dfree(c, save);
+  dfree(c, psi);
+  dfree(c, D64);
+  return s;
+}
+
 memd_status memd_create(const int32_t mesh[3], const double box[3], const memd_eps_profile* eps,
                         double c_light, double dt, const memd_options* opt, memd_ctx** out) {
   if (!out) return MEMD_ERR_INVALID;
@@ -555,11 +694,7 @@ memd_status memd_create(const int32_t mesh[3], const double box[3], const memd_e
   if (o.self_mode < 0 || o.self_mode > 2) return MEMD_ERR_INVALID;
   if (o.field_kernel < MEMD_FIELD_AUTO || o.field_kernel > MEMD_FIELD_SITE) return MEMD_ERR_INVALID;
   if (o.step_engine < MEMD_STEP_AUTO || o.step_engine > MEMD_STEP_SINGLE) return MEMD_ERR_INVALID;
-  if (eps->kind < 0 || eps->kind > 4) return MEMD_ERR_INVALID;
-  if ((eps->kind == MEMD_EPS_LINKS || eps->kind == MEMD_EPS_VERTICES) && !eps->values)
-    return MEMD_ERR_INVALID;
-  if ((eps->kind == MEMD_EPS_TANH || eps->kind == MEMD_EPS_SIN) && (eps->axis < 0 || eps->axis > 2))
-    return MEMD_ERR_INVALID;
+  if (!eps_valid(eps, box, a)) return MEMD_ERR_INVALID;
 
   memd_ctx* c = new memd_ctx();
   if (o.device >= 0) {
@@ -623,8 +758,6 @@ memd_status memd_create(const int32_t mesh[3], const double box[3], const memd_e
   c->ds = (DevState*)dalloc(c, sizeof(DevState));
   c->red = (double*)dalloc(c, sizeof(double) * (4 * reduce_blocks() + 32 + green_partials()));
   double* Gdev = nullptr;
-  double* vals = nullptr;
-  double* D64 = nullptr;
   if (!c->Dbuf[0] || !c->Dbuf[1] || !c->Bbuf[0] || !c->Bbuf[1] || !c->ie || !c->ie64 ||
       !c->Lg || !c->Tb || !c->ds || !c->red) {
     s = fail(c, MEMD_ERR_OOM, "field allocation");
@@ -641,26 +774,6 @@ memd_status memd_create(const int32_t mesh[3], const double box[3], const memd_e
     goto done;
   }
   {
-    // eps on the links (Sec. II, Fig. 2b)
-    EpsDesc e{};
-    e.kind = eps->kind;
-    e.axis = eps->axis;
-    for (int t = 0; t < 8; ++t) e.p[t] = eps->params[t];
-    if (eps->kind == MEMD_EPS_LINKS || eps->kind == MEMD_EPS_VERTICES) {
-      const size_t cnt = eps->kind == MEMD_EPS_LINKS ? n3 : (size_t)V;
-      vals = (double*)dalloc(c, cnt * sizeof(double));
-      if (!vals) {
-        s = fail(c, MEMD_ERR_OOM, "eps values");
-        goto done;
-      }
-      if (cudaMemcpyAsync(vals, eps->values, cnt * sizeof(double), cudaMemcpyHostToDevice, st) !=
-          cudaSuccess) {
-        s = fail(c, MEMD_ERR_CUDA, "eps upload");
-        goto done;
-      }
-    }
-    launch_eps_links(c->mesh, e, vals, c->ie64, &c->ds->err, st);
-    launch_cast(c->prec, c->ie, c->ie64, (int64_t)n3, st);
     // lattice Green's table (Sec. III)
     Gdev = c->red + 4 * reduce_blocks() + 32;
     launch_green(c->mesh, Gdev, scal(c) + 16, st);
@@ -673,56 +786,9 @@ memd_status memd_create(const int32_t mesh[3], const double box[3], const memd_e
       s = fail(c, MEMD_ERR_CUDA, "green download");
       goto done;
     }
-    s = check_err(c);
+    s = setup_eps(c, eps);
     if (s != MEMD_OK) goto done;
-    // effective permittivity tensor (Sec. V).  First through the three cell
-    // problems of the scalar potential; if that solver does not converge,
-    // by relaxing a charge-free field of mean D = e_d, whose mean E is then
-    // column d of eps_eff^-1.
-    double M[9];
-    c->psi = (double*)dalloc(c, n3 * sizeof(double));
-    if (c->psi) {
-      double ef[9];
-      const memd_status ms = mg_eps_eff(c, c->psi, ef, std::min(c->relax_tol, 1e-12),
-                                        c->relax_maxit);
-      if (ms == MEMD_OK && invert3(ef, M)) {
-        for (int t = 0; t < 9; ++t) c->eps_eff_inv[t] = M[t];
-        for (int e2 = 0; e2 < 3; ++e2)
-          for (int d = 0; d < 3; ++d)
-            c->Minv[3 * e2 + d] = 0.5 * (M[3 * e2 + d] + M[3 * d + e2]);
-        goto eps_done;
-      }
-      dfree(c, c->psi);
-      c->psi = nullptr;
-      cudaGetLastError();
-    }
-    D64 = (double*)dalloc(c, n3 * sizeof(double));
-    if (!D64) {
-      s = fail(c, MEMD_ERR_OOM, "relaxation field");
-      goto done;
-    }
-    for (int d = 0; d < 3; ++d) {
-      k_fill_unit<<<nb(n3), 256, 0, st>>>(V, D64, d);
-      s = relax(c, D64, c->relax_tol, c->relax_maxit);
-      if (s != MEMD_OK) goto done;
-      for (int e2 = 0; e2 < 3; ++e2) {
-        launch_dot(D64 + e2 * V, c->ie64 + e2 * V, V, c->red, st);
-        launch_finish(c->red, 0, scal(c) + kS_A + e2, st);
-      }
-      double h[3];
-      if (cudaMemcpyAsync(h, scal(c) + kS_A, 3 * sizeof(double), cudaMemcpyDeviceToHost, st) !=
-              cudaSuccess ||
-          cudaStreamSynchronize(st) != cudaSuccess) {
-        s = fail(c, MEMD_ERR_CUDA, "eps_eff download");
-        goto done;
-      }
-      for (int e2 = 0; e2 < 3; ++e2) M[3 * e2 + d] = h[e2] / (double)V;
-    }
-    for (int e2 = 0; e2 < 3; ++e2)
-      for (int d = 0; d < 3; ++d) c->Minv[3 * e2 + d] = 0.5 * (M[3 * e2 + d] + M[3 * d + e2]);
-    for (int t = 0; t < 9; ++t) c->eps_eff_inv[t] = M[t];
   }
-eps_done:
   if (cudaEventCreate(&c->ev0) != cudaSuccess || cudaEventCreate(&c->ev1) != cudaSuccess ||
       cudaEventCreateWithFlags(&c->fork, cudaEventDisableTiming) != cudaSuccess ||
       cudaEventCreateWithFlags(&c->join, cudaEventDisableTiming) != cudaSuccess ||
@@ -734,8 +800,6 @@ eps_done:
   // stepped as one cooperative launch or only in batches never does)
   c->coop_grid = coop_grid(c->prec, c->device);
 done:
-  dfree(c, vals);
-  dfree(c, D64);
   if (s != MEMD_OK) {
     memd_destroy(c);
     return s;
@@ -1259,6 +1323,56 @@ memd_status memd_compute_forces(memd_ctx* c) {
   launch_gather(c->mesh, c->prec, sp, c->P, c->D(), c->ie, c->ie64, c->ds, 0, 1, st);
   CKL();
   return check_err(c);
+}
+
+// A new permittivity on a live context (moving or re-shaped dielectric
+// backgrounds).  Gauss' law constrains D, not E, so the present D stays
+// valid; with relax_field it is rebuilt from the exact ledger and relaxed to
+// the electrostatic minimum of the new medium, as memd_init_field does.
+memd_status memd_set_eps(memd_ctx* c, const memd_eps_profile* eps, int32_t relax_field) {
+  if (!c) return MEMD_ERR_INVALID;
+  if (!eps) return fail(c, MEMD_ERR_INVALID, "no permittivity profile");
+  if (!eps_valid(eps, c->mesh.L, c->mesh.a)) return fail(c, MEMD_ERR_INVALID, "permittivity profile");
+  CK(cudaSetDevice(c->device));
+  const cudaStream_t st = c->stream;
+  if (c->initialised) {
+    const memd_status fe = memd_flush(c);
+    if (fe != MEMD_OK) return fe;
+  }
+  drop_graphs(c);
+  harvest_timing(c);
+  CK(cudaStreamSynchronize(st));
+  memd_status s = setup_eps(c, eps);
+  if (s != MEMD_OK) return s;
+  c->gen += 1;  // batches holding this context rebuild their tables
+  if (!c->initialised) return MEMD_OK;
+  if (relax_field) {
+    const Mesh& m = c->mesh;
+    double* D64 = (double*)dalloc(c, 3 * m.V * sizeof(double));
+    if (!D64) return fail(c, MEMD_ERR_OOM, "relaxation field");
+    const double scale = std::ldexp(1.0, -48) / (m.a * m.a);
+    launch_dipole(m, c->P, c->ds, st);
+    launch_ledger_sums(m, c->Lg, c->ds, st);
+    launch_init_D(m, D64, c->Lg, c->ds, scale, c->Vbox, st);
+    if (c->psi) {
+      int its = 0;
+      const memd_status ms = mg_relax(c, D64, c->psi, c->eps_eff_inv,
+                                      std::min(c->relax_tol, 1e-12), c->relax_maxit, &its);
+      if (ms != MEMD_OK) {
+        cudaGetLastError();
+        launch_init_D(m, D64, c->Lg, c->ds, scale, c->Vbox, st);
+      }
+    }
+    s = relax(c, D64, c->relax_tol, c->relax_maxit);
+    if (s == MEMD_OK) {
+      launch_cast(c->prec, c->D(), D64, 3 * m.V, st);
+      if (cudaMemsetAsync(c->B(), 0, 3 * m.V * esz(c), st) != cudaSuccess)
+        s = fail(c, MEMD_ERR_CUDA, "memset");
+    }
+    dfree(c, D64);
+    if (s != MEMD_OK) return s;
+  }
+  return memd_compute_forces(c);
 }
 
 memd_status memd_get_setup(memd_ctx* c, double* inv_eps, double* G8, double* eps_eff_inv) {

@@ -51,6 +51,7 @@ struct memd_ctx {
   // particles
   Particles P{};
   bool initialised = false;
+  bool eps_ready = false;       // a permittivity is mapped (memd_set_eps restores it on failure)
   // step graphs, one per buffer parity
   cudaGraphExec_t graph[2] = {nullptr, nullptr};
   int step_engine = 0;   // MEMD_STEP_*

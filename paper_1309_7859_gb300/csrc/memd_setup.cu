@@ -31,6 +31,90 @@ __device__ inline void coords(const Mesh& m, int64_t v, int& i, int& j, int& k) 
 // A link takes the mean of its end-vertex values; analytic profiles are
 // sampled at the link midpoint, with the tanh slab using the periodic
 // distance to its centre.
+//
+// Interface links (Sec. II, Eq. dielectric-interpolation): a link whose end
+// values differ across an explicit interface holds the two media in series,
+//   1/eps = t / eps1 + (1 - t) / eps2,
+// t a the distance from its first end to the interface.  The geometry
+// (which side a vertex is on, where a link is cut) is done with explicitly
+// rounded operations so that no contraction moves a decision.
+
+// -1 outside, +1 inside, 0 exactly on the interface (takes the mean)
+__device__ int slab_side(const Mesh& m, const EpsDesc& e, int k) {
+  if (e.p[2] == e.p[3]) return -1;
+  const double lo = e.p[2] / m.a, hi = e.p[3] / m.a, u = (double)k;
+  if (u == lo || u == hi) return 0;
+  return (u > lo && u < hi) ? 1 : -1;
+}
+
+// offset of vertex c from the ball's centre in cells, nearest periodic image
+__device__ double ball_offset(const Mesh& m, const EpsDesc& e, int c, int d) {
+  const double x = __dsub_rn((double)c, e.p[2 + d] / m.a);
+  const double n = (double)m.n[d];
+  return __dsub_rn(x, __dmul_rn(n, round(x / n)));
+}
+
+__device__ int ball_side(const Mesh& m, const EpsDesc& e, const int c[3]) {
+  const double r = e.p[5] / m.a;
+  const double o0 = ball_offset(m, e, c[0], 0), o1 = ball_offset(m, e, c[1], 1),
+               o2 = ball_offset(m, e, c[2], 2);
+  const double r2 = __dadd_rn(__dadd_rn(__dmul_rn(o0, o0), __dmul_rn(o1, o1)), __dmul_rn(o2, o2));
+  const double rr = __dmul_rn(r, r);
+  return r2 < rr ? 1 : (r2 == rr ? 0 : -1);
+}
+
+__device__ double medium(const EpsDesc& e, int side) {
+  return side > 0 ? e.p[1] : (side < 0 ? e.p[0] : 0.5 * (e.p[0] + e.p[1]));
+}
+
+__device__ double clamp_unit(double t) { return t < 0.0 ? 0.0 : (t > 1.0 ? 1.0 : t); }
+
+// 1/eps of link (d, v) for the kinds with values on the vertices or with an
+// explicit interface
+__device__ double interface_kinds(const Mesh& m, const EpsDesc& e, const double* values, int d,
+                                  int64_t v, const int c[3]) {
+  int cn[3] = {c[0], c[1], c[2]};
+  cn[d] = (cn[d] + 1 == m.n[d]) ? 0 : cn[d] + 1;
+  double e1, e2;
+  int s1 = 0, s2 = 0;
+  if (e.kind == 5 || e.kind == 6) {
+    s1 = e.kind == 5 ? slab_side(m, e, c[e.axis]) : ball_side(m, e, c);
+    s2 = e.kind == 5 ? slab_side(m, e, cn[e.axis]) : ball_side(m, e, cn);
+    e1 = medium(e, s1);
+    e2 = medium(e, s2);
+  } else {
+    e1 = values[v];
+    e2 = values[vindex(m, cn[0], cn[1], cn[2])];
+  }
+  double t = -1.0;
+  if (e1 != e2) {
+    if (e.kind == 2) {
+      const double lo = fmin(e1, e2);
+      if (e.p[0] > 0.0 && fabs(e2 - e1) > e.p[0] * lo) t = 0.5;
+    } else if (e.kind == 7) {
+      const double f = values[m.V + d * m.V + v];
+      if (f >= 0.0 && f <= 1.0) t = f;
+    } else if (s1 == 0) {
+      t = 0.0;
+    } else if (s2 == 0) {
+      t = 1.0;
+    } else if (e.kind == 5) {
+      const double face = (s1 < 0 ? e.p[2] : e.p[3]) / m.a;
+      t = clamp_unit(__dsub_rn(face, (double)c[d]));
+    } else {
+      const int d1 = d == 0 ? 1 : 0, d2 = d == 2 ? 1 : 2;
+      const double r = e.p[5] / m.a;
+      const double od = ball_offset(m, e, c[d], d);
+      const double o1 = ball_offset(m, e, c[d1], d1), o2 = ball_offset(m, e, c[d2], d2);
+      const double h2 = __dsub_rn(__dmul_rn(r, r), __dadd_rn(__dmul_rn(o1, o1), __dmul_rn(o2, o2)));
+      const double h = h2 > 0.0 ? sqrt(h2) : 0.0;
+      t = clamp_unit(s1 > 0 ? __dadd_rn(-od, h) : __dsub_rn(-od, h));
+    }
+  }
+  if (t < 0.0) return 1.0 / (0.5 * (e1 + e2));
+  return t / e1 + (1.0 - t) / e2;
+}
+
 __global__ void k_eps_links(Mesh m, EpsDesc e, const double* __restrict__ values,
                             double* __restrict__ ie, unsigned int* err) {
   const int64_t V = m.V;
@@ -48,10 +132,16 @@ __global__ void k_eps_links(Mesh m, EpsDesc e, const double* __restrict__ values
     case 1:
       eps = values[l];
       break;
-    case 2: {
-      int cn[3] = {c[0], c[1], c[2]};
-      cn[d] = (cn[d] + 1 == m.n[d]) ? 0 : cn[d] + 1;
-      eps = 0.5 * (values[v] + values[vindex(m, cn[0], cn[1], cn[2])]);
+    case 2:
+    case 5:
+    case 6:
+    case 7: {
+      const double inv = interface_kinds(m, e, values, d, v, c);
+      eps = 1.0 / inv;
+      if (eps > 0.0 && isfinite(eps) && isfinite(inv)) {
+        ie[l] = inv;
+        return;
+      }
       break;
     }
     case 3:

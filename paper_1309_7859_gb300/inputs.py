@@ -22,8 +22,12 @@ import numpy as np
 @dataclass
 class EpsSpec:
     """Permittivity profile: kind is one of 'const', 'links', 'vertices',
-    'tanh', 'sin'.  tanh: eps = p0 + p1 tanh((|s - p2| - p3) / p4) with s the
-    periodic distance along `axis`; sin: eps = p0 + p1 sin(2 pi s / L + p2)."""
+    'tanh', 'sin', 'planes', 'sphere', 'cut'.  tanh: eps = p0 + p1 tanh((|s -
+    p2| - p3) / p4) with s the periodic distance along `axis`; sin: eps = p0 +
+    p1 sin(2 pi s / L + p2); planes: p1 between s = p2 and s = p3 along `axis`,
+    p0 elsewhere; sphere: p1 within p5 of (p2, p3, p4), p0 outside; cut:
+    vertex values then per-link cut fractions; vertices: params[0] is the
+    interface threshold (0: none)."""
     kind: str = "const"
     axis: int = 0
     params: tuple = (1.0,)

@@ -19,14 +19,16 @@ from . import build as _build
 
 FP64, FP32 = 0, 1
 SELF_NONE, SELF_GF, SELF_DIRECT = 0, 1, 2
-EPS_KINDS = {"const": 0, "links": 1, "vertices": 2, "tanh": 3, "sin": 4}
+EPS_KINDS = {"const": 0, "links": 1, "vertices": 2, "tanh": 3, "sin": 4, "planes": 5,
+             "sphere": 6, "cut": 7}
 STATUS = {0: "OK", 1: "INVALID", 2: "COURANT", 3: "OOM", 4: "CUDA", 5: "CELL_JUMP", 6: "GAUSS",
           7: "RELAX_NOCONV", 8: "DIPOLE_DRIFT", 9: "TIMEOUT", 10: "STATE", 11: "OVERFLOW"}
 
 EXPORTS = ("memd_default_options", "memd_status_string", "memd_last_error", "memd_create",
            "memd_destroy", "memd_init_field", "memd_step", "memd_forces", "memd_forces_device",
            "memd_energy", "memd_get_particles", "memd_set_particles", "memd_move",
-           "memd_get_fields", "memd_set_fields", "memd_compute_forces", "memd_get_setup",
+           "memd_get_fields", "memd_set_fields", "memd_compute_forces", "memd_set_eps",
+           "memd_get_setup",
            "memd_get_kernel_stats", "memd_reset_kernel_stats", "memd_synchronize",
            "memd_batch_create", "memd_batch_step", "memd_batch_synchronize",
            "memd_batch_kernel_stats", "memd_batch_destroy", "memd_server_default_options",
@@ -147,6 +149,7 @@ def lib(build_if_missing=True):
     L.memd_get_fields.argtypes = [vp, f64p, f64p, i64p]
     L.memd_set_fields.argtypes = [vp, f64p, f64p, i64p]
     L.memd_compute_forces.argtypes = [vp]
+    L.memd_set_eps.argtypes = [vp, C.POINTER(EpsProfile), C.c_int32]
     L.memd_get_setup.argtypes = [vp, f64p, f64p, f64p]
     L.memd_get_kernel_stats.argtypes = [vp, C.POINTER(KernelStats)]
     L.memd_reset_kernel_stats.argtypes = [vp]
@@ -396,6 +399,13 @@ class Memd:
 
     def compute_forces(self):
         self._check(self._L.memd_compute_forces(self._h), "memd_compute_forces")
+
+    def set_eps(self, eps, relax=False):
+        """New permittivity profile (an inputs.EpsSpec or dict); D is kept, or
+        relaxed to the new electrostatic minimum with relax=True."""
+        e, keep = make_eps(eps)
+        self._check(self._L.memd_set_eps(self._h, C.byref(e), 1 if relax else 0), "memd_set_eps")
+        del keep
 
     def setup(self):
         Nx, Ny, Nz = self.mesh

@@ -23,7 +23,8 @@ from tests import refs
 pytestmark = pytest.mark.gpu
 
 OKIND = {"const": O.EPS_CONST, "links": O.EPS_LINKS, "vertices": O.EPS_VERTICES,
-         "tanh": O.EPS_TANH, "sin": O.EPS_SIN}
+         "tanh": O.EPS_TANH, "sin": O.EPS_SIN, "planes": O.EPS_PLANES,
+         "sphere": O.EPS_SPHERE, "cut": O.EPS_CUT}
 
 
 def rel(a, b):
