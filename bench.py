@@ -45,6 +45,10 @@ def workload(name, rank=0):
     if name.startswith("bigslab-"):
         N = int(name.split("-")[1])
         return inputs.big_slab(N=N, seed=1005 + 7919 * rank)
+    if name.startswith("colloid-"):
+        return inputs.colloid(N=int(name.split("-")[1]), seed=1006 + 7919 * rank)
+    if name.startswith("cloud-wall-"):
+        return inputs.cloud_wall(N=int(name.split("-")[2]), seed=1007 + 7919 * rank)
     raise SystemExit(f"unknown workload {name}")
 
 
@@ -308,6 +312,8 @@ def run_memd(args, world, rank, local):
     g.close()
     if rank == 0 and out is not None and args.large > 0:
         out["large_mesh"] = large_mesh(args.large, dev, stream, args)
+    if rank == 0 and out is not None and args.validation:
+        out["validation"] = validation_systems(dev, stream, args)
     if rank == 0 and out is not None and args.batch > 0:
         out["batched"] = batched(args.batch, dev, args)
     if rank == 0 and out is not None and args.serve > 0:
@@ -502,6 +508,60 @@ def large_mesh(N, dev, stream, args):
             "gauss_exact": bool(e["gauss_exact"])}
 
 
+def validation_systems(dev, stream, args):
+    """The paper's validation systems as synthetic workloads (our own
+    parameters): the dielectric colloid in salt water and the cloud-wall
+    system.  Each is stepped as the default line is (L2 flushed before every
+    step, CUDA events on the library's stream)."""
+    import torch
+    from paper_1309_7859_gb300.memd import Memd
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    out = {}
+    for name in ("colloid-64", "cloud-wall-32"):
+        sysc = workload(name)
+        g = Memd(sysc.mesh, sysc.box, sysc.eps, c_light=sysc.c_light, dt=sysc.dt,
+                 precision=sysc.precision, seed=sysc.seed, time_kernels=True, stream=stream,
+                 field_kernel=args.field_kernel, step_engine=args.step_engine)
+        g.init_field(sysc.x, sysc.q, sysc.m, sysc.v)
+        th = sysc.thermostat
+        steps = max(10, min(args.steps, 2000))
+        x0 = g.particles()[0]
+        with torch.cuda.stream(stream):
+            g.step(args.warmup, thermostat=th)
+            g.synchronize()
+            g.reset_kernel_stats()
+            evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+                   for _ in range(steps)]
+            for i in range(steps):
+                flush.fill_(float(i))
+                evs[i][0].record(stream)
+                g.step(1, thermostat=th)
+                evs[i][1].record(stream)
+            torch.cuda.synchronize()
+        ms = sum(a.elapsed_time(b) for a, b in evs)
+        ks = g.kernel_stats()
+        per = ks.field_ms / max(1, ks.field_launches)
+        hbm, kind = peaks()
+        ach = ks.field_bytes / (per * 1e-3) / 1e9
+        e = g.energy()
+        x1 = g.particles()[0]
+        nh = sysc.extra["heavy"]
+        drift = float(np.max(np.abs(x1[:nh] - x0[:nh]))) if nh else 0.0
+        g.close()
+        out[name] = {"workload": sysc.name, "steps": steps, "ms_per_step": ms / steps,
+                     "link_updates_per_s": 3 * sysc.sites * steps / (ms * 1e-3),
+                     "particle_steps_per_s": sysc.n * steps / (ms * 1e-3),
+                     "eps": sysc.eps.kind, "engine": "single" if ks.single else "graph",
+                     "roofline": {"bound": "hbm", "kernel": ks.field_kernel, "achieved": ach,
+                                  "peak": hbm, "unit": "GB/s", "frac": ach / hbm,
+                                  "peak_kind": kind, "bytes_per_launch": ks.field_bytes,
+                                  "ms_per_launch": per},
+                     "fixed_charges_max_move": drift,
+                     "dipole": [e["P0"], e["P1"], e["P2"]],
+                     "gauss_exact": bool(e["gauss_exact"])}
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -522,6 +582,8 @@ def main():
     ap.add_argument("--serve-max-steps", type=int, default=5000)
     ap.add_argument("--large", type=int, default=256,
                     help="edge of the extra larger-than-L2 system (0: skip)")
+    ap.add_argument("--validation", type=int, default=1,
+                    help="1: also step the colloid and cloud-wall systems (0: skip)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

@@ -192,3 +192,88 @@ def big_slab(N=256, n=100000, seed=1005, steps=200, precision="fp32"):
     rng = np.random.default_rng(seed)
     eps = random_slab_eps(rng, N)
     return _system(f"bigslab-{N}^3-{n}q", (N, N, N), n, eps, 0.005, precision, steps, seed)
+
+
+def fibonacci_sphere(n, radius, centre):
+    """n nearly uniform points on a sphere (golden-angle spiral)."""
+    k = np.arange(n, dtype=np.float64) + 0.5
+    z = 1.0 - 2.0 * k / n
+    r = np.sqrt(1.0 - z * z)
+    phi = k * math.pi * (3.0 - math.sqrt(5.0))
+    pts = np.stack([r * np.cos(phi), r * np.sin(phi), z], axis=1)
+    return np.asarray(centre, dtype=np.float64) + radius * pts
+
+
+def outside_ball(rng, n, box, centre, radius):
+    """n uniform positions in the box farther than `radius` from `centre`
+    (periodic distance)."""
+    box = np.asarray(box, dtype=np.float64)
+    out = np.empty((0, 3))
+    while out.shape[0] < n:
+        cand = rng.uniform(0.0, 1.0, size=(2 * n + 16, 3)) * box
+        d = cand - centre
+        d -= box * np.round(d / box)
+        out = np.concatenate([out, cand[np.sum(d * d, axis=1) > radius * radius]])
+    return out[:n]
+
+
+def salt_pairs(mM, box_cells, cell_nm):
+    """ion pairs of a 1:1 salt at `mM` millimol per litre in a box of
+    box_cells cells of edge cell_nm nanometres (1 mol/l = 0.6022 per nm^3)."""
+    volume_nm3 = float(np.prod(box_cells)) * cell_nm ** 3
+    return int(round(mM * 1e-3 * 0.602214076 * volume_nm3))
+
+
+def colloid(N=64, seed=1006, precision="fp32", Qc=60, salt_mM=50.0, cell_nm=1.0,
+            eps_in=2.0, eps_out=80.0, heavy=1e12, steps=2000):
+    """Dielectric colloid in salt water (the dynamic-sphere validation system
+    of the paper, with our own parameters, which the text does not give): a
+    ball of eps_in = 2 and radius N/8 at the box centre in water of eps_out =
+    80, with sharp interface links; its charge Qc as Qc unit charges fixed
+    half a cell inside its surface (mass `heavy`: their thermal speed
+    sqrt(kT/m) is 1e-6, so a step moves them by ~5e-9 cells); Qc monovalent
+    counterions and 1:1 salt at 50 mmol/l (a cell
+    edge of 1 nm) placed uniformly at least one cell outside the ball."""
+    rng = np.random.default_rng(seed)
+    box = (float(N),) * 3
+    c = np.array(box) / 2.0
+    R = N / 8.0
+    eps = EpsSpec("sphere", 0, (eps_out, eps_in, c[0], c[1], c[2], R))
+    pairs = salt_pairs(salt_mM, (N, N, N), cell_nm)
+    surf = fibonacci_sphere(Qc, R - 0.5, c)
+    ions = outside_ball(rng, Qc + 2 * pairs, box, c, R + 1.0)
+    x = np.concatenate([surf, ions])
+    q = np.concatenate([np.ones(Qc, np.int32), -np.ones(Qc, np.int32),
+                        neutral_charges(rng, 2 * pairs)])
+    m = np.concatenate([np.full(Qc, heavy), np.ones(Qc + 2 * pairs)])
+    v = np.concatenate([np.zeros((Qc, 3)), thermal_velocities(rng, Qc + 2 * pairs)])
+    return System(name=f"colloid-{N}^3-{x.shape[0]}q", mesh=(N, N, N), box=box, eps=eps,
+                  c_light=1.0, dt=0.005, precision=precision, x=x, q=q, m=m, v=v,
+                  steps=steps, thermostat=(1.0, 1.0), seed=seed,
+                  extra=dict(Qc=Qc, radius=R, salt_pairs=pairs, heavy=Qc))
+
+
+def cloud_wall(N=32, seed=1007, precision="fp32", spacing=2, n_cloud=2000, heavy=1e12,
+               steps=2000):
+    """Cloud-wall (the paper's third error system, our own parameters): two
+    oppositely charged walls normal to z at L/4 and 3L/4, each a square grid
+    of fixed unit charges `spacing` cells apart (mass `heavy`), in a neutral
+    cloud of n_cloud random +-1 charges; eps = 1.  The walls give the box a
+    large dipole moment and a field throughout."""
+    rng = np.random.default_rng(seed)
+    box = (float(N),) * 3
+    g = (np.arange(N // spacing) * spacing + 0.5).astype(np.float64)
+    gx, gy = np.meshgrid(g, g, indexing="ij")
+    w = np.stack([gx.ravel(), gy.ravel()], axis=1)
+    nw = w.shape[0]
+    lo = np.concatenate([w, np.full((nw, 1), N / 4.0 + 0.5)], axis=1)
+    hi = np.concatenate([w, np.full((nw, 1), 3.0 * N / 4.0 + 0.5)], axis=1)
+    x = np.concatenate([lo, hi, uniform_positions(rng, n_cloud, box)])
+    q = np.concatenate([np.ones(nw, np.int32), -np.ones(nw, np.int32),
+                        neutral_charges(rng, n_cloud)])
+    m = np.concatenate([np.full(2 * nw, heavy), np.ones(n_cloud)])
+    v = np.concatenate([np.zeros((2 * nw, 3)), thermal_velocities(rng, n_cloud)])
+    return System(name=f"cloud-wall-{N}^3-{x.shape[0]}q", mesh=(N, N, N), box=box,
+                  eps=EpsSpec("const", 0, (1.0,)), c_light=1.0, dt=0.005, precision=precision,
+                  x=x, q=q, m=m, v=v, steps=steps, thermostat=(1.0, 1.0), seed=seed,
+                  extra=dict(wall_charges=nw, heavy=2 * nw))
