@@ -432,7 +432,7 @@ def batched(count, dev, args):
         g.init_field(s.x, s.q, s.m, s.v)
         members.append(g)
     setup_s = time.perf_counter() - t0
-    b = Batch(members)
+    b = Batch(members, field_kernel=args.batch_kernel)
     th = systems[0].thermostat
     steps = max(20, min(args.steps, 200))
     with torch.cuda.stream(stream):
@@ -582,6 +582,8 @@ def main():
     ap.add_argument("--serve-max-steps", type=int, default=5000)
     ap.add_argument("--large", type=int, default=256,
                     help="edge of the extra larger-than-L2 system (0: skip)")
+    ap.add_argument("--batch-kernel", default="auto", choices=["auto", "site", "rows"],
+                    help="field kernel of the batched replicas (auto: timed choice)")
     ap.add_argument("--validation", type=int, default=1,
                     help="1: also step the colloid and cloud-wall systems (0: skip)")
     args = ap.parse_args()

@@ -136,7 +136,8 @@ typedef struct memd_options {
   int32_t reserved[5];
 } memd_options;
 
-enum { MEMD_FIELD_AUTO = 0, MEMD_FIELD_LDG = 1, MEMD_FIELD_TMA = 2, MEMD_FIELD_SITE = 3 };
+enum { MEMD_FIELD_AUTO = 0, MEMD_FIELD_LDG = 1, MEMD_FIELD_TMA = 2, MEMD_FIELD_SITE = 3,
+       MEMD_FIELD_ROWS = 4 /* batches only: see memd_batch_create_kernel */ };
 enum { MEMD_STEP_AUTO = 0, MEMD_STEP_GRAPH = 1, MEMD_STEP_SINGLE = 2 };
 
 typedef struct memd_thermostat {
@@ -171,6 +172,8 @@ typedef struct memd_kernel_stats {
   int32_t step_single;    /* 1: steps run as one cooperative launch; field_ms, field_bytes
                              and field_launches then time that whole kernel */
   int32_t field_tx;       /* tile width in sites (32, or 16 in batches of narrow meshes) */
+  int32_t field_rows;     /* batches: nt > 0 when the row kernel runs (nt threads a CTA,
+                             persistent grid), 0 for site tiles */
 } memd_kernel_stats;
 
 /* Fill *opt with defaults: FP64, GF self term, dipole correction on,
@@ -285,20 +288,30 @@ memd_status memd_synchronize(memd_ctx *ctx);
  * one CUDA graph of four kernels over all members (deposition beside the
  * field update, then transfer application, then the gather), each kernel
  * covering every member through a per-replica descriptor table.  A member
- * gives the same result in the batch as stepped alone (the batched field
- * kernel is the one-thread-per-site kernel, whose arithmetic all field kernels
- * share).  Members must share the device, the
+ * gives the same result in the batch as stepped alone: the batched field
+ * kernels (site tiles, or whole rows of 16-byte vectors on a persistent grid)
+ * do the arithmetic of every field kernel, term for term.  Members must share
+ * the device, the
  * precision and the CUDA stream; the batch does not own them, and they stay
  * usable one by one (memd_forces, memd_energy, ...) between batch steps.
  * Re-initialising a member is noticed at the next batch step. */
 typedef struct memd_batch memd_batch;
 
-/* Group count >= 1 initialised contexts.  The field tiles of the batched
- * kernel (tile height 4 or 8 rows, 1 or 2 planes loaded ahead, 4 to 32
- * planes per CTA) are chosen here by timing each shape on the members' own
- * buffers, which leaves their state unchanged.  Errors: INVALID (mixed
- * device, precision or stream, or a member not initialised), OOM, CUDA. */
+/* Group count >= 1 initialised contexts.  The field kernel is chosen here by
+ * timing each candidate on the members' own buffers, which leaves their
+ * state unchanged: site tiles (width 16 or 32, height 4, 8 or 16 rows, 1 or
+ * 2 planes loaded ahead, 4 to 32 planes per CTA) and the row kernel (256 or
+ * 512 threads a CTA; it needs every member's x extent to be a multiple of 4
+ * sites for FP32 fields, 2 for FP64).  Errors: INVALID (mixed device,
+ * precision or stream, or a member not initialised), OOM, CUDA. */
 memd_status memd_batch_create(int32_t count, memd_ctx *const *members, memd_batch **out);
+
+/* As memd_batch_create, with the field kernel family fixed: MEMD_FIELD_AUTO
+ * (both, as memd_batch_create), MEMD_FIELD_SITE (site tiles only) or
+ * MEMD_FIELD_ROWS (the row kernel; site tiles when a member does not fit it).
+ * Any other value: INVALID. */
+memd_status memd_batch_create_kernel(int32_t count, memd_ctx *const *members,
+                                     int32_t field_kernel, memd_batch **out);
 
 /* Advance every member by nsteps steps (th NULL: constant energy).
  * Asynchronous like memd_step; errors of members are reported by their own

@@ -32,6 +32,7 @@ SOURCES = {
     "memd_batch.cu": [],
     "memd_server.cu": [],
     "memd_mg.cu": [],
+    "memd_rows.cu": ["--fmad=false"],
 }
 
 

@@ -36,6 +36,11 @@ struct memd_batch {
   double field_bytes = 0.0;
   int f_ty = kBatchTY, f_pf = kBatchPF32, f_z = kBatchZ;  // field tiles (autotuned)
   int f_w = 32;                                          // tile width: 32 or 16 sites
+  int f_rows = 0;         // 0: site tiles; nt > 0: the row kernel, nt threads a CTA
+  int f_kind = MEMD_FIELD_AUTO;  // the kernel family asked for at create
+  RowSeg* d_segs = nullptr;
+  int* d_seg_first = nullptr;
+  int n_rows_ctas = 0;
   cudaGraphExec_t graph[2] = {nullptr, nullptr};
   int g_thermo = -1;
   double g_gamma = 0.0, g_kT = 0.0;
@@ -96,6 +101,106 @@ void free_tables(memd_batch* b) {
   b->blocks.clear();
   b->d_desc = nullptr;
   b->d_field_rep = b->d_part_rep = nullptr;
+  b->d_segs = nullptr;
+  b->d_seg_first = nullptr;
+  b->n_rows_ctas = 0;
+}
+
+// Work of the row kernel: every replica's planes cut into full-width tiles
+// of at most nt / (nx / W) - 2 rows (one halo row on either side), each
+// tile-plane weighted by its cost (below); the weighted list is split
+// into nctas contiguous ranges of equal weight, one per CTA of a persistent
+// grid, each range a list of segments.  False when a replica does not fit
+// (x extent not a multiple of the vector width, rows too wide for nt, or a
+// field buffer not 16-byte aligned).
+// cost model of the row plan (measured on 64 mixed replicas): a tile-plane
+// costs no less than 256 threads' worth of vectors, the latency of one plane
+// in flight that small tiles cannot cover; a segment's prologue costs two
+// planes
+constexpr long long kRowsFloor = 256;
+constexpr long long kRowsPro = 2;
+bool rows_plan(const std::vector<memd_ctx*>& m, int prec, int nt, int nctas,
+               std::vector<RowSeg>& segs, std::vector<int>& first) {
+  const int W = rows_sites_per_thread(prec);
+  struct Tile {
+    int rep, y0, rows, nz;
+    long long w;
+  };
+  std::vector<Tile> tiles;
+  for (size_t r = 0; r < m.size(); ++r) {
+    const memd_ctx* c = m[r];
+    const int nx = c->mesh.n[0], ny = c->mesh.n[1], nz = c->mesh.n[2];
+    if (nx % W != 0) return false;
+    for (int t = 0; t < 2; ++t)
+      if (((uintptr_t)c->Dbuf[t] | (uintptr_t)c->Bbuf[t]) % 16 != 0) return false;
+    if ((uintptr_t)c->ie % 16 != 0) return false;
+    const int TQ = nx / W;
+    const int maxrows = nt / TQ;
+    if (maxrows < 3) return false;
+    const int ntl = (ny + maxrows - 3) / (maxrows - 2);
+    const int Rt = (ny + ntl - 1) / ntl;
+    for (int y0 = 0; y0 < ny; y0 += Rt) {
+      const int rows = std::min(Rt, ny - y0);
+      // a tile-plane costs its bytes (threads x 16-byte vectors) once the
+      // memory pipe is full, but no less than kRowsFloor
+      const long long w = std::max<long long>(TQ * (rows + 2), kRowsFloor);
+      tiles.push_back(Tile{(int)r, y0, rows, nz, w});
+    }
+  }
+  // Greedy cut in order with a capacity per CTA: a segment's first plane
+  // also pays its prologue (the plane below and the wait for the first
+  // planes), `pro` planes' worth.  The capacity is the least for which the
+  // greedy cut needs no more than nctas CTAs (bisection).
+  const long long pro = kRowsPro;
+  auto cut = [&](long long cap, bool build) {
+    int cta = 0;
+    long long load = 0;
+    bool open = false;  // the current CTA holds a segment
+    if (build) {
+      segs.clear();
+      first.assign(nctas + 1, 0);
+    }
+    int last_rep = -1, last_y0 = -1, last_zb = -1;
+    for (const Tile& t : tiles) {
+      for (int k = 0; k < t.nz; ++k) {
+        const bool cont = open && last_rep == t.rep && last_y0 == t.y0 && last_zb == k;
+        long long cost = t.w + (cont ? 0 : pro * t.w);
+        bool fresh = !cont;
+        if (open && load + cost > cap) {  // close this CTA
+          ++cta;
+          if (build && cta <= nctas) first[cta] = (int)segs.size();
+          load = 0;
+          cost = t.w + pro * t.w;
+          fresh = true;
+        }
+        if (build && cta < nctas) {
+          if (fresh)
+            segs.push_back(RowSeg{t.rep, t.y0, t.rows, k, k + 1});
+          else
+            segs.back().zb = k + 1;
+        }
+        open = true;
+        load += cost;
+        last_rep = t.rep;
+        last_y0 = t.y0;
+        last_zb = k + 1;
+      }
+    }
+    if (build)
+      while (cta < nctas) first[++cta] = (int)segs.size();
+    return cta + 1;  // CTAs used
+  };
+  long long lo = 1, hi = 0;
+  for (const Tile& t : tiles) hi += (long long)t.nz * t.w + pro * t.w * (long long)t.nz;
+  while (lo < hi) {
+    const long long mid = lo + (hi - lo) / 2;
+    if (cut(mid, false) <= nctas)
+      hi = mid;
+    else
+      lo = mid + 1;
+  }
+  cut(lo, true);
+  return true;
 }
 
 // (Re)build the descriptor table and the CTA maps from the members' state;
@@ -155,8 +260,37 @@ memd_status build_tables(memd_batch* b) {
                       cudaMemcpyHostToDevice, b->stream));
   BCK(cudaMemcpyAsync(b->d_part_rep, prep.data(), sizeof(int) * b->n_part,
                       cudaMemcpyHostToDevice, b->stream));
+  if (b->f_rows > 0) {
+    int sms = 0;
+    BCK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, b->device));
+    const int occ = rows_occupancy(b->prec, b->f_rows);
+    std::vector<RowSeg> segs;
+    std::vector<int> first;
+    if (occ > 0 && rows_plan(b->m, b->prec, b->f_rows, occ * sms, segs, first)) {
+      b->n_rows_ctas = occ * sms;
+      b->d_segs = (RowSeg*)balloc(b, sizeof(RowSeg) * std::max<size_t>(1, segs.size()));
+      b->d_seg_first = (int*)balloc(b, sizeof(int) * first.size());
+      if (!b->d_segs || !b->d_seg_first) return bfail(b, MEMD_ERR_OOM, "batch row tables");
+      BCK(cudaMemcpyAsync(b->d_segs, segs.data(), sizeof(RowSeg) * segs.size(),
+                          cudaMemcpyHostToDevice, b->stream));
+      BCK(cudaMemcpyAsync(b->d_seg_first, first.data(), sizeof(int) * first.size(),
+                          cudaMemcpyHostToDevice, b->stream));
+    } else {
+      b->f_rows = 0;  // some member does not fit the row kernel: site tiles
+    }
+  }
   BCK(cudaStreamSynchronize(b->stream));
   return MEMD_OK;
+}
+
+// the batch's field update: row kernel or site tiles
+cudaError_t launch_field(memd_batch* b, int par, cudaStream_t st) {
+  if (b->f_rows > 0)
+    return launch_rows_batch(b->prec, b->d_desc, b->d_segs, b->d_seg_first, b->n_rows_ctas,
+                             b->f_rows, par, st);
+  launch_fused_batch(b->prec, b->d_desc, b->d_field_rep, b->n_field, par, b->f_ty, b->f_pf,
+                     b->f_w, st);
+  return cudaGetLastError();
 }
 
 // Reads a scratch buffer larger than L2, leaving L2 full of clean lines of
@@ -201,44 +335,55 @@ memd_status autotune_batch(memd_batch* b) {
   }
   cudaMemsetAsync(flush, 0, flush_bytes, b->stream);
   float best = 1e30f;
-  int bt = b->f_ty, bpf = b->f_pf, bz = b->f_z, bw = b->f_w;
+  int bt = b->f_ty, bpf = b->f_pf, bz = b->f_z, bw = b->f_w, brows = 0;
   memd_status s = MEMD_OK;
-  for (int w = 32; w >= 16 && s == MEMD_OK; w /= 2)
-  for (int a = 0; a < nty && s == MEMD_OK; ++a)
-    for (int pf = 1; pf <= pfs && s == MEMD_OK; ++pf)
-      for (int zi = 0; zi < 4 && s == MEMD_OK; ++zi) {
-        b->f_w = w;
-        b->f_ty = tys[a];
-        b->f_pf = pf;
-        b->f_z = zs[zi];
-        s = build_tables(b);
-        if (s != MEMD_OK) break;
-        launch_fused_batch(b->prec, b->d_desc, b->d_field_rep, b->n_field, 0, b->f_ty, b->f_pf,
-                           b->f_w, b->stream);
-        float t[3];
-        for (int r = 0; r < 3; ++r) {
-          k_read_flush<<<4 * 152, 512, 0, b->stream>>>((const float4*)flush, flush_bytes / 16,
-                                                        (float*)flush);
-          cudaEventRecord(e0, b->stream);
-          launch_fused_batch(b->prec, b->d_desc, b->d_field_rep, b->n_field, 0, b->f_ty, b->f_pf,
-                             b->f_w, b->stream);
-          cudaEventRecord(e1, b->stream);
-          cudaEventSynchronize(e1);
-          cudaEventElapsedTime(&t[r], e0, e1);
-        }
-        if (cudaGetLastError() != cudaSuccess) {
-          s = bfail(b, MEMD_ERR_CUDA, "batch field autotune");
-          break;
-        }
-        const float med = std::max(std::min(t[0], t[1]), std::min(std::max(t[0], t[1]), t[2]));
-        if (med < best) {
-          best = med;
-          bt = b->f_ty;
-          bpf = b->f_pf;
-          bz = b->f_z;
-          bw = b->f_w;
-        }
-      }
+  // one candidate: tables for it, a warm-up launch, then the median of three
+  // launches each after an L2-evicting read
+  auto sample = [&]() {
+    s = build_tables(b);
+    if (s != MEMD_OK) return;
+    launch_field(b, 0, b->stream);
+    float t[3];
+    for (int r = 0; r < 3; ++r) {
+      k_read_flush<<<4 * 152, 512, 0, b->stream>>>((const float4*)flush, flush_bytes / 16,
+                                                    (float*)flush);
+      cudaEventRecord(e0, b->stream);
+      launch_field(b, 0, b->stream);
+      cudaEventRecord(e1, b->stream);
+      cudaEventSynchronize(e1);
+      cudaEventElapsedTime(&t[r], e0, e1);
+    }
+    if (cudaGetLastError() != cudaSuccess) {
+      s = bfail(b, MEMD_ERR_CUDA, "batch field autotune");
+      return;
+    }
+    const float med = std::max(std::min(t[0], t[1]), std::min(std::max(t[0], t[1]), t[2]));
+    if (med < best) {
+      best = med;
+      bt = b->f_ty;
+      bpf = b->f_pf;
+      bz = b->f_z;
+      bw = b->f_w;
+      brows = b->f_rows;
+    }
+  };
+  if (b->f_kind != MEMD_FIELD_ROWS)
+    for (int w = 32; w >= 16 && s == MEMD_OK; w /= 2)
+      for (int a = 0; a < nty && s == MEMD_OK; ++a)
+        for (int pf = 1; pf <= pfs && s == MEMD_OK; ++pf)
+          for (int zi = 0; zi < 4 && s == MEMD_OK; ++zi) {
+            b->f_rows = 0;
+            b->f_w = w;
+            b->f_ty = tys[a];
+            b->f_pf = pf;
+            b->f_z = zs[zi];
+            sample();
+          }
+  if (b->f_kind != MEMD_FIELD_SITE)
+    for (int nt = 256; nt <= 512 && s == MEMD_OK; nt *= 2) {
+      b->f_rows = nt;
+      sample();  // falls back to site tiles (f_rows = 0) when a member does not fit
+    }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   cudaStreamSynchronize(b->stream);
@@ -251,6 +396,7 @@ memd_status autotune_batch(memd_batch* b) {
   b->f_pf = bpf;
   b->f_z = bz;
   b->f_w = bw;
+  b->f_rows = brows;
   return build_tables(b);
 }
 
@@ -264,7 +410,7 @@ memd_status record(memd_batch* b, int par, int thermo, double gamma, double kT, 
     BCK(cudaEventRecord(b->join, b->side));
   }
   if (timed) BCK(cudaEventRecordWithFlags(b->ev0, st, cudaEventRecordExternal));
-  launch_fused_batch(b->prec, b->d_desc, b->d_field_rep, b->n_field, par, b->f_ty, b->f_pf, b->f_w, st);
+  BCK(launch_field(b, par, st));
   if (timed) BCK(cudaEventRecordWithFlags(b->ev1, st, cudaEventRecordExternal));
   if (serial)
     launch_deposit_batch(b->d_desc, b->d_part_rep, b->n_part, thermo, gamma, kT, st);
@@ -292,7 +438,7 @@ void harvest(memd_batch* b) {
 
 // the batch, with its field tiles autotuned (tune) or the defaults
 memd_status memd_batch_create_opt(int32_t count, memd_ctx* const* members, memd_batch** out,
-                                  bool tune) {
+                                  bool tune, int kind) {
   if (!out) return MEMD_ERR_INVALID;
   *out = nullptr;
   if (count < 1 || !members) return MEMD_ERR_INVALID;
@@ -325,6 +471,8 @@ memd_status memd_batch_create_opt(int32_t count, memd_ctx* const* members, memd_
     // members' own queued work comes first
     for (memd_ctx* c : b->m) cudaStreamSynchronize(c->stream);
     b->f_pf = b->prec == MEMD_FP32 ? kBatchPF32 : kBatchPF64;
+    b->f_kind = kind;
+    if (kind == MEMD_FIELD_ROWS) b->f_rows = 256;
     s = tune ? autotune_batch(b) : build_tables(b);
   }
   if (s != MEMD_OK) {
@@ -352,7 +500,15 @@ void memd_batch_destroy(memd_batch* b) {
 }
 
 memd_status memd_batch_create(int32_t count, memd_ctx* const* members, memd_batch** out) {
-  return memd_batch_create_opt(count, members, out, true);
+  return memd_batch_create_opt(count, members, out, true, MEMD_FIELD_AUTO);
+}
+
+memd_status memd_batch_create_kernel(int32_t count, memd_ctx* const* members,
+                                     int32_t field_kernel, memd_batch** out) {
+  if (field_kernel != MEMD_FIELD_AUTO && field_kernel != MEMD_FIELD_SITE &&
+      field_kernel != MEMD_FIELD_ROWS)
+    return MEMD_ERR_INVALID;
+  return memd_batch_create_opt(count, members, out, true, field_kernel);
 }
 
 memd_status memd_batch_step(memd_batch* b, int64_t nsteps, const memd_thermostat* th) {
@@ -430,7 +586,8 @@ memd_status memd_batch_kernel_stats(memd_batch* b, memd_kernel_stats* out) {
   out->field_tma = 0;
   out->field_tx = b->f_w;
   out->field_zchunk = b->f_z;
-  out->field_site = b->f_pf;
+  out->field_site = b->f_rows > 0 ? 0 : b->f_pf;
+  out->field_rows = b->f_rows;
   b->field_ms = 0.0;
   b->field_launches = 0;
   return MEMD_OK;

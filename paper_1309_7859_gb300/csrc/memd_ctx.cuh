@@ -93,7 +93,8 @@ memd_status mg_eps_eff(memd_ctx* c, double* psi, double eps_eff[9], double tol, 
 memd_status mg_relax(memd_ctx* c, double* D64, const double* psi, const double eps_eff_inv[9],
                      double tol, int maxit, int* iters);
 }  // namespace memd
-// memd_batch.cu, for the server: a batch whose field tiles are autotuned
-// (tune) or left at their defaults
+// memd_batch.cu, for the server: a batch whose field kernel is autotuned
+// (tune) or left at its defaults, within the family `kind` (MEMD_FIELD_AUTO,
+// MEMD_FIELD_SITE or MEMD_FIELD_ROWS)
 memd_status memd_batch_create_opt(int32_t count, memd_ctx* const* members, memd_batch** out,
-                                  bool tune);
+                                  bool tune, int kind);

@@ -234,6 +234,17 @@ constexpr int kBatchPF32 = 2;          // its prefetch depth in planes, FP32 fie
 constexpr int kBatchPF64 = 1;          // and FP64 fields (register bound)
 constexpr int kBatchZ = 8;             // and its planes per CTA
 constexpr int kBatchQuadThreads = 128;  // 32 particles per CTA in the batched quad kernels
+// One segment of the row kernel's work (memd_rows.cu): rows y0 .. y0 + rows - 1
+// of replica rep, planes za .. zb - 1.
+struct RowSeg {
+  int rep, y0, rows, za, zb;
+};
+// row kernel: sites a thread (16 bytes of the field type), CTAs an SM, launch
+size_t rows_smem_bytes(int nt, size_t esz);
+int rows_sites_per_thread(int prec);
+int rows_occupancy(int prec, int nt);
+cudaError_t launch_rows_batch(int prec, const RepDesc* desc, const RowSeg* segs,
+                              const int* seg_first, int nctas, int nt, int par, cudaStream_t st);
 // field update of every replica (memd_field.cu)
 void launch_fused_batch(int prec, const RepDesc* desc, const int* cta_rep, int nctas, int par,
                         int ty, int pf, int tw, cudaStream_t st);

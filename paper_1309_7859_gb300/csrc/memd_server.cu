@@ -404,7 +404,8 @@ memd_status memd_server_pump(memd_server* s, int32_t* n_active, int32_t* n_queue
     if (!s->active.empty()) {
       std::vector<memd_ctx*> m;
       for (int64_t id : s->active) m.push_back(s->reqs[id].ctx);
-      memd_status st = memd_batch_create_opt((int32_t)m.size(), m.data(), &s->batch, false);
+      memd_status st = memd_batch_create_opt((int32_t)m.size(), m.data(), &s->batch, false,
+                                              MEMD_FIELD_AUTO);
       if (st != MEMD_OK) return sfail(s, st, "batch rebuild failed");
     }
     s->dirty = false;

@@ -30,7 +30,8 @@ EXPORTS = ("memd_default_options", "memd_status_string", "memd_last_error", "mem
            "memd_get_fields", "memd_set_fields", "memd_compute_forces", "memd_set_eps",
            "memd_get_setup",
            "memd_get_kernel_stats", "memd_reset_kernel_stats", "memd_synchronize",
-           "memd_batch_create", "memd_batch_step", "memd_batch_synchronize",
+           "memd_batch_create", "memd_batch_create_kernel", "memd_batch_step",
+           "memd_batch_synchronize",
            "memd_batch_kernel_stats", "memd_batch_destroy", "memd_server_default_options",
            "memd_server_create", "memd_server_destroy", "memd_server_submit", "memd_server_pump",
            "memd_server_status", "memd_server_result", "memd_server_release",
@@ -110,7 +111,8 @@ class KernelStats(C.Structure):
     _fields_ = [("field_ms", C.c_double), ("field_launches", C.c_int64),
                 ("field_bytes", C.c_double), ("launches_per_step", C.c_int64),
                 ("field_tma", C.c_int32), ("field_ty", C.c_int32), ("field_zchunk", C.c_int32),
-                ("field_site", C.c_int32), ("step_single", C.c_int32), ("field_tx", C.c_int32)]
+                ("field_site", C.c_int32), ("step_single", C.c_int32), ("field_tx", C.c_int32),
+                ("field_rows", C.c_int32)]
 
 
 _lib = None
@@ -155,6 +157,7 @@ def lib(build_if_missing=True):
     L.memd_reset_kernel_stats.argtypes = [vp]
     L.memd_synchronize.argtypes = [vp]
     L.memd_batch_create.argtypes = [C.c_int32, C.POINTER(vp), C.POINTER(vp)]
+    L.memd_batch_create_kernel.argtypes = [C.c_int32, C.POINTER(vp), C.c_int32, C.POINTER(vp)]
     L.memd_batch_step.argtypes = [vp, C.c_int64, C.POINTER(Thermostat)]
     L.memd_batch_synchronize.argtypes = [vp]
     L.memd_batch_kernel_stats.argtypes = [vp, C.POINTER(KernelStats)]
@@ -442,13 +445,16 @@ class Batch:
     all of them.  The members must share one stream (pass the same `stream`
     when creating them) and precision; they stay usable one by one."""
 
-    def __init__(self, members):
+    def __init__(self, members, field_kernel="auto"):
+        """field_kernel: "auto" (timed choice between site tiles and the row
+        kernel), "site" or "rows"."""
         self._L = lib()
         _live["batch"].add(self)
         self.members = list(members)
         arr = (C.c_void_p * len(self.members))(*[m._h.value for m in self.members])
         self._h = C.c_void_p(None)
-        st = self._L.memd_batch_create(len(self.members), arr, C.byref(self._h))
+        kind = {"auto": 0, "site": 3, "rows": 4}[field_kernel]
+        st = self._L.memd_batch_create_kernel(len(self.members), arr, kind, C.byref(self._h))
         if st != 0:
             raise MemdError(st, "memd_batch_create failed")
 
@@ -470,9 +476,10 @@ class Batch:
         st = self._L.memd_batch_kernel_stats(self._h, C.byref(k))
         if st != 0:
             raise MemdError(st, "memd_batch_kernel_stats failed")
-        return StepTiming(k.field_ms, k.field_launches, k.field_bytes, k.launches_per_step,
-                          f"k_fused_site_batch<tx={k.field_tx}, ty={k.field_ty}, zchunk={k.field_zchunk}, "
-                          f"planes_ahead={k.field_site}>")
+        name = (f"k_rows_batch<nt={k.field_rows}>" if k.field_rows else
+                f"k_fused_site_batch<tx={k.field_tx}, ty={k.field_ty}, zchunk={k.field_zchunk}, "
+                f"planes_ahead={k.field_site}>")
+        return StepTiming(k.field_ms, k.field_launches, k.field_bytes, k.launches_per_step, name)
 
     def close(self):
         if self._h:

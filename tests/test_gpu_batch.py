@@ -91,3 +91,46 @@ def test_batch_follows_members_stepped_alone():
         ga.step(6 if i == 1 else 5, thermostat=(1.0, 1.0))
     for gm, ga in zip(members, alone):
         assert_same(state(gm), state(ga))
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_row_kernel_members_match_alone(precision):
+    # the row kernel (whole rows of 16-byte vectors, persistent balanced grid)
+    # does the field arithmetic of the site kernels term for term
+    import torch
+    from paper_1309_7859_gb300.memd import Batch
+    sys_ = [s for s in systems(precision) if s["mesh"][0] % 4 == 0]
+    stream = torch.cuda.Stream()
+    members = [make(s, stream) for s in sys_]
+    alone = [make(s) for s in sys_]
+    batch = Batch(members, field_kernel="rows")
+    batch.step(3)
+    batch.step(5, thermostat=(1.0, 1.0))
+    batch.synchronize()
+    assert batch.kernel_stats().field_kernel.startswith("k_rows_batch")
+    for g in alone:
+        g.step(3)
+        g.step(5, thermostat=(1.0, 1.0))
+    for gm, ga in zip(members, alone):
+        assert_same(state(gm), state(ga))
+        assert gm.energy()["gauss_exact"] == 1.0
+
+
+def test_row_kernel_falls_back_to_site_tiles():
+    # a member whose x extent is not a multiple of 4 sites keeps the batch on
+    # site tiles, with the same results
+    import torch
+    from paper_1309_7859_gb300.memd import Batch
+    sys_ = systems("fp32")[2:5]       # includes the 33-wide mesh
+    assert any(s["mesh"][0] % 4 for s in sys_)
+    stream = torch.cuda.Stream()
+    members = [make(s, stream) for s in sys_]
+    alone = [make(s) for s in sys_]
+    batch = Batch(members, field_kernel="rows")
+    batch.step(4, thermostat=(1.0, 1.0))
+    batch.synchronize()
+    assert batch.kernel_stats().field_kernel.startswith("k_fused_site_batch")
+    for g in alone:
+        g.step(4, thermostat=(1.0, 1.0))
+    for gm, ga in zip(members, alone):
+        assert_same(state(gm), state(ga))
