@@ -118,12 +118,16 @@ typedef struct memd_options {
   void *alloc_user;
   int32_t time_kernels;   /* 1: CUDA events around the field kernels, see
                              memd_get_kernel_stats */
-  int32_t field_kernel;   /* MEMD_FIELD_AUTO: autotuned over the three kernels below;
+  int32_t field_kernel;   /* MEMD_FIELD_AUTO: autotuned over the kernels below;
                              MEMD_FIELD_LDG: plain-load kernel, halo loops per thread;
                              MEMD_FIELD_TMA: TMA-staged kernel (when x rows are
                              16-byte multiples, else the plain-load kernel);
                              MEMD_FIELD_SITE: plain loads, one thread per site of the
-                             tile and its halo.  All three give identical results. */
+                             tile and its halo;
+                             MEMD_FIELD_ROWS: whole rows of 16-byte vectors staged by
+                             asynchronous copies on a persistent grid (x extent a
+                             multiple of 4 sites for FP32, 2 for FP64; else the site
+                             kernel).  All give the same results (TMA to rounding). */
   int32_t step_engine;    /* MEMD_STEP_AUTO: the single launch for small systems (at
                              most 2^17 sites and 16 particles per SM), else the graph;
                              MEMD_STEP_GRAPH: four kernels a step (field update beside
@@ -137,7 +141,7 @@ typedef struct memd_options {
 } memd_options;
 
 enum { MEMD_FIELD_AUTO = 0, MEMD_FIELD_LDG = 1, MEMD_FIELD_TMA = 2, MEMD_FIELD_SITE = 3,
-       MEMD_FIELD_ROWS = 4 /* batches only: see memd_batch_create_kernel */ };
+       MEMD_FIELD_ROWS = 4 };
 enum { MEMD_STEP_AUTO = 0, MEMD_STEP_GRAPH = 1, MEMD_STEP_SINGLE = 2 };
 
 typedef struct memd_thermostat {

@@ -376,8 +376,60 @@ static memd_status relax(memd_ctx* c, double* D64, double tol, int maxit) {
 }
 
 // the fused field update of buffer parity par with the context's kernel choice
+// The row kernel for this context alone: a one-entry descriptor table
+// (buffers by absolute parity) and the work split over a persistent grid.
+// False when the mesh does not fit the kernel (x extent not a multiple of
+// the vector width, buffers not 16-byte aligned) or memory is short.
+static bool rows_setup(memd_ctx* c, int nt) {
+  if (c->rows_nt == nt && c->rows_desc) return true;
+  dfree(c, c->rows_desc);
+  dfree(c, c->rows_segs);
+  dfree(c, c->rows_first);
+  c->rows_desc = nullptr;
+  c->rows_segs = nullptr;
+  c->rows_first = nullptr;
+  c->rows_nt = 0;
+  int sms = 0;
+  if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c->device) != cudaSuccess)
+    return false;
+  const int occ = rows_occupancy(c->prec, nt);
+  std::vector<RowSeg> segs;
+  std::vector<int> first;
+  if (occ <= 0 || !rows_plan(std::vector<memd_ctx*>{c}, c->prec, nt, occ * sms, segs, first))
+    return false;
+  RepDesc d;
+  std::memset(&d, 0, sizeof(d));
+  d.m = c->mesh;
+  d.sp = step_params(c, 0, 0.0, 0.0);
+  for (int k = 0; k < 2; ++k) {
+    d.D[k] = c->Dbuf[k];
+    d.B[k] = c->Bbuf[k];
+  }
+  d.ie = c->ie;
+  c->rows_desc = (RepDesc*)dalloc(c, sizeof(RepDesc));
+  c->rows_segs = (RowSeg*)dalloc(c, sizeof(RowSeg) * std::max<size_t>(1, segs.size()));
+  c->rows_first = (int*)dalloc(c, sizeof(int) * first.size());
+  if (!c->rows_desc || !c->rows_segs || !c->rows_first ||
+      cudaMemcpyAsync(c->rows_desc, &d, sizeof(d), cudaMemcpyHostToDevice, c->stream) !=
+          cudaSuccess ||
+      cudaMemcpyAsync(c->rows_segs, segs.data(), sizeof(RowSeg) * segs.size(),
+                      cudaMemcpyHostToDevice, c->stream) != cudaSuccess ||
+      cudaMemcpyAsync(c->rows_first, first.data(), sizeof(int) * first.size(),
+                      cudaMemcpyHostToDevice, c->stream) != cudaSuccess ||
+      cudaStreamSynchronize(c->stream) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  c->rows_nctas = occ * sms;
+  c->rows_nt = nt;
+  return true;
+}
+
 static void launch_field(memd_ctx* c, int par, double cB, double cD, FusedCfg cfg) {
-  if (cfg.tma)
+  if (cfg.rows)
+    launch_rows_batch(c->prec, c->rows_desc, c->rows_segs, c->rows_first, c->rows_nctas,
+                      cfg.rows, par, c->stream);
+  else if (cfg.tma)
     launch_fused_tma(c->mesh, c->prec, c->tma, par, c->Dbuf[par], c->Bbuf[par], c->ie,
                      c->Dbuf[par ^ 1], c->Bbuf[par ^ 1], cB, cD, cfg, &c->ds->err, c->stream);
   else
@@ -402,7 +454,7 @@ static memd_status autotune_fused(memd_ctx* c) {
   {
     std::lock_guard<std::mutex> g(mu);
     auto it = cache.find(key);
-    if (it != cache.end()) {
+    if (it != cache.end() && (it->second.rows == 0 || rows_setup(c, it->second.rows))) {
       c->fcfg = it->second;
       return MEMD_OK;
     }
@@ -430,9 +482,32 @@ static memd_status autotune_fused(memd_ctx* c) {
   if (c->tma_ok) {
     FusedCfg t[32];
     const int nt = fused_candidates(c->mesh, 1, t, 32);  // the TMA kernel has all three heights
-    for (int i = 0; i < nt && nc < 160; ++i) {
+    for (int i = 0; i < nt && nc < 158; ++i) {
       t[i].tma = 1;
       cand[nc++] = t[i];
+    }
+  }
+  // the row kernel (whole rows of 16-byte vectors), where the mesh fits it;
+  // asked for alone and not fitting, the site kernel's shapes stand in
+  if (fk == MEMD_FIELD_AUTO || fk == MEMD_FIELD_ROWS) {
+    const bool fits = rows_setup(c, 256);
+    for (int nt = 256; nt <= 512 && fits; nt *= 2) {
+      FusedCfg r = fused_default(c->mesh);
+      r.tma = 0;
+      r.site = 0;
+      r.rows = nt;
+      cand[nc++] = r;
+    }
+    if (fk == MEMD_FIELD_ROWS && !fits) {
+      for (int pf = 1; pf <= 2; ++pf) {
+        FusedCfg t[32];
+        const int nt2 = fused_candidates(c->mesh, c->prec, t, 32);
+        for (int i = 0; i < nt2 && nc < 160; ++i) {
+          if (pf > 1 && t[i].zchunk < 4) continue;
+          t[i].site = pf;
+          cand[nc++] = t[i];
+        }
+      }
     }
   }
   cudaEvent_t e0, e1;
@@ -449,6 +524,7 @@ static memd_status autotune_fused(memd_ctx* c) {
     // reads the current parity, writes a copy of it into the other one
     auto run = [&]() { launch_field(c, c->cur, 0.0, 0.0, cand[i]); };
     if (cand[i].tma && !c->tma_ok) continue;
+    if (cand[i].rows && !rows_setup(c, cand[i].rows)) continue;
     run();
     if (cand[i].tma && !tma_checked) {
       // the first TMA launch runs alone: if any of its bounded waits gave up,
@@ -483,6 +559,7 @@ static memd_status autotune_fused(memd_ctx* c) {
     const memd_status e = check_err(c);
     if (e != MEMD_OK) return e;
   }
+  if (pick.rows && !rows_setup(c, pick.rows)) pick = fused_default(c->mesh);
   c->fcfg = pick;
   std::lock_guard<std::mutex> g(mu);
   cache[key] = pick;
@@ -692,7 +769,7 @@ memd_status memd_create(const int32_t mesh[3], const double box[3], const memd_e
   if (!(c_light * dt * std::sqrt(3.0) < a)) return MEMD_ERR_COURANT;
   if (o.precision != MEMD_FP32 && o.precision != MEMD_FP64) return MEMD_ERR_INVALID;
   if (o.self_mode < 0 || o.self_mode > 2) return MEMD_ERR_INVALID;
-  if (o.field_kernel < MEMD_FIELD_AUTO || o.field_kernel > MEMD_FIELD_SITE) return MEMD_ERR_INVALID;
+  if (o.field_kernel < MEMD_FIELD_AUTO || o.field_kernel > MEMD_FIELD_ROWS) return MEMD_ERR_INVALID;
   if (o.step_engine < MEMD_STEP_AUTO || o.step_engine > MEMD_STEP_SINGLE) return MEMD_ERR_INVALID;
   if (!eps_valid(eps, box, a)) return MEMD_ERR_INVALID;
 
@@ -1406,6 +1483,7 @@ memd_status memd_get_kernel_stats(memd_ctx* c, memd_kernel_stats* out) {
   out->field_ty = c->fcfg.ty;
   out->field_zchunk = c->fcfg.zchunk;
   out->field_site = c->fcfg.site;
+  out->field_rows = c->fcfg.rows;
   return MEMD_OK;
 }
 

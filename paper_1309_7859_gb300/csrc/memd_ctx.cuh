@@ -51,7 +51,13 @@ struct memd_ctx {
   // particles
   Particles P{};
   bool initialised = false;
-  bool eps_ready = false;       // a permittivity is mapped (memd_set_eps restores it on failure)
+  bool eps_ready = false;
+  // the row kernel's tables for this context alone (built when tuned)
+  memd::RepDesc* rows_desc = nullptr;
+  memd::RowSeg* rows_segs = nullptr;
+  int* rows_first = nullptr;
+  int rows_nctas = 0;
+  int rows_nt = 0;       // a permittivity is mapped (memd_set_eps restores it on failure)
   // step graphs, one per buffer parity
   cudaGraphExec_t graph[2] = {nullptr, nullptr};
   int step_engine = 0;   // MEMD_STEP_*
@@ -92,6 +98,10 @@ namespace memd {
 memd_status mg_eps_eff(memd_ctx* c, double* psi, double eps_eff[9], double tol, int maxit);
 memd_status mg_relax(memd_ctx* c, double* D64, const double* psi, const double eps_eff_inv[9],
                      double tol, int maxit, int* iters);
+// memd_rows.cu: the row kernel's work split for a set of contexts (false
+// when one of them does not fit the kernel)
+bool rows_plan(const std::vector<memd_ctx*>& m, int prec, int nt, int nctas,
+               std::vector<RowSeg>& segs, std::vector<int>& first);
 }  // namespace memd
 // memd_batch.cu, for the server: a batch whose field kernel is autotuned
 // (tune) or left at its defaults, within the family `kind` (MEMD_FIELD_AUTO,

@@ -71,6 +71,7 @@ struct FusedCfg {
   int tma;   // 1: TMA-staged kernel (memd_tma.cu)
   int site;  // k >= 1: one-thread-per-site kernel (k_fused_site), loads k planes ahead;
              // 0: k_fused_curl
+  int rows;  // nt > 0: the row kernel (memd_rows.cu) with nt threads a CTA
 };
 void launch_fused_curl(const Mesh& m, int prec, const void* Din, const void* Bin, const void* ie,
                        void* Dout, void* Bout, double cB, double cD, FusedCfg cfg,

@@ -21,6 +21,10 @@
 //
 // Arithmetic per site is that of the other field kernels, term for term, so
 // the result is bit identical to them.
+#include <algorithm>
+#include <vector>
+
+#include "memd_ctx.cuh"
 #include "memd_internal.cuh"
 
 namespace memd {
@@ -366,6 +370,96 @@ cudaError_t launch_rows_batch(int prec, const RepDesc* desc, const RowSeg* segs,
   const RowsArgs a{desc, segs, seg_first, par};
   if (prec == 1) return nt == 256 ? rows_launch<float, 256>(a, nctas, st) : rows_launch<float, 512>(a, nctas, st);
   return nt == 256 ? rows_launch<double, 256>(a, nctas, st) : rows_launch<double, 512>(a, nctas, st);
+}
+
+// cost model of the row plan (measured on 64 mixed replicas): a tile-plane
+// costs no less than 256 threads' worth of vectors, the latency of one plane
+// in flight that small tiles cannot cover; a segment's prologue costs two
+// planes
+constexpr long long kRowsFloor = 256;
+constexpr long long kRowsPro = 2;
+bool rows_plan(const std::vector<memd_ctx*>& m, int prec, int nt, int nctas,
+               std::vector<RowSeg>& segs, std::vector<int>& first) {
+  const int W = rows_sites_per_thread(prec);
+  struct Tile {
+    int rep, y0, rows, nz;
+    long long w;
+  };
+  std::vector<Tile> tiles;
+  for (size_t r = 0; r < m.size(); ++r) {
+    const memd_ctx* c = m[r];
+    const int nx = c->mesh.n[0], ny = c->mesh.n[1], nz = c->mesh.n[2];
+    if (nx % W != 0) return false;
+    for (int t = 0; t < 2; ++t)
+      if (((uintptr_t)c->Dbuf[t] | (uintptr_t)c->Bbuf[t]) % 16 != 0) return false;
+    if ((uintptr_t)c->ie % 16 != 0) return false;
+    const int TQ = nx / W;
+    const int maxrows = nt / TQ;
+    if (maxrows < 3) return false;
+    const int ntl = (ny + maxrows - 3) / (maxrows - 2);
+    const int Rt = (ny + ntl - 1) / ntl;
+    for (int y0 = 0; y0 < ny; y0 += Rt) {
+      const int rows = std::min(Rt, ny - y0);
+      // a tile-plane costs its bytes (threads x 16-byte vectors) once the
+      // memory pipe is full, but no less than kRowsFloor
+      const long long w = std::max<long long>(TQ * (rows + 2), kRowsFloor);
+      tiles.push_back(Tile{(int)r, y0, rows, nz, w});
+    }
+  }
+  // Greedy cut in order with a capacity per CTA: a segment's first plane
+  // also pays its prologue (the plane below and the wait for the first
+  // planes), `pro` planes' worth.  The capacity is the least for which the
+  // greedy cut needs no more than nctas CTAs (bisection).
+  const long long pro = kRowsPro;
+  auto cut = [&](long long cap, bool build) {
+    int cta = 0;
+    long long load = 0;
+    bool open = false;  // the current CTA holds a segment
+    if (build) {
+      segs.clear();
+      first.assign(nctas + 1, 0);
+    }
+    int last_rep = -1, last_y0 = -1, last_zb = -1;
+    for (const Tile& t : tiles) {
+      for (int k = 0; k < t.nz; ++k) {
+        const bool cont = open && last_rep == t.rep && last_y0 == t.y0 && last_zb == k;
+        long long cost = t.w + (cont ? 0 : pro * t.w);
+        bool fresh = !cont;
+        if (open && load + cost > cap) {  // close this CTA
+          ++cta;
+          if (build && cta <= nctas) first[cta] = (int)segs.size();
+          load = 0;
+          cost = t.w + pro * t.w;
+          fresh = true;
+        }
+        if (build && cta < nctas) {
+          if (fresh)
+            segs.push_back(RowSeg{t.rep, t.y0, t.rows, k, k + 1});
+          else
+            segs.back().zb = k + 1;
+        }
+        open = true;
+        load += cost;
+        last_rep = t.rep;
+        last_y0 = t.y0;
+        last_zb = k + 1;
+      }
+    }
+    if (build)
+      while (cta < nctas) first[++cta] = (int)segs.size();
+    return cta + 1;  // CTAs used
+  };
+  long long lo = 1, hi = 0;
+  for (const Tile& t : tiles) hi += (long long)t.nz * t.w + pro * t.w * (long long)t.nz;
+  while (lo < hi) {
+    const long long mid = lo + (hi - lo) / 2;
+    if (cut(mid, false) <= nctas)
+      hi = mid;
+    else
+      lo = mid + 1;
+  }
+  cut(lo, true);
+  return true;
 }
 
 }  // namespace memd

@@ -273,7 +273,7 @@ class Memd:
         o.seed = int(seed) & ((1 << 64) - 1)
         o.use_graphs = 1 if use_graphs else 0
         o.time_kernels = 1 if time_kernels else 0
-        o.field_kernel = {"auto": 0, "ldg": 1, "tma": 2, "site": 3}[field_kernel]
+        o.field_kernel = {"auto": 0, "ldg": 1, "tma": 2, "site": 3, "rows": 4}[field_kernel]
         o.step_engine = {"auto": 0, "graph": 1, "single": 2}[step_engine]
         self._alloc = None
         self._stream = stream
@@ -424,6 +424,8 @@ class Memd:
         self._check(self._L.memd_get_kernel_stats(self._h, C.byref(k)), "memd_get_kernel_stats")
         if k.step_single:
             kind = "k_step_coop (whole step, one cooperative launch)"
+        elif k.field_rows:
+            kind = f"k_rows<nt={k.field_rows}>"
         elif k.field_tma:
             kind = f"k_fused_tma<ty={k.field_ty}, zchunk={k.field_zchunk}>"
         elif k.field_site:

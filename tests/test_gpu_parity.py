@@ -43,7 +43,8 @@ def oracle_eps(e):
 
 # (step engine, field kernel) pairs: the graph of four kernels with each
 # field kernel, and the single cooperative launch (its own field tiles)
-ENGINES = [("graph", "ldg"), ("graph", "site"), ("graph", "tma"), ("single", "auto")]
+ENGINES = [("graph", "ldg"), ("graph", "site"), ("graph", "tma"), ("graph", "rows"),
+           ("single", "auto")]
 
 
 def make_pair(sysc, self_mode=1, dipole_corr=1, precision=None, init=True, field_kernel="auto",
@@ -309,11 +310,13 @@ def test_field_kernels_agree_on_a_large_mesh(precision):
     from paper_1309_7859_gb300.memd import Memd
     sysc = small_system((96, 44, 37), 2000, SLAB, precision=precision, dt=0.005)
     out = []
-    for fk in ("ldg", "tma", "site"):
+    for fk in ("ldg", "tma", "site", "rows"):
         g = Memd(sysc.mesh, sysc.box, sysc.eps, c_light=1.0, dt=sysc.dt, precision=precision,
                  seed=3, field_kernel=fk)
         g.init_field(sysc.x, sysc.q, sysc.m, sysc.v)
         g.step(3, thermostat=(1.0, 1.0))
+        if fk == "rows":
+            assert g.kernel_stats().field_kernel.startswith("k_rows")
         D, B, Lg = g.fields()
         out.append((D, B, Lg, g.forces()))
     # FP32: B is the circulation of a nearly curl-free E, so the two kernels'
@@ -324,9 +327,11 @@ def test_field_kernels_agree_on_a_large_mesh(precision):
         for a, b in zip(out[0][:2], other[:2]):
             assert rel(a, b) < tol
         assert rel(out[0][3], other[3]) < tol
-    # the two plain-load kernels share every operation: bit-identical
-    for a, b in zip(out[0], out[2]):
-        assert np.array_equal(a, b)
+    # the plain-load kernels (halo loops, one thread per site, whole rows)
+    # share every operation: bit-identical
+    for other in (out[2], out[3]):
+        for a, b in zip(out[0], other):
+            assert np.array_equal(a, b)
 
 
 @pytest.mark.parametrize("mesh,n,eps,precision", [((8, 8, 8), 16, EpsSpec("const", 0, (1.0,)), "fp64"),
