@@ -246,22 +246,19 @@ def run_memd(args, world, rank, local):
     field_ms_per_launch = ks.field_ms / max(1, ks.field_launches)
     e = g.energy()
 
-    # end to end through the C ABI with pinned host buffers, copies inside
+    # end to end through the C ABI with the library's page-locked I/O block,
+    # copies inside: each step loads positions, images and velocities from
+    # host memory and reads state and forces back
     n = sysc.n
-    hx = torch.empty((n, 3), dtype=torch.float64, pin_memory=True).numpy()
-    hv = torch.empty((n, 3), dtype=torch.float64, pin_memory=True).numpy()
-    hi = torch.empty((n, 3), dtype=torch.int32, pin_memory=True).numpy()
-    hf = torch.empty((n, 3), dtype=torch.float64, pin_memory=True).numpy()
-    g.get_particles_into(hx, hv, hi)
+    io = g.io_buffers()
+    g.step_io(0, thermostat=th, load=False)   # the present state into the buffers
     e2e_steps = max(1, min(args.steps, 1000))
     barrier(world)
     t0 = time.perf_counter()
     for _ in range(e2e_steps):
-        g.set_particles(hx, hv, hi)
-        g.step(1, thermostat=th)
-        g.get_particles_into(hx, hv, hi)
-        g.forces(hf)
+        g.step_io(1, thermostat=th, load=True)
     e2e_s = allmax(time.perf_counter() - t0, world, dev)
+    assert np.all(np.isfinite(io["f"]))
     h2d = n * (24 + 24 + 12)
     d2h = n * (24 + 24 + 12 + 24)
 
@@ -304,7 +301,7 @@ def run_memd(args, world, rank, local):
             "cpu_baseline": cpu,
             "e2e": {"value": world * links * e2e_steps / e2e_s, "unit": "link-updates/s",
                     "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
-                    "api": "memd_set_particles + memd_step(1) + memd_get_particles + memd_forces"},
+                    "api": "memd_step_io: one copy in (positions, images, velocities), one step, one copy out (state and forces), one sync"},
             "clocks": clk.summary(),
             "gpu_launches": int(ks.launches_per_step * args.steps),
             "gauss_exact": bool(e["gauss_exact"]),

@@ -237,6 +237,35 @@ memd_status memd_energy(memd_ctx *ctx, memd_energy_terms *out);
 memd_status memd_get_particles(memd_ctx *ctx, double *pos, double *vel,
                                int32_t *img);
 
+/* One call for a loop driven from the host: an optional state load (as
+ * memd_set_particles: positions with image counters, velocities; any input
+ * NULL is kept), nsteps steps (as memd_step), then copies of positions,
+ * velocities, image counters and electrostatic forces (any output NULL is
+ * skipped), with a single synchronisation at the end.  Host buffers in
+ * page-locked memory make every copy asynchronous.  Errors as memd_step and
+ * memd_set_particles. */
+memd_status memd_step_host(memd_ctx *ctx, const double *pos_in, const double *vel_in,
+                           const int32_t *img_in, int64_t nsteps, const memd_thermostat *th,
+                           double *pos_out, double *vel_out, int32_t *img_out, double *f_out);
+
+/* Library-owned page-locked I/O buffers for memd_step_io, n x 3 each, valid
+ * until the next memd_init_field or memd_destroy. */
+typedef struct memd_io {
+  double *pos;   /* positions (in and out) */
+  double *vel;   /* velocities (in and out) */
+  int32_t *img;  /* image counters (in and out) */
+  double *f;     /* electrostatic forces (out) */
+} memd_io;
+memd_status memd_io_buffers(memd_ctx *ctx, memd_io *io);
+
+/* memd_step_host over the buffers of memd_io_buffers, laid out as one block:
+ * load != 0 takes positions, image counters and velocities from them (as
+ * memd_set_particles), then nsteps steps, then the buffers receive the state
+ * and the forces.  One host-to-device copy, one device-to-host copy, one
+ * synchronisation.  Errors as memd_step_host. */
+memd_status memd_step_io(memd_ctx *ctx, int32_t load, int64_t nsteps,
+                         const memd_thermostat *th);
+
 /* Overwrite positions (folded, with img), velocities and image counters of
  * the n particles without depositing any current (state load).  img NULL
  * keeps the counters, vel NULL keeps the velocities. */

@@ -604,6 +604,8 @@ void memd_destroy(memd_ctx* c) {
   if (c->fork) cudaEventDestroy(c->fork);
   if (c->join) cudaEventDestroy(c->join);
   if (c->side) cudaStreamDestroy(c->side);
+  if (c->err_host) cudaFreeHost(c->err_host);
+  if (c->io_host) cudaFreeHost(c->io_host);
   while (!c->blocks.empty()) dfree(c, c->blocks.back().first);
   if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
   delete c;
@@ -898,6 +900,11 @@ static void free_particles(memd_ctx* c) {
   dfree(c, c->P.sig);
   dfree(c, c->pin);
   c->pin = nullptr;
+  if (c->io_host) cudaFreeHost(c->io_host);
+  dfree(c, c->io_dev);
+  c->io_host = nullptr;
+  c->io_dev = nullptr;
+  c->io_n = -1;
   c->P = Particles{};
   c->sig_ready = false;
 }
@@ -1276,12 +1283,13 @@ memd_status memd_get_particles(memd_ctx* c, double* pos, double* vel, int32_t* i
   return check_err(c);
 }
 
-memd_status memd_set_particles(memd_ctx* c, const double* pos, const double* vel,
-                               const int32_t* img) {
-  if (!c) return MEMD_ERR_INVALID;
-  if (!c->initialised) return fail(c, MEMD_ERR_STATE, "memd_init_field first");
-  CK(cudaSetDevice(c->device));
-  {
+// state load on the stream (no synchronisation): velocities, positions with
+// their image counters folded on the device, or image counters alone.  The
+// transfers a single-launch step left pending concern D and the ledger
+// only, so the load itself does not need them applied.
+static memd_status load_particles(memd_ctx* c, const double* pos, const double* vel,
+                                  const int32_t* img, bool flush) {
+  if (flush) {
     const memd_status fe = memd_flush(c);
     if (fe != MEMD_OK) return fe;
   }
@@ -1299,11 +1307,116 @@ memd_status memd_set_particles(memd_ctx* c, const double* pos, const double* vel
       CK(cudaMemcpyAsync(iin, c->P.img, 3 * n * sizeof(int), cudaMemcpyDeviceToDevice, st));
     launch_fold_init(c->mesh, c->P, pin, iin, &c->ds->err, st);
     CKL();
-    return check_err(c);  // synchronises the stream
   } else if (img) {
     CK(cudaMemcpyAsync(c->P.img, img, 3 * n * sizeof(int), cudaMemcpyHostToDevice, st));
   }
+  return MEMD_OK;
+}
+
+memd_status memd_set_particles(memd_ctx* c, const double* pos, const double* vel,
+                               const int32_t* img) {
+  if (!c) return MEMD_ERR_INVALID;
+  if (!c->initialised) return fail(c, MEMD_ERR_STATE, "memd_init_field first");
+  CK(cudaSetDevice(c->device));
+  const memd_status s = load_particles(c, pos, vel, img, true);
+  if (s != MEMD_OK) return s;
+  return check_err(c);  // synchronises the stream
+}
+
+memd_status memd_step_host(memd_ctx* c, const double* pos_in, const double* vel_in,
+                           const int32_t* img_in, int64_t nsteps, const memd_thermostat* th,
+                           double* pos_out, double* vel_out, int32_t* img_out, double* f_out) {
+  if (!c) return MEMD_ERR_INVALID;
+  if (!c->initialised) return fail(c, MEMD_ERR_STATE, "memd_init_field first");
+  if (nsteps < 0) return fail(c, MEMD_ERR_INVALID, "negative step count");
+  CK(cudaSetDevice(c->device));
+  if (!c->err_host) {
+    if (cudaHostAlloc((void**)&c->err_host, sizeof(unsigned int), cudaHostAllocDefault) !=
+        cudaSuccess) {
+      cudaGetLastError();
+      c->err_host = nullptr;
+      return fail(c, MEMD_ERR_OOM, "pinned error word");
+    }
+  }
+  memd_status s = MEMD_OK;
+  if (pos_in || vel_in || img_in) {
+    s = load_particles(c, pos_in, vel_in, img_in, false);
+    if (s != MEMD_OK) return s;
+  }
+  s = memd_step(c, nsteps, th);
+  if (s != MEMD_OK) return s;
+  const size_t n = (size_t)c->P.n;
+  const cudaStream_t st = c->stream;
+  if (n) {
+    if (pos_out) CK(cudaMemcpyAsync(pos_out, c->P.x, 3 * n * sizeof(double), cudaMemcpyDeviceToHost, st));
+    if (vel_out) CK(cudaMemcpyAsync(vel_out, c->P.v, 3 * n * sizeof(double), cudaMemcpyDeviceToHost, st));
+    if (img_out) CK(cudaMemcpyAsync(img_out, c->P.img, 3 * n * sizeof(int), cudaMemcpyDeviceToHost, st));
+    if (f_out) CK(cudaMemcpyAsync(f_out, c->P.F, 3 * n * sizeof(double), cudaMemcpyDeviceToHost, st));
+  }
+  CK(cudaMemcpyAsync(c->err_host, &c->ds->err, sizeof(unsigned int), cudaMemcpyDeviceToHost, st));
   CK(cudaStreamSynchronize(st));
+  if (*c->err_host) return check_err(c);
+  return MEMD_OK;
+}
+
+// the I/O block for the present particle count (page-locked host copy and
+// its device mirror), allocated on first use and after a particle count change
+static memd_status io_block(memd_ctx* c) {
+  if (c->io_n == c->P.n && c->io_host && c->io_dev) return MEMD_OK;
+  if (c->io_host) cudaFreeHost(c->io_host);
+  dfree(c, c->io_dev);
+  c->io_host = nullptr;
+  c->io_dev = nullptr;
+  c->io_n = -1;
+  const IoLayout L = io_layout(c->P.n);
+  if (cudaHostAlloc((void**)&c->io_host, (size_t)L.bytes, cudaHostAllocDefault) != cudaSuccess) {
+    cudaGetLastError();
+    c->io_host = nullptr;
+    return fail(c, MEMD_ERR_OOM, "page-locked I/O block");
+  }
+  std::memset(c->io_host, 0, (size_t)L.bytes);
+  c->io_dev = dalloc(c, (size_t)L.bytes);
+  if (!c->io_dev) return fail(c, MEMD_ERR_OOM, "device I/O block");
+  c->io_n = c->P.n;
+  return MEMD_OK;
+}
+
+memd_status memd_io_buffers(memd_ctx* c, memd_io* io) {
+  if (!c || !io) return MEMD_ERR_INVALID;
+  if (!c->initialised) return fail(c, MEMD_ERR_STATE, "memd_init_field first");
+  CK(cudaSetDevice(c->device));
+  const memd_status s = io_block(c);
+  if (s != MEMD_OK) return s;
+  const IoLayout L = io_layout(c->P.n);
+  io->pos = (double*)(c->io_host + L.pos);
+  io->vel = (double*)(c->io_host + L.vel);
+  io->img = (int32_t*)(c->io_host + L.img);
+  io->f = (double*)(c->io_host + L.f);
+  return MEMD_OK;
+}
+
+memd_status memd_step_io(memd_ctx* c, int32_t load, int64_t nsteps, const memd_thermostat* th) {
+  if (!c) return MEMD_ERR_INVALID;
+  if (!c->initialised) return fail(c, MEMD_ERR_STATE, "memd_init_field first");
+  if (nsteps < 0) return fail(c, MEMD_ERR_INVALID, "negative step count");
+  CK(cudaSetDevice(c->device));
+  memd_status s = io_block(c);
+  if (s != MEMD_OK) return s;
+  const IoLayout L = io_layout(c->P.n);
+  const cudaStream_t st = c->stream;
+  if (load && c->P.n > 0) {
+    // positions, velocities and image counters: the first 60 n bytes
+    CK(cudaMemcpyAsync(c->io_dev, c->io_host, (size_t)L.f, cudaMemcpyHostToDevice, st));
+    launch_io_unpack(c->mesh, c->P, c->io_dev, &c->ds->err, st);
+    CKL();
+  }
+  s = memd_step(c, nsteps, th);
+  if (s != MEMD_OK) return s;
+  launch_io_pack(c->P, c->io_dev, &c->ds->err, st);
+  CKL();
+  CK(cudaMemcpyAsync(c->io_host, c->io_dev, (size_t)L.bytes, cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  if (*(const unsigned int*)(c->io_host + L.err)) return check_err(c);
   return MEMD_OK;
 }
 

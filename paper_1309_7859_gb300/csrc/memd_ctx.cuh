@@ -52,6 +52,12 @@ struct memd_ctx {
   Particles P{};
   bool initialised = false;
   bool eps_ready = false;
+  unsigned int* err_host = nullptr;  // page-locked copy of the error word (memd_step_host)
+  // the host I/O block of memd_step_io: page-locked on the host, mirrored on
+  // the device; sized for io_n particles
+  unsigned char* io_host = nullptr;
+  void* io_dev = nullptr;
+  int64_t io_n = -1;
   // the row kernel's tables for this context alone (built when tuned)
   memd::RepDesc* rows_desc = nullptr;
   memd::RowSeg* rows_segs = nullptr;

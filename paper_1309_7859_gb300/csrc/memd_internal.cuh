@@ -192,6 +192,23 @@ cudaError_t launch_step_coop(const Mesh& m, int prec, const StepParams& sp, Part
                              long long* Lg, DevState* ds, int grid, int zchunk, cudaStream_t st);
 void launch_fold_init(const Mesh& m, Particles p, const double* pos_in, const int* img_in,
                       unsigned int* err, cudaStream_t st);
+// byte offsets of the host I/O block of n particles (memd_step_io)
+struct IoLayout {
+  int64_t pos, vel, img, f, err, bytes;
+};
+__host__ __device__ inline IoLayout io_layout(int64_t n) {
+  IoLayout L;
+  L.pos = 0;
+  L.vel = 24 * n;
+  L.img = 48 * n;
+  L.f = L.img + ((12 * n + 7) / 8) * 8;
+  L.err = L.f + 24 * n;
+  L.bytes = L.err + 8;
+  return L;
+}
+void launch_io_unpack(const Mesh& m, Particles p, const void* io, unsigned int* err,
+                      cudaStream_t st);
+void launch_io_pack(Particles p, void* io, const unsigned int* err, cudaStream_t st);
 void launch_cic(const Mesh& m, Particles p, long long* Q, long long bg, cudaStream_t st);
 void launch_dipole(const Mesh& m, Particles p, DevState* ds, cudaStream_t st);
 void launch_kick_drift_deposit(const Mesh& m, const StepParams& sp, Particles p,

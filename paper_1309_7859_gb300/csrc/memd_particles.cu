@@ -957,6 +957,60 @@ __global__ void __launch_bounds__(kRedThreads)
 
 }  // namespace
 
+// One block of host I/O (memd_step_io): positions, velocities (n x 3
+// doubles each), image counters (n x 3 ints, padded to 8 bytes), forces
+// (n x 3 doubles), the error word.  unpack loads a state from it (positions
+// folded as at init), pack writes the state and forces back into it.
+__global__ void k_io_unpack(Mesh m, Particles P, const unsigned char* __restrict__ io,
+                            unsigned int* err) {
+  const int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (p >= P.n) return;
+  const IoLayout L = io_layout(P.n);
+  const double* pos = reinterpret_cast<const double*>(io + L.pos);
+  const double* vel = reinterpret_cast<const double*>(io + L.vel);
+  const int* img = reinterpret_cast<const int*>(io + L.img);
+  for (int d = 0; d < 3; ++d) {
+    double x = pos[3 * p + d];
+    int k = img[3 * p + d];
+    if (!(fabs(x) <= 4.0 * m.L[d])) {
+      atomicOr(err, kErrNonFinite);
+      x = 0.0;
+    }
+    fold(m.L[d], x, k);
+    P.x[3 * p + d] = x;
+    P.img[3 * p + d] = k;
+    P.v[3 * p + d] = vel[3 * p + d];
+  }
+}
+
+__global__ void k_io_pack(Particles P, unsigned char* __restrict__ io,
+                          const unsigned int* __restrict__ err) {
+  const int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  const IoLayout L = io_layout(P.n);
+  if (p == 0) *reinterpret_cast<unsigned int*>(io + L.err) = *err;
+  if (p >= P.n) return;
+  double* pos = reinterpret_cast<double*>(io + L.pos);
+  double* vel = reinterpret_cast<double*>(io + L.vel);
+  int* img = reinterpret_cast<int*>(io + L.img);
+  double* f = reinterpret_cast<double*>(io + L.f);
+  for (int d = 0; d < 3; ++d) {
+    pos[3 * p + d] = P.x[3 * p + d];
+    vel[3 * p + d] = P.v[3 * p + d];
+    img[3 * p + d] = P.img[3 * p + d];
+    f[3 * p + d] = P.F[3 * p + d];
+  }
+}
+
+void launch_io_unpack(const Mesh& m, Particles p, const void* io, unsigned int* err,
+                      cudaStream_t st) {
+  if (p.n > 0)
+    k_io_unpack<<<blocks_for(p.n), kThreads, 0, st>>>(m, p, (const unsigned char*)io, err);
+}
+
+void launch_io_pack(Particles p, void* io, const unsigned int* err, cudaStream_t st) {
+  k_io_pack<<<blocks_for(p.n > 0 ? p.n : 1), kThreads, 0, st>>>(p, (unsigned char*)io, err);
+}
+
 void launch_fold_init(const Mesh& m, Particles p, const double* pos_in, const int* img_in,
                       unsigned int* err, cudaStream_t st) {
   if (p.n > 0) k_fold_init<<<blocks_for(p.n), kThreads, 0, st>>>(m, p, pos_in, img_in, err);

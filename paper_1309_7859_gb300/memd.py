@@ -28,6 +28,7 @@ EXPORTS = ("memd_default_options", "memd_status_string", "memd_last_error", "mem
            "memd_destroy", "memd_init_field", "memd_step", "memd_forces", "memd_forces_device",
            "memd_energy", "memd_get_particles", "memd_set_particles", "memd_move",
            "memd_get_fields", "memd_set_fields", "memd_compute_forces", "memd_set_eps",
+           "memd_step_host", "memd_io_buffers", "memd_step_io",
            "memd_get_setup",
            "memd_get_kernel_stats", "memd_reset_kernel_stats", "memd_synchronize",
            "memd_batch_create", "memd_batch_create_kernel", "memd_batch_step",
@@ -107,6 +108,11 @@ class ServerStats(C.Structure):
                 ("step_gpu_s", C.c_double)]
 
 
+class IoBuffers(C.Structure):
+    _fields_ = [("pos", C.POINTER(C.c_double)), ("vel", C.POINTER(C.c_double)),
+                ("img", C.POINTER(C.c_int32)), ("f", C.POINTER(C.c_double))]
+
+
 class KernelStats(C.Structure):
     _fields_ = [("field_ms", C.c_double), ("field_launches", C.c_int64),
                 ("field_bytes", C.c_double), ("launches_per_step", C.c_int64),
@@ -147,6 +153,10 @@ def lib(build_if_missing=True):
     L.memd_energy.argtypes = [vp, C.POINTER(EnergyTerms)]
     L.memd_get_particles.argtypes = [vp, f64p, f64p, i32p]
     L.memd_set_particles.argtypes = [vp, f64p, f64p, i32p]
+    L.memd_step_host.argtypes = [vp, f64p, f64p, i32p, C.c_int64, C.POINTER(Thermostat),
+                                 f64p, f64p, i32p, f64p]
+    L.memd_io_buffers.argtypes = [vp, C.POINTER(IoBuffers)]
+    L.memd_step_io.argtypes = [vp, C.c_int32, C.c_int64, C.POINTER(Thermostat)]
     L.memd_move.argtypes = [vp, f64p, i32p]
     L.memd_get_fields.argtypes = [vp, f64p, f64p, i64p]
     L.memd_set_fields.argtypes = [vp, f64p, f64p, i64p]
@@ -377,6 +387,47 @@ class Memd:
         img = None if img is None else _i32(img, (self.n, 3))
         self._check(self._L.memd_set_particles(self._h, _ptr(x, C.c_double), _ptr(v, C.c_double),
                                                _ptr(img, C.c_int32)), "memd_set_particles")
+
+    def step_host(self, nsteps=1, thermostat=None, x_in=None, v_in=None, img_in=None,
+                  x_out=None, v_out=None, img_out=None, f_out=None):
+        """State load, nsteps steps and state read-back in one call with one
+        synchronisation (memd_step_host).  Arrays are used in place (page-
+        locked ones make the copies asynchronous); outputs must be C-contiguous
+        (n, 3) arrays of float64 (int32 for the image counters)."""
+        th = None
+        if thermostat is not None:
+            th = Thermostat(float(thermostat[0]), float(thermostat[1]))
+        for a, dt in ((x_out, np.float64), (v_out, np.float64), (img_out, np.int32),
+                      (f_out, np.float64)):
+            if a is not None and (a.dtype != dt or not a.flags["C_CONTIGUOUS"] or
+                                  a.shape != (self.n, 3)):
+                raise ValueError("outputs must be C-contiguous (n, 3) arrays")
+        x_in = None if x_in is None else _f64(x_in, (self.n, 3))
+        v_in = None if v_in is None else _f64(v_in, (self.n, 3))
+        img_in = None if img_in is None else _i32(img_in, (self.n, 3))
+        self._check(self._L.memd_step_host(
+            self._h, _ptr(x_in, C.c_double), _ptr(v_in, C.c_double), _ptr(img_in, C.c_int32),
+            int(nsteps), C.byref(th) if th else None, _ptr(x_out, C.c_double),
+            _ptr(v_out, C.c_double), _ptr(img_out, C.c_int32), _ptr(f_out, C.c_double)),
+            "memd_step_host")
+
+    def io_buffers(self):
+        """The library's page-locked I/O buffers as (n, 3) numpy views: pos,
+        vel, img (in and out) and f (out), valid until the next init_field."""
+        io = IoBuffers()
+        self._check(self._L.memd_io_buffers(self._h, C.byref(io)), "memd_io_buffers")
+        n = self.n
+        view = lambda p: np.ctypeslib.as_array(p, shape=(n, 3)) if n else np.zeros((0, 3))
+        return {"pos": view(io.pos), "vel": view(io.vel), "img": view(io.img), "f": view(io.f)}
+
+    def step_io(self, nsteps=1, thermostat=None, load=True):
+        """memd_step_io: load the state from the I/O buffers (load), step, and
+        read state and forces back into them; one copy each way, one sync."""
+        th = None
+        if thermostat is not None:
+            th = Thermostat(float(thermostat[0]), float(thermostat[1]))
+        self._check(self._L.memd_step_io(self._h, 1 if load else 0, int(nsteps),
+                                         C.byref(th) if th else None), "memd_step_io")
 
     def move(self, x, img=None):
         x = _f64(x, (self.n, 3))

@@ -381,3 +381,58 @@ def test_direct_launches_match_graphs_with_timing(engine):
         g.close()
     for a, b in zip(out[0], out[1]):
         assert np.array_equal(a, b)
+
+
+@pytest.mark.parametrize("engine", ["graph", "single"])
+def test_step_host_equals_the_separate_calls(engine):
+    # memd_step_host (load, step, read back, one sync) against memd_set_particles
+    # + memd_step + memd_get_particles + memd_forces, bit for bit
+    import torch
+    sysc = small_system((16, 12, 8), 60, SLAB, precision="fp32", dt=0.005)
+    a, _ = make_pair(sysc, step_engine=engine)
+    b, _ = make_pair(sysc, step_engine=engine)
+    n = sysc.n
+    pin = lambda dt: torch.empty((n, 3), dtype=dt, pin_memory=True).numpy()
+    hx, hv, hi, hf = pin(torch.float64), pin(torch.float64), pin(torch.int32), pin(torch.float64)
+    a.get_particles_into(hx, hv, hi)
+    x2, v2, i2 = a.particles()
+    for _ in range(6):
+        a.step_host(1, thermostat=(1.0, 1.0), x_in=hx, v_in=hv, img_in=hi, x_out=hx, v_out=hv,
+                    img_out=hi, f_out=hf)
+        b.set_particles(x2, v2, i2)
+        b.step(1, thermostat=(1.0, 1.0))
+        x2, v2, i2 = b.particles()
+        f2 = b.forces()
+        assert np.array_equal(hx, x2) and np.array_equal(hv, v2) and np.array_equal(hi, i2)
+        assert np.array_equal(hf, f2)
+    a.step_host(3)                          # no load, no read-back
+    b.step(3)
+    assert np.array_equal(a.particles()[0], b.particles()[0])
+    D1, B1, L1 = a.fields()
+    D2, B2, L2 = b.fields()
+    assert np.array_equal(D1, D2) and np.array_equal(L1, L2)
+
+
+@pytest.mark.parametrize("engine", ["graph", "single"])
+def test_step_io_equals_the_separate_calls(engine):
+    # an odd particle count (the image counters end off an 8-byte boundary):
+    # 60 charges and one neutral particle
+    sysc = small_system((16, 12, 8), 60, SLAB, precision="fp32", dt=0.005)
+    sysc.x = np.concatenate([sysc.x, [[3.3, 4.4, 5.5]]])
+    sysc.v = np.concatenate([sysc.v, [[0.1, -0.2, 0.3]]])
+    sysc.m = np.concatenate([sysc.m, [1.0]])
+    sysc.q = np.concatenate([sysc.q, [0]]).astype(np.int32)
+    a, _ = make_pair(sysc, step_engine=engine)
+    b, _ = make_pair(sysc, step_engine=engine)
+    io = a.io_buffers()
+    a.step_io(0, load=False)
+    x2, v2, i2 = b.particles()
+    assert np.array_equal(io["pos"], x2) and np.array_equal(io["vel"], v2)
+    for _ in range(5):
+        io["vel"] *= 0.999                  # the host edits the state between steps
+        a.step_io(1, thermostat=(1.0, 1.0), load=True)
+        b.set_particles(x2, v2 * 0.999, i2)
+        b.step(1, thermostat=(1.0, 1.0))
+        x2, v2, i2 = b.particles()
+        assert np.array_equal(io["pos"], x2) and np.array_equal(io["vel"], v2)
+        assert np.array_equal(io["img"], i2) and np.array_equal(io["f"], b.forces())
