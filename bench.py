@@ -369,7 +369,7 @@ def served(count, args):
     rng = np.random.default_rng(4242)
     arrivals = np.cumsum(rng.exponential(1.0 / args.serve_rate, size=count)).tolist()
     srv = Server(precision="fp32", budget_bytes=args.serve_budget << 30, max_slots=128,
-                 quantum=50, thermostat=(1.0, 1.0))
+                 quantum=50, thermostat=(1.0, 1.0), admission_workers=args.serve_workers)
     t0 = time.perf_counter()
     rec = serve(srv, reqs, arrivals)
     wall = time.perf_counter() - t0
@@ -399,7 +399,7 @@ def served(count, args):
             "p50_latency_s": float(np.percentile(lat, 50)),
             "p99_latency_s": float(np.percentile(lat, 99)),
             "link_updates_per_s": links / wall, "particle_steps_per_s": parts / wall,
-            "setup_s_summed": st["setup_s"], "admission_workers": 3,
+            "setup_s_summed": st["setup_s"], "admission_workers": args.serve_workers,
             "step_gpu_s": st["step_gpu_s"],
             "stepping_link_updates_per_s": links / max(st["step_gpu_s"], 1e-9),
             "mean_budget_use": st["budget_use_sum"] / max(1, st["rounds"]),
@@ -577,6 +577,8 @@ def main():
     ap.add_argument("--serve-rate", type=float, default=40.0)
     ap.add_argument("--serve-budget", type=int, default=8, help="GiB")
     ap.add_argument("--serve-max-steps", type=int, default=5000)
+    ap.add_argument("--serve-workers", type=int, default=3,
+                    help="admission threads of the server (request setup beside stepping)")
     ap.add_argument("--large", type=int, default=256,
                     help="edge of the extra larger-than-L2 system (0: skip)")
     ap.add_argument("--batch-kernel", default="auto", choices=["auto", "site", "rows"],

@@ -392,7 +392,9 @@ typedef struct memd_server_options {
   int32_t thermostat;    /* 1: Langevin (gamma, kT) for every request, 0: constant energy */
   int32_t pad;
   double gamma, kT;
-  int32_t reserved[4];
+  int32_t admission_workers;  /* threads (each with its own stream) that set requests
+                                 up beside the stepping; 0: 3 */
+  int32_t reserved[3];
 } memd_server_options;
 
 typedef struct memd_request {

@@ -79,7 +79,7 @@ struct memd_server {
   bool step_timed = false;
 };
 
-constexpr int kAdmitWorkers = 3;  // concurrent setups
+constexpr int kAdmitWorkers = 3;  // concurrent setups unless the options say otherwise
 
 namespace {
 
@@ -207,12 +207,13 @@ memd_status start_workers(memd_server* s) {
   int dev = s->opt.device;
   if (dev < 0 && cudaGetDevice(&dev) != cudaSuccess) return MEMD_ERR_CUDA;
   s->opt.device = dev;
-  for (int w = 0; w < kAdmitWorkers; ++w) {
+  const int nw = s->opt.admission_workers > 0 ? s->opt.admission_workers : kAdmitWorkers;
+  for (int w = 0; w < nw; ++w) {
     cudaStream_t st;
     if (cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess) return MEMD_ERR_CUDA;
     s->wstreams.push_back(st);
   }
-  for (int w = 0; w < kAdmitWorkers; ++w) s->workers.emplace_back(worker, s, w);
+  for (int w = 0; w < nw; ++w) s->workers.emplace_back(worker, s, w);
   return MEMD_OK;
 }
 

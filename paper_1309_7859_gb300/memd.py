@@ -90,7 +90,8 @@ class ServerOptions(C.Structure):
                 ("quantum", C.c_int32), ("device", C.c_int32), ("cuda_stream", C.c_void_p),
                 ("alloc", ALLOC), ("free", FREE), ("alloc_user", C.c_void_p),
                 ("thermostat", C.c_int32), ("pad", C.c_int32), ("gamma", C.c_double),
-                ("kT", C.c_double), ("reserved", C.c_int32 * 4)]
+                ("kT", C.c_double), ("admission_workers", C.c_int32),
+                ("reserved", C.c_int32 * 3)]
 
 
 class Request(C.Structure):
@@ -551,7 +552,7 @@ class Server:
     a step count, pump scheduling rounds, collect results."""
 
     def __init__(self, precision="fp32", budget_bytes=8 << 30, max_slots=64, quantum=50,
-                 thermostat=None, use_torch=True, stream=None):
+                 thermostat=None, use_torch=True, stream=None, admission_workers=0):
         self._L = lib()
         _live["server"].add(self)
         o = ServerOptions()
@@ -560,6 +561,7 @@ class Server:
         o.budget_bytes = int(budget_bytes)
         o.max_slots = int(max_slots)
         o.quantum = int(quantum)
+        o.admission_workers = int(admission_workers)
         if thermostat is not None:
             o.thermostat, o.gamma, o.kT = 1, float(thermostat[0]), float(thermostat[1])
         self._alloc = None
