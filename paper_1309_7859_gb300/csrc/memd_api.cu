@@ -103,6 +103,9 @@ StepParams memd_step_params(const memd_ctx* c, int thermo, double gamma, double 
   for (int t = 0; t < 8; ++t) sp.G[t] = c->G[t];
   for (int t = 0; t < 9; ++t) sp.Minv[t] = c->Minv[t];
   for (int t = 0; t < 9; ++t) sp.Mdip[t] = c->Minv[t] * sp.dip_unit * sp.inv_V;
+  for (int t = 0; t < 8; ++t) sp.Gf[t] = (float)sp.G[t];
+  for (int t = 0; t < 9; ++t) sp.Mdipf[t] = (float)sp.Mdip[t];
+  sp.self_pref = (float)sp.self_pre;
   sp.self_mode = c->self_mode;
   sp.dipole_corr = c->dipole_corr;
   sp.thermo = thermo;

@@ -173,6 +173,11 @@ struct StepParams {
   double G[8];
   double Minv[9];
   double Mdip[9];   // Minv (a / S) / Vbox: dipole force per unit charge per fixed-point P
+  // the same constants rounded to FP32, for the force terms with FP32 fields
+  // (the values a conversion at each use would give)
+  float Gf[8];
+  float Mdipf[9];
+  float self_pref;
   int self_mode;
   int dipole_corr;
   int thermo;

@@ -486,6 +486,26 @@ __device__ inline SelfC<R> self_coeffs(const int f[3]) {
   return s;
 }
 
+// step constants in the force precision R
+template <typename R>
+__device__ inline R sp_G(const StepParams& sp, int i);
+template <>
+__device__ inline double sp_G<double>(const StepParams& sp, int i) { return sp.G[i]; }
+template <>
+__device__ inline float sp_G<float>(const StepParams& sp, int i) { return sp.Gf[i]; }
+template <typename R>
+__device__ inline R sp_Mdip(const StepParams& sp, int i);
+template <>
+__device__ inline double sp_Mdip<double>(const StepParams& sp, int i) { return sp.Mdip[i]; }
+template <>
+__device__ inline float sp_Mdip<float>(const StepParams& sp, int i) { return sp.Mdipf[i]; }
+template <typename R>
+__device__ inline R sp_self_pre(const StepParams& sp);
+template <>
+__device__ inline double sp_self_pre<double>(const StepParams& sp) { return sp.self_pre; }
+template <>
+__device__ inline float sp_self_pre<float>(const StepParams& sp) { return sp.self_pref; }
+
 // sum_r G(r) a_x(r_x) a_y(r_y) a_z(r_z) with the derivative factor along
 // `dir`, summed axis by axis (x first, then y, then z)
 template <typename R>
@@ -496,8 +516,8 @@ __device__ inline R self_sum(const StepParams& sp, const SelfC<R>& s, int dir) {
   R sz[2];
 #pragma unroll
   for (int z = 0; z < 2; ++z) {
-    const R s0 = (R)sp.G[4 * z] * x0 + (R)sp.G[4 * z + 1] * x1;
-    const R s1 = (R)sp.G[4 * z + 2] * x0 + (R)sp.G[4 * z + 3] * x1;
+    const R s0 = sp_G<R>(sp, 4 * z) * x0 + sp_G<R>(sp, 4 * z + 1) * x1;
+    const R s1 = sp_G<R>(sp, 4 * z + 2) * x0 + sp_G<R>(sp, 4 * z + 3) * x1;
     sz[z] = s0 * y0 + s1 * y1;
   }
   return sz[0] * z0 + sz[1] * z1;
@@ -593,8 +613,11 @@ __device__ __forceinline__ void gather_body(const Mesh& m, const StepParams& sp,
     if (thermo) sig = P.sig[p];
   }
   // pre (optional): the dipole sum and the step counter, read by the caller
+  // (the warp's lanes all hold charges of one system: lane 0 reads it for the
+  // warp, and lane 0 is active whenever any lane of its warp is)
+  const int wlane = (threadIdx.x + blockDim.x * threadIdx.y) & 31;
   long long Pl[3] = {0, 0, 0};
-  if (comp && sp.dipole_corr) {
+  if (active && wlane == 0 && sp.dipole_corr) {
     Pl[0] = pre ? pre[0] : (long long)ds->Pacc[0];
     Pl[1] = pre ? pre[1] : (long long)ds->Pacc[1];
     Pl[2] = pre ? pre[2] : (long long)ds->Pacc[2];
@@ -618,7 +641,9 @@ __device__ __forceinline__ void gather_body(const Mesh& m, const StepParams& sp,
     f[e] = __shfl_sync(full, fq, base + e);
   }
   T E[3] = {T(0), T(0), T(0)};
-  double iw[3] = {0.0, 0.0, 0.0}, itot = 0.0;
+  // 1/eps of the self term, summed in the field precision: the FP64 table
+  // with FP64 fields, the field's own 1/eps with FP32 fields
+  T iw[3] = {T(0), T(0), T(0)}, itot = T(0);
   if (active) {
     T Dv[3], Iv[3];
     double I64[3] = {0.0, 0.0, 0.0};
@@ -642,13 +667,11 @@ __device__ __forceinline__ void gather_body(const Mesh& m, const StepParams& sp,
       const int e1 = (d + 1) % 3, e2 = (d + 2) % 3;
       const T w = ((T)wgt(f[e1], a1) / (T)kS) * ((T)wgt(f[e2], a2) / (T)kS);
       E[d] = Dv[d] * Iv[d] * w;
-      // 1/eps of the self term: FP64 table with FP64 fields, the field's
-      // own 1/eps with FP32 fields
-      if (sizeof(T) == 4) I64[d] = (double)Iv[d];
-      if (sp.self_mode != 0) itot += I64[d];
+      const T iv = sizeof(T) == 8 ? (T)I64[d] : Iv[d];
+      if (sp.self_mode != 0) itot += iv;
       if (sp.self_mode == 2) {
-        const double wd = ((double)wgt(f[e1], a1) / (double)kS) * ((double)wgt(f[e2], a2) / (double)kS);
-        iw[d] = I64[d] * wd;
+        const T wd = ((T)wgt(f[e1], a1) / (T)kS) * ((T)wgt(f[e2], a2) / (T)kS);
+        iw[d] = iv * wd;
       }
     }
   }
@@ -669,6 +692,18 @@ __device__ __forceinline__ void gather_body(const Mesh& m, const StepParams& sp,
     itot = itot + __shfl_xor_sync(full, itot, 1);
     itot = itot + __shfl_xor_sync(full, itot, 2);
   }
+  // dipole force per unit charge, M P per component, computed by lane 0 for
+  // the warp (same expression and rounding for every lane) and broadcast
+  T MPw[3] = {T(0), T(0), T(0)};
+  if (sp.dipole_corr) {
+    if (wlane == 0)
+#pragma unroll
+      for (int e = 0; e < 3; ++e)
+        MPw[e] = sp_Mdip<T>(sp, 3 * e) * (T)Pl[0] + sp_Mdip<T>(sp, 3 * e + 1) * (T)Pl[1] +
+                 sp_Mdip<T>(sp, 3 * e + 2) * (T)Pl[2];
+#pragma unroll
+    for (int e = 0; e < 3; ++e) MPw[e] = __shfl_sync(full, MPw[e], 0);
+  }
   if (comp) {
     // field force terms (q E, self energy, dipole) in R = T: FP64 with FP64
     // fields, FP32 with FP32 fields; the Langevin force, the velocity and the
@@ -681,14 +716,13 @@ __device__ __forceinline__ void gather_body(const Mesh& m, const StepParams& sp,
     R F = q * (R)Ed;
     if (sp.self_mode != 0) {
       const R ie_cell = (R)itot * (R(1) / R(12));
-      const double iwd = d == 0 ? iw[0] : (d == 1 ? iw[1] : iw[2]);
-      const R ie_d = (sp.self_mode == 2) ? (R)iwd : ie_cell;
+      const R iwd = d == 0 ? iw[0] : (d == 1 ? iw[1] : iw[2]);
+      const R ie_d = (sp.self_mode == 2) ? iwd : ie_cell;
       const SelfC<R> sc = self_coeffs<R>(f);
-      F = F + (q * q * (R)sp.self_pre) * ie_d * self_sum<R>(sp, sc, d);
+      F = F + (q * q * sp_self_pre<R>(sp)) * ie_d * self_sum<R>(sp, sc, d);
     }
     if (sp.dipole_corr) {
-      const R MP = (R)sp.Mdip[3 * d] * (R)Pl[0] + (R)sp.Mdip[3 * d + 1] * (R)Pl[1] +
-                   (R)sp.Mdip[3 * d + 2] * (R)Pl[2];
+      const R MP = d == 0 ? MPw[0] : (d == 1 ? MPw[1] : MPw[2]);
       F = F + q * MP;
     }
     const double Fd = (double)F;

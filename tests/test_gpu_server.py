@@ -26,7 +26,9 @@ def requests(count=8, seed=11):
                           c_light=1.0, dt=0.005, precision="fp32",
                           x=inputs.uniform_positions(rng, n, box), q=inputs.neutral_charges(rng, n),
                           m=np.ones(n), v=inputs.thermal_velocities(rng, n),
-                          steps=int(rng.integers(7, 40)), thermostat=TH, seed=500 + r))
+                          # long enough (8-20 rounds of 8 steps) that admissions
+                          # finishing on the worker threads overlap running requests
+                          steps=int(rng.integers(64, 160)), thermostat=TH, seed=500 + r))
     return out
 
 
