@@ -208,9 +208,18 @@ memd_status start_workers(memd_server* s) {
   if (dev < 0 && cudaGetDevice(&dev) != cudaSuccess) return MEMD_ERR_CUDA;
   s->opt.device = dev;
   const int nw = s->opt.admission_workers > 0 ? s->opt.admission_workers : kAdmitWorkers;
+  // setup runs many small, latency-bound kernels (multigrid levels, scans);
+  // on streams of the highest priority their blocks are scheduled ahead of
+  // the batch's waiting tiles instead of queueing behind a whole step
+  int lo = 0, hi = 0;
+  if (cudaDeviceGetStreamPriorityRange(&lo, &hi) != cudaSuccess) {
+    cudaGetLastError();
+    lo = hi = 0;
+  }
   for (int w = 0; w < nw; ++w) {
     cudaStream_t st;
-    if (cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess) return MEMD_ERR_CUDA;
+    if (cudaStreamCreateWithPriority(&st, cudaStreamNonBlocking, hi) != cudaSuccess)
+      return MEMD_ERR_CUDA;
     s->wstreams.push_back(st);
   }
   for (int w = 0; w < nw; ++w) s->workers.emplace_back(worker, s, w);

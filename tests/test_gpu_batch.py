@@ -134,3 +134,46 @@ def test_row_kernel_falls_back_to_site_tiles():
         g.step(4, thermostat=(1.0, 1.0))
     for gm, ga in zip(members, alone):
         assert_same(state(gm), state(ga))
+
+
+def test_batch_of_64_at_bench_size_matches_alone_and_the_oracle():
+    # the bench's batched workload itself (64 replicas, meshes 16-48^3,
+    # 200-8000 charges, FP32) in the launch configuration it times (the
+    # autotuned field kernel): every member keeps Gauss's law exact, sampled
+    # members are bit identical to their solo runs, and one small member's
+    # forces are recomputed by the oracle from its batched state
+    import torch
+    from oracle import oracle as O
+    from paper_1309_7859_gb300.memd import Batch, Memd
+    from tests.test_gpu_parity import oracle_eps, rel
+    systems = inputs.batch_replicas(count=64)
+    stream = torch.cuda.Stream()
+
+    def mk(s, st=None):
+        g = Memd(s.mesh, s.box, s.eps, c_light=s.c_light, dt=s.dt, precision=s.precision,
+                 seed=s.seed, stream=st, field_kernel="ldg")
+        g.init_field(s.x, s.q, s.m, s.v)
+        return g
+    members = [mk(s, stream) for s in systems]
+    batch = Batch(members)
+    batch.step(4, thermostat=systems[0].thermostat)
+    batch.synchronize()
+    for g in members:
+        assert g.energy()["gauss_exact"] == 1.0
+    for i in (0, 17, 40, 63):
+        ga = mk(systems[i])
+        ga.step(4, thermostat=systems[i].thermostat)
+        assert_same(state(members[i]), state(ga))
+        ga.close()
+    i = min(range(64), key=lambda k: systems[k].sites)
+    s = systems[i]
+    D, B, Lg = members[i].fields()
+    x, v, img = members[i].particles()
+    o = O.OracleSystem(s.mesh, s.box, eps=oracle_eps(s.eps), c_light=s.c_light, dt=s.dt,
+                       seed=s.seed)
+    o.set_particles(x, s.q, s.m, v, img)
+    o.field("D")[...] = D
+    o.field("Lg")[...] = Lg
+    o.gather()
+    assert rel(members[i].forces(), o.particles("F")) < 1e-5
+    batch.close()
