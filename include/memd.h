@@ -302,6 +302,21 @@ memd_status memd_compute_forces(memd_ctx *ctx);
  * the previous D.  Batches holding the context rebuild their tables. */
 memd_status memd_set_eps(memd_ctx *ctx, const memd_eps_profile *eps, int32_t relax_field);
 
+/* Checkpoint and resume.  A saved state holds the whole dynamical state: D
+ * and B in the field precision, the exact ledger, positions, velocities,
+ * image counters, forces, valences, masses, the step counter (which keys the
+ * Langevin noise) and the dipole of the last update; pending transfers are
+ * applied first.  It is restored into a context created with the same mesh,
+ * box and precision and initialised with the same particle count (the
+ * permittivity, options and thermostat are the context's own); stepping on
+ * from it gives bit for bit what the saved context would have given.
+ * memd_state_bytes is the size of a saved state of ctx.  Errors: INVALID
+ * (buffer too small, not a saved state, or a mesh, precision or particle
+ * count mismatch; nothing changed), STATE before memd_init_field. */
+int64_t memd_state_bytes(const memd_ctx *ctx);
+memd_status memd_save_state(memd_ctx *ctx, void *buf, int64_t bytes);
+memd_status memd_load_state(memd_ctx *ctx, const void *buf, int64_t bytes);
+
 /* Create-time results: 1/eps per link (3V, may be NULL), the lattice Green's
  * table G(dx,dy,dz) at index dx + 2 dy + 4 dz (8, may be NULL) and the inverse
  * effective permittivity tensor (9, row major, may be NULL). */

@@ -1502,6 +1502,122 @@ memd_status memd_set_fields(memd_ctx* c, const double* D, const double* B, const
   return MEMD_OK;
 }
 
+// ----------------------------------------------------- checkpoint / resume
+// A saved state: this header, then D and B in the field precision, the
+// ledger, and the particle arrays x, v, F, Ft (FP64), img, q (int32), m.
+struct StateHeader {
+  char magic[8];
+  int32_t version, prec;
+  int32_t mesh[3], pad;
+  int64_t n, step;
+  int64_t Plast[3];
+  double box[3];
+};
+static const char kStateMagic[8] = {'M', 'E', 'M', 'D', 'S', 'T', 'A', 'T'};
+
+int64_t memd_state_bytes(const memd_ctx* c) {
+  if (!c) return 0;
+  const int64_t V3 = 3 * c->mesh.V, n = c->P.n;
+  return (int64_t)sizeof(StateHeader) + V3 * (2 * (int64_t)memd_esz(c) + 8) + n * 120;
+}
+
+memd_status memd_save_state(memd_ctx* c, void* buf, int64_t bytes) {
+  if (!c || !buf) return MEMD_ERR_INVALID;
+  if (!c->initialised) return fail(c, MEMD_ERR_STATE, "memd_init_field first");
+  if (bytes < memd_state_bytes(c)) return fail(c, MEMD_ERR_INVALID, "state buffer too small");
+  CK(cudaSetDevice(c->device));
+  {
+    const memd_status fe = memd_flush(c);
+    if (fe != MEMD_OK) return fe;
+  }
+  const cudaStream_t st = c->stream;
+  const size_t V3 = 3 * (size_t)c->mesh.V, n = (size_t)c->P.n, es = memd_esz(c);
+  StateHeader h;
+  std::memset(&h, 0, sizeof(h));
+  std::memcpy(h.magic, kStateMagic, 8);
+  h.version = 1;
+  h.prec = c->prec;
+  for (int d = 0; d < 3; ++d) {
+    h.mesh[d] = c->mesh.n[d];
+    h.box[d] = c->mesh.L[d];
+  }
+  h.n = (int64_t)n;
+  CK(cudaMemcpyAsync(&h.step, &c->ds->step, sizeof(long long), cudaMemcpyDeviceToHost, st));
+  CK(cudaMemcpyAsync(h.Plast, c->ds->Plast, 3 * sizeof(long long), cudaMemcpyDeviceToHost, st));
+  char* p = (char*)buf + sizeof(StateHeader);
+  bool ok = true;
+  auto get = [&](const void* src, size_t b) {
+    if (b && cudaMemcpyAsync(p, src, b, cudaMemcpyDeviceToHost, st) != cudaSuccess) ok = false;
+    p += b;
+  };
+  get(c->D(), V3 * es);
+  get(c->B(), V3 * es);
+  get(c->Lg, V3 * 8);
+  get(c->P.x, 3 * n * 8);
+  get(c->P.v, 3 * n * 8);
+  get(c->P.F, 3 * n * 8);
+  get(c->P.Ft, 3 * n * 8);
+  get(c->P.img, 3 * n * 4);
+  get(c->P.q, n * 4);
+  get(c->P.m, n * 8);
+  if (!ok) return fail(c, MEMD_ERR_CUDA, "state copy");
+  CK(cudaStreamSynchronize(st));
+  std::memcpy(buf, &h, sizeof(h));
+  return check_err(c);
+}
+
+memd_status memd_load_state(memd_ctx* c, const void* buf, int64_t bytes) {
+  if (!c || !buf) return MEMD_ERR_INVALID;
+  if (!c->initialised) return fail(c, MEMD_ERR_STATE, "memd_init_field first");
+  StateHeader h;
+  if (bytes < (int64_t)sizeof(h)) return fail(c, MEMD_ERR_INVALID, "state buffer too small");
+  std::memcpy(&h, buf, sizeof(h));
+  if (std::memcmp(h.magic, kStateMagic, 8) != 0 || h.version != 1)
+    return fail(c, MEMD_ERR_INVALID, "not a saved state");
+  if (h.prec != c->prec || h.n != c->P.n || h.mesh[0] != c->mesh.n[0] ||
+      h.mesh[1] != c->mesh.n[1] || h.mesh[2] != c->mesh.n[2] || h.box[0] != c->mesh.L[0] ||
+      h.box[1] != c->mesh.L[1] || h.box[2] != c->mesh.L[2])
+    return fail(c, MEMD_ERR_INVALID, "saved state of another mesh, precision or particle count");
+  if (bytes < memd_state_bytes(c)) return fail(c, MEMD_ERR_INVALID, "state buffer too small");
+  CK(cudaSetDevice(c->device));
+  const cudaStream_t st = c->stream;
+  drop_graphs(c);
+  harvest_timing(c);
+  CK(cudaStreamSynchronize(st));
+  const size_t V3 = 3 * (size_t)c->mesh.V, n = (size_t)c->P.n, es = memd_esz(c);
+  const char* p = (const char*)buf + sizeof(StateHeader);
+  bool ok = true;
+  auto put = [&](void* dst, size_t b) {
+    if (b && cudaMemcpyAsync(dst, p, b, cudaMemcpyHostToDevice, st) != cudaSuccess) ok = false;
+    p += b;
+  };
+  put(c->D(), V3 * es);
+  put(c->B(), V3 * es);
+  put(c->Lg, V3 * 8);
+  put(c->P.x, 3 * n * 8);
+  put(c->P.v, 3 * n * 8);
+  put(c->P.F, 3 * n * 8);
+  put(c->P.Ft, 3 * n * 8);
+  put(c->P.img, 3 * n * 4);
+  put(c->P.q, n * 4);
+  put(c->P.m, n * 8);
+  if (!ok) return fail(c, MEMD_ERR_CUDA, "state copy");
+  // transfers none pending, the step counter and last dipole of the saved
+  // state, the accumulators clear; the per-particle constants are formed
+  // again from the masses at the next step
+  CK(cudaMemsetAsync(c->Tb, 0, V3 * sizeof(long long), st));
+  if (c->Tb2) CK(cudaMemsetAsync(c->Tb2, 0, V3 * sizeof(long long), st));
+  c->pending = false;
+  CK(cudaMemcpyAsync(&c->ds->step, &h.step, sizeof(long long), cudaMemcpyHostToDevice, st));
+  CK(cudaMemcpyAsync(c->ds->Plast, h.Plast, 3 * sizeof(long long), cudaMemcpyHostToDevice, st));
+  CK(cudaMemsetAsync(c->ds->Pacc, 0, sizeof(c->ds->Pacc), st));
+  CK(cudaMemsetAsync(&c->ds->ticket, 0, sizeof(unsigned int), st));
+  CK(cudaStreamSynchronize(st));
+  c->sig_ready = false;
+  c->gen += 1;
+  return check_err(c);
+}
+
 memd_status memd_compute_forces(memd_ctx* c) {
   if (!c) return MEMD_ERR_INVALID;
   if (!c->initialised) return fail(c, MEMD_ERR_STATE, "memd_init_field first");

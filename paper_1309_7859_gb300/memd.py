@@ -28,7 +28,8 @@ EXPORTS = ("memd_default_options", "memd_status_string", "memd_last_error", "mem
            "memd_destroy", "memd_init_field", "memd_step", "memd_forces", "memd_forces_device",
            "memd_energy", "memd_get_particles", "memd_set_particles", "memd_move",
            "memd_get_fields", "memd_set_fields", "memd_compute_forces", "memd_set_eps",
-           "memd_step_host", "memd_io_buffers", "memd_step_io",
+           "memd_step_host", "memd_io_buffers", "memd_step_io", "memd_state_bytes",
+           "memd_save_state", "memd_load_state",
            "memd_get_setup",
            "memd_get_kernel_stats", "memd_reset_kernel_stats", "memd_synchronize",
            "memd_batch_create", "memd_batch_create_kernel", "memd_batch_step",
@@ -157,6 +158,10 @@ def lib(build_if_missing=True):
     L.memd_step_host.argtypes = [vp, f64p, f64p, i32p, C.c_int64, C.POINTER(Thermostat),
                                  f64p, f64p, i32p, f64p]
     L.memd_io_buffers.argtypes = [vp, C.POINTER(IoBuffers)]
+    L.memd_state_bytes.restype = C.c_int64
+    L.memd_state_bytes.argtypes = [vp]
+    L.memd_save_state.argtypes = [vp, C.c_void_p, C.c_int64]
+    L.memd_load_state.argtypes = [vp, C.c_void_p, C.c_int64]
     L.memd_step_io.argtypes = [vp, C.c_int32, C.c_int64, C.POINTER(Thermostat)]
     L.memd_move.argtypes = [vp, f64p, i32p]
     L.memd_get_fields.argtypes = [vp, f64p, f64p, i64p]
@@ -411,6 +416,19 @@ class Memd:
             int(nsteps), C.byref(th) if th else None, _ptr(x_out, C.c_double),
             _ptr(v_out, C.c_double), _ptr(img_out, C.c_int32), _ptr(f_out, C.c_double)),
             "memd_step_host")
+
+    def save_state(self):
+        """The whole dynamical state as bytes (memd_save_state)."""
+        nb = self._L.memd_state_bytes(self._h)
+        buf = np.zeros(nb, dtype=np.uint8)
+        self._check(self._L.memd_save_state(self._h, buf.ctypes.data, nb), "memd_save_state")
+        return buf
+
+    def load_state(self, buf):
+        """Restore a state from save_state (same mesh, box, precision and
+        particle count)."""
+        buf = np.ascontiguousarray(buf, dtype=np.uint8)
+        self._check(self._L.memd_load_state(self._h, buf.ctypes.data, buf.size), "memd_load_state")
 
     def io_buffers(self):
         """The library's page-locked I/O buffers as (n, 3) numpy views: pos,

@@ -436,3 +436,35 @@ def test_step_io_equals_the_separate_calls(engine):
         x2, v2, i2 = b.particles()
         assert np.array_equal(io["pos"], x2) and np.array_equal(io["vel"], v2)
         assert np.array_equal(io["img"], i2) and np.array_equal(io["f"], b.forces())
+
+
+@pytest.mark.parametrize("engine,precision", [("graph", "fp64"), ("single", "fp32"),
+                                              ("graph", "fp32")])
+def test_resume_from_a_saved_state_is_bit_identical(engine, precision):
+    # run A: 7 steps, save, 9 more; run B: a fresh context, any initial state
+    # of the same particle count, load A's saved state, 9 steps: identical
+    sysc = small_system((16, 12, 10), 80, SLAB, precision=precision, dt=0.005)
+    a, _ = make_pair(sysc, step_engine=engine)
+    a.step(7, thermostat=(1.0, 1.0))
+    saved = a.save_state()
+    a.step(9, thermostat=(1.0, 1.0))
+    b, _ = make_pair(sysc, step_engine=engine, init=False)
+    b.init_field(sysc.x[::-1].copy(), sysc.q, sysc.m, None)
+    b.load_state(saved)
+    b.step(9, thermostat=(1.0, 1.0))
+    for u, w in zip(a.fields(), b.fields()):
+        assert np.array_equal(u, w)
+    for u, w in zip(a.particles(), b.particles()):
+        assert np.array_equal(u, w)
+    assert np.array_equal(a.forces(), b.forces())
+    ea, eb = a.energy(), b.energy()
+    for k in ("total", "P0", "P1", "P2", "step"):
+        assert ea[k] == eb[k], k
+    # a state of another particle count is refused and changes nothing
+    from paper_1309_7859_gb300.memd import MemdError
+    c, _ = make_pair(small_system((16, 12, 10), 20, SLAB, precision=precision), init=True,
+                     step_engine=engine)
+    before = c.particles()[0].copy()
+    with pytest.raises(MemdError):
+        c.load_state(saved)
+    assert np.array_equal(c.particles()[0], before)

@@ -110,3 +110,21 @@ def test_serve_driver_records_latency():
     for r in rec:
         assert r["done"] is not None and r["latency"] > 0
     srv.close()
+
+
+def test_served_stream_sample_matches_alone():
+    # requests drawn from the bench's served stream itself (meshes 16-96,
+    # 100-50000 charges, smooth random eps), run through the server with the
+    # bench's options and arrivals while others run, each against its solo run
+    # (step counts shortened to keep the solo runs quick)
+    from paper_1309_7859_gb300.memd import Server, serve
+    reqs = inputs.served_stream(count=10, smin=40, smax=120)
+    srv = Server(precision="fp32", budget_bytes=8 << 30, max_slots=128, quantum=50,
+                 thermostat=TH)
+    rng = np.random.default_rng(4)
+    arrivals = np.cumsum(rng.exponential(1.0 / 40.0, size=len(reqs))).tolist()
+    rec = serve(srv, reqs, arrivals)
+    assert len(rec) == len(reqs)
+    for s, r in zip(reqs, rec):
+        check_same(srv.result(r["id"]), alone(s))
+    srv.close()
