@@ -447,6 +447,7 @@ static void launch_field(memd_ctx* c, int par, double cB, double cD, FusedCfg cf
 // 20 back-to-back launches, after one warm-up).  Results are cached per mesh
 // shape, precision and kernel choice for the life of the process.
 static memd_status autotune_fused(memd_ctx* c) {
+  memd::NvtxRange nvtx_("autotune_fused");
   static std::mutex mu;
   static std::map<std::tuple<int, int, int, int, int>, FusedCfg> cache;
   c->tma_ok = (c->field_kernel == MEMD_FIELD_AUTO || c->field_kernel == MEMD_FIELD_TMA) &&
@@ -755,6 +756,7 @@ out:
 
 memd_status memd_create(const int32_t mesh[3], const double box[3], const memd_eps_profile* eps,
                         double c_light, double dt, const memd_options* opt, memd_ctx** out) {
+  memd::NvtxRange nvtx_("memd_create");
   if (!out) return MEMD_ERR_INVALID;
   *out = nullptr;
   if (!mesh || !box || !eps) return MEMD_ERR_INVALID;
@@ -914,6 +916,7 @@ static void free_particles(memd_ctx* c) {
 
 memd_status memd_init_field(memd_ctx* c, int64_t n, const double* pos, const int32_t* q,
                             const double* mass, const double* vel) {
+  memd::NvtxRange nvtx_("memd_init_field");
   if (!c) return MEMD_ERR_INVALID;
   if (n < 0 || (n > 0 && (!pos || !q))) return fail(c, MEMD_ERR_INVALID, "bad particle arrays");
   CK(cudaSetDevice(c->device));
@@ -1113,6 +1116,7 @@ static memd_status poll_err(memd_ctx* c, bool block) {
 }
 
 memd_status memd_step(memd_ctx* c, int64_t nsteps, const memd_thermostat* th) {
+  memd::NvtxRange nvtx_("memd_step");
   if (!c) return MEMD_ERR_INVALID;
   if (!c->initialised) return fail(c, MEMD_ERR_STATE, "memd_init_field first");
   if (nsteps < 0) return fail(c, MEMD_ERR_INVALID, "negative step count");
@@ -1399,6 +1403,7 @@ memd_status memd_io_buffers(memd_ctx* c, memd_io* io) {
 }
 
 memd_status memd_step_io(memd_ctx* c, int32_t load, int64_t nsteps, const memd_thermostat* th) {
+  memd::NvtxRange nvtx_("memd_step_io");
   if (!c) return MEMD_ERR_INVALID;
   if (!c->initialised) return fail(c, MEMD_ERR_STATE, "memd_init_field first");
   if (nsteps < 0) return fail(c, MEMD_ERR_INVALID, "negative step count");
@@ -1639,6 +1644,7 @@ memd_status memd_compute_forces(memd_ctx* c) {
 // valid; with relax_field it is rebuilt from the exact ledger and relaxed to
 // the electrostatic minimum of the new medium, as memd_init_field does.
 memd_status memd_set_eps(memd_ctx* c, const memd_eps_profile* eps, int32_t relax_field) {
+  memd::NvtxRange nvtx_("memd_set_eps");
   if (!c) return MEMD_ERR_INVALID;
   if (!eps) return fail(c, MEMD_ERR_INVALID, "no permittivity profile");
   if (!eps_valid(eps, c->mesh.L, c->mesh.a)) return fail(c, MEMD_ERR_INVALID, "permittivity profile");

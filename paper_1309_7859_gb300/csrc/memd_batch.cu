@@ -221,6 +221,7 @@ __global__ void k_read_flush(const float4* __restrict__ p, size_t n4, float* sin
 // step overwrites with the same values).  Each sample is one launch after
 // a 256 MiB read that evicts L2; median of 3 samples after a warm-up.
 memd_status autotune_batch(memd_batch* b) {
+  memd::NvtxRange nvtx_("autotune_batch");
   static const int tys[3] = {4, 8, 16}, zs[4] = {4, 8, 16, 32};
   const int nty = b->prec == MEMD_FP32 ? 3 : 2;  // FP64 16-row tiles exceed static shared memory
   const int pfs = b->prec == MEMD_FP32 ? 2 : 1;  // FP64: one plane ahead (registers)
@@ -422,6 +423,7 @@ memd_status memd_batch_create_kernel(int32_t count, memd_ctx* const* members,
 }
 
 memd_status memd_batch_step(memd_batch* b, int64_t nsteps, const memd_thermostat* th) {
+  memd::NvtxRange nvtx_("memd_batch_step");
   if (!b) return MEMD_ERR_INVALID;
   if (nsteps < 0) return bfail(b, MEMD_ERR_INVALID, "negative step count");
   BCK(cudaSetDevice(b->device));

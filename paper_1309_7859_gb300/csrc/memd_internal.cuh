@@ -9,9 +9,20 @@
 
 #include <cuda.h>
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 #include <stdint.h>
 
 namespace memd {
+
+// NVTX range around a host-side phase (create, init, step, batch step,
+// server round, request setup, autotuning): visible in a profiler's
+// timeline, a no-op without one
+struct NvtxRange {
+  explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+  ~NvtxRange() { nvtxRangePop(); }
+  NvtxRange(const NvtxRange&) = delete;
+  NvtxRange& operator=(const NvtxRange&) = delete;
+};
 
 constexpr int kWBits = 16;
 constexpr int64_t kS = int64_t(1) << kWBits;

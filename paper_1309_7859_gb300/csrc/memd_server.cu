@@ -192,7 +192,11 @@ void worker(memd_server* s, int w) {
       r = s->todo.front();
       s->todo.pop_front();
     }
-    const memd_status st = admit(s, *r, s->wstreams[w]);
+    memd_status st;
+    {
+      memd::NvtxRange nvtx_("request setup");
+      st = admit(s, *r, s->wstreams[w]);
+    }
     {
       std::lock_guard<std::mutex> g(s->mu);
       s->ready.emplace_back(r, st);
@@ -327,6 +331,7 @@ memd_status memd_server_submit(memd_server* s, const memd_request* q, int64_t* i
 
 memd_status memd_server_pump(memd_server* s, int32_t* n_active, int32_t* n_queued,
                              int32_t* n_done) {
+  memd::NvtxRange nvtx_("memd_server_pump");
   if (!s) return MEMD_ERR_INVALID;
   // 1. retire requests that have taken all their steps (the batch refers to
   // its members, so it goes first when any member leaves)

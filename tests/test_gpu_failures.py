@@ -1,0 +1,117 @@
+"""Failure detection, with every failure made on the host: a corrupted ledger
+entry, a device allocator that runs dry, invalid inputs, a server request
+whose setup fails among requests that succeed.  No test faults, traps or
+hangs the GPU; each checks the reported status and that the library stays
+usable afterwards."""
+import numpy as np
+import pytest
+
+from paper_1309_7859_gb300.inputs import EpsSpec
+from tests.test_gpu_parity import SLAB, small_system
+
+pytestmark = pytest.mark.gpu
+
+
+def make(sysc, **kw):
+    from paper_1309_7859_gb300.memd import Memd
+    g = Memd(sysc.mesh, sysc.box, sysc.eps, c_light=sysc.c_light, dt=sysc.dt,
+             precision=sysc.precision, seed=sysc.seed, **kw)
+    return g
+
+
+def test_corrupted_ledger_entry_is_flagged():
+    sysc = small_system((12, 10, 8), 40, SLAB, precision="fp32")
+    g = make(sysc)
+    g.init_field(sysc.x, sysc.q, sysc.m, sysc.v)
+    g.step(3, thermostat=(1.0, 1.0))
+    assert g.energy()["gauss_exact"] == 1.0
+    D, B, Lg = g.fields()
+    Lg[1, 2, 3, 4] += 1                      # one fixed-point unit on one link
+    g.set_fields(Lg=Lg)
+    e = g.energy()
+    assert e["gauss_exact"] == 0.0
+    Lg[1, 2, 3, 4] -= 1                      # restored: exact again
+    g.set_fields(Lg=Lg)
+    assert g.energy()["gauss_exact"] == 1.0
+    g.step(2, thermostat=(1.0, 1.0))
+
+
+@pytest.mark.parametrize("fail_after", [0, 3, 12])
+def test_device_allocator_running_dry_is_reported(monkeypatch, fail_after):
+    # the allocator callback returns NULL after `fail_after` allocations:
+    # create (or init) reports OOM, frees what it took, and the next context
+    # with a working allocator runs normally
+    from paper_1309_7859_gb300 import memd as M
+    sysc = small_system((12, 10, 8), 40, SLAB, precision="fp32")
+    real = M._TorchAllocator._alloc
+    count = {"n": 0}
+
+    def dry(self, user, nbytes, stream):
+        count["n"] += 1
+        if count["n"] > fail_after:
+            return None
+        return real(self, user, nbytes, stream)
+
+    monkeypatch.setattr(M._TorchAllocator, "_alloc", dry)
+    with pytest.raises(M.MemdError) as err:
+        g = make(sysc)
+        g.init_field(sysc.x, sysc.q, sysc.m, sysc.v)
+    assert err.value.status == 3             # MEMD_ERR_OOM
+    monkeypatch.setattr(M._TorchAllocator, "_alloc", real)
+    g = make(sysc)
+    g.init_field(sysc.x, sysc.q, sysc.m, sysc.v)
+    g.step(3, thermostat=(1.0, 1.0))
+    assert g.energy()["gauss_exact"] == 1.0
+
+
+def test_invalid_inputs_are_refused():
+    from paper_1309_7859_gb300.memd import Memd, MemdError
+    # 960 vertices: one unit of excess charge has no exact background per vertex
+    sysc = small_system((12, 10, 8), 16, SLAB, precision="fp64")
+    with pytest.raises(MemdError) as err:    # c dt sqrt(3) >= a (Eq. 30)
+        Memd(sysc.mesh, sysc.box, sysc.eps, c_light=100.0, dt=0.01)
+    assert err.value.status == 2             # MEMD_ERR_COURANT
+    g = make(sysc)
+    x = sysc.x.copy()
+    x[3, 1] = np.nan
+    with pytest.raises(MemdError) as err:
+        g.init_field(x, sysc.q, sysc.m, sysc.v)
+    assert err.value.status == 1             # non-finite position
+    q = sysc.q.copy()
+    q[0] += 1                                # one unit of charge over 960 vertices
+    with pytest.raises(MemdError) as err:
+        g.init_field(sysc.x, q, sysc.m, sysc.v)
+    assert err.value.status == 1
+    with pytest.raises(MemdError) as err:
+        g.step(1)                            # not initialised
+    assert err.value.status == 10            # MEMD_ERR_STATE
+    g.init_field(sysc.x, sysc.q, sysc.m, sysc.v)
+    g.step(2, thermostat=(1.0, 1.0))
+    assert g.energy()["gauss_exact"] == 1.0
+
+
+def test_server_request_whose_setup_fails_leaves_the_others_intact():
+    # a request whose permittivity is invalid (negative on a link) fails in
+    # its admission worker; the requests around it finish with the results
+    # they get alone
+    from paper_1309_7859_gb300.memd import MemdError, Server
+    from tests.test_gpu_server import TH, alone, check_same, requests
+    reqs = requests(4, seed=21)
+    bad = requests(1, seed=22)[0]
+    V = bad.mesh[0] * bad.mesh[1] * bad.mesh[2]
+    bad.eps = EpsSpec("links", 0, (), -np.ones(3 * V))
+    srv = Server(precision="fp32", budget_bytes=256 << 20, max_slots=8, quantum=16, thermostat=TH)
+    ids = [srv.submit(s) for s in reqs[:2]]
+    bad_id = srv.submit(bad)
+    ids += [srv.submit(s) for s in reqs[2:]]
+    for _ in range(1000):
+        a, q, d = srv.pump()
+        if d == len(reqs) + 1:
+            break
+    assert srv.status(bad_id) == 3           # failed
+    with pytest.raises(MemdError):
+        srv.result(bad_id)
+    for s, rid in zip(reqs, ids):
+        assert srv.status(rid) == 2
+        check_same(srv.result(rid), alone(s))
+    srv.close()
