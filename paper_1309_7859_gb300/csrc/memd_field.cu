@@ -354,21 +354,6 @@ __global__ void __launch_bounds__(TX* TY)
                         zchunk);
 }
 
-// Many independent systems in one launch: CTA b works on a tile of replica
-// cta_rep[b]; each replica's tiles are a contiguous range of CTAs.
-template <typename T, int TX, int TY>
-__global__ void __launch_bounds__(TX* TY)
-    k_fused_curl_batch(const RepDesc* __restrict__ desc, const int* __restrict__ cta_rep,
-                       int par) {
-  const RepDesc& r = desc[cta_rep[blockIdx.x]];
-  const int local = blockIdx.x - r.f_first;
-  const int per_z = r.f_tx * r.f_ty;
-  const int tz = local / per_z, rem = local - tz * per_z;
-  const int ty = rem / r.f_tx, tx = rem - ty * r.f_tx;
-  fused_tile<T, TX, TY>(r.m, (const T*)r.D[par], (const T*)r.B[par], (const T*)r.ie,
-                        (T*)r.D[par ^ 1], (T*)r.B[par ^ 1], (T)r.sp.coefB, (T)r.sp.coefD, tx,
-                        ty, tz, r.f_zchunk);
-}
 
 __device__ inline double block_sum(double x, double* sh) {
   for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xffffffffu, x, o);
