@@ -331,6 +331,8 @@ __global__ void __launch_bounds__(34 * (TY + 2))
                        zchunk, threadIdx.x, threadIdx.y, true, CtaSync{});
 }
 
+// Many independent systems in one launch: CTA b works on a site tile of
+// replica cta_rep[b]; each replica's tiles are a contiguous range of CTAs.
 template <typename T, int TY, int PF, int TX>
 __global__ void __launch_bounds__((TX + 2) * (TY + 2))
     k_fused_site_batch(const RepDesc* __restrict__ desc, const int* __restrict__ cta_rep, int par) {
