@@ -262,7 +262,8 @@ memd_status memd_io_buffers(memd_ctx *ctx, memd_io *io);
  * load != 0 takes positions, image counters and velocities from them (as
  * memd_set_particles), then nsteps steps, then the buffers receive the state
  * and the forces.  One host-to-device copy, one device-to-host copy, one
- * synchronisation.  Errors as memd_step_host. */
+ * synchronisation; with load and one step the whole round trip is replayed
+ * as one CUDA graph.  Errors as memd_step_host. */
 memd_status memd_step_io(memd_ctx *ctx, int32_t load, int64_t nsteps,
                          const memd_thermostat *th);
 

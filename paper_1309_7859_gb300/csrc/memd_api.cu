@@ -165,11 +165,16 @@ void harvest_timing(memd_ctx* c) {
 }
 
 void drop_graphs(memd_ctx* c) {
-  for (int t = 0; t < 2; ++t)
+  for (int t = 0; t < 2; ++t) {
     if (c->graph[t]) {
       cudaGraphExecDestroy(c->graph[t]);
       c->graph[t] = nullptr;
     }
+    if (c->io_graph[t]) {
+      cudaGraphExecDestroy(c->io_graph[t]);
+      c->io_graph[t] = nullptr;
+    }
+  }
 }
 
 double* scal(memd_ctx* c) { return c->red + 4 * reduce_blocks(); }
@@ -1115,16 +1120,14 @@ static memd_status poll_err(memd_ctx* c, bool block) {
   return MEMD_OK;
 }
 
-memd_status memd_step(memd_ctx* c, int64_t nsteps, const memd_thermostat* th) {
-  memd::NvtxRange nvtx_("memd_step");
-  if (!c) return MEMD_ERR_INVALID;
-  if (!c->initialised) return fail(c, MEMD_ERR_STATE, "memd_init_field first");
-  if (nsteps < 0) return fail(c, MEMD_ERR_INVALID, "negative step count");
-  CK(cudaSetDevice(c->device));
+// what every step needs before it is launched: the per-particle constants
+// of this thermostat, the engine (decided when the step graphs are built),
+// the second transfer buffer of the single launch, applied transfers for the
+// graph engine, the tuned field kernel
+static memd_status step_prepare(memd_ctx* c, const memd_thermostat* th, StepParams& sp) {
   const int thermo = th ? 1 : 0;
   const double gamma = th ? th->gamma : 0.0, kT = th ? th->kT : 0.0;
-  const StepParams sp = step_params(c, thermo, gamma, kT);
-  const bool timed = c->time_kernels != 0;
+  sp = step_params(c, thermo, gamma, kT);
   if (c->graph_thermo != thermo || c->graph_gamma != gamma || c->graph_kT != kT || !c->sig_ready) {
     drop_graphs(c);
     // per-particle Langevin amplitude for this thermostat (same expression as per step)
@@ -1149,6 +1152,23 @@ memd_status memd_step(memd_ctx* c, int64_t nsteps, const memd_thermostat* th) {
     if (e != MEMD_OK) return e;
     c->fcfg_ready = true;
   }
+  return MEMD_OK;
+}
+
+memd_status memd_step(memd_ctx* c, int64_t nsteps, const memd_thermostat* th) {
+  memd::NvtxRange nvtx_("memd_step");
+  if (!c) return MEMD_ERR_INVALID;
+  if (!c->initialised) return fail(c, MEMD_ERR_STATE, "memd_init_field first");
+  if (nsteps < 0) return fail(c, MEMD_ERR_INVALID, "negative step count");
+  CK(cudaSetDevice(c->device));
+  const int thermo = th ? 1 : 0;
+  const double gamma = th ? th->gamma : 0.0, kT = th ? th->kT : 0.0;
+  StepParams sp;
+  {
+    const memd_status e = step_prepare(c, th, sp);
+    if (e != MEMD_OK) return e;
+  }
+  const bool timed = c->time_kernels != 0;
   auto record = [&](int par) {
     return c->coop ? record_step_coop(c, sp, par, timed) : record_step(c, sp, par, timed);
   };
@@ -1370,6 +1390,7 @@ memd_status memd_step_host(memd_ctx* c, const double* pos_in, const double* vel_
 // its device mirror), allocated on first use and after a particle count change
 static memd_status io_block(memd_ctx* c) {
   if (c->io_n == c->P.n && c->io_host && c->io_dev) return MEMD_OK;
+  drop_graphs(c);  // the round-trip graphs hold the old block's addresses
   if (c->io_host) cudaFreeHost(c->io_host);
   dfree(c, c->io_dev);
   c->io_host = nullptr;
@@ -1412,6 +1433,45 @@ memd_status memd_step_io(memd_ctx* c, int32_t load, int64_t nsteps, const memd_t
   if (s != MEMD_OK) return s;
   const IoLayout L = io_layout(c->P.n);
   const cudaStream_t st = c->stream;
+  if (load && nsteps == 1 && c->P.n > 0 && c->use_graphs && c->io_graph_ok) {
+    // the usual host loop: one graph launch a call
+    StepParams sp;
+    s = step_prepare(c, th, sp);
+    if (s != MEMD_OK) return s;
+    if (!c->coop || c->coop_graph_ok) {
+      const bool timed = c->time_kernels != 0;
+      const int par = c->cur;
+      harvest_timing(c);
+      if (!c->io_graph[par]) {
+        cudaGraph_t g = nullptr;
+        CK(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
+        cudaMemcpyAsync(c->io_dev, c->io_host, (size_t)L.f, cudaMemcpyHostToDevice, st);
+        launch_io_unpack(c->mesh, c->P, c->io_dev, &c->ds->err, st);
+        const memd_status r = c->coop ? record_step_coop(c, sp, par, timed)
+                                      : record_step(c, sp, par, timed);
+        launch_io_pack(c->P, c->io_dev, &c->ds->err, st);
+        cudaMemcpyAsync(c->io_host, c->io_dev, (size_t)L.bytes, cudaMemcpyDeviceToHost, st);
+        const cudaError_t e = cudaStreamEndCapture(st, &g);
+        cudaError_t ie = cudaErrorUnknown;
+        if (r == MEMD_OK && e == cudaSuccess) ie = cudaGraphInstantiate(&c->io_graph[par], g, 0);
+        if (g) cudaGraphDestroy(g);
+        if (ie != cudaSuccess) {  // not capturable here: copies and step one by one
+          cudaGetLastError();
+          c->io_graph[par] = nullptr;
+          c->io_graph_ok = false;
+        }
+      }
+      if (c->io_graph[par]) {
+        CK(cudaGraphLaunch(c->io_graph[par], st));
+        c->timing_pending = timed;
+        c->cur = par ^ 1;
+        if (c->coop) c->pending = true;
+        CK(cudaStreamSynchronize(st));
+        if (*(const unsigned int*)(c->io_host + L.err)) return check_err(c);
+        return MEMD_OK;
+      }
+    }
+  }
   if (load && c->P.n > 0) {
     // positions, velocities and image counters: the first 60 n bytes
     CK(cudaMemcpyAsync(c->io_dev, c->io_host, (size_t)L.f, cudaMemcpyHostToDevice, st));

@@ -66,6 +66,10 @@ struct memd_ctx {
   int rows_nt = 0;       // a permittivity is mapped (memd_set_eps restores it on failure)
   // step graphs, one per buffer parity
   cudaGraphExec_t graph[2] = {nullptr, nullptr};
+  // memd_step_io's whole round trip (copy in, unpack, step, pack, copy out)
+  // as one graph per buffer parity; io_graph_ok false once capture failed
+  cudaGraphExec_t io_graph[2] = {nullptr, nullptr};
+  bool io_graph_ok = true;
   int step_engine = 0;   // MEMD_STEP_*
   int coop_grid = 0;     // CTAs of the single-launch step (0: unsupported)
   bool coop = false;     // the steps run as one cooperative launch
