@@ -375,6 +375,11 @@ memd_status memd_batch_synchronize(memd_batch *b);
  * timing resets it. */
 memd_status memd_batch_kernel_stats(memd_batch *b, memd_kernel_stats *out);
 
+/* Time the batched field update with CUDA events inside the step graph (on != 0)
+ * or not; by default the batch times it when its first member was created with
+ * time_kernels.  The step graphs are rebuilt at the next step. */
+memd_status memd_batch_set_timing(memd_batch *b, int32_t on);
+
 /* Release the batch's own tables (members are untouched; destroy the batch
  * before any of its members). */
 void memd_batch_destroy(memd_batch *b);

@@ -42,6 +42,7 @@ struct memd_batch {
   int* d_seg_first = nullptr;
   int n_rows_ctas = 0;
   cudaGraphExec_t graph[2] = {nullptr, nullptr};
+  int timing = -1;  // -1: time the field update when member 0 does; 0 / 1: off / on
   int g_thermo = -1;
   double g_gamma = 0.0, g_kT = 0.0;
   bool timing_pending = false;
@@ -451,7 +452,7 @@ memd_status memd_batch_step(memd_batch* b, int64_t nsteps, const memd_thermostat
     b->g_gamma = gamma;
     b->g_kT = kT;
   }
-  const bool timed = b->m[0]->time_kernels != 0;
+  const bool timed = b->timing >= 0 ? b->timing != 0 : b->m[0]->time_kernels != 0;
   for (int64_t s = 0; s < nsteps; ++s) {
     const int par = b->bpar;
     harvest(b);
@@ -481,6 +482,19 @@ memd_status memd_batch_synchronize(memd_batch* b) {
   for (memd_ctx* c : b->m) {
     const memd_status s = memd_check_err(c);
     if (s != MEMD_OK) return bfail(b, s, c->last_error);
+  }
+  return MEMD_OK;
+}
+
+memd_status memd_batch_set_timing(memd_batch* b, int32_t on) {
+  if (!b) return MEMD_ERR_INVALID;
+  BCK(cudaSetDevice(b->device));
+  harvest(b);
+  const int t = on ? 1 : 0;
+  if (t != b->timing) {
+    BCK(cudaStreamSynchronize(b->stream));
+    drop(b);  // the step graphs hold (or lack) the timing events
+    b->timing = t;
   }
   return MEMD_OK;
 }

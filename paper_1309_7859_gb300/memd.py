@@ -34,7 +34,8 @@ EXPORTS = ("memd_default_options", "memd_status_string", "memd_last_error", "mem
            "memd_get_kernel_stats", "memd_reset_kernel_stats", "memd_synchronize",
            "memd_batch_create", "memd_batch_create_kernel", "memd_batch_step",
            "memd_batch_synchronize",
-           "memd_batch_kernel_stats", "memd_batch_destroy", "memd_server_default_options",
+           "memd_batch_kernel_stats", "memd_batch_set_timing", "memd_batch_destroy",
+           "memd_server_default_options",
            "memd_server_create", "memd_server_destroy", "memd_server_submit", "memd_server_pump",
            "memd_server_status", "memd_server_result", "memd_server_release",
            "memd_server_used_bytes", "memd_server_get_stats", "memd_server_last_error",
@@ -177,6 +178,7 @@ def lib(build_if_missing=True):
     L.memd_batch_step.argtypes = [vp, C.c_int64, C.POINTER(Thermostat)]
     L.memd_batch_synchronize.argtypes = [vp]
     L.memd_batch_kernel_stats.argtypes = [vp, C.POINTER(KernelStats)]
+    L.memd_batch_set_timing.argtypes = [vp, C.c_int32]
     L.memd_batch_destroy.argtypes = [vp]
     L.memd_server_default_options.argtypes = [C.POINTER(ServerOptions)]
     L.memd_server_create.argtypes = [C.POINTER(ServerOptions), C.POINTER(vp)]
@@ -542,6 +544,12 @@ class Batch:
         st = self._L.memd_batch_synchronize(self._h)
         if st != 0:
             raise MemdError(st, "memd_batch_synchronize failed")
+
+    def set_timing(self, on):
+        """CUDA events around the batched field update in the step graph."""
+        st = self._L.memd_batch_set_timing(self._h, 1 if on else 0)
+        if st != 0:
+            raise MemdError(st, "memd_batch_set_timing failed")
 
     def kernel_stats(self):
         k = KernelStats()
