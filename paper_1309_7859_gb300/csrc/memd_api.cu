@@ -131,7 +131,7 @@ memd_status memd_check_err(memd_ctx* c) {
   if (err) {
     CK(cudaMemsetAsync(&c->ds->err, 0, sizeof(unsigned int), c->stream));
     if (err & kErrTimeout)  // a grid barrier gave up: start its words afresh
-      CK(cudaMemsetAsync(&c->ds->bar_count, 0, 2 * sizeof(unsigned int), c->stream));
+      CK(cudaMemsetAsync(&c->ds->bar_arrivals, 0, sizeof(unsigned long long), c->stream));
     CK(cudaStreamSynchronize(c->stream));
     if (err & kErrCellJump) return fail(c, MEMD_ERR_CELL_JUMP, "a charge moved more than one cell");
     if (err & kErrGauss) return fail(c, MEMD_ERR_GAUSS, "Gauss scan did not close (system not neutral)");

@@ -53,8 +53,8 @@ struct DevState {
   long long step;              // steps since init (Langevin counter)
   unsigned int err;            // kErr* bits
   unsigned int ticket;         // blocks of the gather that have finished
-  unsigned int bar_count;      // grid barrier of the single-launch step: arrivals
-  unsigned int bar_gen;        // and its generation
+  unsigned long long bar_arrivals;  // grid barrier of the single-launch step: CTA arrivals
+                                    // since init (grows by the grid size a barrier)
   long long lsum[3];           // scratch: sum of the ledger per component
   double scal[16];             // scratch scalars for the relaxation
 };

@@ -792,33 +792,36 @@ __global__ void __launch_bounds__(kBatchQuadThreads)
 // CTA closes the step.  The values are those of the four launches of the
 // graph step, bit for bit.
 
-// Grid-wide barrier of a cooperative launch: each CTA releases its writes
-// with its arrival, the last CTA to arrive acquires them all and opens the
-// next generation with a release store; the others poll that word with
-// relaxed loads and acquire once it has changed.  The wait is bounded by the
-// global timer (0.2 s); a wait that runs out sets kErrTimeout and goes on,
-// the step is then void and the host resets the barrier words when it
+// Grid-wide barrier of a cooperative launch over a monotonic 64-bit count
+// of CTA arrivals: each CTA adds one with release and acquire semantics and
+// learns its arrival number a; its barrier is complete when the count
+// reaches the next multiple of the grid size (the count starts at 0 and
+// grows by exactly the grid size a barrier).  The last CTA to arrive knows
+// it from a alone and goes on; the others poll the count with relaxed loads
+// and acquire once it is reached.  The arrivals are read-modify-writes of one
+// word, so they form one release sequence: the last arrival, and a poll that
+// reads the completed count, acquire every CTA's earlier writes.  The wait is bounded
+// by the global timer (0.2 s); a wait that runs out sets kErrTimeout and
+// goes on, the step is then void and the host resets the count when it
 // reports the error.
 __device__ inline void grid_barrier(DevState* ds, unsigned nctas) {
   __syncthreads();
   if (threadIdx.x == 0) {
-    unsigned gen, arrived;
-    asm volatile("ld.relaxed.gpu.global.u32 %0, [%1];" : "=r"(gen) : "l"(&ds->bar_gen) : "memory");
-    asm volatile("atom.acq_rel.gpu.global.add.u32 %0, [%1], 1;"
-                 : "=r"(arrived)
-                 : "l"(&ds->bar_count)
+    unsigned long long a;
+    asm volatile("atom.acq_rel.gpu.global.add.u64 %0, [%1], 1;"
+                 : "=l"(a)
+                 : "l"(&ds->bar_arrivals)
                  : "memory");
-    if (arrived == nctas - 1) {
-      asm volatile("st.relaxed.gpu.global.u32 [%0], %1;" ::"l"(&ds->bar_count), "r"(0u) : "memory");
-      asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(&ds->bar_gen), "r"(gen + 1u)
-                   : "memory");
-    } else {
-      unsigned long long t0, t;
+    const unsigned long long target = a - a % nctas + nctas;
+    if (a + 1 != target) {
+      unsigned long long t0, t, cur;
       asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t0));
-      unsigned cur = gen;
       for (unsigned it = 1;; ++it) {
-        asm volatile("ld.relaxed.gpu.global.u32 %0, [%1];" : "=r"(cur) : "l"(&ds->bar_gen) : "memory");
-        if (cur != gen) break;
+        asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];"
+                     : "=l"(cur)
+                     : "l"(&ds->bar_arrivals)
+                     : "memory");
+        if (cur >= target) break;
         if ((it & 255u) == 0u) {
           asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
           if (t - t0 > 200000000ull) {
