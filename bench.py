@@ -619,7 +619,7 @@ def main():
     ap.add_argument("--step-engine", default="auto", choices=["auto", "graph", "single"])
     ap.add_argument("--batch", type=int, default=64,
                     help="replicas of the extra batched measurement (0: skip)")
-    ap.add_argument("--serve", type=int, default=128,
+    ap.add_argument("--serve", type=int, default=512,
                     help="requests of the extra served-stream measurement (0: skip)")
     ap.add_argument("--serve-rate", type=float, default=40.0)
     ap.add_argument("--serve-budget", type=int, default=8, help="GiB")
