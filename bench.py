@@ -319,6 +319,8 @@ def run_memd(args, world, rank, local):
     g.close()
     if rank == 0 and out is not None and args.large > 0:
         out["large_mesh"] = large_mesh(args.large, dev, stream, args)
+    if rank == 0 and out is not None and args.salt:
+        out["salt"] = stepped_systems(("salt-64",), dev, stream, args)["salt-64"]
     if rank == 0 and out is not None and args.validation:
         out["validation"] = validation_systems(dev, stream, args)
     if rank == 0 and out is not None and args.batch > 0:
@@ -554,13 +556,20 @@ def large_mesh(N, dev, stream, args):
 def validation_systems(dev, stream, args):
     """The paper's validation systems as synthetic workloads (our own
     parameters): the dielectric colloid in salt water and the cloud-wall
-    system.  Each is stepped as the default line is (L2 flushed before every
-    step, CUDA events on the library's stream)."""
+    system."""
+    return stepped_systems(("colloid-64", "cloud-wall-32"), dev, stream, args)
+
+
+def stepped_systems(names, dev, stream, args):
+    """Single systems beside the default line, each stepped as that line is
+    (L2 flushed before every step, CUDA events on the library's stream), up
+    to 2000 steps; field-kernel duration from an instrumented context when
+    the step is not one launch."""
     import torch
     from paper_1309_7859_gb300.memd import Memd
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
     out = {}
-    for name in ("colloid-64", "cloud-wall-32"):
+    for name in names:
         sysc = workload(name)
         g = Memd(sysc.mesh, sysc.box, sysc.eps, c_light=sysc.c_light, dt=sysc.dt,
                  precision=sysc.precision, seed=sysc.seed, time_kernels=False, stream=stream,
@@ -589,7 +598,7 @@ def validation_systems(dev, stream, args):
         ach = ks.field_bytes / (per * 1e-3) / 1e9
         e = g.energy()
         x1 = g.particles()[0]
-        nh = sysc.extra["heavy"]
+        nh = sysc.extra.get("heavy", 0)
         drift = float(np.max(np.abs(x1[:nh] - x0[:nh]))) if nh else 0.0
         g.close()
         out[name] = {"workload": sysc.name, "steps": steps, "ms_per_step": ms / steps,
@@ -600,7 +609,7 @@ def validation_systems(dev, stream, args):
                                   "peak": hbm, "unit": "GB/s", "frac": ach / hbm,
                                   "peak_kind": kind, "bytes_per_launch": ks.field_bytes,
                                   "ms_per_launch": per},
-                     "fixed_charges_max_move": drift,
+                     "fixed_charges_max_move": drift if nh else None,
                      "dipole": [e["P0"], e["P1"], e["P2"]],
                      "gauss_exact": bool(e["gauss_exact"])}
     return out
@@ -630,6 +639,8 @@ def main():
                     help="edge of the extra larger-than-L2 system (0: skip)")
     ap.add_argument("--batch-kernel", default="auto", choices=["auto", "site", "rows"],
                     help="field kernel of the batched replicas (auto: timed choice)")
+    ap.add_argument("--salt", type=int, default=1,
+                    help="1: also step the 64^3 salt system (32768 charges, eps from salt density)")
     ap.add_argument("--validation", type=int, default=1,
                     help="1: also step the colloid and cloud-wall systems (0: skip)")
     args = ap.parse_args()

@@ -122,6 +122,24 @@ __device__ inline void quad_dipole_add(unsigned long long* Pacc, long long val) 
   if (lane < 3 && val != 0) atomicAdd(&Pacc[lane], (unsigned long long)val);
 }
 
+// the same sum over a whole CTA (at most kQuadThreads threads, every thread
+// calls it, all adding into the same Pacc): one atomic per component and
+// CTA instead of one per warp, since the three words share one L2 line and
+// their atomics are processed one after another
+static_assert(kBatchQuadThreads <= kQuadThreads, "cta_dipole_add sizes its table for kQuadThreads");
+__device__ inline void cta_dipole_add(unsigned long long* Pacc, long long val) {
+  __shared__ long long part[kQuadThreads / 32][3];
+  for (int o = 16; o >= 4; o >>= 1) val += __shfl_down_sync(0xffffffffu, val, o);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  if (lane < 3) part[warp][lane] = val;
+  __syncthreads();
+  if (threadIdx.x < 3) {
+    long long s = 0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += part[w][threadIdx.x];
+    if (s != 0) atomicAdd(&Pacc[threadIdx.x], (unsigned long long)s);
+  }
+}
+
 // ------------------------------------------------------------ Philox4x32-10
 // Salmon, Moraes, Dror, Shaw (SC'11): ten rounds of two 32x32 -> 64-bit
 // products with a Weyl-sequence key schedule.
@@ -204,14 +222,16 @@ __device__ inline void deposit_axis(const Mesh& m, int d, int q, int c0, int f0,
 // quad exchanges the quantised coordinates, deposits one axis per lane and
 // commits the move, or leaves the particle where it was (ok == false) when
 // some axis would cross more than one cell.  Every lane of the warp must
-// call this; inactive lanes pass active = false.
+// call this; inactive lanes pass active = false.  Returns the lane's term of
+// the dipole sum (valence times the unfolded fixed-point coordinate along d;
+// 0 for lane 3 and inactive lanes), which the caller adds into Pacc.
 // pf_ie (optional, element size pf_es): 1/eps in the field precision; the
 // links of the cell the charge ends in, which the gather reads next, and the
 // charge's mass, valence and noise amplitude are then prefetched into L2.
-__device__ inline void quad_move(const Mesh& m, Particles P, int64_t p, int d, bool active,
-                                 double x, int ko, double xn, int kn, bool ok_in,
-                                 unsigned long long* __restrict__ Tb, DevState* ds,
-                                 const char* pf_ie = nullptr, int pf_es = 0) {
+__device__ inline long long quad_move(const Mesh& m, Particles P, int64_t p, int d, bool active,
+                                      double x, int ko, double xn, int kn, bool ok_in,
+                                      unsigned long long* __restrict__ Tb, DevState* ds,
+                                      const char* pf_ie = nullptr, int pf_es = 0) {
   const unsigned full = 0xffffffffu;
   const int lane = threadIdx.x & 31, base = lane & ~3;
   int c0 = 0, f0 = 0, c1 = 0, f1 = 0, dc = 0;
@@ -276,7 +296,7 @@ __device__ inline void quad_move(const Mesh& m, Particles P, int64_t p, int d, b
     }
     U *= (long long)P.q[p];
   }
-  quad_dipole_add(ds->Pacc, U);
+  return U;
 }
 
 // ------------------------------------------------------------------ kernels
@@ -340,9 +360,9 @@ __global__ void k_particle_constants(StepParams sp, Particles P) {
   if (sp.thermo) P.sig[p] = sqrt(2.0 * sp.gamma * mass * sp.kT / sp.dt);
 }
 
-// half kick with the stored force, drift, charge transfer, dipole sum;
-// g is the thread's index within its system
-__device__ __forceinline__ void deposit_body(const Mesh& m, const StepParams& sp, Particles P,
+// half kick with the stored force, drift, charge transfer; g is the
+// thread's index within its system; returns the lane's dipole term
+__device__ __forceinline__ long long deposit_body(const Mesh& m, const StepParams& sp, Particles P,
                                              unsigned long long* __restrict__ Tb, DevState* ds,
                                              int64_t g, const char* pf_ie = nullptr,
                                              int pf_es = 0) {
@@ -367,14 +387,15 @@ __device__ __forceinline__ void deposit_body(const Mesh& m, const StepParams& sp
       ok = false;
     }
   }
-  quad_move(m, P, p, d, active, x, ko, xn, kn, ok, Tb, ds, pf_ie, pf_es);
+  return quad_move(m, P, p, d, active, x, ko, xn, kn, ok, Tb, ds, pf_ie, pf_es);
 }
 
 __global__ void __launch_bounds__(kQuadThreads)
     k_kick_drift_deposit(const __grid_constant__ Mesh m, const __grid_constant__ StepParams sp,
                          Particles P, unsigned long long* __restrict__ Tb,
                          DevState* ds) {
-  deposit_body(m, sp, P, Tb, ds, blockIdx.x * (int64_t)blockDim.x + threadIdx.x);
+  cta_dipole_add(ds->Pacc,
+                 deposit_body(m, sp, P, Tb, ds, blockIdx.x * (int64_t)blockDim.x + threadIdx.x));
 }
 
 // prescribed move to (pos_new, img_new) with its charge transfer
@@ -399,7 +420,7 @@ __global__ void __launch_bounds__(kQuadThreads)
     else
       ok = false;
   }
-  quad_move(m, P, p, d, active, x, ko, xn, kn, ok, Tb, ds);
+  cta_dipole_add(ds->Pacc, quad_move(m, P, p, d, active, x, ko, xn, kn, ok, Tb, ds));
 }
 
 // Apply the step's transfers: the first lane to take a link's buffered
@@ -758,7 +779,8 @@ __global__ void __launch_bounds__(kBatchQuadThreads)
     k_deposit_batch(const RepDesc* __restrict__ desc, const int* __restrict__ cta_rep, int thermo,
                     double gamma, double kT) {
   const RepDesc& r = desc[cta_rep[blockIdx.x]];
-  deposit_body(r.m, r.sp, r.P, (unsigned long long*)r.Tb, r.ds, batch_local(r));
+  cta_dipole_add(r.ds->Pacc,
+                 deposit_body(r.m, r.sp, r.P, (unsigned long long*)r.Tb, r.ds, batch_local(r)));
 }
 
 template <typename T>
@@ -892,7 +914,8 @@ __global__ void __launch_bounds__(kCoopThreads)
     }
   } else {
     for (int64_t b = (int64_t)blockIdx.x * 32; b < nq; b += stride)
-      deposit_body(m, sp, P, Tcur, ds, b + lane, (const char*)ie, (int)sizeof(T));
+      quad_dipole_add(ds->Pacc,
+                      deposit_body(m, sp, P, Tcur, ds, b + lane, (const char*)ie, (int)sizeof(T)));
   }
   grid_barrier(ds, G);
   if (pwarp) {
