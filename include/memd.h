@@ -206,9 +206,10 @@ void memd_destroy(memd_ctx *ctx);
 
 /* Initial field solution (Sec. II, Fig. 1, Eqs. 1-3).  n particles: pos (n x 3)
  * any real positions (folded into the box), q integer valences |q| < 2^15,
- * mass (n, NULL = 1), vel (n x 3, NULL = 0).  Deposits the charges, solves
- * Gauss's law exactly in the int64 ledger, sets the k = 0 mode of D to -P/V,
- * relaxes to curl E = 0 in FP64, sets B = 0 and computes the forces.  A
+ * mass (n, positive and finite; NULL = 1), vel (n x 3, NULL = 0).  Deposits
+ * the charges, solves Gauss's law exactly in the int64 ledger, sets the k = 0
+ * mode of D to -P/V, relaxes to curl E = 0 in FP64, sets B = 0 and computes
+ * the forces.  A
  * non-neutral system gets a uniform background, which must be an integer in
  * units of e 2^-48 per vertex.  Errors: INVALID, OOM, GAUSS, RELAX_NOCONV,
  * CUDA. */
@@ -312,8 +313,10 @@ memd_status memd_set_eps(memd_ctx *ctx, const memd_eps_profile *eps, int32_t rel
  * permittivity, options and thermostat are the context's own); stepping on
  * from it gives bit for bit what the saved context would have given.
  * memd_state_bytes is the size of a saved state of ctx.  Errors: INVALID
- * (buffer too small, not a saved state, or a mesh, precision or particle
- * count mismatch; nothing changed), STATE before memd_init_field. */
+ * (buffer too small, not a saved state, a mesh, precision or particle count
+ * mismatch, or a particle array out of range: a position outside [0, L), a
+ * valence beyond +-32767, a mass not positive and finite; nothing changed),
+ * STATE before memd_init_field. */
 int64_t memd_state_bytes(const memd_ctx *ctx);
 memd_status memd_save_state(memd_ctx *ctx, void *buf, int64_t bytes);
 memd_status memd_load_state(memd_ctx *ctx, const void *buf, int64_t bytes);

@@ -932,6 +932,11 @@ memd_status memd_init_field(memd_ctx* c, int64_t n, const double* pos, const int
     if (q[p] > 32767 || q[p] < -32767) return fail(c, MEMD_ERR_INVALID, "valence out of range");
     qtot += q[p];
   }
+  // the half kick divides by the mass
+  if (mass)
+    for (int64_t p = 0; p < n; ++p)
+      if (!(mass[p] > 0.0) || !std::isfinite(mass[p]))
+        return fail(c, MEMD_ERR_INVALID, "mass not positive and finite");
   // a non-neutral system gets a uniform background, exact in units e 2^-48
   const __int128 tot = (__int128)qtot * ((__int128)1 << 48);
   if (tot % m.V != 0)
@@ -1644,6 +1649,30 @@ memd_status memd_load_state(memd_ctx* c, const void* buf, int64_t bytes) {
       h.box[1] != c->mesh.L[1] || h.box[2] != c->mesh.L[2])
     return fail(c, MEMD_ERR_INVALID, "saved state of another mesh, precision or particle count");
   if (bytes < memd_state_bytes(c)) return fail(c, MEMD_ERR_INVALID, "state buffer too small");
+  {
+    // the particle arrays are checked before anything is copied: a saved
+    // state holds folded positions (the deposition indexes cells by them),
+    // valences in range and positive masses
+    const size_t V3 = 3 * (size_t)c->mesh.V, n = (size_t)c->P.n;
+    const char* base = (const char*)buf + sizeof(StateHeader) + V3 * (2 * memd_esz(c) + 8);
+    // x, v, F, Ft (3n doubles each), img (3n int32), q (n int32), m (n doubles)
+    const char* x = base;
+    const char* q = base + 3 * n * 8 * 4 + 3 * n * 4;
+    const char* ms = q + n * 4;
+    for (size_t i = 0; i < n; ++i) {
+      double xi[3], mi;
+      int32_t qi;
+      std::memcpy(xi, x + 24 * i, sizeof(xi));  // the caller's buffer may be unaligned
+      std::memcpy(&qi, q + 4 * i, sizeof(qi));
+      std::memcpy(&mi, ms + 8 * i, sizeof(mi));
+      for (int d = 0; d < 3; ++d)
+        if (!(xi[d] >= 0.0 && xi[d] < c->mesh.L[d]))
+          return fail(c, MEMD_ERR_INVALID, "saved position outside the box");
+      if (qi > 32767 || qi < -32767) return fail(c, MEMD_ERR_INVALID, "saved valence out of range");
+      if (!(mi > 0.0) || !std::isfinite(mi))
+        return fail(c, MEMD_ERR_INVALID, "saved mass not positive and finite");
+    }
+  }
   CK(cudaSetDevice(c->device));
   const cudaStream_t st = c->stream;
   drop_graphs(c);

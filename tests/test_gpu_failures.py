@@ -77,6 +77,12 @@ def test_invalid_inputs_are_refused():
     with pytest.raises(MemdError) as err:
         g.init_field(x, sysc.q, sysc.m, sysc.v)
     assert err.value.status == 1             # non-finite position
+    for bad in (0.0, -1.0, np.inf, np.nan):  # the half kick divides by the mass
+        m = sysc.m.copy()
+        m[2] = bad
+        with pytest.raises(MemdError) as err:
+            g.init_field(sysc.x, sysc.q, m, sysc.v)
+        assert err.value.status == 1
     q = sysc.q.copy()
     q[0] += 1                                # one unit of charge over 960 vertices
     with pytest.raises(MemdError) as err:

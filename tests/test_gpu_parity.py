@@ -468,3 +468,41 @@ def test_resume_from_a_saved_state_is_bit_identical(engine, precision):
     with pytest.raises(MemdError):
         c.load_state(saved)
     assert np.array_equal(c.particles()[0], before)
+
+
+@pytest.mark.parametrize("field", ["x_outside", "x_nan", "mass_zero", "valence"])
+def test_corrupted_saved_state_is_refused(field):
+    # a saved state ends with the particle arrays x, v, F, Ft (3n doubles
+    # each), img (3n int32), q (n int32), m (n doubles); one corrupted entry
+    # is refused before anything is copied
+    from paper_1309_7859_gb300.memd import Memd, MemdError
+    sysc = small_system((16, 12, 10), 40, SLAB, precision="fp32", dt=0.005)
+    a = Memd(sysc.mesh, sysc.box, sysc.eps, c_light=sysc.c_light, dt=sysc.dt, precision="fp32",
+             seed=sysc.seed)
+    a.init_field(sysc.x, sysc.q, sysc.m, sysc.v)
+    a.step(3, thermostat=(1.0, 1.0))
+    saved = a.save_state()
+    n, size = 40, saved.size
+    bad = saved.copy()
+    x = bad[size - 120 * n: size - 96 * n].view(np.float64)
+    q = bad[size - 12 * n: size - 8 * n].view(np.int32)
+    m = bad[size - 8 * n:].view(np.float64)
+    assert np.array_equal(x.reshape(n, 3), a.particles()[0])   # the layout read above
+    if field == "x_outside":
+        x[7] = sysc.box[1] + 0.25
+    elif field == "x_nan":
+        x[11] = np.nan
+    elif field == "mass_zero":
+        m[5] = 0.0
+    else:
+        q[3] = 40000
+    before = [u.copy() for u in a.fields()] + [u.copy() for u in a.particles()]
+    with pytest.raises(MemdError) as err:
+        a.load_state(bad)
+    assert err.value.status == 1                                 # MEMD_ERR_INVALID
+    after = list(a.fields()) + list(a.particles())
+    for u, w in zip(before, after):
+        assert np.array_equal(u, w)
+    a.load_state(saved)                                          # the intact state loads
+    a.step(2, thermostat=(1.0, 1.0))
+    assert a.energy()["gauss_exact"] == 1.0
