@@ -222,7 +222,8 @@ def run_memd(args, world, rank, local):
     # step graph (each event node adds a few microseconds to a step)
     g = Memd(sysc.mesh, sysc.box, sysc.eps, c_light=sysc.c_light, dt=sysc.dt,
              precision=sysc.precision, seed=sysc.seed, time_kernels=False, stream=stream,
-             field_kernel=args.field_kernel, step_engine=args.step_engine)
+             field_kernel=args.field_kernel, step_engine=args.step_engine,
+             apply_mode=args.apply)
     g.init_field(sysc.x, sysc.q, sysc.m, sysc.v)
     th = sysc.thermostat
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
@@ -340,7 +341,8 @@ def field_kernel_ms(sysc, args, dev, stream, flush, steps=None):
     from paper_1309_7859_gb300.memd import Memd
     g = Memd(sysc.mesh, sysc.box, sysc.eps, c_light=sysc.c_light, dt=sysc.dt,
              precision=sysc.precision, seed=sysc.seed, time_kernels=True, stream=stream,
-             field_kernel=args.field_kernel, step_engine=args.step_engine)
+             field_kernel=args.field_kernel, step_engine=args.step_engine,
+             apply_mode=args.apply)
     g.init_field(sysc.x, sysc.q, sysc.m, sysc.v)
     th = sysc.thermostat
     steps = steps or max(10, min(args.steps, 500))
@@ -463,7 +465,8 @@ def batched(count, dev, args):
     members = []
     for i, s in enumerate(systems):
         g = Memd(s.mesh, s.box, s.eps, c_light=s.c_light, dt=s.dt, precision=s.precision,
-                 seed=s.seed, stream=stream, time_kernels=False, field_kernel="ldg")
+                 seed=s.seed, stream=stream, time_kernels=False, field_kernel="ldg",
+                 apply_mode=args.apply)
         g.init_field(s.x, s.q, s.m, s.v)
         members.append(g)
     setup_s = time.perf_counter() - t0
@@ -521,7 +524,8 @@ def large_mesh(N, dev, stream, args):
     sysc = workload(f"bigslab-{N}")
     g = Memd(sysc.mesh, sysc.box, sysc.eps, c_light=sysc.c_light, dt=sysc.dt,
              precision=sysc.precision, seed=sysc.seed, time_kernels=False, stream=stream,
-             field_kernel=args.field_kernel, step_engine=args.step_engine)
+             field_kernel=args.field_kernel, step_engine=args.step_engine,
+             apply_mode=args.apply)
     g.init_field(sysc.x, sysc.q, sysc.m, sysc.v)
     th = sysc.thermostat
     steps = max(10, min(args.steps, 50))
@@ -573,7 +577,8 @@ def stepped_systems(names, dev, stream, args):
         sysc = workload(name)
         g = Memd(sysc.mesh, sysc.box, sysc.eps, c_light=sysc.c_light, dt=sysc.dt,
                  precision=sysc.precision, seed=sysc.seed, time_kernels=False, stream=stream,
-                 field_kernel=args.field_kernel, step_engine=args.step_engine)
+                 field_kernel=args.field_kernel, step_engine=args.step_engine,
+                 apply_mode=args.apply)
         g.init_field(sysc.x, sysc.q, sysc.m, sysc.v)
         th = sysc.thermostat
         steps = max(10, min(args.steps, 2000))
@@ -626,6 +631,8 @@ def main():
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
     ap.add_argument("--field-kernel", default="auto", choices=["auto", "ldg", "tma", "site"])
     ap.add_argument("--step-engine", default="auto", choices=["auto", "graph", "single"])
+    ap.add_argument("--apply", default="auto", choices=["auto", "sparse", "dense"],
+                    help="how graph steps and batches apply the charge transfers")
     ap.add_argument("--batch", type=int, default=64,
                     help="replicas of the extra batched measurement (0: skip)")
     ap.add_argument("--serve", type=int, default=512,

@@ -137,12 +137,21 @@ typedef struct memd_options {
                              that reads or replaces the state applies them first);
                              when the device has no cooperative launches, the graph.
                              Both give identical results. */
-  int32_t reserved[5];
+  int32_t apply_mode;     /* how the graph step and batches apply a step's charge
+                             transfers to D and the ledger: MEMD_APPLY_AUTO is the
+                             sparse form (faster on the systems measured so far);
+                             MEMD_APPLY_SPARSE: each charge's
+                             quad takes its crossed links' transfers by atomic
+                             exchange; MEMD_APPLY_DENSE: one pass over every link's
+                             transfer word.  Both add each word once, so they give
+                             identical results. */
+  int32_t reserved[4];
 } memd_options;
 
 enum { MEMD_FIELD_AUTO = 0, MEMD_FIELD_LDG = 1, MEMD_FIELD_TMA = 2, MEMD_FIELD_SITE = 3,
        MEMD_FIELD_ROWS = 4 };
 enum { MEMD_STEP_AUTO = 0, MEMD_STEP_GRAPH = 1, MEMD_STEP_SINGLE = 2 };
+enum { MEMD_APPLY_AUTO = 0, MEMD_APPLY_SPARSE = 1, MEMD_APPLY_DENSE = 2 };
 
 typedef struct memd_thermostat {
   double gamma; /* friction rate; Langevin force -gamma m v + sqrt(2 gamma m kT / dt) xi */

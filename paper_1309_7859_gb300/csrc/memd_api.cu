@@ -783,6 +783,7 @@ memd_status memd_create(const int32_t mesh[3], const double box[3], const memd_e
   if (o.self_mode < 0 || o.self_mode > 2) return MEMD_ERR_INVALID;
   if (o.field_kernel < MEMD_FIELD_AUTO || o.field_kernel > MEMD_FIELD_ROWS) return MEMD_ERR_INVALID;
   if (o.step_engine < MEMD_STEP_AUTO || o.step_engine > MEMD_STEP_SINGLE) return MEMD_ERR_INVALID;
+  if (o.apply_mode < MEMD_APPLY_AUTO || o.apply_mode > MEMD_APPLY_DENSE) return MEMD_ERR_INVALID;
   if (!eps_valid(eps, box, a)) return MEMD_ERR_INVALID;
 
   memd_ctx* c = new memd_ctx();
@@ -821,6 +822,7 @@ memd_status memd_create(const int32_t mesh[3], const double box[3], const memd_e
   c->time_kernels = o.time_kernels;
   c->field_kernel = o.field_kernel;
   c->step_engine = o.step_engine;
+  c->apply_mode = o.apply_mode;
   c->alloc = o.alloc;
   c->free_fn = o.free;
   c->alloc_user = o.alloc_user;
@@ -1070,7 +1072,10 @@ static memd_status record_step(memd_ctx* c, const StepParams& sp, int par, bool 
     launch_kick_drift_deposit(m, sp, c->P, c->Tb, c->ds, st);
   else
     CK(cudaStreamWaitEvent(st, c->join, 0));
-  launch_apply(m, c->prec, c->P, c->Tb, c->Lg, c->Dbuf[par ^ 1], sp.scale, st);
+  if (apply_dense(c->apply_mode, m.V, c->P.n))
+    launch_apply_dense(c->prec, 3 * m.V, c->Tb, c->Lg, c->Dbuf[par ^ 1], sp.scale, st);
+  else
+    launch_apply(m, c->prec, c->P, c->Tb, c->Lg, c->Dbuf[par ^ 1], sp.scale, st);
   launch_gather(m, c->prec, sp, c->P, c->Dbuf[par ^ 1], c->ie, c->ie64, c->ds, 1, 2, st);
   CKL();
   return MEMD_OK;

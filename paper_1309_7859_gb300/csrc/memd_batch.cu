@@ -41,6 +41,12 @@ struct memd_batch {
   RowSeg* d_segs = nullptr;
   int* d_seg_first = nullptr;
   int n_rows_ctas = 0;
+  // transfer application: dense pass over (replica, chunk) pairs, or the
+  // sparse per-charge form (MEMD_APPLY_* of member 0, AUTO decided on the
+  // batch's totals)
+  bool apply_dense = false;
+  int2* d_apply_chunk = nullptr;
+  int n_apply_chunk = 0;
   cudaGraphExec_t graph[2] = {nullptr, nullptr};
   int timing = -1;  // -1: time the field update when member 0 does; 0 / 1: off / on
   int g_thermo = -1;
@@ -105,6 +111,8 @@ void free_tables(memd_batch* b) {
   b->d_segs = nullptr;
   b->d_seg_first = nullptr;
   b->n_rows_ctas = 0;
+  b->d_apply_chunk = nullptr;
+  b->n_apply_chunk = 0;
 }
 
 // Work of the row kernel: every replica's planes cut into full-width tiles
@@ -122,6 +130,8 @@ memd_status build_tables(memd_batch* b) {
   const int R = (int)b->m.size();
   std::vector<RepDesc> desc(R);
   std::vector<int> frep, prep;
+  std::vector<int2> achunk;
+  int64_t Vsum = 0, nsum = 0;
   b->field_bytes = 0.0;
   for (int r = 0; r < R; ++r) {
     memd_ctx* c = b->m[r];
@@ -153,6 +163,10 @@ memd_status build_tables(memd_batch* b) {
     d.p_first = (int)prep.size();
     d.p_ctas = (int)std::max<int64_t>(1, (4 * c->P.n + kBatchQuadThreads - 1) / kBatchQuadThreads);
     for (int t = 0; t < d.p_ctas; ++t) prep.push_back(r);
+    const int64_t nch = (3 * c->mesh.V + kApplyChunk - 1) / kApplyChunk;
+    for (int64_t k = 0; k < nch; ++k) achunk.push_back(make_int2(r, (int)k));
+    Vsum += c->mesh.V;
+    nsum += c->P.n;
     b->base[r] = c->cur;
     b->gen[r] = c->gen;
     b->field_bytes += 15.0 * (double)memd_esz(c) * (double)c->mesh.V;
@@ -171,6 +185,14 @@ memd_status build_tables(memd_batch* b) {
                       cudaMemcpyHostToDevice, b->stream));
   BCK(cudaMemcpyAsync(b->d_part_rep, prep.data(), sizeof(int) * b->n_part,
                       cudaMemcpyHostToDevice, b->stream));
+  b->apply_dense = apply_dense(b->m[0]->apply_mode, Vsum, nsum);
+  if (b->apply_dense) {
+    b->n_apply_chunk = (int)achunk.size();
+    b->d_apply_chunk = (int2*)balloc(b, sizeof(int2) * std::max(1, b->n_apply_chunk));
+    if (!b->d_apply_chunk) return bfail(b, MEMD_ERR_OOM, "batch apply table");
+    BCK(cudaMemcpyAsync(b->d_apply_chunk, achunk.data(), sizeof(int2) * b->n_apply_chunk,
+                        cudaMemcpyHostToDevice, b->stream));
+  }
   if (b->f_rows > 0) {
     int sms = 0;
     BCK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, b->device));
@@ -328,7 +350,10 @@ memd_status record(memd_batch* b, int par, int thermo, double gamma, double kT, 
     launch_deposit_batch(b->d_desc, b->d_part_rep, b->n_part, thermo, gamma, kT, st);
   else
     BCK(cudaStreamWaitEvent(st, b->join, 0));
-  launch_apply_batch(b->prec, b->d_desc, b->d_part_rep, b->n_part, par, st);
+  if (b->apply_dense)
+    launch_apply_dense_batch(b->prec, b->d_desc, b->d_apply_chunk, b->n_apply_chunk, par, st);
+  else
+    launch_apply_batch(b->prec, b->d_desc, b->d_part_rep, b->n_part, par, st);
   launch_gather_batch(b->prec, b->d_desc, b->d_part_rep, b->n_part, par, thermo, gamma, kT, st);
   BCK(cudaGetLastError());
   return MEMD_OK;

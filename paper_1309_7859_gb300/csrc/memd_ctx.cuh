@@ -71,6 +71,7 @@ struct memd_ctx {
   cudaGraphExec_t io_graph[2] = {nullptr, nullptr};
   bool io_graph_ok = true;
   int step_engine = 0;   // MEMD_STEP_*
+  int apply_mode = 0;    // MEMD_APPLY_*
   int coop_grid = 0;     // CTAs of the single-launch step (0: unsupported)
   bool coop = false;     // the steps run as one cooperative launch
   bool coop_graph_ok = true;  // its launch can be captured in a graph

@@ -233,6 +233,24 @@ void launch_move_deposit(const Mesh& m, Particles p, const double* pos_new,
                          const int* img_new, long long* Tb, DevState* ds, cudaStream_t st);
 void launch_apply(const Mesh& m, int prec, Particles p, long long* Tb, long long* Lg, void* D,
                   double scale, cudaStream_t st);
+// the same over every one of nlinks transfer words (one pass, no particle
+// data); identical results.  Cheaper when the mesh has few links per charge.
+void launch_apply_dense(int prec, int64_t nlinks, long long* Tb, long long* Lg, void* D,
+                        double scale, cudaStream_t st);
+// MEMD_APPLY_AUTO: dense when V < kApplyDenseSitesPerCharge n (0: never).
+// A dense pass reads 24 B a vertex and rewrites the words that carry a
+// transfer; the sparse pass costs ~0.25-0.3 ns a charge on GB300 (12 atomic
+// round trips per quad, issued together).  Measured a step: the 64^3 system
+// with 32768 charges 44.1 us dense vs 44.8 sparse (within run-to-run
+// spread); 64 replicas with 124k charges and fields larger than L2, 161.5 vs
+// 142.0 (the 71 MB of transfer words cost more than the exchanges).  AUTO
+// keeps the sparse pass.
+constexpr int64_t kApplyDenseSitesPerCharge = 0;
+inline bool apply_dense(int mode, int64_t V, int64_t n) {
+  if (mode == 2) return true;   // MEMD_APPLY_DENSE
+  if (mode == 1) return false;  // MEMD_APPLY_SPARSE
+  return V < kApplyDenseSitesPerCharge * n;
+}
 // finish: 0 nothing, 1 close the update (P of this state, clear the
 // accumulator), 2 also advance the step counter; done by the last CTA
 void launch_gather(const Mesh& m, int prec, const StepParams& sp, Particles p, const void* D,
@@ -287,6 +305,13 @@ void launch_deposit_batch(const RepDesc* desc, const int* cta_rep, int nctas, in
                           double gamma, double kT, cudaStream_t st);
 void launch_apply_batch(int prec, const RepDesc* desc, const int* cta_rep, int nctas, int par,
                         cudaStream_t st);
+// dense form: CTA b takes the kApplyChunk transfer words from chunk[b].y *
+// kApplyChunk of replica chunk[b].x
+constexpr int kApplyThreads = 256;
+constexpr int kApplyPairs = 4;  // 16-byte word pairs a thread, all loaded before any store
+constexpr int64_t kApplyChunk = 2 * kApplyPairs * kApplyThreads;  // words a CTA
+void launch_apply_dense_batch(int prec, const RepDesc* desc, const int2* chunk, int nchunks,
+                              int par, cudaStream_t st);
 void launch_gather_batch(int prec, const RepDesc* desc, const int* cta_rep, int nctas, int par,
                          int thermo, double gamma, double kT, cudaStream_t st);
 // per-particle constants: h = (dt/2)/m always; sig when thermo is set

@@ -481,6 +481,76 @@ __global__ void __launch_bounds__(kQuadThreads)
   apply_body<T>(m, P, Tb, Lg, D, scale, blockIdx.x * (int64_t)blockDim.x + threadIdx.x);
 }
 
+// Dense form of the same: every transfer word of links [l0, l1) once (l0
+// even), each non-zero word added to the ledger and, scaled, to D, then
+// cleared.  Each word gets the one addition the sparse form gives it, so
+// D + x is rounded once the same way.  Words are read in 16-byte pairs when
+// the buffer is 16-byte aligned (a caller's allocator need not align it),
+// else one by one.
+template <typename T>
+__device__ __forceinline__ void apply_word(long long* __restrict__ Tb, long long* __restrict__ Lg,
+                                           T* __restrict__ D, double scale, int64_t l,
+                                           long long t) {
+  if (t != 0) {
+    Tb[l] = 0;
+    Lg[l] += t;
+    D[l] = D[l] + (T)((double)t * scale);
+  }
+}
+
+// a CTA's chunk is kApplyPairs pairs a thread; every load (the pairs, then
+// the ledger and D words of the non-zero ones) is issued before any store,
+// so a thread waits for two round trips, not two per pair
+template <typename T>
+__device__ __forceinline__ void apply_dense_range(long long* __restrict__ Tb,
+                                                  long long* __restrict__ Lg, T* __restrict__ D,
+                                                  double scale, int64_t l0, int64_t l1) {
+  if (reinterpret_cast<uintptr_t>(Tb) & 15) {
+    for (int64_t l = l0 + threadIdx.x; l < l1; l += blockDim.x)
+      apply_word<T>(Tb, Lg, D, scale, l, Tb[l]);
+    return;
+  }
+  const longlong2* T2 = reinterpret_cast<const longlong2*>(Tb);
+  const int64_t p1 = l1 >> 1;
+  long long t[2 * kApplyPairs], lg[2 * kApplyPairs];
+  T dv[2 * kApplyPairs];
+  int64_t w[kApplyPairs];
+#pragma unroll
+  for (int k = 0; k < kApplyPairs; ++k) {
+    const int64_t i = (l0 >> 1) + threadIdx.x + (int64_t)k * blockDim.x;
+    w[k] = 2 * i;
+    const longlong2 v = i < p1 ? __ldcs(T2 + i) : make_longlong2(0, 0);
+    t[2 * k] = v.x;
+    t[2 * k + 1] = v.y;
+  }
+#pragma unroll
+  for (int j = 0; j < 2 * kApplyPairs; ++j) {
+    lg[j] = 0;
+    dv[j] = T(0);
+    if (t[j] != 0) {
+      lg[j] = Lg[w[j >> 1] + (j & 1)];
+      dv[j] = D[w[j >> 1] + (j & 1)];
+    }
+  }
+#pragma unroll
+  for (int j = 0; j < 2 * kApplyPairs; ++j)
+    if (t[j] != 0) {
+      const int64_t l = w[j >> 1] + (j & 1);
+      Tb[l] = 0;
+      Lg[l] = lg[j] + t[j];
+      D[l] = dv[j] + (T)((double)t[j] * scale);
+    }
+  if ((l1 & 1) && threadIdx.x == 0) apply_word<T>(Tb, Lg, D, scale, l1 - 1, Tb[l1 - 1]);
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kApplyThreads)
+    k_apply_dense(int64_t nl, long long* __restrict__ Tb, long long* __restrict__ Lg,
+                  T* __restrict__ D, double scale) {
+  const int64_t l0 = (int64_t)blockIdx.x * kApplyChunk;
+  apply_dense_range<T>(Tb, Lg, D, scale, l0, l0 + kApplyChunk < nl ? l0 + kApplyChunk : nl);
+}
+
 // ------------------------------------------------------------- self energy
 // U_self = q^2 / (2 a eps) sum_{r in {0,1}^3} G(r) prod_d c_d(r_d) with
 // c(0) = (1-f)^2 + f^2, c(1) = 2 f (1-f); the correction force is +dU/dx.
@@ -789,6 +859,17 @@ __global__ void __launch_bounds__(kBatchQuadThreads)
   const RepDesc& r = desc[cta_rep[blockIdx.x]];
   apply_body<T>(r.m, r.P, (unsigned long long*)r.Tb, r.Lg, (T*)r.D[par ^ 1], r.sp.scale,
                 batch_local(r));
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kApplyThreads)
+    k_apply_dense_batch(const RepDesc* __restrict__ desc, const int2* __restrict__ chunk,
+                        int par) {
+  const int2 c = chunk[blockIdx.x];
+  const RepDesc& r = desc[c.x];
+  const int64_t nl = 3 * r.m.V, l0 = (int64_t)c.y * kApplyChunk;
+  apply_dense_range<T>(r.Tb, r.Lg, (T*)r.D[par ^ 1], r.sp.scale, l0,
+                       l0 + kApplyChunk < nl ? l0 + kApplyChunk : nl);
 }
 
 template <typename T>
@@ -1117,6 +1198,16 @@ void launch_apply(const Mesh& m, int prec, Particles p, long long* Tb, long long
                                                  scale);
 }
 
+void launch_apply_dense(int prec, int64_t nlinks, long long* Tb, long long* Lg, void* D,
+                        double scale, cudaStream_t st) {
+  if (nlinks <= 0) return;
+  const unsigned nb = (unsigned)((nlinks + kApplyChunk - 1) / kApplyChunk);
+  if (prec == 1)
+    k_apply_dense<float><<<nb, kApplyThreads, 0, st>>>(nlinks, Tb, Lg, (float*)D, scale);
+  else
+    k_apply_dense<double><<<nb, kApplyThreads, 0, st>>>(nlinks, Tb, Lg, (double*)D, scale);
+}
+
 int coop_grid(int prec, int device) {
   int coop = 0, sms = 0, per = 0;
   if (cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, device) != cudaSuccess || !coop ||
@@ -1199,6 +1290,15 @@ void launch_apply_batch(int prec, const RepDesc* desc, const int* cta_rep, int n
     k_apply_batch<float><<<nctas, kBatchQuadThreads, 0, st>>>(desc, cta_rep, par);
   else
     k_apply_batch<double><<<nctas, kBatchQuadThreads, 0, st>>>(desc, cta_rep, par);
+}
+
+void launch_apply_dense_batch(int prec, const RepDesc* desc, const int2* chunk, int nchunks,
+                              int par, cudaStream_t st) {
+  if (nchunks <= 0) return;
+  if (prec == 1)
+    k_apply_dense_batch<float><<<nchunks, kApplyThreads, 0, st>>>(desc, chunk, par);
+  else
+    k_apply_dense_batch<double><<<nchunks, kApplyThreads, 0, st>>>(desc, chunk, par);
 }
 
 void launch_gather_batch(int prec, const RepDesc* desc, const int* cta_rep, int nctas, int par,

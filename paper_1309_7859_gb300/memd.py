@@ -66,7 +66,8 @@ class Options(C.Structure):
                 ("cuda_stream", C.c_void_p), ("device", C.c_int32), ("use_graphs", C.c_int32),
                 ("alloc", ALLOC), ("free", FREE), ("alloc_user", C.c_void_p),
                 ("time_kernels", C.c_int32), ("field_kernel", C.c_int32),
-                ("step_engine", C.c_int32), ("reserved", C.c_int32 * 5)]
+                ("step_engine", C.c_int32), ("apply_mode", C.c_int32),
+                ("reserved", C.c_int32 * 4)]
 
 
 class Thermostat(C.Structure):
@@ -273,7 +274,7 @@ class Memd:
     def __init__(self, mesh, box, eps=None, c_light=1.0, dt=0.01, precision="fp64",
                  self_mode=SELF_GF, dipole_corr=True, relax_tol=1e-12, relax_max_iter=200000,
                  seed=0, use_graphs=True, time_kernels=False, use_torch=True, stream=None,
-                 device=None, field_kernel="auto", step_engine="auto"):
+                 device=None, field_kernel="auto", step_engine="auto", apply_mode="auto"):
         self._L = lib()
         _live["memd"].add(self)
         self._h = C.c_void_p(None)
@@ -293,6 +294,7 @@ class Memd:
         o.time_kernels = 1 if time_kernels else 0
         o.field_kernel = {"auto": 0, "ldg": 1, "tma": 2, "site": 3, "rows": 4}[field_kernel]
         o.step_engine = {"auto": 0, "graph": 1, "single": 2}[step_engine]
+        o.apply_mode = {"auto": 0, "sparse": 1, "dense": 2}[apply_mode]
         self._alloc = None
         self._stream = stream
         if use_torch:

@@ -31,10 +31,10 @@ def systems(precision):
     return out
 
 
-def make(s, stream=None):
+def make(s, stream=None, apply_mode="auto"):
     from paper_1309_7859_gb300.memd import Memd
     g = Memd(s["mesh"], s["box"], s["eps"], c_light=1.0, dt=0.005, precision=s["precision"],
-             seed=s["seed"], field_kernel="ldg", stream=stream)
+             seed=s["seed"], field_kernel="ldg", stream=stream, apply_mode=apply_mode)
     g.init_field(s["x"], s["q"], None, s["v"])
     return g
 
@@ -71,6 +71,29 @@ def test_batch_members_match_alone(precision):
     for gm, ga in zip(members, alone):
         assert_same(state(gm), state(ga))
         assert gm.energy()["gauss_exact"] == 1.0
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_batch_apply_modes_match(precision):
+    # a batch applies its transfers per charge or by a dense pass over
+    # (replica, chunk) pairs, following member 0's mode; the members end
+    # identical either way (one member has an odd word count over two chunks)
+    import torch
+    from paper_1309_7859_gb300.memd import Batch
+    sys_ = systems(precision)
+    res = []
+    for mode in ("sparse", "dense"):
+        stream = torch.cuda.Stream()
+        members = [make(s, stream, apply_mode=mode) for s in sys_]
+        batch = Batch(members)
+        batch.step(3)
+        batch.step(7, thermostat=(1.0, 1.0))
+        batch.synchronize()
+        res.append([state(g) for g in members])
+        for g in members:
+            assert g.energy()["gauss_exact"] == 1.0
+    for a, b in zip(res[0], res[1]):
+        assert_same(a, b)
 
 
 def test_batch_follows_members_stepped_alone():

@@ -361,6 +361,32 @@ def test_step_engines_bit_identical(mesh, n, eps, precision):
         assert np.array_equal(np.asarray(a), np.asarray(b))
 
 
+@pytest.mark.parametrize("mesh,n,precision", [((15, 9, 7), 60, "fp32"),     # 3V odd
+                                               ((16, 12, 10), 80, "fp64"),   # two chunks
+                                               ((24, 24, 24), 5000, "fp32"),
+                                               ((40, 8, 8), 10, "fp64")])    # 24 per charge
+def test_apply_modes_bit_identical(mesh, n, precision):
+    # the transfers of a step applied per charge (atomic exchanges on the
+    # crossed links) or by one pass over every link's word: each word gets
+    # one addition either way, so 20 thermostatted graph steps agree bit for bit
+    from paper_1309_7859_gb300.memd import Memd
+    sysc = small_system(mesh, n, SLAB, precision=precision, dt=0.005)
+    out = []
+    for mode in ("sparse", "dense"):
+        g = Memd(sysc.mesh, sysc.box, sysc.eps, c_light=1.0, dt=sysc.dt, precision=precision,
+                 seed=5, step_engine="graph", apply_mode=mode)
+        g.init_field(sysc.x, sysc.q, sysc.m, sysc.v)
+        g.step(20, thermostat=(1.0, 1.0))
+        D, B, Lg = g.fields()
+        x, v, img = g.particles()
+        e = g.energy()
+        assert e["gauss_exact"] == 1.0
+        out.append((D, B, Lg, x, v, img, g.forces(), e["total"], e["P0"], e["step"]))
+        g.close()
+    for a, b in zip(out[0], out[1]):
+        assert np.array_equal(np.asarray(a), np.asarray(b))
+
+
 @pytest.mark.parametrize("engine", ["graph", "single"])
 def test_direct_launches_match_graphs_with_timing(engine):
     # the same steps launched directly (no CUDA graph) with kernel timing on
