@@ -233,17 +233,29 @@ memd_status memd_init_field(memd_ctx *ctx, int64_t n, const double *pos,
  * not move), CUDA. */
 memd_status memd_step(memd_ctx *ctx, int64_t nsteps, const memd_thermostat *th);
 
-/* Copy the electrostatic forces (n x 3, without the Langevin part). */
+/* Copy the electrostatic forces of the current state (Eq. 18 with the
+ * self-energy and dipole corrections of Secs. III and V; without the
+ * Langevin part) into the caller's host array f_out of n x 3 doubles,
+ * particle major.  Synchronises.  Errors: INVALID (NULL argument), STATE
+ * before memd_init_field, CUDA. */
 memd_status memd_forces(memd_ctx *ctx, double *f_out);
 
-/* Device address of the n x 3 FP64 force array, valid until the next
- * memd_init_field or memd_destroy. */
+/* Device address of the n x 3 FP64 force array (the library's own memory:
+ * read it on ctx's stream or after memd_synchronize; do not free it), valid
+ * until the next memd_init_field or memd_destroy.  Errors: INVALID, STATE. */
 memd_status memd_forces_device(memd_ctx *ctx, const double **f_dev);
 
-/* Energy terms, dipole moment and Gauss-law residuals (FP64 reductions). */
+/* Energy terms (kinetic, a^3 sum D^2 / 2 eps, the time-centred magnetic term,
+ * the self energy and the dipole term of Secs. III and V), the dipole moment
+ * P and the Gauss-law check (Sec. II: the largest |div D - rho| in FP64 and
+ * the exact int64 identity div Lg == Q) into *out, all FP64 reductions on
+ * the device; pending transfers are applied first.  Synchronises.  Errors:
+ * INVALID, STATE before memd_init_field, CUDA. */
 memd_status memd_energy(memd_ctx *ctx, memd_energy_terms *out);
 
-/* Copy the folded positions, velocities and image counters (any may be NULL). */
+/* Copy the folded positions (in [0, L)), velocities and image counters into
+ * caller host arrays of n x 3, particle major (any may be NULL).
+ * Synchronises.  Errors: INVALID, STATE before memd_init_field, CUDA. */
 memd_status memd_get_particles(memd_ctx *ctx, double *pos, double *vel,
                                int32_t *img);
 
@@ -258,8 +270,10 @@ memd_status memd_step_host(memd_ctx *ctx, const double *pos_in, const double *ve
                            const int32_t *img_in, int64_t nsteps, const memd_thermostat *th,
                            double *pos_out, double *vel_out, int32_t *img_out, double *f_out);
 
-/* Library-owned page-locked I/O buffers for memd_step_io, n x 3 each, valid
- * until the next memd_init_field or memd_destroy. */
+/* Library-owned page-locked I/O buffers for memd_step_io, n x 3 each,
+ * particle major, valid until the next memd_init_field or memd_destroy (the
+ * caller reads and writes them between calls, never frees them).  Errors:
+ * INVALID, STATE before memd_init_field, OOM (page-locked allocation). */
 typedef struct memd_io {
   double *pos;   /* positions (in and out) */
   double *vel;   /* velocities (in and out) */
@@ -278,8 +292,12 @@ memd_status memd_step_io(memd_ctx *ctx, int32_t load, int64_t nsteps,
                          const memd_thermostat *th);
 
 /* Overwrite positions (folded, with img), velocities and image counters of
- * the n particles without depositing any current (state load).  img NULL
- * keeps the counters, vel NULL keeps the velocities. */
+ * the n particles without depositing any current (state load); host arrays
+ * of n x 3, copied.  img NULL keeps the counters, vel NULL keeps the
+ * velocities.  The ledger is not rebuilt, so Gauss' law stays exact only if
+ * the charges sit where the ledger has them (memd_move transfers charge).
+ * Errors: INVALID (NULL pos; a position not finite or beyond 4 box lengths),
+ * STATE before memd_init_field, OOM, CUDA. */
 memd_status memd_set_particles(memd_ctx *ctx, const double *pos,
                                const double *vel, const int32_t *img);
 
@@ -289,15 +307,23 @@ memd_status memd_set_particles(memd_ctx *ctx, const double *pos,
  * Errors: CELL_JUMP, STATE. */
 memd_status memd_move(memd_ctx *ctx, const double *pos, const int32_t *img);
 
-/* Copy D, B (FP64, 3V each) and the ledger Lg (int64, 3V); any may be NULL. */
+/* Copy D, B (FP64, 3V each) and the ledger Lg (int64 in units of e 2^-48,
+ * 3V) into caller host arrays in the library's layout: component major, x
+ * fastest (element (d, i, j, k) at d V + i + Nx (j + Ny k)); D on the links,
+ * B on the plaquettes (Sec. II).  Any may be NULL.  Pending transfers are
+ * applied first.  Errors: INVALID, OOM (conversion scratch), CUDA. */
 memd_status memd_get_fields(memd_ctx *ctx, double *D, double *B, int64_t *Lg);
 
-/* Overwrite D, B and Lg (any may be NULL); FP32 contexts round D and B. */
+/* Overwrite D, B and Lg from caller host arrays in the layout of
+ * memd_get_fields (any may be NULL; copied); FP32 contexts round D and B.
+ * Nothing checks that the new D satisfies Gauss' law: memd_energy reports
+ * it.  Errors: INVALID, OOM (conversion scratch), CUDA. */
 memd_status memd_set_fields(memd_ctx *ctx, const double *D, const double *B,
                             const int64_t *Lg);
 
-/* Recompute the forces from the current state (gather with corrections);
- * the stored kick force becomes the electrostatic force. */
+/* Recompute the forces from the current state (gather with corrections,
+ * Eq. 18, Secs. III and V); the stored kick force becomes the electrostatic
+ * force.  Errors: INVALID, STATE before memd_init_field, CUDA. */
 memd_status memd_compute_forces(memd_ctx *ctx);
 
 /* Replace the permittivity of a context (Sec. II; moving or re-shaped
@@ -333,10 +359,19 @@ memd_status memd_load_state(memd_ctx *ctx, const void *buf, int64_t bytes);
 /* Create-time results: 1/eps per link (3V, may be NULL), the lattice Green's
  * table G(dx,dy,dz) at index dx + 2 dy + 4 dz (8, may be NULL) and the inverse
  * effective permittivity tensor (9, row major, may be NULL). */
+/* Create-time quantities, into caller host arrays (any may be NULL):
+ * inv_eps the FP64 1/eps of every link (3V, layout of memd_get_fields;
+ * Eq. 24 on interface links), G8 the lattice Green's function at the 8
+ * offsets {0,1}^3 (index rx + 2 ry + 4 rz; Eqs. 25-27, k = 0 removed),
+ * eps_eff_inv the inverse effective permittivity tensor (9, row major) of
+ * the dipole correction (Sec. V).  Synchronises.  Errors: INVALID, CUDA. */
 memd_status memd_get_setup(memd_ctx *ctx, double *inv_eps, double *G8,
                            double *eps_eff_inv);
 
-/* Event timing of the field kernels and launch counts (needs time_kernels). */
+/* Event timing of the field kernels and launch counts into *out (the timing
+ * needs time_kernels; the kernel choice and byte counts are always filled).
+ * memd_reset_kernel_stats zeroes the accumulated time and launch count.
+ * Errors: INVALID. */
 memd_status memd_get_kernel_stats(memd_ctx *ctx, memd_kernel_stats *out);
 memd_status memd_reset_kernel_stats(memd_ctx *ctx);
 
@@ -446,6 +481,11 @@ typedef struct memd_request {
 
 /* Defaults: FP32, 64 slots, 8 GiB budget, quantum 50, constant energy. */
 void memd_server_default_options(memd_server_options *opt);
+/* Create a server on opt->device (the device current at this call when -1;
+ * its own stream unless opt->cuda_stream is given, and its admission
+ * threads); opt NULL takes the defaults; *out is NULL on failure.
+ * memd_server_destroy stops the threads, releases every request and all
+ * device memory (NULL is accepted).  Errors: INVALID (bad options), CUDA. */
 memd_status memd_server_create(const memd_server_options *opt, memd_server **out);
 void memd_server_destroy(memd_server *s);
 
@@ -493,6 +533,8 @@ typedef struct memd_server_stats {
                               stream) */
 } memd_server_stats;
 
+/* Counters since create into *out (Errors: INVALID); the reason for the
+ * last failure on s (empty when none). */
 memd_status memd_server_get_stats(const memd_server *s, memd_server_stats *out);
 const char *memd_server_last_error(const memd_server *s);
 

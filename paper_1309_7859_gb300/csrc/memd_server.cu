@@ -182,7 +182,7 @@ memd_status admit(memd_server* s, memd_server::Req& r, cudaStream_t wst) {
 }
 
 void worker(memd_server* s, int w) {
-  cudaSetDevice(s->opt.device >= 0 ? s->opt.device : 0);
+  cudaSetDevice(s->opt.device);  // resolved at create
   for (;;) {
     memd_server::Req* r = nullptr;
     {
@@ -269,6 +269,17 @@ memd_status memd_server_create(const memd_server_options* opt, memd_server** out
       (s->opt.precision != MEMD_FP32 && s->opt.precision != MEMD_FP64)) {
     delete s;
     return MEMD_ERR_INVALID;
+  }
+  // -1 means the device current at create: resolved here once, so the
+  // admission threads (whose current device starts at 0) and the stream
+  // below all use the same device
+  if (s->opt.device < 0 && cudaGetDevice(&s->opt.device) != cudaSuccess) {
+    delete s;
+    return MEMD_ERR_CUDA;
+  }
+  if (cudaSetDevice(s->opt.device) != cudaSuccess) {
+    delete s;
+    return MEMD_ERR_CUDA;
   }
   if (!s->opt.cuda_stream) {
     // one stream shared by every resident system (a batch requirement)
