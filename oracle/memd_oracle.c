@@ -16,8 +16,12 @@
  *   curl updates, energy                pinned (Yee dispersion, conservation)
  *   relaxation                          pinned (FFT / layered exact solves)
  *   lattice Green's table, GF self term pinned (relaxed single-charge energy)
- *   DIRECT self term                    parity unpinned (Eq. 29 is garbled;
- *                                       pinned only by its reduction to GF)
+ *   DIRECT self term                    pinned by special cases and symmetry
+ *                                       (Eq. 29 is garbled, so the reading
+ *                                       itself has no printed values: GF at
+ *                                       constant eps, uniform-medium values
+ *                                       in layered media, mirror and axis
+ *                                       rotation of a random medium)
  *   dipole correction, eps_eff          pinned (layered closed forms)
  *   interface links (planes, ball, cut) pinned (series closed form across
  *                                       off-lattice planes, chord lengths

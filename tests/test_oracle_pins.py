@@ -276,6 +276,80 @@ def test_self_force_symmetry_and_direct_reduces_to_gf():
         assert abs(Ug - Ud) < 1e-15 and np.max(np.abs(Fg - Fd)) < 1e-15
 
 
+# ------------------------------------------ DIRECT self term in varying eps
+# Eq. 29 is garbled; the reading (per direction d, 1/eps averaged over the
+# cell's four d-links with the charge's weights) has no printed values to
+# check against.  These pins use only what any correct reading of a local
+# self term must satisfy: special media where it reduces to the uniform
+# case (whose Green's table is pinned above), and lattice symmetries.
+def _link_eps(N, fn):
+    """eps on every link in the oracle's layout (component major, x
+    fastest); fn(d, k, j, i) gives the (Nz, Ny, Nx) array of direction d."""
+    return np.concatenate([np.asarray(fn(d, *np.meshgrid(np.arange(N[2]), np.arange(N[1]),
+                                                           np.arange(N[0]), indexing="ij")),
+                                      dtype=np.float64).ravel() for d in range(3)])
+
+
+def test_direct_self_force_in_a_layered_medium_reduces_to_uniform_media():
+    # eps varies only along z: the four z-links of a cell lie in one layer,
+    # so the z-force is the uniform-medium self force of that layer; a charge
+    # on lattice plane k puts no weight on plane k + 1, so its x- and y-forces
+    # are those of a uniform medium with plane k's in-plane eps
+    N = (8, 8, 8)
+    rng = np.random.default_rng(31)
+    ez = rng.uniform(2.0, 80.0, N[2])    # z-links from plane k to k + 1
+    exy = rng.uniform(2.0, 80.0, N[2])   # x- and y-links in plane k
+    vals = _link_eps(N, lambda d, k, j, i: (ez if d == 2 else exy)[k] + 0.0 * i)
+    lay = make(N, eps=dict(kind=O.EPS_LINKS, values=vals), self_mode=O.SELF_DIRECT)
+    gf = make(N, eps=dict(kind=O.EPS_LINKS, values=vals), self_mode=O.SELF_GF)
+    for cell, f in (([2, 3, 4], [1000, 30000, 60000]), ([5, 0, 7], [40000, 5, 12345]),
+                    ([0, 6, 1], [65535, 200, 33000])):
+        k = cell[2]
+        _, Fd = lay.self_force(cell, f)
+        _, Fu = make(N, eps=dict(kind=O.EPS_CONST, params=(ez[k],))).self_force(cell, f)
+        assert abs(Fd[2] - Fu[2]) <= 1e-14 * abs(Fu[2])
+        _, Fg = gf.self_force(cell, f)          # the 12-link mean misses it
+        assert abs(Fg[2] - Fu[2]) > 1e-3 * abs(Fu[2])
+        f0 = [f[0], f[1], 0]
+        _, Fd0 = lay.self_force(cell, f0)
+        _, Fu0 = make(N, eps=dict(kind=O.EPS_CONST, params=(exy[k],))).self_force(cell, f0)
+        assert np.max(np.abs(Fd0[:2] - Fu0[:2])) <= 1e-14 * np.max(np.abs(Fu0[:2]))
+
+
+def test_direct_self_force_mirror_and_rotation_symmetry():
+    # a random medium made mirror symmetric in z: the mirrored charge has the
+    # same self energy and in-plane force and the opposite z-force; the same
+    # medium with its axes permuted cyclically (a rotation) on a non-cubic
+    # mesh: the force components permute with it
+    S = refs.S
+    N = (6, 8, 10)
+    Nx, Ny, Nz = N
+    rng = np.random.default_rng(37)
+    A = rng.uniform(2.0, 80.0, (3, Nz, Ny, Nx))
+    k = np.arange(Nz)
+    mir = np.stack([A[0][(Nz - k) % Nz], A[1][(Nz - k) % Nz], A[2][Nz - 1 - k]])
+    sym = 2.0 / (1.0 / A + 1.0 / mir)
+    s = make(N, eps=dict(kind=O.EPS_LINKS, values=sym.ravel()), self_mode=O.SELF_DIRECT)
+    # rotation: new (x, y, z) = old (z, x, y); direction d becomes (d + 1) % 3
+    rot = np.empty((3, Ny, Nx, Nz))
+    for d in range(3):
+        rot[(d + 1) % 3] = A[d].transpose(1, 2, 0)
+    r0 = make(N, eps=dict(kind=O.EPS_LINKS, values=A.ravel()), self_mode=O.SELF_DIRECT)
+    r1 = make((Nz, Nx, Ny), eps=dict(kind=O.EPS_LINKS, values=rot.ravel()),
+              self_mode=O.SELF_DIRECT)
+    for cell, f in (([2, 3, 4], [1000, 30000, 60000]), ([5, 0, 9], [40000, 5, 12345]),
+                    ([0, 7, 1], [65535, 200, 33000])):
+        U1, F1 = s.self_force(cell, f)
+        U2, F2 = s.self_force([cell[0], cell[1], Nz - 1 - cell[2]], [f[0], f[1], S - f[2]])
+        tol = 1e-13 * np.max(np.abs(F1))
+        assert abs(U1 - U2) <= 1e-13 * abs(U1)
+        assert np.max(np.abs(F1[:2] - F2[:2])) <= tol and abs(F1[2] + F2[2]) <= tol
+        U3, F3 = r0.self_force(cell, f)
+        U4, F4 = r1.self_force([cell[2], cell[0], cell[1]], [f[2], f[0], f[1]])
+        assert abs(U3 - U4) <= 1e-12 * abs(U3)
+        assert np.max(np.abs(F4 - F3[[2, 0, 1]])) <= 1e-12 * np.max(np.abs(F3))
+
+
 # ------------------------------------------------------ planar dielectric jump
 def image_force_z(ein, eout, d, W, L):
     # charge +1 in a slab of eps_in, a distance d below its upper face, its
