@@ -1072,7 +1072,7 @@ static memd_status record_step(memd_ctx* c, const StepParams& sp, int par, bool 
     launch_kick_drift_deposit(m, sp, c->P, c->Tb, c->ds, st);
   else
     CK(cudaStreamWaitEvent(st, c->join, 0));
-  if (apply_dense(c->apply_mode, m.V, c->P.n))
+  if (apply_dense(c->apply_mode))
     launch_apply_dense(c->prec, 3 * m.V, c->Tb, c->Lg, c->Dbuf[par ^ 1], sp.scale, st);
   else
     launch_apply(m, c->prec, c->P, c->Tb, c->Lg, c->Dbuf[par ^ 1], sp.scale, st);

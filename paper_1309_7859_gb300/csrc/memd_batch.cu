@@ -42,8 +42,7 @@ struct memd_batch {
   int* d_seg_first = nullptr;
   int n_rows_ctas = 0;
   // transfer application: dense pass over (replica, chunk) pairs, or the
-  // sparse per-charge form (MEMD_APPLY_* of member 0, AUTO decided on the
-  // batch's totals)
+  // sparse per-charge form (MEMD_APPLY_* of member 0; AUTO is sparse)
   bool apply_dense = false;
   int2* d_apply_chunk = nullptr;
   int n_apply_chunk = 0;
@@ -131,7 +130,6 @@ memd_status build_tables(memd_batch* b) {
   std::vector<RepDesc> desc(R);
   std::vector<int> frep, prep;
   std::vector<int2> achunk;
-  int64_t Vsum = 0, nsum = 0;
   b->field_bytes = 0.0;
   for (int r = 0; r < R; ++r) {
     memd_ctx* c = b->m[r];
@@ -165,8 +163,6 @@ memd_status build_tables(memd_batch* b) {
     for (int t = 0; t < d.p_ctas; ++t) prep.push_back(r);
     const int64_t nch = (3 * c->mesh.V + kApplyChunk - 1) / kApplyChunk;
     for (int64_t k = 0; k < nch; ++k) achunk.push_back(make_int2(r, (int)k));
-    Vsum += c->mesh.V;
-    nsum += c->P.n;
     b->base[r] = c->cur;
     b->gen[r] = c->gen;
     b->field_bytes += 15.0 * (double)memd_esz(c) * (double)c->mesh.V;
@@ -185,7 +181,7 @@ memd_status build_tables(memd_batch* b) {
                       cudaMemcpyHostToDevice, b->stream));
   BCK(cudaMemcpyAsync(b->d_part_rep, prep.data(), sizeof(int) * b->n_part,
                       cudaMemcpyHostToDevice, b->stream));
-  b->apply_dense = apply_dense(b->m[0]->apply_mode, Vsum, nsum);
+  b->apply_dense = apply_dense(b->m[0]->apply_mode);
   if (b->apply_dense) {
     b->n_apply_chunk = (int)achunk.size();
     b->d_apply_chunk = (int2*)balloc(b, sizeof(int2) * std::max(1, b->n_apply_chunk));

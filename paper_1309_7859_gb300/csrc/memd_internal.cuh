@@ -237,20 +237,14 @@ void launch_apply(const Mesh& m, int prec, Particles p, long long* Tb, long long
 // data); identical results.  Cheaper when the mesh has few links per charge.
 void launch_apply_dense(int prec, int64_t nlinks, long long* Tb, long long* Lg, void* D,
                         double scale, cudaStream_t st);
-// MEMD_APPLY_AUTO: dense when V < kApplyDenseSitesPerCharge n (0: never).
-// A dense pass reads 24 B a vertex and rewrites the words that carry a
-// transfer; the sparse pass costs ~0.25-0.3 ns a charge on GB300 (12 atomic
-// round trips per quad, issued together).  Measured a step: the 64^3 system
-// with 32768 charges 44.1 us dense vs 44.8 sparse (within run-to-run
-// spread); 64 replicas with 124k charges and fields larger than L2, 161.5 vs
-// 142.0 (the 71 MB of transfer words cost more than the exchanges).  AUTO
-// keeps the sparse pass.
-constexpr int64_t kApplyDenseSitesPerCharge = 0;
-inline bool apply_dense(int mode, int64_t V, int64_t n) {
-  if (mode == 2) return true;   // MEMD_APPLY_DENSE
-  if (mode == 1) return false;  // MEMD_APPLY_SPARSE
-  return V < kApplyDenseSitesPerCharge * n;
-}
+// MEMD_APPLY_AUTO is the sparse pass.  A dense pass reads 24 B a vertex and
+// rewrites the words that carry a transfer; the sparse pass costs ~0.25-0.3 ns
+// a charge on GB300 (12 atomic round trips per quad, issued together).
+// Measured a step: the 64^3 system with 32768 charges 44.1 us dense vs 44.8
+// sparse (within run-to-run spread); 64 replicas with 124k charges and
+// fields larger than L2, 161.5 vs 142.0 (the 71 MB of transfer words cost
+// more than the exchanges).
+inline bool apply_dense(int mode) { return mode == 2; }  // MEMD_APPLY_DENSE
 // finish: 0 nothing, 1 close the update (P of this state, clear the
 // accumulator), 2 also advance the step counter; done by the last CTA
 void launch_gather(const Mesh& m, int prec, const StepParams& sp, Particles p, const void* D,
