@@ -192,37 +192,6 @@ namespace {
 // After the recursive residual meets the tolerance the iteration freezes
 // (kS_DONE): continuing in round-off would divide noise by noise.  The host
 // then checks the true residual and restarts from it if needed.
-__global__ void __launch_bounds__(256)
-    k_pcg_update(int64_t n, double* __restrict__ D, const double* __restrict__ u,
-                 double* __restrict__ r, const double* __restrict__ w, double* __restrict__ z,
-                 const double* __restrict__ diag, const double* __restrict__ sc, int rz_slot,
-                 double* __restrict__ part) {
-  __shared__ double sh[8];
-  const bool done = sc[kS_DONE] != 0.0;
-  const double pw = sc[kS_PW], rz = sc[rz_slot];
-  const double alpha = (!done && pw > 0.0) ? rz / pw : 0.0;
-  double mx = 0.0;
-  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < n;
-       t += (int64_t)gridDim.x * blockDim.x) {
-    double rn = r[t];
-    if (!done) {
-      D[t] += alpha * u[t];
-      rn = rn - alpha * w[t];
-      r[t] = rn;
-      z[t] = rn / diag[t];
-    }
-    mx = fmax(mx, fabs(rn));
-  }
-  for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_down_sync(0xffffffffu, mx, o));
-  if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = mx;
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    double r2 = 0.0;
-    for (int q = 0; q < (int)(blockDim.x >> 5); ++q) r2 = fmax(r2, sh[q]);
-    part[blockIdx.x] = r2;
-  }
-}
-
 __global__ void k_pcg_dir(int64_t n, double* __restrict__ p, const double* __restrict__ z,
                           double* __restrict__ sc, int rz_new, int rz_old, int first) {
   const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
@@ -249,12 +218,6 @@ __global__ void k_div(int64_t n, double* __restrict__ z, const double* __restric
                       const double* __restrict__ diag) {
   const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (t < n) z[t] = r[t] / diag[t];
-}
-
-__global__ void k_mul(int64_t n, double* __restrict__ out, const double* __restrict__ x,
-                      const double* __restrict__ y) {
-  const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (t < n) out[t] = x[t] * y[t];
 }
 
 __global__ void k_fill_unit(int64_t V, double* __restrict__ D, int d) {

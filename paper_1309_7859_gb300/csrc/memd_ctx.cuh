@@ -85,7 +85,7 @@ struct memd_ctx {
   long long field_launches = 0;
   int relax_iters_last = 0;
   int gen = 0;  // bumped by every memd_init_field (batches rebuild their tables)
-  FusedCfg fcfg{8, 1, 0, 0};
+  FusedCfg fcfg{8, 1, 0, 0, 0};
   bool fcfg_ready = false;  // fcfg autotuned (at the first step that needs it)
   int field_kernel = 0;
   TmaMaps tma{};

@@ -666,7 +666,7 @@ void launch_fused_curl(const Mesh& m, int prec, const void* Din, const void* Bin
 FusedCfg fused_default(const Mesh& m) {
   // enough CTAs to fill the GPU a few times over, but chunks long enough
   // that the recomputed prologue plane stays a small overhead
-  FusedCfg c{8, 1, 0, 0};
+  FusedCfg c{8, 1, 0, 0, 0};
   const int64_t tiles = (int64_t)((m.n[0] + 31) / 32) * ((m.n[1] + 7) / 8);
   const int64_t target = 4 * 152;
   const int64_t nchunks = (target + tiles - 1) / tiles;
@@ -724,7 +724,7 @@ int fused_candidates(const Mesh& m, int prec, FusedCfg* out, int cap) {
   for (int a = 0; a < (prec == 1 ? 3 : 2); ++a)
     for (int b = 0; b < 8; ++b) {
       if (zcs[b] > m.n[2] && b > 0 && zcs[b - 1] >= m.n[2]) continue;
-      if (n < cap) out[n++] = FusedCfg{tys[a], zcs[b] < m.n[2] ? zcs[b] : m.n[2], 0, 0};
+      if (n < cap) out[n++] = FusedCfg{tys[a], zcs[b] < m.n[2] ? zcs[b] : m.n[2], 0, 0, 0};
     }
   return n;
 }
