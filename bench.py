@@ -550,7 +550,7 @@ def large_mesh(N, dev, stream, args):
     return {"workload": sysc.name, "steps": steps, "ms_per_step": ms / steps,
             "link_updates_per_s": links * steps / (ms * 1e-3),
             "particle_steps_per_s": sysc.n * steps / (ms * 1e-3),
-            "l2": "fields (1 GB) larger than L2, no flush",
+            "l2": f"fields ({ks.field_bytes / 1e9:.1f} GB a pass) larger than L2, no flush",
             "roofline": {"bound": "hbm", "kernel": ks.field_kernel, "achieved": ach, "peak": hbm,
                          "unit": "GB/s", "frac": ach / hbm, "peak_kind": kind,
                          "bytes_per_launch": ks.field_bytes, "ms_per_launch": per},
