@@ -1,4 +1,5 @@
-"""CPU checks of memd_create's argument validation through the C ABI.
+"""CPU checks of memd_create's and memd_server_create's argument validation
+through the C ABI.
 
 Every check below runs before the library touches CUDA, so these calls need
 no GPU: each bad argument must come back as its status code (INVALID, or
@@ -62,3 +63,15 @@ def test_status_strings_and_null_context_messages():
     texts = {L.memd_status_string(s) for s in range(11)}
     assert len(texts) == 11 and all(texts)
     assert L.memd_last_error(None)           # a static message for a NULL context
+
+
+@pytest.mark.parametrize("field,value", [("max_slots", 0), ("quantum", 0), ("budget_bytes", 0),
+                                         ("precision", 5)])
+def test_server_create_refuses_bad_options_before_touching_the_gpu(field, value):
+    L = M.lib()
+    o = M.ServerOptions()
+    L.memd_server_default_options(C.byref(o))
+    setattr(o, field, value)
+    h = C.c_void_p(12345)
+    assert L.memd_server_create(C.byref(o), C.byref(h)) == INVALID
+    assert h.value is None
