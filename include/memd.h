@@ -419,12 +419,13 @@ memd_status memd_batch_synchronize(memd_batch *b);
 
 /* Event timing of the batched field kernel (when member 0 has time_kernels)
  * and the algorithmic bytes of one launch over all members; reading the
- * timing resets it. */
+ * timing resets it.  Errors: INVALID. */
 memd_status memd_batch_kernel_stats(memd_batch *b, memd_kernel_stats *out);
 
 /* Time the batched field update with CUDA events inside the step graph (on != 0)
  * or not; by default the batch times it when its first member was created with
- * time_kernels.  The step graphs are rebuilt at the next step. */
+ * time_kernels.  The step graphs are rebuilt at the next step.  Errors:
+ * INVALID. */
 memd_status memd_batch_set_timing(memd_batch *b, int32_t on);
 
 /* Release the batch's own tables (members are untouched; destroy the batch
@@ -500,11 +501,14 @@ memd_status memd_server_submit(memd_server *s, const memd_request *req, int64_t 
  * beside the stepping; a system joins the batch at the first round after its
  * setup finished.  A request counts as queued until it joins.  Blocks only
  * to collect the previous round's finished steps, or for at most 2 ms when
- * nothing is resident yet but setups are under way. */
+ * nothing is resident yet but setups are under way.  Errors: INVALID; the
+ * status of a failed batch step (memd_server_last_error says why).  A
+ * request whose own setup fails is marked failed and does not fail the
+ * call. */
 memd_status memd_server_pump(memd_server *s, int32_t *n_active, int32_t *n_queued,
                              int32_t *n_done);
 
-/* MEMD_REQ_* state of a request. */
+/* MEMD_REQ_* state of a request into *state.  Errors: INVALID (unknown id). */
 memd_status memd_server_status(memd_server *s, int64_t id, int32_t *state);
 
 /* Results of a finished request (any pointer may be NULL): folded positions,
@@ -513,10 +517,12 @@ memd_status memd_server_status(memd_server *s, int64_t id, int32_t *state);
 memd_status memd_server_result(memd_server *s, int64_t id, double *pos, double *vel,
                                int32_t *img, double *forces, memd_energy_terms *e);
 
-/* Forget a finished request and its stored results. */
+/* Forget a finished (or failed) request and its stored results.  Errors:
+ * INVALID (unknown id), STATE (still queued or running). */
 memd_status memd_server_release(memd_server *s, int64_t id);
 
-/* Device bytes held by the resident systems (the admission ledger). */
+/* Device bytes held by the resident systems (the admission ledger; 0 for a
+ * NULL server). */
 int64_t memd_server_used_bytes(const memd_server *s);
 
 typedef struct memd_server_stats {
