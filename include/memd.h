@@ -51,8 +51,8 @@ typedef enum memd_status {
   MEMD_ERR_CELL_JUMP = 5,     /* a charge moved by more than one cell in a step */
   MEMD_ERR_GAUSS = 6,         /* the ledger does not close (non-neutral scan) */
   MEMD_ERR_RELAX_NOCONV = 7,  /* the relaxation did not reach its tolerance */
-  MEMD_ERR_DIPOLE_DRIFT = 8,  /* reserved: dipole correction outgrew the force */
-  MEMD_ERR_TIMEOUT = 9,       /* reserved: a bounded wait gave up */
+  MEMD_ERR_DIPOLE_DRIFT = 8,  /* the dipole correction outgrew the field force (Sec. V) */
+  MEMD_ERR_TIMEOUT = 9,       /* a bounded wait in a kernel gave up (step void) */
   MEMD_ERR_STATE = 10,        /* call out of order (e.g. step before init) */
   MEMD_ERR_OVERFLOW = 11      /* fixed-point range exceeded */
 } memd_status;
@@ -566,10 +566,14 @@ const char *memd_server_last_error(const memd_server *s);
  * more than MEMD_STATIC_MAX_SITES vertices are rejected with
  * MEMD_ERR_INVALID.  The first call on each device (made with that device
  * current) looks up the array's device address; make that first call before
- * any CUDA stream capture.  All calls share the array and each overwrites it
+ * any CUDA stream capture.  That address is kept until the process exits, so
+ * resetting the device (cudaDeviceReset) after the first call is not
+ * supported.  All calls share the array and each overwrites it
  * completely, so nothing has to be cleared, but calls whose kernels overlap
  * on the GPU race: queue them on one stream or order them with events.
- * Errors: INVALID (bad argument, mesh too large), CUDA. */
+ * Errors: INVALID (bad argument, mesh too large, an edge or vertex count
+ * that overflows), CUDA (also when an error of the caller's earlier work is
+ * pending: the call then queues nothing and leaves that error in place). */
 #define MEMD_STATIC_SITES_PER_BLOCK 2048
 #define MEMD_STATIC_MAX_BLOCKS 65536
 #define MEMD_STATIC_MAX_SITES ((int64_t)MEMD_STATIC_SITES_PER_BLOCK * MEMD_STATIC_MAX_BLOCKS)

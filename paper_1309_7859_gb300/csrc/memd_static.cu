@@ -103,7 +103,8 @@ __global__ void __launch_bounds__(kThreads)
 }
 
 // device address of the scratch array, looked up once per device with that
-// device current
+// device current and kept for the life of the process (a device reset after
+// the first call would leave it stale: not supported)
 std::mutex g_mu;
 double* g_addr[64] = {nullptr};
 
@@ -118,10 +119,18 @@ extern "C" memd_status memd_field_energy_static(const int32_t mesh[3], double a,
   if (!mesh || !D || !B || !inv_eps || !out2) return MEMD_ERR_INVALID;
   if (precision != MEMD_FP32 && precision != MEMD_FP64) return MEMD_ERR_INVALID;
   if (!(a > 0.0) || !(c_light > 0.0) || !(dt > 0.0)) return MEMD_ERR_INVALID;
-  for (int d = 0; d < 3; ++d)
-    if (mesh[d] < 2) return MEMD_ERR_INVALID;
-  const int64_t V = (int64_t)mesh[0] * mesh[1] * mesh[2];
+  // each edge, then the vertex count, is bounded before it can wrap: a
+  // wrapped count would pass the limit and send the kernel far outside the
+  // caller's arrays
+  int64_t V = 1;
+  for (int d = 0; d < 3; ++d) {
+    if (mesh[d] < 2 || (int64_t)mesh[d] > MEMD_STATIC_MAX_SITES) return MEMD_ERR_INVALID;
+    if (__builtin_mul_overflow(V, (int64_t)mesh[d], &V)) return MEMD_ERR_INVALID;
+  }
   if (V > MEMD_STATIC_MAX_SITES) return MEMD_ERR_INVALID;  // beyond the fixed scratch
+  // an error left by the caller's earlier work is the caller's: refuse
+  // without clearing it
+  if (cudaPeekAtLastError() != cudaSuccess) return MEMD_ERR_CUDA;
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return MEMD_ERR_CUDA;
   double* scratch = nullptr;
@@ -145,15 +154,27 @@ extern "C" memd_status memd_field_energy_static(const int32_t mesh[3], double a,
   m.V = V;
   m.a = a;
   const int nb = (int)((V + kSitesPerBlock - 1) / kSitesPerBlock);
-  const cudaStream_t st = (cudaStream_t)cuda_stream;
   const double cB = dt / a, a3 = a * a * a;
-  if (precision == MEMD_FP32)
-    k_energy_partials<float><<<nb, kThreads, 0, st>>>(m, (const float*)D, (const float*)B,
-                                                      (const float*)inv_eps, cB, scratch, nb);
-  else
-    k_energy_partials<double><<<nb, kThreads, 0, st>>>(m, (const double*)D, (const double*)B,
-                                                       (const double*)inv_eps, cB, scratch, nb);
-  k_energy_finish<<<1, kThreads, 0, st>>>(scratch, nb, a3, 0.5 * c_light * c_light * a3, out2);
-  if (cudaGetLastError() != cudaSuccess) return MEMD_ERR_CUDA;
+  cudaLaunchConfig_t cfg{};
+  cfg.gridDim = dim3((unsigned)nb, 1, 1);
+  cfg.blockDim = dim3(kThreads, 1, 1);
+  cfg.stream = (cudaStream_t)cuda_stream;
+  // each launch's own status: a failed launch is this call's error, cleared
+  // here so that it does not surface in the caller's later work
+  cudaError_t e =
+      precision == MEMD_FP32
+          ? cudaLaunchKernelEx(&cfg, k_energy_partials<float>, m, (const float*)D,
+                               (const float*)B, (const float*)inv_eps, cB, scratch, nb)
+          : cudaLaunchKernelEx(&cfg, k_energy_partials<double>, m, (const double*)D,
+                               (const double*)B, (const double*)inv_eps, cB, scratch, nb);
+  if (e == cudaSuccess) {
+    cfg.gridDim = dim3(1, 1, 1);
+    e = cudaLaunchKernelEx(&cfg, k_energy_finish, (const double*)scratch, nb, a3,
+                           0.5 * c_light * c_light * a3, out2);
+  }
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return MEMD_ERR_CUDA;
+  }
   return MEMD_OK;
 }

@@ -75,3 +75,17 @@ def test_server_create_refuses_bad_options_before_touching_the_gpu(field, value)
     h = C.c_void_p(12345)
     assert L.memd_server_create(C.byref(o), C.byref(h)) == INVALID
     assert h.value is None
+
+
+@pytest.mark.parametrize("mesh", [(1 << 30, 1 << 30, 16),     # V wraps to 0 in int64
+                                  ((1 << 31) - 1, 2, 2),       # one edge beyond the limit
+                                  (65536, 65536, 65536),       # no wrap, far beyond the limit
+                                  (2, 1, 2)])                  # an edge below 2
+def test_static_energy_refuses_bad_meshes_before_touching_the_gpu(mesh):
+    """memd_field_energy_static bounds each edge and the vertex count before
+    any CUDA call; the dummy pointers below are never dereferenced."""
+    L = M.lib()
+    m = (C.c_int32 * 3)(*mesh)
+    dummy = C.c_void_p(0x1000)
+    st = L.memd_field_energy_static(m, 1.0, 1.0, 0.01, 1, dummy, dummy, dummy, dummy, None)
+    assert st == INVALID

@@ -564,17 +564,90 @@ def test_nve_energy_bounded():
     assert np.max(np.abs(H - H[0])) / abs(H[0]) < 1e-3
 
 
-def test_langevin_uses_counter_noise_and_drives_to_kT():
+def test_langevin_drives_charged_system_to_kT():
+    # a charged system of mixed masses equilibrates its kinetic energy to
+    # 3/2 N kT (the thermostat acts on the particles, the fields follow
+    # through the coupled dynamics); 4000 steps at gamma = 5 average over
+    # about 5000 independent samples (2% statistical error)
     from paper_1309_7859_gb300 import inputs
     sysc = inputs.plain_8()
     s = O.OracleSystem(sysc.mesh, sysc.box, dt=0.01, seed=77)
-    s.set_particles(sysc.x, sysc.q, sysc.m, np.zeros((16, 3)))
+    m = np.tile([0.5, 2.0], 8)
+    s.set_particles(sysc.x, sysc.q, m, np.zeros((16, 3)))
     s.init_field()
+    s.step(200, thermostat=(5.0, 1.0))
     ke = []
-    for _ in range(300):
-        s.step(1, thermostat=(1.0, 1.0))
-        ke.append(s.energy()["kinetic"])
-    assert 0.5 * 1.5 * 16 < np.mean(ke[150:]) < 1.6 * 1.5 * 16
+    for _ in range(4000):
+        s.step(1, thermostat=(5.0, 1.0))
+        v = s.particles("v")
+        ke.append(np.sum(0.5 * m[:, None] * v * v))
+    assert abs(np.mean(ke) / (1.5 * 16) - 1.0) < 0.08
+
+
+def free_langevin_velocities(gamma, kT, dt=0.01, n=600, burn=200, steps=4000):
+    """Velocities (steps x n x 3) of uncharged particles with masses 0.25, 1
+    and 4 in turn under the thermostat alone (no field force acts)."""
+    rng = np.random.default_rng(5)
+    x = rng.uniform(0.0, 4.0, (n, 3))
+    m = np.tile([0.25, 1.0, 4.0], n // 3)
+    s = O.OracleSystem((4, 4, 4), (4.0, 4.0, 4.0), dt=dt, seed=91)
+    s.set_particles(x, np.zeros(n, dtype=np.int32), m, np.zeros((n, 3)))
+    s.init_field()
+    s.step(burn, thermostat=(gamma, kT))
+    V = np.empty((steps, n, 3))
+    for i in range(steps):
+        s.step(1, thermostat=(gamma, kT))
+        V[i] = s.particles("v")
+    return V, m
+
+
+def test_langevin_equipartition_for_every_mass():
+    # Free particles under the velocity-Verlet Langevin scheme (friction on
+    # the half-step velocity u, kick factor dt/2m on each side): per step
+    # u' = (1 - gamma dt) u + (dt/m) sigma xi with sigma^2 = 2 gamma m kT/dt,
+    # whose stationary variance makes the full-step velocity v = (1 -
+    # gamma dt/2) u + (dt/2m) sigma xi have m <v^2> = kT exactly, for any dt
+    # and any mass (textbook fluctuation-dissipation balance).  A noise
+    # amplitude scaled as sqrt(2 gamma kT/(m dt)) gives kT/m^2; friction
+    # without the mass gives m kT; a kT slip gives the wrong level.  Each
+    # mass group averages ~10^4 independent samples (1.4% error).
+    kT = 1.5
+    V, m = free_langevin_velocities(gamma=2.0, kT=kT)
+    for mm in (0.25, 1.0, 4.0):
+        sel = m == mm
+        assert abs(np.mean(mm * V[:, sel, :] ** 2) / kT - 1.0) < 0.05, mm
+
+
+def test_langevin_velocity_autocorrelation_is_ornstein_uhlenbeck():
+    # The same scheme's full-step velocity autocorrelation after k >= 1
+    # steps is (1 - gamma dt)^(k-1) (1 - gamma dt/2), the discrete form of
+    # exp(-gamma t), the same for every mass.  Friction without the mass
+    # would decay at gamma/m instead (e^-0.25 or e^-4 at t = 0.5 for m = 4,
+    # 0.25); a wrong gamma moves the decay for all.
+    gamma, dt, k = 2.0, 0.01, 50
+    V, m = free_langevin_velocities(gamma=gamma, kT=1.5, dt=dt)
+    want = (1 - gamma * dt) ** (k - 1) * (1 - gamma * dt / 2)
+    for mm in (0.25, 1.0, 4.0):
+        sel = m == mm
+        c = np.mean(V[k:, sel] * V[:-k, sel]) / np.mean(V[:, sel] ** 2)
+        assert abs(c - want) < 0.03, (mm, c, want)
+
+
+def test_langevin_noise_is_keyed_by_counter():
+    # the noise of a step is a function of (seed, particle, step) only: two
+    # systems with the same seed and state draw the same words, another seed
+    # draws others
+    from paper_1309_7859_gb300 import inputs
+    sysc = inputs.plain_8()
+    out = []
+    for seed in (77, 77, 78):
+        s = O.OracleSystem(sysc.mesh, sysc.box, dt=0.01, seed=seed)
+        s.set_particles(sysc.x, sysc.q, sysc.m, np.zeros((16, 3)))
+        s.init_field()
+        s.step(5, thermostat=(1.0, 1.0))
+        out.append(s.particles("v").copy())
+    assert np.array_equal(out[0], out[1])
+    assert not np.array_equal(out[0], out[2])
 
 
 def test_fold_keeps_unfolded_position():

@@ -57,18 +57,29 @@ def test_static_energy_matches_memd_energy(precision):
     stream = torch.cuda.Stream(device=dev)
     L = lib()
     prec = FP32 if precision == "fp32" else FP64
+    # every output buffer exists before free device memory is first read
+    bufs = [torch.full((2,), float("nan"), dtype=torch.float64, device=dev) for _ in range(6)]
+    torch.cuda.synchronize()
+    free = [torch.cuda.mem_get_info(dev)[0]]
     outs = []
-    for _ in range(2):  # two calls in a row share the scratch array
-        out = torch.full((2,), float("nan"), dtype=torch.float64, device=dev)
-        torch.cuda.synchronize()
+    for out in bufs:  # calls in a row share the scratch array
         st = call_static(L, mesh, 1.0, 1.0, 0.01, prec, Dt, Bt, It, out, stream)
         assert st == 0
         stream.synchronize()
+        free.append(torch.cuda.mem_get_info(dev)[0])
         outs.append(out.cpu().numpy())
+    # No call allocates device memory.  cudaMemGetInfo moves in steps of
+    # 2 MiB pages, so this sees any allocation of that order: from the first
+    # call on (which looks up the scratch address and, with lazy module
+    # loading, may load the library's own image of at most a few MiB,
+    # scratch array included) free memory stays exactly the same.
+    assert free[0] - free[1] <= 4 << 20
+    assert all(f == free[1] for f in free[1:]), free
     for o in outs:
         assert abs(o[0] - want["electric"]) <= 1e-12 * abs(want["electric"])
         assert abs(o[1] - want["magnetic"]) <= 1e-12 * max(abs(want["magnetic"]), 1e-300) + 1e-18
-    assert np.array_equal(outs[0], outs[1])
+    for o in outs[1:]:
+        assert np.array_equal(outs[0], o)
 
 
 def test_static_energy_rejects_oversized_mesh():
