@@ -2,15 +2,18 @@
 
 A step is one MEMD time step of the whole hot path (half kick, plaquette
 update, drift with charge transfer, link update, transfer application,
-dipole sum, force gather with corrections and Langevin force, half kick) on
-the workload's synthetic system.  The default workload is the 32^3 slab with
-1000 charges and FP32 fields.  It fits in L2, so L2 is flushed (a 256 MiB
+dipole sum, force gather with corrections and Langevin force, half kick).
+The default workload is the batched one: 64 independent replicas (meshes
+from {16,24,32,48}^3, 200-8000 charges, random dielectric slabs, FP32 fields)
+stepped together; a step advances every replica by one time step.  Their
+fields (177 MB) exceed L2 (129 MB), so no flush is needed between steps.
+Single-system workloads (--workload slab-32, salt-64, ...) flush L2 (a 256 MiB
 write) before every timed step.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--workload NAME]
   python bench.py --impl reference ...   (the FP64 CPU oracle on the same workload)
 
-Under torchrun (N > 1) every rank runs its own replica (seed + rank, weak
+Under torchrun (N > 1) every rank runs its own batch (seed + rank, weak
 scaling, no collective on the data path); timings are max-reduced over ranks.
 """
 from __future__ import annotations
@@ -33,6 +36,21 @@ sys.path.insert(0, ROOT)
 METRIC = "lattice link-updates/s + particle-steps/s (HBM % of peak); served p50/p99"
 L2_FLUSH_BYTES = 256 << 20
 L2_BYTES = 129e6
+
+
+def is_batch(name):
+    return name.startswith("batch-")
+
+
+def batch_systems(name, rank=0):
+    from paper_1309_7859_gb300 import inputs
+    count = int(name.split("-")[1])
+    return inputs.batch_replicas(seed=1003 + 7919 * rank, count=count)
+
+
+def batch_name(count):
+    return (f"batch-{count} replicas (meshes {{16,24,32,48}}^3, 200-8000 charges, "
+            f"random slabs, FP32)")
 
 
 def workload(name, rank=0):
@@ -145,6 +163,106 @@ def barrier(world):
 
 
 # ------------------------------------------------------------------ oracle arm
+def host_cpu():
+    """Core count and CPU model of the host the oracle runs on."""
+    model = None
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.lower().startswith("model name"):
+                model = line.split(":", 1)[1].strip()
+                break
+    except Exception:
+        pass
+    if model is None:
+        try:
+            for line in open("/proc/cpuinfo"):
+                if line.lower().startswith(("model name", "cpu part")):
+                    model = line.split(":", 1)[1].strip()
+                    break
+        except Exception:
+            pass
+    return {"nproc": os.cpu_count(), "model": model}
+
+
+def oracle_system(sysc):
+    from oracle import oracle as O
+    kinds = {"const": O.EPS_CONST, "links": O.EPS_LINKS, "vertices": O.EPS_VERTICES,
+             "tanh": O.EPS_TANH, "sin": O.EPS_SIN}
+    e = dict(kind=kinds[sysc.eps.kind], axis=sysc.eps.axis, params=sysc.eps.params)
+    if sysc.eps.values is not None:
+        e["values"] = sysc.eps.values
+    o = O.OracleSystem(sysc.mesh, sysc.box, eps=e, c_light=sysc.c_light, dt=sysc.dt,
+                       seed=sysc.seed)
+    o.set_particles(sysc.x, sysc.q, sysc.m, sysc.v)
+    o.init_field()
+    return o
+
+
+class OracleBatchModel:
+    """The FP64 oracle on a bounded sample of a batch: the first replica of
+    each mesh size, created and initialised untimed, then stepped one step at
+    a time (timed).  A linear cost model t = a V + b n (sites, charges) is fitted
+    to the samples' mean step times (non-negative least squares) and summed
+    over every replica of the batch: the extrapolated single-core time of one
+    batch step."""
+
+    def __init__(self, systems):
+        self.systems = systems
+        self.samples = []
+        seen = set()
+        for s in systems:
+            if s.mesh[0] in seen:
+                continue
+            seen.add(s.mesh[0])
+            self.samples.append((s, oracle_system(s)))
+        self.times = [[] for _ in self.samples]
+
+    def step(self, k=1):
+        for i, (s, o) in enumerate(self.samples):
+            for _ in range(k):
+                t0 = time.perf_counter()
+                o.step(1, thermostat=s.thermostat)
+                self.times[i].append(time.perf_counter() - t0)
+
+    def batch_step_seconds(self):
+        from scipy.optimize import nnls
+        A = np.array([[s.sites, s.n] for s, _ in self.samples], dtype=np.float64)
+        t = np.array([np.mean(ts) for ts in self.times])
+        scale = A.max(axis=0)
+        coef, _ = nnls(A / scale, t)
+        coef = coef / scale
+        per = [coef[0] * s.sites + coef[1] * s.n for s in self.systems]
+        return float(np.sum(per)), coef, t
+
+    def describe(self):
+        steps = len(self.times[0]) if self.times else 0
+        names = ", ".join(s.name for s, _ in self.samples)
+        return (f"extrapolated: {steps} timed steps of each of {len(self.samples)} sample "
+                f"replicas ({names}; FP64 oracle, single thread, untimed create and init); "
+                f"cost per step fitted as a*sites + b*charges and summed over all "
+                f"{len(self.systems)} replicas")
+
+
+def oracle_batch_baseline(systems, steps=10):
+    m = OracleBatchModel(systems)
+    m.step(steps)
+    t, coef, tm = m.batch_step_seconds()
+    sites = sum(s.sites for s in systems)
+    parts = sum(s.n for s in systems)
+    cpu = host_cpu()
+    v = 3 * sites / t
+    return {"value": v, "unit": "link-updates/s", "cores": 1, "kind": "oracle",
+            "sample": m.describe(), "particle_steps_per_s": parts / t,
+            "ms_per_batch_step": t * 1e3,
+            "fit_s_per_site": float(coef[0]), "fit_s_per_charge": float(coef[1]),
+            "sample_ms_per_step": [float(x * 1e3) for x in tm],
+            "host_cpu": cpu["model"], "host_nproc": cpu["nproc"],
+            "all_cores_extrapolated": {"value": v * (cpu["nproc"] or 1),
+                                       "note": "single-core rate x nproc (independent "
+                                               "replicas, one per core; not measured)"}}
+
+
 def oracle_rate(sysc, budget_s, cores_note=1):
     """Time the FP64 CPU oracle on a bounded sample of steps of the workload."""
     from oracle import oracle as O
@@ -171,11 +289,44 @@ def oracle_rate(sysc, budget_s, cores_note=1):
                       f"{el:.1f} s after an untimed init)"}
 
 
+def run_reference_batch(args):
+    """The oracle on the batched workload: its sample replicas (one per mesh
+    size) created and initialised untimed, W warm-up steps each, then K timed
+    steps each; the batch step time extrapolated by the fitted cost model."""
+    systems = batch_systems(args.workload)
+    m = OracleBatchModel(systems)
+    for (s, o) in m.samples:
+        o.step(args.warmup, thermostat=s.thermostat)
+    m.step(args.steps)
+    t, coef, tm = m.batch_step_seconds()
+    sites = sum(s.sites for s in systems)
+    parts = sum(s.n for s in systems)
+    v = 3 * sites / t
+    cpu = host_cpu()
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "link-updates/s",
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": t * 1e3, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": batch_name(len(systems)), "replicas": len(systems),
+                       "sites": sites, "charges": parts, "fields": "fp64 (oracle)"},
+            "particle_steps_per_s": parts / t,
+            "cpu_baseline": {"value": v, "unit": "link-updates/s", "cores": 1, "kind": "oracle",
+                             "sample": m.describe(), "host_cpu": cpu["model"],
+                             "host_nproc": cpu["nproc"],
+                             "sample_ms_per_step": [float(x * 1e3) for x in tm]},
+            "e2e": {"value": v, "unit": "link-updates/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def run_reference(args, world, rank):
     """The oracle on this workload: one untimed create + init, W warm-up steps,
     then K steps timed one by one on the host cores."""
     if rank != 0:
         return 0
+    if is_batch(args.workload):
+        return run_reference_batch(args)
     from oracle import oracle as O
     sysc = workload(args.workload)
     kinds = {"const": O.EPS_CONST, "links": O.EPS_LINKS, "vertices": O.EPS_VERTICES,
@@ -211,14 +362,211 @@ def run_reference(args, world, rank):
 
 
 # --------------------------------------------------------------------- GPU arm
-def run_memd(args, world, rank, local):
+# Algorithmic bytes of the particle kernels per charge (FP32 fields; each word
+# counted once, the cell's links at their minimum): deposition 96 B of state
+# read (x, v, Ft, h, img, q), 84 B written (x, v, img, move record) and 12
+# transfer words added (8 B each); application 24 B of move record and 12
+# links' transfer word (read and cleared), ledger word and D (read and
+# written); gather 84 B read (x, q, v, m, h, sig), 72 B written (F, Ft, v) and
+# D and 1/eps of 12 links.
+def particle_bytes(esz):
+    return {"deposit": 96 + 84 + 12 * 8,
+            "apply": 24 + 12 * (8 + 8 + 8 + 8 + 2 * esz),
+            "gather": 84 + 72 + 12 * 2 * esz}
+
+
+def clock_preroll(step_fn, sync, seconds=1.0, max_steps=20000):
+    """Untimed steps for about `seconds` so that the nvidia-smi sampler (200 ms
+    period) sees the GPU under this load just before the timed steps."""
+    t0 = time.perf_counter()
+    k = 1
+    done = 0
+    while time.perf_counter() - t0 < seconds and done < max_steps:
+        step_fn(k)
+        sync()
+        done += k
+        k = min(2 * k, 1024)
+    return done
+
+
+def batch_line(args, world, rank, local):
+    """The headline: the batched replicas, every replica advanced one step per
+    step, device time of exactly K steps between a barrier and a synchronise
+    on both sides, max over ranks."""
     import torch
-    from paper_1309_7859_gb300.memd import Memd
+    from paper_1309_7859_gb300.memd import Batch, Memd
 
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
     stream = torch.cuda.Stream(device=dev)
-    sysc = workload(args.workload, rank)
+    systems = batch_systems(args.workload, rank)
+    t0 = time.perf_counter()
+    members = []
+    for s in systems:
+        g = Memd(s.mesh, s.box, s.eps, c_light=s.c_light, dt=s.dt, precision=s.precision,
+                 seed=s.seed, stream=stream, time_kernels=False, field_kernel="ldg",
+                 apply_mode=args.apply)
+        g.init_field(s.x, s.q, s.m, s.v)
+        members.append(g)
+    setup_s = time.perf_counter() - t0
+    b = Batch(members, field_kernel=args.batch_kernel)
+    th = systems[0].thermostat
+    sites = sum(s.sites for s in systems)
+    parts = sum(s.n for s in systems)
+    links = 3 * sites
+    ev = (torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+    with torch.cuda.stream(stream):
+        b.step(args.warmup, thermostat=th)
+        b.synchronize()
+        with ClockSampler(local) as clk:
+            pre = clock_preroll(lambda k: b.step(k, thermostat=th), b.synchronize)
+            barrier(world)
+            torch.cuda.synchronize()
+            ev[0].record(stream)
+            b.step(args.steps, thermostat=th)
+            ev[1].record(stream)
+            torch.cuda.synchronize()
+            barrier(world)
+    tot_ms = allmax(ev[0].elapsed_time(ev[1]), world, dev)
+    ks0 = b.kernel_stats()
+    # kernel durations inside the step: the same batch stepped again with an
+    # event pair around each of its launches
+    b.set_timing(True)
+    tsteps = max(20, min(args.steps, 200))
+    with torch.cuda.stream(stream):
+        b.step(3, thermostat=th)
+        b.synchronize()
+        b.kernel_stats()  # reset
+        b.step(tsteps, thermostat=th)
+        b.synchronize()
+    ks = b.kernel_stats()
+    b.set_timing(False)
+    nl = max(1, ks.field_launches)
+    esz = 4 if systems[0].precision == "fp32" else 8
+    pb = particle_bytes(esz)
+    kern = {ks.field_kernel: (ks.field_bytes, ks.field_ms / nl),
+            "k_deposit_batch": (pb["deposit"] * parts, ks.phase_ms[0] / nl),
+            "k_apply_batch": (pb["apply"] * parts, ks.phase_ms[1] / nl),
+            "k_gather_batch": (pb["gather"] * parts, ks.phase_ms[2] / nl)}
+    inst_ms = sum(v[1] for v in kern.values())
+    dom = max(kern, key=lambda k: kern[k][1])
+    dbytes, dms = kern[dom]
+    # end to end through the C ABI: one page-locked block for all replicas,
+    # each step copies every replica's positions, image counters and velocities
+    # in and their state and forces out, with one synchronisation
+    io = b.io_buffers()
+    b.step_io(0, thermostat=th, load=False)
+    e2e_steps = max(1, min(args.steps, 1000))
+    barrier(world)
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        b.step_io(1, thermostat=th, load=True)
+    e2e_s = allmax(time.perf_counter() - t0, world, dev)
+    assert np.all(np.isfinite(io["f"]))
+    h2d = parts * (24 + 24 + 12)
+    d2h = parts * (24 + 24 + 12 + 24) + 4 * len(systems)
+    exact = all(g.energy()["gauss_exact"] == 1.0 for g in members)
+    b.close()
+    for g in members:
+        g.close()
+    hbm, peak_kind = peaks()
+    ach = dbytes / (dms * 1e-3) / 1e9
+    field_ach = ks.field_bytes / (ks.field_ms / nl * 1e-3) / 1e9
+    out = None
+    if rank == 0:
+        traffic = None
+        prof = os.path.join(ROOT, "profiles", "traffic.json")
+        if os.path.exists(prof):
+            try:
+                traffic = json.load(open(prof)).get(dom.split("<")[0] + "@" + args.workload)
+            except Exception:
+                traffic = None
+        out = {
+            "metric": METRIC, "value": world * links * args.steps / (tot_ms * 1e-3),
+            "unit": "link-updates/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": tot_ms / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32" if esz == 4 else "f64", "data": "synthetic",
+            "config": {"workload": batch_name(len(systems)), "replicas": len(systems),
+                       "sites": sites, "charges": parts, "fields": systems[0].precision,
+                       "dt": systems[0].dt,
+                       "thermostat": "langevin gamma=1 kT=1" if th else "none",
+                       "l2": f"inputs larger than L2: fields {ks.field_bytes / 1e6:.0f} MB a "
+                             "step (L2 129 MB), no flush",
+                       "parallelism": f"replicas x{world}" if world > 1 else "one batch",
+                       "clock_window": f"{pre} untimed steps (~1 s) just before the timed "
+                                       "steps, sampled with them"},
+            "particle_steps_per_s": world * parts * args.steps / (tot_ms * 1e-3),
+            "roofline": {"bound": "hbm", "kernel": dom,
+                         "achieved": ach, "peak": hbm, "unit": "GB/s", "frac": ach / hbm,
+                         "peak_kind": peak_kind, "traffic": traffic,
+                         "bytes_per_launch": dbytes, "ms_per_launch": dms,
+                         "note": "dominant kernel of the step by CUDA-event time in an "
+                                 "instrumented run of the same batch (event pair around "
+                                 "each launch)"},
+            "kernels": {k: {"ms_per_launch": v[1], "share": v[1] / inst_ms,
+                            "bytes_per_launch": v[0],
+                            "GBps": v[0] / (v[1] * 1e-3) / 1e9 if v[1] > 0 else None}
+                        for k, v in kern.items()},
+            "field_roofline": {"kernel": ks.field_kernel, "achieved": field_ach, "peak": hbm,
+                               "frac": field_ach / hbm, "bytes_per_launch": ks.field_bytes,
+                               "ms_per_launch": ks.field_ms / nl},
+            "launches_per_step": ks0.launches_per_step,
+            "cpu_baseline": None,
+            "e2e": {"value": world * links * e2e_steps / e2e_s, "unit": "link-updates/s",
+                    "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+                    "api": "memd_batch_step_io: one copy in (every replica's positions, "
+                           "images, velocities), one batch step, one copy out (state and "
+                           "forces), one sync"},
+            "clocks": clk.summary(),
+            "gpu_launches": int(ks0.launches_per_step * args.steps),
+            "setup_s": setup_s,
+            "gauss_exact": bool(exact),
+        }
+        if world == 1 and not args.no_cpu_baseline:
+            out["cpu_baseline"] = oracle_batch_baseline(systems, steps=args.cpu_steps)
+    return out
+
+
+def run_memd(args, world, rank, local):
+    if is_batch(args.workload):
+        out = batch_line(args, world, rank, local)
+        extras = ("slab32", "large", "salt", "validation", "serve", "precision")
+    else:
+        out = single_line(args, world, rank, local, args.workload)
+        extras = ("large", "salt", "validation", "batch", "serve", "precision")
+    if rank != 0 or out is None:
+        return out
+    import torch
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.Stream(device=dev)
+    if "slab32" in extras and args.slab32:
+        out["slab32"] = single_line(args, 1, 0, local, "slab-32", steps=args.single_steps)
+    if "large" in extras and args.large > 0:
+        out["large_mesh"] = large_mesh(args.large, dev, stream, args)
+    if "salt" in extras and args.salt:
+        out["salt"] = stepped_systems(("salt-64",), dev, stream, args)["salt-64"]
+    if "validation" in extras and args.validation:
+        out["validation"] = validation_systems(dev, stream, args)
+    if "batch" in extras and args.batch > 0:
+        out["batched"] = batched(args.batch, dev, args)
+    if "serve" in extras and args.serve > 0:
+        out["served"] = served(args.serve, args)
+    if "precision" in extras and not args.no_cpu_baseline:
+        out["precision_report"] = precision_report(workload("slab-32"))
+    return out
+
+
+def single_line(args, world, rank, local, name, steps=None):
+    """One system stepped alone (L2 flushed before every timed step)."""
+    import torch
+    from paper_1309_7859_gb300.memd import Memd
+
+    steps = steps or args.steps
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.Stream(device=dev)
+    sysc = workload(name, rank)
     # the timed steps run as a user runs them: no timing events inside the
     # step graph (each event node adds a few microseconds to a step)
     g = Memd(sysc.mesh, sysc.box, sysc.eps, c_light=sysc.c_light, dt=sysc.dt,
@@ -234,11 +582,11 @@ def run_memd(args, world, rank, local):
         g.synchronize()
         g.reset_kernel_stats()
         evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
-               for _ in range(args.steps)]
+               for _ in range(steps)]
         barrier(world)
         torch.cuda.synchronize()
         with ClockSampler(local) as clk:
-            for i in range(args.steps):
+            for i in range(steps):
                 flush.fill_(float(i))           # evict the system from L2
                 evs[i][0].record(stream)
                 g.step(1, thermostat=th)
@@ -251,7 +599,7 @@ def run_memd(args, world, rank, local):
     if ks.single:
         # one launch a step: the per-step event time bounds the kernel's
         # duration from above (it includes the launch)
-        field_ms_per_launch = sum(step_ms) / args.steps
+        field_ms_per_launch = sum(step_ms) / steps
     else:
         field_ms_per_launch = field_kernel_ms(sysc, args, dev, stream, flush)
     e = g.energy()
@@ -262,7 +610,7 @@ def run_memd(args, world, rank, local):
     n = sysc.n
     io = g.io_buffers()
     g.step_io(0, thermostat=th, load=False)   # the present state into the buffers
-    e2e_steps = max(1, min(args.steps, 1000))
+    e2e_steps = max(1, min(steps, 1000))
     barrier(world)
     t0 = time.perf_counter()
     for _ in range(e2e_steps):
@@ -274,7 +622,7 @@ def run_memd(args, world, rank, local):
 
     hbm, peak_kind = peaks()
     achieved = ks.field_bytes / (field_ms_per_launch * 1e-3) / 1e9
-    value = world * links * args.steps / (tot_ms * 1e-3)
+    value = world * links * steps / (tot_ms * 1e-3)
     out = None
     if rank == 0:
         traffic = None
@@ -289,7 +637,7 @@ def run_memd(args, world, rank, local):
             cpu = oracle_rate(sysc, args.cpu_seconds)
         out = {
             "metric": METRIC, "value": value, "unit": "link-updates/s", "n_gpus": world,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": tot_ms / args.steps,
+            "steps": steps, "warmup": args.warmup, "ms_per_step": tot_ms / steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "f32" if sysc.precision == "fp32" else "f64", "data": "synthetic",
             "config": {"workload": sysc.name, "mesh": list(sysc.mesh), "charges": sysc.n,
@@ -297,7 +645,7 @@ def run_memd(args, world, rank, local):
                        "thermostat": "langevin gamma=1 kT=1" if th else "none",
                        "l2": "flushed (256 MiB write) before every timed step",
                        "parallelism": f"replicas x{world}" if world > 1 else "single system"},
-            "particle_steps_per_s": world * n * args.steps / (tot_ms * 1e-3),
+            "particle_steps_per_s": world * n * steps / (tot_ms * 1e-3),
             "roofline": {"bound": "hbm",
                          "kernel": ks.field_kernel if ks.single
                          else ks.field_kernel + " (B then D update, one pass)",
@@ -315,22 +663,10 @@ def run_memd(args, world, rank, local):
                     "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                     "api": "memd_step_io: one copy in (positions, images, velocities), one step, one copy out (state and forces), one sync"},
             "clocks": clk.summary(),
-            "gpu_launches": int(ks.launches_per_step * args.steps),
+            "gpu_launches": int(ks.launches_per_step * steps),
             "gauss_exact": bool(e["gauss_exact"]),
         }
     g.close()
-    if rank == 0 and out is not None and args.large > 0:
-        out["large_mesh"] = large_mesh(args.large, dev, stream, args)
-    if rank == 0 and out is not None and args.salt:
-        out["salt"] = stepped_systems(("salt-64",), dev, stream, args)["salt-64"]
-    if rank == 0 and out is not None and args.validation:
-        out["validation"] = validation_systems(dev, stream, args)
-    if rank == 0 and out is not None and args.batch > 0:
-        out["batched"] = batched(args.batch, dev, args)
-    if rank == 0 and out is not None and args.serve > 0:
-        out["served"] = served(args.serve, args)
-    if rank == 0 and out is not None and not args.no_cpu_baseline:
-        out["precision_report"] = precision_report(sysc)
     return out
 
 
@@ -631,15 +967,25 @@ def main():
     ap.add_argument("--steps", type=int, default=20000)
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", default="memd", choices=["memd", "reference"])
-    ap.add_argument("--workload", default="slab-32")
+    ap.add_argument("--workload", default="batch-64",
+                    help="batch-<count> (the default line: 64 replicas), or one system: "
+                         "slab-32, plain-8, salt-64, bigslab-<N>, colloid-64, cloud-wall-32")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--cpu-seconds", type=float, default=10.0)
+    ap.add_argument("--cpu-seconds", type=float, default=10.0,
+                    help="oracle time budget of a single system's cpu_baseline")
+    ap.add_argument("--cpu-steps", type=int, default=10,
+                    help="timed oracle steps of each sample replica of a batch's cpu_baseline")
+    ap.add_argument("--slab32", type=int, default=1,
+                    help="1: beside a batch line, also the single 32^3 slab system (slab32)")
+    ap.add_argument("--single-steps", type=int, default=2000,
+                    help="timed steps of the slab32 object")
     ap.add_argument("--field-kernel", default="auto", choices=["auto", "ldg", "tma", "site"])
     ap.add_argument("--step-engine", default="auto", choices=["auto", "graph", "single"])
     ap.add_argument("--apply", default="auto", choices=["auto", "sparse", "dense"],
                     help="how graph steps and batches apply the charge transfers")
     ap.add_argument("--batch", type=int, default=64,
-                    help="replicas of the extra batched measurement (0: skip)")
+                    help="beside a single-system line: replicas of the extra batched "
+                         "measurement (0: skip)")
     ap.add_argument("--serve", type=int, default=512,
                     help="requests of the extra served-stream measurement (0: skip)")
     ap.add_argument("--serve-rate", type=float, default=40.0)

@@ -145,7 +145,14 @@ typedef struct memd_options {
                              exchange; MEMD_APPLY_DENSE: one pass over every link's
                              transfer word.  Both add each word once, so they give
                              identical results. */
-  int32_t reserved[4];
+  int32_t field_shape[4]; /* 0 everywhere: the field kernel's shape is autotuned.  Else
+                             the shape is fixed: {ty, zchunk, planes_ahead, rows_nt}:
+                             tile height 4, 8 or 16 (16 needs FP32) and z planes per
+                             CTA >= 1 of the LDG, SITE and TMA kernels (SITE: planes
+                             loaded ahead 1 or 2), threads a CTA 256 or 512 of the ROWS
+                             kernel; a value the chosen field_kernel does not use must be
+                             0, and field_kernel must not be AUTO.  Out of range:
+                             INVALID at create. */
 } memd_options;
 
 enum { MEMD_FIELD_AUTO = 0, MEMD_FIELD_LDG = 1, MEMD_FIELD_TMA = 2, MEMD_FIELD_SITE = 3,
@@ -187,6 +194,10 @@ typedef struct memd_kernel_stats {
   int32_t field_tx;       /* tile width in sites (32, or 16 in batches of narrow meshes) */
   int32_t field_rows;     /* batches: nt > 0 when the row kernel runs (nt threads a CTA,
                              persistent grid), 0 for site tiles */
+  int32_t pad;
+  double phase_ms[3];     /* batches with timing on: summed CUDA-event time of the
+                             deposition, the transfer application and the gather
+                             (field_launches of each); 0 otherwise */
 } memd_kernel_stats;
 
 /* Fill *opt with defaults: FP64, GF self term, dipole correction on,
@@ -413,6 +424,32 @@ memd_status memd_batch_create_kernel(int32_t count, memd_ctx *const *members,
  * Asynchronous like memd_step; errors of members are reported by their own
  * synchronising calls and by memd_batch_synchronize. */
 memd_status memd_batch_step(memd_batch *b, int64_t nsteps, const memd_thermostat *th);
+
+/* A host loop over a whole batch.  memd_batch_io_buffers gives the batch's
+ * library-owned page-locked I/O block: positions, velocities, image counters
+ * and electrostatic forces of every member, n_total x 3 each, particle major,
+ * member r's particles at rows offsets[r] .. offsets[r + 1] - 1 (count + 1
+ * offsets, in member order).  The block and the offsets stay valid until the
+ * batch is destroyed or a member's particle count changes (the caller reads
+ * and writes the arrays between calls and never frees them).
+ * memd_batch_step_io is memd_step_io for all members at once: load != 0 takes
+ * positions, image counters and velocities from the block (as
+ * memd_set_particles on each member), then nsteps batch steps, then the
+ * block receives every member's state and forces: one host-to-device copy,
+ * one device-to-host copy and one synchronisation for the whole batch.
+ * Errors: INVALID, STATE (a member not initialised), OOM (page-locked or
+ * device block), CUDA; a member's own error (as memd_step_io reports it). */
+typedef struct memd_batch_io {
+  double *pos;
+  double *vel;
+  int32_t *img;
+  double *f;
+  const int64_t *offsets;
+  int64_t n_total;
+} memd_batch_io;
+memd_status memd_batch_io_buffers(memd_batch *b, memd_batch_io *io);
+memd_status memd_batch_step_io(memd_batch *b, int32_t load, int64_t nsteps,
+                               const memd_thermostat *th);
 
 /* Wait for the batch's work; returns the first member error, if any. */
 memd_status memd_batch_synchronize(memd_batch *b);

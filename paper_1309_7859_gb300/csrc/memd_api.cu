@@ -421,6 +421,28 @@ static memd_status autotune_fused(memd_ctx* c) {
   c->tma_ok = (c->field_kernel == MEMD_FIELD_AUTO || c->field_kernel == MEMD_FIELD_TMA) &&
               tma_supported(c->mesh, c->prec) &&
               tma_make_maps(c->mesh, c->prec, c->Dbuf, c->Bbuf, c->ie, &c->tma);
+  {
+    // a shape fixed at create is taken as it is (checked there); the row
+    // kernel falls back to the default site shape where the mesh does not fit
+    const int* fs = c->field_shape;
+    if (fs[0] || fs[3]) {
+      FusedCfg f = fused_default(c->mesh);
+      if (fs[3]) {
+        if (rows_setup(c, fs[3])) {
+          f.rows = fs[3];
+        } else {
+          f.site = 1;
+        }
+      } else {
+        f.ty = fs[0];
+        f.zchunk = std::min(fs[1], c->mesh.n[2]);
+        f.site = c->field_kernel == MEMD_FIELD_SITE ? fs[2] : 0;
+        f.tma = c->field_kernel == MEMD_FIELD_TMA && c->tma_ok ? 1 : 0;
+      }
+      c->fcfg = f;
+      return MEMD_OK;
+    }
+  }
   const auto key = std::make_tuple(c->mesh.n[0], c->mesh.n[1], c->mesh.n[2], c->prec,
                                    c->field_kernel * 2 + (c->tma_ok ? 1 : 0));
   {
@@ -747,6 +769,22 @@ memd_status memd_create(const int32_t mesh[3], const double box[3], const memd_e
   if (o.field_kernel < MEMD_FIELD_AUTO || o.field_kernel > MEMD_FIELD_ROWS) return MEMD_ERR_INVALID;
   if (o.step_engine < MEMD_STEP_AUTO || o.step_engine > MEMD_STEP_SINGLE) return MEMD_ERR_INVALID;
   if (o.apply_mode < MEMD_APPLY_AUTO || o.apply_mode > MEMD_APPLY_DENSE) return MEMD_ERR_INVALID;
+  {
+    // a fixed field-kernel shape: only the values its kernel uses, in range
+    const int32_t* fs = o.field_shape;
+    const bool any = fs[0] || fs[1] || fs[2] || fs[3];
+    if (any) {
+      const int fk = o.field_kernel;
+      if (fk == MEMD_FIELD_AUTO) return MEMD_ERR_INVALID;
+      if (fk == MEMD_FIELD_ROWS) {
+        if (fs[0] || fs[1] || fs[2] || (fs[3] != 256 && fs[3] != 512)) return MEMD_ERR_INVALID;
+      } else {
+        if (fs[3] || (fs[0] != 4 && fs[0] != 8 && fs[0] != 16) || fs[1] < 1) return MEMD_ERR_INVALID;
+        if (fs[0] == 16 && o.precision != MEMD_FP32) return MEMD_ERR_INVALID;
+        if (fk == MEMD_FIELD_SITE ? (fs[2] != 1 && fs[2] != 2) : fs[2] != 0) return MEMD_ERR_INVALID;
+      }
+    }
+  }
   if (!eps_valid(eps, box, a)) return MEMD_ERR_INVALID;
 
   memd_ctx* c = new memd_ctx();
@@ -784,6 +822,7 @@ memd_status memd_create(const int32_t mesh[3], const double box[3], const memd_e
   c->use_graphs = o.use_graphs;
   c->time_kernels = o.time_kernels;
   c->field_kernel = o.field_kernel;
+  for (int k = 0; k < 4; ++k) c->field_shape[k] = o.field_shape[k];
   c->step_engine = o.step_engine;
   c->apply_mode = o.apply_mode;
   c->alloc = o.alloc;

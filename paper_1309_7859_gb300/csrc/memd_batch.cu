@@ -29,6 +29,7 @@ struct memd_batch {
   cudaStream_t stream = nullptr;
   cudaStream_t side = nullptr;
   cudaEvent_t fork = nullptr, join = nullptr, ev0 = nullptr, ev1 = nullptr;
+  cudaEvent_t evp[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};  // phases
   RepDesc* d_desc = nullptr;
   int* d_field_rep = nullptr;
   int* d_part_rep = nullptr;
@@ -47,11 +48,19 @@ struct memd_batch {
   int2* d_apply_chunk = nullptr;
   int n_apply_chunk = 0;
   cudaGraphExec_t graph[2] = {nullptr, nullptr};
+  // memd_batch_step_io: the members' particle offsets (host and device) and
+  // the I/O block (page-locked host memory and its device mirror)
+  std::vector<int64_t> ioff;
+  int64_t* d_ioff = nullptr;
+  unsigned char* io_host = nullptr;
+  void* io_dev = nullptr;
+  int64_t io_ntot = -1;
   int timing = -1;  // -1: time the field update when member 0 does; 0 / 1: off / on
   int g_thermo = -1;
   double g_gamma = 0.0, g_kT = 0.0;
   bool timing_pending = false;
   double field_ms = 0.0;
+  double phase_ms[3] = {0.0, 0.0, 0.0};  // deposition, transfer application, gather
   long long field_launches = 0;
   std::string last_error;
   // the batch's own tables come from member 0's allocator but are tracked
@@ -112,6 +121,21 @@ void free_tables(memd_batch* b) {
   b->n_rows_ctas = 0;
   b->d_apply_chunk = nullptr;
   b->n_apply_chunk = 0;
+  b->d_ioff = nullptr;
+}
+
+void free_io(memd_batch* b) {
+  if (b->io_host) cudaFreeHost(b->io_host);
+  b->io_host = nullptr;
+  if (b->io_dev) {
+    if (b->free_fn)
+      b->free_fn(b->alloc_user, b->io_dev, (size_t)batch_io_bytes(b->io_ntot, (int)b->m.size()),
+                 (void*)b->stream);
+    else
+      cudaFree(b->io_dev);
+  }
+  b->io_dev = nullptr;
+  b->io_ntot = -1;
 }
 
 // Work of the row kernel: every replica's planes cut into full-width tiles
@@ -167,14 +191,19 @@ memd_status build_tables(memd_batch* b) {
     b->gen[r] = c->gen;
     b->field_bytes += 15.0 * (double)memd_esz(c) * (double)c->mesh.V;
   }
+  b->ioff.assign(R + 1, 0);
+  for (int r = 0; r < R; ++r) b->ioff[r + 1] = b->ioff[r] + b->m[r]->P.n;
   b->bpar = 0;
   b->n_field = (int)frep.size();
   b->n_part = (int)prep.size();
   b->d_desc = (RepDesc*)balloc(b, sizeof(RepDesc) * R);
   b->d_field_rep = (int*)balloc(b, sizeof(int) * std::max(1, b->n_field));
   b->d_part_rep = (int*)balloc(b, sizeof(int) * std::max(1, b->n_part));
-  if (!b->d_desc || !b->d_field_rep || !b->d_part_rep)
+  b->d_ioff = (int64_t*)balloc(b, sizeof(int64_t) * (R + 1));
+  if (!b->d_desc || !b->d_field_rep || !b->d_part_rep || !b->d_ioff)
     return bfail(b, MEMD_ERR_OOM, "batch tables");
+  BCK(cudaMemcpyAsync(b->d_ioff, b->ioff.data(), sizeof(int64_t) * (R + 1),
+                      cudaMemcpyHostToDevice, b->stream));
   BCK(cudaMemcpyAsync(b->d_desc, desc.data(), sizeof(RepDesc) * R, cudaMemcpyHostToDevice,
                       b->stream));
   BCK(cudaMemcpyAsync(b->d_field_rep, frep.data(), sizeof(int) * b->n_field,
@@ -333,24 +362,37 @@ memd_status autotune_batch(memd_batch* b) {
 memd_status record(memd_batch* b, int par, int thermo, double gamma, double kT, bool timed) {
   const cudaStream_t st = b->stream;
   const bool serial = b->field_bytes >= kSerialFieldBytes;
+  // with timing on, an event pair around each launch (on the launch's stream)
+  auto mark = [&](cudaEvent_t e, cudaStream_t s) {
+    return timed ? cudaEventRecordWithFlags(e, s, cudaEventRecordExternal) : cudaSuccess;
+  };
   if (!serial) {
     BCK(cudaEventRecord(b->fork, st));
     BCK(cudaStreamWaitEvent(b->side, b->fork, 0));
+    BCK(mark(b->evp[0], b->side));
     launch_deposit_batch(b->d_desc, b->d_part_rep, b->n_part, thermo, gamma, kT, b->side);
+    BCK(mark(b->evp[1], b->side));
     BCK(cudaEventRecord(b->join, b->side));
   }
-  if (timed) BCK(cudaEventRecordWithFlags(b->ev0, st, cudaEventRecordExternal));
+  BCK(mark(b->ev0, st));
   BCK(launch_field(b, par, st));
-  if (timed) BCK(cudaEventRecordWithFlags(b->ev1, st, cudaEventRecordExternal));
-  if (serial)
+  BCK(mark(b->ev1, st));
+  if (serial) {
+    BCK(mark(b->evp[0], st));
     launch_deposit_batch(b->d_desc, b->d_part_rep, b->n_part, thermo, gamma, kT, st);
-  else
+    BCK(mark(b->evp[1], st));
+  } else {
     BCK(cudaStreamWaitEvent(st, b->join, 0));
+  }
+  BCK(mark(b->evp[2], st));
   if (b->apply_dense)
     launch_apply_dense_batch(b->prec, b->d_desc, b->d_apply_chunk, b->n_apply_chunk, par, st);
   else
     launch_apply_batch(b->prec, b->d_desc, b->d_part_rep, b->n_part, par, st);
+  BCK(mark(b->evp[3], st));
+  BCK(mark(b->evp[4], st));
   launch_gather_batch(b->prec, b->d_desc, b->d_part_rep, b->n_part, par, thermo, gamma, kT, st);
+  BCK(mark(b->evp[5], st));
   BCK(cudaGetLastError());
   return MEMD_OK;
 }
@@ -358,13 +400,56 @@ memd_status record(memd_batch* b, int par, int thermo, double gamma, double kT, 
 void harvest(memd_batch* b) {
   if (!b->timing_pending) return;
   float ms = 0;
-  if (cudaEventSynchronize(b->ev1) == cudaSuccess &&
+  if (cudaEventSynchronize(b->evp[5]) == cudaSuccess &&
       cudaEventElapsedTime(&ms, b->ev0, b->ev1) == cudaSuccess) {
     b->field_ms += ms;
     b->field_launches += 1;
+    for (int k = 0; k < 3; ++k)
+      if (cudaEventElapsedTime(&ms, b->evp[2 * k], b->evp[2 * k + 1]) == cudaSuccess)
+        b->phase_ms[k] += ms;
   }
   cudaGetLastError();
   b->timing_pending = false;
+}
+
+// the I/O block for the members' present particle counts, allocated on
+// first use and after a count change
+memd_status batch_io_block(memd_batch* b) {
+  const int64_t ntot = b->ioff.empty() ? 0 : b->ioff.back();
+  if (b->io_ntot == ntot && b->io_host && b->io_dev) return MEMD_OK;
+  free_io(b);
+  const size_t bytes = (size_t)batch_io_bytes(ntot, (int)b->m.size());
+  if (cudaHostAlloc((void**)&b->io_host, bytes, cudaHostAllocDefault) != cudaSuccess) {
+    cudaGetLastError();
+    b->io_host = nullptr;
+    return bfail(b, MEMD_ERR_OOM, "page-locked batch I/O block");
+  }
+  std::memset(b->io_host, 0, bytes);
+  if (b->alloc) {
+    b->io_dev = b->alloc(b->alloc_user, bytes, (void*)b->stream);
+  } else if (cudaMalloc(&b->io_dev, bytes) != cudaSuccess) {
+    cudaGetLastError();
+    b->io_dev = nullptr;
+  }
+  if (!b->io_dev) {
+    cudaFreeHost(b->io_host);
+    b->io_host = nullptr;
+    return bfail(b, MEMD_ERR_OOM, "device batch I/O block");
+  }
+  b->io_ntot = ntot;
+  return MEMD_OK;
+}
+
+// tables current for the members' present state (rebuilt when a member was
+// re-initialised or stepped alone since they were built)
+memd_status batch_refresh(memd_batch* b) {
+  bool stale = false;
+  for (size_t r = 0; r < b->m.size(); ++r) {
+    memd_ctx* c = b->m[r];
+    if (!c->initialised) return bfail(b, MEMD_ERR_STATE, "a member is not initialised");
+    if (c->gen != b->gen[r] || c->cur != ((b->base[r] + b->bpar) & 1)) stale = true;
+  }
+  return stale ? build_tables(b) : MEMD_OK;
 }
 
 }  // namespace
@@ -398,7 +483,12 @@ memd_status memd_batch_create_opt(int32_t count, memd_ctx* const* members, memd_
       cudaStreamCreateWithFlags(&b->side, cudaStreamNonBlocking) != cudaSuccess ||
       cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming) != cudaSuccess ||
       cudaEventCreateWithFlags(&b->join, cudaEventDisableTiming) != cudaSuccess ||
-      cudaEventCreate(&b->ev0) != cudaSuccess || cudaEventCreate(&b->ev1) != cudaSuccess) {
+      cudaEventCreate(&b->ev0) != cudaSuccess || cudaEventCreate(&b->ev1) != cudaSuccess ||
+      [&] {
+        for (auto& e : b->evp)
+          if (cudaEventCreate(&e) != cudaSuccess) return true;
+        return false;
+      }()) {
     s = MEMD_ERR_CUDA;
   } else {
     // members' own queued work comes first
@@ -424,10 +514,13 @@ void memd_batch_destroy(memd_batch* b) {
   if (b->stream) cudaStreamSynchronize(b->stream);
   drop(b);
   free_tables(b);
+  free_io(b);
   if (b->fork) cudaEventDestroy(b->fork);
   if (b->join) cudaEventDestroy(b->join);
   if (b->ev0) cudaEventDestroy(b->ev0);
   if (b->ev1) cudaEventDestroy(b->ev1);
+  for (auto& e : b->evp)
+    if (e) cudaEventDestroy(e);
   if (b->side) cudaStreamDestroy(b->side);
   delete b;
 }
@@ -450,14 +543,8 @@ memd_status memd_batch_step(memd_batch* b, int64_t nsteps, const memd_thermostat
   if (nsteps < 0) return bfail(b, MEMD_ERR_INVALID, "negative step count");
   BCK(cudaSetDevice(b->device));
   // members re-initialised or stepped on their own since the tables were built
-  bool stale = false;
-  for (size_t r = 0; r < b->m.size(); ++r) {
-    memd_ctx* c = b->m[r];
-    if (!c->initialised) return bfail(b, MEMD_ERR_STATE, "a member is not initialised");
-    if (c->gen != b->gen[r] || c->cur != ((b->base[r] + b->bpar) & 1)) stale = true;
-  }
-  if (stale) {
-    memd_status s = build_tables(b);
+  {
+    const memd_status s = batch_refresh(b);
     if (s != MEMD_OK) return s;
   }
   const int thermo = th ? 1 : 0;
@@ -520,6 +607,57 @@ memd_status memd_batch_set_timing(memd_batch* b, int32_t on) {
   return MEMD_OK;
 }
 
+memd_status memd_batch_io_buffers(memd_batch* b, memd_batch_io* io) {
+  if (!b || !io) return MEMD_ERR_INVALID;
+  BCK(cudaSetDevice(b->device));
+  memd_status s = batch_refresh(b);
+  if (s == MEMD_OK) s = batch_io_block(b);
+  if (s != MEMD_OK) return s;
+  const IoLayout L = io_layout(b->io_ntot);
+  io->pos = (double*)(b->io_host + L.pos);
+  io->vel = (double*)(b->io_host + L.vel);
+  io->img = (int32_t*)(b->io_host + L.img);
+  io->f = (double*)(b->io_host + L.f);
+  io->offsets = b->ioff.data();
+  io->n_total = b->io_ntot;
+  return MEMD_OK;
+}
+
+memd_status memd_batch_step_io(memd_batch* b, int32_t load, int64_t nsteps,
+                               const memd_thermostat* th) {
+  memd::NvtxRange nvtx_("memd_batch_step_io");
+  if (!b) return MEMD_ERR_INVALID;
+  if (nsteps < 0) return bfail(b, MEMD_ERR_INVALID, "negative step count");
+  BCK(cudaSetDevice(b->device));
+  memd_status s = batch_refresh(b);
+  if (s == MEMD_OK) s = batch_io_block(b);
+  if (s != MEMD_OK) return s;
+  const int R = (int)b->m.size();
+  const int64_t ntot = b->io_ntot;
+  const IoLayout L = io_layout(ntot);
+  const cudaStream_t st = b->stream;
+  if (load && ntot > 0) {
+    // positions, velocities and image counters of every member: one copy
+    BCK(cudaMemcpyAsync(b->io_dev, b->io_host, (size_t)L.f, cudaMemcpyHostToDevice, st));
+    launch_io_unpack_batch(b->d_desc, b->d_ioff, R, ntot, b->io_dev, st);
+    BCK(cudaGetLastError());
+  }
+  s = memd_batch_step(b, nsteps, th);
+  if (s != MEMD_OK) return s;
+  launch_io_pack_batch(b->d_desc, b->d_ioff, R, ntot, b->io_dev, st);
+  BCK(cudaGetLastError());
+  BCK(cudaMemcpyAsync(b->io_host, b->io_dev, (size_t)batch_io_bytes(ntot, R),
+                      cudaMemcpyDeviceToHost, st));
+  BCK(cudaStreamSynchronize(st));
+  const unsigned int* err = (const unsigned int*)(b->io_host + L.err);
+  for (int r = 0; r < R; ++r)
+    if (err[r]) {
+      const memd_status e = memd_check_err(b->m[r]);
+      if (e != MEMD_OK) return bfail(b, e, b->m[r]->last_error);
+    }
+  return MEMD_OK;
+}
+
 memd_status memd_batch_kernel_stats(memd_batch* b, memd_kernel_stats* out) {
   if (!b || !out) return MEMD_ERR_INVALID;
   harvest(b);
@@ -535,6 +673,10 @@ memd_status memd_batch_kernel_stats(memd_batch* b, memd_kernel_stats* out) {
   out->field_zchunk = b->f_z;
   out->field_site = b->f_rows > 0 ? 0 : b->f_pf;
   out->field_rows = b->f_rows;
+  for (int k = 0; k < 3; ++k) {
+    out->phase_ms[k] = b->phase_ms[k];
+    b->phase_ms[k] = 0.0;
+  }
   b->field_ms = 0.0;
   b->field_launches = 0;
   return MEMD_OK;

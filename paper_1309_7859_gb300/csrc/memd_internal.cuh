@@ -294,6 +294,16 @@ cudaError_t launch_rows_batch(int prec, const RepDesc* desc, const RowSeg* segs,
 // field update of every replica (memd_field.cu)
 void launch_fused_batch(int prec, const RepDesc* desc, const int* cta_rep, int nctas, int par,
                         int ty, int pf, int tw, cudaStream_t st);
+// the batch's host I/O block (memd_batch_step_io): the members' particles in
+// order, member r from entry off[r] of ntot = off[count]; io_layout(ntot),
+// with count error words at its err offset
+inline int64_t batch_io_bytes(int64_t ntot, int count) {
+  return io_layout(ntot).err + 4 * (((int64_t)count + 1) / 2) * 2;
+}
+void launch_io_unpack_batch(const RepDesc* desc, const int64_t* off, int count, int64_t ntot,
+                            const void* io, cudaStream_t st);
+void launch_io_pack_batch(const RepDesc* desc, const int64_t* off, int count, int64_t ntot,
+                          void* io, cudaStream_t st);
 // particle kernels of every replica (memd_particles.cu); thermostat from the arguments
 void launch_deposit_batch(const RepDesc* desc, const int* cta_rep, int nctas, int thermo,
                           double gamma, double kT, cudaStream_t st);

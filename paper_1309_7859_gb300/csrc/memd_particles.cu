@@ -1102,17 +1102,17 @@ __global__ void __launch_bounds__(kRedThreads)
 // doubles each), image counters (n x 3 ints, padded to 8 bytes), forces
 // (n x 3 doubles), the error word.  unpack loads a state from it (positions
 // folded as at init), pack writes the state and forces back into it.
-__global__ void k_io_unpack(Mesh m, Particles P, const unsigned char* __restrict__ io,
-                            unsigned int* err) {
-  const int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (p >= P.n) return;
-  const IoLayout L = io_layout(P.n);
+// particle p of a system from block entry e (the same index for a single
+// system; the system's offset plus p in a batch block)
+__device__ inline void io_unpack_one(const Mesh& m, Particles P, const IoLayout& L,
+                                     const unsigned char* __restrict__ io, int64_t p, int64_t e,
+                                     unsigned int* err) {
   const double* pos = reinterpret_cast<const double*>(io + L.pos);
   const double* vel = reinterpret_cast<const double*>(io + L.vel);
   const int* img = reinterpret_cast<const int*>(io + L.img);
   for (int d = 0; d < 3; ++d) {
-    double x = pos[3 * p + d];
-    int k = img[3 * p + d];
+    double x = pos[3 * e + d];
+    int k = img[3 * e + d];
     if (!(fabs(x) <= 4.0 * m.L[d])) {
       atomicOr(err, kErrNonFinite);
       x = 0.0;
@@ -1120,8 +1120,29 @@ __global__ void k_io_unpack(Mesh m, Particles P, const unsigned char* __restrict
     fold(m.L[d], x, k);
     P.x[3 * p + d] = x;
     P.img[3 * p + d] = k;
-    P.v[3 * p + d] = vel[3 * p + d];
+    P.v[3 * p + d] = vel[3 * e + d];
   }
+}
+
+__device__ inline void io_pack_one(Particles P, const IoLayout& L, unsigned char* __restrict__ io,
+                                   int64_t p, int64_t e) {
+  double* pos = reinterpret_cast<double*>(io + L.pos);
+  double* vel = reinterpret_cast<double*>(io + L.vel);
+  int* img = reinterpret_cast<int*>(io + L.img);
+  double* f = reinterpret_cast<double*>(io + L.f);
+  for (int d = 0; d < 3; ++d) {
+    pos[3 * e + d] = P.x[3 * p + d];
+    vel[3 * e + d] = P.v[3 * p + d];
+    img[3 * e + d] = P.img[3 * p + d];
+    f[3 * e + d] = P.F[3 * p + d];
+  }
+}
+
+__global__ void k_io_unpack(Mesh m, Particles P, const unsigned char* __restrict__ io,
+                            unsigned int* err) {
+  const int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (p >= P.n) return;
+  io_unpack_one(m, P, io_layout(P.n), io, p, p, err);
 }
 
 __global__ void k_io_pack(Particles P, unsigned char* __restrict__ io,
@@ -1130,16 +1151,47 @@ __global__ void k_io_pack(Particles P, unsigned char* __restrict__ io,
   const IoLayout L = io_layout(P.n);
   if (p == 0) *reinterpret_cast<unsigned int*>(io + L.err) = *err;
   if (p >= P.n) return;
-  double* pos = reinterpret_cast<double*>(io + L.pos);
-  double* vel = reinterpret_cast<double*>(io + L.vel);
-  int* img = reinterpret_cast<int*>(io + L.img);
-  double* f = reinterpret_cast<double*>(io + L.f);
-  for (int d = 0; d < 3; ++d) {
-    pos[3 * p + d] = P.x[3 * p + d];
-    vel[3 * p + d] = P.v[3 * p + d];
-    img[3 * p + d] = P.img[3 * p + d];
-    f[3 * p + d] = P.F[3 * p + d];
+  io_pack_one(P, L, io, p, p);
+}
+
+// The batch block: the members' particles one after another (member r from
+// entry off[r]), laid out as one system of off[count] particles, the error
+// words of the members after it.  Entry e belongs to the member r with
+// off[r] <= e < off[r + 1] (binary search over count + 1 offsets).
+__device__ inline int io_member(const int64_t* __restrict__ off, int count, int64_t e) {
+  int lo = 0, hi = count;  // off[lo] <= e < off[hi]
+  while (hi - lo > 1) {
+    const int mid = (lo + hi) >> 1;
+    if (off[mid] <= e)
+      lo = mid;
+    else
+      hi = mid;
   }
+  return lo;
+}
+
+__global__ void k_io_unpack_batch(const RepDesc* __restrict__ desc,
+                                  const int64_t* __restrict__ off, int count,
+                                  const unsigned char* __restrict__ io) {
+  const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  const int64_t ntot = off[count];
+  if (e >= ntot) return;
+  const int r = io_member(off, count, e);
+  const RepDesc& d = desc[r];
+  io_unpack_one(d.m, d.P, io_layout(ntot), io, e - off[r], e, &d.ds->err);
+}
+
+__global__ void k_io_pack_batch(const RepDesc* __restrict__ desc,
+                                const int64_t* __restrict__ off, int count,
+                                unsigned char* __restrict__ io) {
+  const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  const int64_t ntot = off[count];
+  const IoLayout L = io_layout(ntot);
+  if (e < count)
+    reinterpret_cast<unsigned int*>(io + L.err)[e] = desc[e].ds->err;
+  if (e >= ntot) return;
+  const int r = io_member(off, count, e);
+  io_pack_one(desc[r].P, L, io, e - off[r], e);
 }
 
 void launch_io_unpack(const Mesh& m, Particles p, const void* io, unsigned int* err,
@@ -1150,6 +1202,19 @@ void launch_io_unpack(const Mesh& m, Particles p, const void* io, unsigned int* 
 
 void launch_io_pack(Particles p, void* io, const unsigned int* err, cudaStream_t st) {
   k_io_pack<<<blocks_for(p.n > 0 ? p.n : 1), kThreads, 0, st>>>(p, (unsigned char*)io, err);
+}
+
+void launch_io_unpack_batch(const RepDesc* desc, const int64_t* off, int count, int64_t ntot,
+                            const void* io, cudaStream_t st) {
+  if (ntot > 0)
+    k_io_unpack_batch<<<blocks_for(ntot), kThreads, 0, st>>>(desc, off, count,
+                                                            (const unsigned char*)io);
+}
+
+void launch_io_pack_batch(const RepDesc* desc, const int64_t* off, int count, int64_t ntot,
+                          void* io, cudaStream_t st) {
+  k_io_pack_batch<<<blocks_for(ntot > count ? ntot : count), kThreads, 0, st>>>(
+      desc, off, count, (unsigned char*)io);
 }
 
 void launch_fold_init(const Mesh& m, Particles p, const double* pos_in, const int* img_in,

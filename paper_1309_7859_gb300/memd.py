@@ -33,7 +33,7 @@ EXPORTS = ("memd_default_options", "memd_status_string", "memd_last_error", "mem
            "memd_get_setup",
            "memd_get_kernel_stats", "memd_reset_kernel_stats", "memd_synchronize",
            "memd_batch_create", "memd_batch_create_kernel", "memd_batch_step",
-           "memd_batch_synchronize",
+           "memd_batch_synchronize", "memd_batch_io_buffers", "memd_batch_step_io",
            "memd_batch_kernel_stats", "memd_batch_set_timing", "memd_batch_destroy",
            "memd_server_default_options",
            "memd_server_create", "memd_server_destroy", "memd_server_submit", "memd_server_pump",
@@ -67,7 +67,7 @@ class Options(C.Structure):
                 ("alloc", ALLOC), ("free", FREE), ("alloc_user", C.c_void_p),
                 ("time_kernels", C.c_int32), ("field_kernel", C.c_int32),
                 ("step_engine", C.c_int32), ("apply_mode", C.c_int32),
-                ("reserved", C.c_int32 * 4)]
+                ("field_shape", C.c_int32 * 4)]
 
 
 class Thermostat(C.Structure):
@@ -117,12 +117,18 @@ class IoBuffers(C.Structure):
                 ("img", C.POINTER(C.c_int32)), ("f", C.POINTER(C.c_double))]
 
 
+class BatchIo(C.Structure):
+    _fields_ = [("pos", C.POINTER(C.c_double)), ("vel", C.POINTER(C.c_double)),
+                ("img", C.POINTER(C.c_int32)), ("f", C.POINTER(C.c_double)),
+                ("offsets", C.POINTER(C.c_int64)), ("n_total", C.c_int64)]
+
+
 class KernelStats(C.Structure):
     _fields_ = [("field_ms", C.c_double), ("field_launches", C.c_int64),
                 ("field_bytes", C.c_double), ("launches_per_step", C.c_int64),
                 ("field_tma", C.c_int32), ("field_ty", C.c_int32), ("field_zchunk", C.c_int32),
                 ("field_site", C.c_int32), ("step_single", C.c_int32), ("field_tx", C.c_int32),
-                ("field_rows", C.c_int32)]
+                ("field_rows", C.c_int32), ("pad", C.c_int32), ("phase_ms", C.c_double * 3)]
 
 
 _lib = None
@@ -178,6 +184,8 @@ def lib(build_if_missing=True):
     L.memd_batch_create_kernel.argtypes = [C.c_int32, C.POINTER(vp), C.c_int32, C.POINTER(vp)]
     L.memd_batch_step.argtypes = [vp, C.c_int64, C.POINTER(Thermostat)]
     L.memd_batch_synchronize.argtypes = [vp]
+    L.memd_batch_io_buffers.argtypes = [vp, C.POINTER(BatchIo)]
+    L.memd_batch_step_io.argtypes = [vp, C.c_int32, C.c_int64, C.POINTER(Thermostat)]
     L.memd_batch_kernel_stats.argtypes = [vp, C.POINTER(KernelStats)]
     L.memd_batch_set_timing.argtypes = [vp, C.c_int32]
     L.memd_batch_destroy.argtypes = [vp]
@@ -266,6 +274,7 @@ class StepTiming:
     launches_per_step: int
     field_kernel: str = ""
     single: bool = False
+    phase_ms: tuple = (0.0, 0.0, 0.0)  # batches: deposition, transfer application, gather
 
 
 class Memd:
@@ -274,7 +283,8 @@ class Memd:
     def __init__(self, mesh, box, eps=None, c_light=1.0, dt=0.01, precision="fp64",
                  self_mode=SELF_GF, dipole_corr=True, relax_tol=1e-12, relax_max_iter=200000,
                  seed=0, use_graphs=True, time_kernels=False, use_torch=True, stream=None,
-                 device=None, field_kernel="auto", step_engine="auto", apply_mode="auto"):
+                 device=None, field_kernel="auto", step_engine="auto", apply_mode="auto",
+                 field_shape=None):
         self._L = lib()
         _live["memd"].add(self)
         self._h = C.c_void_p(None)
@@ -295,6 +305,9 @@ class Memd:
         o.field_kernel = {"auto": 0, "ldg": 1, "tma": 2, "site": 3, "rows": 4}[field_kernel]
         o.step_engine = {"auto": 0, "graph": 1, "single": 2}[step_engine]
         o.apply_mode = {"auto": 0, "sparse": 1, "dense": 2}[apply_mode]
+        if field_shape is not None:   # (ty, zchunk, planes_ahead, rows_nt), 0 = unused
+            for k, v in enumerate(field_shape):
+                o.field_shape[k] = int(v)
         self._alloc = None
         self._stream = stream
         if use_torch:
@@ -547,6 +560,32 @@ class Batch:
         if st != 0:
             raise MemdError(st, "memd_batch_synchronize failed")
 
+    def io_buffers(self):
+        """The batch's page-locked I/O block as (n_total, 3) numpy views pos,
+        vel, img (in and out) and f (out), plus the members' row offsets
+        (count + 1)."""
+        io = BatchIo()
+        st = self._L.memd_batch_io_buffers(self._h, C.byref(io))
+        if st != 0:
+            raise MemdError(st, "memd_batch_io_buffers failed")
+        n = io.n_total
+        view = lambda p: np.ctypeslib.as_array(p, shape=(n, 3)) if n else np.zeros((0, 3))
+        off = np.ctypeslib.as_array(io.offsets, shape=(len(self.members) + 1,)).copy()
+        return {"pos": view(io.pos), "vel": view(io.vel), "img": view(io.img), "f": view(io.f),
+                "offsets": off}
+
+    def step_io(self, nsteps=1, thermostat=None, load=True):
+        """memd_batch_step_io: every member's state from the I/O block (load),
+        nsteps batch steps, state and forces back into it; one copy each way,
+        one synchronisation."""
+        th = None
+        if thermostat is not None:
+            th = Thermostat(float(thermostat[0]), float(thermostat[1]))
+        st = self._L.memd_batch_step_io(self._h, 1 if load else 0, int(nsteps),
+                                        C.byref(th) if th else None)
+        if st != 0:
+            raise MemdError(st, "memd_batch_step_io failed")
+
     def set_timing(self, on):
         """CUDA events around the batched field update in the step graph."""
         st = self._L.memd_batch_set_timing(self._h, 1 if on else 0)
@@ -561,7 +600,8 @@ class Batch:
         name = (f"k_rows_batch<nt={k.field_rows}>" if k.field_rows else
                 f"k_fused_site_batch<tx={k.field_tx}, ty={k.field_ty}, zchunk={k.field_zchunk}, "
                 f"planes_ahead={k.field_site}>")
-        return StepTiming(k.field_ms, k.field_launches, k.field_bytes, k.launches_per_step, name)
+        return StepTiming(k.field_ms, k.field_launches, k.field_bytes, k.launches_per_step, name,
+                          False, tuple(k.phase_ms))
 
     def close(self):
         if self._h:

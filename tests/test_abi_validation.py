@@ -20,7 +20,11 @@ def create(mesh=(8, 8, 8), box=(8.0, 8.0, 8.0), kind=0, axis=0, params=(1.0,), v
     o = M.Options()
     L.memd_default_options(C.byref(o))
     for k, v in opts.items():
-        setattr(o, k, v)
+        if k == "field_shape":
+            for i, x in enumerate(v):
+                o.field_shape[i] = x
+        else:
+            setattr(o, k, v)
     e = M.EpsProfile()
     e.kind, e.axis = kind, axis
     for i, p in enumerate(params):
@@ -51,6 +55,14 @@ def create(mesh=(8, 8, 8), box=(8.0, 8.0, 8.0), kind=0, axis=0, params=(1.0,), v
     (dict(kind=1), INVALID),                                        # per-link eps without values
     (dict(kind=6, params=(80.0, 2.0, 4.0, 4.0, 4.0, 4.5)), INVALID),       # ball wider than the box
     (dict(kind=99), INVALID),                                       # unknown profile
+    (dict(field_shape=(8, 4, 0, 0)), INVALID),                      # a fixed shape needs a kernel
+    (dict(field_kernel=4, field_shape=(0, 0, 0, 384)), INVALID),    # rows: 256 or 512 threads
+    (dict(field_kernel=4, field_shape=(8, 0, 0, 256)), INVALID),    # rows use no tile height
+    (dict(field_kernel=3, field_shape=(6, 4, 1, 0)), INVALID),      # no such tile height
+    (dict(field_kernel=3, field_shape=(8, 0, 1, 0)), INVALID),      # no planes per CTA
+    (dict(field_kernel=3, field_shape=(8, 4, 3, 0)), INVALID),      # 1 or 2 planes ahead
+    (dict(field_kernel=1, field_shape=(8, 4, 1, 0)), INVALID),      # halo loops load no planes ahead
+    (dict(field_kernel=3, field_shape=(16, 4, 1, 0)), INVALID),     # 16 rows need FP32
 ])
 def test_create_refuses_bad_arguments_before_touching_the_gpu(args, status):
     st, h = create(**args)
