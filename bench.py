@@ -429,28 +429,52 @@ def batch_line(args, world, rank, local):
             barrier(world)
     tot_ms = allmax(ev[0].elapsed_time(ev[1]), world, dev)
     ks0 = b.kernel_stats()
-    # kernel durations inside the step: the same batch stepped again with an
-    # event pair around each of its launches
-    b.set_timing(True)
-    tsteps = max(20, min(args.steps, 200))
-    with torch.cuda.stream(stream):
-        b.step(3, thermostat=th)
-        b.synchronize()
-        b.kernel_stats()  # reset
-        b.step(tsteps, thermostat=th)
-        b.synchronize()
-    ks = b.kernel_stats()
-    b.set_timing(False)
-    nl = max(1, ks.field_launches)
     esz = 4 if systems[0].precision == "fp32" else 8
     pb = particle_bytes(esz)
-    kern = {ks.field_kernel: (ks.field_bytes, ks.field_ms / nl),
-            "k_deposit_batch": (pb["deposit"] * parts, ks.phase_ms[0] / nl),
-            "k_apply_batch": (pb["apply"] * parts, ks.phase_ms[1] / nl),
-            "k_gather_batch": (pb["gather"] * parts, ks.phase_ms[2] / nl)}
+
+    def instrumented():
+        """Kernel durations inside the step: the same batch stepped again with
+        an event pair around each of its launches."""
+        b.set_timing(True)
+        tsteps = max(20, min(args.steps, 200))
+        with torch.cuda.stream(stream):
+            b.step(3, thermostat=th)
+            b.synchronize()
+            b.kernel_stats()  # reset
+            b.step(tsteps, thermostat=th)
+            b.synchronize()
+        k = b.kernel_stats()
+        b.set_timing(False)
+        n = max(1, k.field_launches)
+        if k.single:
+            # one launch a step: its bytes are the field pass and every
+            # charge's particle work
+            return k, {k.field_kernel: (k.field_bytes + sum(pb.values()) * parts,
+                                        k.field_ms / n)}
+        return k, {k.field_kernel: (k.field_bytes, k.field_ms / n),
+                   "k_deposit_batch": (pb["deposit"] * parts, k.phase_ms[0] / n),
+                   "k_apply_batch": (pb["apply"] * parts, k.phase_ms[1] / n),
+                   "k_gather_batch": (pb["gather"] * parts, k.phase_ms[2] / n)}
+
+    ks, kern = instrumented()
+    graph_kern = None
+    if ks.single:
+        # the same batch as a graph of four kernels, for the breakdown
+        b.set_engine("graph")
+        gks, graph_kern = instrumented()
+        b.set_engine("auto")
+    else:
+        gks = ks
+    nl = max(1, gks.field_launches)
     inst_ms = sum(v[1] for v in kern.values())
     dom = max(kern, key=lambda k: kern[k][1])
     dbytes, dms = kern[dom]
+
+    def table(kk):
+        tot = sum(v[1] for v in kk.values())
+        return {k: {"ms_per_launch": v[1], "share": v[1] / tot, "bytes_per_launch": v[0],
+                    "GBps": v[0] / (v[1] * 1e-3) / 1e9 if v[1] > 0 else None}
+                for k, v in kk.items()}
     # end to end through the C ABI: one page-locked block for all replicas,
     # each step copies every replica's positions, image counters and velocities
     # in and their state and forces out, with one synchronisation
@@ -471,7 +495,7 @@ def batch_line(args, world, rank, local):
         g.close()
     hbm, peak_kind = peaks()
     ach = dbytes / (dms * 1e-3) / 1e9
-    field_ach = ks.field_bytes / (ks.field_ms / nl * 1e-3) / 1e9
+    field_ach = gks.field_bytes / (gks.field_ms / nl * 1e-3) / 1e9
     out = None
     if rank == 0:
         traffic = None
@@ -501,16 +525,22 @@ def batch_line(args, world, rank, local):
                          "achieved": ach, "peak": hbm, "unit": "GB/s", "frac": ach / hbm,
                          "peak_kind": peak_kind, "traffic": traffic,
                          "bytes_per_launch": dbytes, "ms_per_launch": dms,
-                         "note": "dominant kernel of the step by CUDA-event time in an "
+                         "note": ("the whole step is one launch: bytes are the field pass "
+                                  "(60 B a site) and every charge's particle work "
+                                  f"({sum(pb.values())} B a charge); duration from a CUDA-event "
+                                  "pair around the launch in an instrumented run")
+                         if ks.single else
+                                 "dominant kernel of the step by CUDA-event time in an "
                                  "instrumented run of the same batch (event pair around "
                                  "each launch)"},
-            "kernels": {k: {"ms_per_launch": v[1], "share": v[1] / inst_ms,
-                            "bytes_per_launch": v[0],
-                            "GBps": v[0] / (v[1] * 1e-3) / 1e9 if v[1] > 0 else None}
-                        for k, v in kern.items()},
-            "field_roofline": {"kernel": ks.field_kernel, "achieved": field_ach, "peak": hbm,
-                               "frac": field_ach / hbm, "bytes_per_launch": ks.field_bytes,
-                               "ms_per_launch": ks.field_ms / nl},
+            "engine": "single launch" if ks.single else "graph of four kernels",
+            "kernels": table(kern),
+            "graph_kernels": table(graph_kern) if graph_kern else None,
+            "field_roofline": {"kernel": gks.field_kernel, "achieved": field_ach, "peak": hbm,
+                               "frac": field_ach / hbm, "bytes_per_launch": gks.field_bytes,
+                               "ms_per_launch": gks.field_ms / nl,
+                               "note": "the batch's field kernel in the graph of four "
+                                       "kernels (event pair around it)"},
             "launches_per_step": ks0.launches_per_step,
             "cpu_baseline": None,
             "e2e": {"value": world * links * e2e_steps / e2e_s, "unit": "link-updates/s",

@@ -451,6 +451,27 @@ memd_status memd_batch_io_buffers(memd_batch *b, memd_batch_io *io);
 memd_status memd_batch_step_io(memd_batch *b, int32_t load, int64_t nsteps,
                                const memd_thermostat *th);
 
+/* How the batch steps.  MEMD_STEP_GRAPH: the graph of four kernels above.
+ * MEMD_STEP_SINGLE: the whole step of every member in one cooperative launch
+ * of persistent CTAs that claim work items from device queues: field
+ * segments (row tiles over ranges of planes), deposition, transfer
+ * application and gather chunks; a member's application chunks start as soon
+ * as its own field segments and deposition chunks are done and its gather
+ * chunks as soon as its application chunks are, so particle work of some
+ * members overlaps the field update of others, with no grid-wide barrier.
+ * Every member must fit the row tiles (x extent a multiple of 4 sites for
+ * FP32, 2 for FP64), else INVALID.  MEMD_STEP_AUTO (the default): the graph,
+ * the faster of the two on the batches measured (the single launch holds its
+ * CTAs to the row tiles' shared memory and registers, 16 warps an SM, too few
+ * to hide the latency of the particle work).  field_ctas: CTAs that start with
+ * field segments (-1: half the grid; the others start with deposition);
+ * item_planes: planes per field segment (0: about one segment per CTA).
+ * Both engines give identical results.  A wait in the single launch is
+ * bounded (0.5 s): when one runs out, memd_batch_synchronize reports
+ * MEMD_ERR_TIMEOUT and the step is void.  Errors: INVALID, OOM, CUDA. */
+memd_status memd_batch_set_engine(memd_batch *b, int32_t engine, int32_t field_ctas,
+                                  int32_t item_planes);
+
 /* Wait for the batch's work; returns the first member error, if any. */
 memd_status memd_batch_synchronize(memd_batch *b);
 

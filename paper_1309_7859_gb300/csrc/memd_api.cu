@@ -179,6 +179,13 @@ void drop_graphs(memd_ctx* c) {
 
 double* scal(memd_ctx* c) { return c->red + 4 * reduce_blocks(); }
 
+// zero the transfer words (every kLT-th word) of a buffer, leaving the
+// ledger words between them
+cudaError_t clear_transfers(memd_ctx* c, long long* T, cudaStream_t st) {
+  launch_clear_transfers(T, 3 * c->mesh.V, st);
+  return cudaGetLastError();
+}
+
 }  // namespace
 
 // ------------------------------------------------------------------ relaxation
@@ -846,8 +853,9 @@ memd_status memd_create(const int32_t mesh[3], const double box[3], const memd_e
   }
   c->ie = dalloc(c, n3 * esz(c));
   c->ie64 = (double*)dalloc(c, n3 * sizeof(double));
-  c->Lg = (long long*)dalloc(c, n3 * sizeof(long long));
-  c->Tb = (long long*)dalloc(c, n3 * sizeof(long long));
+  // transfer and ledger words interleaved (kLT): one block of 2 x 3V words
+  c->Tb = (long long*)dalloc(c, kLT * n3 * sizeof(long long));
+  c->Lg = c->Tb ? c->Tb + 1 : nullptr;
   c->ds = (DevState*)dalloc(c, sizeof(DevState));
   c->red = (double*)dalloc(c, sizeof(double) * (4 * reduce_blocks() + 32 + green_partials()));
   double* Gdev = nullptr;
@@ -861,8 +869,7 @@ memd_status memd_create(const int32_t mesh[3], const double box[3], const memd_e
       cudaMemsetAsync(c->Dbuf[1], 0, n3 * esz(c), st) != cudaSuccess ||
       cudaMemsetAsync(c->Bbuf[0], 0, n3 * esz(c), st) != cudaSuccess ||
       cudaMemsetAsync(c->Bbuf[1], 0, n3 * esz(c), st) != cudaSuccess ||
-      cudaMemsetAsync(c->Lg, 0, n3 * sizeof(long long), st) != cudaSuccess ||
-      cudaMemsetAsync(c->Tb, 0, n3 * sizeof(long long), st) != cudaSuccess) {
+      cudaMemsetAsync(c->Tb, 0, kLT * n3 * sizeof(long long), st) != cudaSuccess) {
     s = fail(c, MEMD_ERR_CUDA, "memset");
     goto done;
   }
@@ -912,6 +919,7 @@ static void free_particles(memd_ctx* c) {
   dfree(c, c->P.mv);
   dfree(c, c->P.h);
   dfree(c, c->P.sig);
+  dfree(c, c->P.gm);
   dfree(c, c->pin);
   c->pin = nullptr;
   if (c->io_host) cudaFreeHost(c->io_host);
@@ -960,13 +968,14 @@ memd_status memd_init_field(memd_ctx* c, int64_t n, const double* pos, const int
   c->P.Ft = (double*)dalloc(c, 3 * nn * sizeof(double));
   c->P.img = (int*)dalloc(c, 3 * nn * sizeof(int));
   c->P.q = (int*)dalloc(c, nn * sizeof(int));
-  c->P.mv = (int*)dalloc(c, 6 * nn * sizeof(int));
+  c->P.mv = (int*)dalloc(c, kMoveInts * nn * sizeof(int));
   c->P.h = (double*)dalloc(c, nn * sizeof(double));
   c->P.sig = (double*)dalloc(c, nn * sizeof(double));
+  c->P.gm = (double*)dalloc(c, nn * sizeof(double));
   // staging of memd_set_particles (positions and images), kept with the particles
   c->pin = (double*)dalloc(c, 3 * nn * sizeof(double) + 3 * nn * sizeof(int));
   if (!c->P.x || !c->P.v || !c->P.m || !c->P.F || !c->P.Ft || !c->P.img || !c->P.q || !c->P.mv ||
-      !c->P.h || !c->P.sig || !c->pin)
+      !c->P.h || !c->P.sig || !c->P.gm || !c->pin)
     return fail(c, MEMD_ERR_OOM, "particle allocation");
   double* pin = (double*)dalloc(c, 3 * nn * sizeof(double));
   long long* Q = (long long*)dalloc(c, sizeof(long long) * m.V);
@@ -1024,8 +1033,8 @@ memd_status memd_init_field(memd_ctx* c, int64_t n, const double* pos, const int
       c->cur = 0;
       launch_cast(c->prec, c->D(), D64, 3 * m.V, st);
       CK(cudaMemsetAsync(c->B(), 0, 3 * m.V * esz(c), st));
-      CK(cudaMemsetAsync(c->Tb, 0, 3 * m.V * sizeof(long long), st));
-      if (c->Tb2) CK(cudaMemsetAsync(c->Tb2, 0, 3 * m.V * sizeof(long long), st));
+      CK(clear_transfers(c, c->Tb, st));
+      if (c->Tb2) CK(clear_transfers(c, c->Tb2, st));
       c->pending = false;
       CK(cudaMemsetAsync(&c->ds->ticket, 0, sizeof(unsigned int), st));
       const StepParams sp = step_params(c, 0, 0.0, 0.0);
@@ -1151,9 +1160,10 @@ static memd_status step_prepare(memd_ctx* c, const memd_thermostat* th, StepPara
   }
   if (!c->graph[0] && !c->graph[1]) c->coop = want_coop(c);
   if (c->coop && !c->Tb2) {
-    c->Tb2 = (long long*)dalloc(c, 3 * c->mesh.V * sizeof(long long));
+    // the same stride as the first (its odd words unused)
+    c->Tb2 = (long long*)dalloc(c, kLT * 3 * c->mesh.V * sizeof(long long));
     if (!c->Tb2) return fail(c, MEMD_ERR_OOM, "second transfer buffer");
-    CK(cudaMemsetAsync(c->Tb2, 0, 3 * c->mesh.V * sizeof(long long), c->stream));
+    CK(cudaMemsetAsync(c->Tb2, 0, kLT * 3 * c->mesh.V * sizeof(long long), c->stream));
   }
   if (!c->coop) {
     const memd_status e = memd_flush(c);
@@ -1545,7 +1555,7 @@ memd_status memd_get_fields(memd_ctx* c, double* D, double* B, int64_t* Lg) {
     CK(cudaMemcpyAsync(B, tmp, n3 * sizeof(double), cudaMemcpyDeviceToHost, st));
     CK(cudaStreamSynchronize(st));
   }
-  if (Lg) CK(cudaMemcpyAsync(Lg, c->Lg, n3 * sizeof(long long), cudaMemcpyDeviceToHost, st));
+  if (Lg) CK(cudaMemcpy2DAsync(Lg, 8, c->Lg, kLT * 8, 8, n3, cudaMemcpyDeviceToHost, st));
   CK(cudaStreamSynchronize(st));
   dfree(c, tmp);
   return MEMD_OK;
@@ -1572,7 +1582,7 @@ memd_status memd_set_fields(memd_ctx* c, const double* D, const double* B, const
     launch_cast(c->prec, c->B(), tmp, (int64_t)n3, st);
     CK(cudaStreamSynchronize(st));
   }
-  if (Lg) CK(cudaMemcpyAsync(c->Lg, Lg, n3 * sizeof(long long), cudaMemcpyHostToDevice, st));
+  if (Lg) CK(cudaMemcpy2DAsync(c->Lg, kLT * 8, Lg, 8, 8, n3, cudaMemcpyHostToDevice, st));
   CKL();
   CK(cudaStreamSynchronize(st));
   dfree(c, tmp);
@@ -1629,7 +1639,9 @@ memd_status memd_save_state(memd_ctx* c, void* buf, int64_t bytes) {
   };
   get(c->D(), V3 * es);
   get(c->B(), V3 * es);
-  get(c->Lg, V3 * 8);
+  if (ok && cudaMemcpy2DAsync(p, 8, c->Lg, kLT * 8, 8, V3, cudaMemcpyDeviceToHost, st) != cudaSuccess)
+    ok = false;
+  p += V3 * 8;
   get(c->P.x, 3 * n * 8);
   get(c->P.v, 3 * n * 8);
   get(c->P.F, 3 * n * 8);
@@ -1694,7 +1706,9 @@ memd_status memd_load_state(memd_ctx* c, const void* buf, int64_t bytes) {
   };
   put(c->D(), V3 * es);
   put(c->B(), V3 * es);
-  put(c->Lg, V3 * 8);
+  if (ok && cudaMemcpy2DAsync(c->Lg, kLT * 8, p, 8, 8, V3, cudaMemcpyHostToDevice, st) != cudaSuccess)
+    ok = false;
+  p += V3 * 8;
   put(c->P.x, 3 * n * 8);
   put(c->P.v, 3 * n * 8);
   put(c->P.F, 3 * n * 8);
@@ -1706,8 +1720,8 @@ memd_status memd_load_state(memd_ctx* c, const void* buf, int64_t bytes) {
   // transfers none pending, the step counter and last dipole of the saved
   // state, the accumulators clear; the per-particle constants are formed
   // again from the masses at the next step
-  CK(cudaMemsetAsync(c->Tb, 0, V3 * sizeof(long long), st));
-  if (c->Tb2) CK(cudaMemsetAsync(c->Tb2, 0, V3 * sizeof(long long), st));
+  CK(clear_transfers(c, c->Tb, st));
+  if (c->Tb2) CK(clear_transfers(c, c->Tb2, st));
   c->pending = false;
   CK(cudaMemcpyAsync(&c->ds->step, &h.step, sizeof(long long), cudaMemcpyHostToDevice, st));
   CK(cudaMemcpyAsync(c->ds->Plast, h.Plast, 3 * sizeof(long long), cudaMemcpyHostToDevice, st));

@@ -48,6 +48,19 @@ struct memd_batch {
   int2* d_apply_chunk = nullptr;
   int n_apply_chunk = 0;
   cudaGraphExec_t graph[2] = {nullptr, nullptr};
+  // single-launch step (k_batch_step): the engine asked for, whether it runs,
+  // its grid, the CTAs that start with field work, planes per field item, the
+  // four work queues and the scheduling state
+  int engine = MEMD_STEP_AUTO;
+  bool single = false;
+  bool single_graph_ok = true;  // its launch can be captured in a graph
+  int bs_grid = 0;
+  int bs_field_ctas = -1;   // -1: half the grid
+  int bs_item_planes = 0;   // 0: chosen from the work (about one item per CTA)
+  BatchItem* d_q[2] = {nullptr, nullptr};
+  int nq[2] = {0, 0};
+  BatchSched* d_sched = nullptr;
+  RepSync* d_sync = nullptr;
   // memd_batch_step_io: the members' particle offsets (host and device) and
   // the I/O block (page-locked host memory and its device mirror)
   std::vector<int64_t> ioff;
@@ -122,6 +135,69 @@ void free_tables(memd_batch* b) {
   b->d_apply_chunk = nullptr;
   b->n_apply_chunk = 0;
   b->d_ioff = nullptr;
+  for (int q = 0; q < 2; ++q) {
+    b->d_q[q] = nullptr;
+    b->nq[q] = 0;
+  }
+  b->d_sched = nullptr;
+  b->d_sync = nullptr;
+  b->single = false;
+}
+
+// Work items of the single-launch step.  Field: each member's row tiles (the
+// row kernel's geometry for kBatchStepThreads threads) cut into ranges of at
+// most `planes` planes; particles: chunks of kBatchStepThreads / 4 charges,
+// kBatchChunksPerItem a particle item, at least one item per member (its last
+// gather item closes the member's step); the deposition items go in a queue,
+// the application and gather items are counted per member.  False when a
+// member does not fit the row tiles.
+bool batch_items(memd_batch* b, std::vector<RepDesc>& desc, int grid,
+                 std::vector<BatchItem> (&q)[2]) {
+  const int W = rows_sites_per_thread(b->prec);
+  const int nt = kBatchStepThreads;
+  struct Tile {
+    int rep, y0, rows, nz;
+  };
+  std::vector<Tile> tiles;
+  long long tile_planes = 0;
+  for (size_t r = 0; r < b->m.size(); ++r) {
+    const memd_ctx* c = b->m[r];
+    const int nx = c->mesh.n[0], ny = c->mesh.n[1], nz = c->mesh.n[2];
+    if (nx % W != 0) return false;
+    for (int t = 0; t < 2; ++t)
+      if (((uintptr_t)c->Dbuf[t] | (uintptr_t)c->Bbuf[t]) % 16 != 0) return false;
+    if ((uintptr_t)c->ie % 16 != 0) return false;
+    const int TQ = nx / W;
+    const int maxrows = nt / TQ;
+    if (maxrows < 3) return false;
+    const int ntl = (ny + maxrows - 3) / (maxrows - 2);
+    const int Rt = (ny + ntl - 1) / ntl;
+    for (int y0 = 0; y0 < ny; y0 += Rt) {
+      tiles.push_back(Tile{(int)r, y0, std::min(Rt, ny - y0), nz});
+      tile_planes += nz;
+    }
+  }
+  int planes = b->bs_item_planes;
+  if (planes <= 0) planes = std::max<long long>(8, (tile_planes + grid - 1) / grid);
+  for (auto& v : q) v.clear();
+  for (size_t r = 0; r < b->m.size(); ++r) {
+    desc[r].b_nf = 0;
+    for (const Tile& t : tiles) {
+      if (t.rep != (int)r) continue;
+      const int nseg = (t.nz + planes - 1) / planes;
+      for (int k = 0; k < nseg; ++k) {
+        const int za = (int)((int64_t)t.nz * k / nseg), zb = (int)((int64_t)t.nz * (k + 1) / nseg);
+        q[kItemField].push_back(BatchItem{(int)r, t.y0, t.rows, za, zb});
+        desc[r].b_nf += 1;
+      }
+    }
+    const int nc = (int)std::max<int64_t>(1, (4 * b->m[r]->P.n + nt - 1) / nt);
+    const int np = (nc + kBatchChunksPerItem - 1) / kBatchChunksPerItem;
+    desc[r].b_nc = nc;
+    desc[r].b_np = np;
+    for (int k = 0; k < np; ++k) q[kItemDeposit].push_back(BatchItem{(int)r, k, 0, 0, 0});
+  }
+  return true;
 }
 
 void free_io(memd_batch* b) {
@@ -193,6 +269,17 @@ memd_status build_tables(memd_batch* b) {
   }
   b->ioff.assign(R + 1, 0);
   for (int r = 0; r < R; ++r) b->ioff[r + 1] = b->ioff[r] + b->m[r]->P.n;
+  // the single-launch step when asked for and it can run: cooperative
+  // launches, a resident grid of its CTAs, and every member in row tiles
+  std::vector<BatchItem> items[2];
+  if (b->engine == MEMD_STEP_SINGLE) {
+    int coop = 0, sms = 0;
+    BCK(cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, b->device));
+    BCK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, b->device));
+    const int occ = coop ? batch_step_occupancy(b->prec) : 0;
+    b->bs_grid = occ * sms;
+    b->single = b->bs_grid > 0 && batch_items(b, desc, b->bs_grid, items);
+  }
   b->bpar = 0;
   b->n_field = (int)frep.size();
   b->n_part = (int)prep.size();
@@ -210,6 +297,20 @@ memd_status build_tables(memd_batch* b) {
                       cudaMemcpyHostToDevice, b->stream));
   BCK(cudaMemcpyAsync(b->d_part_rep, prep.data(), sizeof(int) * b->n_part,
                       cudaMemcpyHostToDevice, b->stream));
+  if (b->single) {
+    for (int q = 0; q < 2; ++q) {
+      b->nq[q] = (int)items[q].size();
+      b->d_q[q] = (BatchItem*)balloc(b, sizeof(BatchItem) * std::max<size_t>(1, items[q].size()));
+      if (!b->d_q[q]) return bfail(b, MEMD_ERR_OOM, "batch work queues");
+      BCK(cudaMemcpyAsync(b->d_q[q], items[q].data(), sizeof(BatchItem) * items[q].size(),
+                          cudaMemcpyHostToDevice, b->stream));
+    }
+    b->d_sched = (BatchSched*)balloc(b, sizeof(BatchSched));
+    b->d_sync = (RepSync*)balloc(b, sizeof(RepSync) * R);
+    if (!b->d_sched || !b->d_sync) return bfail(b, MEMD_ERR_OOM, "batch scheduling state");
+    BCK(cudaMemsetAsync(b->d_sched, 0, sizeof(BatchSched), b->stream));
+    BCK(cudaMemsetAsync(b->d_sync, 0, sizeof(RepSync) * R, b->stream));
+  }
   b->apply_dense = apply_dense(b->m[0]->apply_mode);
   if (b->apply_dense) {
     b->n_apply_chunk = (int)achunk.size();
@@ -361,6 +462,32 @@ memd_status autotune_batch(memd_batch* b) {
 
 memd_status record(memd_batch* b, int par, int thermo, double gamma, double kT, bool timed) {
   const cudaStream_t st = b->stream;
+  if (b->single) {
+    // the whole step in one cooperative launch; with timing on, the event
+    // pair brackets that launch
+    BatchStepArgs a{};
+    a.desc = b->d_desc;
+    a.nrep = (int)b->m.size();
+    for (int q = 0; q < 2; ++q) {
+      a.q[q] = b->d_q[q];
+      a.n[q] = b->nq[q];
+    }
+    a.sched = b->d_sched;
+    a.sync = b->d_sync;
+    a.par = par;
+    a.thermo = thermo;
+    a.gamma = gamma;
+    a.kT = kT;
+    a.field_ctas = b->bs_field_ctas >= 0 ? std::min(b->bs_field_ctas, b->bs_grid) : b->bs_grid / 2;
+    a.wait_ns = 500000000ull;
+    if (timed) BCK(cudaEventRecordWithFlags(b->ev0, st, cudaEventRecordExternal));
+    BCK(launch_batch_step(b->prec, a, b->bs_grid, st));
+    if (timed) {
+      BCK(cudaEventRecordWithFlags(b->ev1, st, cudaEventRecordExternal));
+      for (int k = 0; k < 6; ++k) BCK(cudaEventRecordWithFlags(b->evp[k], st, cudaEventRecordExternal));
+    }
+    return MEMD_OK;
+  }
   const bool serial = b->field_bytes >= kSerialFieldBytes;
   // with timing on, an event pair around each launch (on the launch's stream)
   auto mark = [&](cudaEvent_t e, cudaStream_t s) {
@@ -564,15 +691,33 @@ memd_status memd_batch_step(memd_batch* b, int64_t nsteps, const memd_thermostat
   for (int64_t s = 0; s < nsteps; ++s) {
     const int par = b->bpar;
     harvest(b);
+    if (b->single && !b->single_graph_ok) {
+      // the cooperative launch could not be captured here: launched directly
+      const memd_status r = record(b, par, thermo, gamma, kT, timed);
+      if (r != MEMD_OK) return r;
+      b->timing_pending = timed;
+      b->bpar ^= 1;
+      continue;
+    }
     if (!b->graph[par]) {
-      cudaGraph_t g;
+      cudaGraph_t g = nullptr;
       BCK(cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal));
       memd_status r = record(b, par, thermo, gamma, kT, timed);
       cudaError_t e = cudaStreamEndCapture(b->stream, &g);
-      if (r != MEMD_OK) return r;
-      if (e != cudaSuccess) return bfail(b, MEMD_ERR_CUDA, "graph capture");
-      BCK(cudaGraphInstantiate(&b->graph[par], g, 0));
-      cudaGraphDestroy(g);
+      if (r != MEMD_OK) {
+        if (g) cudaGraphDestroy(g);
+        return r;
+      }
+      cudaError_t ie = e == cudaSuccess ? cudaGraphInstantiate(&b->graph[par], g, 0) : e;
+      if (g) cudaGraphDestroy(g);
+      if (ie != cudaSuccess) {
+        b->graph[par] = nullptr;
+        if (!b->single) return bfail(b, MEMD_ERR_CUDA, "graph capture");
+        cudaGetLastError();
+        b->single_graph_ok = false;
+        --s;  // this step again, launched directly
+        continue;
+      }
     }
     BCK(cudaGraphLaunch(b->graph[par], b->stream));
     b->timing_pending = timed;
@@ -587,6 +732,17 @@ memd_status memd_batch_synchronize(memd_batch* b) {
   BCK(cudaSetDevice(b->device));
   harvest(b);
   BCK(cudaStreamSynchronize(b->stream));
+  if (b->single && b->d_sched) {
+    // a wait of the single-launch step that ran out leaves its counts out of
+    // step: start them afresh (the step is void)
+    unsigned int err = 0;
+    BCK(cudaMemcpy(&err, &b->d_sched->err, sizeof(err), cudaMemcpyDeviceToHost));
+    if (err) {
+      BCK(cudaMemset(b->d_sched, 0, sizeof(BatchSched)));
+      BCK(cudaMemset(b->d_sync, 0, sizeof(RepSync) * b->m.size()));
+      return bfail(b, MEMD_ERR_TIMEOUT, "a wait of the single-launch batch step ran out");
+    }
+  }
   for (memd_ctx* c : b->m) {
     const memd_status s = memd_check_err(c);
     if (s != MEMD_OK) return bfail(b, s, c->last_error);
@@ -658,6 +814,24 @@ memd_status memd_batch_step_io(memd_batch* b, int32_t load, int64_t nsteps,
   return MEMD_OK;
 }
 
+memd_status memd_batch_set_engine(memd_batch* b, int32_t engine, int32_t field_ctas,
+                                  int32_t item_planes) {
+  if (!b) return MEMD_ERR_INVALID;
+  if (engine < MEMD_STEP_AUTO || engine > MEMD_STEP_SINGLE || item_planes < 0)
+    return bfail(b, MEMD_ERR_INVALID, "bad engine options");
+  BCK(cudaSetDevice(b->device));
+  harvest(b);
+  BCK(cudaStreamSynchronize(b->stream));
+  b->engine = engine;
+  b->bs_field_ctas = field_ctas;
+  b->bs_item_planes = item_planes;
+  const memd_status s = build_tables(b);
+  if (s != MEMD_OK) return s;
+  if (engine == MEMD_STEP_SINGLE && !b->single)
+    return bfail(b, MEMD_ERR_INVALID, "the single-launch step cannot run this batch");
+  return MEMD_OK;
+}
+
 memd_status memd_batch_kernel_stats(memd_batch* b, memd_kernel_stats* out) {
   if (!b || !out) return MEMD_ERR_INVALID;
   harvest(b);
@@ -665,7 +839,8 @@ memd_status memd_batch_kernel_stats(memd_batch* b, memd_kernel_stats* out) {
   out->field_ms = b->field_ms;
   out->field_launches = b->field_launches;
   out->field_bytes = b->field_bytes;
-  out->launches_per_step = 4;
+  out->launches_per_step = b->single ? 1 : 4;
+  out->step_single = b->single ? 1 : 0;
   out->field_tma = 0;
   out->field_ty = b->f_ty;
   out->field_tma = 0;

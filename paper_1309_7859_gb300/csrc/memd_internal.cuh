@@ -37,6 +37,14 @@ struct Mesh {
   double inv_aS; // S / a (exact when a is a power of two)
 };
 
+// The transfer buffer and the ledger of a system share one allocation of
+// 6 V int64 words: link l's transfer word at [kLT l], its ledger word at
+// [kLT l + 1].  The transfer application reads one and adds into the other,
+// which then share a sector; the deposition (transfer words) and the
+// application touch the same sectors.  Kernels index both arrays with this
+// stride (the ledger pointer is the allocation plus one word).
+constexpr int kLT = 2;
+
 // error bits raised by kernels into a device word
 enum : unsigned int {
   kErrCellJump = 1u,
@@ -146,6 +154,8 @@ void launch_gauss_scan(const Mesh& m, const long long* Q, long long* Lg, long lo
 void launch_init_D(const Mesh& m, double* D64, const long long* Lg, DevState* ds,
                    double scale, double Vbox, cudaStream_t st);
 void launch_ledger_sums(const Mesh& m, const long long* Lg, DevState* ds, cudaStream_t st);
+// zero the transfer words of a transfer buffer of count links (stride kLT)
+void launch_clear_transfers(long long* T, int64_t count, cudaStream_t st);
 
 // deterministic FP64 reductions (memd_setup.cu)
 int reduce_blocks();
@@ -168,10 +178,13 @@ struct Particles {
   double* Ft;
   int* img;
   int* q;
-  int* mv;      // 6 ints per particle: old cell (3), new cell (3) of the last move
+  int* mv;      // kMoveInts ints per particle: old cell (3), new cell (3) and new
+                // sub-cell step (3) of the last move
   double* h;    // dt / (2 m): half-kick factor
   double* sig;  // sqrt(2 gamma m kT / dt): Langevin noise amplitude
+  double* gm;   // -gamma m: Langevin friction per unit velocity
 };
+constexpr int kMoveInts = 9;
 struct StepParams {
   double dt;
   double coefB;   // dt / a
@@ -267,6 +280,8 @@ struct RepDesc {
   DevState* ds;
   int f_first, f_tx, f_ty, f_zchunk;  // field tiles: first CTA, tiles along x, y; planes per CTA
   int p_first, p_ctas;                // particle CTAs of the quad kernels
+  int b_nf, b_np, b_nc;               // single-launch step: field items, particle items,
+                                      // particle chunks (kBatchStepThreads quad lanes)
 };
 // A field pass that moves at least this many bytes is HBM bound: the step
 // then runs the deposition after it on the same stream instead of beside it.
@@ -291,6 +306,64 @@ int rows_sites_per_thread(int prec);
 int rows_occupancy(int prec, int nt);
 cudaError_t launch_rows_batch(int prec, const RepDesc* desc, const RowSeg* segs,
                               const int* seg_first, int nctas, int nt, int par, cudaStream_t st);
+// ------------------------------------------- single-launch batch step
+// (memd_particles.cu) The whole step of every replica in one cooperative
+// launch of persistent CTAs that claim work: field segments (a row tile over
+// a range of planes) and deposition items from two device queues, transfer
+// application and gather items of a replica from that replica's own claim
+// counts, once ready.  A particle item is kBatchChunksPerItem chunks of
+// kBatchStepThreads / 4 charges.  A replica's application items become ready
+// when its field segments and deposition items have all finished, its gather
+// items when its application items have; counts per replica say so.  Nothing
+// waits on a grid-wide barrier: while some CTAs stream field segments, others
+// deposit, apply and gather the replicas whose fields were just written
+// (still in L2).
+constexpr int kBatchStepThreads = 256;
+constexpr int kBatchChunksPerItem = 2;
+enum : int { kItemField = 0, kItemDeposit = 1, kItemApply = 2, kItemGather = 3 };
+struct BatchItem {
+  int rep;
+  int a, b, c, d;  // field: y0, rows, za, zb; deposition: item index in the replica
+};
+// queue claims and the launch count; counts only grow (the bases move to the
+// claims reached by the end of each launch), so nothing is reset between
+// launches
+struct BatchSched {
+  unsigned long long epoch;     // launches completed
+  unsigned long long next[2];   // claims made on the field and deposition queues
+  unsigned long long base[2];   // claims made before this launch
+  unsigned long long exits;     // CTAs that have left a launch
+  unsigned int err;             // kErrTimeout when a wait ran out
+  unsigned int pad;
+};
+// one replica: items of each kind finished (grows by its item count every
+// launch), and claims of its application and gather items with their values
+// at the start of this launch
+struct RepSync {
+  unsigned long long done[4];
+  unsigned long long claim[2];
+  unsigned long long base[2];
+};
+struct BatchStepArgs {
+  const RepDesc* desc;
+  int nrep;
+  const BatchItem* q[2];  // field and deposition items
+  int n[2];
+  BatchSched* sched;
+  RepSync* sync;
+  int par;
+  int thermo;
+  double gamma, kT;
+  int field_ctas;          // CTAs [0, field_ctas) start with field items, the rest with
+                           // particle work; all take field items once theirs run out
+  unsigned long long wait_ns;  // bound of a wait for dependent work
+};
+// dynamic shared memory of the kernel (that of the row tiles) and its CTAs
+// per SM (0: it cannot run); the launch is cooperative with grid = CTAs per
+// SM x SMs, so every CTA is resident together
+size_t batch_step_smem();
+int batch_step_occupancy(int prec);
+cudaError_t launch_batch_step(int prec, const BatchStepArgs& a, int grid, cudaStream_t st);
 // field update of every replica (memd_field.cu)
 void launch_fused_batch(int prec, const RepDesc* desc, const int* cta_rep, int nctas, int par,
                         int ty, int pf, int tw, cudaStream_t st);

@@ -17,6 +17,7 @@
 // position update is two IEEE roundings (a product, then a sum), never a
 // fused multiply-add.
 #include "memd_internal.cuh"
+#include "memd_rows.cuh"
 #include "memd_site.cuh"
 
 namespace memd {
@@ -126,9 +127,12 @@ __device__ inline void quad_dipole_add(unsigned long long* Pacc, long long val) 
 // calls it, all adding into the same Pacc): one atomic per component and
 // CTA instead of one per warp, since the three words share one L2 line and
 // their atomics are processed one after another
-static_assert(kBatchQuadThreads <= kQuadThreads, "cta_dipole_add sizes its table for kQuadThreads");
+constexpr int kDipoleWarps = 16;  // CTAs of up to 512 threads
+static_assert(kBatchQuadThreads <= 32 * kDipoleWarps && kQuadThreads <= 32 * kDipoleWarps &&
+                  kBatchStepThreads <= 32 * kDipoleWarps,
+              "cta_dipole_add sizes its table for kDipoleWarps warps");
 __device__ inline void cta_dipole_add(unsigned long long* Pacc, long long val) {
-  __shared__ long long part[kQuadThreads / 32][3];
+  __shared__ long long part[kDipoleWarps][3];
   for (int o = 16; o >= 4; o >>= 1) val += __shfl_down_sync(0xffffffffu, val, o);
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   if (lane < 3) part[warp][lane] = val;
@@ -159,11 +163,14 @@ __device__ inline void philox4x32_10(unsigned c[4], unsigned k0, unsigned k1) {
   }
 }
 
-// xi = sqrt(3) (2 u - 1), u = (r + 1/2) 2^-32; 2 u is formed as (r + 1/2) 2^-31,
-// which is the same double (scaling by 2 is exact)
+// xi = sqrt(3) (2 u - 1), u = (r + 1/2) 2^-32.  2 u - 1 = k 2^-32 with the
+// integer k = 2 r + 1 - 2^32 (|k| < 2^32: converted exactly), and scaling the
+// double sqrt(3) by 2^-32 is exact, so xi is the one rounding of k times
+// sqrt(3) 2^-32: the same double as rounding sqrt(3) (2 u - 1) after forming
+// 2 u - 1 exactly, with one conversion and one product on the FP64 pipe
 __device__ inline double unit_noise(unsigned r) {
-  const double u2 = __dmul_rn(__dadd_rn((double)r, 0.5), 4.656612873077393e-10);  // 2^-31
-  return __dmul_rn(1.7320508075688772, __dsub_rn(u2, 1.0));
+  const long long k = 2 * (long long)r + 1 - (1ll << 32);
+  return __dmul_rn(__ll2double_rn(k), 0x1.bb67ae8584caap-32);  // sqrt(3) 2^-32
 }
 
 // ---------------------------------------------------------- charge transfer
@@ -200,19 +207,19 @@ __device__ inline void deposit_axis(const Mesh& m, int d, int q, int c0, int f0,
       const int64_t l0 = u0 + perp;
       if (dc == 0) {
         const long long t = -(long long)q * (long long)(f1 - f0) * wp;
-        if (t) atomicAdd(&Tb[l0], (unsigned long long)t);
+        if (t) atomicAdd(&Tb[kLT * l0], (unsigned long long)t);
       } else if (dc == 1) {
         const int64_t l1 = u1 + perp;
         const long long t0 = -(long long)q * (long long)(kS - f0) * wp;
         const long long t1 = -(long long)q * (long long)f1 * wp;
-        if (t0) atomicAdd(&Tb[l0], (unsigned long long)t0);
-        if (t1) atomicAdd(&Tb[l1], (unsigned long long)t1);
+        if (t0) atomicAdd(&Tb[kLT * l0], (unsigned long long)t0);
+        if (t1) atomicAdd(&Tb[kLT * l1], (unsigned long long)t1);
       } else {
         const int64_t l1 = u1 + perp;
         const long long t0 = (long long)q * (long long)f0 * wp;
         const long long t1 = (long long)q * (long long)(kS - f1) * wp;
-        if (t0) atomicAdd(&Tb[l0], (unsigned long long)t0);
-        if (t1) atomicAdd(&Tb[l1], (unsigned long long)t1);
+        if (t0) atomicAdd(&Tb[kLT * l0], (unsigned long long)t0);
+        if (t1) atomicAdd(&Tb[kLT * l1], (unsigned long long)t1);
       }
     }
 }
@@ -267,14 +274,14 @@ __device__ inline long long quad_move(const Mesh& m, Particles P, int64_t p, int
       asm volatile("prefetch.global.L2 [%0];" ::"l"(a));
     }
     if (d == 0) {
-      asm volatile("prefetch.global.L2 [%0];" ::"l"(P.m + p));
+      asm volatile("prefetch.global.L2 [%0];" ::"l"(P.gm + p));
       asm volatile("prefetch.global.L2 [%0];" ::"l"(P.sig + p));
       asm volatile("prefetch.global.L2 [%0];" ::"l"(P.q + p));
     }
   }
   long long U = 0;
   if (active && d < 3) {
-    int* mv = P.mv + 6 * p;
+    int* mv = P.mv + kMoveInts * p;
     if (all_ok) {
       int cc[3], cf[3];
 #pragma unroll
@@ -287,10 +294,12 @@ __device__ inline long long quad_move(const Mesh& m, Particles P, int64_t p, int
       P.img[3 * p + d] = kn;
       mv[d] = c0;
       mv[3 + d] = c1;
+      mv[6 + d] = f1;
       U = ((long long)kn * m.n[d] + c1) * kS + f1;
     } else {
       mv[d] = c0;
       mv[3 + d] = c0;
+      mv[6 + d] = f0;
       U = ((long long)ko * m.n[d] + c0) * kS + f0;
       if (d == 0) atomicOr(&ds->err, kErrCellJump);
     }
@@ -357,7 +366,10 @@ __global__ void k_particle_constants(StepParams sp, Particles P) {
   if (p >= P.n) return;
   const double mass = P.m[p];
   P.h[p] = __ddiv_rn(0.5 * sp.dt, mass);
-  if (sp.thermo) P.sig[p] = sqrt(2.0 * sp.gamma * mass * sp.kT / sp.dt);
+  if (sp.thermo) {
+    P.sig[p] = sqrt(2.0 * sp.gamma * mass * sp.kT / sp.dt);
+    P.gm[p] = __dmul_rn(-sp.gamma, mass);  // the friction's first product, (-gamma) m
+  }
 }
 
 // half kick with the stored force, drift, charge transfer; g is the
@@ -436,9 +448,11 @@ __device__ __forceinline__ void apply_body(const Mesh& m, Particles P,
   if (p >= P.n) return;
   const int corner = (int)(g & 3);
   const int a1 = corner & 1, a2 = corner >> 1;
-  const int* mv = P.mv + 6 * p;
-  const int c0[3] = {mv[0], mv[1], mv[2]};
-  const int c1[3] = {mv[3], mv[4], mv[5]};
+  // the move record may have been written in this launch by another CTA
+  // (single-launch batch step): read through L2
+  const int* mv = P.mv + kMoveInts * p;
+  const int c0[3] = {__ldcg(mv), __ldcg(mv + 1), __ldcg(mv + 2)};
+  const int c1[3] = {__ldcg(mv + 3), __ldcg(mv + 4), __ldcg(mv + 5)};
   // slot 2d: the d-link at the old cell along d; slot 2d+1: at the new
   // cell, when the move crossed a face
   int64_t l[6];
@@ -462,14 +476,14 @@ __device__ __forceinline__ void apply_body(const Mesh& m, Particles P,
   }
   long long t[6];
 #pragma unroll
-  for (int s = 0; s < 6; ++s) t[s] = has[s] ? (long long)atomicExch(&Tb[l[s]], 0ull) : 0ll;
+  for (int s = 0; s < 6; ++s) t[s] = has[s] ? (long long)atomicExch(&Tb[kLT * l[s]], 0ull) : 0ll;
   // only the lane that took a link's transfer adds it, so each reduction
   // below is the one addition to its word in this kernel: exact for the
   // ledger, D + x rounded once for the field
 #pragma unroll
   for (int s = 0; s < 6; ++s)
     if (t[s] != 0) {
-      atomicAdd((unsigned long long*)&Lg[l[s]], (unsigned long long)t[s]);
+      atomicAdd((unsigned long long*)&Lg[kLT * l[s]], (unsigned long long)t[s]);
       atomicAdd(&D[l[s]], (T)((double)t[s] * scale));
     }
 }
@@ -481,66 +495,51 @@ __global__ void __launch_bounds__(kQuadThreads)
   apply_body<T>(m, P, Tb, Lg, D, scale, blockIdx.x * (int64_t)blockDim.x + threadIdx.x);
 }
 
-// Dense form of the same: every transfer word of links [l0, l1) once (l0
-// even), each non-zero word added to the ledger and, scaled, to D, then
-// cleared.  Each word gets the one addition the sparse form gives it, so
-// D + x is rounded once the same way.  Words are read in 16-byte pairs when
-// the buffer is 16-byte aligned (a caller's allocator need not align it),
-// else one by one.
+// Dense form of the same: every link of [l0, l1) once, each non-zero
+// transfer word added to the ledger and, scaled, to D, then cleared.  Each
+// word gets the one addition the sparse form gives it, so D + x is rounded
+// once the same way.  A link's transfer and ledger words are one 16-byte pair
+// (read and written as a vector when the allocation is 16-byte aligned: a
+// caller's allocator need not align it; else word by word).
 template <typename T>
 __device__ __forceinline__ void apply_word(long long* __restrict__ Tb, long long* __restrict__ Lg,
-                                           T* __restrict__ D, double scale, int64_t l,
-                                           long long t) {
+                                           T* __restrict__ D, double scale, int64_t l) {
+  const long long t = Tb[kLT * l];
   if (t != 0) {
-    Tb[l] = 0;
-    Lg[l] += t;
+    Tb[kLT * l] = 0;
+    Lg[kLT * l] += t;
     D[l] = D[l] + (T)((double)t * scale);
   }
 }
 
-// a CTA's chunk is kApplyPairs pairs a thread; every load (the pairs, then
-// the ledger and D words of the non-zero ones) is issued before any store,
-// so a thread waits for two round trips, not two per pair
+// a CTA's range is kApplyPairs links a thread; every load (the pairs, then
+// D of the non-zero ones) is issued before any store, so a thread waits for
+// two round trips, not two per link
 template <typename T>
 __device__ __forceinline__ void apply_dense_range(long long* __restrict__ Tb,
                                                   long long* __restrict__ Lg, T* __restrict__ D,
                                                   double scale, int64_t l0, int64_t l1) {
   if (reinterpret_cast<uintptr_t>(Tb) & 15) {
-    for (int64_t l = l0 + threadIdx.x; l < l1; l += blockDim.x)
-      apply_word<T>(Tb, Lg, D, scale, l, Tb[l]);
+    for (int64_t l = l0 + threadIdx.x; l < l1; l += blockDim.x) apply_word<T>(Tb, Lg, D, scale, l);
     return;
   }
-  const longlong2* T2 = reinterpret_cast<const longlong2*>(Tb);
-  const int64_t p1 = l1 >> 1;
-  long long t[2 * kApplyPairs], lg[2 * kApplyPairs];
+  longlong2* TL = reinterpret_cast<longlong2*>(Tb);  // (transfer, ledger) of each link
+  longlong2 tl[2 * kApplyPairs];
   T dv[2 * kApplyPairs];
-  int64_t w[kApplyPairs];
-#pragma unroll
-  for (int k = 0; k < kApplyPairs; ++k) {
-    const int64_t i = (l0 >> 1) + threadIdx.x + (int64_t)k * blockDim.x;
-    w[k] = 2 * i;
-    const longlong2 v = i < p1 ? __ldcs(T2 + i) : make_longlong2(0, 0);
-    t[2 * k] = v.x;
-    t[2 * k + 1] = v.y;
-  }
+  int64_t w[2 * kApplyPairs];
 #pragma unroll
   for (int j = 0; j < 2 * kApplyPairs; ++j) {
-    lg[j] = 0;
-    dv[j] = T(0);
-    if (t[j] != 0) {
-      lg[j] = Lg[w[j >> 1] + (j & 1)];
-      dv[j] = D[w[j >> 1] + (j & 1)];
-    }
+    w[j] = l0 + threadIdx.x + (int64_t)j * blockDim.x;
+    tl[j] = w[j] < l1 ? __ldcs(TL + w[j]) : make_longlong2(0, 0);
   }
 #pragma unroll
+  for (int j = 0; j < 2 * kApplyPairs; ++j) dv[j] = tl[j].x != 0 ? D[w[j]] : T(0);
+#pragma unroll
   for (int j = 0; j < 2 * kApplyPairs; ++j)
-    if (t[j] != 0) {
-      const int64_t l = w[j >> 1] + (j & 1);
-      Tb[l] = 0;
-      Lg[l] = lg[j] + t[j];
-      D[l] = dv[j] + (T)((double)t[j] * scale);
+    if (tl[j].x != 0) {
+      TL[w[j]] = make_longlong2(0, tl[j].y + tl[j].x);
+      D[w[j]] = dv[j] + (T)((double)tl[j].x * scale);
     }
-  if ((l1 & 1) && threadIdx.x == 0) apply_word<T>(Tb, Lg, D, scale, l1 - 1, Tb[l1 - 1]);
 }
 
 template <typename T>
@@ -680,7 +679,8 @@ __device__ __forceinline__ void gather_body(const Mesh& m, const StepParams& sp,
                                             const double* __restrict__ ie64, DevState* ds,
                                             int kick, int finish, unsigned nctas, int64_t g,
                                             const long long* __restrict__ Tpend = nullptr,
-                                            bool exact32 = false, const long long* pre = nullptr) {
+                                            bool exact32 = false, const long long* pre = nullptr,
+                                            bool use_mv = false) {
   const int64_t p = g >> 2;
   const int lane4 = (int)(g & 3);
   const bool active = p < P.n;
@@ -689,19 +689,27 @@ __device__ __forceinline__ void gather_body(const Mesh& m, const StepParams& sp,
   const int a1 = lane4 & 1, a2 = lane4 >> 1;
   // every independent load first: positions, the lane's particle data, the
   // dipole accumulator and the step counter
-  double x3[3] = {0.0, 0.0, 0.0}, vd = 0.0, mass = 0.0, sig = 0.0, hh = 0.0;
-  int qi = 0;
-  if (active) {
-    x3[0] = P.x[3 * p];
-    x3[1] = P.x[3 * p + 1];
-    x3[2] = P.x[3 * p + 2];
-    qi = P.q[p];
-  }
+  // use_mv: the move just made recorded the cell and sub-cell step of every
+  // axis (the quantisation of the new position), so they are read instead of
+  // computed again
+  double xd = 0.0, vd = 0.0, gm = 0.0, sig = 0.0, hh = 0.0;
+  int qi = 0, cq = 0, fq = 0;
+  if (active) qi = P.q[p];
   if (comp) {
-    vd = P.v[3 * p + lane4];
-    mass = P.m[p];
+    // the move and its half kick may have been made in this launch by another
+    // CTA (single-launch batch step): read through L2
+    if (use_mv) {
+      cq = __ldcg(P.mv + kMoveInts * p + 3 + lane4);
+      fq = __ldcg(P.mv + kMoveInts * p + 6 + lane4);
+    } else {
+      xd = __ldcg(P.x + 3 * p + lane4);
+    }
+    vd = __ldcg(P.v + 3 * p + lane4);
     hh = P.h[p];
-    if (thermo) sig = P.sig[p];
+    if (thermo) {
+      sig = P.sig[p];
+      gm = P.gm[p];
+    }
   }
   // pre (optional): the dipole sum and the step counter, read by the caller
   // (the warp's lanes all hold charges of one system: lane 0 reads it for the
@@ -709,21 +717,20 @@ __device__ __forceinline__ void gather_body(const Mesh& m, const StepParams& sp,
   const int wlane = (threadIdx.x + blockDim.x * threadIdx.y) & 31;
   long long Pl[3] = {0, 0, 0};
   if (active && wlane == 0 && sp.dipole_corr) {
-    Pl[0] = pre ? pre[0] : (long long)ds->Pacc[0];
-    Pl[1] = pre ? pre[1] : (long long)ds->Pacc[1];
-    Pl[2] = pre ? pre[2] : (long long)ds->Pacc[2];
+    Pl[0] = pre ? pre[0] : (long long)__ldcg(&ds->Pacc[0]);
+    Pl[1] = pre ? pre[1] : (long long)__ldcg(&ds->Pacc[1]);
+    Pl[2] = pre ? pre[2] : (long long)__ldcg(&ds->Pacc[2]);
   }
   unsigned rnd = 0;
   if (comp && thermo) {
-    const long long step = pre ? pre[3] : ds->step;
+    const long long step = pre ? pre[3] : __ldcg(&ds->step);
     unsigned ctr[4] = {(unsigned)p, (unsigned)((unsigned long long)p >> 32), (unsigned)step,
                        (unsigned)((unsigned long long)step >> 32)};
     philox4x32_10(ctr, (unsigned)sp.seed, (unsigned)(sp.seed >> 32));
     rnd = lane4 == 0 ? ctr[0] : (lane4 == 1 ? ctr[1] : ctr[2]);
   }
   // lane d < 3 quantises axis d; the quad shares the cells and sub-cell steps
-  int cq = 0, fq = 0;
-  if (comp) quantize(m, lane4, lane4 == 0 ? x3[0] : (lane4 == 1 ? x3[1] : x3[2]), cq, fq);
+  if (comp && !use_mv) quantize(m, lane4, xd, cq, fq);
   const int base = (threadIdx.x + blockDim.x * threadIdx.y) & 28;
   int c[3], f[3];
 #pragma unroll
@@ -749,7 +756,7 @@ __device__ __forceinline__ void gather_body(const Mesh& m, const StepParams& sp,
       Iv[d] = ie[l];
       if (sp.self_mode != 0 && sizeof(T) == 8) I64[d] = ie64[l];
       if (Tpend) {  // transfers of this step not yet applied: as their application rounds
-        const long long t = __ldcg(Tpend + l);
+        const long long t = __ldcg(Tpend + kLT * l);
         if (t != 0) Dv[d] = Dv[d] + pending_inc<T>(t, sp.scale, exact32);
       }
     }
@@ -819,7 +826,7 @@ __device__ __forceinline__ void gather_body(const Mesh& m, const StepParams& sp,
     const double Fd = (double)F;
     double Ft = Fd;
     if (thermo) {
-      const double fr = -gamma * mass * vd;
+      const double fr = gm * vd;  // (-gamma m) v
       const double fn = sig * unit_noise(rnd);
       Ft = Fd + (fr + fn);
     }
@@ -834,8 +841,10 @@ template <typename T>
 __global__ void __launch_bounds__(kQuadThreads)
     k_gather(const __grid_constant__ Mesh m, const __grid_constant__ StepParams sp, Particles P, const T* __restrict__ D, const T* __restrict__ ie,
              const double* __restrict__ ie64, DevState* ds, int kick, int finish) {
+  // kick: the step's gather, right after the move that recorded the cells
   gather_body<T>(m, sp, sp.thermo, sp.gamma, sp.kT, P, D, ie, ie64, ds, kick, finish, gridDim.x,
-                 blockIdx.x * (int64_t)blockDim.x + threadIdx.x);
+                 blockIdx.x * (int64_t)blockDim.x + threadIdx.x, nullptr, false, nullptr,
+                 kick != 0);
 }
 
 // ------------------------------------------------------- batched replicas
@@ -878,7 +887,222 @@ __global__ void __launch_bounds__(kBatchQuadThreads)
                    int thermo, double gamma, double kT) {
   const RepDesc& r = desc[cta_rep[blockIdx.x]];
   gather_body<T>(r.m, r.sp, thermo, gamma, kT, r.P, (const T*)r.D[par ^ 1], (const T*)r.ie, r.ie64, r.ds, 1, 2,
-                 (unsigned)r.p_ctas, batch_local(r));
+                 (unsigned)r.p_ctas, batch_local(r), nullptr, false, nullptr, true);
+}
+
+// ------------------------------------------- single-launch batch step
+__device__ inline unsigned long long ld_acquire_u64(const unsigned long long* p) {
+  unsigned long long v;
+  asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ inline unsigned long long ld_relaxed_u64(const unsigned long long* p) {
+  unsigned long long v;
+  asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ inline unsigned long long add_acq_rel_u64(unsigned long long* p, unsigned long long v) {
+  unsigned long long r;
+  asm volatile("atom.acq_rel.gpu.global.add.u64 %0, [%1], %2;" : "=l"(r) : "l"(p), "l"(v) : "memory");
+  return r;
+}
+__device__ inline unsigned long long global_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+// Warp 0 of a CTA claims its next item.  Dependent work first: lane l looks
+// at replica cursor + l (32 at a time); a replica's gather items are
+// claimable when all its application items have finished, its application
+// items when all its field segments and deposition items have, and some of
+// them are not yet claimed; the lowest such replica (gathers before
+// applications: they finish replicas) is claimed with one atomic add on its
+// own count (a count past the end means another CTA took the last item: look
+// again).  Then independent work: field segments first for field CTAs,
+// deposition items first for the others.  A CTA waits only when every
+// independent item has been claimed and no dependent item is ready; dependent
+// items are claimed only when ready and so never wait once claimed, and the
+// ones left depend only on claimed items, so the wait ends.  It is bounded by
+// the global timer all the same (kErrTimeout, and the CTA leaves).  Returns
+// the kind (setting *rep and *item) or -1 when nothing is left; every lane of
+// warp 0 gets the same answer.
+__device__ int batch_claim(const BatchStepArgs& a, unsigned long long e1, bool field_first,
+                           bool& fdone, bool& ddone, int& cursor, int* rep, int* item) {
+  const unsigned full = 0xffffffffu;
+  const int lane = threadIdx.x & 31;
+  BatchSched* S = a.sched;
+  unsigned long long t0 = 0;
+  for (;;) {
+    bool left = false;  // some replica has dependent items not yet claimed
+    for (int r0 = cursor; r0 < a.nrep; r0 += 32) {
+      const int r = r0 + lane;
+      bool cg = false, ca = false, gone = true;
+      unsigned long long np = 0;
+      if (r < a.nrep) {
+        const RepDesc& d = a.desc[r];
+        RepSync& y = a.sync[r];
+        np = (unsigned long long)d.b_np;
+        const unsigned long long ka = ld_relaxed_u64(&y.claim[0]) - y.base[0];
+        const unsigned long long kg = ld_relaxed_u64(&y.claim[1]) - y.base[1];
+        gone = ka >= np && kg >= np;
+        if (kg < np) cg = ld_acquire_u64(&y.done[kItemApply]) >= e1 * np;
+        if (!cg && ka < np)
+          ca = ld_acquire_u64(&y.done[kItemField]) >= e1 * (unsigned long long)d.b_nf &&
+               ld_acquire_u64(&y.done[kItemDeposit]) >= e1 * np;
+      }
+      const unsigned bg = __ballot_sync(full, cg), ba = __ballot_sync(full, ca);
+      const unsigned bgone = __ballot_sync(full, gone);
+      if (r0 == cursor) cursor += bgone == full ? 32 : __ffs(~bgone) - 1;  // skip finished
+      left = left || bgone != full;
+      if (bg | ba) {
+        const int src = bg ? __ffs(bg) - 1 : __ffs(ba) - 1;
+        const int kind = bg ? kItemGather : kItemApply;
+        unsigned long long k = 0;
+        if (lane == src) k = atomicAdd(&a.sync[r].claim[kind - kItemApply], 1ull) - a.sync[r].base[kind - kItemApply];
+        k = __shfl_sync(full, k, src);
+        const unsigned long long nps = __shfl_sync(full, np, src);
+        if (k < nps) {
+          *rep = r0 + src;
+          *item = (int)k;
+          return kind;
+        }
+        r0 -= 32;  // another CTA took the last one: look at these replicas again
+        continue;
+      }
+    }
+    int q = -1, k = 0;
+    if (lane == 0) {
+      const int first = field_first ? kItemField : kItemDeposit;
+      for (int j = 0; j < 2 && q < 0; ++j) {
+        const int qq = j == 0 ? first : kItemField + kItemDeposit - first;
+        bool& done = qq == kItemField ? fdone : ddone;
+        if (done) continue;
+        const unsigned long long c = atomicAdd(&S->next[qq], 1ull) - S->base[qq];
+        if (c < (unsigned long long)a.n[qq]) {
+          q = qq;
+          k = (int)c;
+        } else {
+          done = true;
+        }
+      }
+    }
+    q = __shfl_sync(full, q, 0);
+    fdone = __shfl_sync(full, fdone, 0);
+    ddone = __shfl_sync(full, ddone, 0);
+    if (q >= 0) {
+      k = __shfl_sync(full, k, 0);
+      *rep = a.q[q][k].rep;
+      *item = k;
+      return q;
+    }
+    if (!left) return -1;
+    unsigned long long t = 0;
+    if (lane == 0) t = global_ns();
+    t = __shfl_sync(full, t, 0);
+    if (t0 == 0) {
+      t0 = t;
+    } else if (t - t0 > a.wait_ns) {
+      if (lane == 0) atomicOr(&S->err, kErrTimeout);
+      return -1;
+    }
+    __nanosleep(200);
+  }
+}
+
+// The step of every replica in one cooperative launch (see BatchStepArgs).
+// Each item runs on the whole CTA; its completion is published by thread 0
+// after the CTA's barrier (a gpu-scope fence, then an acquire-release count).
+// The CTA that completes a replica's last gather item closes that replica's
+// step (P of this state reported, the sum cleared, the counter advanced), and
+// the last CTA to leave moves the claim bases and the launch count on.
+template <typename T>
+__global__ void __launch_bounds__(kBatchStepThreads, 2)
+    k_batch_step(const __grid_constant__ BatchStepArgs a) {
+  extern __shared__ __align__(16) unsigned char bs_smem[];
+  __shared__ int s_kind, s_rep, s_item, s_last;
+  BatchSched* S = a.sched;
+  const unsigned long long e1 = ld_relaxed_u64(&S->epoch) + 1;
+  bool fdone = false, ddone = false;
+  int cursor = 0;
+  const bool field_first = (int)blockIdx.x < a.field_ctas;
+  for (;;) {
+    if (threadIdx.x < 32) {
+      int rep = 0, item = 0;
+      const int kind = batch_claim(a, e1, field_first, fdone, ddone, cursor, &rep, &item);
+      if (threadIdx.x == 0) {
+        s_kind = kind;
+        s_rep = rep;
+        s_item = item;
+      }
+    }
+    __syncthreads();
+    const int kind = s_kind;
+    if (kind < 0) break;
+    const int rep = s_rep, item = s_item;
+    const RepDesc& r = a.desc[rep];
+    if (kind == kItemField) {
+      const BatchItem it = a.q[kItemField][item];
+      unsigned char* stg = bs_smem;
+      T* sE = reinterpret_cast<T*>(bs_smem + (size_t)3 * 6 * kBatchStepThreads * 16);
+      T* sB = sE + 3 * (it.b + 2) * r.m.n[0];
+      rows::rows_segment<T, kBatchStepThreads>(
+          r.m, (const T*)r.D[a.par], (const T*)r.B[a.par], (const T*)r.ie, (T*)r.D[a.par ^ 1],
+          (T*)r.B[a.par ^ 1], (T)r.sp.coefB, (T)r.sp.coefD, it.a, it.b, it.c, it.d, sE, sB, stg);
+    } else {
+      // the item's chunks of kBatchStepThreads quad lanes
+      const int k = kind == kItemDeposit ? a.q[kItemDeposit][item].a : item;
+      const int c1 = min((k + 1) * kBatchChunksPerItem, r.b_nc);
+      for (int c = k * kBatchChunksPerItem; c < c1; ++c) {
+        const int64_t g = (int64_t)c * kBatchStepThreads + threadIdx.x;
+        if (kind == kItemDeposit)
+          cta_dipole_add(r.ds->Pacc,
+                         deposit_body(r.m, r.sp, r.P, (unsigned long long*)r.Tb, r.ds, g));
+        else if (kind == kItemApply)
+          apply_body<T>(r.m, r.P, (unsigned long long*)r.Tb, r.Lg, (T*)r.D[a.par ^ 1],
+                        r.sp.scale, g);
+        else
+          gather_body<T>(r.m, r.sp, a.thermo, a.gamma, a.kT, r.P, (const T*)r.D[a.par ^ 1],
+                         (const T*)r.ie, r.ie64, r.ds, 1, 0, 0, g, nullptr, false, nullptr, true);
+      }
+    }
+    __syncthreads();  // the item is done (and s_kind, s_rep, s_item read by every thread)
+    if (threadIdx.x == 0) {
+      __threadfence();
+      const unsigned long long t = add_acq_rel_u64(&a.sync[rep].done[kind], 1ull);
+      if (kind == kItemGather && t + 1 == e1 * (unsigned long long)r.b_np) {
+        DevState* ds = r.ds;
+        const unsigned long long p0 = __ldcg(&ds->Pacc[0]), p1 = __ldcg(&ds->Pacc[1]),
+                                 p2 = __ldcg(&ds->Pacc[2]);
+        ds->Plast[0] = (long long)p0;
+        ds->Plast[1] = (long long)p1;
+        ds->Plast[2] = (long long)p2;
+        ds->Pacc[0] = 0ull;
+        ds->Pacc[1] = 0ull;
+        ds->Pacc[2] = 0ull;
+        ds->step = __ldcg(&ds->step) + 1;
+      }
+    }
+  }
+  if (threadIdx.x == 0) {
+    const unsigned long long t = add_acq_rel_u64(&S->exits, 1ull);
+    s_last = (t + 1) % gridDim.x == 0;
+  }
+  __syncthreads();
+  if (s_last) {
+    // every CTA has left: all claims of this launch are made
+    __threadfence();
+    for (int r = threadIdx.x; r < a.nrep; r += blockDim.x) {
+      RepSync& y = a.sync[r];
+      y.base[0] = ld_relaxed_u64(&y.claim[0]);
+      y.base[1] = ld_relaxed_u64(&y.claim[1]);
+    }
+    if (threadIdx.x == 0) {
+      S->base[0] = ld_relaxed_u64(&S->next[0]);
+      S->base[1] = ld_relaxed_u64(&S->next[1]);
+      S->epoch = e1;
+    }
+  }
 }
 
 // ---------------------------------------------------- single-launch step
@@ -959,10 +1183,10 @@ __device__ __forceinline__ void commit_tile(const Mesh& m, int txi, int tyi, int
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
       const int64_t l = (int64_t)c * m.V + (int64_t)k * P + (int64_t)y * nx + x;
-      const long long t = Tp[l];
+      const long long t = Tp[kLT * l];
       if (t != 0) {
-        Lg[l] += t;
-        Tp[l] = 0;
+        Lg[kLT * l] += t;
+        Tp[kLT * l] = 0;
       }
     }
 }
@@ -1015,7 +1239,7 @@ __global__ void __launch_bounds__(kCoopThreads)
     asm volatile("bar.arrive 2, 64;" ::"l"(used) : "memory");
     for (int64_t b = (int64_t)blockIdx.x * 32; b < nq; b += stride)
       gather_body<T>(m, sp, sp.thermo, sp.gamma, sp.kT, P, Dout, ie, ie64, ds, 1, 0, G, b + lane,
-                     (const long long*)Tcur, exact32, pre);
+                     (const long long*)Tcur, exact32, pre, true);
   } else {
     for (int t = blockIdx.x; t < ntiles; t += (int)G) {
       const int tz = t / (tiles_x * tiles_y), r = t - tz * (tiles_x * tiles_y);
@@ -1271,6 +1495,54 @@ void launch_apply_dense(int prec, int64_t nlinks, long long* Tb, long long* Lg, 
     k_apply_dense<float><<<nb, kApplyThreads, 0, st>>>(nlinks, Tb, Lg, (float*)D, scale);
   else
     k_apply_dense<double><<<nb, kApplyThreads, 0, st>>>(nlinks, Tb, Lg, (double*)D, scale);
+}
+
+size_t batch_step_smem() { return rows_smem_bytes(kBatchStepThreads, 4); }
+
+namespace {
+template <typename T>
+cudaError_t batch_step_attr() {
+  static cudaError_t done = cudaFuncSetAttribute(
+      k_batch_step<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)batch_step_smem());
+  return done;
+}
+}  // namespace
+
+int batch_step_occupancy(int prec) {
+  int n = 0;
+  const cudaError_t e =
+      prec == 1 ? (batch_step_attr<float>() != cudaSuccess
+                       ? cudaErrorInvalidValue
+                       : cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+                             &n, k_batch_step<float>, kBatchStepThreads, batch_step_smem()))
+                : (batch_step_attr<double>() != cudaSuccess
+                       ? cudaErrorInvalidValue
+                       : cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+                             &n, k_batch_step<double>, kBatchStepThreads, batch_step_smem()));
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return 0;
+  }
+  return n;
+}
+
+cudaError_t launch_batch_step(int prec, const BatchStepArgs& a, int grid, cudaStream_t st) {
+  cudaLaunchConfig_t cfg{};
+  cfg.gridDim = dim3((unsigned)grid, 1, 1);
+  cfg.blockDim = dim3(kBatchStepThreads, 1, 1);
+  cfg.dynamicSmemBytes = batch_step_smem();
+  cfg.stream = st;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeCooperative;
+  at[0].val.cooperative = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  if (prec == 1) {
+    const cudaError_t e = batch_step_attr<float>();
+    return e != cudaSuccess ? e : cudaLaunchKernelEx(&cfg, k_batch_step<float>, a);
+  }
+  const cudaError_t e = batch_step_attr<double>();
+  return e != cudaSuccess ? e : cudaLaunchKernelEx(&cfg, k_batch_step<double>, a);
 }
 
 int coop_grid(int prec, int device) {

@@ -94,7 +94,7 @@ int64_t footprint(const memd_server_options& o, const memd_server::Req& r) {
   // ledger, the transfer buffer and the cell-problem potentials (8 B each)
   const int64_t fields = 3 * V * (5 * es + 8 + 16 + 8);
   const int64_t init = 3 * V * 8 * 7 + V * 16;
-  const int64_t parts = (r.q.size() + 1) * (8 * 3 * 5 + 8 * 3 + 4 * 4 + 24);
+  const int64_t parts = (r.q.size() + 1) * (8 * 3 * 5 + 8 * 4 + 4 * 4 + 36);
   return fields + init + parts + (1 << 20);
 }
 

@@ -293,7 +293,7 @@ __global__ void k_zflux(Mesh m, const long long* __restrict__ Q, const long long
   const int64_t t = v - (int64_t)k * P;
   const long long out = share(F[k], P, t);
   const long long in = (k == 0) ? 0 : share(F[k - 1], P, t);
-  Lg[2 * m.V + v] = out;
+  Lg[kLT * (2 * m.V + v)] = out;
   r[v] = Q[v] - (out - in);
 }
 
@@ -331,7 +331,7 @@ __global__ void k_yflux(Mesh m, const long long* __restrict__ Fy, long long* __r
   const int j = (int)(line % m.n[1]);
   const long long out = share(Fy[line], m.n[0], i);
   const long long in = (j == 0) ? 0 : share(Fy[line - 1], m.n[0], i);
-  Lg[m.V + v] = out;
+  Lg[kLT * (m.V + v)] = out;
   r[v] -= out - in;
 }
 
@@ -343,9 +343,17 @@ __global__ void k_xscan(Mesh m, const long long* __restrict__ r, long long* __re
   long long s = 0;
   for (int i = 0; i < m.n[0]; ++i) {
     s += r[line * m.n[0] + i];
-    Lg[line * m.n[0] + i] = s;
+    Lg[kLT * (line * m.n[0] + i)] = s;
   }
   if (s != 0) atomicOr(err, kErrGauss);
+}
+
+// zero every kLT-th word of count pairs (the transfer words, leaving the
+// ledger words between them)
+__global__ void k_clear_transfers(long long* __restrict__ T, int64_t count) {
+  for (int64_t l = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; l < count;
+       l += (int64_t)gridDim.x * blockDim.x)
+    T[kLT * l] = 0;
 }
 
 // per-component ledger sums (exact int64)
@@ -356,7 +364,7 @@ __global__ void __launch_bounds__(kThreads)
   long long s = 0;
   for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < m.V;
        v += (int64_t)gridDim.x * blockDim.x)
-    s += Lg[d * m.V + v];
+    s += Lg[kLT * (d * m.V + v)];
   s = block_sum_ll(s, sh);
   if (threadIdx.x == 0) atomicAdd((unsigned long long*)&ds->lsum[d], (unsigned long long)s);
 }
@@ -369,7 +377,7 @@ __global__ void k_init_D(Mesh m, double* __restrict__ D, const long long* __rest
   const int d = (int)(l / m.V);
   const double P = (double)(long long)ds->Pacc[d] * (m.a / (double)kS);
   const double shift = -P / Vbox - ((double)ds->lsum[d] * scale) / (double)m.V;
-  D[l] = (double)Lg[l] * scale + shift;
+  D[l] = (double)Lg[kLT * l] * scale + shift;
 }
 
 // ------------------------------------------------------------- reductions
@@ -479,6 +487,10 @@ void launch_gauss_scan(const Mesh& m, const long long* Q, long long* Lg, long lo
   k_line_prefix<<<blocks_for(m.n[2], 64), 64, 0, st>>>(m, lam, Fy, err);
   k_yflux<<<blocks_for(m.V), kThreads, 0, st>>>(m, Fy, Lg, r);
   k_xscan<<<blocks_for(nl, 128), 128, 0, st>>>(m, r, Lg, err);
+}
+
+void launch_clear_transfers(long long* T, int64_t count, cudaStream_t st) {
+  if (count > 0) k_clear_transfers<<<2 * 152, 256, 0, st>>>(T, count);
 }
 
 void launch_ledger_sums(const Mesh& m, const long long* Lg, DevState* ds, cudaStream_t st) {

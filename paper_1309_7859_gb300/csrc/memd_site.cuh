@@ -16,7 +16,7 @@ namespace memd {
 // 9 PF values per thread are in flight while a plane is computed.  Same
 // arithmetic per site as k_fused_curl.
 //
-// Tp (optional): transfers not yet applied to D (int64, 3V): D(site) is
+// Tp (optional): transfers not yet applied to D (int64, 3V, stride kLT): D(site) is
 // then read as D + Tp scale, rounded exactly as their application would
 // (pending_inc).
 
@@ -88,10 +88,10 @@ __device__ __forceinline__ void site_tile(const Mesh& m, const T* __restrict__ D
   auto ldD = [&](int k, T (&r)[3]) {
     ld3(Din, k, r);
     if (!live || !Tp) return;
-    const long long* q = Tp + (int64_t)k * P + off;
+    const long long* q = Tp + kLT * ((int64_t)k * P + off);
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
-      const long long t = q[c * V];
+      const long long t = q[kLT * c * V];
       if (t != 0) r[c] = r[c] + pending_inc<T>(t, tscale, exact32);
     }
   };

@@ -34,6 +34,7 @@ EXPORTS = ("memd_default_options", "memd_status_string", "memd_last_error", "mem
            "memd_get_kernel_stats", "memd_reset_kernel_stats", "memd_synchronize",
            "memd_batch_create", "memd_batch_create_kernel", "memd_batch_step",
            "memd_batch_synchronize", "memd_batch_io_buffers", "memd_batch_step_io",
+           "memd_batch_set_engine",
            "memd_batch_kernel_stats", "memd_batch_set_timing", "memd_batch_destroy",
            "memd_server_default_options",
            "memd_server_create", "memd_server_destroy", "memd_server_submit", "memd_server_pump",
@@ -185,6 +186,7 @@ def lib(build_if_missing=True):
     L.memd_batch_step.argtypes = [vp, C.c_int64, C.POINTER(Thermostat)]
     L.memd_batch_synchronize.argtypes = [vp]
     L.memd_batch_io_buffers.argtypes = [vp, C.POINTER(BatchIo)]
+    L.memd_batch_set_engine.argtypes = [vp, C.c_int32, C.c_int32, C.c_int32]
     L.memd_batch_step_io.argtypes = [vp, C.c_int32, C.c_int64, C.POINTER(Thermostat)]
     L.memd_batch_kernel_stats.argtypes = [vp, C.POINTER(KernelStats)]
     L.memd_batch_set_timing.argtypes = [vp, C.c_int32]
@@ -560,6 +562,14 @@ class Batch:
         if st != 0:
             raise MemdError(st, "memd_batch_synchronize failed")
 
+    def set_engine(self, engine="auto", field_ctas=-1, item_planes=0):
+        """memd_batch_set_engine: "graph" (four kernels a step), "single" (the
+        whole step in one cooperative launch of persistent CTAs) or "auto"."""
+        e = {"auto": 0, "graph": 1, "single": 2}[engine]
+        st = self._L.memd_batch_set_engine(self._h, e, int(field_ctas), int(item_planes))
+        if st != 0:
+            raise MemdError(st, "memd_batch_set_engine failed")
+
     def io_buffers(self):
         """The batch's page-locked I/O block as (n_total, 3) numpy views pos,
         vel, img (in and out) and f (out), plus the members' row offsets
@@ -597,11 +607,15 @@ class Batch:
         st = self._L.memd_batch_kernel_stats(self._h, C.byref(k))
         if st != 0:
             raise MemdError(st, "memd_batch_kernel_stats failed")
-        name = (f"k_rows_batch<nt={k.field_rows}>" if k.field_rows else
-                f"k_fused_site_batch<tx={k.field_tx}, ty={k.field_ty}, zchunk={k.field_zchunk}, "
-                f"planes_ahead={k.field_site}>")
+        if k.step_single:
+            name = "k_batch_step (whole step, one cooperative launch)"
+        elif k.field_rows:
+            name = f"k_rows_batch<nt={k.field_rows}>"
+        else:
+            name = (f"k_fused_site_batch<tx={k.field_tx}, ty={k.field_ty}, "
+                    f"zchunk={k.field_zchunk}, planes_ahead={k.field_site}>")
         return StepTiming(k.field_ms, k.field_launches, k.field_bytes, k.launches_per_step, name,
-                          False, tuple(k.phase_ms))
+                          bool(k.step_single), tuple(k.phase_ms))
 
     def close(self):
         if self._h:

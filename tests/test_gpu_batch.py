@@ -127,6 +127,7 @@ def test_row_kernel_members_match_alone(precision):
     members = [make(s, stream) for s in sys_]
     alone = [make(s) for s in sys_]
     batch = Batch(members, field_kernel="rows")
+    batch.set_engine("graph")                  # the row kernel of the four-kernel step
     batch.step(3)
     batch.step(5, thermostat=(1.0, 1.0))
     batch.synchronize()
@@ -200,3 +201,124 @@ def test_batch_of_64_at_bench_size_matches_alone_and_the_oracle():
     o.gather()
     assert rel(members[i].forces(), o.particles("F")) < 1e-5
     batch.close()
+
+
+# ------------------------------------------------ single-launch batch step
+ROW_SPECS = [((16, 16, 16), 200, EpsSpec("tanh", 2, (41.0, 39.0, 8.0, 3.0, 1.5))),
+             ((24, 13, 11), 300, EpsSpec("sin", 0, (60.0, -20.0, 0.0))),   # ragged tiles
+             ((48, 16, 16), 0, EpsSpec("tanh", 0, (41.0, 39.0, 24.0, 8.0, 1.5))),
+             ((32, 32, 20), 900, EpsSpec("const", 0, (3.0,))),
+             ((8, 8, 8), 16, EpsSpec("const", 0, (1.0,))),
+             ((20, 22, 18), 70, EpsSpec("tanh", 1, (20.0, 15.0, 2.0, 2.0, 1.0)))]
+
+
+def row_systems(precision):
+    out = []
+    for i, (mesh, n, eps) in enumerate(ROW_SPECS):
+        rng = np.random.default_rng(300 + i)
+        box = tuple(float(N) for N in mesh)
+        out.append(dict(mesh=mesh, box=box, eps=eps, q=inputs.neutral_charges(rng, n),
+                        x=inputs.uniform_positions(rng, n, box),
+                        v=inputs.thermal_velocities(rng, n), seed=40 + i, precision=precision))
+    return out
+
+
+@pytest.mark.parametrize("precision", ["fp32", "fp64"])
+def test_single_launch_step_matches_graph_and_alone(precision):
+    # the whole step of every member in one cooperative launch (work queues,
+    # per-member readiness counts) against the graph of four kernels and the
+    # members stepped alone: bit identical, over many launches (the queue
+    # bases and launch count carry from one launch to the next)
+    import torch
+    from paper_1309_7859_gb300.memd import Batch
+    sys_ = row_systems(precision)
+    res = {}
+    for engine in ("single", "graph"):
+        stream = torch.cuda.Stream()
+        members = [make(s, stream) for s in sys_]
+        batch = Batch(members)
+        batch.set_engine(engine)
+        batch.step(4)
+        batch.step(9, thermostat=(1.0, 1.0))
+        batch.synchronize()
+        ks = batch.kernel_stats()
+        assert ks.single == (engine == "single")
+        assert ks.launches_per_step == (1 if engine == "single" else 4)
+        res[engine] = [state(g) for g in members]
+        for g in members:
+            assert g.energy()["gauss_exact"] == 1.0
+        batch.close()
+    for s, a, b in zip(sys_, res["single"], res["graph"]):
+        assert_same(a, b)
+        ga = make(s)
+        ga.step(4)
+        ga.step(9, thermostat=(1.0, 1.0))
+        assert_same(a, state(ga))
+
+
+def test_single_launch_scheduling_variants_agree():
+    # every CTA starting with deposition, every CTA starting with field work,
+    # and field segments of two planes: the schedule changes, the results do not
+    import torch
+    from paper_1309_7859_gb300.memd import Batch
+    sys_ = row_systems("fp32")
+    res = []
+    for field_ctas, planes in ((-1, 0), (0, 0), (100000, 0), (-1, 2)):
+        stream = torch.cuda.Stream()
+        members = [make(s, stream) for s in sys_]
+        batch = Batch(members)
+        batch.set_engine("single", field_ctas=field_ctas, item_planes=planes)
+        batch.step(6, thermostat=(1.0, 1.0))
+        batch.synchronize()
+        res.append([state(g) for g in members])
+        batch.close()
+    for other in res[1:]:
+        for a, b in zip(res[0], other):
+            assert_same(a, b)
+
+
+def test_engines_switch_mid_run():
+    # single launch, then the graph, then the single launch again (and a
+    # member stepped alone in between): the members end as when stepped alone
+    import torch
+    from paper_1309_7859_gb300.memd import Batch
+    sys_ = row_systems("fp32")
+    stream = torch.cuda.Stream()
+    members = [make(s, stream) for s in sys_]
+    batch = Batch(members)
+    batch.set_engine("single")
+    batch.step(3, thermostat=(1.0, 1.0))
+    batch.set_engine("graph")
+    batch.step(2, thermostat=(1.0, 1.0))
+    members[3].step(1, thermostat=(1.0, 1.0))
+    batch.set_engine("single")
+    batch.step(4, thermostat=(1.0, 1.0))
+    batch.set_timing(True)                     # an event pair around the launch
+    batch.step(2, thermostat=(1.0, 1.0))
+    batch.synchronize()
+    assert batch.kernel_stats().field_launches == 2
+    for i, s in enumerate(sys_):
+        ga = make(s)
+        ga.step(12 if i == 3 else 11, thermostat=(1.0, 1.0))
+        assert_same(state(members[i]), state(ga))
+
+
+def test_single_launch_refused_for_site_tile_members():
+    # a member whose x extent is not a multiple of 4 sites cannot run in row
+    # tiles: the single launch is refused, the automatic choice is the graph
+    import torch
+    from paper_1309_7859_gb300.memd import Batch, MemdError
+    sys_ = systems("fp32")[2:5]
+    stream = torch.cuda.Stream()
+    members = [make(s, stream) for s in sys_]
+    batch = Batch(members)
+    assert not batch.kernel_stats().single
+    with pytest.raises(MemdError):
+        batch.set_engine("single")
+    batch.set_engine("auto")
+    batch.step(2, thermostat=(1.0, 1.0))
+    batch.synchronize()
+    for s, g in zip(sys_, members):
+        ga = make(s)
+        ga.step(2, thermostat=(1.0, 1.0))
+        assert_same(state(g), state(ga))
