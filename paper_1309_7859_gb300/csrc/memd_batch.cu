@@ -33,7 +33,9 @@ struct memd_batch {
   RepDesc* d_desc = nullptr;
   int* d_field_rep = nullptr;
   int* d_part_rep = nullptr;
-  int n_field = 0, n_part = 0;
+  int* d_part_rep_w = nullptr;  // CTA -> replica of the one-thread-per-charge kernels
+  int n_field = 0, n_part = 0, n_part_w = 0;
+  bool wide = false;            // deposition and gather one thread per charge
   double field_bytes = 0.0;
   int f_ty = kBatchTY, f_pf = kBatchPF32, f_z = kBatchZ;  // field tiles (autotuned)
   int f_w = 32;                                          // tile width: 32 or 16 sites
@@ -128,7 +130,7 @@ void free_tables(memd_batch* b) {
   }
   b->blocks.clear();
   b->d_desc = nullptr;
-  b->d_field_rep = b->d_part_rep = nullptr;
+  b->d_field_rep = b->d_part_rep = b->d_part_rep_w = nullptr;
   b->d_segs = nullptr;
   b->d_seg_first = nullptr;
   b->n_rows_ctas = 0;
@@ -228,7 +230,7 @@ memd_status build_tables(memd_batch* b) {
   free_tables(b);
   const int R = (int)b->m.size();
   std::vector<RepDesc> desc(R);
-  std::vector<int> frep, prep;
+  std::vector<int> frep, prep, pwrep;
   std::vector<int2> achunk;
   b->field_bytes = 0.0;
   for (int r = 0; r < R; ++r) {
@@ -261,6 +263,9 @@ memd_status build_tables(memd_batch* b) {
     d.p_first = (int)prep.size();
     d.p_ctas = (int)std::max<int64_t>(1, (4 * c->P.n + kBatchQuadThreads - 1) / kBatchQuadThreads);
     for (int t = 0; t < d.p_ctas; ++t) prep.push_back(r);
+    d.pw_first = (int)pwrep.size();
+    d.pw_ctas = (int)std::max<int64_t>(1, (c->P.n + kWideThreads - 1) / kWideThreads);
+    for (int t = 0; t < d.pw_ctas; ++t) pwrep.push_back(r);
     const int64_t nch = (3 * c->mesh.V + kApplyChunk - 1) / kApplyChunk;
     for (int64_t k = 0; k < nch; ++k) achunk.push_back(make_int2(r, (int)k));
     b->base[r] = c->cur;
@@ -269,6 +274,8 @@ memd_status build_tables(memd_batch* b) {
   }
   b->ioff.assign(R + 1, 0);
   for (int r = 0; r < R; ++r) b->ioff[r + 1] = b->ioff[r] + b->m[r]->P.n;
+  b->wide = b->ioff[R] >= kWideMinCharges;
+  b->n_part_w = (int)pwrep.size();
   // the single-launch step when asked for and it can run: cooperative
   // launches, a resident grid of its CTAs, and every member in row tiles
   std::vector<BatchItem> items[2];
@@ -287,8 +294,11 @@ memd_status build_tables(memd_batch* b) {
   b->d_field_rep = (int*)balloc(b, sizeof(int) * std::max(1, b->n_field));
   b->d_part_rep = (int*)balloc(b, sizeof(int) * std::max(1, b->n_part));
   b->d_ioff = (int64_t*)balloc(b, sizeof(int64_t) * (R + 1));
-  if (!b->d_desc || !b->d_field_rep || !b->d_part_rep || !b->d_ioff)
+  b->d_part_rep_w = (int*)balloc(b, sizeof(int) * std::max(1, b->n_part_w));
+  if (!b->d_desc || !b->d_field_rep || !b->d_part_rep || !b->d_ioff || !b->d_part_rep_w)
     return bfail(b, MEMD_ERR_OOM, "batch tables");
+  BCK(cudaMemcpyAsync(b->d_part_rep_w, pwrep.data(), sizeof(int) * b->n_part_w,
+                      cudaMemcpyHostToDevice, b->stream));
   BCK(cudaMemcpyAsync(b->d_ioff, b->ioff.data(), sizeof(int64_t) * (R + 1),
                       cudaMemcpyHostToDevice, b->stream));
   BCK(cudaMemcpyAsync(b->d_desc, desc.data(), sizeof(RepDesc) * R, cudaMemcpyHostToDevice,
@@ -489,6 +499,12 @@ memd_status record(memd_batch* b, int par, int thermo, double gamma, double kT, 
     return MEMD_OK;
   }
   const bool serial = b->field_bytes >= kSerialFieldBytes;
+  auto deposit = [&](cudaStream_t s) {
+    if (b->wide)
+      launch_deposit_batch_wide(b->d_desc, b->d_part_rep_w, b->n_part_w, s);
+    else
+      launch_deposit_batch(b->d_desc, b->d_part_rep, b->n_part, thermo, gamma, kT, s);
+  };
   // with timing on, an event pair around each launch (on the launch's stream)
   auto mark = [&](cudaEvent_t e, cudaStream_t s) {
     return timed ? cudaEventRecordWithFlags(e, s, cudaEventRecordExternal) : cudaSuccess;
@@ -497,7 +513,7 @@ memd_status record(memd_batch* b, int par, int thermo, double gamma, double kT, 
     BCK(cudaEventRecord(b->fork, st));
     BCK(cudaStreamWaitEvent(b->side, b->fork, 0));
     BCK(mark(b->evp[0], b->side));
-    launch_deposit_batch(b->d_desc, b->d_part_rep, b->n_part, thermo, gamma, kT, b->side);
+    deposit(b->side);
     BCK(mark(b->evp[1], b->side));
     BCK(cudaEventRecord(b->join, b->side));
   }
@@ -506,7 +522,7 @@ memd_status record(memd_batch* b, int par, int thermo, double gamma, double kT, 
   BCK(mark(b->ev1, st));
   if (serial) {
     BCK(mark(b->evp[0], st));
-    launch_deposit_batch(b->d_desc, b->d_part_rep, b->n_part, thermo, gamma, kT, st);
+    deposit(st);
     BCK(mark(b->evp[1], st));
   } else {
     BCK(cudaStreamWaitEvent(st, b->join, 0));
@@ -518,7 +534,10 @@ memd_status record(memd_batch* b, int par, int thermo, double gamma, double kT, 
     launch_apply_batch(b->prec, b->d_desc, b->d_part_rep, b->n_part, par, st);
   BCK(mark(b->evp[3], st));
   BCK(mark(b->evp[4], st));
-  launch_gather_batch(b->prec, b->d_desc, b->d_part_rep, b->n_part, par, thermo, gamma, kT, st);
+  if (b->wide)
+    launch_gather_batch_wide(b->prec, b->d_desc, b->d_part_rep_w, b->n_part_w, par, thermo, st);
+  else
+    launch_gather_batch(b->prec, b->d_desc, b->d_part_rep, b->n_part, par, thermo, gamma, kT, st);
   BCK(mark(b->evp[5], st));
   BCK(cudaGetLastError());
   return MEMD_OK;

@@ -280,6 +280,7 @@ struct RepDesc {
   DevState* ds;
   int f_first, f_tx, f_ty, f_zchunk;  // field tiles: first CTA, tiles along x, y; planes per CTA
   int p_first, p_ctas;                // particle CTAs of the quad kernels
+  int pw_first, pw_ctas;              // and of the one-thread-per-charge kernels
   int b_nf, b_np, b_nc;               // single-launch step: field items, particle items,
                                       // particle chunks (kBatchStepThreads quad lanes)
 };
@@ -295,6 +296,12 @@ constexpr int kBatchPF32 = 2;          // its prefetch depth in planes, FP32 fie
 constexpr int kBatchPF64 = 1;          // and FP64 fields (register bound)
 constexpr int kBatchZ = 8;             // and its planes per CTA
 constexpr int kBatchQuadThreads = 128;  // 32 particles per CTA in the batched quad kernels
+// Deposition and gather run one thread per charge (kWideThreads a CTA) from
+// kWideMinCharges charges a system (a batch: charges over all members) on:
+// there the instruction count per charge, not latency, bounds them; below
+// it four lanes per charge split each charge's serial FP64 chain.
+constexpr int kWideThreads = 128;
+constexpr int64_t kWideMinCharges = 16384;
 // One segment of the row kernel's work (memd_rows.cu): rows y0 .. y0 + rows - 1
 // of replica rep, planes za .. zb - 1.
 struct RowSeg {
@@ -382,6 +389,11 @@ void launch_deposit_batch(const RepDesc* desc, const int* cta_rep, int nctas, in
                           double gamma, double kT, cudaStream_t st);
 void launch_apply_batch(int prec, const RepDesc* desc, const int* cta_rep, int nctas, int par,
                         cudaStream_t st);
+// one thread per charge (cta_rep over kWideThreads charges a CTA)
+void launch_deposit_batch_wide(const RepDesc* desc, const int* cta_rep, int nctas,
+                               cudaStream_t st);
+void launch_gather_batch_wide(int prec, const RepDesc* desc, const int* cta_rep, int nctas,
+                              int par, int thermo, cudaStream_t st);
 // dense form: CTA b takes the kApplyChunk transfer words from chunk[b].y *
 // kApplyChunk of replica chunk[b].x
 constexpr int kApplyThreads = 256;

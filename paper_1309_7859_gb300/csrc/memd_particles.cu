@@ -144,6 +144,25 @@ __device__ inline void cta_dipole_add(unsigned long long* Pacc, long long val) {
   }
 }
 
+// the same sum with every thread holding all three components (one thread
+// per charge)
+__device__ inline void cta_dipole_add3(unsigned long long* Pacc, const long long U[3]) {
+  __shared__ long long part3[kDipoleWarps][3];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int e = 0; e < 3; ++e) {
+    long long v = U[e];
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    if (lane == 0) part3[warp][e] = v;
+  }
+  __syncthreads();
+  if (threadIdx.x < 3) {
+    long long s = 0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += part3[w][threadIdx.x];
+    if (s != 0) atomicAdd(&Pacc[threadIdx.x], (unsigned long long)s);
+  }
+}
+
 // ------------------------------------------------------------ Philox4x32-10
 // Salmon, Moraes, Dror, Shaw (SC'11): ten rounds of two 32x32 -> 64-bit
 // products with a Weyl-sequence key schedule.
@@ -400,6 +419,85 @@ __device__ __forceinline__ long long deposit_body(const Mesh& m, const StepParam
     }
   }
   return quad_move(m, P, p, d, active, x, ko, xn, kn, ok, Tb, ds, pf_ie, pf_es);
+}
+
+// One thread per charge: the half kick, drift and charge transfer of
+// deposit_body and quad_move with the same expressions, the three axes in
+// turn.  Sets U to the dipole terms (valence times the unfolded fixed-point
+// coordinate of each axis; 0 for a thread past the last charge).  For large
+// charge counts: a warp then moves 32 charges an instruction instead of 8,
+// with no exchange of cells between lanes.
+__device__ __forceinline__ void deposit_wide(const Mesh& m, const StepParams& sp, Particles P,
+                                             unsigned long long* __restrict__ Tb, DevState* ds,
+                                             int64_t p, long long U[3]) {
+  U[0] = U[1] = U[2] = 0;
+  if (p >= P.n) return;
+  const double h = P.h[p];
+  const int q = P.q[p];
+  double x[3], xn[3];
+  int ko[3], kn[3];
+  bool ok = true;
+#pragma unroll
+  for (int d = 0; d < 3; ++d) {
+    const double v = __dadd_rn(P.v[3 * p + d], __dmul_rn(h, P.Ft[3 * p + d]));
+    P.v[3 * p + d] = v;
+    const double step = __dmul_rn(sp.dt, v);
+    x[d] = P.x[3 * p + d];
+    ko[d] = P.img[3 * p + d];
+    kn[d] = ko[d];
+    xn[d] = x[d];
+    if (fabs(step) <= 2.0 * m.a) {
+      xn[d] = __dadd_rn(x[d], step);
+      fold(m.L[d], xn[d], kn[d]);
+    } else {
+      ok = false;
+    }
+  }
+  int c0[3], f0[3], c1[3], f1[3], dc[3];
+#pragma unroll
+  for (int d = 0; d < 3; ++d) {
+    quantize(m, d, x[d], c0[d], f0[d]);
+    quantize(m, d, xn[d], c1[d], f1[d]);
+    dc[d] = c1[d] + (kn[d] - ko[d]) * m.n[d] - c0[d];
+    if (dc[d] < -1 || dc[d] > 1) ok = false;
+  }
+  int* mv = P.mv + kMoveInts * p;
+  if (ok) {
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+      // perpendicular weights of the moves made so far
+      int cc[3], cf[3];
+#pragma unroll
+      for (int e = 0; e < 3; ++e) {
+        cc[e] = (e < d) ? c1[e] : c0[e];
+        cf[e] = (e < d) ? f1[e] : f0[e];
+      }
+      deposit_axis(m, d, q, c0[d], f0[d], f1[d], dc[d], cc, cf, Tb);
+      P.x[3 * p + d] = xn[d];
+      P.img[3 * p + d] = kn[d];
+      mv[d] = c0[d];
+      mv[3 + d] = c1[d];
+      mv[6 + d] = f1[d];
+      U[d] = (((long long)kn[d] * m.n[d] + c1[d]) * kS + f1[d]) * (long long)q;
+    }
+  } else {
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+      mv[d] = c0[d];
+      mv[3 + d] = c0[d];
+      mv[6 + d] = f0[d];
+      U[d] = (((long long)ko[d] * m.n[d] + c0[d]) * kS + f0[d]) * (long long)q;
+    }
+    atomicOr(&ds->err, kErrCellJump);
+  }
+}
+
+__global__ void __launch_bounds__(kWideThreads)
+    k_deposit_wide(const __grid_constant__ Mesh m, const __grid_constant__ StepParams sp,
+                   Particles P, unsigned long long* __restrict__ Tb, DevState* ds) {
+  long long U[3];
+  deposit_wide(m, sp, P, Tb, ds, blockIdx.x * (int64_t)blockDim.x + threadIdx.x, U);
+  cta_dipole_add3(ds->Pacc, U);
 }
 
 __global__ void __launch_bounds__(kQuadThreads)
@@ -847,6 +945,119 @@ __global__ void __launch_bounds__(kQuadThreads)
                  kick != 0);
 }
 
+// One thread per charge: the gather of gather_body with the same
+// expressions and the same order of every sum (each corner's three links,
+// then the corners as ((c0 + c1) + (c2 + c3))), one Philox block a charge.
+template <typename T>
+__device__ __forceinline__ void gather_wide(const Mesh& m, const StepParams& sp, int thermo,
+                                            Particles P, const T* __restrict__ D,
+                                            const T* __restrict__ ie,
+                                            const double* __restrict__ ie64, DevState* ds,
+                                            int kick, int64_t p, bool use_mv) {
+  if (p >= P.n) return;
+  const int qi = P.q[p];
+  int c[3], f[3];
+#pragma unroll
+  for (int d = 0; d < 3; ++d) {
+    if (use_mv) {
+      c[d] = __ldcg(P.mv + kMoveInts * p + 3 + d);
+      f[d] = __ldcg(P.mv + kMoveInts * p + 6 + d);
+    } else {
+      quantize(m, d, __ldcg(P.x + 3 * p + d), c[d], f[d]);
+    }
+  }
+  long long Pl[3] = {0, 0, 0};
+  if (sp.dipole_corr) {
+    Pl[0] = (long long)__ldcg(&ds->Pacc[0]);
+    Pl[1] = (long long)__ldcg(&ds->Pacc[1]);
+    Pl[2] = (long long)__ldcg(&ds->Pacc[2]);
+  }
+  unsigned ctr[4] = {0u, 0u, 0u, 0u};
+  if (thermo) {
+    const long long step = __ldcg(&ds->step);
+    ctr[0] = (unsigned)p;
+    ctr[1] = (unsigned)((unsigned long long)p >> 32);
+    ctr[2] = (unsigned)step;
+    ctr[3] = (unsigned)((unsigned long long)step >> 32);
+    philox4x32_10(ctr, (unsigned)sp.seed, (unsigned)(sp.seed >> 32));
+  }
+  T Ek[4][3], iwk[4][3], itk[4];
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    const int a1 = k & 1, a2 = k >> 1;
+    T Dv[3], Iv[3];
+    double I64[3] = {0.0, 0.0, 0.0};
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+      const int e1 = (d + 1) % 3, e2 = (d + 2) % 3;
+      int at[3] = {c[0], c[1], c[2]};
+      at[e1] += a1;
+      at[e2] += a2;
+      const int64_t l = link_index(m, d, at[0], at[1], at[2]);
+      Dv[d] = __ldcg(D + l);
+      Iv[d] = ie[l];
+      if (sp.self_mode != 0 && sizeof(T) == 8) I64[d] = ie64[l];
+    }
+    itk[k] = T(0);
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+      const int e1 = (d + 1) % 3, e2 = (d + 2) % 3;
+      const T w = ((T)wgt(f[e1], a1) / (T)kS) * ((T)wgt(f[e2], a2) / (T)kS);
+      Ek[k][d] = Dv[d] * Iv[d] * w;
+      const T iv = sizeof(T) == 8 ? (T)I64[d] : Iv[d];
+      itk[k] += iv;
+      iwk[k][d] = iv * w;
+    }
+  }
+  using R = T;
+  const R q = (R)qi;
+  const R itot = (itk[0] + itk[1]) + (itk[2] + itk[3]);
+  const SelfC<R> sc = self_coeffs<R>(f);
+  const double hh = P.h[p];
+  double sig = 0.0, gm = 0.0;
+  if (thermo) {
+    sig = P.sig[p];
+    gm = P.gm[p];
+  }
+#pragma unroll
+  for (int d = 0; d < 3; ++d) {
+    const T Ed = (Ek[0][d] + Ek[1][d]) + (Ek[2][d] + Ek[3][d]);
+    R F = q * (R)Ed;
+    if (sp.self_mode != 0) {
+      const R ie_cell = (R)itot * (R(1) / R(12));
+      const R iwd = (iwk[0][d] + iwk[1][d]) + (iwk[2][d] + iwk[3][d]);
+      const R ie_d = (sp.self_mode == 2) ? iwd : ie_cell;
+      F = F + (q * q * sp_self_pre<R>(sp)) * ie_d * self_sum<R>(sp, sc, d);
+    }
+    if (sp.dipole_corr) {
+      const R MP = sp_Mdip<T>(sp, 3 * d) * (T)Pl[0] + sp_Mdip<T>(sp, 3 * d + 1) * (T)Pl[1] +
+                   sp_Mdip<T>(sp, 3 * d + 2) * (T)Pl[2];
+      F = F + q * MP;
+    }
+    const double vd = __ldcg(P.v + 3 * p + d);
+    const double Fd = (double)F;
+    double Ft = Fd;
+    if (thermo) {
+      const double fr = gm * vd;  // (-gamma m) v
+      const double fn = sig * unit_noise(ctr[d]);
+      Ft = Fd + (fr + fn);
+    }
+    P.F[3 * p + d] = Fd;
+    P.Ft[3 * p + d] = Ft;
+    if (kick) P.v[3 * p + d] = __dadd_rn(vd, __dmul_rn(hh, Ft));
+  }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kWideThreads)
+    k_gather_wide(const __grid_constant__ Mesh m, const __grid_constant__ StepParams sp,
+                  Particles P, const T* __restrict__ D, const T* __restrict__ ie,
+                  const double* __restrict__ ie64, DevState* ds, int kick, int finish) {
+  gather_wide<T>(m, sp, sp.thermo, P, D, ie, ie64, ds, kick,
+                 blockIdx.x * (int64_t)blockDim.x + threadIdx.x, kick != 0);
+  if (finish) finish_update(ds, finish, gridDim.x);
+}
+
 // ------------------------------------------------------- batched replicas
 // CTA b works on particles of replica cta_rep[b]; a replica's CTAs form a
 // contiguous range, so warps and CTAs never mix replicas.
@@ -888,6 +1099,29 @@ __global__ void __launch_bounds__(kBatchQuadThreads)
   const RepDesc& r = desc[cta_rep[blockIdx.x]];
   gather_body<T>(r.m, r.sp, thermo, gamma, kT, r.P, (const T*)r.D[par ^ 1], (const T*)r.ie, r.ie64, r.ds, 1, 2,
                  (unsigned)r.p_ctas, batch_local(r), nullptr, false, nullptr, true);
+}
+
+// one thread per charge: CTA b works on charges of replica cta_rep_w[b]
+__device__ inline int64_t batch_local_w(const RepDesc& r) {
+  return (int64_t)(blockIdx.x - r.pw_first) * blockDim.x + threadIdx.x;
+}
+
+__global__ void __launch_bounds__(kWideThreads)
+    k_deposit_batch_wide(const RepDesc* __restrict__ desc, const int* __restrict__ cta_rep) {
+  const RepDesc& r = desc[cta_rep[blockIdx.x]];
+  long long U[3];
+  deposit_wide(r.m, r.sp, r.P, (unsigned long long*)r.Tb, r.ds, batch_local_w(r), U);
+  cta_dipole_add3(r.ds->Pacc, U);
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kWideThreads)
+    k_gather_batch_wide(const RepDesc* __restrict__ desc, const int* __restrict__ cta_rep,
+                        int par, int thermo) {
+  const RepDesc& r = desc[cta_rep[blockIdx.x]];
+  gather_wide<T>(r.m, r.sp, thermo, r.P, (const T*)r.D[par ^ 1], (const T*)r.ie, r.ie64, r.ds, 1,
+                 batch_local_w(r), true);
+  finish_update(r.ds, 2, (unsigned)r.pw_ctas);
 }
 
 // ------------------------------------------- single-launch batch step
@@ -1463,7 +1697,10 @@ void launch_particle_constants(const StepParams& sp, Particles p, cudaStream_t s
 
 void launch_kick_drift_deposit(const Mesh& m, const StepParams& sp, Particles p, long long* Tb,
                                DevState* ds, cudaStream_t st) {
-  if (p.n > 0)
+  if (p.n >= kWideMinCharges)
+    k_deposit_wide<<<blocks_for(p.n, kWideThreads), kWideThreads, 0, st>>>(
+        m, sp, p, (unsigned long long*)Tb, ds);
+  else if (p.n > 0)
     k_kick_drift_deposit<<<blocks_for(4 * p.n, quad_threads(p.n)), quad_threads(p.n), 0, st>>>(
         m, sp, p, (unsigned long long*)Tb, ds);
 }
@@ -1600,6 +1837,16 @@ void launch_gather(const Mesh& m, int prec, const StepParams& sp, Particles p, c
     if (finish) k_step_end<<<1, 32, 0, st>>>(ds, finish == 2 ? 1 : 0);
     return;
   }
+  if (p.n >= kWideMinCharges) {
+    const unsigned nw = blocks_for(p.n, kWideThreads);
+    if (prec == 1)
+      k_gather_wide<float><<<nw, kWideThreads, 0, st>>>(m, sp, p, (const float*)D,
+                                                        (const float*)ie, ie64, ds, kick, finish);
+    else
+      k_gather_wide<double><<<nw, kWideThreads, 0, st>>>(m, sp, p, (const double*)D,
+                                                         (const double*)ie, ie64, ds, kick, finish);
+    return;
+  }
   const int qt = quad_threads(p.n);
   const unsigned nb = blocks_for(4 * p.n, qt);
   if (prec == 1)
@@ -1618,6 +1865,20 @@ void launch_deposit_batch(const RepDesc* desc, const int* cta_rep, int nctas, in
                           double gamma, double kT, cudaStream_t st) {
   if (nctas > 0)
     k_deposit_batch<<<nctas, kBatchQuadThreads, 0, st>>>(desc, cta_rep, thermo, gamma, kT);
+}
+
+void launch_deposit_batch_wide(const RepDesc* desc, const int* cta_rep, int nctas,
+                               cudaStream_t st) {
+  if (nctas > 0) k_deposit_batch_wide<<<nctas, kWideThreads, 0, st>>>(desc, cta_rep);
+}
+
+void launch_gather_batch_wide(int prec, const RepDesc* desc, const int* cta_rep, int nctas,
+                              int par, int thermo, cudaStream_t st) {
+  if (nctas <= 0) return;
+  if (prec == 1)
+    k_gather_batch_wide<float><<<nctas, kWideThreads, 0, st>>>(desc, cta_rep, par, thermo);
+  else
+    k_gather_batch_wide<double><<<nctas, kWideThreads, 0, st>>>(desc, cta_rep, par, thermo);
 }
 
 void launch_apply_batch(int prec, const RepDesc* desc, const int* cta_rep, int nctas, int par,
