@@ -264,6 +264,35 @@ memd_status memd_forces_device(memd_ctx *ctx, const double **f_dev);
  * INVALID, STATE before memd_init_field, CUDA. */
 memd_status memd_energy(memd_ctx *ctx, memd_energy_terms *out);
 
+/* Dipole drift (Sec. V).  The metallic correction removes P eps_eff^-1 / V
+ * from the field every charge feels, P the dipole moment of the unfolded
+ * charges.  A current driven through the system (an external field pulling
+ * charges apart) makes P grow without bound until the correction outweighs
+ * the field of the charges themselves and the method breaks down; the
+ * remedy is a fresh initial solution (memd_init_field at the present
+ * positions, or memd_set_eps with relax_field).  The lattice field's mean
+ * tracks -eps_eff^-1 P / V (Sec. V), so the field the charges produce about
+ * it is sqrt(sum_d mean over the d-links of (E_d - mean E_d)^2), E = D / eps.
+ * This check compares the correction's field |eps_eff^-1 P| / V with that:
+ * *ratio (may be NULL) receives their quotient, and a quotient above limit
+ * (> 0; 1 is the paper's "outweighs") returns MEMD_ERR_DIPOLE_DRIFT.
+ * Pending transfers are applied first.  Synchronises.  Errors: INVALID,
+ * STATE before memd_init_field, CUDA, DIPOLE_DRIFT. */
+memd_status memd_dipole_check(memd_ctx *ctx, double limit, double *ratio);
+
+/* Failure injection for tests, on the host: no GPU fault, trap or hang.
+ * MEMD_INJECT_BARRIER_SKEW adds one arrival to the grid-barrier count of a
+ * context that steps as one cooperative launch (MEMD_STEP_SINGLE in effect,
+ * decided at its first step), so the next step's barrier cannot complete:
+ * its wait runs out after wait_s seconds (0: the default 0.2 s), the step is
+ * void (fields and forces of that step are not to be used; reload a saved
+ * state) and the next synchronising call reports MEMD_ERR_TIMEOUT and starts
+ * the count afresh.  MEMD_INJECT_NONE only sets the wait bound (wait_s, 0:
+ * the default).  Errors: INVALID (unknown kind, wait_s outside [0, 10]),
+ * STATE (not initialised, or no grid barrier in this context's steps), CUDA. */
+enum { MEMD_INJECT_NONE = 0, MEMD_INJECT_BARRIER_SKEW = 1 };
+memd_status memd_inject(memd_ctx *ctx, int32_t kind, double wait_s);
+
 /* Copy the folded positions (in [0, L)), velocities and image counters into
  * caller host arrays of n x 3, particle major (any may be NULL).
  * Synchronises.  Errors: INVALID, STATE before memd_init_field, CUDA. */

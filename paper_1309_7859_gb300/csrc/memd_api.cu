@@ -112,6 +112,7 @@ StepParams memd_step_params(const memd_ctx* c, int thermo, double gamma, double 
   sp.gamma = gamma;
   sp.kT = kT;
   sp.seed = c->seed;
+  sp.wait_ns = c->wait_ns;
   return sp;
 }
 
@@ -1317,6 +1318,71 @@ memd_status memd_energy(memd_ctx* c, memd_energy_terms* out) {
   out->pad = 0;
   out->step = step;
   return check_err(c);
+}
+
+memd_status memd_dipole_check(memd_ctx* c, double limit, double* ratio) {
+  if (!c || !(limit > 0.0)) return MEMD_ERR_INVALID;
+  if (!c->initialised) return fail(c, MEMD_ERR_STATE, "memd_init_field first");
+  CK(cudaSetDevice(c->device));
+  {
+    const memd_status fe = memd_flush(c);
+    if (fe != MEMD_OK) return fe;
+  }
+  const Mesh& m = c->mesh;
+  const cudaStream_t st = c->stream;
+  double* part = c->red;
+  double* sc = scal(c);
+  const int R = reduce_blocks();
+  launch_field_moments(c->prec, c->D(), c->ie, m.V, part, st);
+  for (int k = 0; k < 4; ++k) launch_finish(part + k * R, 0, sc + 8 + k, st);
+  CKL();
+  double h[4];
+  long long Pl[3];
+  CK(cudaMemcpyAsync(h, sc + 8, 4 * sizeof(double), cudaMemcpyDeviceToHost, st));
+  CK(cudaMemcpyAsync(Pl, c->ds->Plast, sizeof(Pl), cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  // the correction's field eps_eff^-1 P / V, as the gather applies it
+  double P[3], E[3], mp2 = 0.0;
+  for (int d = 0; d < 3; ++d) P[d] = (double)Pl[d] * (m.a / (double)kS);
+  for (int e = 0; e < 3; ++e) {
+    E[e] = (c->Minv[3 * e] * P[0] + c->Minv[3 * e + 1] * P[1] + c->Minv[3 * e + 2] * P[2]) / c->Vbox;
+    mp2 += E[e] * E[e];
+  }
+  // the field of the charges about its mean: sum_d mean over the d-links of
+  // (E_d - mean E_d)^2 = sum_d mean(E_d^2) - sum_d (mean E_d)^2
+  const double Vd = (double)m.V;
+  double fl2 = h[0] / Vd;
+  for (int d = 0; d < 3; ++d) fl2 -= (h[1 + d] / Vd) * (h[1 + d] / Vd);
+  const double efl = std::sqrt(std::max(fl2, 0.0));
+  const double r = efl > 0.0 ? std::sqrt(mp2) / efl : (mp2 > 0.0 ? HUGE_VAL : 0.0);
+  if (ratio) *ratio = r;
+  const memd_status s = check_err(c);
+  if (s != MEMD_OK) return s;
+  if (r > limit)
+    return fail(c, MEMD_ERR_DIPOLE_DRIFT,
+                "the dipole correction outgrew the lattice field: re-initialise the field");
+  return MEMD_OK;
+}
+
+memd_status memd_inject(memd_ctx* c, int32_t kind, double wait_s) {
+  if (!c) return MEMD_ERR_INVALID;
+  if (kind != MEMD_INJECT_NONE && kind != MEMD_INJECT_BARRIER_SKEW)
+    return fail(c, MEMD_ERR_INVALID, "unknown injection");
+  if (!(wait_s >= 0.0) || wait_s > 10.0) return fail(c, MEMD_ERR_INVALID, "wait bound out of range");
+  CK(cudaSetDevice(c->device));
+  drop_graphs(c);  // the step graphs hold the wait bound
+  c->wait_ns = wait_s > 0.0 ? (unsigned long long)(wait_s * 1e9) : kBarrierWaitNs;
+  if (kind == MEMD_INJECT_BARRIER_SKEW) {
+    if (!c->initialised) return fail(c, MEMD_ERR_STATE, "memd_init_field first");
+    if (!c->coop) return fail(c, MEMD_ERR_STATE, "the steps of this context have no grid barrier");
+    // one extra arrival: the next barrier's count cannot reach its target
+    unsigned long long n = 0;
+    CK(cudaStreamSynchronize(c->stream));
+    CK(cudaMemcpy(&n, &c->ds->bar_arrivals, sizeof(n), cudaMemcpyDeviceToHost));
+    n += 1;
+    CK(cudaMemcpy(&c->ds->bar_arrivals, &n, sizeof(n), cudaMemcpyHostToDevice));
+  }
+  return MEMD_OK;
 }
 
 memd_status memd_get_particles(memd_ctx* c, double* pos, double* vel, int32_t* img) {

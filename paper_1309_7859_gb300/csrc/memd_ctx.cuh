@@ -89,6 +89,7 @@ struct memd_ctx {
   bool fcfg_ready = false;  // fcfg autotuned (at the first step that needs it)
   int field_kernel = 0;
   int field_shape[4] = {0, 0, 0, 0};  // {ty, zchunk, planes_ahead, rows_nt}; 0: autotuned
+  unsigned long long wait_ns = memd::kBarrierWaitNs;  // grid-barrier wait bound (memd_inject)
   TmaMaps tma{};
   bool tma_ok = false;
   bool sig_ready = false;

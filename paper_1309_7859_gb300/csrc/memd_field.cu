@@ -770,6 +770,39 @@ void launch_field_energy(const Mesh& m, int prec, const void* D, const void* B, 
         m, (const double*)D, (const double*)B, (const double*)ie, coefB, part_el, part_mag);
 }
 
+// block sums over the links of E = D ie: part[b] of E^2 (all 3V links),
+// part[(1 + d) R + b] of E_d (the V links of component d)
+template <typename T>
+__global__ void __launch_bounds__(kRedThreads)
+    k_field_moments(const T* __restrict__ D, const T* __restrict__ ie, int64_t V, double* part) {
+  __shared__ double sh[kRedThreads / 32];
+  const int R = (int)gridDim.x;
+  double s2 = 0.0, s[3] = {0.0, 0.0, 0.0};
+  for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < V;
+       v += (int64_t)gridDim.x * blockDim.x)
+    for (int d = 0; d < 3; ++d) {
+      const double e = (double)D[d * V + v] * (double)ie[d * V + v];
+      s[d] += e;
+      s2 += e * e;
+    }
+  s2 = block_sum(s2, sh);
+  if (threadIdx.x == 0) part[blockIdx.x] = s2;
+  for (int d = 0; d < 3; ++d) {
+    const double t = block_sum(s[d], sh);
+    if (threadIdx.x == 0) part[(1 + d) * R + blockIdx.x] = t;
+  }
+}
+
+void launch_field_moments(int prec, const void* D, const void* ie, int64_t V, double* part,
+                          cudaStream_t st) {
+  if (prec == 1)
+    k_field_moments<float><<<kRedBlocks, kRedThreads, 0, st>>>((const float*)D, (const float*)ie,
+                                                              V, part);
+  else
+    k_field_moments<double><<<kRedBlocks, kRedThreads, 0, st>>>((const double*)D,
+                                                               (const double*)ie, V, part);
+}
+
 void launch_gauss_check(const Mesh& m, int prec, const void* D, const long long* Lg,
                         const long long* Q, double a2, double* part_res,
                         unsigned long long* mismatch, cudaStream_t st) {

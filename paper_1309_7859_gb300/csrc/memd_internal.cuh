@@ -208,7 +208,9 @@ struct StepParams {
   double gamma;
   double kT;
   unsigned long long seed;
+  unsigned long long wait_ns;  // bound of the single-launch step's grid-barrier wait
 };
+constexpr unsigned long long kBarrierWaitNs = 200000000ull;  // 0.2 s
 // single-launch step (memd_particles.cu): the whole time step in one
 // cooperative launch, for systems small enough that launch gaps dominate
 constexpr int kCoopFieldWarps = 11;                  // 34 x 10 site tile of 8 rows
@@ -415,6 +417,10 @@ void launch_particle_energy(const Mesh& m, const StepParams& sp, Particles p,
 void launch_field_energy(const Mesh& m, int prec, const void* D, const void* B,
                          const void* ie, double coefB, double* part_el, double* part_mag,
                          cudaStream_t st);
+// partial sums (reduce_blocks() each) of E^2 over the 3V links, then of
+// E_x, E_y, E_z over their V links, E = D / eps
+void launch_field_moments(int prec, const void* D, const void* ie, int64_t V, double* part,
+                          cudaStream_t st);
 // Gauss check: mismatch count of div Lg vs Q and max |a^2 div D - Q 2^-48|
 void launch_gauss_check(const Mesh& m, int prec, const void* D, const long long* Lg,
                         const long long* Q, double a2, double* part_res,

@@ -1365,7 +1365,7 @@ __global__ void __launch_bounds__(kBatchStepThreads, 2)
 // by the global timer (0.2 s); a wait that runs out sets kErrTimeout and
 // goes on, the step is then void and the host resets the count when it
 // reports the error.
-__device__ inline void grid_barrier(DevState* ds, unsigned nctas) {
+__device__ inline void grid_barrier(DevState* ds, unsigned nctas, unsigned long long wait_ns) {
   __syncthreads();
   if (threadIdx.x == 0) {
     unsigned long long a;
@@ -1385,7 +1385,7 @@ __device__ inline void grid_barrier(DevState* ds, unsigned nctas) {
         if (cur >= target) break;
         if ((it & 255u) == 0u) {
           asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-          if (t - t0 > 200000000ull) {
+          if (t - t0 > wait_ns) {
             atomicOr(&ds->err, kErrTimeout);
             break;
           }
@@ -1456,7 +1456,7 @@ __global__ void __launch_bounds__(kCoopThreads)
       quad_dipole_add(ds->Pacc,
                       deposit_body(m, sp, P, Tcur, ds, b + lane, (const char*)ie, (int)sizeof(T)));
   }
-  grid_barrier(ds, G);
+  grid_barrier(ds, G, sp.wait_ns);
   if (pwarp) {
     // the dipole sum of this move and the step counter, read once; the
     // particle warp then signals field warp 0 (named barrier 2), which takes

@@ -29,7 +29,7 @@ EXPORTS = ("memd_default_options", "memd_status_string", "memd_last_error", "mem
            "memd_energy", "memd_get_particles", "memd_set_particles", "memd_move",
            "memd_get_fields", "memd_set_fields", "memd_compute_forces", "memd_set_eps",
            "memd_step_host", "memd_io_buffers", "memd_step_io", "memd_state_bytes",
-           "memd_save_state", "memd_load_state",
+           "memd_save_state", "memd_load_state", "memd_dipole_check", "memd_inject",
            "memd_get_setup",
            "memd_get_kernel_stats", "memd_reset_kernel_stats", "memd_synchronize",
            "memd_batch_create", "memd_batch_create_kernel", "memd_batch_step",
@@ -178,6 +178,8 @@ def lib(build_if_missing=True):
     L.memd_compute_forces.argtypes = [vp]
     L.memd_set_eps.argtypes = [vp, C.POINTER(EpsProfile), C.c_int32]
     L.memd_get_setup.argtypes = [vp, f64p, f64p, f64p]
+    L.memd_dipole_check.argtypes = [vp, C.c_double, f64p]
+    L.memd_inject.argtypes = [vp, C.c_int32, C.c_double]
     L.memd_get_kernel_stats.argtypes = [vp, C.POINTER(KernelStats)]
     L.memd_reset_kernel_stats.argtypes = [vp]
     L.memd_synchronize.argtypes = [vp]
@@ -491,6 +493,18 @@ class Memd:
 
     def compute_forces(self):
         self._check(self._L.memd_compute_forces(self._h), "memd_compute_forces")
+
+    def dipole_check(self, limit):
+        """memd_dipole_check: (status, ratio) of the dipole correction's field to
+        the RMS lattice field; status 8 (DIPOLE_DRIFT) above `limit`."""
+        r = C.c_double(0.0)
+        st = self._L.memd_dipole_check(self._h, float(limit), C.byref(r))
+        return st, r.value
+
+    def inject(self, kind="barrier_skew", wait_s=0.0):
+        """memd_inject: host-side failure injection for tests."""
+        k = {"none": 0, "barrier_skew": 1}[kind]
+        self._check(self._L.memd_inject(self._h, k, float(wait_s)), "memd_inject")
 
     def set_eps(self, eps, relax=False):
         """New permittivity profile (an inputs.EpsSpec or dict); D is kept, or

@@ -121,3 +121,92 @@ def test_server_request_whose_setup_fails_leaves_the_others_intact():
         assert srv.status(rid) == 2
         check_same(srv.result(rid), alone(s))
     srv.close()
+
+
+def test_grid_barrier_wait_runs_out_and_stepping_resumes():
+    # one extra arrival on the grid-barrier count (host side): the next
+    # single-launch step's barrier cannot complete, its bounded wait (2 ms
+    # here) runs out, the step is void and the next synchronising call
+    # reports TIMEOUT; reloaded from a saved state, the context then steps
+    # exactly as an uninterrupted one
+    from paper_1309_7859_gb300.memd import MemdError
+    TH = (1.0, 1.0)
+    sysc = small_system((16, 16, 12), 60, SLAB, precision="fp32", dt=0.005)
+    g = make(sysc, step_engine="single")
+    g.init_field(sysc.x, sysc.q, sysc.m, sysc.v)
+    g.step(2, thermostat=TH)
+    assert g.kernel_stats().single
+    saved = g.save_state()
+    ref = make(sysc, step_engine="single")
+    ref.init_field(sysc.x, sysc.q, sysc.m, sysc.v)
+    ref.load_state(saved)
+    ref.step(6, thermostat=TH)
+    g.inject("barrier_skew", wait_s=0.002)
+    g.step(1, thermostat=TH)
+    with pytest.raises(MemdError) as err:
+        g.energy()
+    assert err.value.status == 9                 # MEMD_ERR_TIMEOUT
+    g.inject("none")                             # the default bound again
+    g.load_state(saved)
+    g.step(6, thermostat=TH)
+    D, B, Lg = g.fields()
+    Dr, Br, Lgr = ref.fields()
+    assert np.array_equal(D, Dr) and np.array_equal(B, Br) and np.array_equal(Lg, Lgr)
+    assert np.array_equal(g.particles()[0], ref.particles()[0])
+    assert np.array_equal(g.forces(), ref.forces())
+    assert g.energy()["gauss_exact"] == 1.0
+
+
+def test_barrier_skew_needs_a_grid_barrier():
+    from paper_1309_7859_gb300.memd import MemdError
+    sysc = small_system((12, 10, 8), 20, SLAB)
+    g = make(sysc, step_engine="graph")
+    g.init_field(sysc.x, sysc.q, sysc.m, sysc.v)
+    g.step(1)
+    with pytest.raises(MemdError) as err:
+        g.inject("barrier_skew", wait_s=0.002)
+    assert err.value.status == 10                # STATE: no grid barrier
+    g.inject("none")
+    g.step(1)
+
+
+def test_dipole_drift_of_a_driven_pair():
+    # Sec. V: a pair pulled apart (its velocities imposed every 150 steps, a
+    # current driven through the box at a fifth of the speed of light, the
+    # fields following the dynamics) makes the dipole moment of the unfolded
+    # charges grow until the metallic correction outweighs the field of the
+    # charges; the check reports it, and a fresh initial solution at the
+    # present positions clears it
+    from paper_1309_7859_gb300.memd import Memd
+    N, eps = 16, 2.0
+    g = Memd((N, N, N), (float(N),) * 3, EpsSpec("const", 0, (eps,)), dt=0.05, precision="fp64")
+    x0 = np.array([[7.2, 8.3, 8.1], [8.6, 8.3, 8.1]])
+    q = np.array([1, -1], dtype=np.int32)
+    drive = np.array([[0.2, 0.0, 0.0], [-0.2, 0.0, 0.0]])
+    g.init_field(x0, q, None, drive)
+    limit = 1.0
+    ratios = []
+    tripped = None
+    for k in range(40):
+        g.step(150)
+        x, v, img = g.particles()
+        g.set_particles(x=x, v=drive, img=img)
+        st, r = g.dipole_check(limit)
+        assert st == (8 if r > limit else 0)
+        ratios.append(r)
+        if st == 8 and tripped is None:
+            tripped = k
+    # the ratio against its definition, from the fields, P and eps_eff^-1
+    D, _, _ = g.fields()
+    ie, _, M = g.setup()
+    P = np.array([g.energy()[f"P{d}"] for d in range(3)])
+    E = D * ie
+    fl = np.sqrt(sum(np.mean((E[d] - E[d].mean()) ** 2) for d in range(3)))
+    want = np.linalg.norm(M @ P / N ** 3) / fl
+    assert abs(ratios[-1] - want) <= 1e-10 * want
+    assert P[0] > 80                             # about 100 cells apart, unfolded
+    assert tripped is not None and ratios[-1] > 5 * ratios[0]
+    x, _, img = g.particles()
+    g.init_field(x, q)                           # folded positions: P back inside the box
+    st, r = g.dipole_check(limit)
+    assert st == 0 and r < limit
