@@ -618,12 +618,13 @@ typedef struct memd_server_stats {
   double budget_use_sum;   /* sum over rounds of resident footprint / budget */
   int64_t rounds;          /* memd_server_pump calls */
   int64_t steps_rounds;    /* rounds that stepped the batch */
-  int64_t rebuilds;        /* batch rebuilds after membership changes */
+  int64_t rebuilds;        /* batches created (one while requests keep it resident) */
   int64_t admitted;
   int64_t link_updates;    /* 3 V per system per step, summed */
   int64_t particle_steps;
   double step_gpu_s;       /* device time of the batch steps (CUDA events on the server's
                               stream) */
+  int64_t table_updates;   /* batch tables rebuilt in place for a new membership */
 } memd_server_stats;
 
 /* Counters since create into *out (Errors: INVALID); the reason for the

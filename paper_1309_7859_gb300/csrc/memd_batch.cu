@@ -225,7 +225,7 @@ void free_io(memd_batch* b) {
 // field buffer not 16-byte aligned).
 // (Re)build the descriptor table and the CTA maps from the members' state;
 // the batch parity restarts at 0 with each member's current buffer first.
-memd_status build_tables(memd_batch* b) {
+memd_status build_tables(memd_batch* b, bool sync = true) {
   drop(b);
   free_tables(b);
   const int R = (int)b->m.size();
@@ -348,7 +348,9 @@ memd_status build_tables(memd_batch* b) {
       b->f_rows = 0;  // some member does not fit the row kernel: site tiles
     }
   }
-  BCK(cudaStreamSynchronize(b->stream));
+  // the host tables were staged by the copies above, so they may go; a
+  // caller that queues more work on the stream need not wait
+  if (sync) BCK(cudaStreamSynchronize(b->stream));
   return MEMD_OK;
 }
 
@@ -599,6 +601,38 @@ memd_status batch_refresh(memd_batch* b) {
 }
 
 }  // namespace
+
+// New members for an existing batch (the request server between rounds):
+// the tables are rebuilt with the batch's field-kernel choice, stream-ordered
+// behind the work already queued (the old tables and step graphs are released
+// behind it too), with no stream or event created and no synchronisation.
+// Members must share the batch's device, precision and stream.  Members that
+// were not in the batch before get the per-particle constants of the
+// batch's thermostat.
+memd_status memd_batch_update_members(memd_batch* b, int32_t count, memd_ctx* const* members) {
+  if (!b || count < 1 || !members) return MEMD_ERR_INVALID;
+  for (int r = 0; r < count; ++r) {
+    const memd_ctx* c = members[r];
+    if (!c || !c->initialised || c->device != b->device || c->prec != b->prec ||
+        c->stream != b->stream)
+      return bfail(b, MEMD_ERR_INVALID, "member does not fit the batch");
+  }
+  BCK(cudaSetDevice(b->device));
+  harvest(b);
+  std::vector<memd_ctx*> old = b->m;
+  b->m.assign(members, members + count);
+  b->gen.assign(count, -1);
+  b->base.assign(count, 0);
+  if (b->g_thermo >= 0)
+    for (memd_ctx* c : b->m)
+      if (std::find(old.begin(), old.end(), c) == old.end()) {
+        launch_particle_constants(memd_step_params(c, b->g_thermo, b->g_gamma, b->g_kT), c->P,
+                                  b->stream);
+        c->sig_ready = false;
+      }
+  free_io(b);
+  return build_tables(b, false);
+}
 
 // the batch, with its field tiles autotuned (tune) or the defaults
 memd_status memd_batch_create_opt(int32_t count, memd_ctx* const* members, memd_batch** out,

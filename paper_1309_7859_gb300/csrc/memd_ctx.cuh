@@ -121,3 +121,6 @@ bool rows_plan(const std::vector<memd_ctx*>& m, int prec, int nt, int nctas,
 // MEMD_FIELD_SITE or MEMD_FIELD_ROWS)
 memd_status memd_batch_create_opt(int32_t count, memd_ctx* const* members, memd_batch** out,
                                   bool tune, int kind);
+// new members for a batch, its tables rebuilt behind the queued work (no
+// synchronisation); members share the batch's device, precision and stream
+memd_status memd_batch_update_members(memd_batch* b, int32_t count, memd_ctx* const* members);

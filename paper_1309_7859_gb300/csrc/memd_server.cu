@@ -75,8 +75,13 @@ struct memd_server {
   int in_flight = 0;
   bool stop = false;
   bool own_stream = false;  // the server created opt.cuda_stream
-  cudaEvent_t ev0 = nullptr, ev1 = nullptr;  // around the last batch step
-  bool step_timed = false;
+  // an event pair around every quantum (added to step_gpu_s once both have
+  // completed), the end of the latest quantum (ev_done), the event pairs free
+  // for reuse; results of leaving requests are copied on rstream
+  std::deque<std::pair<cudaEvent_t, cudaEvent_t>> timed, spare;
+  cudaEvent_t ev_done = nullptr;
+  cudaStream_t rstream = nullptr;
+  bool any_launched = false;
 };
 
 constexpr int kAdmitWorkers = 3;  // concurrent setups unless the options say otherwise
@@ -302,8 +307,13 @@ void memd_server_destroy(memd_server* s) {
   s->batch = nullptr;
   for (auto& kv : s->reqs)
     if (kv.second.ctx) memd_destroy(kv.second.ctx);
-  if (s->ev0) cudaEventDestroy(s->ev0);
-  if (s->ev1) cudaEventDestroy(s->ev1);
+  for (auto* q : {&s->timed, &s->spare})
+    for (auto& pr : *q) {
+      cudaEventDestroy(pr.first);
+      cudaEventDestroy(pr.second);
+    }
+  if (s->ev_done) cudaEventDestroy(s->ev_done);
+  if (s->rstream) cudaStreamDestroy(s->rstream);
   if (s->own_stream) cudaStreamDestroy((cudaStream_t)s->opt.cuda_stream);
   delete s;
 }
@@ -344,42 +354,37 @@ memd_status memd_server_pump(memd_server* s, int32_t* n_active, int32_t* n_queue
                              int32_t* n_done) {
   memd::NvtxRange nvtx_("memd_server_pump");
   if (!s) return MEMD_ERR_INVALID;
-  // 1. retire requests that have taken all their steps (the batch refers to
-  // its members, so it goes first when any member leaves)
-  if (s->batch) {
-    memd_status st = memd_batch_synchronize(s->batch);
-    if (st != MEMD_OK) return sfail(s, st, "batch step failed");
-    if (s->step_timed) {
-      float ms = 0.f;
-      if (cudaEventElapsedTime(&ms, s->ev0, s->ev1) == cudaSuccess) s->stats.step_gpu_s += 1e-3 * ms;
-      cudaGetLastError();
-      s->step_timed = false;
-    }
-    bool leaving = false;
-    for (int64_t id : s->active) leaving = leaving || s->reqs[id].remaining <= 0;
-    if (leaving) {
-      memd_batch_destroy(s->batch);
-      s->batch = nullptr;
-    }
-  }
-  std::vector<int64_t> keep;
-  for (int64_t id : s->active) {
-    memd_server::Req& r = s->reqs[id];
-    if (r.remaining <= 0) {
-      retire(s, r);
-      s->dirty = true;
-    } else {
-      keep.push_back(id);
-    }
-  }
-  s->active.swap(keep);
-  // 2. systems whose setup has finished join; queued requests go to the
-  // admission workers in arrival order while memory and slots allow (their
-  // footprint is reserved from the hand-over on)
+  const cudaStream_t sst = (cudaStream_t)s->opt.cuda_stream;
   {
     const memd_status se = start_workers(s);
     if (se != MEMD_OK) return sfail(s, se, "admission workers");
   }
+  if (!s->ev_done && (cudaEventCreateWithFlags(&s->ev_done, cudaEventDisableTiming) != cudaSuccess ||
+                      cudaStreamCreateWithFlags(&s->rstream, cudaStreamNonBlocking) != cudaSuccess))
+    return sfail(s, MEMD_ERR_CUDA, "server events");
+  // device time of the quanta that have finished
+  auto harvest = [&](bool wait) {
+    while (!s->timed.empty()) {
+      auto pr = s->timed.front();
+      if (wait) cudaEventSynchronize(pr.second);
+      if (cudaEventQuery(pr.second) != cudaSuccess) break;
+      float ms = 0.f;
+      if (cudaEventElapsedTime(&ms, pr.first, pr.second) == cudaSuccess)
+        s->stats.step_gpu_s += 1e-3 * ms;
+      s->timed.pop_front();
+      s->spare.push_back(pr);
+    }
+    cudaGetLastError();
+  };
+  harvest(false);
+  // 1. requests whose last steps are in the quantum in flight leave the
+  // batch now (the host counted their steps at launch); their results are
+  // collected below, once that quantum has finished
+  std::vector<int64_t> keep, leaving;
+  for (int64_t id : s->active) (s->reqs[id].remaining <= 0 ? leaving : keep).push_back(id);
+  // 2. systems whose setup has finished join; queued requests go to the
+  // admission workers in arrival order while memory and slots allow (their
+  // footprint is reserved from the hand-over on)
   std::vector<std::pair<memd_server::Req*, memd_status>> got;
   int in_flight = 0;
   {
@@ -387,6 +392,7 @@ memd_status memd_server_pump(memd_server* s, int32_t* n_active, int32_t* n_queue
     got.swap(s->ready);
     in_flight = s->in_flight;
   }
+  bool changed = !leaving.empty();
   for (auto& pr : got) {
     memd_server::Req& r = *pr.first;
     if (pr.second != MEMD_OK) {
@@ -395,10 +401,10 @@ memd_status memd_server_pump(memd_server* s, int32_t* n_active, int32_t* n_queue
       continue;
     }
     r.state = MEMD_REQ_RUNNING;
-    s->active.push_back(r.id);
-    s->dirty = true;
+    keep.push_back(r.id);
+    changed = true;
   }
-  while (!s->queue.empty() && (int)s->active.size() + in_flight < s->opt.max_slots) {
+  while (!s->queue.empty() && (int)(keep.size() + leaving.size()) + in_flight < s->opt.max_slots) {
     memd_server::Req& r = s->reqs[s->queue.front()];
     if (r.footprint > s->opt.budget_bytes) {
       r.state = MEMD_REQ_FAILED;
@@ -417,38 +423,41 @@ memd_status memd_server_pump(memd_server* s, int32_t* n_active, int32_t* n_queue
     in_flight += 1;
     s->cv_todo.notify_one();
   }
-  if (s->active.empty() && in_flight > 0) {
-    // nothing to step yet: wait a little for a setup to finish
-    std::unique_lock<std::mutex> g(s->mu);
-    s->cv_ready.wait_for(g, std::chrono::milliseconds(2), [&] { return !s->ready.empty(); });
-  }
-  // 3. batch of the live systems, one quantum (bounded by the nearest finish)
-  if (s->dirty) {
-    s->stats.rebuilds += 1;
-    if (s->batch) memd_batch_destroy(s->batch);
-    s->batch = nullptr;
-    if (!s->active.empty()) {
+  // 3. the next quantum, queued behind the one in flight: the batch's tables
+  // are updated in place when its membership changed
+  s->active.swap(keep);
+  bool launched = false;
+  if (!s->active.empty()) {
+    if (changed || !s->batch) {
       std::vector<memd_ctx*> m;
       for (int64_t id : s->active) m.push_back(s->reqs[id].ctx);
-      memd_status st = memd_batch_create_opt((int32_t)m.size(), m.data(), &s->batch, false,
-                                              MEMD_FIELD_AUTO);
-      if (st != MEMD_OK) return sfail(s, st, "batch rebuild failed");
+      memd_status st;
+      if (!s->batch) {
+        st = memd_batch_create_opt((int32_t)m.size(), m.data(), &s->batch, false, MEMD_FIELD_AUTO);
+        s->stats.rebuilds += 1;
+      } else {
+        st = memd_batch_update_members(s->batch, (int32_t)m.size(), m.data());
+      }
+      if (st != MEMD_OK) return sfail(s, st, "batch tables");
+      s->stats.table_updates += 1;
     }
-    s->dirty = false;
-  }
-  if (s->batch) {
     int64_t k = s->opt.quantum;
     for (int64_t id : s->active) k = std::min(k, s->reqs[id].remaining);
     if (k > 0) {
       memd_thermostat th{s->opt.gamma, s->opt.kT};
-      const cudaStream_t sst = (cudaStream_t)s->opt.cuda_stream;
-      if (!s->ev0 && (cudaEventCreate(&s->ev0) != cudaSuccess || cudaEventCreate(&s->ev1) != cudaSuccess))
-        return sfail(s, MEMD_ERR_CUDA, "events");
-      cudaEventRecord(s->ev0, sst);
+      std::pair<cudaEvent_t, cudaEvent_t> pr{nullptr, nullptr};
+      if (!s->spare.empty()) {
+        pr = s->spare.front();
+        s->spare.pop_front();
+      } else if (cudaEventCreate(&pr.first) != cudaSuccess ||
+                 cudaEventCreate(&pr.second) != cudaSuccess) {
+        return sfail(s, MEMD_ERR_CUDA, "server events");
+      }
+      cudaEventRecord(pr.first, sst);
       memd_status st = memd_batch_step(s->batch, k, s->opt.thermostat ? &th : nullptr);
       if (st != MEMD_OK) return sfail(s, st, "batch step failed");
-      cudaEventRecord(s->ev1, sst);
-      s->step_timed = true;
+      cudaEventRecord(pr.second, sst);
+      s->timed.push_back(pr);
       for (int64_t id : s->active) {
         s->reqs[id].remaining -= k;
         s->stats.link_updates += 3 * k * (int64_t)s->reqs[id].mesh[0] * s->reqs[id].mesh[1] *
@@ -456,7 +465,32 @@ memd_status memd_server_pump(memd_server* s, int32_t* n_active, int32_t* n_queue
         s->stats.particle_steps += k * (int64_t)s->reqs[id].q.size();
       }
       s->stats.steps_rounds += 1;
+      launched = true;
     }
+  }
+  // 4. the quantum before this one has finished once the stream reaches this
+  // point; results of the requests that left are copied on the server's
+  // second stream meanwhile, so the quantum just queued keeps the GPU busy
+  if (!leaving.empty() || (!launched && s->any_launched)) {
+    if (cudaStreamSynchronize(s->rstream) != cudaSuccess || cudaEventSynchronize(s->ev_done) != cudaSuccess)
+      return sfail(s, MEMD_ERR_CUDA, "waiting for the last quantum");
+    for (int64_t id : leaving) {
+      memd_server::Req& r = s->reqs[id];
+      r.ctx->stream = s->rstream;
+      retire(s, r);
+    }
+  }
+  if (launched) {
+    cudaEventRecord(s->ev_done, sst);
+    s->any_launched = true;
+  } else if (s->any_launched) {
+    harvest(true);  // the stream has drained
+    s->any_launched = false;
+  }
+  if (s->active.empty() && in_flight > 0) {
+    // nothing to step yet: wait a little for a setup to finish
+    std::unique_lock<std::mutex> g(s->mu);
+    s->cv_ready.wait_for(g, std::chrono::milliseconds(2), [&] { return !s->ready.empty(); });
   }
   s->stats.rounds += 1;
   int64_t resident = 0;

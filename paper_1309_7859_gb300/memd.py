@@ -110,7 +110,7 @@ class ServerStats(C.Structure):
     _fields_ = [("setup_s", C.c_double), ("budget_use_sum", C.c_double), ("rounds", C.c_int64),
                 ("steps_rounds", C.c_int64), ("rebuilds", C.c_int64), ("admitted", C.c_int64),
                 ("link_updates", C.c_int64), ("particle_steps", C.c_int64),
-                ("step_gpu_s", C.c_double)]
+                ("step_gpu_s", C.c_double), ("table_updates", C.c_int64)]
 
 
 class IoBuffers(C.Structure):
