@@ -1034,6 +1034,84 @@ int32_t orc_set_eps(orc_sys *s, const orc_eps *eps, int32_t relax) {
   return ORC_OK;
 }
 
+/* ----------------------------------------------- eps from salt density
+ * Sec. I motivation, reading in memd_oracle.h: cloud-in-cell |q| density at
+ * the vertices, periodic Gaussian smoothing axis by axis, a clamped linear
+ * map to eps, applied as vertex values. */
+void orc_smooth_periodic(const int32_t N[3], double sigma, double *rho) {
+  if (!(sigma > 0.0)) return;
+  int R = (int)ceil(3.0 * sigma);
+  double *w = (double *)malloc(sizeof(double) * (2 * R + 1));
+  double wsum = 0.0;
+  for (int j = -R; j <= R; ++j) {
+    w[j + R] = exp(-(double)(j * j) / (2.0 * sigma * sigma));
+    wsum += w[j + R];
+  }
+  for (int j = 0; j <= 2 * R; ++j) w[j] /= wsum;
+  int64_t V = (int64_t)N[0] * N[1] * N[2];
+  double *tmp = (double *)malloc(sizeof(double) * V);
+  for (int d = 0; d < 3; ++d) {
+    for (int64_t k = 0; k < N[2]; ++k)
+      for (int64_t jj = 0; jj < N[1]; ++jj)
+        for (int64_t i = 0; i < N[0]; ++i) {
+          int64_t c[3] = {i, jj, k};
+          double acc = 0.0;
+          for (int j = -R; j <= R; ++j) {
+            int64_t e[3] = {c[0], c[1], c[2]};
+            e[d] = ((e[d] + j) % N[d] + N[d]) % N[d];
+            acc += w[j + R] * rho[e[0] + N[0] * (e[1] + N[1] * e[2])];
+          }
+          tmp[i + N[0] * (jj + N[1] * k)] = acc;
+        }
+    memcpy(rho, tmp, sizeof(double) * V);
+  }
+  free(tmp);
+  free(w);
+}
+
+int32_t orc_eps_from_density(orc_sys *s, const double rule[5], int32_t relax, double *eps_out) {
+  double eps0 = rule[0], slope = rule[1], lo = rule[2], hi = rule[3], sigma = rule[4];
+  double *rho = (double *)malloc(sizeof(double) * s->V);
+  double *ev = (double *)malloc(sizeof(double) * s->V);
+  if (!rho || !ev) {
+    free(rho);
+    free(ev);
+    return ORC_ERR_OOM;
+  }
+  /* |q| weights in fixed point (exact), then in units of e */
+  for (int64_t v = 0; v < s->V; ++v) rho[v] = 0.0;
+  int64_t *Qa = (int64_t *)calloc((size_t)s->V, sizeof(int64_t));
+  for (int64_t p = 0; p < s->n; ++p) {
+    int32_t c[3], f[3];
+    for (int d = 0; d < 3; ++d) quantize(s, d, s->x[3 * p + d], &c[d], &f[d]);
+    int64_t aq = s->q[p] < 0 ? -(int64_t)s->q[p] : (int64_t)s->q[p];
+    for (int az = 0; az < 2; ++az)
+      for (int ay = 0; ay < 2; ++ay)
+        for (int ax = 0; ax < 2; ++ax)
+          Qa[vidx(s, c[0] + ax, c[1] + ay, c[2] + az)] +=
+              aq * (wgt(f[0], ax) * wgt(f[1], ay) * wgt(f[2], az));
+  }
+  for (int64_t v = 0; v < s->V; ++v) rho[v] = (double)Qa[v] * ldexp(1.0, -48);
+  free(Qa);
+  orc_smooth_periodic(s->N, sigma, rho);
+  double mean = 0.0;
+  for (int64_t v = 0; v < s->V; ++v) mean += rho[v];
+  mean /= (double)s->V;
+  for (int64_t v = 0; v < s->V; ++v) {
+    double e = mean > 0.0 ? eps0 + slope * (rho[v] / mean - 1.0) : eps0;
+    ev[v] = e < lo ? lo : (e > hi ? hi : e);
+  }
+  if (eps_out) memcpy(eps_out, ev, sizeof(double) * s->V);
+  orc_eps e;
+  memset(&e, 0, sizeof(e));
+  e.kind = ORC_EPS_VERTICES;
+  e.values = ev;
+  int32_t st = orc_set_eps(s, &e, relax);
+  free(rho);
+  free(ev);
+  return st;
+}
+
 /* -------------------------------------------------------------- time step
  * One step of the coupled system, leapfrog in the fields and velocity
  * Verlet in the particles:

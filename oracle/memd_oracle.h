@@ -116,6 +116,23 @@ int32_t orc_relax(orc_sys *s, double tol, int32_t maxit, int32_t *iters);
  * as orc_init_field does (B = 0).  Forces are gathered again. */
 int32_t orc_set_eps(orc_sys *s, const orc_eps *eps, int32_t relax);
 
+/* Permittivity from the local salt density (Sec. I: the dielectric
+ * response of water falls with its salt content; the paper gives no rule,
+ * this is the reading used here).  rho(v) = sum over charges of |q| times
+ * their cloud-in-cell weight at vertex v (in e); smoothed by the periodic
+ * Gaussian of sigma cells, truncated at R = ceil(3 sigma) cells, weights
+ * exp(-j^2 / (2 sigma^2)) normalised to sum 1, along x, then y, then z
+ * (sigma = 0: no smoothing); then eps(v) = eps0 + slope (rho(v) / mean(rho)
+ * - 1), clamped to [eps_lo, eps_hi] (eps0 clamped when there are no
+ * charges).  The vertex values are applied as ORC_EPS_VERTICES with theta
+ * = 0 (links take the mean of their ends) by orc_set_eps(relax).  rule =
+ * {eps0, slope, eps_lo, eps_hi, sigma}; eps_out (V, may be NULL) receives
+ * the vertex values.  Returns orc_set_eps's status. */
+int32_t orc_eps_from_density(orc_sys *s, const double rule[5], int32_t relax, double *eps_out);
+/* the density and smoothing steps alone: rho (V) on input is smoothed in
+ * place as above */
+void orc_smooth_periodic(const int32_t N[3], double sigma, double *rho);
+
 /* building blocks exposed for the tests */
 void orc_cic_charges(const orc_sys *s, int64_t *Q);
 int32_t orc_gauss_scan(const int32_t N[3], const int64_t *Q, int64_t *flux);

@@ -92,6 +92,9 @@ def lib():
         L.orc_set_eps.restype = C.c_int32
         L.orc_set_eps.argtypes = [C.c_void_p, C.POINTER(_Eps), C.c_int32]
         L.orc_cic_charges.argtypes = [C.c_void_p, i64p]
+        L.orc_eps_from_density.restype = C.c_int32
+        L.orc_eps_from_density.argtypes = [C.c_void_p, f64p, C.c_int32, f64p]
+        L.orc_smooth_periodic.argtypes = [i32p, C.c_double, f64p]
         L.orc_gauss_scan.restype = C.c_int32
         L.orc_gauss_scan.argtypes = [i32p, i64p, i64p]
         L.orc_divergence.argtypes = [i32p, i64p, i64p]
@@ -130,6 +133,14 @@ def gauss_scan(N, Q):
     flux = np.zeros(3 * Q.size, dtype=np.int64)
     st = lib().orc_gauss_scan(_p(n, C.c_int32), _p(Q, C.c_int64), _p(flux, C.c_int64))
     return st, flux
+
+
+def smooth_periodic(N, sigma, rho):
+    """The oracle's periodic Gaussian smoothing of a vertex array (x fastest)."""
+    n = np.asarray(N, dtype=np.int32)
+    r = np.ascontiguousarray(rho, dtype=np.float64).ravel().copy()
+    lib().orc_smooth_periodic(_p(n, C.c_int32), float(sigma), _p(r, C.c_double))
+    return r
 
 
 def divergence(N, flux):
@@ -286,6 +297,18 @@ class OracleSystem:
         del keep
         if st != OK:
             raise OracleError(f"orc_set_eps failed with status {st}")
+
+    def eps_from_density(self, eps0, slope, eps_lo, eps_hi, sigma, relax=False):
+        """orc_eps_from_density: the vertex permittivity from the local |q|
+        density (returned as [Nz, Ny, Nx]), applied to the system."""
+        rule = np.array([eps0, slope, eps_lo, eps_hi, sigma], dtype=np.float64)
+        out = np.zeros(self.V, dtype=np.float64)
+        st = self._lib.orc_eps_from_density(self._h, _p(rule, C.c_double), 1 if relax else 0,
+                                            _p(out, C.c_double))
+        if st != OK:
+            raise OracleError(f"orc_eps_from_density failed with status {st}")
+        Nx, Ny, Nz = self.N
+        return out.reshape(Nz, Ny, Nx)
 
     def energy(self):
         out = np.zeros(len(ENERGY_KEYS))

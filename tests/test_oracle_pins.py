@@ -901,3 +901,96 @@ def test_set_eps_failure_leaves_the_system_unchanged():
     with pytest.raises(O.OracleError):
         s.set_eps(dict(kind=O.EPS_LINKS, values=-np.ones(3 * 512)))
     assert np.array_equal(s.field("ie"), ie0) and np.array_equal(s.Minv, M0)
+
+
+# ------------------------------------------- permittivity from salt density
+# Reading of Sec. I (eps falls with the local salt content; the paper gives
+# no rule): |q| cloud-in-cell density at the vertices, periodic Gaussian
+# smoothing, eps = eps0 + slope (rho / mean - 1) clamped, applied as vertex
+# values.  Pinned by a uniform density, the convolution theorem, an exact
+# profile through the map and clamps, and the salt-modulated workload.
+def _gauss_kernel(sigma, N):
+    R = int(np.ceil(3 * sigma))
+    j = np.arange(-R, R + 1)
+    w = np.exp(-(j * j) / (2 * sigma * sigma))
+    w /= w.sum()
+    k = np.zeros(N)
+    np.add.at(k, j % N, w)           # the truncated kernel folded onto a periodic axis
+    return k
+
+
+def test_uniform_salt_density_gives_eps0_everywhere():
+    # one unit charge at every cell centre (a checkerboard of signs): each
+    # vertex receives 8 x 1/8 of |q|, exactly 1, so eps = eps0 at every vertex
+    N = (6, 4, 8)
+    cells = np.stack(np.meshgrid(*[np.arange(n) for n in N], indexing="ij"), -1).reshape(-1, 3)
+    x = cells + 0.5
+    q = np.where(cells.sum(axis=1) % 2 == 0, 1, -1).astype(np.int32)
+    for sigma in (0.0, 1.5):
+        s = make(N, 1.0)
+        s.set_particles(x, q)
+        e = s.eps_from_density(55.0, -30.0, 40.0, 80.0, sigma)
+        assert np.all(e == 55.0)
+        assert np.allclose(s.field("ie"), 1 / 55.0, rtol=1e-15)
+
+
+def test_salt_smoothing_is_a_periodic_convolution():
+    # direct periodic sums along x, y, z against the convolution theorem
+    # (product of discrete Fourier transforms) with the same folded kernel;
+    # the smoothing keeps the mean
+    rng = np.random.default_rng(21)
+    N = (10, 7, 9)
+    rho = rng.uniform(0.0, 2.0, size=(N[2], N[1], N[0]))
+    for sigma in (0.7, 1.3, 2.6):       # 2.6: the kernel is wider than the 7-cell axis
+        got = O.smooth_periodic(N, sigma, rho).reshape(rho.shape)
+        F = np.fft.fftn(rho)
+        for ax, n in zip((2, 1, 0), N):
+            shape = [1, 1, 1]
+            shape[ax] = n
+            F = F * np.fft.fft(_gauss_kernel(sigma, n)).reshape(shape)
+        want = np.real(np.fft.ifftn(F))
+        assert np.max(np.abs(got - want)) < 1e-13
+        assert abs(got.mean() - rho.mean()) < 1e-14
+
+
+def test_salt_map_and_clamps_on_an_exact_profile():
+    # valences on the vertices (sub-cell step 0: all weight on one vertex) give
+    # an exact integer density along x; eps follows the linear map and clamps
+    N = (12, 3, 2)
+    L = float(N[0])
+    xs, qs = [], []
+    prof = np.round(100 * (2 + np.cos(2 * np.pi * np.arange(N[0]) / L))).astype(int)
+    for i in range(N[0]):
+        for j in range(N[1]):
+            for k in range(N[2]):
+                xs += [[i, j, k], [i, j, k]]
+                qs += [prof[i], -prof[i]]      # a neutral pair at each vertex
+    s = make(N, 1.0)
+    s.set_particles(np.array(xs, dtype=float), np.array(qs, dtype=np.int32))
+    e = s.eps_from_density(60.0, -45.0, 42.0, 78.0, 0.0)
+    rho = 2.0 * prof
+    want = np.clip(60.0 - 45.0 * (rho / rho.mean() - 1.0), 42.0, 78.0)
+    assert np.array_equal(e, np.broadcast_to(want, e.shape))
+    assert want.min() == 42.0 and want.max() == 78.0         # both clamps reached
+    assert np.any((want > 42.0) & (want < 78.0))            # and the map between them
+
+
+def test_salt_rule_reproduces_the_modulated_profile():
+    # the salt-modulated workload's charges (density 1 + 0.5 sin(2 pi x / L))
+    # through eps0 = 60, slope -40, sigma 2: the vertex eps follows
+    # 60 - 20 H sin(2 pi x / L), H = exp(-(sigma k)^2 / 2) the attenuation of
+    # the smoothing at that wave number, up to sampling noise
+    from paper_1309_7859_gb300 import inputs
+    N, n, sigma = 32, 8000, 2.0
+    rng = np.random.default_rng(5)
+    x = inputs.sine_modulated_positions(rng, n, (float(N),) * 3, 0, 0.5)
+    q = inputs.neutral_charges(rng, n)
+    s = make((N, N, N), 1.0, eps_eff_inv=np.eye(3) / 60.0)
+    s.set_particles(x, q)
+    e = s.eps_from_density(60.0, -40.0, 40.0, 80.0, sigma)
+    prof = e.mean(axis=(0, 1))                       # along x
+    sx = np.sin(2 * np.pi * np.arange(N) / N)
+    amp = 2 * np.mean(prof * sx)
+    H = np.exp(-(sigma * 2 * np.pi / N) ** 2 / 2)
+    assert abs(prof.mean() - 60.0) < 0.5
+    assert abs(amp - (-20.0 * H)) < 2.0
