@@ -379,6 +379,28 @@ memd_status memd_compute_forces(memd_ctx *ctx);
  * the previous D.  Batches holding the context rebuild their tables. */
 memd_status memd_set_eps(memd_ctx *ctx, const memd_eps_profile *eps, int32_t relax_field);
 
+/* Permittivity from the local salt density (Sec. I: the dielectric response
+ * of water falls with its salt content, which the paper names as the
+ * motivation of spatially varying eps; it gives no rule, so this one is
+ * stated here).  The |q| of every charge is deposited on its cell's vertices
+ * with the cloud-in-cell weights (the salt density rho(v), in e), smoothed by
+ * the periodic Gaussian of sigma cells (weights exp(-j^2 / (2 sigma^2)) for
+ * |j| <= ceil(3 sigma), normalised to sum 1) along x, then y, then z (sigma =
+ * 0: no smoothing), and mapped to eps(v) = eps0 + slope (rho(v) / mean(rho) -
+ * 1) clamped to [eps_lo, eps_hi] (eps0, clamped, when there are no charges).
+ * The vertex values then replace the permittivity as memd_set_eps with
+ * MEMD_EPS_VERTICES (theta 0: each link the mean of its ends) would, keeping D
+ * or relaxing it (relax_field).  eps_out (host, V, may be NULL) receives the
+ * vertex values.  Call it every few steps to let the medium follow the salt.
+ * Errors: INVALID (a rule value not finite, eps_lo <= 0, eps_hi < eps_lo,
+ * sigma outside [0, 64]), STATE before memd_init_field, OOM, CUDA, and those
+ * of memd_set_eps. */
+typedef struct memd_salt_rule {
+  double eps0, slope, eps_lo, eps_hi, sigma;
+} memd_salt_rule;
+memd_status memd_eps_from_density(memd_ctx *ctx, const memd_salt_rule *rule, int32_t relax_field,
+                                  double *eps_out);
+
 /* Checkpoint and resume.  A saved state holds the whole dynamical state: D
  * and B in the field precision, the exact ledger, positions, velocities,
  * image counters, forces, valences, masses, the step counter (which keys the

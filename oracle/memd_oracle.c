@@ -1069,15 +1069,10 @@ void orc_smooth_periodic(const int32_t N[3], double sigma, double *rho) {
   free(w);
 }
 
-int32_t orc_eps_from_density(orc_sys *s, const double rule[5], int32_t relax, double *eps_out) {
+int32_t orc_salt_vertex_eps(const orc_sys *s, const double rule[5], double *ev) {
   double eps0 = rule[0], slope = rule[1], lo = rule[2], hi = rule[3], sigma = rule[4];
   double *rho = (double *)malloc(sizeof(double) * s->V);
-  double *ev = (double *)malloc(sizeof(double) * s->V);
-  if (!rho || !ev) {
-    free(rho);
-    free(ev);
-    return ORC_ERR_OOM;
-  }
+  if (!rho) return ORC_ERR_OOM;
   /* |q| weights in fixed point (exact), then in units of e */
   for (int64_t v = 0; v < s->V; ++v) rho[v] = 0.0;
   int64_t *Qa = (int64_t *)calloc((size_t)s->V, sizeof(int64_t));
@@ -1101,13 +1096,24 @@ int32_t orc_eps_from_density(orc_sys *s, const double rule[5], int32_t relax, do
     double e = mean > 0.0 ? eps0 + slope * (rho[v] / mean - 1.0) : eps0;
     ev[v] = e < lo ? lo : (e > hi ? hi : e);
   }
+  free(rho);
+  return ORC_OK;
+}
+
+int32_t orc_eps_from_density(orc_sys *s, const double rule[5], int32_t relax, double *eps_out) {
+  double *ev = (double *)malloc(sizeof(double) * s->V);
+  if (!ev) return ORC_ERR_OOM;
+  int32_t st = orc_salt_vertex_eps(s, rule, ev);
+  if (st != ORC_OK) {
+    free(ev);
+    return st;
+  }
   if (eps_out) memcpy(eps_out, ev, sizeof(double) * s->V);
   orc_eps e;
   memset(&e, 0, sizeof(e));
   e.kind = ORC_EPS_VERTICES;
   e.values = ev;
-  int32_t st = orc_set_eps(s, &e, relax);
-  free(rho);
+  st = orc_set_eps(s, &e, relax);
   free(ev);
   return st;
 }

@@ -129,6 +129,8 @@ int32_t orc_set_eps(orc_sys *s, const orc_eps *eps, int32_t relax);
  * {eps0, slope, eps_lo, eps_hi, sigma}; eps_out (V, may be NULL) receives
  * the vertex values.  Returns orc_set_eps's status. */
 int32_t orc_eps_from_density(orc_sys *s, const double rule[5], int32_t relax, double *eps_out);
+/* the vertex values alone (V), nothing applied */
+int32_t orc_salt_vertex_eps(const orc_sys *s, const double rule[5], double *eps_out);
 /* the density and smoothing steps alone: rho (V) on input is smoothed in
  * place as above */
 void orc_smooth_periodic(const int32_t N[3], double sigma, double *rho);

@@ -95,6 +95,8 @@ def lib():
         L.orc_eps_from_density.restype = C.c_int32
         L.orc_eps_from_density.argtypes = [C.c_void_p, f64p, C.c_int32, f64p]
         L.orc_smooth_periodic.argtypes = [i32p, C.c_double, f64p]
+        L.orc_salt_vertex_eps.restype = C.c_int32
+        L.orc_salt_vertex_eps.argtypes = [C.c_void_p, f64p, f64p]
         L.orc_gauss_scan.restype = C.c_int32
         L.orc_gauss_scan.argtypes = [i32p, i64p, i64p]
         L.orc_divergence.argtypes = [i32p, i64p, i64p]
@@ -307,6 +309,17 @@ class OracleSystem:
                                             _p(out, C.c_double))
         if st != OK:
             raise OracleError(f"orc_eps_from_density failed with status {st}")
+        Nx, Ny, Nz = self.N
+        return out.reshape(Nz, Ny, Nx)
+
+    def salt_vertex_eps(self, eps0, slope, eps_lo, eps_hi, sigma):
+        """orc_salt_vertex_eps: the vertex permittivity of the salt rule alone
+        ([Nz, Ny, Nx]), nothing applied."""
+        rule = np.array([eps0, slope, eps_lo, eps_hi, sigma], dtype=np.float64)
+        out = np.zeros(self.V, dtype=np.float64)
+        st = self._lib.orc_salt_vertex_eps(self._h, _p(rule, C.c_double), _p(out, C.c_double))
+        if st != OK:
+            raise OracleError(f"orc_salt_vertex_eps failed with status {st}")
         Nx, Ny, Nz = self.N
         return out.reshape(Nz, Ny, Nx)
 

@@ -649,7 +649,10 @@ static bool eps_valid(const memd_eps_profile* e, const double box[3], double a) 
 // charge-free field of mean D = e_d, whose mean E is then column d of
 // eps_eff^-1.  A context that already had a permittivity gets it back, with
 // its potentials and tensor, when any step fails.
-static memd_status setup_eps(memd_ctx* c, const memd_eps_profile* eps) {
+// map a profile onto the links and form the effective tensor; dev_values:
+// the profile's values already on the device (else eps->values is copied)
+static memd_status setup_eps(memd_ctx* c, const memd_eps_profile* eps,
+                             const double* dev_values = nullptr) {
   const cudaStream_t st = c->stream;
   const int64_t V = c->mesh.V;
   const size_t n3 = 3 * (size_t)V;
@@ -666,7 +669,7 @@ static memd_status setup_eps(memd_ctx* c, const memd_eps_profile* eps) {
                      : eps->kind == MEMD_EPS_VERTICES ? (size_t)V
                      : eps->kind == MEMD_EPS_CUT      ? 4 * (size_t)V
                                                       : 0;
-  if (cnt) {
+  if (cnt && !dev_values) {
     vals = (double*)dalloc(c, cnt * sizeof(double));
     if (!vals) {
       s = fail(c, MEMD_ERR_OOM, "eps values");
@@ -690,7 +693,7 @@ static memd_status setup_eps(memd_ctx* c, const memd_eps_profile* eps) {
       goto out;
     }
   }
-  launch_eps_links(c->mesh, e, vals, c->ie64, &c->ds->err, st);
+  launch_eps_links(c->mesh, e, dev_values ? dev_values : vals, c->ie64, &c->ds->err, st);
   launch_cast(c->prec, c->ie, c->ie64, (int64_t)n3, st);
   mapped = true;
   if (cudaGetLastError() != cudaSuccess) {
@@ -1819,12 +1822,82 @@ memd_status memd_compute_forces(memd_ctx* c) {
 // backgrounds).  Gauss' law constrains D, not E, so the present D stays
 // valid; with relax_field it is rebuilt from the exact ledger and relaxed to
 // the electrostatic minimum of the new medium, as memd_init_field does.
+static memd_status set_eps_impl(memd_ctx* c, const memd_eps_profile* eps, int32_t relax_field,
+                                const double* dev_values);
+
 memd_status memd_set_eps(memd_ctx* c, const memd_eps_profile* eps, int32_t relax_field) {
   memd::NvtxRange nvtx_("memd_set_eps");
   if (!c) return MEMD_ERR_INVALID;
   if (!eps) return fail(c, MEMD_ERR_INVALID, "no permittivity profile");
   if (!eps_valid(eps, c->mesh.L, c->mesh.a)) return fail(c, MEMD_ERR_INVALID, "permittivity profile");
   CK(cudaSetDevice(c->device));
+  return set_eps_impl(c, eps, relax_field, nullptr);
+}
+
+memd_status memd_eps_from_density(memd_ctx* c, const memd_salt_rule* rule, int32_t relax_field,
+                                  double* eps_out) {
+  memd::NvtxRange nvtx_("memd_eps_from_density");
+  if (!c || !rule) return MEMD_ERR_INVALID;
+  const double r4[4] = {rule->eps0, rule->slope, rule->eps_lo, rule->eps_hi};
+  for (double v : r4)
+    if (!std::isfinite(v)) return fail(c, MEMD_ERR_INVALID, "salt rule not finite");
+  if (!(rule->eps_lo > 0.0) || rule->eps_hi < rule->eps_lo || !(rule->sigma >= 0.0) ||
+      rule->sigma > 64.0)
+    return fail(c, MEMD_ERR_INVALID, "salt rule out of range");
+  if (!c->initialised) return fail(c, MEMD_ERR_STATE, "memd_init_field first");
+  CK(cudaSetDevice(c->device));
+  {
+    const memd_status fe = memd_flush(c);
+    if (fe != MEMD_OK) return fe;
+  }
+  const Mesh& m = c->mesh;
+  const cudaStream_t st = c->stream;
+  // the smoothing weights, normalised to sum 1 (host, FP64)
+  const int R = rule->sigma > 0.0 ? (int)std::ceil(3.0 * rule->sigma) : 0;
+  std::vector<double> w(2 * R + 1, 1.0);
+  if (R > 0) {
+    double ws = 0.0;
+    for (int j = -R; j <= R; ++j) {
+      w[j + R] = std::exp(-(double)(j * j) / (2.0 * rule->sigma * rule->sigma));
+      ws += w[j + R];
+    }
+    for (double& x : w) x /= ws;
+  }
+  long long* Q = (long long*)dalloc(c, sizeof(long long) * m.V);
+  double* rho = (double*)dalloc(c, sizeof(double) * m.V);
+  double* tmp = (double*)dalloc(c, sizeof(double) * m.V);
+  double* ev = (double*)dalloc(c, sizeof(double) * m.V);
+  double* wd = (double*)dalloc(c, sizeof(double) * (w.size() + 1));
+  memd_status s = MEMD_OK;
+  if (!Q || !rho || !tmp || !ev || !wd) {
+    s = fail(c, MEMD_ERR_OOM, "salt density scratch");
+  } else if (cudaMemcpyAsync(wd, w.data(), sizeof(double) * w.size(), cudaMemcpyHostToDevice, st) !=
+             cudaSuccess) {
+    s = fail(c, MEMD_ERR_CUDA, "smoothing weights");
+  } else {
+    launch_cic_abs(m, c->P, Q, st);
+    launch_salt_eps(m, Q, rho, tmp, wd, R, rule->sigma, c->red, wd + w.size(), r4, ev, st);
+    if (cudaGetLastError() != cudaSuccess) s = fail(c, MEMD_ERR_CUDA, "salt density kernels");
+  }
+  if (s == MEMD_OK && eps_out &&
+      (cudaMemcpyAsync(eps_out, ev, sizeof(double) * m.V, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+       cudaStreamSynchronize(st) != cudaSuccess))
+    s = fail(c, MEMD_ERR_CUDA, "eps download");
+  if (s == MEMD_OK) {
+    memd_eps_profile e{};
+    e.kind = MEMD_EPS_VERTICES;
+    s = set_eps_impl(c, &e, relax_field, ev);
+  }
+  dfree(c, Q);
+  dfree(c, rho);
+  dfree(c, tmp);
+  dfree(c, ev);
+  dfree(c, wd);
+  return s;
+}
+
+static memd_status set_eps_impl(memd_ctx* c, const memd_eps_profile* eps, int32_t relax_field,
+                                const double* dev_values) {
   const cudaStream_t st = c->stream;
   if (c->initialised) {
     const memd_status fe = memd_flush(c);
@@ -1833,7 +1906,7 @@ memd_status memd_set_eps(memd_ctx* c, const memd_eps_profile* eps, int32_t relax
   drop_graphs(c);
   harvest_timing(c);
   CK(cudaStreamSynchronize(st));
-  memd_status s = setup_eps(c, eps);
+  memd_status s = setup_eps(c, eps, dev_values);
   if (s != MEMD_OK) return s;
   c->gen += 1;  // batches holding this context rebuild their tables
   if (!c->initialised) return MEMD_OK;

@@ -154,6 +154,13 @@ void launch_gauss_scan(const Mesh& m, const long long* Q, long long* Lg, long lo
 void launch_init_D(const Mesh& m, double* D64, const long long* Lg, DevState* ds,
                    double scale, double Vbox, cudaStream_t st);
 void launch_ledger_sums(const Mesh& m, const long long* Lg, DevState* ds, cudaStream_t st);
+// permittivity from the salt density: rho = |q| density (from its
+// fixed-point deposit Q), smoothed along x, y, z by the weights w[0..2R]
+// (sigma > 0), its sum into sum[0] (partials in part), then eps per vertex
+// from rule {eps0, slope, lo, hi}; tmp is V doubles of scratch
+void launch_salt_eps(const Mesh& m, const long long* Q, double* rho, double* tmp,
+                     const double* w, int R, double sigma, double* part, double* sum,
+                     const double rule[4], double* eps, cudaStream_t st);
 // zero the transfer words of a transfer buffer of count links (stride kLT)
 void launch_clear_transfers(long long* T, int64_t count, cudaStream_t st);
 
@@ -241,6 +248,8 @@ void launch_io_unpack(const Mesh& m, Particles p, const void* io, unsigned int* 
                       cudaStream_t st);
 void launch_io_pack(Particles p, void* io, const unsigned int* err, cudaStream_t st);
 void launch_cic(const Mesh& m, Particles p, long long* Q, long long bg, cudaStream_t st);
+// cloud-in-cell deposit of |q| (int64, e 2^-48) at the vertices
+void launch_cic_abs(const Mesh& m, Particles p, long long* Q, cudaStream_t st);
 void launch_dipole(const Mesh& m, Particles p, DevState* ds, cudaStream_t st);
 void launch_kick_drift_deposit(const Mesh& m, const StepParams& sp, Particles p,
                                long long* Tb, DevState* ds, cudaStream_t st);

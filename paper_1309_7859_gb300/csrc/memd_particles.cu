@@ -362,6 +362,25 @@ __global__ void k_cic(Mesh m, Particles P, unsigned long long* __restrict__ Q) {
       }
 }
 
+// cloud-in-cell density of |q| (the salt content) at the vertices, int64 in
+// units of e 2^-48
+__global__ void k_cic_abs(Mesh m, Particles P, unsigned long long* __restrict__ Q) {
+  const int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (p >= P.n) return;
+  int c[3], f[3];
+  for (int d = 0; d < 3; ++d) quantize(m, d, P.x[3 * p + d], c[d], f[d]);
+  const long long aq = P.q[p] < 0 ? -(long long)P.q[p] : (long long)P.q[p];
+  for (int az = 0; az < 2; ++az)
+    for (int ay = 0; ay < 2; ++ay)
+      for (int ax = 0; ax < 2; ++ax) {
+        const long long w = wgt(f[0], ax) * wgt(f[1], ay) * wgt(f[2], az);
+        if (w == 0) continue;
+        const int64_t v = vindex(m, wrap1(c[0] + ax, m.n[0]), wrap1(c[1] + ay, m.n[1]),
+                                 wrap1(c[2] + az, m.n[2]));
+        atomicAdd(&Q[v], (unsigned long long)(aq * w));
+      }
+}
+
 __global__ void k_sub_background(int64_t V, long long* __restrict__ Q, long long bg) {
   const int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (v < V) Q[v] -= bg;
@@ -1684,6 +1703,11 @@ void launch_cic(const Mesh& m, Particles p, long long* Q, long long bg, cudaStre
   cudaMemsetAsync(Q, 0, sizeof(long long) * m.V, st);
   if (p.n > 0) k_cic<<<blocks_for(p.n), kThreads, 0, st>>>(m, p, (unsigned long long*)Q);
   if (bg != 0) k_sub_background<<<blocks_for(m.V, 256), 256, 0, st>>>(m.V, Q, bg);
+}
+
+void launch_cic_abs(const Mesh& m, Particles p, long long* Q, cudaStream_t st) {
+  cudaMemsetAsync(Q, 0, sizeof(long long) * m.V, st);
+  if (p.n > 0) k_cic_abs<<<blocks_for(p.n), kThreads, 0, st>>>(m, p, (unsigned long long*)Q);
 }
 
 void launch_dipole(const Mesh& m, Particles p, DevState* ds, cudaStream_t st) {

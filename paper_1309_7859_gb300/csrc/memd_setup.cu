@@ -489,6 +489,64 @@ void launch_gauss_scan(const Mesh& m, const long long* Q, long long* Lg, long lo
   k_xscan<<<blocks_for(nl, 128), 128, 0, st>>>(m, r, Lg, err);
 }
 
+// ------------------------------------------- permittivity from salt density
+// |q| density in e at the vertices from its fixed-point deposit
+__global__ void k_density_from_ll(int64_t V, const long long* __restrict__ Q,
+                                  double* __restrict__ rho) {
+  const int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (v < V) rho[v] = __dmul_rn((double)Q[v], 3.552713678800501e-15);  // 2^-48
+}
+
+// one axis of the periodic Gaussian smoothing: out(v) = sum_{j=-R..R} w_j
+// in(v + j e_axis), summed in order of j, every product and sum rounded
+// on its own (the same roundings as a plain sequential loop)
+__global__ void k_smooth_axis(Mesh m, const double* __restrict__ in, double* __restrict__ out,
+                              int axis, const double* __restrict__ w, int R) {
+  const int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (v >= m.V) return;
+  int c[3];
+  coords(m, v, c[0], c[1], c[2]);
+  const int n = m.n[axis];
+  double acc = 0.0;
+  for (int j = -R; j <= R; ++j) {
+    int e[3] = {c[0], c[1], c[2]};
+    e[axis] = ((e[axis] + j) % n + n) % n;
+    acc = __dadd_rn(acc, __dmul_rn(w[j + R], in[vindex(m, e[0], e[1], e[2])]));
+  }
+  out[v] = acc;
+}
+
+// eps(v) = eps0 + slope (rho(v) / mean - 1) clamped to [lo, hi]; mean[0]
+// holds the sum of rho over the V vertices
+__global__ void k_salt_map(int64_t V, const double* __restrict__ rho, const double* __restrict__ sum,
+                           double eps0, double slope, double lo, double hi,
+                           double* __restrict__ eps) {
+  const int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (v >= V) return;
+  const double mean = __ddiv_rn(sum[0], (double)V);
+  double e = eps0;
+  if (mean > 0.0)
+    e = __dadd_rn(eps0, __dmul_rn(slope, __dsub_rn(__ddiv_rn(rho[v], mean), 1.0)));
+  eps[v] = e < lo ? lo : (e > hi ? hi : e);
+}
+
+void launch_salt_eps(const Mesh& m, const long long* Q, double* rho, double* tmp,
+                     const double* w, int R, double sigma, double* part, double* sum,
+                     const double rule[4], double* eps, cudaStream_t st) {
+  const unsigned nb = (unsigned)((m.V + 255) / 256);
+  k_density_from_ll<<<nb, 256, 0, st>>>(m.V, Q, rho);
+  if (sigma > 0.0) {
+    // x, then y, then z (ping-pong through tmp; the result back in rho)
+    k_smooth_axis<<<nb, 256, 0, st>>>(m, rho, tmp, 0, w, R);
+    k_smooth_axis<<<nb, 256, 0, st>>>(m, tmp, rho, 1, w, R);
+    k_smooth_axis<<<nb, 256, 0, st>>>(m, rho, tmp, 2, w, R);
+    cudaMemcpyAsync(rho, tmp, sizeof(double) * m.V, cudaMemcpyDeviceToDevice, st);
+  }
+  launch_dot(rho, nullptr, m.V, part, st);
+  launch_finish(part, 0, sum, st);
+  k_salt_map<<<nb, 256, 0, st>>>(m.V, rho, sum, rule[0], rule[1], rule[2], rule[3], eps);
+}
+
 void launch_clear_transfers(long long* T, int64_t count, cudaStream_t st) {
   if (count > 0) k_clear_transfers<<<2 * 152, 256, 0, st>>>(T, count);
 }

@@ -30,6 +30,7 @@ EXPORTS = ("memd_default_options", "memd_status_string", "memd_last_error", "mem
            "memd_get_fields", "memd_set_fields", "memd_compute_forces", "memd_set_eps",
            "memd_step_host", "memd_io_buffers", "memd_step_io", "memd_state_bytes",
            "memd_save_state", "memd_load_state", "memd_dipole_check", "memd_inject",
+           "memd_eps_from_density",
            "memd_get_setup",
            "memd_get_kernel_stats", "memd_reset_kernel_stats", "memd_synchronize",
            "memd_batch_create", "memd_batch_create_kernel", "memd_batch_step",
@@ -179,6 +180,7 @@ def lib(build_if_missing=True):
     L.memd_set_eps.argtypes = [vp, C.POINTER(EpsProfile), C.c_int32]
     L.memd_get_setup.argtypes = [vp, f64p, f64p, f64p]
     L.memd_dipole_check.argtypes = [vp, C.c_double, f64p]
+    L.memd_eps_from_density.argtypes = [vp, C.POINTER(C.c_double * 5), C.c_int32, f64p]
     L.memd_inject.argtypes = [vp, C.c_int32, C.c_double]
     L.memd_get_kernel_stats.argtypes = [vp, C.POINTER(KernelStats)]
     L.memd_reset_kernel_stats.argtypes = [vp]
@@ -493,6 +495,16 @@ class Memd:
 
     def compute_forces(self):
         self._check(self._L.memd_compute_forces(self._h), "memd_compute_forces")
+
+    def eps_from_density(self, eps0, slope, eps_lo, eps_hi, sigma, relax=False):
+        """memd_eps_from_density: the permittivity from the local |q| density
+        (vertex values returned as [Nz, Ny, Nx])."""
+        rule = (C.c_double * 5)(eps0, slope, eps_lo, eps_hi, sigma)
+        out = np.zeros(self.V, dtype=np.float64)
+        self._check(self._L.memd_eps_from_density(self._h, C.byref(rule), 1 if relax else 0,
+                                                  _ptr(out, C.c_double)), "memd_eps_from_density")
+        Nx, Ny, Nz = self.mesh
+        return out.reshape(Nz, Ny, Nx)
 
     def dipole_check(self, limit):
         """memd_dipole_check: (status, ratio) of the dipole correction's field to
