@@ -76,6 +76,40 @@ __host__ __device__ inline int wrapi(int i, int n) {
   return i < 0 ? i + n : i;
 }
 
+// ------------------------------------------------------------ L2 priorities
+// Cache-priority policies (PTX createpolicy, sm_80 and later).  The transfer
+// and ledger words, scattered by the particle kernels' atomics and touched
+// again by the next particle kernel of the step, are kept in L2 (evict_last);
+// the field planes that the stencil streams through once a step leave first
+// (evict_first).  These are hints: no value and no order of operations
+// changes.  The asm is not volatile, so one policy per thread is hoisted.
+__device__ __forceinline__ unsigned long long l2_policy_last() {
+  unsigned long long p;
+  asm("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(p));
+  return p;
+}
+__device__ __forceinline__ unsigned long long l2_policy_first() {
+  unsigned long long p;
+  asm("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(p));
+  return p;
+}
+// atomicAdd without a result (relaxed, device scope) under an L2 policy
+__device__ __forceinline__ void red_add_hint(unsigned long long* a, unsigned long long v,
+                                             unsigned long long pol) {
+  asm volatile("red.global.add.L2::cache_hint.u64 [%0], %1, %2;" ::"l"(a), "l"(v), "l"(pol)
+               : "memory");
+}
+// atomicExch (relaxed, device scope) under an L2 policy
+__device__ __forceinline__ unsigned long long exch_hint(unsigned long long* a, unsigned long long v,
+                                                        unsigned long long pol) {
+  unsigned long long r;
+  asm volatile("atom.global.exch.L2::cache_hint.b64 %0, [%1], %2, %3;"
+               : "=l"(r)
+               : "l"(a), "l"(v), "l"(pol)
+               : "memory");
+  return r;
+}
+
 // ------------------------------------------------------------ field kernels
 // (memd_field.cu)
 void launch_curl_B(const Mesh& m, int prec, void* B, const void* D, const void* ie,

@@ -226,19 +226,19 @@ __device__ inline void deposit_axis(const Mesh& m, int d, int q, int c0, int f0,
       const int64_t l0 = u0 + perp;
       if (dc == 0) {
         const long long t = -(long long)q * (long long)(f1 - f0) * wp;
-        if (t) atomicAdd(&Tb[kLT * l0], (unsigned long long)t);
+        if (t) red_add_hint(&Tb[kLT * l0], (unsigned long long)t, l2_policy_last());
       } else if (dc == 1) {
         const int64_t l1 = u1 + perp;
         const long long t0 = -(long long)q * (long long)(kS - f0) * wp;
         const long long t1 = -(long long)q * (long long)f1 * wp;
-        if (t0) atomicAdd(&Tb[kLT * l0], (unsigned long long)t0);
-        if (t1) atomicAdd(&Tb[kLT * l1], (unsigned long long)t1);
+        if (t0) red_add_hint(&Tb[kLT * l0], (unsigned long long)t0, l2_policy_last());
+        if (t1) red_add_hint(&Tb[kLT * l1], (unsigned long long)t1, l2_policy_last());
       } else {
         const int64_t l1 = u1 + perp;
         const long long t0 = (long long)q * (long long)f0 * wp;
         const long long t1 = (long long)q * (long long)(kS - f1) * wp;
-        if (t0) atomicAdd(&Tb[kLT * l0], (unsigned long long)t0);
-        if (t1) atomicAdd(&Tb[kLT * l1], (unsigned long long)t1);
+        if (t0) red_add_hint(&Tb[kLT * l0], (unsigned long long)t0, l2_policy_last());
+        if (t1) red_add_hint(&Tb[kLT * l1], (unsigned long long)t1, l2_policy_last());
       }
     }
 }
@@ -591,16 +591,18 @@ __device__ __forceinline__ void apply_body(const Mesh& m, Particles P,
     l[2 * d + 1] = link_index(m, d, at[0], at[1], at[2]);
     has[2 * d + 1] = c1[d] != c0[d];
   }
+  // the transfer and ledger words stay in L2 for the gather's ledger reads
+  const unsigned long long pol = l2_policy_last();
   long long t[6];
 #pragma unroll
-  for (int s = 0; s < 6; ++s) t[s] = has[s] ? (long long)atomicExch(&Tb[kLT * l[s]], 0ull) : 0ll;
+  for (int s = 0; s < 6; ++s) t[s] = has[s] ? (long long)exch_hint(&Tb[kLT * l[s]], 0ull, pol) : 0ll;
   // only the lane that took a link's transfer adds it, so each reduction
   // below is the one addition to its word in this kernel: exact for the
   // ledger, D + x rounded once for the field
 #pragma unroll
   for (int s = 0; s < 6; ++s)
     if (t[s] != 0) {
-      atomicAdd((unsigned long long*)&Lg[kLT * l[s]], (unsigned long long)t[s]);
+      red_add_hint((unsigned long long*)&Lg[kLT * l[s]], (unsigned long long)t[s], pol);
       atomicAdd(&D[l[s]], (T)((double)t[s] * scale));
     }
 }

@@ -49,10 +49,38 @@ __device__ __forceinline__ float4 repack(const Pack<float>& p) {
 __device__ __forceinline__ double2 repack(const Pack<double>& p) { return make_double2(p.v[0], p.v[1]); }
 
 // per-thread asynchronous 16-byte copy global -> shared (L2 only), and its
-// group bookkeeping
+// group bookkeeping.  The stencil reads and writes each field word once a
+// step: its copies, loads and stores carry the evict_first policy, so that
+// they do not push the particle kernels' transfer words out of L2.
 __device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
   const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
-  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(sa), "l"(gmem) : "memory");
+  asm volatile("cp.async.cg.shared.global.L2::cache_hint [%0], [%1], 16, %2;" ::"r"(sa),
+               "l"(gmem), "l"(l2_policy_first())
+               : "memory");
+}
+__device__ __forceinline__ float4 ldcg_first(const float4* a) {
+  float4 v;
+  asm volatile("ld.global.cg.L2::cache_hint.v4.f32 {%0,%1,%2,%3}, [%4], %5;"
+               : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w)
+               : "l"(a), "l"(l2_policy_first()));
+  return v;
+}
+__device__ __forceinline__ double2 ldcg_first(const double2* a) {
+  double2 v;
+  asm volatile("ld.global.cg.L2::cache_hint.v2.f64 {%0,%1}, [%2], %3;"
+               : "=d"(v.x), "=d"(v.y)
+               : "l"(a), "l"(l2_policy_first()));
+  return v;
+}
+__device__ __forceinline__ void st_first(float4* a, const float4& v) {
+  asm volatile("st.global.L2::cache_hint.v4.f32 [%0], {%1,%2,%3,%4}, %5;" ::"l"(a), "f"(v.x),
+               "f"(v.y), "f"(v.z), "f"(v.w), "l"(l2_policy_first())
+               : "memory");
+}
+__device__ __forceinline__ void st_first(double2* a, const double2& v) {
+  asm volatile("st.global.L2::cache_hint.v2.f64 [%0], {%1,%2}, %3;" ::"l"(a), "d"(v.x), "d"(v.y),
+               "l"(l2_policy_first())
+               : "memory");
 }
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
 template <int N>
@@ -99,10 +127,10 @@ __device__ __forceinline__ void rows_segment(const Mesh& m, const T* __restrict_
     return unpack(__ldg(reinterpret_cast<const VT*>(a + (int64_t)c * V + (int64_t)k * P + off)));
   };
   auto ldcg = [&](const T* a, int k, int c) {
-    return unpack(__ldcg(reinterpret_cast<const VT*>(a + (int64_t)c * V + (int64_t)k * P + off)));
+    return unpack(ldcg_first(reinterpret_cast<const VT*>(a + (int64_t)c * V + (int64_t)k * P + off)));
   };
   auto st = [&](T* a, int k, int c, const Pack<T>& v) {
-    *reinterpret_cast<VT*>(a + (int64_t)c * V + (int64_t)k * P + off) = repack(v);
+    st_first(reinterpret_cast<VT*>(a + (int64_t)c * V + (int64_t)k * P + off), repack(v));
   };
   auto sput = [&](T* s, int c, const Pack<T>& v) {
     *reinterpret_cast<VT*>(s + c * plane + s0) = repack(v);
