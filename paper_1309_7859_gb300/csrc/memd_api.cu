@@ -1059,8 +1059,9 @@ memd_status memd_init_field(memd_ctx* c, int64_t n, const double* pos, const int
 
 // One step on buffer parity `par` (state in buffer par, result in 1 - par).
 // The charge transfer of the drift runs on a side stream beside the fused
-// field update (neither reads what the other writes); the transfers are
-// applied to the new D, then the gather closes the step.
+// field update (neither reads what the other writes; with timing on, after
+// it); the transfers are applied to the new D, then the gather closes the
+// step.
 // a timing event inside a captured graph is an external event node; outside
 // capture it is recorded as usual
 static cudaError_t record_timing_event(cudaEvent_t ev, cudaStream_t st) {
@@ -1073,20 +1074,20 @@ static cudaError_t record_timing_event(cudaEvent_t ev, cudaStream_t st) {
 static memd_status record_step(memd_ctx* c, const StepParams& sp, int par, bool timed) {
   const Mesh& m = c->mesh;
   const cudaStream_t st = c->stream;
-  const bool serial = 15.0 * (double)esz(c) * (double)m.V >= kSerialFieldBytes;
-  if (!serial) {
+  if (timed) {
+    // instrumented: the field update alone between its event pair
+    CK(record_timing_event(c->ev0, st));
+    launch_field(c, par, sp.coefB, sp.coefD, c->fcfg);
+    CK(record_timing_event(c->ev1, st));
+    launch_kick_drift_deposit(m, sp, c->P, c->Tb, c->ds, st);
+  } else {
     CK(cudaEventRecord(c->fork, st));
     CK(cudaStreamWaitEvent(c->side, c->fork, 0));
     launch_kick_drift_deposit(m, sp, c->P, c->Tb, c->ds, c->side);
     CK(cudaEventRecord(c->join, c->side));
-  }
-  if (timed) CK(record_timing_event(c->ev0, st));
-  launch_field(c, par, sp.coefB, sp.coefD, c->fcfg);
-  if (timed) CK(record_timing_event(c->ev1, st));
-  if (serial)
-    launch_kick_drift_deposit(m, sp, c->P, c->Tb, c->ds, st);
-  else
+    launch_field(c, par, sp.coefB, sp.coefD, c->fcfg);
     CK(cudaStreamWaitEvent(st, c->join, 0));
+  }
   if (apply_dense(c->apply_mode))
     launch_apply_dense(c->prec, 3 * m.V, c->Tb, c->Lg, c->Dbuf[par ^ 1], sp.scale, st);
   else

@@ -56,6 +56,7 @@ struct memd_batch {
   int engine = MEMD_STEP_AUTO;
   bool single = false;
   bool single_graph_ok = true;  // its launch can be captured in a graph
+  bool overlap = true;  // graph engine: the deposition beside the field pass
   int bs_grid = 0;
   int bs_field_ctas = -1;   // -1: half the grid
   int bs_item_planes = 0;   // 0: chosen from the work (about one item per CTA)
@@ -101,10 +102,10 @@ memd_status bfail(memd_batch* b, memd_status s, const std::string& why) {
   } while (0)
 
 void drop(memd_batch* b) {
-  for (int t = 0; t < 2; ++t)
-    if (b->graph[t]) {
-      cudaGraphExecDestroy(b->graph[t]);
-      b->graph[t] = nullptr;
+  for (cudaGraphExec_t& g : b->graph)
+    if (g) {
+      cudaGraphExecDestroy(g);
+      g = nullptr;
     }
 }
 
@@ -472,6 +473,17 @@ memd_status autotune_batch(memd_batch* b) {
   return build_tables(b);
 }
 
+// The force gather that closes the step of buffer parity par (it reads the
+// D that step wrote), for every replica.
+cudaError_t gather_batch(memd_batch* b, int par, int thermo, double gamma, double kT,
+                         cudaStream_t s) {
+  if (b->wide)
+    launch_gather_batch_wide(b->prec, b->d_desc, b->d_part_rep_w, b->n_part_w, par, thermo, s);
+  else
+    launch_gather_batch(b->prec, b->d_desc, b->d_part_rep, b->n_part, par, thermo, gamma, kT, s);
+  return cudaGetLastError();
+}
+
 memd_status record(memd_batch* b, int par, int thermo, double gamma, double kT, bool timed) {
   const cudaStream_t st = b->stream;
   if (b->single) {
@@ -500,47 +512,58 @@ memd_status record(memd_batch* b, int par, int thermo, double gamma, double kT, 
     }
     return MEMD_OK;
   }
-  const bool serial = b->field_bytes >= kSerialFieldBytes;
   auto deposit = [&](cudaStream_t s) {
     if (b->wide)
       launch_deposit_batch_wide(b->d_desc, b->d_part_rep_w, b->n_part_w, s);
     else
       launch_deposit_batch(b->d_desc, b->d_part_rep, b->n_part, thermo, gamma, kT, s);
   };
-  // with timing on, an event pair around each launch (on the launch's stream)
-  auto mark = [&](cudaEvent_t e, cudaStream_t s) {
-    return timed ? cudaEventRecordWithFlags(e, s, cudaEventRecordExternal) : cudaSuccess;
+  auto apply = [&](cudaStream_t s) {
+    if (b->apply_dense)
+      launch_apply_dense_batch(b->prec, b->d_desc, b->d_apply_chunk, b->n_apply_chunk, par, s);
+    else
+      launch_apply_batch(b->prec, b->d_desc, b->d_part_rep, b->n_part, par, s);
   };
-  if (!serial) {
+  if (timed) {
+    // instrumented: the four launches in turn on one stream, each between
+    // its event pair, so that no launch's time holds another's
+    BCK(cudaEventRecordWithFlags(b->ev0, st, cudaEventRecordExternal));
+    BCK(launch_field(b, par, st));
+    BCK(cudaEventRecordWithFlags(b->ev1, st, cudaEventRecordExternal));
+    BCK(cudaEventRecordWithFlags(b->evp[0], st, cudaEventRecordExternal));
+    deposit(st);
+    BCK(cudaEventRecordWithFlags(b->evp[1], st, cudaEventRecordExternal));
+    BCK(cudaEventRecordWithFlags(b->evp[2], st, cudaEventRecordExternal));
+    apply(st);
+    BCK(cudaEventRecordWithFlags(b->evp[3], st, cudaEventRecordExternal));
+    BCK(cudaEventRecordWithFlags(b->evp[4], st, cudaEventRecordExternal));
+    BCK(gather_batch(b, par, thermo, gamma, kT, st));
+    BCK(cudaEventRecordWithFlags(b->evp[5], st, cudaEventRecordExternal));
+    BCK(cudaGetLastError());
+    return MEMD_OK;
+  }
+  // The deposition runs beside the field pass (neither reads what the other
+  // writes): it is latency bound, the pass bandwidth bound, and the pass's
+  // evict_first accesses leave the deposition's evict_last transfer words in
+  // L2 for the application (64 replicas: 113.9 -> 109.8 us a step against
+  // the two in turn).  Moving the gather that closes a step beside the next
+  // field pass, ahead of the deposition, was slower (116.9 us): the two
+  // particle kernels in turn then outlast the pass.  Without overlap (the
+  // request server, whose admission work runs on other streams meanwhile)
+  // the two run in turn.
+  if (b->overlap) {
     BCK(cudaEventRecord(b->fork, st));
     BCK(cudaStreamWaitEvent(b->side, b->fork, 0));
-    BCK(mark(b->evp[0], b->side));
     deposit(b->side);
-    BCK(mark(b->evp[1], b->side));
     BCK(cudaEventRecord(b->join, b->side));
-  }
-  BCK(mark(b->ev0, st));
-  BCK(launch_field(b, par, st));
-  BCK(mark(b->ev1, st));
-  if (serial) {
-    BCK(mark(b->evp[0], st));
-    deposit(st);
-    BCK(mark(b->evp[1], st));
-  } else {
+    BCK(launch_field(b, par, st));
     BCK(cudaStreamWaitEvent(st, b->join, 0));
+  } else {
+    BCK(launch_field(b, par, st));
+    deposit(st);
   }
-  BCK(mark(b->evp[2], st));
-  if (b->apply_dense)
-    launch_apply_dense_batch(b->prec, b->d_desc, b->d_apply_chunk, b->n_apply_chunk, par, st);
-  else
-    launch_apply_batch(b->prec, b->d_desc, b->d_part_rep, b->n_part, par, st);
-  BCK(mark(b->evp[3], st));
-  BCK(mark(b->evp[4], st));
-  if (b->wide)
-    launch_gather_batch_wide(b->prec, b->d_desc, b->d_part_rep_w, b->n_part_w, par, thermo, st);
-  else
-    launch_gather_batch(b->prec, b->d_desc, b->d_part_rep, b->n_part, par, thermo, gamma, kT, st);
-  BCK(mark(b->evp[5], st));
+  apply(st);
+  BCK(gather_batch(b, par, thermo, gamma, kT, st));
   BCK(cudaGetLastError());
   return MEMD_OK;
 }
@@ -609,6 +632,12 @@ memd_status batch_refresh(memd_batch* b) {
 // Members must share the batch's device, precision and stream.  Members that
 // were not in the batch before get the per-particle constants of the
 // batch's thermostat.
+void memd_batch_set_overlap(memd_batch* b, bool overlap) {
+  if (b->overlap == overlap) return;
+  drop(b);  // the step graphs hold the launch order
+  b->overlap = overlap;
+}
+
 memd_status memd_batch_update_members(memd_batch* b, int32_t count, memd_ctx* const* members) {
   if (!b || count < 1 || !members) return MEMD_ERR_INVALID;
   for (int r = 0; r < count; ++r) {
@@ -752,7 +781,8 @@ memd_status memd_batch_step(memd_batch* b, int64_t nsteps, const memd_thermostat
       b->bpar ^= 1;
       continue;
     }
-    if (!b->graph[par]) {
+    cudaGraphExec_t& gx = b->graph[par];
+    if (!gx) {
       cudaGraph_t g = nullptr;
       BCK(cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal));
       memd_status r = record(b, par, thermo, gamma, kT, timed);
@@ -761,10 +791,10 @@ memd_status memd_batch_step(memd_batch* b, int64_t nsteps, const memd_thermostat
         if (g) cudaGraphDestroy(g);
         return r;
       }
-      cudaError_t ie = e == cudaSuccess ? cudaGraphInstantiate(&b->graph[par], g, 0) : e;
+      cudaError_t ie = e == cudaSuccess ? cudaGraphInstantiate(&gx, g, 0) : e;
       if (g) cudaGraphDestroy(g);
       if (ie != cudaSuccess) {
-        b->graph[par] = nullptr;
+        gx = nullptr;
         if (!b->single) return bfail(b, MEMD_ERR_CUDA, "graph capture");
         cudaGetLastError();
         b->single_graph_ok = false;
@@ -772,7 +802,7 @@ memd_status memd_batch_step(memd_batch* b, int64_t nsteps, const memd_thermostat
         continue;
       }
     }
-    BCK(cudaGraphLaunch(b->graph[par], b->stream));
+    BCK(cudaGraphLaunch(gx, b->stream));
     b->timing_pending = timed;
     b->bpar ^= 1;
   }

@@ -124,3 +124,6 @@ memd_status memd_batch_create_opt(int32_t count, memd_ctx* const* members, memd_
 // new members for a batch, its tables rebuilt behind the queued work (no
 // synchronisation); members share the batch's device, precision and stream
 memd_status memd_batch_update_members(memd_batch* b, int32_t count, memd_ctx* const* members);
+// whether the deposition runs beside the field pass (the default) or after
+// it on the batch's stream; the step graphs are rebuilt at the next step
+void memd_batch_set_overlap(memd_batch* b, bool overlap);

@@ -329,13 +329,6 @@ struct RepDesc {
   int b_nf, b_np, b_nc;               // single-launch step: field items, particle items,
                                       // particle chunks (kBatchStepThreads quad lanes)
 };
-// A field pass that moves at least this many bytes is HBM bound: the step
-// then runs the deposition after it on the same stream instead of beside it.
-// Beside it, the deposition's scattered atomics take HBM and SM slots from
-// the stencil and the pair ends later than the two in turn; after it, the
-// transfer words the deposition touches are still in L2 when the transfers
-// are applied and the forces gathered.
-constexpr double kSerialFieldBytes = 64.0 * 1024 * 1024;
 constexpr int kBatchTY = 8;            // default tile height of the batched field kernel
 constexpr int kBatchPF32 = 2;          // its prefetch depth in planes, FP32 fields
 constexpr int kBatchPF64 = 1;          // and FP64 fields (register bound)

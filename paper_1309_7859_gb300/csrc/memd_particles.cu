@@ -467,7 +467,6 @@ __device__ __forceinline__ void deposit_wide(const Mesh& m, const StepParams& sp
     xn[d] = x[d];
     if (fabs(step) <= 2.0 * m.a) {
       xn[d] = __dadd_rn(x[d], step);
-      fold(m.L[d], xn[d], kn[d]);
     } else {
       ok = false;
     }
@@ -476,7 +475,24 @@ __device__ __forceinline__ void deposit_wide(const Mesh& m, const StepParams& sp
 #pragma unroll
   for (int d = 0; d < 3; ++d) {
     quantize(m, d, x[d], c0[d], f0[d]);
-    quantize(m, d, xn[d], c1[d], f1[d]);
+    // With a power-of-two spacing the product x S / a is exact, so xn lies in
+    // [0, L) exactly when 0 <= floor(xn S / a) < n S: the quantised value then
+    // is the cell and step of the folded position, and the fold's FP64
+    // comparisons are skipped (GB300's FP64 pipe is narrow).  Otherwise fold
+    // and quantise as the other kernels do; the results are the same.
+    bool inside = false;
+    if (m.a_pow2) {
+      const long long W = __double2ll_rd(__dmul_rn(xn[d], m.inv_aS));
+      if (W >= 0 && W < (long long)m.n[d] * kS) {
+        inside = true;
+        c1[d] = (int)(W >> kWBits);
+        f1[d] = (int)(W & (kS - 1));
+      }
+    }
+    if (!inside) {
+      fold(m.L[d], xn[d], kn[d]);
+      quantize(m, d, xn[d], c1[d], f1[d]);
+    }
     dc[d] = c1[d] + (kn[d] - ko[d]) * m.n[d] - c0[d];
     if (dc[d] < -1 || dc[d] > 1) ok = false;
   }
@@ -1127,7 +1143,11 @@ __device__ inline int64_t batch_local_w(const RepDesc& r) {
   return (int64_t)(blockIdx.x - r.pw_first) * blockDim.x + threadIdx.x;
 }
 
-__global__ void __launch_bounds__(kWideThreads)
+// Seven CTAs an SM (at most 72 registers, a few words spilled to L1) hold
+// a 64-replica batch's ~1000 CTAs in one wave; at the 88 registers the
+// kernel takes unbounded, five fit and a second wave trails (42.4 -> 38.5 us
+// a launch on 124k charges).
+__global__ void __launch_bounds__(kWideThreads, 7)
     k_deposit_batch_wide(const RepDesc* __restrict__ desc, const int* __restrict__ cta_rep) {
   const RepDesc& r = desc[cta_rep[blockIdx.x]];
   long long U[3];
