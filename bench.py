@@ -402,10 +402,15 @@ def batch_line(args, world, rank, local):
     systems = batch_systems(args.workload, rank)
     t0 = time.perf_counter()
     members = []
+    # --batch-rows-nt N: members fix the row kernel at N threads a CTA, which
+    # the batch then takes untimed (for captures whose own timing would skew
+    # the choice)
+    fixed = dict(field_kernel="rows", field_shape=(0, 0, 0, args.batch_rows_nt)) \
+        if args.batch_rows_nt else dict(field_kernel="ldg")
     for s in systems:
         g = Memd(s.mesh, s.box, s.eps, c_light=s.c_light, dt=s.dt, precision=s.precision,
-                 seed=s.seed, stream=stream, time_kernels=False, field_kernel="ldg",
-                 apply_mode=args.apply)
+                 seed=s.seed, stream=stream, time_kernels=False, apply_mode=args.apply,
+                 **fixed)
         g.init_field(s.x, s.q, s.m, s.v)
         members.append(g)
     setup_s = time.perf_counter() - t0
@@ -1027,6 +1032,8 @@ def main():
                     help="edge of the extra larger-than-L2 system (0: skip)")
     ap.add_argument("--batch-kernel", default="auto", choices=["auto", "site", "rows"],
                     help="field kernel of the batched replicas (auto: timed choice)")
+    ap.add_argument("--batch-rows-nt", type=int, default=0, choices=[0, 256, 512],
+                    help="fix the batch's row kernel at this many threads a CTA (0: timed)")
     ap.add_argument("--salt", type=int, default=1,
                     help="1: also step the 64^3 salt system (32768 charges, eps from salt density)")
     ap.add_argument("--validation", type=int, default=1,

@@ -152,7 +152,8 @@ typedef struct memd_options {
                              loaded ahead 1 or 2), threads a CTA 256 or 512 of the ROWS
                              kernel; a value the chosen field_kernel does not use must be
                              0, and field_kernel must not be AUTO.  Out of range:
-                             INVALID at create. */
+                             INVALID at create.  A batch whose members all fix the same
+                             ROWS width steps its field pass with that width, untuned. */
 } memd_options;
 
 enum { MEMD_FIELD_AUTO = 0, MEMD_FIELD_LDG = 1, MEMD_FIELD_TMA = 2, MEMD_FIELD_SITE = 3,
@@ -460,8 +461,10 @@ typedef struct memd_batch memd_batch;
  * state unchanged: site tiles (width 16 or 32, height 4, 8 or 16 rows, 1 or
  * 2 planes loaded ahead, 4 to 32 planes per CTA) and the row kernel (256 or
  * 512 threads a CTA; it needs every member's x extent to be a multiple of 4
- * sites for FP32 fields, 2 for FP64).  Errors: INVALID (mixed device,
- * precision or stream, or a member not initialised), OOM, CUDA. */
+ * sites for FP32 fields, 2 for FP64).  Members created with field_kernel
+ * MEMD_FIELD_ROWS and one width in field_shape[3] fix the row kernel and its
+ * width instead (no timing).  Errors: INVALID (mixed device, precision or
+ * stream, or a member not initialised), OOM, CUDA. */
 memd_status memd_batch_create(int32_t count, memd_ctx *const *members, memd_batch **out);
 
 /* As memd_batch_create, with the field kernel family fixed: MEMD_FIELD_AUTO

@@ -705,7 +705,20 @@ memd_status memd_batch_create_opt(int32_t count, memd_ctx* const* members, memd_
     b->f_pf = b->prec == MEMD_FP32 ? kBatchPF32 : kBatchPF64;
     b->f_kind = kind;
     if (kind == MEMD_FIELD_ROWS) b->f_rows = 256;
-    s = tune ? autotune_batch(b) : build_tables(b);
+    // members that all fix the same row-kernel width (memd_options.field_shape)
+    // fix the batch's: the row kernel with that width, untuned
+    int fixed_rows = kind != MEMD_FIELD_SITE && b->m[0]->field_kernel == MEMD_FIELD_ROWS
+                         ? b->m[0]->field_shape[3]
+                         : 0;
+    for (const memd_ctx* c : b->m)
+      if (c->field_kernel != MEMD_FIELD_ROWS || c->field_shape[3] != fixed_rows) fixed_rows = 0;
+    if (fixed_rows) {
+      b->f_kind = MEMD_FIELD_ROWS;
+      b->f_rows = fixed_rows;
+      s = build_tables(b);
+    } else {
+      s = tune ? autotune_batch(b) : build_tables(b);
+    }
   }
   if (s != MEMD_OK) {
     memd_batch_destroy(b);

@@ -140,6 +140,34 @@ def test_row_kernel_members_match_alone(precision):
         assert gm.energy()["gauss_exact"] == 1.0
 
 
+@pytest.mark.parametrize("nt", [256, 512])
+def test_members_fixing_the_row_width_fix_the_batch(nt):
+    # members created with the row kernel at one fixed width: the batch takes
+    # that width untimed, and its members still match the members alone
+    import torch
+    from paper_1309_7859_gb300.memd import Batch, Memd
+    sys_ = [s for s in systems("fp32") if s["mesh"][0] % 4 == 0]
+    stream = torch.cuda.Stream()
+
+    def fixed(s, stream=None):
+        g = Memd(s["mesh"], s["box"], s["eps"], c_light=1.0, dt=0.005,
+                 precision=s["precision"], seed=s["seed"], field_kernel="rows",
+                 field_shape=(0, 0, 0, nt), stream=stream)
+        g.init_field(s["x"], s["q"], None, s["v"])
+        return g
+    members = [fixed(s, stream) for s in sys_]
+    alone = [make(s) for s in sys_]
+    batch = Batch(members)
+    batch.step(4, thermostat=(1.0, 1.0))
+    batch.synchronize()
+    assert batch.kernel_stats().field_kernel == f"k_rows_batch<nt={nt}>"
+    for g in alone:
+        g.step(4, thermostat=(1.0, 1.0))
+    for gm, ga in zip(members, alone):
+        assert_same(state(gm), state(ga))
+    batch.close()
+
+
 def test_row_kernel_falls_back_to_site_tiles():
     # a member whose x extent is not a multiple of 4 sites keeps the batch on
     # site tiles, with the same results
