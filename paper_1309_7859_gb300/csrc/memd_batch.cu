@@ -29,6 +29,9 @@ struct memd_batch {
   cudaStream_t stream = nullptr;
   cudaStream_t side = nullptr;
   cudaEvent_t fork = nullptr, join = nullptr, ev0 = nullptr, ev1 = nullptr;
+  // memd_batch_step_io's one-step graph (per buffer parity) and its events
+  cudaGraphExec_t io_graph[2] = {nullptr, nullptr};
+  cudaEvent_t io_dep = nullptr, io_join = nullptr;
   cudaEvent_t evp[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};  // phases
   RepDesc* d_desc = nullptr;
   int* d_field_rep = nullptr;
@@ -103,6 +106,11 @@ memd_status bfail(memd_batch* b, memd_status s, const std::string& why) {
 
 void drop(memd_batch* b) {
   for (cudaGraphExec_t& g : b->graph)
+    if (g) {
+      cudaGraphExecDestroy(g);
+      g = nullptr;
+    }
+  for (cudaGraphExec_t& g : b->io_graph)
     if (g) {
       cudaGraphExecDestroy(g);
       g = nullptr;
@@ -204,6 +212,11 @@ bool batch_items(memd_batch* b, std::vector<RepDesc>& desc, int grid,
 }
 
 void free_io(memd_batch* b) {
+  for (cudaGraphExec_t& g : b->io_graph)  // they hold the block's addresses
+    if (g) {
+      cudaGraphExecDestroy(g);
+      g = nullptr;
+    }
   if (b->io_host) cudaFreeHost(b->io_host);
   b->io_host = nullptr;
   if (b->io_dev) {
@@ -484,6 +497,40 @@ cudaError_t gather_batch(memd_batch* b, int par, int thermo, double gamma, doubl
   return cudaGetLastError();
 }
 
+// the kick, drift and charge transfer of every replica
+void deposit_batch(memd_batch* b, int thermo, double gamma, double kT, cudaStream_t s) {
+  if (b->wide)
+    launch_deposit_batch_wide(b->d_desc, b->d_part_rep_w, b->n_part_w, s);
+  else
+    launch_deposit_batch(b->d_desc, b->d_part_rep, b->n_part, thermo, gamma, kT, s);
+}
+
+// the step's transfers into the ledgers and the new D of every replica
+void apply_batch(memd_batch* b, int par, cudaStream_t s) {
+  if (b->apply_dense)
+    launch_apply_dense_batch(b->prec, b->d_desc, b->d_apply_chunk, b->n_apply_chunk, par, s);
+  else
+    launch_apply_batch(b->prec, b->d_desc, b->d_part_rep, b->n_part, par, s);
+}
+
+bool batch_timed(const memd_batch* b) {
+  return b->timing >= 0 ? b->timing != 0 : b->m[0]->time_kernels != 0;
+}
+
+// a new thermostat: the step graphs go, and every member's per-particle
+// Langevin amplitudes are computed for it
+void set_thermostat(memd_batch* b, int thermo, double gamma, double kT) {
+  if (b->g_thermo == thermo && b->g_gamma == gamma && b->g_kT == kT) return;
+  drop(b);
+  for (memd_ctx* c : b->m) {
+    launch_particle_constants(memd_step_params(c, thermo, gamma, kT), c->P, b->stream);
+    c->sig_ready = false;  // a member stepped alone recomputes its own
+  }
+  b->g_thermo = thermo;
+  b->g_gamma = gamma;
+  b->g_kT = kT;
+}
+
 memd_status record(memd_batch* b, int par, int thermo, double gamma, double kT, bool timed) {
   const cudaStream_t st = b->stream;
   if (b->single) {
@@ -512,18 +559,8 @@ memd_status record(memd_batch* b, int par, int thermo, double gamma, double kT, 
     }
     return MEMD_OK;
   }
-  auto deposit = [&](cudaStream_t s) {
-    if (b->wide)
-      launch_deposit_batch_wide(b->d_desc, b->d_part_rep_w, b->n_part_w, s);
-    else
-      launch_deposit_batch(b->d_desc, b->d_part_rep, b->n_part, thermo, gamma, kT, s);
-  };
-  auto apply = [&](cudaStream_t s) {
-    if (b->apply_dense)
-      launch_apply_dense_batch(b->prec, b->d_desc, b->d_apply_chunk, b->n_apply_chunk, par, s);
-    else
-      launch_apply_batch(b->prec, b->d_desc, b->d_part_rep, b->n_part, par, s);
-  };
+  auto deposit = [&](cudaStream_t s) { deposit_batch(b, thermo, gamma, kT, s); };
+  auto apply = [&](cudaStream_t s) { apply_batch(b, par, s); };
   if (timed) {
     // instrumented: the four launches in turn on one stream, each between
     // its event pair, so that no launch's time holds another's
@@ -564,6 +601,41 @@ memd_status record(memd_batch* b, int par, int thermo, double gamma, double kT, 
   }
   apply(st);
   BCK(gather_batch(b, par, thermo, gamma, kT, st));
+  BCK(cudaGetLastError());
+  return MEMD_OK;
+}
+
+// One step of memd_batch_step_io with its copies.  The inputs' copy, their
+// unpacking and the deposition run on the side stream beside the field pass
+// (which reads no particle data); once the deposition is done, the moved part
+// of the block (positions and image counters, final after the drift) is
+// packed and copied back there beside the application and gather; the rest
+// (velocities, forces, error words) after the gather.  The same kernels in
+// the same order for every word as the copies around a step of the graph.
+memd_status record_io(memd_batch* b, int par, int thermo, double gamma, double kT) {
+  const cudaStream_t st = b->stream, sd = b->side;
+  const int R = (int)b->m.size();
+  const int64_t ntot = b->io_ntot;
+  const IoLayout L = io_layout(ntot);
+  const int64_t bytes = batch_io_bytes(ntot, R);
+  unsigned char* dev = (unsigned char*)b->io_dev;
+  BCK(cudaEventRecord(b->fork, st));
+  BCK(cudaStreamWaitEvent(sd, b->fork, 0));
+  BCK(cudaMemcpyAsync(dev, b->io_host, (size_t)L.f, cudaMemcpyHostToDevice, sd));
+  launch_io_unpack_batch(b->d_desc, b->d_ioff, R, ntot, dev, sd);
+  deposit_batch(b, thermo, gamma, kT, sd);
+  BCK(cudaEventRecord(b->io_dep, sd));
+  launch_io_pack_batch(b->d_desc, b->d_ioff, R, ntot, dev, sd, kIoMoved);
+  BCK(cudaMemcpyAsync(b->io_host, dev, (size_t)L.vel, cudaMemcpyDeviceToHost, sd));
+  BCK(cudaEventRecord(b->io_join, sd));
+  BCK(launch_field(b, par, st));
+  BCK(cudaStreamWaitEvent(st, b->io_dep, 0));
+  apply_batch(b, par, st);
+  BCK(gather_batch(b, par, thermo, gamma, kT, st));
+  launch_io_pack_batch(b->d_desc, b->d_ioff, R, ntot, dev, st, kIoRest);
+  BCK(cudaMemcpyAsync(b->io_host + L.vel, dev + L.vel, (size_t)(bytes - L.vel),
+                      cudaMemcpyDeviceToHost, st));
+  BCK(cudaStreamWaitEvent(st, b->io_join, 0));
   BCK(cudaGetLastError());
   return MEMD_OK;
 }
@@ -692,6 +764,8 @@ memd_status memd_batch_create_opt(int32_t count, memd_ctx* const* members, memd_
       cudaStreamCreateWithFlags(&b->side, cudaStreamNonBlocking) != cudaSuccess ||
       cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming) != cudaSuccess ||
       cudaEventCreateWithFlags(&b->join, cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&b->io_dep, cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&b->io_join, cudaEventDisableTiming) != cudaSuccess ||
       cudaEventCreate(&b->ev0) != cudaSuccess || cudaEventCreate(&b->ev1) != cudaSuccess ||
       [&] {
         for (auto& e : b->evp)
@@ -739,6 +813,8 @@ void memd_batch_destroy(memd_batch* b) {
   free_io(b);
   if (b->fork) cudaEventDestroy(b->fork);
   if (b->join) cudaEventDestroy(b->join);
+  if (b->io_dep) cudaEventDestroy(b->io_dep);
+  if (b->io_join) cudaEventDestroy(b->io_join);
   if (b->ev0) cudaEventDestroy(b->ev0);
   if (b->ev1) cudaEventDestroy(b->ev1);
   for (auto& e : b->evp)
@@ -771,18 +847,8 @@ memd_status memd_batch_step(memd_batch* b, int64_t nsteps, const memd_thermostat
   }
   const int thermo = th ? 1 : 0;
   const double gamma = th ? th->gamma : 0.0, kT = th ? th->kT : 0.0;
-  if (b->g_thermo != thermo || b->g_gamma != gamma || b->g_kT != kT) {
-    drop(b);
-    // per-particle Langevin amplitudes of every member for this thermostat
-    for (memd_ctx* c : b->m) {
-      launch_particle_constants(memd_step_params(c, thermo, gamma, kT), c->P, b->stream);
-      c->sig_ready = false;  // a member stepped alone recomputes its own
-    }
-    b->g_thermo = thermo;
-    b->g_gamma = gamma;
-    b->g_kT = kT;
-  }
-  const bool timed = b->timing >= 0 ? b->timing != 0 : b->m[0]->time_kernels != 0;
+  set_thermostat(b, thermo, gamma, kT);
+  const bool timed = batch_timed(b);
   for (int64_t s = 0; s < nsteps; ++s) {
     const int par = b->bpar;
     harvest(b);
@@ -888,6 +954,45 @@ memd_status memd_batch_step_io(memd_batch* b, int32_t load, int64_t nsteps,
   const int64_t ntot = b->io_ntot;
   const IoLayout L = io_layout(ntot);
   const cudaStream_t st = b->stream;
+  auto member_errors = [&]() -> memd_status {
+    const unsigned int* err = (const unsigned int*)(b->io_host + L.err);
+    for (int r = 0; r < R; ++r)
+      if (err[r]) {
+        const memd_status e = memd_check_err(b->m[r]);
+        if (e != MEMD_OK) return bfail(b, e, b->m[r]->last_error);
+      }
+    return MEMD_OK;
+  };
+  if (load && nsteps == 1 && ntot > 0 && !b->single && b->overlap && !batch_timed(b)) {
+    // the usual host loop: one graph a call, the copies beside the step
+    const int thermo = th ? 1 : 0;
+    const double gamma = th ? th->gamma : 0.0, kT = th ? th->kT : 0.0;
+    set_thermostat(b, thermo, gamma, kT);
+    harvest(b);
+    const int par = b->bpar;
+    cudaGraphExec_t& gx = b->io_graph[par];
+    if (!gx) {
+      cudaGraph_t g = nullptr;
+      BCK(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
+      const memd_status r = record_io(b, par, thermo, gamma, kT);
+      const cudaError_t e = cudaStreamEndCapture(st, &g);
+      if (r != MEMD_OK) {
+        if (g) cudaGraphDestroy(g);
+        return r;
+      }
+      const cudaError_t ie = e == cudaSuccess ? cudaGraphInstantiate(&gx, g, 0) : e;
+      if (g) cudaGraphDestroy(g);
+      if (ie != cudaSuccess) {
+        gx = nullptr;
+        return bfail(b, MEMD_ERR_CUDA, "I/O step graph capture");
+      }
+    }
+    BCK(cudaGraphLaunch(gx, st));
+    b->bpar ^= 1;
+    for (size_t r = 0; r < b->m.size(); ++r) b->m[r]->cur = (b->base[r] + b->bpar) & 1;
+    BCK(cudaStreamSynchronize(st));
+    return member_errors();
+  }
   if (load && ntot > 0) {
     // positions, velocities and image counters of every member: one copy
     BCK(cudaMemcpyAsync(b->io_dev, b->io_host, (size_t)L.f, cudaMemcpyHostToDevice, st));
@@ -901,13 +1006,7 @@ memd_status memd_batch_step_io(memd_batch* b, int32_t load, int64_t nsteps,
   BCK(cudaMemcpyAsync(b->io_host, b->io_dev, (size_t)batch_io_bytes(ntot, R),
                       cudaMemcpyDeviceToHost, st));
   BCK(cudaStreamSynchronize(st));
-  const unsigned int* err = (const unsigned int*)(b->io_host + L.err);
-  for (int r = 0; r < R; ++r)
-    if (err[r]) {
-      const memd_status e = memd_check_err(b->m[r]);
-      if (e != MEMD_OK) return bfail(b, e, b->m[r]->last_error);
-    }
-  return MEMD_OK;
+  return member_errors();
 }
 
 memd_status memd_batch_set_engine(memd_batch* b, int32_t engine, int32_t field_ctas,

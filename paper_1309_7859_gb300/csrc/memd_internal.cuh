@@ -265,19 +265,27 @@ cudaError_t launch_step_coop(const Mesh& m, int prec, const StepParams& sp, Part
 void launch_fold_init(const Mesh& m, Particles p, const double* pos_in, const int* img_in,
                       unsigned int* err, cudaStream_t st);
 // byte offsets of the host I/O block of n particles (memd_step_io)
+// The host I/O block of n particles: positions, image counters and
+// velocities (a step's inputs: the range [0, f)), then forces and the error
+// word(s).  Positions and image counters are final once the drift is done
+// and form the range [0, vel), which can go back while the step's gather
+// runs; velocities, forces and errors, the range [vel, end), after it.
 struct IoLayout {
   int64_t pos, vel, img, f, err, bytes;
 };
 __host__ __device__ inline IoLayout io_layout(int64_t n) {
   IoLayout L;
   L.pos = 0;
-  L.vel = 24 * n;
-  L.img = 48 * n;
-  L.f = L.img + ((12 * n + 7) / 8) * 8;
+  L.img = 24 * n;
+  L.vel = L.img + ((12 * n + 7) / 8) * 8;
+  L.f = L.vel + 24 * n;
   L.err = L.f + 24 * n;
   L.bytes = L.err + 8;
   return L;
 }
+// what a pack writes: everything, the moved part (positions, image
+// counters) or the rest (velocities, forces, error words)
+enum : int { kIoAll = 0, kIoMoved = 1, kIoRest = 2 };
 void launch_io_unpack(const Mesh& m, Particles p, const void* io, unsigned int* err,
                       cudaStream_t st);
 void launch_io_pack(Particles p, void* io, const unsigned int* err, cudaStream_t st);
@@ -421,7 +429,7 @@ inline int64_t batch_io_bytes(int64_t ntot, int count) {
 void launch_io_unpack_batch(const RepDesc* desc, const int64_t* off, int count, int64_t ntot,
                             const void* io, cudaStream_t st);
 void launch_io_pack_batch(const RepDesc* desc, const int64_t* off, int count, int64_t ntot,
-                          void* io, cudaStream_t st);
+                          void* io, cudaStream_t st, int part = kIoAll);
 // particle kernels of every replica (memd_particles.cu); thermostat from the arguments
 void launch_deposit_batch(const RepDesc* desc, const int* cta_rep, int nctas, int thermo,
                           double gamma, double kT, cudaStream_t st);

@@ -1624,16 +1624,20 @@ __device__ inline void io_unpack_one(const Mesh& m, Particles P, const IoLayout&
 }
 
 __device__ inline void io_pack_one(Particles P, const IoLayout& L, unsigned char* __restrict__ io,
-                                   int64_t p, int64_t e) {
+                                   int64_t p, int64_t e, int part = kIoAll) {
   double* pos = reinterpret_cast<double*>(io + L.pos);
   double* vel = reinterpret_cast<double*>(io + L.vel);
   int* img = reinterpret_cast<int*>(io + L.img);
   double* f = reinterpret_cast<double*>(io + L.f);
   for (int d = 0; d < 3; ++d) {
-    pos[3 * e + d] = P.x[3 * p + d];
-    vel[3 * e + d] = P.v[3 * p + d];
-    img[3 * e + d] = P.img[3 * p + d];
-    f[3 * e + d] = P.F[3 * p + d];
+    if (part != kIoRest) {
+      pos[3 * e + d] = P.x[3 * p + d];
+      img[3 * e + d] = P.img[3 * p + d];
+    }
+    if (part != kIoMoved) {
+      vel[3 * e + d] = P.v[3 * p + d];
+      f[3 * e + d] = P.F[3 * p + d];
+    }
   }
 }
 
@@ -1682,15 +1686,15 @@ __global__ void k_io_unpack_batch(const RepDesc* __restrict__ desc,
 
 __global__ void k_io_pack_batch(const RepDesc* __restrict__ desc,
                                 const int64_t* __restrict__ off, int count,
-                                unsigned char* __restrict__ io) {
+                                unsigned char* __restrict__ io, int part) {
   const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   const int64_t ntot = off[count];
   const IoLayout L = io_layout(ntot);
-  if (e < count)
+  if (e < count && part != kIoMoved)
     reinterpret_cast<unsigned int*>(io + L.err)[e] = desc[e].ds->err;
   if (e >= ntot) return;
   const int r = io_member(off, count, e);
-  io_pack_one(desc[r].P, L, io, e - off[r], e);
+  io_pack_one(desc[r].P, L, io, e - off[r], e, part);
 }
 
 void launch_io_unpack(const Mesh& m, Particles p, const void* io, unsigned int* err,
@@ -1711,9 +1715,9 @@ void launch_io_unpack_batch(const RepDesc* desc, const int64_t* off, int count, 
 }
 
 void launch_io_pack_batch(const RepDesc* desc, const int64_t* off, int count, int64_t ntot,
-                          void* io, cudaStream_t st) {
+                          void* io, cudaStream_t st, int part) {
   k_io_pack_batch<<<blocks_for(ntot > count ? ntot : count), kThreads, 0, st>>>(
-      desc, off, count, (unsigned char*)io);
+      desc, off, count, (unsigned char*)io, part);
 }
 
 void launch_fold_init(const Mesh& m, Particles p, const double* pos_in, const int* img_in,

@@ -168,6 +168,45 @@ def test_members_fixing_the_row_width_fix_the_batch(nt):
     batch.close()
 
 
+@pytest.mark.parametrize("nsteps", [1, 2])
+def test_batch_step_io_equals_the_separate_calls(nsteps):
+    # every member's state through the batch's host block (one step a call:
+    # the copies run beside the step; two: around it), against the same
+    # edits made member by member and batch steps; the members include odd
+    # particle counts and one without charges
+    import torch
+    from paper_1309_7859_gb300.memd import Batch
+    sys_ = systems("fp32")
+    sa, sb = torch.cuda.Stream(), torch.cuda.Stream()
+    A = [make(s, sa) for s in sys_]
+    Bm = [make(s, sb) for s in sys_]
+    ba, bb = Batch(A), Batch(Bm)
+    io = ba.io_buffers()
+    off = io["offsets"]
+    ba.step_io(0, load=False)
+    th = (1.0, 1.0)
+    for it in range(4):
+        io["vel"] *= 0.999                  # the host edits the state between calls
+        ba.step_io(nsteps, thermostat=th, load=True)
+        for g in Bm:
+            x, v, img = g.particles()
+            g.set_particles(x, v * 0.999, img)
+        bb.step(nsteps, thermostat=th)
+        bb.synchronize()
+        for r, g in enumerate(Bm):
+            x, v, img = g.particles()
+            sl = slice(off[r], off[r + 1])
+            assert np.array_equal(io["pos"][sl], x) and np.array_equal(io["vel"][sl], v)
+            assert np.array_equal(io["img"][sl], img)
+            if g.n:
+                assert np.array_equal(io["f"][sl], g.forces())
+    for ga, gb in zip(A, Bm):
+        assert_same(state(ga), state(gb))
+        assert ga.energy()["gauss_exact"] == 1.0
+    ba.close()
+    bb.close()
+
+
 def test_row_kernel_falls_back_to_site_tiles():
     # a member whose x extent is not a multiple of 4 sites keeps the batch on
     # site tiles, with the same results
