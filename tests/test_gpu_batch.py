@@ -168,15 +168,30 @@ def test_members_fixing_the_row_width_fix_the_batch(nt):
     batch.close()
 
 
-@pytest.mark.parametrize("nsteps", [1, 2])
-def test_batch_step_io_equals_the_separate_calls(nsteps):
+@pytest.mark.parametrize("nsteps,wide", [(1, False), (2, False), (1, True)])
+def test_batch_step_io_equals_the_separate_calls(nsteps, wide):
     # every member's state through the batch's host block (one step a call:
-    # the copies run beside the step; two: around it), against the same
-    # edits made member by member and batch steps; the members include odd
-    # particle counts and one without charges
+    # the copies run beside the step; two steps: around it), against the
+    # same edits made member by member and batch steps, with the quad and
+    # the one-thread-per-charge particle kernels (more than 16384 charges);
+    # the members include one without charges
     import torch
     from paper_1309_7859_gb300.memd import Batch
     sys_ = systems("fp32")
+    if wide:
+        counts = [4000, 6000, 3002, 2000, 1500, 0]
+        assert sum(counts) > 16384
+        for i, (s, n) in enumerate(zip(sys_, counts)):
+            rng = np.random.default_rng(300 + i)
+            s["q"] = inputs.neutral_charges(rng, n)
+            s["x"] = inputs.uniform_positions(rng, n, s["box"])
+            s["v"] = inputs.thermal_velocities(rng, n)
+        # one particle without charge: an odd total, so the image counters
+        # end off an 8-byte boundary
+        s0 = sys_[0]
+        s0["q"] = np.concatenate([s0["q"], [0]]).astype(np.int32)
+        s0["x"] = np.concatenate([s0["x"], [[3.3, 4.4, 5.5]]])
+        s0["v"] = np.concatenate([s0["v"], [[0.1, -0.2, 0.3]]])
     sa, sb = torch.cuda.Stream(), torch.cuda.Stream()
     A = [make(s, sa) for s in sys_]
     Bm = [make(s, sb) for s in sys_]
