@@ -490,7 +490,11 @@ memd_status memd_batch_step(memd_batch *b, int64_t nsteps, const memd_thermostat
  * positions, image counters and velocities from the block (as
  * memd_set_particles on each member), then nsteps batch steps, then the
  * block receives every member's state and forces: one host-to-device copy,
- * one device-to-host copy and one synchronisation for the whole batch.
+ * the device-to-host copies and one synchronisation for the whole batch.
+ * With load and one step the call is one CUDA graph in which the input copy
+ * runs beside the field update and the positions and image counters are
+ * copied back beside the transfer application and force gather; the result
+ * is the same as with the copies around the step.
  * Errors: INVALID, STATE (a member not initialised), OOM (page-locked or
  * device block), CUDA; a member's own error (as memd_step_io reports it). */
 typedef struct memd_batch_io {
