@@ -180,6 +180,30 @@ void drop_graphs(memd_ctx* c) {
 
 double* scal(memd_ctx* c) { return c->red + 4 * reduce_blocks(); }
 
+// the ledger between a component-major host array of 3 V words (link (d, v)
+// at d V + v) and its vertex-major words on the device: one strided copy a
+// component
+cudaError_t ledger_to_host(memd_ctx* c, void* host, cudaStream_t st) {
+  const int64_t V = c->mesh.V;
+  for (int d = 0; d < 3; ++d) {
+    const cudaError_t e =
+        cudaMemcpy2DAsync((long long*)host + d * V, 8, c->Lg + kLT * tl_pair(d, 0), 3 * kLT * 8, 8,
+                          (size_t)V, cudaMemcpyDeviceToHost, st);
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
+}
+cudaError_t ledger_from_host(memd_ctx* c, const void* host, cudaStream_t st) {
+  const int64_t V = c->mesh.V;
+  for (int d = 0; d < 3; ++d) {
+    const cudaError_t e =
+        cudaMemcpy2DAsync(c->Lg + kLT * tl_pair(d, 0), 3 * kLT * 8, (const long long*)host + d * V,
+                          8, 8, (size_t)V, cudaMemcpyHostToDevice, st);
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
+}
+
 // zero the transfer words (every kLT-th word) of a buffer, leaving the
 // ledger words between them
 cudaError_t clear_transfers(memd_ctx* c, long long* T, cudaStream_t st) {
@@ -1625,7 +1649,7 @@ memd_status memd_get_fields(memd_ctx* c, double* D, double* B, int64_t* Lg) {
     CK(cudaMemcpyAsync(B, tmp, n3 * sizeof(double), cudaMemcpyDeviceToHost, st));
     CK(cudaStreamSynchronize(st));
   }
-  if (Lg) CK(cudaMemcpy2DAsync(Lg, 8, c->Lg, kLT * 8, 8, n3, cudaMemcpyDeviceToHost, st));
+  if (Lg) CK(ledger_to_host(c, Lg, st));
   CK(cudaStreamSynchronize(st));
   dfree(c, tmp);
   return MEMD_OK;
@@ -1652,7 +1676,7 @@ memd_status memd_set_fields(memd_ctx* c, const double* D, const double* B, const
     launch_cast(c->prec, c->B(), tmp, (int64_t)n3, st);
     CK(cudaStreamSynchronize(st));
   }
-  if (Lg) CK(cudaMemcpy2DAsync(c->Lg, kLT * 8, Lg, 8, 8, n3, cudaMemcpyHostToDevice, st));
+  if (Lg) CK(ledger_from_host(c, Lg, st));
   CKL();
   CK(cudaStreamSynchronize(st));
   dfree(c, tmp);
@@ -1709,8 +1733,7 @@ memd_status memd_save_state(memd_ctx* c, void* buf, int64_t bytes) {
   };
   get(c->D(), V3 * es);
   get(c->B(), V3 * es);
-  if (ok && cudaMemcpy2DAsync(p, 8, c->Lg, kLT * 8, 8, V3, cudaMemcpyDeviceToHost, st) != cudaSuccess)
-    ok = false;
+  if (ok && ledger_to_host(c, p, st) != cudaSuccess) ok = false;
   p += V3 * 8;
   get(c->P.x, 3 * n * 8);
   get(c->P.v, 3 * n * 8);
@@ -1776,8 +1799,7 @@ memd_status memd_load_state(memd_ctx* c, const void* buf, int64_t bytes) {
   };
   put(c->D(), V3 * es);
   put(c->B(), V3 * es);
-  if (ok && cudaMemcpy2DAsync(c->Lg, kLT * 8, p, 8, 8, V3, cudaMemcpyHostToDevice, st) != cudaSuccess)
-    ok = false;
+  if (ok && ledger_from_host(c, p, st) != cudaSuccess) ok = false;
   p += V3 * 8;
   put(c->P.x, 3 * n * 8);
   put(c->P.v, 3 * n * 8);

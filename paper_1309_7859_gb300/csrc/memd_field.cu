@@ -444,8 +444,10 @@ __global__ void __launch_bounds__(kRedThreads)
     const int jm = (j == 0) ? m.n[1] - 1 : j - 1;
     const int km = (k == 0) ? m.n[2] - 1 : k - 1;
     const int64_t vx = vindex(m, im, j, k), vy = vindex(m, i, jm, k), vz = vindex(m, i, j, km);
-    const long long dl = (Lg[kLT * v] - Lg[kLT * vx]) + (Lg[kLT * (V + v)] - Lg[kLT * (V + vy)]) +
-                         (Lg[kLT * (2 * V + v)] - Lg[kLT * (2 * V + vz)]);
+    const long long dl =
+        (Lg[kLT * tl_pair(0, v)] - Lg[kLT * tl_pair(0, vx)]) +
+        (Lg[kLT * tl_pair(1, v)] - Lg[kLT * tl_pair(1, vy)]) +
+        (Lg[kLT * tl_pair(2, v)] - Lg[kLT * tl_pair(2, vz)]);
     if (dl != Q[v]) ++bad;
     const double dd = ((double)D[v] - (double)D[vx]) + ((double)D[V + v] - (double)D[V + vy]) +
                       ((double)D[2 * V + v] - (double)D[2 * V + vz]);

@@ -38,12 +38,22 @@ struct Mesh {
 };
 
 // The transfer buffer and the ledger of a system share one allocation of
-// 6 V int64 words: link l's transfer word at [kLT l], its ledger word at
-// [kLT l + 1].  The transfer application reads one and adds into the other,
-// which then share a sector; the deposition (transfer words) and the
-// application touch the same sectors.  Kernels index both arrays with this
-// stride (the ledger pointer is the allocation plus one word).
+// 6 V int64 words, vertex major: the links (0, v), (1, v), (2, v) leaving
+// vertex v are pairs 3 v, 3 v + 1, 3 v + 2, and pair k holds the transfer
+// word at [kLT k] and the ledger word at [kLT k + 1].  The transfer
+// application reads one and adds into the other, which then share a sector;
+// a charge's links (the twelve edges of its cell) sit at seven vertices in
+// four rows, a few L2 lines, where the fields' component-major order would
+// spread them over a dozen.  Kernels index both arrays with this stride
+// (the ledger pointer is the allocation plus one word).
 constexpr int kLT = 2;
+// pair of link (d, v)
+__host__ __device__ inline int64_t tl_pair(int d, int64_t v) { return 3 * v + d; }
+// pair of the link with field index l = d V + v
+__host__ __device__ inline int64_t tl_pair_of(int64_t l, int64_t V) {
+  const int d = l >= 2 * V ? 2 : (l >= V ? 1 : 0);
+  return tl_pair(d, l - d * V);
+}
 
 // error bits raised by kernels into a device word
 enum : unsigned int {

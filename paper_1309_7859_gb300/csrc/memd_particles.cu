@@ -105,8 +105,13 @@ __device__ inline long long wgt(int f, int a) { return a ? (long long)f : (long 
 // look one cell beyond a quantised cell, so no integer division is needed
 __device__ inline int wrap1(int i, int n) { return i < 0 ? i + n : (i >= n ? i - n : i); }
 
+// the vertex a link leaves (its cell coordinates wrapped once)
+__device__ inline int64_t link_vertex(const Mesh& m, int ci, int cj, int ck) {
+  return vindex(m, wrap1(ci, m.n[0]), wrap1(cj, m.n[1]), wrap1(ck, m.n[2]));
+}
+
 __device__ inline int64_t link_index(const Mesh& m, int d, int ci, int cj, int ck) {
-  return (int64_t)d * m.V + vindex(m, wrap1(ci, m.n[0]), wrap1(cj, m.n[1]), wrap1(ck, m.n[2]));
+  return (int64_t)d * m.V + link_vertex(m, ci, cj, ck);
 }
 
 // warp-aggregated int64 atomic add into a device word
@@ -214,8 +219,10 @@ __device__ inline void deposit_axis(const Mesh& m, int d, int q, int c0, int f0,
   const int64_t s2 = e2 == 0 ? st[0] : (e2 == 1 ? st[1] : st[2]);
   const int v0 = sel3(e1, cc[0], cc[1], cc[2]), w0 = sel3(e2, cc[0], cc[1], cc[2]);
   const int fv = sel3(e1, cf[0], cf[1], cf[2]), fw = sel3(e2, cf[0], cf[1], cf[2]);
-  const int64_t u0 = (int64_t)d * m.V + (int64_t)wrap1(c0, nd) * sd;
-  const int64_t u1 = (int64_t)d * m.V + (int64_t)wrap1(c0 + dc, nd) * sd;
+  // vertex indices of the old and new cell along d (the link's pair is
+  // tl_pair(d, vertex))
+  const int64_t u0 = (int64_t)wrap1(c0, nd) * sd;
+  const int64_t u1 = (int64_t)wrap1(c0 + dc, nd) * sd;
 #pragma unroll
   for (int a2 = 0; a2 < 2; ++a2)
 #pragma unroll
@@ -226,19 +233,19 @@ __device__ inline void deposit_axis(const Mesh& m, int d, int q, int c0, int f0,
       const int64_t l0 = u0 + perp;
       if (dc == 0) {
         const long long t = -(long long)q * (long long)(f1 - f0) * wp;
-        if (t) red_add_hint(&Tb[kLT * l0], (unsigned long long)t, l2_policy_last());
+        if (t) red_add_hint(&Tb[kLT * tl_pair(d, l0)], (unsigned long long)t, l2_policy_last());
       } else if (dc == 1) {
         const int64_t l1 = u1 + perp;
         const long long t0 = -(long long)q * (long long)(kS - f0) * wp;
         const long long t1 = -(long long)q * (long long)f1 * wp;
-        if (t0) red_add_hint(&Tb[kLT * l0], (unsigned long long)t0, l2_policy_last());
-        if (t1) red_add_hint(&Tb[kLT * l1], (unsigned long long)t1, l2_policy_last());
+        if (t0) red_add_hint(&Tb[kLT * tl_pair(d, l0)], (unsigned long long)t0, l2_policy_last());
+        if (t1) red_add_hint(&Tb[kLT * tl_pair(d, l1)], (unsigned long long)t1, l2_policy_last());
       } else {
         const int64_t l1 = u1 + perp;
         const long long t0 = (long long)q * (long long)f0 * wp;
         const long long t1 = (long long)q * (long long)(kS - f1) * wp;
-        if (t0) red_add_hint(&Tb[kLT * l0], (unsigned long long)t0, l2_policy_last());
-        if (t1) red_add_hint(&Tb[kLT * l1], (unsigned long long)t1, l2_policy_last());
+        if (t0) red_add_hint(&Tb[kLT * tl_pair(d, l0)], (unsigned long long)t0, l2_policy_last());
+        if (t1) red_add_hint(&Tb[kLT * tl_pair(d, l1)], (unsigned long long)t1, l2_policy_last());
       }
     }
 }
@@ -587,8 +594,8 @@ __device__ __forceinline__ void apply_body(const Mesh& m, Particles P,
   const int c0[3] = {__ldcg(mv), __ldcg(mv + 1), __ldcg(mv + 2)};
   const int c1[3] = {__ldcg(mv + 3), __ldcg(mv + 4), __ldcg(mv + 5)};
   // slot 2d: the d-link at the old cell along d; slot 2d+1: at the new
-  // cell, when the move crossed a face
-  int64_t l[6];
+  // cell, when the move crossed a face; v: the vertex the link leaves
+  int64_t v[6];
   bool has[6];
 #pragma unroll
   for (int d = 0; d < 3; ++d) {
@@ -601,25 +608,27 @@ __device__ __forceinline__ void apply_body(const Mesh& m, Particles P,
     at[e1] = p1 + a1;
     at[e2] = p2 + a2;
     at[d] = c0[d];
-    l[2 * d] = link_index(m, d, at[0], at[1], at[2]);
+    v[2 * d] = link_vertex(m, at[0], at[1], at[2]);
     has[2 * d] = true;
     at[d] = c1[d];
-    l[2 * d + 1] = link_index(m, d, at[0], at[1], at[2]);
+    v[2 * d + 1] = link_vertex(m, at[0], at[1], at[2]);
     has[2 * d + 1] = c1[d] != c0[d];
   }
   // the transfer and ledger words stay in L2 for the gather's ledger reads
   const unsigned long long pol = l2_policy_last();
   long long t[6];
 #pragma unroll
-  for (int s = 0; s < 6; ++s) t[s] = has[s] ? (long long)exch_hint(&Tb[kLT * l[s]], 0ull, pol) : 0ll;
+  for (int s = 0; s < 6; ++s)
+    t[s] = has[s] ? (long long)exch_hint(&Tb[kLT * tl_pair(s >> 1, v[s])], 0ull, pol) : 0ll;
   // only the lane that took a link's transfer adds it, so each reduction
   // below is the one addition to its word in this kernel: exact for the
   // ledger, D + x rounded once for the field
 #pragma unroll
   for (int s = 0; s < 6; ++s)
     if (t[s] != 0) {
-      red_add_hint((unsigned long long*)&Lg[kLT * l[s]], (unsigned long long)t[s], pol);
-      atomicAdd(&D[l[s]], (T)((double)t[s] * scale));
+      red_add_hint((unsigned long long*)&Lg[kLT * tl_pair(s >> 1, v[s])], (unsigned long long)t[s],
+                   pol);
+      atomicAdd(&D[(int64_t)(s >> 1) * m.V + v[s]], (T)((double)t[s] * scale));
     }
 }
 
@@ -630,19 +639,25 @@ __global__ void __launch_bounds__(kQuadThreads)
   apply_body<T>(m, P, Tb, Lg, D, scale, blockIdx.x * (int64_t)blockDim.x + threadIdx.x);
 }
 
-// Dense form of the same: every link of [l0, l1) once, each non-zero
-// transfer word added to the ledger and, scaled, to D, then cleared.  Each
-// word gets the one addition the sparse form gives it, so D + x is rounded
-// once the same way.  A link's transfer and ledger words are one 16-byte pair
-// (read and written as a vector when the allocation is 16-byte aligned: a
-// caller's allocator need not align it; else word by word).
+// Dense form of the same: every link pair of [l0, l1) once (pair 3 v + d
+// is link (d, v), field index d V + v), each non-zero transfer word added to
+// the ledger and, scaled, to D, then cleared.  Each word gets the one
+// addition the sparse form gives it, so D + x is rounded once the same way.
+// A link's transfer and ledger words are one 16-byte pair (read and written
+// as a vector when the allocation is 16-byte aligned: a caller's allocator
+// need not align it; else word by word).
+__device__ inline int64_t pair_field_index(int64_t w, int64_t V) {
+  const int64_t v = w / 3;
+  return (w - 3 * v) * V + v;
+}
 template <typename T>
 __device__ __forceinline__ void apply_word(long long* __restrict__ Tb, long long* __restrict__ Lg,
-                                           T* __restrict__ D, double scale, int64_t l) {
-  const long long t = Tb[kLT * l];
+                                           T* __restrict__ D, double scale, int64_t w, int64_t V) {
+  const long long t = Tb[kLT * w];
   if (t != 0) {
-    Tb[kLT * l] = 0;
-    Lg[kLT * l] += t;
+    const int64_t l = pair_field_index(w, V);
+    Tb[kLT * w] = 0;
+    Lg[kLT * w] += t;
     D[l] = D[l] + (T)((double)t * scale);
   }
 }
@@ -653,9 +668,11 @@ __device__ __forceinline__ void apply_word(long long* __restrict__ Tb, long long
 template <typename T>
 __device__ __forceinline__ void apply_dense_range(long long* __restrict__ Tb,
                                                   long long* __restrict__ Lg, T* __restrict__ D,
-                                                  double scale, int64_t l0, int64_t l1) {
+                                                  double scale, int64_t l0, int64_t l1,
+                                                  int64_t V) {
   if (reinterpret_cast<uintptr_t>(Tb) & 15) {
-    for (int64_t l = l0 + threadIdx.x; l < l1; l += blockDim.x) apply_word<T>(Tb, Lg, D, scale, l);
+    for (int64_t l = l0 + threadIdx.x; l < l1; l += blockDim.x)
+      apply_word<T>(Tb, Lg, D, scale, l, V);
     return;
   }
   longlong2* TL = reinterpret_cast<longlong2*>(Tb);  // (transfer, ledger) of each link
@@ -668,12 +685,13 @@ __device__ __forceinline__ void apply_dense_range(long long* __restrict__ Tb,
     tl[j] = w[j] < l1 ? __ldcs(TL + w[j]) : make_longlong2(0, 0);
   }
 #pragma unroll
-  for (int j = 0; j < 2 * kApplyPairs; ++j) dv[j] = tl[j].x != 0 ? D[w[j]] : T(0);
+  for (int j = 0; j < 2 * kApplyPairs; ++j)
+    dv[j] = tl[j].x != 0 ? D[pair_field_index(w[j], V)] : T(0);
 #pragma unroll
   for (int j = 0; j < 2 * kApplyPairs; ++j)
     if (tl[j].x != 0) {
       TL[w[j]] = make_longlong2(0, tl[j].y + tl[j].x);
-      D[w[j]] = dv[j] + (T)((double)tl[j].x * scale);
+      D[pair_field_index(w[j], V)] = dv[j] + (T)((double)tl[j].x * scale);
     }
 }
 
@@ -682,7 +700,8 @@ __global__ void __launch_bounds__(kApplyThreads)
     k_apply_dense(int64_t nl, long long* __restrict__ Tb, long long* __restrict__ Lg,
                   T* __restrict__ D, double scale) {
   const int64_t l0 = (int64_t)blockIdx.x * kApplyChunk;
-  apply_dense_range<T>(Tb, Lg, D, scale, l0, l0 + kApplyChunk < nl ? l0 + kApplyChunk : nl);
+  apply_dense_range<T>(Tb, Lg, D, scale, l0, l0 + kApplyChunk < nl ? l0 + kApplyChunk : nl,
+                       nl / 3);
 }
 
 // ------------------------------------------------------------- self energy
@@ -886,12 +905,13 @@ __device__ __forceinline__ void gather_body(const Mesh& m, const StepParams& sp,
       int at[3] = {c[0], c[1], c[2]};
       at[e1] += a1;
       at[e2] += a2;
-      const int64_t l = link_index(m, d, at[0], at[1], at[2]);
+      const int64_t vtx = link_vertex(m, at[0], at[1], at[2]);
+      const int64_t l = (int64_t)d * m.V + vtx;
       Dv[d] = __ldcg(D + l);  // D was updated in this launch by other CTAs (single launch)
       Iv[d] = ie[l];
       if (sp.self_mode != 0 && sizeof(T) == 8) I64[d] = ie64[l];
       if (Tpend) {  // transfers of this step not yet applied: as their application rounds
-        const long long t = __ldcg(Tpend + kLT * l);
+        const long long t = __ldcg(Tpend + kLT * tl_pair(d, vtx));
         if (t != 0) Dv[d] = Dv[d] + pending_inc<T>(t, sp.scale, exact32);
       }
     }
@@ -1126,7 +1146,7 @@ __global__ void __launch_bounds__(kApplyThreads)
   const RepDesc& r = desc[c.x];
   const int64_t nl = 3 * r.m.V, l0 = (int64_t)c.y * kApplyChunk;
   apply_dense_range<T>(r.Tb, r.Lg, (T*)r.D[par ^ 1], r.sp.scale, l0,
-                       l0 + kApplyChunk < nl ? l0 + kApplyChunk : nl);
+                       l0 + kApplyChunk < nl ? l0 + kApplyChunk : nl, r.m.V);
 }
 
 template <typename T>
@@ -1457,11 +1477,11 @@ __device__ __forceinline__ void commit_tile(const Mesh& m, int txi, int tyi, int
   for (int k = z0; k < z1; ++k)
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
-      const int64_t l = (int64_t)c * m.V + (int64_t)k * P + (int64_t)y * nx + x;
-      const long long t = Tp[kLT * l];
+      const int64_t w = tl_pair(c, (int64_t)k * P + (int64_t)y * nx + x);
+      const long long t = Tp[kLT * w];
       if (t != 0) {
-        Lg[kLT * l] += t;
-        Tp[kLT * l] = 0;
+        Lg[kLT * w] += t;
+        Tp[kLT * w] = 0;
       }
     }
 }

@@ -293,7 +293,7 @@ __global__ void k_zflux(Mesh m, const long long* __restrict__ Q, const long long
   const int64_t t = v - (int64_t)k * P;
   const long long out = share(F[k], P, t);
   const long long in = (k == 0) ? 0 : share(F[k - 1], P, t);
-  Lg[kLT * (2 * m.V + v)] = out;
+  Lg[kLT * tl_pair(2, v)] = out;
   r[v] = Q[v] - (out - in);
 }
 
@@ -331,7 +331,7 @@ __global__ void k_yflux(Mesh m, const long long* __restrict__ Fy, long long* __r
   const int j = (int)(line % m.n[1]);
   const long long out = share(Fy[line], m.n[0], i);
   const long long in = (j == 0) ? 0 : share(Fy[line - 1], m.n[0], i);
-  Lg[kLT * (m.V + v)] = out;
+  Lg[kLT * tl_pair(1, v)] = out;
   r[v] -= out - in;
 }
 
@@ -343,7 +343,7 @@ __global__ void k_xscan(Mesh m, const long long* __restrict__ r, long long* __re
   long long s = 0;
   for (int i = 0; i < m.n[0]; ++i) {
     s += r[line * m.n[0] + i];
-    Lg[kLT * (line * m.n[0] + i)] = s;
+    Lg[kLT * tl_pair(0, line * m.n[0] + i)] = s;
   }
   if (s != 0) atomicOr(err, kErrGauss);
 }
@@ -364,7 +364,7 @@ __global__ void __launch_bounds__(kThreads)
   long long s = 0;
   for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < m.V;
        v += (int64_t)gridDim.x * blockDim.x)
-    s += Lg[kLT * (d * m.V + v)];
+    s += Lg[kLT * tl_pair(d, v)];
   s = block_sum_ll(s, sh);
   if (threadIdx.x == 0) atomicAdd((unsigned long long*)&ds->lsum[d], (unsigned long long)s);
 }
@@ -377,7 +377,7 @@ __global__ void k_init_D(Mesh m, double* __restrict__ D, const long long* __rest
   const int d = (int)(l / m.V);
   const double P = (double)(long long)ds->Pacc[d] * (m.a / (double)kS);
   const double shift = -P / Vbox - ((double)ds->lsum[d] * scale) / (double)m.V;
-  D[l] = (double)Lg[kLT * l] * scale + shift;
+  D[l] = (double)Lg[kLT * tl_pair(d, l - d * m.V)] * scale + shift;
 }
 
 // ------------------------------------------------------------- reductions

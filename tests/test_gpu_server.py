@@ -2,6 +2,8 @@
 footprint, steps the resident ones together and retires them; every request
 must get exactly the result it gets when run alone, whatever it was mixed
 with, and the admission ledger must stay inside the budget."""
+import time
+
 import numpy as np
 import pytest
 
@@ -68,6 +70,10 @@ def test_server_results_match_alone_with_queuing():
         assert a <= 3
         if d == len(reqs):
             break
+        if seen_active < 2:
+            # a quantum of these small systems is shorter than a request's
+            # setup on the admission threads: give them time to finish one
+            time.sleep(0.005)
     assert d == len(reqs) and seen_active >= 2
     for s, rid in zip(reqs, ids):
         assert srv.status(rid) == 2
