@@ -1062,7 +1062,7 @@ memd_status memd_init_field(memd_ctx* c, int64_t n, const double* pos, const int
       launch_cast(c->prec, c->D(), D64, 3 * m.V, st);
       CK(cudaMemsetAsync(c->B(), 0, 3 * m.V * esz(c), st));
       CK(clear_transfers(c, c->Tb, st));
-      if (c->Tb2) CK(clear_transfers(c, c->Tb2, st));
+      if (c->Tb2) CK(cudaMemsetAsync(c->Tb2, 0, kLT * 3 * m.V * sizeof(long long), st));
       c->pending = false;
       CK(cudaMemsetAsync(&c->ds->ticket, 0, sizeof(unsigned int), st));
       const StepParams sp = step_params(c, 0, 0.0, 0.0);
@@ -1121,10 +1121,12 @@ static memd_status record_step(memd_ctx* c, const StepParams& sp, int par, bool 
   return MEMD_OK;
 }
 
-// transfer buffer of buffer parity q: the single-launch step leaves the
-// transfers of its move, not yet applied, in the buffer of the parity it
-// wrote (the graph step uses buffer 0 only, and applies them at once)
-static long long* tbuf(memd_ctx* c, int q) { return q == 0 ? c->Tb : c->Tb2; }
+// transfer buffer of buffer parity q of the single-launch step, which leaves
+// the transfers of its move, not yet applied, in the buffer of the parity it
+// wrote: transfer words only, component major (tw_index with cmV = V), the
+// two buffers one after the other in Tb2 (the graph step uses the pairs of
+// Tb, and applies them at once)
+static long long* tbuf(memd_ctx* c, int q) { return c->Tb2 + q * 3 * c->mesh.V; }
 
 // the whole step as one cooperative launch (same kernels' device functions)
 static memd_status record_step_coop(memd_ctx* c, const StepParams& sp, int par, bool timed) {
@@ -1147,7 +1149,7 @@ static memd_status record_step_coop(memd_ctx* c, const StepParams& sp, int par, 
 memd_status memd_flush(memd_ctx* c) {
   if (!c->pending) return MEMD_OK;
   launch_apply(c->mesh, c->prec, c->P, tbuf(c, c->cur), c->Lg, c->D(),
-               std::ldexp(1.0, -48) / (c->mesh.a * c->mesh.a), c->stream);
+               std::ldexp(1.0, -48) / (c->mesh.a * c->mesh.a), c->stream, c->mesh.V);
   c->pending = false;
   if (cudaGetLastError() != cudaSuccess) return fail(c, MEMD_ERR_CUDA, "applying pending transfers");
   return MEMD_OK;
@@ -1189,7 +1191,7 @@ static memd_status step_prepare(memd_ctx* c, const memd_thermostat* th, StepPara
   }
   if (!c->graph[0] && !c->graph[1]) c->coop = want_coop(c);
   if (c->coop && !c->Tb2) {
-    // the same stride as the first (its odd words unused)
+    // the single-launch step's two transfer buffers (3 V words each)
     c->Tb2 = (long long*)dalloc(c, kLT * 3 * c->mesh.V * sizeof(long long));
     if (!c->Tb2) return fail(c, MEMD_ERR_OOM, "second transfer buffer");
     CK(cudaMemsetAsync(c->Tb2, 0, kLT * 3 * c->mesh.V * sizeof(long long), c->stream));
@@ -1813,7 +1815,7 @@ memd_status memd_load_state(memd_ctx* c, const void* buf, int64_t bytes) {
   // state, the accumulators clear; the per-particle constants are formed
   // again from the masses at the next step
   CK(clear_transfers(c, c->Tb, st));
-  if (c->Tb2) CK(clear_transfers(c, c->Tb2, st));
+  if (c->Tb2) CK(cudaMemsetAsync(c->Tb2, 0, kLT * 3 * c->mesh.V * sizeof(long long), st));
   c->pending = false;
   CK(cudaMemcpyAsync(&c->ds->step, &h.step, sizeof(long long), cudaMemcpyHostToDevice, st));
   CK(cudaMemcpyAsync(c->ds->Plast, h.Plast, 3 * sizeof(long long), cudaMemcpyHostToDevice, st));

@@ -54,6 +54,13 @@ __host__ __device__ inline int64_t tl_pair_of(int64_t l, int64_t V) {
   const int d = l >= 2 * V ? 2 : (l >= V ? 1 : 0);
   return tl_pair(d, l - d * V);
 }
+// The word of link (d, v) in a transfer buffer: the transfer word of its
+// pair (cmV == 0), or, in the single-launch step's own buffers of transfer
+// words only (cmV == V), component major at d V + v, where the field tiles'
+// dense reads of a plane's pending transfers are coalesced.
+__host__ __device__ inline int64_t tw_index(int d, int64_t v, int64_t cmV) {
+  return cmV ? d * cmV + v : kLT * tl_pair(d, v);
+}
 
 // error bits raised by kernels into a device word
 enum : unsigned int {
@@ -307,8 +314,9 @@ void launch_kick_drift_deposit(const Mesh& m, const StepParams& sp, Particles p,
                                long long* Tb, DevState* ds, cudaStream_t st);
 void launch_move_deposit(const Mesh& m, Particles p, const double* pos_new,
                          const int* img_new, long long* Tb, DevState* ds, cudaStream_t st);
+// cmV: the layout of Tb (tw_index); the ledger Lg is always the pairs'
 void launch_apply(const Mesh& m, int prec, Particles p, long long* Tb, long long* Lg, void* D,
-                  double scale, cudaStream_t st);
+                  double scale, cudaStream_t st, int64_t cmV = 0);
 // the same over every one of nlinks transfer words (one pass, no particle
 // data); identical results.  Cheaper when the mesh has few links per charge.
 void launch_apply_dense(int prec, int64_t nlinks, long long* Tb, long long* Lg, void* D,

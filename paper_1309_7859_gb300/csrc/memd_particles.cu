@@ -205,9 +205,10 @@ __device__ inline double unit_noise(unsigned r) {
 // far (axes before d at their new cells, axes after d at their old ones).
 __device__ inline int sel3(int d, int a, int b, int c) { return d == 0 ? a : (d == 1 ? b : c); }
 
+// cmV: the layout of Tb (tw_index)
 __device__ inline void deposit_axis(const Mesh& m, int d, int q, int c0, int f0, int f1, int dc,
                                     const int cc[3], const int cf[3],
-                                    unsigned long long* __restrict__ Tb) {
+                                    unsigned long long* __restrict__ Tb, int64_t cmV = 0) {
   // axis d is the lane's own (a run-time value): select sizes, strides and
   // perpendicular coordinates instead of indexing arrays with it
   const int e1 = d == 2 ? 0 : d + 1, e2 = d == 0 ? 2 : d - 1;
@@ -233,19 +234,19 @@ __device__ inline void deposit_axis(const Mesh& m, int d, int q, int c0, int f0,
       const int64_t l0 = u0 + perp;
       if (dc == 0) {
         const long long t = -(long long)q * (long long)(f1 - f0) * wp;
-        if (t) red_add_hint(&Tb[kLT * tl_pair(d, l0)], (unsigned long long)t, l2_policy_last());
+        if (t) red_add_hint(&Tb[tw_index(d, l0, cmV)], (unsigned long long)t, l2_policy_last());
       } else if (dc == 1) {
         const int64_t l1 = u1 + perp;
         const long long t0 = -(long long)q * (long long)(kS - f0) * wp;
         const long long t1 = -(long long)q * (long long)f1 * wp;
-        if (t0) red_add_hint(&Tb[kLT * tl_pair(d, l0)], (unsigned long long)t0, l2_policy_last());
-        if (t1) red_add_hint(&Tb[kLT * tl_pair(d, l1)], (unsigned long long)t1, l2_policy_last());
+        if (t0) red_add_hint(&Tb[tw_index(d, l0, cmV)], (unsigned long long)t0, l2_policy_last());
+        if (t1) red_add_hint(&Tb[tw_index(d, l1, cmV)], (unsigned long long)t1, l2_policy_last());
       } else {
         const int64_t l1 = u1 + perp;
         const long long t0 = (long long)q * (long long)f0 * wp;
         const long long t1 = (long long)q * (long long)(kS - f1) * wp;
-        if (t0) red_add_hint(&Tb[kLT * tl_pair(d, l0)], (unsigned long long)t0, l2_policy_last());
-        if (t1) red_add_hint(&Tb[kLT * tl_pair(d, l1)], (unsigned long long)t1, l2_policy_last());
+        if (t0) red_add_hint(&Tb[tw_index(d, l0, cmV)], (unsigned long long)t0, l2_policy_last());
+        if (t1) red_add_hint(&Tb[tw_index(d, l1, cmV)], (unsigned long long)t1, l2_policy_last());
       }
     }
 }
@@ -264,7 +265,8 @@ __device__ inline void deposit_axis(const Mesh& m, int d, int q, int c0, int f0,
 __device__ inline long long quad_move(const Mesh& m, Particles P, int64_t p, int d, bool active,
                                       double x, int ko, double xn, int kn, bool ok_in,
                                       unsigned long long* __restrict__ Tb, DevState* ds,
-                                      const char* pf_ie = nullptr, int pf_es = 0) {
+                                      const char* pf_ie = nullptr, int pf_es = 0,
+                                      int64_t cmV = 0) {
   const unsigned full = 0xffffffffu;
   const int lane = threadIdx.x & 31, base = lane & ~3;
   int c0 = 0, f0 = 0, c1 = 0, f1 = 0, dc = 0;
@@ -315,7 +317,7 @@ __device__ inline long long quad_move(const Mesh& m, Particles P, int64_t p, int
         cc[e] = (e < d) ? C1[e] : C0[e];
         cf[e] = (e < d) ? F1[e] : F0[e];
       }
-      deposit_axis(m, d, P.q[p], c0, f0, f1, dc, cc, cf, Tb);
+      deposit_axis(m, d, P.q[p], c0, f0, f1, dc, cc, cf, Tb, cmV);
       P.x[3 * p + d] = xn;
       P.img[3 * p + d] = kn;
       mv[d] = c0;
@@ -422,7 +424,7 @@ __global__ void k_particle_constants(StepParams sp, Particles P) {
 __device__ __forceinline__ long long deposit_body(const Mesh& m, const StepParams& sp, Particles P,
                                              unsigned long long* __restrict__ Tb, DevState* ds,
                                              int64_t g, const char* pf_ie = nullptr,
-                                             int pf_es = 0) {
+                                             int pf_es = 0, int64_t cmV = 0) {
   const int64_t p = g >> 2;
   const int d = (int)(g & 3);
   const bool active = p < P.n;
@@ -444,7 +446,7 @@ __device__ __forceinline__ long long deposit_body(const Mesh& m, const StepParam
       ok = false;
     }
   }
-  return quad_move(m, P, p, d, active, x, ko, xn, kn, ok, Tb, ds, pf_ie, pf_es);
+  return quad_move(m, P, p, d, active, x, ko, xn, kn, ok, Tb, ds, pf_ie, pf_es, cmV);
 }
 
 // One thread per charge: the half kick, drift and charge transfer of
@@ -583,7 +585,7 @@ template <typename T>
 __device__ __forceinline__ void apply_body(const Mesh& m, Particles P,
                                            unsigned long long* __restrict__ Tb,
                                            long long* __restrict__ Lg, T* __restrict__ D,
-                                           double scale, int64_t g) {
+                                           double scale, int64_t g, int64_t cmV = 0) {
   const int64_t p = g >> 2;
   if (p >= P.n) return;
   const int corner = (int)(g & 3);
@@ -619,7 +621,7 @@ __device__ __forceinline__ void apply_body(const Mesh& m, Particles P,
   long long t[6];
 #pragma unroll
   for (int s = 0; s < 6; ++s)
-    t[s] = has[s] ? (long long)exch_hint(&Tb[kLT * tl_pair(s >> 1, v[s])], 0ull, pol) : 0ll;
+    t[s] = has[s] ? (long long)exch_hint(&Tb[tw_index(s >> 1, v[s], cmV)], 0ull, pol) : 0ll;
   // only the lane that took a link's transfer adds it, so each reduction
   // below is the one addition to its word in this kernel: exact for the
   // ledger, D + x rounded once for the field
@@ -635,8 +637,8 @@ __device__ __forceinline__ void apply_body(const Mesh& m, Particles P,
 template <typename T>
 __global__ void __launch_bounds__(kQuadThreads)
     k_apply(const __grid_constant__ Mesh m, Particles P, unsigned long long* __restrict__ Tb, long long* __restrict__ Lg,
-            T* __restrict__ D, double scale) {
-  apply_body<T>(m, P, Tb, Lg, D, scale, blockIdx.x * (int64_t)blockDim.x + threadIdx.x);
+            T* __restrict__ D, double scale, int64_t cmV) {
+  apply_body<T>(m, P, Tb, Lg, D, scale, blockIdx.x * (int64_t)blockDim.x + threadIdx.x, cmV);
 }
 
 // Dense form of the same: every link pair of [l0, l1) once (pair 3 v + d
@@ -911,7 +913,7 @@ __device__ __forceinline__ void gather_body(const Mesh& m, const StepParams& sp,
       Iv[d] = ie[l];
       if (sp.self_mode != 0 && sizeof(T) == 8) I64[d] = ie64[l];
       if (Tpend) {  // transfers of this step not yet applied: as their application rounds
-        const long long t = __ldcg(Tpend + kLT * tl_pair(d, vtx));
+        const long long t = __ldcg(Tpend + tw_index(d, vtx, m.V));  // the step's own buffer
         if (t != 0) Dv[d] = Dv[d] + pending_inc<T>(t, sp.scale, exact32);
       }
     }
@@ -1477,11 +1479,12 @@ __device__ __forceinline__ void commit_tile(const Mesh& m, int txi, int tyi, int
   for (int k = z0; k < z1; ++k)
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
-      const int64_t w = tl_pair(c, (int64_t)k * P + (int64_t)y * nx + x);
-      const long long t = Tp[kLT * w];
+      const int64_t v = (int64_t)k * P + (int64_t)y * nx + x;
+      const int64_t w = tw_index(c, v, m.V);  // the step's own buffer: component major
+      const long long t = Tp[w];
       if (t != 0) {
-        Lg[kLT * w] += t;
-        Tp[kLT * w] = 0;
+        Lg[kLT * tl_pair(c, v)] += t;
+        Tp[w] = 0;
       }
     }
 }
@@ -1514,8 +1517,8 @@ __global__ void __launch_bounds__(kCoopThreads)
     }
   } else {
     for (int64_t b = (int64_t)blockIdx.x * 32; b < nq; b += stride)
-      quad_dipole_add(ds->Pacc,
-                      deposit_body(m, sp, P, Tcur, ds, b + lane, (const char*)ie, (int)sizeof(T)));
+      quad_dipole_add(ds->Pacc, deposit_body(m, sp, P, Tcur, ds, b + lane, (const char*)ie,
+                                             (int)sizeof(T), m.V));
   }
   grid_barrier(ds, G, sp.wait_ns);
   if (pwarp) {
@@ -1783,15 +1786,15 @@ void launch_move_deposit(const Mesh& m, Particles p, const double* pos_new, cons
 }
 
 void launch_apply(const Mesh& m, int prec, Particles p, long long* Tb, long long* Lg, void* D,
-                  double scale, cudaStream_t st) {
+                  double scale, cudaStream_t st, int64_t cmV) {
   if (p.n <= 0) return;
   const int qt = quad_threads(p.n);
   const unsigned nb = blocks_for(4 * p.n, qt);
   if (prec == 1)
-    k_apply<float><<<nb, qt, 0, st>>>(m, p, (unsigned long long*)Tb, Lg, (float*)D, scale);
+    k_apply<float><<<nb, qt, 0, st>>>(m, p, (unsigned long long*)Tb, Lg, (float*)D, scale, cmV);
   else
-    k_apply<double><<<nb, qt, 0, st>>>(m, p, (unsigned long long*)Tb, Lg, (double*)D,
-                                                 scale);
+    k_apply<double><<<nb, qt, 0, st>>>(m, p, (unsigned long long*)Tb, Lg, (double*)D, scale,
+                                       cmV);
 }
 
 void launch_apply_dense(int prec, int64_t nlinks, long long* Tb, long long* Lg, void* D,

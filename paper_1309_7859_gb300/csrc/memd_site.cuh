@@ -16,9 +16,9 @@ namespace memd {
 // 9 PF values per thread are in flight while a plane is computed.  Same
 // arithmetic per site as k_fused_curl.
 //
-// Tp (optional): transfers not yet applied to D (int64 transfer words of the
-// vertex-major pairs, tl_pair): D(site) is then read as D + Tp scale, rounded
-// exactly as their application would (pending_inc).
+// Tp (optional): transfers not yet applied to D (int64 transfer words only,
+// component major: tw_index with cmV = V): D(site) is then read as D + Tp
+// scale, rounded exactly as their application would (pending_inc).
 
 // (T)((double)t * scale), the increment a transfer t adds to D.  With FP32
 // fields and a power-of-two scale (exact32) it is computed as the rounded
@@ -88,11 +88,10 @@ __device__ __forceinline__ void site_tile(const Mesh& m, const T* __restrict__ D
   auto ldD = [&](int k, T (&r)[3]) {
     ld3(Din, k, r);
     if (!live || !Tp) return;
-    // the site's three links: consecutive pairs
-    const long long* q = Tp + kLT * tl_pair(0, (int64_t)k * P + off);
+    const long long* q = Tp + tw_index(0, (int64_t)k * P + off, V);
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
-      const long long t = q[kLT * c];
+      const long long t = q[c * V];
       if (t != 0) r[c] = r[c] + pending_inc<T>(t, tscale, exact32);
     }
   };
