@@ -488,9 +488,17 @@ static memd_status autotune_fused(memd_ctx* c) {
   FusedCfg cand[160];
   int nc = 0;
   const int fk = c->field_kernel;
-  const bool want_ldg = fk == MEMD_FIELD_AUTO || fk == MEMD_FIELD_LDG ||
-                        (fk == MEMD_FIELD_TMA && !c->tma_ok);
-  const bool want_site = fk == MEMD_FIELD_AUTO || fk == MEMD_FIELD_SITE;
+  // Left to choose, the row kernel's two widths are the only candidates
+  // where the mesh fits it: in the step the field pass runs beside the
+  // deposition, and there the row kernel was the fastest measured on every
+  // such mesh (64^3 salt and colloid systems: 35.2 / 31.2 us a step against
+  // 36-39 / 33-35 for the tile kernels that time fastest alone; 256^3: the
+  // row kernel is also the fastest alone), while the tile kernels' timings
+  // alone do not carry over to the step.
+  const bool rows_only = fk == MEMD_FIELD_AUTO && rows_setup(c, 256);
+  const bool want_ldg = !rows_only && (fk == MEMD_FIELD_AUTO || fk == MEMD_FIELD_LDG ||
+                                       (fk == MEMD_FIELD_TMA && !c->tma_ok));
+  const bool want_site = !rows_only && (fk == MEMD_FIELD_AUTO || fk == MEMD_FIELD_SITE);
   if (want_ldg) nc = fused_candidates(c->mesh, c->prec, cand, 32);
   if (want_site) {
     // the one-thread-per-site plain-load kernel, same tile shapes, loads 1 or
@@ -505,7 +513,7 @@ static memd_status autotune_fused(memd_ctx* c) {
       }
     }
   }
-  if (c->tma_ok) {
+  if (c->tma_ok && !rows_only) {
     FusedCfg t[32];
     const int nt = fused_candidates(c->mesh, 1, t, 32);  // the TMA kernel has all three heights
     for (int i = 0; i < nt && nc < 158; ++i) {
