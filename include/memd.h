@@ -118,7 +118,9 @@ typedef struct memd_options {
   void *alloc_user;
   int32_t time_kernels;   /* 1: CUDA events around the field kernels, see
                              memd_get_kernel_stats */
-  int32_t field_kernel;   /* MEMD_FIELD_AUTO: autotuned over the kernels below;
+  int32_t field_kernel;   /* MEMD_FIELD_AUTO: the ROWS kernel (its two CTA widths
+                             timed) where the mesh fits it, else timed over the
+                             kernels below;
                              MEMD_FIELD_LDG: plain-load kernel, halo loops per thread;
                              MEMD_FIELD_TMA: TMA-staged kernel (when x rows are
                              16-byte multiples, else the plain-load kernel);
