@@ -334,6 +334,35 @@ def test_field_kernels_agree_on_a_large_mesh(precision):
             assert np.array_equal(a, b)
 
 
+def test_automatic_field_kernel_choice():
+    # left to choose, a system steps with the row kernel where its mesh fits
+    # it (x extent a multiple of 4 sites with FP32 fields) and with a tile
+    # kernel where it does not, with the results of the kernel asked for
+    from paper_1309_7859_gb300.memd import Memd
+    for mesh, rows in (((64, 40, 36), True), ((66, 40, 36), False)):
+        sysc = small_system(mesh, 3000, SLAB, precision="fp32", dt=0.005)
+        out = []
+        for fk in ("auto", "rows" if rows else "site"):
+            g = Memd(sysc.mesh, sysc.box, sysc.eps, c_light=1.0, dt=sysc.dt, precision="fp32",
+                     seed=3, field_kernel=fk, step_engine="graph")
+            g.init_field(sysc.x, sysc.q, sysc.m, sysc.v)
+            g.step(4, thermostat=(1.0, 1.0))
+            assert g.energy()["gauss_exact"] == 1.0
+            out.append((g.kernel_stats().field_kernel, g.fields(), g.forces()))
+            g.close()
+        assert out[0][0].startswith("k_rows") == rows, out[0][0]
+        if rows:
+            # the row kernel at either width does the same arithmetic
+            for a, b in zip(out[0][1], out[1][1]):
+                assert np.array_equal(a, b)
+            assert np.array_equal(out[0][2], out[1][2])
+        else:
+            # a tile kernel (the TMA one agrees to rounding)
+            for a, b in zip(out[0][1][:2], out[1][1][:2]):
+                assert rel(a, b) < 1e-5
+            assert rel(out[0][2], out[1][2]) < 1e-5
+
+
 @pytest.mark.parametrize("mesh,n,eps,precision", [((8, 8, 8), 16, EpsSpec("const", 0, (1.0,)), "fp64"),
                                                   ((40, 20, 12), 300, SLAB, "fp32"),
                                                   ((24, 24, 24), 5000, SLAB, "fp32"),
