@@ -109,6 +109,9 @@ memd_status memd_flush(memd_ctx* c);  // apply pending transfers of the single-l
 // potential (multigrid-preconditioned CG on the vertices)
 namespace memd {
 memd_status mg_eps_eff(memd_ctx* c, double* psi, double eps_eff[9], double tol, int maxit);
+// on the calling thread from now on: the cell problems of mg_eps_eff solved
+// in turn (one solver) instead of at once (three solvers, streams, threads)
+void memd_mg_cells_in_turn(bool on);
 memd_status mg_relax(memd_ctx* c, double* D64, const double* psi, const double eps_eff_inv[9],
                      double tol, int maxit, int* iters);
 // memd_rows.cu: the row kernel's work split for a set of contexts (false

@@ -22,6 +22,7 @@
 // FP64 throughout.
 #include <algorithm>
 #include <cmath>
+#include <thread>
 #include <vector>
 
 #include "memd_ctx.cuh"
@@ -582,41 +583,98 @@ struct MgSolver {
 // ------------------------------------------------------------ entry points
 // Cell problems: psi_d (3V, stored), and eps_eff[e][d] = mean over links of
 // eps_e (delta_ed - grad_e psi_d) (row e, column d).
+// Set on a thread (the request server's admission workers, several of which
+// already set systems up at once): that thread's cell problems are solved in
+// turn, with one solver's scratch.
+namespace {
+thread_local bool t_cells_in_turn = false;
+}
+void memd_mg_cells_in_turn(bool on) { t_cells_in_turn = on; }
+
 memd_status mg_eps_eff(memd_ctx* c, double* psi, double eps_eff[9], double tol, int maxit) {
   const Mesh& m = c->mesh;
-  const cudaStream_t st = c->stream;
   const Lv L{m.n[0], m.n[1], m.n[2], m.V};
-  MgSolver S;
-  if (!S.build(c, st)) {
-    S.release();
-    return MEMD_ERR_OOM;
-  }
-  double* f = S.alloc(m.V);
-  double* U = S.alloc(3 * m.V);
-  if (!f || !U) {
-    S.release();
-    return MEMD_ERR_OOM;
-  }
+  // The three cell problems are independent: each gets its own solver (and
+  // scratch, built here on the calling thread), its own stream, and its own
+  // host thread, since a solve waits on its own convergence checks; they run
+  // at once, with the results of solving them in turn (which a thread set by
+  // memd_mg_cells_in_turn does, with one solver on the context's stream).
+  const int ns = t_cells_in_turn ? 1 : 3;
+  MgSolver S[3];
+  double* f[3] = {nullptr, nullptr, nullptr};
+  double* U[3] = {nullptr, nullptr, nullptr};
+  cudaStream_t sts[3] = {c->stream, nullptr, nullptr};
+  cudaEvent_t ready = nullptr;
   memd_status s = MEMD_OK;
-  for (int d = 0; d < 3 && s == MEMD_OK; ++d) {
-    k_div_eps_unit<<<nblk(m.V), kT, 0, st>>>(L, c->ie64, d, 1.0 / m.a, f);
-    s = S.solve(f, psi + d * m.V, tol, maxit, nullptr, st);
-    if (s != MEMD_OK) break;
-    k_flux<<<nblk(3 * m.V), kT, 0, st>>>(L, c->ie64, psi + d * m.V, d, 1.0, 1.0 / m.a, U, 0, 1.0);
+  auto cleanup = [&]() {
+    // no scratch is released while a stream may still use it
+    for (int k = 0; k < 3; ++k)
+      if (sts[k]) cudaStreamSynchronize(sts[k]);
+    for (MgSolver& x : S) x.release();
+    for (int k = 1; k < 3; ++k)
+      if (sts[k]) cudaStreamDestroy(sts[k]);
+    if (ready) cudaEventDestroy(ready);
+  };
+  for (int k = 1; k < ns && s == MEMD_OK; ++k)
+    if (cudaStreamCreateWithFlags(&sts[k], cudaStreamNonBlocking) != cudaSuccess)
+      s = MEMD_ERR_CUDA;
+  if (s == MEMD_OK && ns > 1 &&
+      (cudaEventCreateWithFlags(&ready, cudaEventDisableTiming) != cudaSuccess ||
+       cudaEventRecord(ready, c->stream) != cudaSuccess))
+    s = MEMD_ERR_CUDA;
+  for (int k = 0; k < ns && s == MEMD_OK; ++k) {
+    // the solver's level weights come from 1/eps, written on the context's stream
+    if (k > 0 && cudaStreamWaitEvent(sts[k], ready, 0) != cudaSuccess) s = MEMD_ERR_CUDA;
+    if (s == MEMD_OK && !S[k].build(c, sts[k])) s = MEMD_ERR_OOM;
+    if (s == MEMD_OK) {
+      f[k] = S[k].alloc(m.V);
+      U[k] = S[k].alloc(3 * m.V);
+      if (!f[k] || !U[k]) s = MEMD_ERR_OOM;
+    }
+  }
+  if (s != MEMD_OK) {
+    cleanup();
+    return s;
+  }
+  memd_status st_d[3] = {MEMD_OK, MEMD_OK, MEMD_OK};
+  // cell problem d with solver k
+  auto cell_problem = [&](int d, int k) {
+    const cudaStream_t st = sts[k];
+    k_div_eps_unit<<<nblk(m.V), kT, 0, st>>>(L, c->ie64, d, 1.0 / m.a, f[k]);
+    memd_status r = S[k].solve(f[k], psi + d * m.V, tol, maxit, nullptr, st);
+    if (r != MEMD_OK) {
+      st_d[d] = r;
+      return;
+    }
+    k_flux<<<nblk(3 * m.V), kT, 0, st>>>(L, c->ie64, psi + d * m.V, d, 1.0, 1.0 / m.a, U[k], 0,
+                                         1.0);
     for (int e = 0; e < 3; ++e) {
-      launch_dot(U + e * m.V, nullptr, m.V, S.part, st);
-      launch_finish(S.part, 0, S.sc + 8 + e, st);
+      launch_dot(U[k] + e * m.V, nullptr, m.V, S[k].part, st);
+      launch_finish(S[k].part, 0, S[k].sc + 8 + e, st);
     }
     double h[3];
-    if (cudaMemcpyAsync(h, S.sc + 8, 3 * sizeof(double), cudaMemcpyDeviceToHost, st) !=
+    if (cudaMemcpyAsync(h, S[k].sc + 8, 3 * sizeof(double), cudaMemcpyDeviceToHost, st) !=
             cudaSuccess ||
         cudaStreamSynchronize(st) != cudaSuccess) {
-      s = MEMD_ERR_CUDA;
-      break;
+      st_d[d] = MEMD_ERR_CUDA;
+      return;
     }
     for (int e = 0; e < 3; ++e) eps_eff[3 * e + d] = h[e] / (double)m.V;
+  };
+  if (ns == 1) {
+    for (int d = 0; d < 3; ++d) {
+      cell_problem(d, 0);
+      if (st_d[d] != MEMD_OK) break;
+    }
+  } else {
+    std::thread t1(cell_problem, 1, 1), t2(cell_problem, 2, 2);
+    cell_problem(0, 0);
+    t1.join();
+    t2.join();
   }
-  S.release();
+  for (int d = 0; d < 3 && s == MEMD_OK; ++d) s = st_d[d];
+  // every stream's work is done (each ended with a synchronisation)
+  cleanup();
   return s;
 }
 

@@ -90,8 +90,9 @@ namespace {
 
 // device bytes a request holds while resident: double-buffered D and B,
 // 1/eps in the field precision and in FP64, the int64 ledger and transfer
-// buffer, particle arrays, plus the initial solve's scratch (released after
-// init but needed at admission)
+// buffer, particle arrays, plus the setup's multigrid scratch (released
+// after init but needed at admission; the workers solve the cell problems
+// in turn, one solver)
 int64_t footprint(const memd_server_options& o, const memd_server::Req& r) {
   const int64_t V = (int64_t)r.mesh[0] * r.mesh[1] * r.mesh[2];
   const int64_t es = o.precision == MEMD_FP32 ? 4 : 8;
@@ -188,6 +189,10 @@ memd_status admit(memd_server* s, memd_server::Req& r, cudaStream_t wst) {
 
 void worker(memd_server* s, int w) {
   cudaSetDevice(s->opt.device);  // resolved at create
+  // several workers already set systems up at once: each solves a system's
+  // cell problems in turn (three at once per worker slowed the served
+  // stream: p50 1.2-1.35 s -> 1.8-2.05 s)
+  memd::memd_mg_cells_in_turn(true);
   for (;;) {
     memd_server::Req* r = nullptr;
     {
