@@ -564,7 +564,8 @@ class Batch:
 
     def __init__(self, members, field_kernel="auto"):
         """field_kernel: "auto" (timed choice between site tiles and the row
-        kernel), "site" or "rows"."""
+        kernel; members created with the row kernel at one fixed width fix
+        it), "site" or "rows"."""
         self._L = lib()
         _live["batch"].add(self)
         self.members = list(members)
@@ -612,8 +613,9 @@ class Batch:
 
     def step_io(self, nsteps=1, thermostat=None, load=True):
         """memd_batch_step_io: every member's state from the I/O block (load),
-        nsteps batch steps, state and forces back into it; one copy each way,
-        one synchronisation."""
+        nsteps batch steps, state and forces back into it; one copy in, the
+        copies out (beside the step with load and one step), one
+        synchronisation."""
         th = None
         if thermostat is not None:
             th = Thermostat(float(thermostat[0]), float(thermostat[1]))
