@@ -551,8 +551,10 @@ def batch_line(args, world, rank, local):
             "e2e": {"value": world * links * e2e_steps / e2e_s, "unit": "link-updates/s",
                     "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                     "api": "memd_batch_step_io: one copy in (every replica's positions, "
-                           "images, velocities), one batch step, one copy out (state and "
-                           "forces), one sync"},
+                           "images, velocities) beside the field update, one batch step, "
+                           "positions and images copied out beside the transfer "
+                           "application and gather, velocities, forces and error words "
+                           "after it, one sync"},
             "clocks": clk.summary(),
             "gpu_launches": int(ks0.launches_per_step * args.steps),
             "setup_s": setup_s,
