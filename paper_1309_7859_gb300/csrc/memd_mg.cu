@@ -667,10 +667,22 @@ memd_status mg_eps_eff(memd_ctx* c, double* psi, double eps_eff[9], double tol, 
       if (st_d[d] != MEMD_OK) break;
     }
   } else {
-    std::thread t1(cell_problem, 1, 1), t2(cell_problem, 2, 2);
+    // a thread that cannot be started (no exception leaves the C ABI) is
+    // replaced by this one solving that problem after its own
+    std::thread th[2];
+    for (int k = 1; k < 3; ++k) {
+      try {
+        th[k - 1] = std::thread(cell_problem, k, k);
+      } catch (...) {
+      }
+    }
     cell_problem(0, 0);
-    t1.join();
-    t2.join();
+    for (int k = 1; k < 3; ++k) {
+      if (th[k - 1].joinable())
+        th[k - 1].join();
+      else
+        cell_problem(k, k);
+    }
   }
   for (int d = 0; d < 3 && s == MEMD_OK; ++d) s = st_d[d];
   // every stream's work is done (each ended with a synchronisation)

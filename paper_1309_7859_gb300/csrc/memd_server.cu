@@ -236,8 +236,15 @@ memd_status start_workers(memd_server* s) {
       return MEMD_ERR_CUDA;
     s->wstreams.push_back(st);
   }
-  for (int w = 0; w < nw; ++w) s->workers.emplace_back(worker, s, w);
-  return MEMD_OK;
+  // as many workers as threads can be started (no exception leaves the C ABI)
+  for (int w = 0; w < nw; ++w) {
+    try {
+      s->workers.emplace_back(worker, s, w);
+    } catch (...) {
+      break;
+    }
+  }
+  return s->workers.empty() ? MEMD_ERR_OOM : MEMD_OK;
 }
 
 void stop_workers(memd_server* s) {
