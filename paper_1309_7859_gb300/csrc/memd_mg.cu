@@ -22,7 +22,6 @@
 // FP64 throughout.
 #include <algorithm>
 #include <cmath>
-#include <thread>
 #include <vector>
 
 #include "memd_ctx.cuh"
@@ -512,13 +511,14 @@ struct MgSolver {
     launch_finish(part, 0, sc + 3, st);
   }
 
-  // x = L^-1 f (f of zero mean up to rounding; x of zero mean); stops when
-  // |r| <= tol |f| (2-norms), or, once the recursion has reached its
-  // rounding floor and the residual grows again (to 10 times its least
-  // value), when that least value was below 100 tol |f|; at most
-  // min(maxit, 400) iterations
-  memd_status solve(const double* f, double* out, double tol, int maxit, int* iters,
-                    cudaStream_t st) {
+  // A solve in stages, so that one host thread can interleave several
+  // solvers on their own streams: begin (to the first residual), then
+  // launch_step / check until done, then finish.
+  double f2 = 0.0, least = 0.0;
+  int its = 0, cap = 0;
+  bool done = false;
+
+  memd_status begin(const double* f, int maxit, cudaStream_t st) {
     const int64_t V = lv[0].L.V;
     // r = f - mean(f), x = 0, z = M r, p = z
     cudaMemcpyAsync(res, f, V * sizeof(double), cudaMemcpyDeviceToDevice, st);
@@ -545,38 +545,64 @@ struct MgSolver {
       }
       cudaGetLastError();
     }
-    double h[2] = {0, 0};
-    if (cudaMemcpyAsync(&h[1], sc + 5, sizeof(double), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+    double h = 0.0;
+    if (cudaMemcpyAsync(&h, sc + 5, sizeof(double), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
         cudaStreamSynchronize(st) != cudaSuccess)
       return MEMD_ERR_CUDA;
-    const double f2 = h[1];
-    int it = 0;
-    bool ok = f2 == 0.0;
-    double least = f2;
-    const int cap = maxit < 400 ? maxit : 400;
-    while (!ok && it < cap) {
-      if (it_graph) {
-        if (cudaGraphLaunch(it_graph, st) != cudaSuccess) return MEMD_ERR_CUDA;
-      } else {
-        iterations(st);
-      }
-      it += 2;
-      if (cudaMemcpyAsync(&h[0], sc + 3, sizeof(double), cudaMemcpyDeviceToHost, st) !=
-              cudaSuccess ||
-          cudaStreamSynchronize(st) != cudaSuccess)
-        return MEMD_ERR_CUDA;
-      ok = h[0] <= tol * tol * f2;
-      if (!ok && h[0] > 100.0 * least && least <= 1e4 * tol * tol * f2) ok = true;
-      least = std::min(least, h[0]);
+    f2 = h;
+    its = 0;
+    done = f2 == 0.0;
+    least = f2;
+    cap = maxit < 400 ? maxit : 400;
+    return MEMD_OK;
+  }
+  bool running() const { return !done && its < cap; }
+  // two iterations queued on st
+  memd_status launch_step(cudaStream_t st) {
+    if (it_graph) {
+      if (cudaGraphLaunch(it_graph, st) != cudaSuccess) return MEMD_ERR_CUDA;
+    } else {
+      iterations(st);
     }
-    if (iters) *iters = it;
+    its += 2;
+    return MEMD_OK;
+  }
+  // waits for st and tests the residual of the last step
+  memd_status check(double tol, cudaStream_t st) {
+    double h = 0.0;
+    if (cudaMemcpyAsync(&h, sc + 3, sizeof(double), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+        cudaStreamSynchronize(st) != cudaSuccess)
+      return MEMD_ERR_CUDA;
+    done = h <= tol * tol * f2;
+    if (!done && h > 100.0 * least && least <= 1e4 * tol * tol * f2) done = true;
+    least = std::min(least, h);
+    return MEMD_OK;
+  }
+  memd_status finish(double* out, int* iters, cudaStream_t st) {
+    const int64_t V = lv[0].L.V;
+    if (iters) *iters = its;
     // zero-mean solution
     launch_dot(x, nullptr, V, part, st);
     launch_finish(part, 0, sc + 6, st);
     k_sub_mean<<<nblk(V), kT, 0, st>>>(V, x, sc + 6);
     cudaMemcpyAsync(out, x, V * sizeof(double), cudaMemcpyDeviceToDevice, st);
     if (cudaGetLastError() != cudaSuccess) return MEMD_ERR_CUDA;
-    return ok ? MEMD_OK : MEMD_ERR_RELAX_NOCONV;
+    return done ? MEMD_OK : MEMD_ERR_RELAX_NOCONV;
+  }
+
+  // x = L^-1 f (f of zero mean up to rounding; x of zero mean); stops when
+  // |r| <= tol |f| (2-norms), or, once the recursion has reached its
+  // rounding floor and the residual grows again (to 100 times its least
+  // value), when that least value was below 100 tol |f|; at most
+  // min(maxit, 400) iterations
+  memd_status solve(const double* f, double* out, double tol, int maxit, int* iters,
+                    cudaStream_t st) {
+    memd_status s = begin(f, maxit, st);
+    while (s == MEMD_OK && running()) {
+      s = launch_step(st);
+      if (s == MEMD_OK) s = check(tol, st);
+    }
+    return s == MEMD_OK ? finish(out, iters, st) : s;
   }
 };
 
@@ -595,10 +621,11 @@ memd_status mg_eps_eff(memd_ctx* c, double* psi, double eps_eff[9], double tol, 
   const Mesh& m = c->mesh;
   const Lv L{m.n[0], m.n[1], m.n[2], m.V};
   // The three cell problems are independent: each gets its own solver (and
-  // scratch, built here on the calling thread), its own stream, and its own
-  // host thread, since a solve waits on its own convergence checks; they run
-  // at once, with the results of solving them in turn (which a thread set by
-  // memd_mg_cells_in_turn does, with one solver on the context's stream).
+  // scratch) and stream, and this thread interleaves them (each one's two
+  // iterations queued, then each one's residual read), so that their small
+  // multigrid launches run at once; the results are those of solving them
+  // in turn, which a thread set by memd_mg_cells_in_turn does, with one
+  // solver on the context's stream.
   const int ns = t_cells_in_turn ? 1 : 3;
   MgSolver S[3];
   double* f[3] = {nullptr, nullptr, nullptr};
@@ -632,60 +659,47 @@ memd_status mg_eps_eff(memd_ctx* c, double* psi, double eps_eff[9], double tol, 
       if (!f[k] || !U[k]) s = MEMD_ERR_OOM;
     }
   }
-  if (s != MEMD_OK) {
-    cleanup();
-    return s;
-  }
-  memd_status st_d[3] = {MEMD_OK, MEMD_OK, MEMD_OK};
-  // cell problem d with solver k
-  auto cell_problem = [&](int d, int k) {
-    const cudaStream_t st = sts[k];
-    k_div_eps_unit<<<nblk(m.V), kT, 0, st>>>(L, c->ie64, d, 1.0 / m.a, f[k]);
-    memd_status r = S[k].solve(f[k], psi + d * m.V, tol, maxit, nullptr, st);
-    if (r != MEMD_OK) {
-      st_d[d] = r;
-      return;
+  // cell problems d0 .. d0 + ns - 1, problem d0 + k with solver k
+  auto solve_cells = [&](int d0) -> memd_status {
+    memd_status r = MEMD_OK;
+    for (int k = 0; k < ns && r == MEMD_OK; ++k) {
+      k_div_eps_unit<<<nblk(m.V), kT, 0, sts[k]>>>(L, c->ie64, d0 + k, 1.0 / m.a, f[k]);
+      r = S[k].begin(f[k], maxit, sts[k]);
     }
-    k_flux<<<nblk(3 * m.V), kT, 0, st>>>(L, c->ie64, psi + d * m.V, d, 1.0, 1.0 / m.a, U[k], 0,
-                                         1.0);
-    for (int e = 0; e < 3; ++e) {
-      launch_dot(U[k] + e * m.V, nullptr, m.V, S[k].part, st);
-      launch_finish(S[k].part, 0, S[k].sc + 8 + e, st);
+    bool any = true;
+    while (r == MEMD_OK && any) {
+      any = false;
+      for (int k = 0; k < ns && r == MEMD_OK; ++k)
+        if (S[k].running()) r = S[k].launch_step(sts[k]);
+      for (int k = 0; k < ns && r == MEMD_OK; ++k)
+        if (S[k].running()) {
+          r = S[k].check(tol, sts[k]);
+          any = true;
+        }
     }
-    double h[3];
-    if (cudaMemcpyAsync(h, S[k].sc + 8, 3 * sizeof(double), cudaMemcpyDeviceToHost, st) !=
-            cudaSuccess ||
-        cudaStreamSynchronize(st) != cudaSuccess) {
-      st_d[d] = MEMD_ERR_CUDA;
-      return;
-    }
-    for (int e = 0; e < 3; ++e) eps_eff[3 * e + d] = h[e] / (double)m.V;
-  };
-  if (ns == 1) {
-    for (int d = 0; d < 3; ++d) {
-      cell_problem(d, 0);
-      if (st_d[d] != MEMD_OK) break;
-    }
-  } else {
-    // a thread that cannot be started (no exception leaves the C ABI) is
-    // replaced by this one solving that problem after its own
-    std::thread th[2];
-    for (int k = 1; k < 3; ++k) {
-      try {
-        th[k - 1] = std::thread(cell_problem, k, k);
-      } catch (...) {
+    for (int k = 0; k < ns && r == MEMD_OK; ++k) {
+      const int d = d0 + k;
+      const cudaStream_t st = sts[k];
+      r = S[k].finish(psi + d * m.V, nullptr, st);
+      if (r != MEMD_OK) break;
+      k_flux<<<nblk(3 * m.V), kT, 0, st>>>(L, c->ie64, psi + d * m.V, d, 1.0, 1.0 / m.a, U[k],
+                                           0, 1.0);
+      for (int e = 0; e < 3; ++e) {
+        launch_dot(U[k] + e * m.V, nullptr, m.V, S[k].part, st);
+        launch_finish(S[k].part, 0, S[k].sc + 8 + e, st);
       }
+      double h[3];
+      if (cudaMemcpyAsync(h, S[k].sc + 8, 3 * sizeof(double), cudaMemcpyDeviceToHost, st) !=
+              cudaSuccess ||
+          cudaStreamSynchronize(st) != cudaSuccess) {
+        r = MEMD_ERR_CUDA;
+        break;
+      }
+      for (int e = 0; e < 3; ++e) eps_eff[3 * e + d] = h[e] / (double)m.V;
     }
-    cell_problem(0, 0);
-    for (int k = 1; k < 3; ++k) {
-      if (th[k - 1].joinable())
-        th[k - 1].join();
-      else
-        cell_problem(k, k);
-    }
-  }
-  for (int d = 0; d < 3 && s == MEMD_OK; ++d) s = st_d[d];
-  // every stream's work is done (each ended with a synchronisation)
+    return r;
+  };
+  for (int d0 = 0; d0 < 3 && s == MEMD_OK; d0 += ns) s = solve_cells(d0);
   cleanup();
   return s;
 }
